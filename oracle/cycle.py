@@ -1,0 +1,208 @@
+"""Oracle Wave-ADR cycle (Algorithm 1) with the ADR V-cycle correction."""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse as sp
+
+from .operators import (Level, adr_apply, adr_coefficients, coarse_size,
+                        helmholtz_apply, helmholtz_diag, inject, prolong, restrict,
+                        sponge_gamma, missing_neighbours)
+from .smoothers import (alpha_spectral, chebyshev, chebyshev_interval, gmres,
+                        jacobi, jacobi_weight_default, lambda_max_gershgorin)
+
+
+@dataclass
+class CycleParams:
+    """Schedule constants.  Defaults follow Algorithm 1 (one Jacobi sweep on
+    level 1, five Chebyshev steps before and after on levels 2 and >= 4, no
+    smoothing on level 3), Section 3.2.2 (one ADR V-cycle with one GMRES(3)
+    sweep before and after), Section 4.2 (M = 8 ADR corrections) and a dense
+    LU on the coarsest level."""
+    n_cmax: int = 15               # coarsen while n > n_cmax
+    jacobi_iters: int = 1
+    cheb_iters: int = 5
+    coarse: str = "lu"             # "lu" | "cheb"
+    coarse_cheb_iters: int = 10
+    M: int = 8                     # ADR correction steps at level 2
+    gmres_m: int = 3
+    adr: bool = True               # False: plain wave cycle
+    omega_jacobi: float | None = None      # None: (4-kappa)/(5-kappa)
+    alphas: dict = field(default_factory=dict)  # level -> alpha; missing: spectral
+
+
+def build_sizes(n: int, n_cmax: int):
+    sizes = [n]
+    while sizes[-1] > n_cmax and coarse_size(sizes[-1]) >= 1:
+        sizes.append(coarse_size(sizes[-1]))
+    return sizes
+
+
+def helmholtz_sparse(lev: Level) -> sp.csr_matrix:
+    """Independent assembly of the Helmholtz matrix, node by node, from the
+    5-point stencil and the boundary rules of Section 2 (used to pin the
+    vectorised stencil apply and for the dense coarsest-level LU)."""
+    n, h = lev.n, lev.h
+    rows, cols, vals = [], [], []
+    ih2 = 1.0 / (h * h)
+    for j in range(n):
+        for i in range(n):
+            p = j * n + i
+            kk = lev.k[j, i]
+            diag = 4.0 - h * h * kk * kk + 0j
+            for (jj, ii) in ((j, i - 1), (j, i + 1), (j - 1, i), (j + 1, i)):
+                if 0 <= jj < n and 0 <= ii < n:
+                    rows.append(p); cols.append(jj * n + ii); vals.append(-ih2)
+                elif lev.bc == "abc1":
+                    # ghost value (1 + i conv k h) u_b moved onto the diagonal
+                    diag -= 1.0 + 1j * lev.conv * kk * h
+            if lev.bc == "sponge":
+                diag -= 1j * lev.conv * h * h * lev.omega * lev.gamma[j, i] * \
+                    (kk / lev.omega) ** 2
+            if lev.shift:
+                diag -= 1j * lev.conv * lev.shift * h * h * kk * kk
+            rows.append(p); cols.append(p); vals.append(diag * ih2)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n * n, n * n), dtype=np.complex128)
+
+
+def adr_sparse(lev: Level) -> sp.csr_matrix:
+    """Assembly of the upwind ADR matrix from its coefficients."""
+    c = adr_coefficients(lev)
+    n = lev.n
+    rows, cols, vals = [], [], []
+    for j in range(n):
+        for i in range(n):
+            p = j * n + i
+            rows.append(p); cols.append(p); vals.append(c.d[j, i])
+            for (jj, ii, cf) in ((j, i - 1, c.cW), (j, i + 1, c.cE),
+                                 (j - 1, i, c.cS), (j + 1, i, c.cN)):
+                if 0 <= jj < n and 0 <= ii < n:
+                    rows.append(p); cols.append(jj * n + ii); vals.append(cf[j, i])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n * n, n * n), dtype=np.complex128)
+
+
+class Hierarchy:
+    """Levels 1..L of one problem, the per-level weights and the coarsest
+    LU factors (Algorithm 1: re-discretised operator A_H on every level;
+    coefficients by injection)."""
+
+    def __init__(self, n: int, k: np.ndarray, phi: np.ndarray, omega: float,
+                 bc: str = "abc1", params: CycleParams | None = None,
+                 conv: int = 1, shift: float = 0.0):
+        self.p = params or CycleParams()
+        sizes = build_sizes(n, self.p.n_cmax)
+        self.L = len(sizes)
+        gamma = sponge_gamma(n, omega) if bc == "sponge" else np.zeros((n, n))
+        self.levels: list[Level] = []
+        kk, ph, ga = np.asarray(k, float), np.asarray(phi, float), gamma
+        for l, nl in enumerate(sizes):
+            if l > 0:
+                kk, ph, ga = inject(kk), inject(ph), inject(ga)
+            self.levels.append(Level(n=nl, h=1.0 / (nl + 1), k=kk, phi=ph, gamma=ga,
+                                     omega=float(omega), bc=bc, conv=conv, shift=shift))
+        f = self.levels[0]
+        self.omega_j = (self.p.omega_jacobi if self.p.omega_jacobi is not None
+                        else jacobi_weight_default(f.h, float(np.max(f.k))))
+        self.lam_max = {}
+        self.alpha = {}
+        for l in range(2, self.L + 1):
+            if self._uses_cheb(l):
+                lev = self.levels[l - 1]
+                self.lam_max[l] = lambda_max_gershgorin(lev)
+                self.alpha[l] = self.p.alphas.get(
+                    l, alpha_spectral(lev.n, lev.h, float(np.max(lev.k))))
+        self.adr = {}
+        self.mod = None
+        if self.p.adr and self.L >= 3:
+            for l in range(2, self.L + 1):
+                self.adr[l] = adr_coefficients(self.levels[l - 1])
+            lv2 = self.levels[1]
+            self.mod = np.exp(1j * conv * omega * lv2.phi)   # e^{+i conv w phi_2}
+        cl = self.levels[-1]
+        self.lu_helm = scipy.linalg.lu_factor(helmholtz_sparse(cl).toarray())
+        self.lu_adr = (scipy.linalg.lu_factor(adr_sparse(cl).toarray())
+                       if self.adr else None)
+
+    # ------------------------------------------------------------ roles
+    def _uses_cheb(self, l: int) -> bool:
+        if l == 1:
+            return False
+        if l == self.L:
+            return self.p.coarse == "cheb"
+        return l != 3
+
+    def weights(self):
+        """The smoother weights [omega_J, alpha_l for Chebyshev levels]."""
+        return [self.omega_j] + [self.alpha[l] for l in sorted(self.alpha)]
+
+    def lev(self, l: int) -> Level:
+        return self.levels[l - 1]
+
+    # ------------------------------------------------------------ pieces
+    def cheb(self, l, u, g, q):
+        a, b = chebyshev_interval(self.lam_max[l], self.alpha[l])
+        return chebyshev(self.lev(l), u, g, a, b, q)
+
+    def coarse_helmholtz(self, u, g):
+        lev = self.lev(self.L)
+        if self.p.coarse == "lu":
+            r = g - helmholtz_apply(lev, u)
+            return u + scipy.linalg.lu_solve(self.lu_helm, r.ravel()).reshape(r.shape)
+        return self.cheb(self.L, u, g, self.p.coarse_cheb_iters)
+
+    def adr_vcycle(self, l: int, b: np.ndarray) -> np.ndarray:
+        """ADR cycle (Section 3.2.2): one V-cycle on the upwind ADR operator
+        from level l down to L, one GMRES(3) sweep before and after the
+        coarse-grid correction, exact solve on the coarsest level."""
+        if l == self.L:
+            return scipy.linalg.lu_solve(self.lu_adr, b.ravel()).reshape(b.shape)
+        c = self.adr[l]
+        op = lambda v: adr_apply(c, v)
+        x = gmres(op, b, None, self.p.gmres_m)
+        r = b - op(x)
+        ec = self.adr_vcycle(l + 1, restrict(r))
+        x = x + prolong(ec, self.lev(l).n)
+        x = gmres(op, b, x, self.p.gmres_m)
+        return x
+
+    def adr_correction(self, u2: np.ndarray, g2: np.ndarray) -> np.ndarray:
+        """Algorithm 1's ADR correction at level 2, repeated M times
+        (Section 4.2): r = g - A u; r_hat = r e^{-i conv w phi};
+        a = ADR cycle(r_hat); u <- u + a e^{+i conv w phi}."""
+        lev = self.lev(2)
+        for _ in range(self.p.M):
+            r = g2 - helmholtz_apply(lev, u2)
+            a = self.adr_vcycle(2, np.conj(self.mod) * r)
+            u2 = u2 + self.mod * a
+        return u2
+
+    def cycle(self, u: np.ndarray, g: np.ndarray, l: int = 1) -> np.ndarray:
+        """One Wave-ADR cycle on level l (Algorithm 1)."""
+        lev = self.lev(l)
+        if l == self.L:
+            return self.coarse_helmholtz(u, g)
+        # pre-smoothing
+        if l == 1:
+            u = jacobi(lev, u, g, self.omega_j, self.p.jacobi_iters)
+        elif l != 3:
+            u = self.cheb(l, u, g, self.p.cheb_iters)
+        # coarse-grid correction with zero initial guess
+        r = g - helmholtz_apply(lev, u)
+        rc = restrict(r)
+        ec = self.cycle(np.zeros_like(rc), rc, l + 1)
+        u = u + prolong(ec, lev.n)
+        # post-smoothing
+        if l == 1:
+            u = jacobi(lev, u, g, self.omega_j, self.p.jacobi_iters)
+        elif l == 2:
+            u = self.cheb(l, u, g, self.p.cheb_iters)
+            if self.adr:
+                u = self.adr_correction(u, g)
+        elif l != 3:
+            u = self.cheb(l, u, g, self.p.cheb_iters)
+        return u
+
+    def residual(self, u, g):
+        return g - helmholtz_apply(self.lev(1), u)
