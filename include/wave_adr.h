@@ -1,0 +1,208 @@
+/*
+ * wave_adr.h -- C ABI of the GB300 (sm_103a) Wave-ADR multigrid library.
+ *
+ * Method: Cui, Jiang, Shu, "A Neural Multigrid Solver for Helmholtz equations
+ * with high wavenumber and heterogeneous media" (arXiv 2404.02493).  The
+ * library implements the solve phase on uniform 2D grids: the 5-point
+ * Helmholtz operator (Section 2), the wave cycle smoothers (damped Jacobi,
+ * eq. sjac; Chebyshev semi-iteration on the normal equations, eq. cheb),
+ * full-weighting restriction and bilinear prolongation (Section 3.1.2,
+ * Section 3.3), the ADR correction (eq. Rytov, eq. ADR, eq. upwind) solved by
+ * one ADR V-cycle with GMRES(3) smoothing (Section 3.2.2) and repeated M
+ * times (Section 4.2), inside the Wave-ADR cycle of Algorithm 1, and outer
+ * iterations around it (Section 4.3.1).  The phase field phi and the
+ * smoother weights are inputs; no neural network runs here.
+ *
+ * Conventions
+ *   - Grid: n x n interior nodes of the unit square, h = 1/(n+1), node (i, j)
+ *     at ((i+1)h, (j+1)h).  User arrays are dense row-major, index j*n + i
+ *     (row j = y).  Batched calls concatenate the instances' arrays in the
+ *     order they were given to mg_setup.
+ *   - Complex vectors are interleaved (re, im): complex128 (double[2]) for
+ *     MG_PREC_FP64 handles, complex64 (float[2]) for the cycle of
+ *     MG_PREC_MIXED handles.  mg_solve always takes complex128.
+ *   - Sign convention: the characteristic error is a*exp(+i*omega*phi); the
+ *     absorbing boundary is d_n u = +i k u (ghost u_g = (1 + i k h) u_b);
+ *     sponge damping enters as -i*omega*gamma*s^2.  This is the complex
+ *     conjugate of the signs printed in eq. sponge / eq. ADR; with real data
+ *     the solutions are conjugates and iteration counts are identical.
+ *   - k(x) = omega * s(x): `omega` is the scalar reference frequency (max k),
+ *     s the dimensionless slowness.
+ *
+ * Pointers: unless stated otherwise a pointer argument may be device memory
+ * or host memory (pageable or pinned); host memory is staged through the
+ * handle's workspace with copies on `stream`.  The caller owns every
+ * pointer it passes; the handle owns its workspace (levels, coefficient
+ * fields, coarsest-level factors), allocated in mg_setup and freed by
+ * mg_destroy.
+ *
+ * Errors: functions return MG_OK (0) or a negative MG_E* code; the text of
+ * the last error is available from mg_last_error().  After MG_ECUDA the
+ * handle should be destroyed.
+ */
+#ifndef WAVE_ADR_H
+#define WAVE_ADR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_handle mg_handle;
+typedef void* mg_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+enum {
+    MG_OK = 0,
+    MG_EINVAL = -1,      /* bad argument (size, pointer, non-finite input) */
+    MG_ECUDA = -2,       /* CUDA runtime error */
+    MG_ENOMEM = -3,      /* device allocation failed */
+    MG_ENOTCONV = -4,    /* mg_solve reached maxit */
+    MG_EDIVERGED = -5,   /* residual not finite or grew by > 1e3 */
+    MG_EUNSUPPORTED = -7 /* option not implemented for this handle */
+};
+
+enum { MG_BC_DIRICHLET = 0, MG_BC_ABC1 = 1, MG_BC_SPONGE = 2 };
+enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 };
+enum { MG_OUTER_STATIONARY = 0, MG_OUTER_IR = 1, MG_OUTER_FGMRES = 2 };
+enum { MG_COARSE_LU = 0, MG_COARSE_CHEB = 1 };
+
+#define MG_MAX_LEVELS 16
+
+/* Schedule constants.  mg_default_params fills the paper's values:
+ * Algorithm 1 (1 Jacobi sweep on level 1; 5 Chebyshev steps before and after
+ * on levels 2 and >= 4; nothing on level 3), Section 3.2.2 (one GMRES(3)
+ * sweep before and after the coarse correction of the ADR V-cycle),
+ * Section 4.2 (M = 8 ADR corrections), Section 4.3.1 (FGMRES restart 20,
+ * tolerance 1e-6). */
+typedef struct mg_params {
+    int precision;          /* MG_PREC_FP64 | MG_PREC_MIXED (complex-FP32 cycle, FP64 outer) */
+    int n_cmax;             /* coarsen while n > n_cmax (default 15); coarsest n^2 <= 1024 */
+    int jacobi_iters;       /* 1 */
+    int cheb_iters;         /* 5 (<= 16) */
+    int coarse;             /* MG_COARSE_LU (dense FP64 LU) | MG_COARSE_CHEB (Algorithm 1, q=10) */
+    int coarse_cheb_iters;  /* 10 */
+    int M;                  /* ADR corrections at level 2 (8) */
+    int adr;                /* 1: Wave-ADR cycle; 0: plain wave cycle */
+    double omega_jacobi;    /* <= 0: (4-kappa)/(5-kappa), kappa = h^2 max k^2 */
+    double alpha[MG_MAX_LEVELS]; /* alpha[l-1] for level l; <= 0: spectral default */
+    int outer;              /* MG_OUTER_STATIONARY | MG_OUTER_IR | MG_OUTER_FGMRES */
+    int restart;            /* FGMRES restart length (20) */
+    int maxit;              /* outer iterations (cycles) limit */
+    double tol;             /* relative residual ||g - A u|| / ||g|| */
+    double shift;           /* shifted Helmholtz: adds -i*shift*k^2 (Section 4.3.2; 0 = off) */
+    int use_graph;          /* 1: replay the cycle as a captured CUDA graph */
+} mg_params;
+
+/* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */
+typedef struct mg_instance {
+    int n;                  /* interior nodes per side, n > n_cmax */
+    double omega;           /* reference angular frequency (= max k), > 0 */
+    const double* k;        /* n*n wavenumber field k(x) > 0 (FP64) */
+    const double* phi;      /* n*n phase field phi (FP64); eikonal travel time */
+    int bc;                 /* MG_BC_* */
+} mg_instance;
+
+typedef struct mg_solve_info {
+    int iterations;         /* cycles applied */
+    int status;             /* MG_OK, MG_ENOTCONV, MG_EDIVERGED */
+    double rel_residual;    /* final ||g - A u|| / ||g|| (FP64) */
+    double* history;        /* optional caller buffer of history_len doubles */
+    int history_len;        /* entries available / written (relative residuals) */
+    double seconds;         /* device time of the solve loop */
+} mg_solve_info;
+
+/* Fill the defaults listed above. */
+void mg_default_params(mg_params* p);
+
+/* Text of the last error of this thread (never NULL). */
+const char* mg_last_error(void);
+
+/* Build the hierarchy for `ninst` independent problems solved together
+ * (batched launches; sizes may differ).  Per instance and level the
+ * coefficients are injected from the fine grid (Algorithm 1's re-discretised
+ * operator), the ADR coefficients (eq. ADR with the upwind stencil of
+ * Section 3.3 and the finite-difference phase derivatives of Section 3.2.1)
+ * and exp(i omega phi) at level 2 are formed in FP64, the Chebyshev interval
+ * [lambda_max/alpha, lambda_max] (Section 3.1.1) is set from the Gershgorin
+ * bound and the spectral alpha rule, and the coarsest Helmholtz and ADR
+ * operators are factored by a device-side dense FP64 LU with partial
+ * pivoting.  Synchronises `stream`.  Errors: MG_EINVAL (n <= n_cmax, n_L^2 >
+ * 1024, omega <= 0, null pointers, non-finite k or phi), MG_ENOMEM,
+ * MG_ECUDA. */
+int mg_setup(mg_handle** h, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream);
+
+/* u <- cycle^ncycles(u, g) (Algorithm 1 from level 1), in the handle's cycle
+ * precision (complex128 for FP64 handles, complex64 for MIXED handles).
+ * u: in/out, g: in; dense concatenated layout.  Asynchronous on `stream`
+ * when both pointers are device memory. */
+int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream);
+
+/* Solve A u = g to ||g - A u|| / ||g|| < p->tol with the outer iteration
+ * chosen in mg_params: MG_OUTER_STATIONARY / MG_OUTER_IR (u += ||r||
+ * cycle(0, r/||r||), the residual and update in FP64), MG_OUTER_FGMRES
+ * (flexible GMRES(restart) preconditioned by one cycle from zero).  u is the
+ * complex128 initial guess (zeros: the paper's zero start) and receives the
+ * solution; g is complex128.  Synchronises `stream` once per outer
+ * iteration.  Returns MG_OK, MG_ENOTCONV or MG_EDIVERGED (also in info). */
+int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_stream stream);
+
+/* Free the workspace. */
+void mg_destroy(mg_handle* h);
+
+/* ------------------------------------------------------------------------
+ * Level operations: single-instance entry points into the same kernels the
+ * cycle uses, for verification.  All vectors are dense n_l x n_l in the
+ * cycle precision of the handle; `inst` selects the instance, `level` is
+ * 1-based.  Synchronous with respect to `stream` only through copies.
+ * ---------------------------------------------------------------------- */
+
+/* Number of levels L of an instance (Algorithm 1's max-level). */
+int mg_num_levels(const mg_handle* h, int inst);
+/* n_l of level `level`. */
+int mg_level_n(const mg_handle* h, int inst, int level);
+/* Setup scalars of a level: out[0] = lambda_max (Gershgorin bound of A^*A),
+ * out[1] = alpha, out[2] = Jacobi weight, out[3] = h.  Returns count. */
+int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int nout);
+
+enum { MG_OP_A = 0, MG_OP_AH = 1, MG_OP_L = 2, MG_OP_LT = 3, MG_OP_LH = 4 };
+/* y = op(x): A (5-point Helmholtz, Section 2), A^* (eq. cheb), L (upwind ADR
+ * operator, eq. ADR / eq. upwind; levels >= 2), L^T, L^*. */
+int mg_apply(mg_handle* h, int inst, int level, int op, const void* x, void* y, mg_stream stream);
+/* r = g - A u on a level (Algorithm 1, residual step). */
+int mg_residual(mg_handle* h, int inst, int level, const void* u, const void* g, void* r, mg_stream stream);
+/* rc = I_h^H (g - A u): full weighting (Section 3.1.2) of the residual,
+ * written to level+1 (size n_{l+1}). */
+int mg_restrict_residual(mg_handle* h, int inst, int level, const void* u, const void* g, void* rc,
+                         mg_stream stream);
+/* u <- u + I_H^h e: bilinear prolongation (Section 3.1.2) of the level+1
+ * vector e. */
+int mg_prolong_add(mg_handle* h, int inst, int level, const void* e, void* u, mg_stream stream);
+/* out = u + w D^{-1} (g - A u) on level 1 (eq. sjac). */
+int mg_jacobi(mg_handle* h, int inst, const void* u, const void* g, void* out, mg_stream stream);
+/* u <- Chebyshev(u, g, alpha_l, iters) on level >= 2 (eq. cheb). */
+int mg_chebyshev(mg_handle* h, int inst, int level, void* u, const void* g, int iters, mg_stream stream);
+/* x <- GMRES(3) sweep on L_l x = b from x (x_nonzero = 0: from zero)
+ * (Section 3.2.2). */
+int mg_gmres3(mg_handle* h, int inst, int level, const void* b, void* x, int x_nonzero, mg_stream stream);
+/* a = ADR V-cycle(b) on levels 2..L (Section 3.2.2), b and a on level 2. */
+int mg_adr_vcycle(mg_handle* h, int inst, const void* b, void* a, mg_stream stream);
+/* One ADR correction at level 2: u <- u + e^{i w phi} ADRV(e^{-i w phi}(g - A u))
+ * (Algorithm 1, post-smoothing on level 2). */
+int mg_adr_correction(mg_handle* h, int inst, void* u, const void* g, mg_stream stream);
+/* x = A_L^{-1} b (which = 0, Helmholtz) or L_L^{-1} b (which = 1, ADR) on
+ * the coarsest level, with the dense FP64 LU factors. */
+int mg_coarse_solve(mg_handle* h, int inst, int which, const void* b, void* x, mg_stream stream);
+
+/* Number of kernel launches of one cycle (counted when the schedule is
+ * emitted). */
+int mg_cycle_launches(const mg_handle* h);
+
+/* sizeof(mg_params), sizeof(mg_instance), sizeof(mg_solve_info): lets a
+ * binding check its struct layout.  Needs no GPU. */
+void mg_abi_sizes(size_t* params, size_t* instance, size_t* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVE_ADR_H */

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of the C ABI declared in include/wave_adr.h.
+
+Only argument marshalling happens here: arrays are passed as raw pointers
+(torch CUDA tensors, torch CPU tensors or NumPy arrays), every step of the
+method runs in the CUDA library.  The library must have been built
+(`paper_2404_02493_gb300.build.build()`); importing this module without it
+raises, there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MG_OK, MG_EINVAL, MG_ECUDA, MG_ENOMEM, MG_ENOTCONV, MG_EDIVERGED, MG_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -7
+MG_BC = {"dirichlet": 0, "abc1": 1, "sponge": 2}
+MG_PREC_FP64, MG_PREC_MIXED = 0, 1
+MG_OUTER = {"stationary": 0, "ir": 1, "fgmres": 2}
+MG_COARSE_LU, MG_COARSE_CHEB = 0, 1
+MG_OP = {"A": 0, "AH": 1, "L": 2, "LT": 3, "LH": 4}
+MG_MAX_LEVELS = 16
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int), ("n_cmax", ctypes.c_int), ("jacobi_iters", ctypes.c_int),
+        ("cheb_iters", ctypes.c_int), ("coarse", ctypes.c_int), ("coarse_cheb_iters", ctypes.c_int),
+        ("M", ctypes.c_int), ("adr", ctypes.c_int), ("omega_jacobi", ctypes.c_double),
+        ("alpha", ctypes.c_double * MG_MAX_LEVELS), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
+        ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("shift", ctypes.c_double),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+class MgInstance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("omega", ctypes.c_double), ("k", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p), ("bc", ctypes.c_int)]
+
+
+class MgSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libwaveadr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB} missing (run build())")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "mg_default_params": (None, [ctypes.POINTER(MgParams)]),
+        "mg_last_error": (ctypes.c_char_p, []),
+        "mg_setup": (ip, [ctypes.POINTER(vp), ctypes.POINTER(MgInstance), ip, ctypes.POINTER(MgParams), vp]),
+        "mg_cycle": (ip, [vp, vp, vp, ip, vp]),
+        "mg_solve": (ip, [vp, vp, vp, ctypes.POINTER(MgSolveInfo), vp]),
+        "mg_destroy": (None, [vp]),
+        "mg_num_levels": (ip, [vp, ip]),
+        "mg_level_n": (ip, [vp, ip, ip]),
+        "mg_level_scalars": (ip, [vp, ip, ip, ctypes.POINTER(dp), ip]),
+        "mg_apply": (ip, [vp, ip, ip, ip, vp, vp, vp]),
+        "mg_residual": (ip, [vp, ip, ip, vp, vp, vp, vp]),
+        "mg_restrict_residual": (ip, [vp, ip, ip, vp, vp, vp, vp]),
+        "mg_prolong_add": (ip, [vp, ip, ip, vp, vp, vp]),
+        "mg_jacobi": (ip, [vp, ip, vp, vp, vp, vp]),
+        "mg_chebyshev": (ip, [vp, ip, ip, vp, vp, ip, vp]),
+        "mg_gmres3": (ip, [vp, ip, ip, vp, vp, ip, vp]),
+        "mg_adr_vcycle": (ip, [vp, ip, vp, vp, vp]),
+        "mg_adr_correction": (ip, [vp, ip, vp, vp, vp]),
+        "mg_coarse_solve": (ip, [vp, ip, ip, vp, vp, vp]),
+        "mg_cycle_launches": (ip, [vp]),
+        "mg_abi_sizes": (None, [ctypes.POINTER(ctypes.c_size_t)] * 3),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared by the C ABI (the binding's signature table)."""
+    return ["mg_default_params", "mg_last_error", "mg_setup", "mg_cycle", "mg_solve", "mg_destroy",
+            "mg_num_levels", "mg_level_n", "mg_level_scalars", "mg_apply", "mg_residual",
+            "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
+            "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes"]
+
+
+class MgError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().mg_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != MG_OK:
+        raise MgError(rc, where)
+    return rc
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or a contiguous NumPy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def default_params(**kw) -> MgParams:
+    p = MgParams()
+    load().mg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "alpha":
+            for l, a in v.items():
+                p.alpha[l - 1] = a
+        elif k == "precision" and isinstance(v, str):
+            p.precision = {"fp64": MG_PREC_FP64, "mixed": MG_PREC_MIXED}[v]
+        elif k == "outer" and isinstance(v, str):
+            p.outer = MG_OUTER[v]
+        elif k == "coarse" and isinstance(v, str):
+            p.coarse = {"lu": MG_COARSE_LU, "cheb": MG_COARSE_CHEB}[v]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+# ------------------------------------------------------------------ C names
+def mg_setup(instances, params: MgParams, stream=None):
+    """instances: sequence of (n, omega, k, phi, bc) with k, phi float64 arrays
+    (device tensors or host arrays).  Returns the opaque handle pointer."""
+    lib = load()
+    arr = (MgInstance * len(instances))()
+    keep = []
+    for i, (n, omega, k, phi, bc) in enumerate(instances):
+        keep += [k, phi]
+        arr[i].n = int(n)
+        arr[i].omega = float(omega)
+        arr[i].k = _ptr(k).value
+        arr[i].phi = _ptr(phi).value
+        arr[i].bc = MG_BC[bc] if isinstance(bc, str) else int(bc)
+    h = ctypes.c_void_p()
+    _check(lib.mg_setup(ctypes.byref(h), arr, len(instances), ctypes.byref(params), _stream(stream)), "mg_setup")
+    return h
+
+
+def mg_destroy(h):
+    load().mg_destroy(h)
+
+
+def mg_cycle(h, u, g, ncycles=1, stream=None):
+    return _check(load().mg_cycle(h, _ptr(u), _ptr(g), int(ncycles), _stream(stream)), "mg_cycle")
+
+
+def mg_solve(h, u, g, history_len=0, stream=None):
+    """Returns (status, iterations, rel_residual, history list, seconds);
+    MG_ENOTCONV / MG_EDIVERGED are reported in status, not raised."""
+    info = MgSolveInfo()
+    hist = (ctypes.c_double * max(history_len, 1))()
+    info.history = hist if history_len > 0 else None
+    info.history_len = history_len
+    rc = load().mg_solve(h, _ptr(u), _ptr(g), ctypes.byref(info), _stream(stream))
+    if rc not in (MG_OK, MG_ENOTCONV, MG_EDIVERGED):
+        _check(rc, "mg_solve")
+    return rc, info.iterations, info.rel_residual, list(hist[:info.history_len]), info.seconds
+
+
+def mg_num_levels(h, inst=0):
+    r = load().mg_num_levels(h, inst)
+    return _check(r, "mg_num_levels") if r < 0 else r
+
+
+def mg_level_n(h, inst, level):
+    r = load().mg_level_n(h, inst, level)
+    return _check(r, "mg_level_n") if r < 0 else r
+
+
+def mg_level_scalars(h, inst, level):
+    out = (ctypes.c_double * 4)()
+    load().mg_level_scalars(h, inst, level, out, 4)
+    return {"lam_max": out[0], "alpha": out[1], "omega_j": out[2], "h": out[3]}
+
+
+def mg_apply(h, inst, level, op, x, y, stream=None):
+    op = MG_OP[op] if isinstance(op, str) else op
+    _check(load().mg_apply(h, inst, level, op, _ptr(x), _ptr(y), _stream(stream)), "mg_apply")
+
+
+def mg_residual(h, inst, level, u, g, r, stream=None):
+    _check(load().mg_residual(h, inst, level, _ptr(u), _ptr(g), _ptr(r), _stream(stream)), "mg_residual")
+
+
+def mg_restrict_residual(h, inst, level, u, g, rc, stream=None):
+    _check(load().mg_restrict_residual(h, inst, level, _ptr(u), _ptr(g), _ptr(rc), _stream(stream)),
+           "mg_restrict_residual")
+
+
+def mg_prolong_add(h, inst, level, e, u, stream=None):
+    _check(load().mg_prolong_add(h, inst, level, _ptr(e), _ptr(u), _stream(stream)), "mg_prolong_add")
+
+
+def mg_jacobi(h, inst, u, g, out, stream=None):
+    _check(load().mg_jacobi(h, inst, _ptr(u), _ptr(g), _ptr(out), _stream(stream)), "mg_jacobi")
+
+
+def mg_chebyshev(h, inst, level, u, g, iters, stream=None):
+    _check(load().mg_chebyshev(h, inst, level, _ptr(u), _ptr(g), int(iters), _stream(stream)), "mg_chebyshev")
+
+
+def mg_gmres3(h, inst, level, b, x, x_nonzero, stream=None):
+    _check(load().mg_gmres3(h, inst, level, _ptr(b), _ptr(x), int(bool(x_nonzero)), _stream(stream)), "mg_gmres3")
+
+
+def mg_adr_vcycle(h, inst, b, a, stream=None):
+    _check(load().mg_adr_vcycle(h, inst, _ptr(b), _ptr(a), _stream(stream)), "mg_adr_vcycle")
+
+
+def mg_adr_correction(h, inst, u, g, stream=None):
+    _check(load().mg_adr_correction(h, inst, _ptr(u), _ptr(g), _stream(stream)), "mg_adr_correction")
+
+
+def mg_coarse_solve(h, inst, which, b, x, stream=None):
+    _check(load().mg_coarse_solve(h, inst, int(which), _ptr(b), _ptr(x), _stream(stream)), "mg_coarse_solve")
+
+
+def mg_cycle_launches(h):
+    return load().mg_cycle_launches(h)
+
+
+def mg_abi_sizes():
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    load().mg_abi_sizes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value

@@ -1,0 +1,124 @@
+// Host-side state of one mg_handle (internal; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "../../include/wave_adr.h"
+
+namespace wadr {
+
+constexpr int MAXB = 2048;          // partial-sum capacity (blocks per segment)
+constexpr int MAX_LEVELS = 16;
+
+struct LevelHost {
+    int n = 0, pitch = 0;
+    double h = 0;
+    size_t slot_stride = 0;         // elements
+    int nslot = 0;
+    void* vec = nullptr;            // slots (cycle precision)
+    void* kf = nullptr;             // k (cycle precision)
+    void* sig = nullptr;            // sponge term (cycle precision) or null
+    void* adr = nullptr;            // ADR quads (cycle precision) or null
+    void* mod = nullptr;            // level 2 modulation (cycle precision) or null
+    double* k64 = nullptr;          // k in FP64 (setup, outer loop at level 1)
+    double* phi64 = nullptr;        // phi in FP64 (setup, adjoint)
+    double* sig64 = nullptr;        // sponge term in FP64 or null
+    double2* inv_helm = nullptr;    // coarsest only
+    double2* inv_adr = nullptr;
+    double lam_max = 0, alpha = 0;  // Chebyshev interval (levels with Chebyshev)
+    int cheb = 0;                   // uses Chebyshev smoothing
+    int desc = -1;                  // index in the cycle descriptor table
+};
+
+struct InstHost {
+    int n = 0, L = 0, bc = 0;
+    double omega = 0;
+    double omega_j = 0;
+    std::vector<LevelHost> lv;      // lv[0] = level 1
+    // outer FP64 level-1 vectors (slots SU, SG, SD, SX2)
+    void* outer_vec = nullptr;
+    size_t outer_stride = 0;
+    int outer_desc = -1;
+    long long off = 0;              // offset of this instance in user arrays (elements)
+};
+
+struct SegTable {
+    Seg* d = nullptr;
+    int nseg = 0, nblocks = 0;
+};
+
+struct Handle {
+    mg_params p{};
+    int prec = MG_PREC_FP64;        // cycle precision
+    std::vector<InstHost> inst;
+    int Lmax = 0;
+    // descriptor tables (device) and host copies
+    std::vector<LevelDesc> hdesc;   // cycle levels of all instances
+    LevelDesc* ddesc = nullptr;
+    std::vector<LevelDesc> houter;  // outer FP64 level-1 descriptors
+    LevelDesc* douter = nullptr;
+    double* scal = nullptr;         // [ndesc + ninst][S::SIZE]
+    double2* part = nullptr;        // [ndesc + ninst][MAXB][MAXDOT]
+    unsigned* counter = nullptr;    // [ndesc + ninst][NCOUNTERS]
+    std::map<std::string, SegTable> segs;
+    std::vector<void*> allocs;      // everything cudaMalloc'ed
+    long long total_elems = 0;      // sum of n^2 over instances
+    // graphs
+    cudaGraphExec_t g_cycle0 = nullptr;     // cycle from u = 0 (level-1 SG -> SD)
+    cudaGraphExec_t g_irstep = nullptr;     // scale + cycle + update + residual
+    cudaStream_t g_stream = nullptr;
+    int launches_cycle = 0;                 // kernels of the last emitted cycle
+    // pinned host scratch for scalars
+    double* hpin = nullptr;
+    std::string last_error;
+
+    void* alloc(size_t bytes);
+    const SegTable& seg(const std::vector<int>& descs, bool outer, int pts_per_block);
+    const SegTable& seg_rows(const std::vector<int>& descs, int rows_per_block);
+};
+
+// level operations of EngineBase::level_op
+enum LevelOp : int {
+    OP_APPLY = 0, OP_RESIDUAL, OP_RESTRICT, OP_PROLONG, OP_JACOBI, OP_CHEB, OP_GMRES, OP_ADRV, OP_ADRCORR,
+    OP_COARSE
+};
+
+// engine interface (one implementation per cycle precision)
+struct EngineBase {
+    virtual ~EngineBase() {}
+    virtual int setup_fields(Handle& H, const mg_instance* in, cudaStream_t st) = 0;
+    virtual void cycle(Handle& H, bool uzero, cudaStream_t st) = 0;
+    virtual void ir_step(Handle& H, cudaStream_t st) = 0;
+    virtual void outer_residual(Handle& H, bool gnorm, cudaStream_t st) = 0;
+    // level operations (single instance) used by the parity tests
+    virtual int level_op(Handle& H, int inst, int level, int what, int a0, int a1, cudaStream_t st) = 0;
+};
+
+EngineBase* make_engine_f32();
+EngineBase* make_engine_f64();
+
+// setup helpers shared by the engines (setup.cu)
+void setup_inject(const double* k_fine, const double* phi_fine, int n1, double omega, int bc, int level,
+                  double* k64, double* phi64, double* sig64, int n, int pitch, cudaStream_t st);
+double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
+                        double* dscratch, cudaStream_t st);
+int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                         double omega, int bc, double shift, int which, double2* inv, cudaStream_t st);
+
+#define WADR_CHECK(x)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (x);                                                           \
+        if (e_ != cudaSuccess) {                                                        \
+            set_error(std::string(#x) + ": " + cudaGetErrorString(e_));                 \
+            return MG_ECUDA;                                                            \
+        }                                                                               \
+    } while (0)
+
+void set_error(const std::string& s);
+
+}  // namespace wadr

@@ -1,0 +1,989 @@
+// Hot-path kernels of the Wave-ADR cycle, templated on the working precision
+// T (float: complex-FP32 cycle of the mixed form; double: plain FP64 form).
+//
+// Every kernel takes (descriptor table, segment table, nseg) and works on
+// slots of the (instance, level) its block belongs to.  Blocks are 32 x 8.
+#pragma once
+#include "common.cuh"
+
+namespace wadr {
+
+// slot indices inside one (instance, level) allocation
+// Level 1 only allocates the first NSLOT_L1 slots.
+enum Slot : int {
+    SU = 0,   // wave iterate u / x
+    SG = 1,   // wave right-hand side g
+    SD = 2,   // Chebyshev direction d; level-1 cycle output; ADR x'
+    SX2 = 3,  // second wave iterate (stencil kernels never update in place)
+    SAX = 4,  // ADR iterate
+    SAB = 5,  // ADR right-hand side
+    SV1 = 6,  // GMRES r0 of the post-smoother
+    SU2 = 7,  // GMRES unnormalised Krylov vectors
+    SU3 = 8,
+    SWA = 9,  // GMRES L-images (ping-pong)
+    SWB = 10,
+    NSLOT = 11,
+    NSLOT_L1 = 4
+};
+
+struct SegCtx {
+    int lb, nb;      // block index within segment, number of blocks of segment
+};
+
+// Copy this block's descriptor into shared memory.
+__device__ __forceinline__ SegCtx seg_begin(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                            int nseg, LevelDesc& sd) {
+    const int s = find_seg(Sg, nseg, blockIdx.x);
+    const Seg g = Sg[s];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) sd = D[g.desc];
+    __syncthreads();
+    SegCtx c;
+    c.lb = blockIdx.x - g.blk0;
+    c.nb = g.blk1 - g.blk0;
+    return c;
+}
+
+// ----------------------------------------------------------- point stencils
+template <typename T>
+__device__ __forceinline__ cplx<T> nbr_sum(const cplx<T>* __restrict__ u, int n, int pitch, int i, int j,
+                                           long long p) {
+    cplx<T> s = zero2<T>();
+    if (i > 0) s = cadd<T>(s, __ldg(u + p - 1));
+    if (i < n - 1) s = cadd<T>(s, __ldg(u + p + 1));
+    if (j > 0) s = cadd<T>(s, __ldg(u + p - pitch));
+    if (j < n - 1) s = cadd<T>(s, __ldg(u + p + pitch));
+    return s;
+}
+
+// (A u)(i,j), conjugated diagonal for A^H (A is complex symmetric).
+template <typename T, bool HERM>
+__device__ __forceinline__ cplx<T> helm_apply_pt(const LevelDesc& d, const cplx<T>* __restrict__ u, int i,
+                                                 int j) {
+    const long long p = (long long)j * d.pitch + i;
+    cplx<T> dg = helm_diag_at<T>(d, i, j);
+    if (HERM) dg.y = -dg.y;
+    const cplx<T> s = nbr_sum<T>(u, d.n, d.pitch, i, j, p);
+    const cplx<T> c = __ldg(u + p);
+    const T ih2 = (T)d.inv_h2;
+    return cscale<T>(csub<T>(cmul<T>(dg, c), s), ih2);
+}
+
+// Upwind ADR stencil at a node from its coefficient quad (phix, phiy, d.re,
+// d.im) and its five values (zero outside the grid).
+template <typename T>
+__device__ __forceinline__ cplx<T> adr_pt(const quad<T>& q, T ih2, T wh, cplx<T> c, cplx<T> w, cplx<T> e,
+                                          cplx<T> s, cplx<T> nn) {
+    // d c - ih2 (w+e+s+n) + i wh [ 2max(px,0) w - 2min(px,0) e + 2max(py,0) s - 2min(py,0) n ]
+    const T px = q.x, py = q.y;
+    const T aw = T(2) * fmax(px, T(0)), ae = T(-2) * fmin(px, T(0));
+    const T as = T(2) * fmax(py, T(0)), an = T(-2) * fmin(py, T(0));
+    cplx<T> adv = mk<T>(aw * w.x + ae * e.x + as * s.x + an * nn.x, aw * w.y + ae * e.y + as * s.y + an * nn.y);
+    cplx<T> lap = mk<T>(w.x + e.x + s.x + nn.x, w.y + e.y + s.y + nn.y);
+    cplx<T> dg = mk<T>(q.z, q.w);
+    cplx<T> r = cmul<T>(dg, c);
+    r.x += -ih2 * lap.x - wh * adv.y;
+    r.y += -ih2 * lap.y + wh * adv.x;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ quad<T> load_adr(const LevelDesc& d, long long p) {
+    return reinterpret_cast<const quad<T>*>(d.adr)[p];
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> adr_apply_pt(const LevelDesc& d, const cplx<T>* __restrict__ u, int i, int j) {
+    const long long p = (long long)j * d.pitch + i;
+    const int n = d.n;
+    cplx<T> z = zero2<T>();
+    cplx<T> w = i > 0 ? __ldg(u + p - 1) : z;
+    cplx<T> e = i < n - 1 ? __ldg(u + p + 1) : z;
+    cplx<T> s = j > 0 ? __ldg(u + p - d.pitch) : z;
+    cplx<T> nn = j < n - 1 ? __ldg(u + p + d.pitch) : z;
+    return adr_pt<T>(load_adr<T>(d, p), (T)d.inv_h2, (T)(d.omega / d.h), __ldg(u + p), w, e, s, nn);
+}
+
+// Transposed ADR stencil (L^T y)(i,j): each neighbour contributes with the
+// coefficient it applies to this node.
+// CONJ: L^H y = conj(L^T conj(y)).
+template <typename T, bool CONJ>
+__device__ __forceinline__ cplx<T> adr_apply_t_pt(const LevelDesc& d, const cplx<T>* __restrict__ y, int i,
+                                                  int j) {
+    const long long p = (long long)j * d.pitch + i;
+    const int n = d.n;
+    const T ih2 = (T)d.inv_h2, wh = (T)(d.omega / d.h);
+    quad<T> qc = load_adr<T>(d, p);
+    auto ld = [&](long long pq) { cplx<T> v = __ldg(y + pq); if (CONJ) v.y = -v.y; return v; };
+    cplx<T> r = cmul<T>(mk<T>(qc.z, qc.w), ld(p));
+    // neighbour q uses coefficient c_dir(q) for this node
+    auto add = [&](long long pq, T a_adv) {  // coefficient -ih2 + i wh a_adv
+        cplx<T> v = ld(pq);
+        r.x += -ih2 * v.x - wh * a_adv * v.y;
+        r.y += -ih2 * v.y + wh * a_adv * v.x;
+    };
+    if (i < n - 1) { quad<T> q = load_adr<T>(d, p + 1); add(p + 1, T(2) * fmax(q.x, T(0))); }        // E nbr's W coef
+    if (i > 0) { quad<T> q = load_adr<T>(d, p - 1); add(p - 1, T(-2) * fmin(q.x, T(0))); }           // W nbr's E coef
+    if (j < n - 1) { quad<T> q = load_adr<T>(d, p + d.pitch); add(p + d.pitch, T(2) * fmax(q.y, T(0))); }  // N nbr's S
+    if (j > 0) { quad<T> q = load_adr<T>(d, p - d.pitch); add(p - d.pitch, T(-2) * fmin(q.y, T(0))); }     // S nbr's N
+    if (CONJ) r.y = -r.y;
+    return r;
+}
+
+// ----------------------------------------------------------- generic ops
+// op: 0 A, 1 A^H, 2 L (ADR), 3 L^T, 4 L^H
+template <typename T>
+__global__ void __launch_bounds__(NT) k_apply(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                              int nseg, int op, int sx, int sy) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* x = slot<T>(d, sx);
+    cplx<T>* y = slot<T>(d, sy);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        cplx<T> r;
+        if (op == 0) r = helm_apply_pt<T, false>(d, x, i, j);
+        else if (op == 1) r = helm_apply_pt<T, true>(d, x, i, j);
+        else if (op == 2) r = adr_apply_pt<T>(d, x, i, j);
+        else if (op == 3) r = adr_apply_t_pt<T, false>(d, x, i, j);
+        else r = adr_apply_t_pt<T, true>(d, x, i, j);
+        y[(long long)j * d.pitch + i] = r;
+    }
+}
+
+// r = g - A u (uzero: r = g)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_residual(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                 int nseg, int su, int sg, int sr, int uzero) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* u = slot<T>(d, su);
+    const cplx<T>* g = slot<T>(d, sg);
+    cplx<T>* r = slot<T>(d, sr);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<T> v = __ldg(g + p);
+        if (!uzero) v = csub<T>(v, helm_apply_pt<T, false>(d, u, i, j));
+        r[p] = v;
+    }
+}
+
+// Damped Jacobi: out = u + w D^{-1} (g - A u)   (eq. sjac)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_jacobi(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                               int nseg, int su, int sg, int sout, int uzero) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* u = slot<T>(d, su);
+    const cplx<T>* g = slot<T>(d, sg);
+    cplx<T>* o = slot<T>(d, sout);
+    const T wj = (T)d.scal[S::OMEGA_J];
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<T> dg = helm_diag_at<T>(d, i, j);
+        cplx<T> rr = __ldg(g + p);
+        cplx<T> uc = uzero ? zero2<T>() : __ldg(u + p);
+        if (!uzero) {
+            cplx<T> s = nbr_sum<T>(u, d.n, d.pitch, i, j, p);
+            rr = csub<T>(rr, cscale<T>(csub<T>(cmul<T>(dg, uc), s), (T)d.inv_h2));
+        }
+        // D = dg / h^2  ->  D^{-1} rr = h^2 rr / dg
+        const T h2 = (T)(d.h * d.h);
+        const T den = dg.x * dg.x + dg.y * dg.y;
+        cplx<T> q = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
+        o[p] = cadd<T>(uc, cscale<T>(q, wj * h2));
+    }
+}
+
+// ----------------------------------------------------------- smem regions
+// Load rows [y0, y0+H) x cols [x0, x0+W) of a grid vector into sm (row
+// stride W); zero outside the grid.
+template <typename T>
+__device__ __forceinline__ void load_region(cplx<T>* sm, const cplx<T>* __restrict__ p, int n, int pitch, int x0,
+                                            int y0, int W, int H) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    for (int e = tid; e < W * H; e += NT) {
+        const int r = e / W, cc = e - r * W;
+        const int gi = x0 + cc, gj = y0 + r;
+        sm[e] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? __ldg(p + (long long)gj * pitch + gi) : zero2<T>();
+    }
+}
+
+// ----------------------------------------------------------- Chebyshev step
+// One step of the Chebyshev semi-iteration on A^*A x = A^*g (eq. cheb),
+// three-term form: s = A^*(g - A x);  d = c1[m] d + c2[m] s;  x += d.
+// Flags: 1 = x is zero on entry (first pre-smoothing step from zero),
+//        2 = do not write d (last step).
+constexpr int CTX = 32, CTY = 16;
+template <typename T>
+__global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                  int nseg, int sxin, int sxout, int m, int flags) {
+    __shared__ LevelDesc d;
+    __shared__ cplx<T> X[(CTY + 4) * (CTX + 4)];
+    __shared__ cplx<T> Tt[(CTY + 2) * (CTX + 2)];
+    __shared__ T K[(CTY + 2) * (CTX + 2)];
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int n = d.n, pitch = d.pitch;
+    const int ntx = (n + CTX - 1) / CTX, nty = (n + CTY - 1) / CTY;
+    const cplx<T>* x = slot<T>(d, sxin);
+    cplx<T>* xo_ = slot<T>(d, sxout);
+    const cplx<T>* g = slot<T>(d, SG);
+    cplx<T>* dd = slot<T>(d, SD);
+    const bool xzero = flags & 1;
+    const T c1 = (T)d.scal[S::CHEB_C1 + m], c2 = (T)d.scal[S::CHEB_C2 + m];
+    const T ih2 = (T)d.inv_h2;
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int x0 = (t % ntx) * CTX, y0 = (t / ntx) * CTY;
+        __syncthreads();
+        if (!xzero) load_region<T>(X, x, n, pitch, x0 - 2, y0 - 2, CTX + 4, CTY + 4);
+        for (int e = tid; e < (CTX + 2) * (CTY + 2); e += NT) {
+            const int r = e / (CTX + 2), cc = e - r * (CTX + 2);
+            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
+            K[e] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? load_k<T>(d, gi, gj) : T(0);
+        }
+        __syncthreads();
+        // t = g - A x on the tile plus a one-node ring
+        for (int e = tid; e < (CTX + 2) * (CTY + 2); e += NT) {
+            const int r = e / (CTX + 2), cc = e - r * (CTX + 2);
+            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
+            cplx<T> tv = zero2<T>();
+            if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
+                tv = __ldg(g + (long long)gj * pitch + gi);
+                if (!xzero) {
+                    const int b = (r + 1) * (CTX + 4) + cc + 1;
+                    cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - (CTX + 4)], X[b + (CTX + 4)]));
+                    cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[e], load_sig<T>(d, gi, gj));
+                    tv = csub<T>(tv, cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
+                }
+            }
+            Tt[e] = tv;
+        }
+        __syncthreads();
+        // s = A^H t, update d and x on the tile
+        for (int e = tid; e < CTX * CTY; e += NT) {
+            const int r = e / CTX, cc = e - r * CTX;
+            const int gi = x0 + cc, gj = y0 + r;
+            if (gi >= n || gj >= n) continue;
+            const int b = (r + 1) * (CTX + 2) + cc + 1;
+            cplx<T> s = cadd<T>(cadd<T>(Tt[b - 1], Tt[b + 1]), cadd<T>(Tt[b - (CTX + 2)], Tt[b + (CTX + 2)]));
+            cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[b], load_sig<T>(d, gi, gj));
+            dg.y = -dg.y;
+            cplx<T> sv = cscale<T>(csub<T>(cmul<T>(dg, Tt[b]), s), ih2);
+            const long long p = (long long)gj * pitch + gi;
+            cplx<T> dn = cscale<T>(sv, c2);
+            if (c1 != T(0)) dn = cadd<T>(dn, cscale<T>(__ldg(dd + p), c1));
+            cplx<T> xo = xzero ? zero2<T>() : X[(r + 2) * (CTX + 4) + cc + 2];
+            xo_[p] = cadd<T>(xo, dn);
+            if (!(flags & 2)) dd[p] = dn;
+        }
+    }
+}
+
+// ----------------------------------------------------------- restriction tile
+// Full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] of a fine residual computed on
+// the fly over the footprint of a 32 x 8 coarse tile.
+//
+// MODE_HELM:  r = g - A u          (uzero flag: r = g)
+// MODE_JAC0:  u1 = w D^{-1} g (written to slot su), r = g - A u1
+// MODE_ADR:   r = b - L x          (ADR operator, slots sx/sb)
+// MODE_GMRES: x = CUPD.(r0,u2,u3) written to SAX, r = CRES.(r0,u2,u3,w3)
+// The coarse result goes to slot `sc` of the next level.
+enum RMode : int { MODE_HELM = 0, MODE_JAC0 = 1, MODE_ADR = 2, MODE_GMRES = 3 };
+constexpr int RCX = 32, RCY = 8;
+constexpr int RFW = 2 * RCX + 1, RFH = 2 * RCY + 1;   // footprint
+constexpr int RHW = RFW + 2, RHH = RFH + 2;            // footprint + ring
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                 int nseg, int sx, int sb, int sc, int uzero) {
+    __shared__ LevelDesc d;
+    __shared__ LevelDesc dc;
+    __shared__ cplx<T> X[RHW * RHH];
+    __shared__ cplx<T> R[RFW * RFH];
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) dc = D[d.coarse];
+    __syncthreads();
+    const int n = d.n, pitch = d.pitch, nc = dc.n;
+    const int ntx = (nc + RCX - 1) / RCX, nty = (nc + RCY - 1) / RCY;
+    const T ih2 = (T)d.inv_h2;
+    cplx<T>* xs = slot<T>(d, sx);
+    const cplx<T>* bs = slot<T>(d, sb);
+    cplx<T>* out = slot<T>(dc, sc);
+    const cplx<T>* r0 = slot<T>(d, sb);     // MODE_GMRES: r0 slot passed as sb
+    const cplx<T>* u2 = slot<T>(d, SU2);
+    const cplx<T>* u3 = slot<T>(d, SU3);
+    const cplx<T>* w3 = slot<T>(d, SWA);
+    cplx<T> cu[3], cr[4];
+    if (MODE == MODE_GMRES) {
+        for (int q = 0; q < 3; ++q) cu[q] = from_d<T>(make_double2(d.scal[S::CUPD + 2 * q], d.scal[S::CUPD + 2 * q + 1]));
+        for (int q = 0; q < 4; ++q) cr[q] = from_d<T>(make_double2(d.scal[S::CRES + 2 * q], d.scal[S::CRES + 2 * q + 1]));
+    }
+    const T wj = (MODE == MODE_JAC0) ? (T)d.scal[S::OMEGA_J] : T(0);
+    const T h2 = (T)(d.h * d.h);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int I0 = (t % ntx) * RCX, J0 = (t / ntx) * RCY;
+        const int fx0 = 2 * I0, fy0 = 2 * J0;   // footprint origin (fine)
+        // own fine rows/cols for writes of the fine iterate
+        const int ox1 = (I0 + RCX >= nc) ? n : 2 * (I0 + RCX);
+        const int oy1 = (J0 + RCY >= nc) ? n : 2 * (J0 + RCY);
+        __syncthreads();
+        if (MODE == MODE_HELM || MODE == MODE_ADR) {
+            if (!uzero) load_region<T>(X, xs, n, pitch, fx0 - 1, fy0 - 1, RHW, RHH);
+        } else if (MODE == MODE_JAC0) {
+            // u1 = w D^{-1} g on footprint + ring
+            for (int e = tid; e < RHW * RHH; e += NT) {
+                const int r = e / RHW, cc = e - r * RHW;
+                const int gi = fx0 - 1 + cc, gj = fy0 - 1 + r;
+                cplx<T> v = zero2<T>();
+                if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
+                    const long long p = (long long)gj * pitch + gi;
+                    cplx<T> gv = __ldg(bs + p);
+                    cplx<T> dg = helm_diag_at<T>(d, gi, gj);
+                    const T den = dg.x * dg.x + dg.y * dg.y;
+                    v = cscale<T>(mk<T>((gv.x * dg.x + gv.y * dg.y) / den, (gv.y * dg.x - gv.x * dg.y) / den), wj * h2);
+                    if (gi >= fx0 && gi < ox1 && gj >= fy0 && gj < oy1) xs[p] = v;
+                }
+                X[e] = v;
+            }
+        }
+        __syncthreads();
+        // fine residual on the footprint
+        for (int e = tid; e < RFW * RFH; e += NT) {
+            const int r = e / RFW, cc = e - r * RFW;
+            const int gi = fx0 + cc, gj = fy0 + r;
+            cplx<T> v = zero2<T>();
+            if (gi < n && gj < n) {
+                const long long p = (long long)gj * pitch + gi;
+                if (MODE == MODE_GMRES) {
+                    cplx<T> a = __ldg(r0 + p), b2 = __ldg(u2 + p), b3 = __ldg(u3 + p);
+                    v = cmul<T>(cr[0], a);
+                    v = cfma<T>(cr[1], b2, v);
+                    v = cfma<T>(cr[2], b3, v);
+                    v = cfma<T>(cr[3], __ldg(w3 + p), v);
+                    if (gi < ox1 && gj < oy1) {
+                        cplx<T> xv = cmul<T>(cu[0], a);
+                        xv = cfma<T>(cu[1], b2, xv);
+                        xv = cfma<T>(cu[2], b3, xv);
+                        xs[p] = xv;   // sx = SAX
+                    }
+                } else {
+                    v = __ldg(bs + p);
+                    if (!(uzero && MODE != MODE_JAC0)) {
+                        const int b = (r + 1) * RHW + cc + 1;
+                        if (MODE == MODE_ADR) {
+                            v = csub<T>(v, adr_pt<T>(load_adr<T>(d, p), ih2, (T)(d.omega / d.h), X[b], X[b - 1],
+                                                     X[b + 1], X[b - RHW], X[b + RHW]));
+                        } else {
+                            cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - RHW], X[b + RHW]));
+                            cplx<T> dg = helm_diag_at<T>(d, gi, gj);
+                            v = csub<T>(v, cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
+                        }
+                    }
+                }
+            }
+            R[e] = v;
+        }
+        __syncthreads();
+        // full weighting
+        {
+            const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+            if (I < nc && J < nc) {
+                const int b = (2 * threadIdx.y + 1) * RFW + 2 * threadIdx.x + 1;
+                cplx<T> s4 = R[b];
+                cplx<T> s2 = cadd<T>(cadd<T>(R[b - 1], R[b + 1]), cadd<T>(R[b - RFW], R[b + RFW]));
+                cplx<T> s1 = cadd<T>(cadd<T>(R[b - RFW - 1], R[b - RFW + 1]), cadd<T>(R[b + RFW - 1], R[b + RFW + 1]));
+                cplx<T> v = cadd<T>(cadd<T>(cscale<T>(s4, T(4)), cscale<T>(s2, T(2))), s1);
+                out[(long long)J * dc.pitch + I] = cscale<T>(v, T(0.0625));
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- prolongation tile
+// Bilinear interpolation P = 4 R^T of the coarse correction (slot `sc` of
+// the next level), fused with the step that consumes it:
+//   PMODE_ADD:  x[sout] = x[sx] + P e  (pointwise; sout may equal sx)
+//   PMODE_JAC:  u = x[sx] + P e;  x[sout] = u + w D^{-1}(g - A u)   (level 1 post)
+//   PMODE_ADR:  x' = x[sx] + P e written to sxo;  r0 = b[sb] - L x' to sout
+// The output slots always differ from the slots read with a halo.
+enum PMode : int { PMODE_ADD = 0, PMODE_JAC = 1, PMODE_ADR = 2 };
+constexpr int PTX = 32, PTY = 8;
+constexpr int PHW = PTX + 2, PHH = PTY + 2;
+constexpr int PCW = PTX / 2 + 3, PCH = PTY / 2 + 3;
+
+template <typename T>
+__device__ __forceinline__ int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                int nseg, int sx, int sc, int sb, int sout, int sxo, int xzero) {
+    __shared__ LevelDesc d;
+    __shared__ LevelDesc dc;
+    __shared__ cplx<T> E[PCW * PCH];
+    __shared__ cplx<T> X[PHW * PHH];
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) dc = D[d.coarse];
+    __syncthreads();
+    const int n = d.n, pitch = d.pitch, nc = dc.n;
+    const int ntx = (n + PTX - 1) / PTX, nty = (n + PTY - 1) / PTY;
+    const cplx<T>* xs = slot<T>(d, sx);
+    const cplx<T>* ec = slot<T>(dc, sc);
+    const cplx<T>* bs = slot<T>(d, sb);
+    cplx<T>* os = slot<T>(d, sout);
+    const T ih2 = (T)d.inv_h2;
+    const int halo = (MODE == PMODE_ADD) ? 0 : 1;
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int x0 = (t % ntx) * PTX, y0 = (t / ntx) * PTY;
+        // coarse index range feeding fine [x0-1, x0+PTX]
+        const int cx0 = fdiv2<T>(x0 - 2), cy0 = fdiv2<T>(y0 - 2);
+        __syncthreads();
+        load_region<T>(E, ec, nc, dc.pitch, cx0, cy0, PCW, PCH);
+        __syncthreads();
+        // u = x + P e on tile (+ ring)
+        for (int e = tid; e < PHW * PHH; e += NT) {
+            const int r = e / PHW, cc = e - r * PHW;
+            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
+            cplx<T> v = zero2<T>();
+            const bool inner = cc >= 1 && cc <= PTX && r >= 1 && r <= PTY;
+            if ((halo || inner) && gi >= 0 && gi < n && gj >= 0 && gj < n) {
+                // 1D weights: odd fine index = coincident coarse node (gi-1)/2
+                T acc_re = 0, acc_im = 0;
+                int ia[2], ja[2];
+                T wa[2], wb[2];
+                int na, nb2;
+                if (gi & 1) { ia[0] = (gi - 1) / 2; wa[0] = T(1); na = 1; }
+                else { ia[0] = gi / 2 - 1; ia[1] = gi / 2; wa[0] = wa[1] = T(0.5); na = 2; }
+                if (gj & 1) { ja[0] = (gj - 1) / 2; wb[0] = T(1); nb2 = 1; }
+                else { ja[0] = gj / 2 - 1; ja[1] = gj / 2; wb[0] = wb[1] = T(0.5); nb2 = 2; }
+                for (int q = 0; q < nb2; ++q)
+                    for (int pp = 0; pp < na; ++pp) {
+                        cplx<T> ev = E[(ja[q] - cy0) * PCW + (ia[pp] - cx0)];
+                        acc_re += wa[pp] * wb[q] * ev.x;
+                        acc_im += wa[pp] * wb[q] * ev.y;
+                    }
+                v = mk<T>(acc_re, acc_im);
+                if (!xzero) v = cadd<T>(__ldg(xs + (long long)gj * pitch + gi), v);
+            }
+            X[e] = v;
+        }
+        __syncthreads();
+        {
+            const int cc = threadIdx.x, r = threadIdx.y;
+            const int gi = x0 + cc, gj = y0 + r;
+            if (gi < n && gj < n) {
+                const long long p = (long long)gj * pitch + gi;
+                const int b = (r + 1) * PHW + cc + 1;
+                if (MODE == PMODE_ADD) {
+                    os[p] = X[b];
+                } else if (MODE == PMODE_JAC) {
+                    cplx<T> dg = helm_diag_at<T>(d, gi, gj);
+                    cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - PHW], X[b + PHW]));
+                    cplx<T> rr = csub<T>(__ldg(bs + p), cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
+                    const T den = dg.x * dg.x + dg.y * dg.y;
+                    const T wj = (T)d.scal[S::OMEGA_J] * (T)(d.h * d.h);
+                    cplx<T> q = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
+                    os[p] = cadd<T>(X[b], cscale<T>(q, wj));
+                } else {
+                    cplx<T> Lx = adr_pt<T>(load_adr<T>(d, p), ih2, (T)(d.omega / d.h), X[b], X[b - 1], X[b + 1],
+                                           X[b - PHW], X[b + PHW]);
+                    os[p] = csub<T>(__ldg(bs + p), Lx);
+                    slot<T>(d, sxo)[p] = X[b];
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- modulation
+// b = exp(-i w phi) (g - A u)  at level 2 (eq. Rytov: r_hat = r e^{-i w phi}
+// in the exp(+i w phi) convention); result in slot SAB.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                 int nseg) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* u = slot<T>(d, SU);
+    const cplx<T>* g = slot<T>(d, SG);
+    cplx<T>* b = slot<T>(d, SAB);
+    const cplx<T>* mod = reinterpret_cast<const cplx<T>*>(d.mod);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<T> r = csub<T>(__ldg(g + p), helm_apply_pt<T, false>(d, u, i, j));
+        b[p] = cmulc<T>(__ldg(mod + p), r);
+    }
+}
+
+// ----------------------------------------------------------- GMRES(3)
+// GMRES(3) smoother of the ADR V-cycle (Section 3.2.2), Arnoldi with
+// classical Gram-Schmidt and lagged normalisation:
+//   A1: w1 = L r0;                   dots |r0|^2, <r0,w1>, |w1|^2
+//   A2: u2 = w1 - c r0 (on the fly); w2 = L u2; dots |u2|^2, <r0,w2>, <u2,w2>, |w2|^2
+//   A3: u3 = w2 - c0 r0 - c1 u2;    w3 = L u3; dots |u3|^2, <r0,w3>, <u2,w3>, <u3,w3>, |w3|^2
+//   B3: u4 = w3 - c0 r0 - c1 u2 - c2 u3;  dot |u4|^2;  then the 4x3 least squares
+// with v1 = r0/beta, v2 = u2/|u2|, v3 = u3/|u3|, v4 = u4/|u4|.
+__device__ __forceinline__ double2 sload2(const double* s, int off) { return make_double2(s[off], s[off + 1]); }
+__device__ __forceinline__ void sstore2(double* s, int off, double2 v) { s[off] = v.x; s[off + 1] = v.y; }
+__device__ __forceinline__ double sinv(double v) { return v > 0.0 ? 1.0 / v : 0.0; }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gm_a1(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                              int nseg, int sr0) {
+    __shared__ LevelDesc d;
+    __shared__ double2 sh[8 * 3];
+    __shared__ int flag;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* r0 = slot<T>(d, sr0);
+    cplx<T>* w = slot<T>(d, SWA);
+    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<T> wv = adr_apply_pt<T>(d, r0, i, j);
+        w[p] = wv;
+        double2 a = to_d(__ldg(r0 + p)), b = to_d(wv);
+        acc[0].x += dabs2(a);
+        acc[1] = dadd(acc[1], dmulc(a, b));
+        acc[2].x += dabs2(b);
+    }
+    block_sum<3>(acc, sh);
+    if (publish_partials<3>(d, c.lb, c.nb, 0, acc, &flag)) {
+        double2 tot[3];
+        finish_partials<3>(d, c.nb, 0, tot, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double* s = d.scal;
+            const double beta = sqrt(tot[0].x);
+            const double ib2 = sinv(tot[0].x);
+            s[S::BETA] = beta;
+            const double2 h11 = dsc(tot[1], ib2);
+            for (int q = 0; q < 24; ++q) s[S::H + q] = 0.0;
+            sstore2(s, S::H + 0, h11);
+            s[S::WN1] = sqrt(tot[2].x) * sinv(beta);
+            sstore2(s, S::CA2, h11);
+        }
+    }
+}
+
+// region-based stencil of the on-the-fly combination
+template <typename T, int STEP>
+__global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                               int nseg, int sr0) {
+    constexpr int NV = STEP == 2 ? 4 : 5;
+    __shared__ LevelDesc d;
+    __shared__ double2 sh[8 * 5];
+    __shared__ int flag;
+    __shared__ cplx<T> Ur[(BY + 2) * (BX + 2)];
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int n = d.n, pitch = d.pitch;
+    const int ntx = (n + BX - 1) / BX, nty = (n + BY - 1) / BY;
+    const cplx<T>* r0 = slot<T>(d, sr0);
+    const cplx<T>* win = slot<T>(d, STEP == 2 ? SWA : SWB);
+    const cplx<T>* u2 = slot<T>(d, SU2);
+    cplx<T>* uout = slot<T>(d, STEP == 2 ? SU2 : SU3);
+    cplx<T>* wout = slot<T>(d, STEP == 2 ? SWB : SWA);
+    cplx<T> ca, cb = zero2<T>();
+    if (STEP == 2) {
+        ca = from_d<T>(sload2(d.scal, S::CA2));
+    } else {
+        ca = from_d<T>(sload2(d.scal, S::CA3));
+        cb = from_d<T>(sload2(d.scal, S::CA3 + 2));
+    }
+    const T ih2 = (T)d.inv_h2, wh = (T)(d.omega / d.h);
+    double2 acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = make_double2(0, 0);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
+        __syncthreads();
+        for (int e = tid; e < (BX + 2) * (BY + 2); e += NT) {
+            const int r = e / (BX + 2), cc = e - r * (BX + 2);
+            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
+            cplx<T> v = zero2<T>();
+            if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
+                const long long p = (long long)gj * pitch + gi;
+                v = csub<T>(__ldg(win + p), cmul<T>(ca, __ldg(r0 + p)));
+                if (STEP == 3) v = csub<T>(v, cmul<T>(cb, __ldg(u2 + p)));
+            }
+            Ur[e] = v;
+        }
+        __syncthreads();
+        const int gi = x0 + threadIdx.x, gj = y0 + threadIdx.y;
+        if (gi < n && gj < n) {
+            const long long p = (long long)gj * pitch + gi;
+            const int b = (threadIdx.y + 1) * (BX + 2) + threadIdx.x + 1;
+            const cplx<T> uc = Ur[b];
+            cplx<T> wv = adr_pt<T>(load_adr<T>(d, p), ih2, wh, uc, Ur[b - 1], Ur[b + 1], Ur[b - (BX + 2)],
+                                   Ur[b + (BX + 2)]);
+            uout[p] = uc;
+            wout[p] = wv;
+            double2 U = to_d(uc), W = to_d(wv), R0 = to_d(__ldg(r0 + p));
+            acc[0].x += dabs2(U);
+            acc[1] = dadd(acc[1], dmulc(R0, W));
+            if (STEP == 2) {
+                acc[2] = dadd(acc[2], dmulc(U, W));
+                acc[3].x += dabs2(W);
+            } else {
+                acc[2] = dadd(acc[2], dmulc(to_d(__ldg(u2 + p)), W));
+                acc[3] = dadd(acc[3], dmulc(U, W));
+                acc[4].x += dabs2(W);
+            }
+        }
+    }
+    block_sum<NV>(acc, sh);
+    if (publish_partials<NV>(d, c.lb, c.nb, 0, acc, &flag)) {
+        double2 tot[NV];
+        finish_partials<NV>(d, c.nb, 0, tot, sh);
+        if (tid == 0) {
+            double* s = d.scal;
+            const double beta = s[S::BETA];
+            if (STEP == 2) {
+                const double nu2 = sqrt(tot[0].x);
+                s[S::NU2] = nu2;
+                const double in2 = sinv(nu2);
+                // h21 = nu2/beta, h12 = <r0,w2>/(beta nu2), h22 = <u2,w2>/nu2^2
+                sstore2(s, S::H + 2 * (1 * 3 + 0), make_double2(nu2 * sinv(beta), 0));
+                const double2 h12 = dsc(tot[1], sinv(beta) * in2);
+                const double2 h22 = dsc(tot[2], in2 * in2);
+                sstore2(s, S::H + 2 * (0 * 3 + 1), h12);
+                sstore2(s, S::H + 2 * (1 * 3 + 1), h22);
+                s[S::WN2] = sqrt(tot[3].x) * in2;
+                sstore2(s, S::CA3, dsc(h12, nu2 * sinv(beta)));
+                sstore2(s, S::CA3 + 2, h22);
+            } else {
+                const double nu2 = s[S::NU2];
+                const double nu3 = sqrt(tot[0].x);
+                s[S::NU3] = nu3;
+                const double in3 = sinv(nu3);
+                sstore2(s, S::H + 2 * (2 * 3 + 1), make_double2(nu3 * sinv(nu2), 0));
+                const double2 h13 = dsc(tot[1], sinv(beta) * in3);
+                const double2 h23 = dsc(tot[2], sinv(nu2) * in3);
+                const double2 h33 = dsc(tot[3], in3 * in3);
+                sstore2(s, S::H + 2 * (0 * 3 + 2), h13);
+                sstore2(s, S::H + 2 * (1 * 3 + 2), h23);
+                sstore2(s, S::H + 2 * (2 * 3 + 2), h33);
+                s[S::WN3] = sqrt(tot[4].x) * in3;
+                sstore2(s, S::CB3 + 0, dsc(h13, nu3 * sinv(beta)));
+                sstore2(s, S::CB3 + 2, dsc(h23, nu3 * sinv(nu2)));
+                sstore2(s, S::CB3 + 4, h33);
+            }
+        }
+    }
+}
+
+// Small dense least squares min || beta e1 - H y ||, H (m+1) x m upper
+// Hessenberg (row-major 4 x 3), by complex Givens rotations; also returns the
+// residual coefficients c = beta e1 - H y.
+__device__ inline void hess_lsq(const double* Hm, double beta, int m, double2* y, double2* cres) {
+    double2 R[4][3], g[4];
+    for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 3; ++q) R[r][q] = make_double2(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]);
+    for (int r = 0; r < 4; ++r) g[r] = make_double2(0, 0);
+    g[0].x = beta;
+    double2 cs[3], sn[3];
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double2 a = R[i][j], b = R[i + 1][j];
+            double2 t = dadd(dmulc(cs[i], a), dmulc(sn[i], b));
+            R[i + 1][j] = dsub(dmul(cs[i], b), dmul(sn[i], a));
+            R[i][j] = t;
+        }
+        double2 a = R[j][j], b = R[j + 1][j];
+        double den = sqrt(dabs2(a) + dabs2(b));
+        if (den > 0) {
+            cs[j] = dsc(a, 1.0 / den);
+            sn[j] = dsc(b, 1.0 / den);
+        } else {
+            cs[j] = make_double2(1, 0);
+            sn[j] = make_double2(0, 0);
+        }
+        R[j][j] = make_double2(den, 0);
+        R[j + 1][j] = make_double2(0, 0);
+        double2 gj = g[j];
+        g[j + 1] = dsc(dmul(sn[j], gj), -1.0);
+        g[j] = dmulc(cs[j], gj);
+    }
+    for (int q = 0; q < 3; ++q) y[q] = make_double2(0, 0);
+    for (int j = m - 1; j >= 0; --j) {
+        double2 acc = g[j];
+        for (int q = j + 1; q < m; ++q) acc = dsub(acc, dmul(R[j][q], y[q]));
+        y[j] = (dabs2(R[j][j]) > 0) ? ddiv(acc, R[j][j]) : make_double2(0, 0);
+    }
+    // c = beta e1 - H y with the original H
+    for (int r = 0; r < 4; ++r) {
+        double2 acc = make_double2(r == 0 ? beta : 0.0, 0);
+        for (int q = 0; q < m; ++q)
+            acc = dsub(acc, dmul(make_double2(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]), y[q]));
+        cres[r] = (r <= m) ? acc : make_double2(0, 0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gm_b3(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                              int nseg, int sr0) {
+    __shared__ LevelDesc d;
+    __shared__ double2 sh[8];
+    __shared__ int flag;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* r0 = slot<T>(d, sr0);
+    const cplx<T>* u2 = slot<T>(d, SU2);
+    const cplx<T>* u3 = slot<T>(d, SU3);
+    const cplx<T>* w3 = slot<T>(d, SWA);
+    const cplx<T> c0 = from_d<T>(sload2(d.scal, S::CB3)), c1 = from_d<T>(sload2(d.scal, S::CB3 + 2)),
+                  c2 = from_d<T>(sload2(d.scal, S::CB3 + 4));
+    double2 acc[1] = {{0, 0}};
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<T> v = __ldg(w3 + p);
+        v = csub<T>(v, cmul<T>(c0, __ldg(r0 + p)));
+        v = csub<T>(v, cmul<T>(c1, __ldg(u2 + p)));
+        v = csub<T>(v, cmul<T>(c2, __ldg(u3 + p)));
+        acc[0].x += dabs2(to_d(v));
+    }
+    block_sum<1>(acc, sh);
+    if (publish_partials<1>(d, c.lb, c.nb, 0, acc, &flag)) {
+        double2 tot[1];
+        finish_partials<1>(d, c.nb, 0, tot, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double* s = d.scal;
+            const double beta = s[S::BETA], nu2 = s[S::NU2], nu3 = s[S::NU3];
+            const double nu4 = sqrt(tot[0].x);
+            s[S::NU4] = nu4;
+            sstore2(s, S::H + 2 * (3 * 3 + 2), make_double2(nu4 * sinv(nu3), 0));
+            // Krylov dimension: stop at an (almost) invariant subspace
+            const double eps = 1e-12;
+            int m = 3;
+            if (!(beta > 0)) m = 0;
+            else if (!(s[S::H + 2 * (1 * 3 + 0)] > eps * s[S::WN1])) m = 1;
+            else if (!(s[S::H + 2 * (2 * 3 + 1)] > eps * s[S::WN2])) m = 2;
+            s[S::M] = m;
+            double2 y[3], cr[4];
+            hess_lsq(s + S::H, beta, m, y, cr);
+            for (int q = 0; q < 3; ++q) sstore2(s, S::Y + 2 * q, y[q]);
+            const double inv[3] = {sinv(beta), sinv(nu2), sinv(nu3)};
+            for (int q = 0; q < 3; ++q) sstore2(s, S::CUPD + 2 * q, dsc(y[q], inv[q]));
+            // r = sum_i c_i v_i; v4 = (w3 - CB3.(r0,u2,u3))/nu4
+            const double2 cb[3] = {sload2(s, S::CB3), sload2(s, S::CB3 + 2), sload2(s, S::CB3 + 4)};
+            const double i4 = sinv(nu4);
+            const double2 c4 = (m == 3) ? dsc(cr[3], i4) : make_double2(0, 0);
+            for (int q = 0; q < 3; ++q) {
+                double2 v = (q <= m) ? dsc(cr[q], inv[q]) : make_double2(0, 0);
+                v = dsub(v, dmul(c4, cb[q]));
+                sstore2(s, S::CRES + 2 * q, v);
+            }
+            sstore2(s, S::CRES + 6, c4);
+        }
+    }
+}
+
+// Post-smoother update SAX = x[sx] + V y (pointwise).  With `mod` (level 2) the
+// ADR result is modulated into the Helmholtz iterate instead:
+// u += exp(+i w phi) (x + V y)   (Algorithm 1's u <- u + e).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gm_update(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                  int nseg, int sr0, int sx, int modulate) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const cplx<T>* r0 = slot<T>(d, sr0);
+    const cplx<T>* u2 = slot<T>(d, SU2);
+    const cplx<T>* u3 = slot<T>(d, SU3);
+    const cplx<T>* x = slot<T>(d, sx);
+    cplx<T>* xout = slot<T>(d, SAX);
+    cplx<T>* u = slot<T>(d, SU);
+    const cplx<T>* mod = reinterpret_cast<const cplx<T>*>(d.mod);
+    const cplx<T> c0 = from_d<T>(sload2(d.scal, S::CUPD)), c1 = from_d<T>(sload2(d.scal, S::CUPD + 2)),
+                  c2 = from_d<T>(sload2(d.scal, S::CUPD + 4));
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<T> v = __ldg(x + p);
+        v = cfma<T>(c0, __ldg(r0 + p), v);
+        v = cfma<T>(c1, __ldg(u2 + p), v);
+        v = cfma<T>(c2, __ldg(u3 + p), v);
+        if (modulate) u[p] = cfma<T>(__ldg(mod + p), v, __ldg(u + p));
+        else xout[p] = v;
+    }
+}
+
+// ----------------------------------------------------------- coarsest level
+// x = A^{-1} b with the dense FP64 inverse formed at setup from the LU
+// factors.  One warp per matrix row; the right-hand side is staged in shared
+// memory (n_L^2 <= 1024).  which: 0 Helmholtz (SG -> SU), 1 ADR (SAB -> SAX).
+constexpr int MAXCOARSE = 1024;
+template <typename T>
+__global__ void __launch_bounds__(NT) k_coarse(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                               int nseg, int which) {
+    __shared__ LevelDesc d;
+    __shared__ double2 bsh[MAXCOARSE];
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int n = d.n, N = n * n;
+    const cplx<T>* b = slot<T>(d, which ? SAB : SG);
+    cplx<T>* x = slot<T>(d, which ? SAX : SU);
+    const double2* Ainv = which ? d.inv_adr : d.inv_helm;
+    for (int q = tid; q < N; q += NT) {
+        const int i = q % n, j = q / n;
+        bsh[q] = to_d(__ldg(b + (long long)j * d.pitch + i));
+    }
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int row = c.lb * (NT / 32) + wid; row < N; row += c.nb * (NT / 32)) {
+        const double2* a = Ainv + (long long)row * N;
+        double2 acc = make_double2(0, 0);
+        for (int q = lane; q < N; q += 32) acc = dadd(acc, dmul(__ldg(a + q), bsh[q]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) {
+            const int i = row % n, j = row / n;
+            x[(long long)j * d.pitch + i] = from_d<T>(acc);
+        }
+    }
+}
+
+}  // namespace wadr
+
+namespace wadr {
+// ----------------------------------------------------------- outer loop (FP64)
+// The outer descriptor table holds one FP64 level-1 descriptor per instance
+// (slots: SU = u, SG = g, SD = r, SX2 = spare) whose xvec/xstride point at
+// the same instance's level-1 cycle slots (precision TC).
+
+// r = g - A u in FP64 (slot SD) and ||r||^2 -> S::NORM; optionally ||g||^2 -> S::NORM+1.
+template <int V = 0>
+__global__ void __launch_bounds__(NT) k_outer_residual(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                       int nseg, int with_gnorm) {
+    __shared__ LevelDesc d;
+    __shared__ double2 sh[8 * 2];
+    __shared__ int flag;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const double2* u = slot<double>(d, SU);
+    const double2* g = slot<double>(d, SG);
+    double2* r = slot<double>(d, SD);
+    double2 acc[2] = {{0, 0}, {0, 0}};
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        double2 gv = __ldg(g + p);
+        double2 v = dsub(gv, helm_apply_pt<double, false>(d, u, i, j));
+        r[p] = v;
+        acc[0].x += dabs2(v);
+        if (with_gnorm) acc[1].x += dabs2(gv);
+    }
+    block_sum<2>(acc, sh);
+    if (publish_partials<2>(d, c.lb, c.nb, 0, acc, &flag)) {
+        double2 tot[2];
+        finish_partials<2>(d, c.nb, 0, tot, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            d.scal[S::NORM] = tot[0].x;
+            if (with_gnorm) d.scal[S::NORM + 1] = tot[1].x;
+            const double nr = sqrt(tot[0].x);
+            d.scal[S::SCALE] = nr;   // IR: e = ||r|| cycle(0, r/||r||)
+        }
+    }
+}
+
+// cycle level-1 SG (precision TC) = r / ||r||
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_outer_scale(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                    int nseg, int src_slot) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const double2* r = slot<double>(d, src_slot);
+    cplx<TC>* out = reinterpret_cast<cplx<TC>*>(d.xvec) + (long long)SG * d.xstride;
+    const double sc = d.scal[S::SCALE];
+    const double inv = sc > 0 ? 1.0 / sc : 0.0;
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        out[p] = from_d<TC>(dsc(__ldg(r + p), inv));
+    }
+}
+
+// u += ||r|| e   (e = cycle level-1 SD, precision TC)
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_outer_update(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                     int nseg) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    double2* u = slot<double>(d, SU);
+    const cplx<TC>* e = reinterpret_cast<const cplx<TC>*>(d.xvec) + (long long)SD * d.xstride;
+    const double sc = d.scal[S::SCALE];
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        double2 ev = to_d(__ldg(e + p));
+        u[p] = dadd(u[p], dsc(ev, sc));
+    }
+}
+}  // namespace wadr
+
+namespace wadr {
+// ----------------------------------------------------------- small utilities
+template <typename T>
+__global__ void __launch_bounds__(NT) k_sub(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg, int nseg,
+                                            int sa, int sb, int sc) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        slot<T>(d, sc)[p] = csub<T>(slot<T>(d, sa)[p], slot<T>(d, sb)[p]);
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(NT) k_copy(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg, int nseg,
+                                             int sa, int sb) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        slot<T>(d, sb)[p] = slot<T>(d, sa)[p];
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(NT) k_zero(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg, int nseg,
+                                             int sa) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        slot<T>(d, sa)[(long long)j * d.pitch + i] = zero2<T>();
+    }
+}
+}  // namespace wadr

@@ -1,0 +1,734 @@
+// C ABI of the Wave-ADR library: handle construction (mg_setup), the cycle
+// and the outer solve loops, level operations for verification.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "kernels.cuh"
+
+struct mg_handle {
+    wadr::Handle H;
+    wadr::EngineBase* eng = nullptr;
+};
+
+namespace wadr {
+
+static thread_local std::string g_err = "";
+void set_error(const std::string& s) { g_err = s; }
+
+void* Handle::alloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return p;
+}
+
+static int blocks_for(long long pts, int per) {
+    long long b = (pts + per - 1) / per;
+    return (int)std::max(1LL, std::min(b, 1216LL));
+}
+
+const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
+    std::string key = std::string(outer ? "o" : "c") + std::to_string(pts);
+    for (int i : ids) key += "," + std::to_string(i);
+    auto it = segs.find(key);
+    if (it != segs.end()) return it->second;
+    std::vector<Seg> h;
+    int blk = 0;
+    for (int i : ids) {
+        const LevelDesc& d = outer ? houter[i] : hdesc[i];
+        Seg s;
+        s.desc = i;
+        s.blk0 = blk;
+        blk += blocks_for((long long)d.n * d.n, pts);
+        s.blk1 = blk;
+        s.pad = 0;
+        h.push_back(s);
+    }
+    SegTable t;
+    t.nseg = (int)h.size();
+    t.nblocks = blk;
+    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
+    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    return segs[key] = t;
+}
+
+const SegTable& Handle::seg_rows(const std::vector<int>& ids, int rows_per_block) {
+    std::string key = "r" + std::to_string(rows_per_block);
+    for (int i : ids) key += "," + std::to_string(i);
+    auto it = segs.find(key);
+    if (it != segs.end()) return it->second;
+    std::vector<Seg> h;
+    int blk = 0;
+    for (int i : ids) {
+        const LevelDesc& d = hdesc[i];
+        Seg s;
+        s.desc = i;
+        s.blk0 = blk;
+        blk += blocks_for((long long)d.n * d.n, rows_per_block);
+        s.blk1 = blk;
+        s.pad = 0;
+        h.push_back(s);
+    }
+    SegTable t;
+    t.nseg = (int)h.size();
+    t.nblocks = blk;
+    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
+    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    return segs[key] = t;
+}
+
+// ------------------------------------------------------------ host helpers
+static double jacobi_default(double h, double kmax) {
+    const double kap = h * h * kmax * kmax;
+    return (4.0 - kap) / (5.0 - kap);
+}
+
+// alpha = max(lambda^2) / median(lambda^2) of the constant-k Dirichlet
+// 5-point symbol, lambda_pq = (4 sin^2(p pi h/2) + 4 sin^2(q pi h/2))/h^2 - k^2
+// (Section 3.1.1: lambda_max/alpha approximates the median of eig(A^*A)).
+static double alpha_spectral(int n, double h, double kref) {
+    std::vector<double> s(n);
+    for (int j = 1; j <= n; ++j) {
+        const double v = std::sin(j * M_PI * h / 2.0);
+        s[j - 1] = 4.0 * v * v / (h * h);
+    }
+    std::vector<double> ev((size_t)n * n);
+    double mx = 0;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) {
+            const double l = s[p] + s[q] - kref * kref;
+            ev[(size_t)p * n + q] = l * l;
+            mx = std::max(mx, l * l);
+        }
+    const size_t N = ev.size();
+    double med;
+    if (N % 2 == 1) {
+        std::nth_element(ev.begin(), ev.begin() + N / 2, ev.end());
+        med = ev[N / 2];
+    } else {
+        std::nth_element(ev.begin(), ev.begin() + N / 2, ev.end());
+        const double hi = ev[N / 2];
+        const double lo = *std::max_element(ev.begin(), ev.begin() + N / 2);
+        med = 0.5 * (lo + hi);
+    }
+    return mx / med;
+}
+
+// Chebyshev three-term coefficients on [a, b] = [lam/alpha, lam]:
+// d_0 = s_0/theta; d_m = rho_m rho_{m-1} d_{m-1} + (2 rho_m/delta) s_m.
+static void cheb_coeffs(double lam, double alpha, int q, double* c1, double* c2) {
+    const double a = lam / alpha, b = lam;
+    const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    c1[0] = 0.0;
+    c2[0] = 1.0 / theta;
+    for (int m = 1; m < q; ++m) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c1[m] = rn * rho;
+        c2[m] = 2.0 * rn / delta;
+        rho = rn;
+    }
+}
+
+static size_t esz(int prec) { return prec == MG_PREC_FP64 ? 16 : 8; }   // complex element
+static size_t rsz(int prec) { return prec == MG_PREC_FP64 ? 8 : 4; }    // real element
+
+static int round_pitch(int n) { return (n + 31) / 32 * 32; }
+
+static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t st) {
+    Handle& H = mh->H;
+    const mg_params& p = H.p;
+    const int prec = H.prec;
+    H.inst.resize(ninst);
+    long long off = 0;
+    // --- sizes, allocation
+    for (int b = 0; b < ninst; ++b) {
+        InstHost& I = H.inst[b];
+        I.n = in[b].n;
+        I.omega = in[b].omega;
+        I.bc = in[b].bc;
+        I.off = off;
+        off += (long long)I.n * I.n;
+        std::vector<int> sizes{I.n};
+        while (sizes.back() > p.n_cmax && sizes.back() / 2 >= 1) sizes.push_back(sizes.back() / 2);
+        I.L = (int)sizes.size();
+        if (I.L < 2) { set_error("mg_setup: n must exceed n_cmax"); return MG_EINVAL; }
+        if (I.L > MG_MAX_LEVELS) { set_error("mg_setup: too many levels"); return MG_EINVAL; }
+        if ((long long)sizes.back() * sizes.back() > MAXCOARSE) {
+            set_error("mg_setup: coarsest level larger than 32 x 32; lower n_cmax");
+            return MG_EINVAL;
+        }
+        if (sizes.back() < 2) { set_error("mg_setup: coarsest level smaller than 2 x 2"); return MG_EINVAL; }
+        H.Lmax = std::max(H.Lmax, I.L);
+        I.lv.resize(I.L);
+        const bool adr = p.adr && I.L >= 3 && p.M > 0;
+        for (int l = 1; l <= I.L; ++l) {
+            LevelHost& lv = I.lv[l - 1];
+            lv.n = sizes[l - 1];
+            lv.pitch = round_pitch(lv.n);
+            lv.h = 1.0 / (lv.n + 1);
+            lv.slot_stride = (size_t)lv.pitch * lv.n;
+            lv.nslot = (l == 1) ? NSLOT_L1 : NSLOT;
+            const size_t npt = lv.slot_stride;
+            lv.vec = H.alloc(npt * lv.nslot * esz(prec));
+            lv.kf = H.alloc(npt * rsz(prec));
+            lv.k64 = (double*)H.alloc(npt * 8);
+            lv.phi64 = (double*)H.alloc(npt * 8);
+            if (I.bc == MG_BC_SPONGE) {
+                lv.sig = H.alloc(npt * rsz(prec));
+                lv.sig64 = (double*)H.alloc(npt * 8);
+            }
+            if (adr && l >= 2) lv.adr = H.alloc(npt * 2 * esz(prec));
+            if (adr && l == 2) lv.mod = H.alloc(npt * esz(prec));
+            if (l == I.L) {
+                const size_t N = (size_t)lv.n * lv.n;
+                lv.inv_helm = (double2*)H.alloc(N * N * sizeof(double2));
+                if (adr) lv.inv_adr = (double2*)H.alloc(N * N * sizeof(double2));
+            }
+            if (!lv.vec || !lv.kf || !lv.k64 || !lv.phi64) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
+            cudaMemsetAsync(lv.vec, 0, npt * lv.nslot * esz(prec), st);
+        }
+        const size_t npt1 = I.lv[0].slot_stride;
+        I.outer_stride = npt1;
+        I.outer_vec = H.alloc(npt1 * 4 * 16);
+        if (!I.outer_vec) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
+        cudaMemsetAsync(I.outer_vec, 0, npt1 * 4 * 16, st);
+    }
+    H.total_elems = off;
+    // --- FP64 fields by injection
+    for (int b = 0; b < ninst; ++b) {
+        InstHost& I = H.inst[b];
+        for (int l = 1; l <= I.L; ++l) {
+            LevelHost& lv = I.lv[l - 1];
+            setup_inject(in[b].k, in[b].phi, I.n, I.omega, I.bc, l, lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, st);
+        }
+    }
+    int rc = mh->eng->setup_fields(H, in, st);
+    if (rc) return rc;
+    // --- descriptor tables and scalar arenas
+    int nd = 0;
+    for (auto& I : H.inst) nd += I.L;
+    const int nslots = nd + ninst;
+    H.scal = (double*)H.alloc(sizeof(double) * S::SIZE * nslots);
+    H.part = (double2*)H.alloc(sizeof(double2) * (size_t)MAXB * MAXDOT * nslots);
+    H.counter = (unsigned*)H.alloc(sizeof(unsigned) * NCOUNTERS * nslots);
+    if (!H.scal || !H.part || !H.counter) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
+    cudaMemsetAsync(H.counter, 0, sizeof(unsigned) * NCOUNTERS * nslots, st);
+    std::vector<double> hs((size_t)S::SIZE * nslots, 0.0);
+    double* dscr = (double*)H.alloc(64);
+    int di = 0;
+    for (int b = 0; b < ninst; ++b) {
+        InstHost& I = H.inst[b];
+        for (int l = 1; l <= I.L; ++l) {
+            LevelHost& lv = I.lv[l - 1];
+            lv.desc = di;
+            LevelDesc d;
+            memset(&d, 0, sizeof(d));
+            d.vec = lv.vec;
+            d.slot_stride = (long long)lv.slot_stride;
+            d.kf = lv.kf;
+            d.sig = lv.sig;
+            d.adr = lv.adr;
+            d.mod = lv.mod;
+            d.inv_helm = lv.inv_helm;
+            d.inv_adr = lv.inv_adr;
+            d.scal = H.scal + (size_t)S::SIZE * di;
+            d.part = H.part + (size_t)MAXB * MAXDOT * di;
+            d.counter = H.counter + (size_t)NCOUNTERS * di;
+            d.n = lv.n;
+            d.pitch = lv.pitch;
+            d.h = lv.h;
+            d.inv_h2 = 1.0 / (lv.h * lv.h);
+            d.omega = I.omega;
+            d.shift = H.p.shift;
+            d.bc = I.bc;
+            d.inst = b;
+            d.level = l;
+            d.coarse = (l < I.L) ? di + 1 : -1;
+            H.hdesc.push_back(d);
+            // scalars
+            double* s = hs.data() + (size_t)S::SIZE * di;
+            if (l == 1) {
+                double kmax = 0;
+                // level-1 max k: from the FP64 field
+                std::vector<double> kk((size_t)lv.n * lv.pitch);
+                cudaMemcpyAsync(kk.data(), lv.k64, kk.size() * 8, cudaMemcpyDeviceToHost, st);
+                cudaStreamSynchronize(st);
+                for (int j = 0; j < lv.n; ++j)
+                    for (int i = 0; i < lv.n; ++i) kmax = std::max(kmax, kk[(size_t)j * lv.pitch + i]);
+                I.omega_j = p.omega_jacobi > 0 ? p.omega_jacobi : jacobi_default(lv.h, kmax);
+                s[S::OMEGA_J] = I.omega_j;
+            }
+            const bool cheb = (l >= 2) && ((l == I.L) ? (p.coarse == MG_COARSE_CHEB) : (l != 3));
+            lv.cheb = cheb;
+            if (cheb) {
+                std::vector<double> kk((size_t)lv.n * lv.pitch);
+                cudaMemcpyAsync(kk.data(), lv.k64, kk.size() * 8, cudaMemcpyDeviceToHost, st);
+                cudaStreamSynchronize(st);
+                double kmax = 0;
+                for (int j = 0; j < lv.n; ++j)
+                    for (int i = 0; i < lv.n; ++i) kmax = std::max(kmax, kk[(size_t)j * lv.pitch + i]);
+                lv.lam_max = setup_lambda_max(lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.bc, p.shift, dscr, st);
+                lv.alpha = (p.alpha[l - 1] > 0) ? p.alpha[l - 1] : alpha_spectral(lv.n, lv.h, kmax);
+                const int q = (l == I.L) ? p.coarse_cheb_iters : p.cheb_iters;
+                s[S::CHEB_N] = q;
+                cheb_coeffs(lv.lam_max, lv.alpha, q, s + S::CHEB_C1, s + S::CHEB_C2);
+            }
+            if (l == I.L) {
+                int r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
+                                             0, lv.inv_helm, st);
+                if (r) return r;
+                if (lv.inv_adr) {
+                    r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc,
+                                             p.shift, 1, lv.inv_adr, st);
+                    if (r) return r;
+                }
+            }
+            ++di;
+        }
+    }
+    // outer descriptors (FP64, level-1 geometry)
+    for (int b = 0; b < ninst; ++b) {
+        InstHost& I = H.inst[b];
+        LevelHost& l1 = I.lv[0];
+        LevelDesc d = H.hdesc[l1.desc];
+        d.vec = I.outer_vec;
+        d.slot_stride = (long long)I.outer_stride;
+        d.kf = l1.k64;
+        d.sig = l1.sig64;
+        d.adr = nullptr;
+        d.mod = nullptr;
+        d.scal = H.scal + (size_t)S::SIZE * (nd + b);
+        d.part = H.part + (size_t)MAXB * MAXDOT * (nd + b);
+        d.counter = H.counter + (size_t)NCOUNTERS * (nd + b);
+        d.coarse = -1;
+        d.xvec = l1.vec;
+        d.xstride = (long long)l1.slot_stride;
+        I.outer_desc = b;
+        H.houter.push_back(d);
+    }
+    H.ddesc = (LevelDesc*)H.alloc(sizeof(LevelDesc) * H.hdesc.size());
+    H.douter = (LevelDesc*)H.alloc(sizeof(LevelDesc) * H.houter.size());
+    cudaMemcpy(H.ddesc, H.hdesc.data(), sizeof(LevelDesc) * H.hdesc.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(H.douter, H.houter.data(), sizeof(LevelDesc) * H.houter.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(H.scal, hs.data(), sizeof(double) * hs.size(), cudaMemcpyHostToDevice);
+    if (cudaMallocHost(&H.hpin, sizeof(double) * S::SIZE * nslots) != cudaSuccess) H.hpin = nullptr;
+    if (cudaStreamCreateWithFlags(&H.g_stream, cudaStreamNonBlocking) != cudaSuccess) return MG_ECUDA;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error(std::string("mg_setup: ") + cudaGetErrorString(e)); return MG_ECUDA; }
+    return MG_OK;
+}
+
+static void free_all(Handle& H) {
+    if (H.g_cycle0) cudaGraphExecDestroy(H.g_cycle0);
+    if (H.g_irstep) cudaGraphExecDestroy(H.g_irstep);
+    if (H.g_stream) cudaStreamDestroy(H.g_stream);
+    for (void* p : H.allocs) cudaFree(p);
+    if (H.hpin) cudaFreeHost(H.hpin);
+    H.allocs.clear();
+}
+
+// user dense (n x n, at element offset) <-> pitched slot
+static cudaError_t copy_in(const void* user, long long off, size_t es, void* slotp, int n, int pitch, cudaStream_t st) {
+    return cudaMemcpy2DAsync(slotp, (size_t)pitch * es, (const char*)user + off * es, (size_t)n * es, (size_t)n * es, n,
+                             cudaMemcpyDefault, st);
+}
+static cudaError_t copy_out(void* user, long long off, size_t es, const void* slotp, int n, int pitch, cudaStream_t st) {
+    return cudaMemcpy2DAsync((char*)user + off * es, (size_t)n * es, slotp, (size_t)pitch * es, (size_t)n * es, n,
+                             cudaMemcpyDefault, st);
+}
+static void* slot_ptr(const Handle& H, const LevelHost& lv, int s) {
+    return (char*)lv.vec + (size_t)s * lv.slot_stride * esz(H.prec);
+}
+
+// Capture `emit` into a graph on the handle's stream (after one plain run
+// that builds every segment table).
+template <class F>
+static int capture(Handle& H, cudaGraphExec_t* out, F emit) {
+    emit(H.g_stream);
+    cudaError_t e = cudaStreamSynchronize(H.g_stream);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    cudaGraph_t g;
+    e = cudaStreamBeginCapture(H.g_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    emit(H.g_stream);
+    e = cudaStreamEndCapture(H.g_stream, &g);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    return MG_OK;
+}
+
+}  // namespace wadr
+
+using namespace wadr;
+
+extern "C" {
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+void mg_default_params(mg_params* p) {
+    memset(p, 0, sizeof(*p));
+    p->precision = MG_PREC_FP64;
+    p->n_cmax = 15;
+    p->jacobi_iters = 1;
+    p->cheb_iters = 5;
+    p->coarse = MG_COARSE_LU;
+    p->coarse_cheb_iters = 10;
+    p->M = 8;
+    p->adr = 1;
+    p->omega_jacobi = 0.0;
+    for (int i = 0; i < MG_MAX_LEVELS; ++i) p->alpha[i] = 0.0;
+    p->outer = MG_OUTER_IR;
+    p->restart = 20;
+    p->maxit = 500;
+    p->tol = 1e-6;
+    p->shift = 0.0;
+    p->use_graph = 1;
+}
+
+int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
+    if (!out || !inst || ninst <= 0 || !p) { set_error("mg_setup: null argument"); return MG_EINVAL; }
+    *out = nullptr;
+    if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) { set_error("mg_setup: precision"); return MG_EINVAL; }
+    if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
+        p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1) {
+        set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1)");
+        return MG_EINVAL;
+    }
+    for (int b = 0; b < ninst; ++b) {
+        if (!inst[b].k || !inst[b].phi || inst[b].n < 3 || !(inst[b].omega > 0) ||
+            inst[b].bc < MG_BC_DIRICHLET || inst[b].bc > MG_BC_SPONGE) {
+            set_error("mg_setup: bad instance " + std::to_string(b));
+            return MG_EINVAL;
+        }
+    }
+    mg_handle* mh = new mg_handle();
+    mh->H.p = *p;
+    mh->H.prec = p->precision;
+    mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();
+    // k and phi may be host memory: stage them on the device for the setup kernels
+    std::vector<mg_instance> staged(inst, inst + ninst);
+    std::vector<void*> tmp;
+    cudaStream_t st0 = (cudaStream_t)stream;
+    for (int b = 0; b < ninst; ++b) {
+        const size_t bytes = sizeof(double) * (size_t)inst[b].n * inst[b].n;
+        for (int f = 0; f < 2; ++f) {
+            const double* src = f ? inst[b].phi : inst[b].k;
+            cudaPointerAttributes a;
+            bool dev = cudaPointerGetAttributes(&a, src) == cudaSuccess &&
+                       (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+            cudaGetLastError();
+            if (dev) continue;
+            void* d = nullptr;
+            if (cudaMalloc(&d, bytes) != cudaSuccess) {
+                for (void* q : tmp) cudaFree(q);
+                delete mh->eng;
+                delete mh;
+                set_error("mg_setup: out of device memory");
+                return MG_ENOMEM;
+            }
+            tmp.push_back(d);
+            cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st0);
+            (f ? staged[b].phi : staged[b].k) = (const double*)d;
+        }
+    }
+    int rc = build(mh, staged.data(), ninst, st0);
+    cudaStreamSynchronize(st0);
+    for (void* q : tmp) cudaFree(q);
+    if (rc) {
+        free_all(mh->H);
+        delete mh->eng;
+        delete mh;
+        return rc;
+    }
+    *out = mh;
+    return MG_OK;
+}
+
+void mg_destroy(mg_handle* h) {
+    if (!h) return;
+    free_all(h->H);
+    delete h->eng;
+    delete h;
+}
+
+int mg_num_levels(const mg_handle* h, int inst) {
+    if (!h || inst < 0 || inst >= (int)h->H.inst.size()) return MG_EINVAL;
+    return h->H.inst[inst].L;
+}
+
+int mg_level_n(const mg_handle* h, int inst, int level) {
+    if (!h || inst < 0 || inst >= (int)h->H.inst.size()) return MG_EINVAL;
+    const InstHost& I = h->H.inst[inst];
+    if (level < 1 || level > I.L) return MG_EINVAL;
+    return I.lv[level - 1].n;
+}
+
+int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int nout) {
+    if (!h || !out || inst < 0 || inst >= (int)h->H.inst.size()) return MG_EINVAL;
+    const InstHost& I = h->H.inst[inst];
+    if (level < 1 || level > I.L) return MG_EINVAL;
+    const LevelHost& lv = I.lv[level - 1];
+    double v[4] = {lv.lam_max, lv.alpha, I.omega_j, lv.h};
+    int k = std::min(nout, 4);
+    for (int i = 0; i < k; ++i) out[i] = v[i];
+    return k;
+}
+
+int mg_cycle_launches(const mg_handle* h) { return h ? h->H.launches_cycle : MG_EINVAL; }
+
+void mg_abi_sizes(size_t* params, size_t* instance, size_t* info) {
+    if (params) *params = sizeof(mg_params);
+    if (instance) *instance = sizeof(mg_instance);
+    if (info) *info = sizeof(mg_solve_info);
+}
+
+static bool is_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    bool dev = cudaPointerGetAttributes(&a, p) == cudaSuccess &&
+               (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    return !dev;
+}
+
+int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream) {
+    if (!h || !u || !g || ncycles < 0) { set_error("mg_cycle: bad argument"); return MG_EINVAL; }
+    Handle& H = h->H;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = esz(H.prec);
+    for (auto& I : H.inst) {
+        LevelHost& l1 = I.lv[0];
+        WADR_CHECK(copy_in(g, I.off, es, slot_ptr(H, l1, SG), l1.n, l1.pitch, st));
+        WADR_CHECK(copy_in(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.pitch, st));
+    }
+    for (int c = 0; c < ncycles; ++c) {
+        h->eng->cycle(H, false, st);
+        for (auto& I : H.inst) {
+            LevelHost& l1 = I.lv[0];
+            WADR_CHECK(cudaMemcpyAsync(slot_ptr(H, l1, SX2), slot_ptr(H, l1, SD), l1.slot_stride * es,
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    for (auto& I : H.inst) {
+        LevelHost& l1 = I.lv[0];
+        WADR_CHECK(copy_out(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.pitch, st));
+    }
+    WADR_CHECK(cudaGetLastError());
+    if (is_host_ptr(u)) WADR_CHECK(cudaStreamSynchronize(st));   // host result must be complete on return
+    return MG_OK;
+}
+
+int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_stream stream) {
+    if (!h || !u || !g) { set_error("mg_solve: bad argument"); return MG_EINVAL; }
+    Handle& H = h->H;
+    if (H.p.outer == MG_OUTER_FGMRES) { set_error("mg_solve: FGMRES outer not available in this build"); return MG_EUNSUPPORTED; }
+    cudaStream_t st = H.g_stream;
+    cudaStream_t ust = (cudaStream_t)stream;
+    // order after the caller's stream
+    cudaEvent_t ev0, ev1, evu;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventCreateWithFlags(&evu, cudaEventDisableTiming);
+    cudaEventRecord(evu, ust);
+    cudaStreamWaitEvent(st, evu, 0);
+    const int ni = (int)H.inst.size();
+    for (auto& I : H.inst) {
+        LevelHost& l1 = I.lv[0];
+        char* ov = (char*)I.outer_vec;
+        WADR_CHECK(copy_in(g, I.off, 16, ov + (size_t)SG * I.outer_stride * 16, l1.n, l1.pitch, st));
+        WADR_CHECK(copy_in(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
+    }
+    const int nd = (int)H.hdesc.size();
+    const double* outer_scal = H.scal + (size_t)S::SIZE * nd;
+    std::vector<double> gn(ni), rn(ni);
+    auto read_norms = [&](bool g2) -> int {
+        WADR_CHECK(cudaMemcpyAsync(H.hpin, outer_scal, sizeof(double) * S::SIZE * ni, cudaMemcpyDeviceToHost, st));
+        WADR_CHECK(cudaStreamSynchronize(st));
+        for (int b = 0; b < ni; ++b) {
+            rn[b] = std::sqrt(H.hpin[(size_t)S::SIZE * b + S::NORM]);
+            if (g2) gn[b] = std::sqrt(H.hpin[(size_t)S::SIZE * b + S::NORM + 1]);
+        }
+        return MG_OK;
+    };
+    h->eng->outer_residual(H, true, st);
+    int rc = read_norms(true);
+    if (rc) return rc;
+    auto relres = [&]() {
+        double m = 0;
+        for (int b = 0; b < ni; ++b) {
+            double v = gn[b] > 0 ? rn[b] / gn[b] : rn[b];
+            if (!std::isfinite(v)) return v;
+            m = std::max(m, v);
+        }
+        return m;
+    };
+    double rel = relres(), rel0 = rel;
+    int it = 0, nh = 0;
+    if (info && info->history && info->history_len > 0) info->history[nh++] = rel;
+    if (H.p.use_graph && !H.g_irstep) {
+        rc = capture(H, &H.g_irstep, [&](cudaStream_t s) { h->eng->ir_step(H, s); });
+        if (rc) return rc;
+        // the capture's plain run already performed one step: restart from u
+        for (auto& I : H.inst) {
+            LevelHost& l1 = I.lv[0];
+            char* ov = (char*)I.outer_vec;
+            WADR_CHECK(copy_in(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
+        }
+        h->eng->outer_residual(H, true, st);
+        rc = read_norms(true);
+        if (rc) return rc;
+    }
+    cudaEventRecord(ev0, st);
+    int status = MG_OK;
+    while (rel >= H.p.tol && it < H.p.maxit) {
+        if (H.p.use_graph) {
+            WADR_CHECK(cudaGraphLaunch(H.g_irstep, st));
+        } else {
+            h->eng->ir_step(H, st);
+        }
+        ++it;
+        rc = read_norms(false);
+        if (rc) return rc;
+        rel = relres();
+        if (info && info->history && nh < info->history_len) info->history[nh++] = rel;
+        if (!std::isfinite(rel) || rel > 1e3 * std::max(rel0, 1.0)) { status = MG_EDIVERGED; break; }
+    }
+    cudaEventRecord(ev1, st);
+    cudaEventSynchronize(ev1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    if (status == MG_OK && rel >= H.p.tol) status = MG_ENOTCONV;
+    for (auto& I : H.inst) {
+        LevelHost& l1 = I.lv[0];
+        char* ov = (char*)I.outer_vec;
+        WADR_CHECK(copy_out(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
+    }
+    cudaEventRecord(evu, st);
+    cudaStreamWaitEvent(ust, evu, 0);
+    WADR_CHECK(cudaStreamSynchronize(st));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaEventDestroy(evu);
+    if (info) {
+        info->iterations = it;
+        info->status = status;
+        info->rel_residual = rel;
+        info->history_len = nh;
+        info->seconds = ms * 1e-3;
+    }
+    return status;
+}
+
+// ------------------------------------------------------------ level ops
+static int check_level(mg_handle* h, int inst, int level) {
+    if (!h || inst < 0 || inst >= (int)h->H.inst.size()) { set_error("bad instance"); return MG_EINVAL; }
+    if (level < 1 || level > h->H.inst[inst].L) { set_error("bad level"); return MG_EINVAL; }
+    return MG_OK;
+}
+
+static int run_op(mg_handle* h, int inst, int level, int what, int a0, int a1,
+                  std::vector<std::pair<int, const void*>> ins, int in_level_shift, void* outp, int out_level_shift,
+                  int out_slot_override, cudaStream_t st) {
+    Handle& H = h->H;
+    InstHost& I = H.inst[inst];
+    const size_t es = esz(H.prec);
+    for (auto& pr : ins) {
+        int lvl = level + (pr.first >= 100 ? in_level_shift : 0);
+        int s = pr.first % 100;
+        LevelHost& lv = I.lv[lvl - 1];
+        WADR_CHECK(copy_in(pr.second, 0, es, slot_ptr(H, lv, s), lv.n, lv.pitch, st));
+    }
+    int s = h->eng->level_op(H, inst, level, what, a0, a1, st);
+    WADR_CHECK(cudaGetLastError());
+    if (s < 0) { set_error("level op failed"); return MG_EINVAL; }
+    if (out_slot_override >= 0) s = out_slot_override;
+    LevelHost& lo = I.lv[level + out_level_shift - 1];
+    WADR_CHECK(copy_out(outp, 0, es, slot_ptr(H, lo, s), lo.n, lo.pitch, st));
+    WADR_CHECK(cudaStreamSynchronize(st));
+    return MG_OK;
+}
+
+int mg_apply(mg_handle* h, int inst, int level, int op, const void* x, void* y, mg_stream stream) {
+    int rc = check_level(h, inst, level);
+    if (rc) return rc;
+    if (op < MG_OP_A || op > MG_OP_LH || !x || !y) { set_error("mg_apply: bad op"); return MG_EINVAL; }
+    if (op >= MG_OP_L && !h->H.inst[inst].lv[level - 1].adr) { set_error("mg_apply: no ADR operator on this level"); return MG_EINVAL; }
+    return run_op(h, inst, level, OP_APPLY, op, 0, {{SU, x}}, 0, y, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_residual(mg_handle* h, int inst, int level, const void* u, const void* g, void* r, mg_stream stream) {
+    int rc = check_level(h, inst, level);
+    if (rc) return rc;
+    return run_op(h, inst, level, OP_RESIDUAL, 0, 0, {{SU, u}, {SG, g}}, 0, r, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_restrict_residual(mg_handle* h, int inst, int level, const void* u, const void* g, void* rc_out, mg_stream stream) {
+    int rc = check_level(h, inst, level);
+    if (rc) return rc;
+    if (level >= h->H.inst[inst].L) { set_error("mg_restrict_residual: coarsest level"); return MG_EINVAL; }
+    return run_op(h, inst, level, OP_RESTRICT, 0, 0, {{SU, u}, {SG, g}}, 0, rc_out, 1, -1, (cudaStream_t)stream);
+}
+
+int mg_prolong_add(mg_handle* h, int inst, int level, const void* e, void* u, mg_stream stream) {
+    int rc = check_level(h, inst, level);
+    if (rc) return rc;
+    if (level >= h->H.inst[inst].L) { set_error("mg_prolong_add: coarsest level"); return MG_EINVAL; }
+    return run_op(h, inst, level, OP_PROLONG, 0, 0, {{SU, u}, {100 + SU, e}}, 1, u, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_jacobi(mg_handle* h, int inst, const void* u, const void* g, void* out, mg_stream stream) {
+    int rc = check_level(h, inst, 1);
+    if (rc) return rc;
+    return run_op(h, inst, 1, OP_JACOBI, 0, 0, {{SX2, u}, {SG, g}}, 0, out, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_chebyshev(mg_handle* h, int inst, int level, void* u, const void* g, int iters, mg_stream stream) {
+    int rc = check_level(h, inst, level);
+    if (rc) return rc;
+    if (!h->H.inst[inst].lv[level - 1].cheb || iters < 1 || iters > 16) {
+        set_error("mg_chebyshev: level has no Chebyshev smoother or iters out of range");
+        return MG_EINVAL;
+    }
+    return run_op(h, inst, level, OP_CHEB, iters, 0, {{SU, u}, {SG, g}}, 0, u, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_gmres3(mg_handle* h, int inst, int level, const void* b, void* x, int x_nonzero, mg_stream stream) {
+    int rc = check_level(h, inst, level);
+    if (rc) return rc;
+    if (level < 2 || !h->H.inst[inst].lv[level - 1].adr) { set_error("mg_gmres3: no ADR operator"); return MG_EINVAL; }
+    std::vector<std::pair<int, const void*>> ins{{SAB, b}};
+    if (x_nonzero) ins.push_back({SAX, x});
+    return run_op(h, inst, level, OP_GMRES, x_nonzero ? 1 : 0, 0, ins, 0, x, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_adr_vcycle(mg_handle* h, int inst, const void* b, void* a, mg_stream stream) {
+    int rc = check_level(h, inst, 2);
+    if (rc) return rc;
+    if (!h->H.inst[inst].lv[1].adr) { set_error("mg_adr_vcycle: ADR disabled"); return MG_EINVAL; }
+    return run_op(h, inst, 2, OP_ADRV, 0, 0, {{SAB, b}}, 0, a, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_adr_correction(mg_handle* h, int inst, void* u, const void* g, mg_stream stream) {
+    int rc = check_level(h, inst, 2);
+    if (rc) return rc;
+    if (!h->H.inst[inst].lv[1].adr) { set_error("mg_adr_correction: ADR disabled"); return MG_EINVAL; }
+    return run_op(h, inst, 2, OP_ADRCORR, 0, 0, {{SU, u}, {SG, g}}, 0, u, 0, -1, (cudaStream_t)stream);
+}
+
+int mg_coarse_solve(mg_handle* h, int inst, int which, const void* b, void* x, mg_stream stream) {
+    if (!h || inst < 0 || inst >= (int)h->H.inst.size()) { set_error("bad instance"); return MG_EINVAL; }
+    const int L = h->H.inst[inst].L;
+    if (which == 1 && !h->H.inst[inst].lv[L - 1].inv_adr) { set_error("no ADR coarse operator"); return MG_EINVAL; }
+    return run_op(h, inst, L, OP_COARSE, which, 0, {{which ? SAB : SG, b}}, 0, x, 0, -1, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Setup kernels (FP64): coefficient injection, ADR coefficients, level-2
+// modulation, the Gershgorin bound of A^*A and the coarsest-level dense LU.
+// These run once per mg_setup; none is on the per-cycle path.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "handle.h"
+#include "setup_kernels.cuh"
+
+namespace wadr {
+
+// Coefficients of level `level` by injection from the fine grid: coarse node
+// I of level l sits on fine node 2^(l-1) (I+1) - 1 (Algorithm 1's
+// re-discretised operator A_H; coefficients sampled at coinciding nodes).
+__global__ void k_inject(const double* __restrict__ kf, const double* __restrict__ pf, int n1, double omega,
+                         int bc, int level, double* k64, double* phi64, double* sig64, int n, int pitch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const long long f = 1LL << (level - 1);
+    const long long fi = f * (i + 1) - 1, fj = f * (j + 1) - 1;
+    const long long q = fj * n1 + fi, p = (long long)j * pitch + i;
+    const double k = kf[q];
+    k64[p] = k;
+    phi64[p] = pf[q];
+    if (sig64) {
+        // sponge mask: gamma(d) = omega ((W-d)/W)^2 for d < W = 2 pi/omega,
+        // d = distance of the fine node to the boundary; sig = omega gamma s^2
+        const double h1 = 1.0 / (n1 + 1);
+        const double x = (fi + 1) * h1, y = (fj + 1) * h1;
+        const double dist = fmin(fmin(x, 1.0 - x), fmin(y, 1.0 - y));
+        const double W = 2.0 * M_PI / omega;
+        const double gam = dist < W ? omega * ((W - dist) / W) * ((W - dist) / W) : 0.0;
+        sig64[p] = omega * gam * (k / omega) * (k / omega);
+    }
+}
+
+void setup_inject(const double* k_fine, const double* phi_fine, int n1, double omega, int bc, int level,
+                  double* k64, double* phi64, double* sig64, int n, int pitch, cudaStream_t st) {
+    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
+    k_inject<<<g, b, 0, st>>>(k_fine, phi_fine, n1, omega, bc, level, k64, phi64, sig64, n, pitch);
+}
+
+// max over nodes of the absolute row sum |A_pp| + (in-grid neighbours)/h^2
+__device__ __forceinline__ double helm_row_sum(const double* k64, const double* sig64, int n, int pitch,
+                                               double h, int bc, double shift, int i, int j) {
+    const long long p = (long long)j * pitch + i;
+    const double k = k64[p], kh = k * h;
+    double re = 4.0 - kh * kh, im = 0.0;
+    const int m = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1);
+    if (bc == BC_ABC1) {
+        re -= m;
+        im -= m * kh;
+    } else if (bc == BC_SPONGE) {
+        im -= h * h * sig64[p];
+    }
+    if (shift != 0.0) im -= shift * kh * kh;
+    return (sqrt(re * re + im * im) + (4 - m)) / (h * h);
+}
+
+__global__ void k_gersh(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
+                        unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const double v = helm_row_sum(k64, sig64, n, pitch, h, bc, shift, i, j);
+    // positive doubles order like their bit patterns
+    atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
+                        double* dscratch, cudaStream_t st) {
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
+    cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
+    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
+    k_gersh<<<g, b, 0, st>>>(k64, sig64, n, pitch, h, bc, shift, o);
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    double r;
+    memcpy(&r, &v, sizeof(r));
+    return r * r;
+}
+
+// ---------------------------------------------------------------- dense LU
+// Dense matrix of the coarsest operator (N = n^2, row p = j*n + i).
+__global__ void k_dense(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                        double omega, int bc, double shift, int which, double2* A) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = n * n;
+    if (p >= N) return;
+    const int i = p % n, j = p / n;
+    double2* row = A + (long long)p * N;
+    for (int q = 0; q < N; ++q) row[q] = make_double2(0, 0);
+    const double ih2 = 1.0 / (h * h);
+    if (which == 0) {
+        const long long pp = (long long)j * pitch + i;
+        const double k = k64[pp], kh = k * h;
+        double re = 4.0 - kh * kh, im = 0.0;
+        const int m = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1);
+        if (bc == BC_ABC1) { re -= m; im -= m * kh; }
+        else if (bc == BC_SPONGE) { im -= h * h * sig64[pp]; }
+        if (shift != 0.0) im -= shift * kh * kh;
+        row[p] = make_double2(re * ih2, im * ih2);
+        if (i > 0) row[p - 1] = make_double2(-ih2, 0);
+        if (i < n - 1) row[p + 1] = make_double2(-ih2, 0);
+        if (j > 0) row[p - n] = make_double2(-ih2, 0);
+        if (j < n - 1) row[p + n] = make_double2(-ih2, 0);
+    } else {
+        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j);
+        row[p] = c.d;
+        if (i > 0) row[p - 1] = c.cw;
+        if (i < n - 1) row[p + 1] = c.ce;
+        if (j > 0) row[p - n] = c.cs;
+        if (j < n - 1) row[p + n] = c.cn;
+    }
+}
+
+// In-place LU with partial pivoting (one block).  perm[i] = original row at
+// position i.  Pivot: largest modulus, smallest index on ties.
+__global__ void k_lu(double2* A, int N, int* perm, int* info) {
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < N; i += nt) perm[i] = i;
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+        double best = -1.0;
+        int bidx = k;
+        for (int i = k + t; i < N; i += nt) {
+            const double v = dabs2(A[(long long)i * N + k]);
+            if (v > best) { best = v; bidx = i; }
+        }
+        bv[t] = best;
+        bi[t] = bidx;
+        __syncthreads();
+        for (int s = nt / 2; s > 0; s >>= 1) {
+            if (t < s) {
+                if (bv[t + s] > bv[t] || (bv[t + s] == bv[t] && bi[t + s] < bi[t])) {
+                    bv[t] = bv[t + s];
+                    bi[t] = bi[t + s];
+                }
+            }
+            __syncthreads();
+        }
+        const int piv = bi[0];
+        if (bv[0] <= 0.0 && t == 0) *info = k + 1;
+        __syncthreads();
+        if (piv != k) {
+            for (int q = t; q < N; q += nt) {
+                double2 a = A[(long long)k * N + q];
+                A[(long long)k * N + q] = A[(long long)piv * N + q];
+                A[(long long)piv * N + q] = a;
+            }
+            if (t == 0) { int a = perm[k]; perm[k] = perm[piv]; perm[piv] = a; }
+        }
+        __syncthreads();
+        const double2 akk = A[(long long)k * N + k];
+        for (int i = k + 1 + t; i < N; i += nt) {
+            double2* a = &A[(long long)i * N + k];
+            *a = (dabs2(akk) > 0) ? ddiv(*a, akk) : make_double2(0, 0);
+        }
+        __syncthreads();
+        const int m = N - k - 1;
+        for (long long e = t; e < (long long)m * m; e += nt) {
+            const int i = k + 1 + (int)(e / m), q = k + 1 + (int)(e % m);
+            A[(long long)i * N + q] = dsub(A[(long long)i * N + q], dmul(A[(long long)i * N + k], A[(long long)k * N + q]));
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse from the factors, one column per thread: solve L U x = P e_c.
+__global__ void k_lu_inv(const double2* LU, const int* perm, int N, double2* inv) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    for (int i = 0; i < N; ++i) {
+        double2 s = make_double2(perm[i] == c ? 1.0 : 0.0, 0.0);
+        for (int q = 0; q < i; ++q) s = dsub(s, dmul(LU[(long long)i * N + q], inv[(long long)q * N + c]));
+        inv[(long long)i * N + c] = s;
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double2 s = inv[(long long)i * N + c];
+        for (int q = i + 1; q < N; ++q) s = dsub(s, dmul(LU[(long long)i * N + q], inv[(long long)q * N + c]));
+        inv[(long long)i * N + c] = ddiv(s, LU[(long long)i * N + i]);
+    }
+}
+
+int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                         double omega, int bc, double shift, int which, double2* inv, cudaStream_t st) {
+    const int N = n * n;
+    double2* A = nullptr;
+    int* perm = nullptr;
+    int* info = nullptr;
+    if (cudaMalloc(&A, sizeof(double2) * (size_t)N * N) != cudaSuccess) return MG_ENOMEM;
+    if (cudaMalloc(&perm, sizeof(int) * (N + 1)) != cudaSuccess) { cudaFree(A); return MG_ENOMEM; }
+    info = perm + N;
+    cudaMemsetAsync(info, 0, sizeof(int), st);
+    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, pitch, h, omega, bc, shift, which, A);
+    k_lu<<<1, 1024, 0, st>>>(A, N, perm, info);
+    k_lu_inv<<<(N + 63) / 64, 64, 0, st>>>(A, perm, N, inv);
+    int hinfo = 0;
+    cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(A);
+    cudaFree(perm);
+    if (e != cudaSuccess) {
+        set_error(std::string("coarse LU: ") + cudaGetErrorString(e));
+        return MG_ECUDA;
+    }
+    if (hinfo != 0) {
+        set_error("coarse LU: singular coarsest operator");
+        return MG_EINVAL;
+    }
+    return MG_OK;
+}
+
+}  // namespace wadr

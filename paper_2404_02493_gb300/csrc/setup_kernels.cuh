@@ -1,0 +1,89 @@
+// Setup-time coefficient kernels (FP64 arithmetic, output in the cycle
+// precision).  Included by setup.cu and by the engine translation units.
+#pragma once
+#include "common.cuh"
+
+namespace wadr {
+
+struct AdrCoef {
+    double2 d, cw, ce, cs, cn;
+    double px, py;
+};
+
+// Coefficients of the upwind ADR operator at node (i, j) (eq. ADR in the
+// exp(+i w phi) convention, eq. upwind with the 5-point form of Section 3.3):
+//   L a = d a_c + cw a_W + ce a_E + cs a_S + cn a_N,
+//   d  = 4/h^2 - 2 i w (|px|+|py|)/h - i w Lap(phi) + w^2 (px^2+py^2 - s^2)
+//        [- i w gamma s^2] [- i shift k^2],
+//   cw = -1/h^2 + i w (px+|px|)/h,  ce = -1/h^2 - i w (px-|px|)/h  (same in y),
+// with central differences of phi after linear extrapolation of one ghost
+// layer (second order inside, first order on the boundary, Section 3.2.1).
+__device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
+                                      double h, double omega, int bc, double shift, int i, int j) {
+    auto P = [&](int ii, int jj) { return phi64[(long long)jj * pitch + ii]; };
+    const double pc = P(i, j);
+    const double pw = i > 0 ? P(i - 1, j) : 2.0 * pc - P(i + 1, j);
+    const double pe = i < n - 1 ? P(i + 1, j) : 2.0 * pc - P(i - 1, j);
+    const double ps = j > 0 ? P(i, j - 1) : 2.0 * pc - P(i, j + 1);
+    const double pn = j < n - 1 ? P(i, j + 1) : 2.0 * pc - P(i, j - 1);
+    const double px = (pe - pw) / (2.0 * h), py = (pn - ps) / (2.0 * h);
+    const double lap = (pe + pw + pn + ps - 4.0 * pc) / (h * h);
+    const long long p = (long long)j * pitch + i;
+    const double k = k64[p];
+    const double s2 = (k / omega) * (k / omega);
+    const double ax = fabs(px), ay = fabs(py);
+    AdrCoef c;
+    double dre = 4.0 / (h * h) + omega * omega * (px * px + py * py - s2);
+    double dim = -2.0 * omega * (ax + ay) / h - omega * lap;
+    if (bc == BC_SPONGE) dim -= sig64[p];
+    if (shift != 0.0) dim -= shift * k * k;
+    c.d = make_double2(dre, dim);
+    const double ih2 = 1.0 / (h * h), wh = omega / h;
+    c.cw = make_double2(-ih2, wh * (px + ax));
+    c.ce = make_double2(-ih2, -wh * (px - ax));
+    c.cs = make_double2(-ih2, wh * (py + ay));
+    c.cn = make_double2(-ih2, -wh * (py - ay));
+    c.px = px;
+    c.py = py;
+    return c;
+}
+
+template <typename T>
+__global__ void k_fields(const double* k64, const double* sig64, int n, int pitch, T* kf, T* sigf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const long long p = (long long)j * pitch + i;
+    kf[p] = (T)k64[p];
+    if (sigf) sigf[p] = (T)sig64[p];
+}
+
+template <typename T>
+__global__ void k_adr_fields(const double* phi64, const double* k64, const double* sig64, int n, int pitch, double h,
+                             double omega, int bc, double shift, quad<T>* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j);
+    quad<T> q;
+    q.x = (T)c.px;
+    q.y = (T)c.py;
+    q.z = (T)c.d.x;
+    q.w = (T)c.d.y;
+    out[(long long)j * pitch + i] = q;
+}
+
+// exp(+i w phi) at level 2, argument and sincos in FP64 (Section 3.2, eq.
+// Rytov).
+template <typename T>
+__global__ void k_mod_field(const double* phi64, int n, int pitch, double omega, cplx<T>* mod) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const long long p = (long long)j * pitch + i;
+    double s, c;
+    sincos(omega * phi64[p], &s, &c);
+    mod[p] = from_d<T>(make_double2(c, s));
+}
+
+}  // namespace wadr

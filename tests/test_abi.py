@@ -1,0 +1,51 @@
+"""The C ABI builds, loads and exports every function include/wave_adr.h
+declares, and the binding's struct layouts match the header (no GPU needed,
+no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2404_02493_gb300 import binding, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "wave_adr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mg_setup", "mg_cycle", "mg_solve", "mg_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert names, "no declarations parsed"
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(binding.exported_symbols()) == names
+
+
+def test_struct_layouts_match(lib):
+    p, i, s = binding.mg_abi_sizes()
+    assert p == ctypes.sizeof(binding.MgParams)
+    assert i == ctypes.sizeof(binding.MgInstance)
+    assert s == ctypes.sizeof(binding.MgSolveInfo)
+
+
+def test_default_params_are_the_papers(lib):
+    p = binding.default_params()
+    assert (p.jacobi_iters, p.cheb_iters, p.coarse_cheb_iters, p.M, p.restart) == (1, 5, 10, 8, 20)
+    assert p.tol == 1e-6 and p.adr == 1 and p.n_cmax == 15
