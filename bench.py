@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the Wave-ADR solve on one GB300 per rank.
+
+Workload: n = 4095 x 4095 interior points, omega = 2000 (k up to 2000,
+k h <= 0.49), six smoothed horizontal layers c in [1.5, 4.5] times
+(1 + 0.1 GRF), centred Gaussian source, eikonal phase; complex-FP32 Wave-ADR
+cycles inside FP64 iterative refinement (the mixed form), n_cmax = 15 (9
+levels), M = 8 ADR corrections.
+
+A step is one outer iteration: FP64 scaling of the residual, one Wave-ADR
+cycle (all of Algorithm 1: Jacobi, Chebyshev, transfers, 8 ADR corrections
+with their GMRES(3) V-cycles, coarsest LU), FP64 update and FP64 residual.
+`value` = cycles per second over all ranks (each rank solves its own
+replica; the single solve does not shard).  Also reported: time to 1e-6
+relative residual, an end-to-end rate through the C ABI with host buffers,
+the roofline of the dominant kernel (CUDA-event profile), and the oracle on
+the host cores.
+
+--impl reference times the oracle (plain complex128 NumPy) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 rel. residual and cycles/s at n=4095,k≈2000; HBM GB/s vs peak"
+UNIT = "cycles/s"
+N_FULL, OMEGA_FULL = 4095, 2000.0
+N_SAMPLE, OMEGA_SAMPLE = 1023, 500.0      # same medium recipe and k h, 1/16 of the points
+
+
+def workload_config(n, omega):
+    return {"workload": f"layered GRF medium n={n} omega={omega:g} (k h <= 0.49), complex-FP32 Wave-ADR "
+                        f"cycles in FP64 iterative refinement, M=8, n_cmax=15",
+            "n": n, "omega": omega, "outer": "IR (FP64 residual and update)", "cycle_dtype": "complex64",
+            "l2": "inputs larger than L2: level-1 vectors are 134 MB each and a step streams ~20 GB"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_cycle_rate(steps: int, warmup: int):
+    """The oracle (complex128 NumPy, single thread) on the sample workload:
+    seconds per outer step (residual, one cycle, update)."""
+    import synth
+    import oracle
+    from oracle.cycle import CycleParams, Hierarchy
+    inst = synth.config_layered(n=N_SAMPLE, omega=OMEGA_SAMPLE, seed=5)
+    H = Hierarchy(inst.n, inst.k, inst.phi, inst.omega, inst.bc, CycleParams(n_cmax=15))
+    u = np.zeros_like(inst.g)
+    lev = H.lev(1)
+
+    def step(u):
+        r = inst.g - oracle.helmholtz_apply(lev, u)
+        nr = np.linalg.norm(r)
+        return u + nr * H.cycle(np.zeros_like(r), r / nr)
+
+    for _ in range(warmup):
+        u = step(u)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = step(u)
+    dt = (time.perf_counter() - t0) / max(steps, 1)
+    return dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    dt = oracle_cycle_rate(args.steps, args.warmup)
+    scale = (N_SAMPLE / N_FULL) ** 2        # work per cycle is proportional to the points
+    value = scale / dt
+    sample = (f"oracle outer steps on the same recipe at n={N_SAMPLE}, omega={OMEGA_SAMPLE:g} "
+              f"({dt:.2f} s per step), scaled to n={N_FULL} by the point ratio {scale:.4f}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / scale,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": workload_config(N_FULL, OMEGA_FULL),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- ours
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2404_02493_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    v = d.get("kernels", {}).get(kernel)
+    return None if v is None else float(v["dram_bytes_per_launch_full"])
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2404_02493_gb300 import binding as B
+    from paper_2404_02493_gb300 import build as Bd
+    if not Bd.up_to_date():
+        raise RuntimeError("CUDA library not built; run __graft_entry__.build() first")
+    B.load()
+    import synth
+    n, omega = args.n, args.omega
+    t0 = time.time()
+    inst = synth.config_layered(n=n, omega=omega, seed=5)
+    t_inputs = time.time() - t0
+    dev = torch.device("cuda", local)
+    k = torch.from_numpy(inst.k).to(dev)
+    phi = torch.from_numpy(inst.phi).to(dev)
+    g = torch.from_numpy(inst.g).to(dev)
+    params = B.default_params(precision="mixed", n_cmax=15, tol=1e-6, maxit=args.tts_maxit)
+    st = torch.cuda.current_stream()
+    t0 = time.time()
+    h = B.mg_setup([(n, omega, k, phi, "abc1")], params, stream=st)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    u0 = torch.zeros_like(g)
+
+    # ---- timed region: exactly K outer steps (cycles)
+    B.mg_solve_begin(h, u0, g, stream=st)
+    B.mg_solve_steps(h, args.warmup, stream=st)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    B.mg_solve_steps(h, args.steps, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    rel_after = B.mg_solve_end(h, stream=st)
+    value = ws * args.steps / (ms * 1e-3)
+    launches_per_step = B.mg_step_launches(h)
+
+    # ---- per-kernel CUDA-event profile (non-graph emission of 2 steps)
+    prof = B.mg_profile_steps(h, 2, stream=st)
+    tot_ms = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda kname: prof[kname][0])
+    d_ms, d_bytes, d_launch = prof[dom]
+    achieved = d_bytes / (d_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": d_bytes / d_launch, "launches_per_step": d_launch / 2,
+                "share_of_step": d_ms / tot_ms}
+    step_bytes = sum(v[1] for v in prof.values()) / 2
+    cycle_roofline = {"algorithmic_GB_per_step": step_bytes / 1e9,
+                      "achieved_GBps": step_bytes / (ms * 1e-3 / args.steps) / 1e9,
+                      "frac_of_peak": step_bytes / (ms * 1e-3 / args.steps) / 1e9 / peak}
+    kernels = {kn: {"ms_per_step": v[0] / 2, "share": v[0] / tot_ms, "launches_per_step": v[2] // 2,
+                    "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None} for kn, v in prof.items()}
+
+    # ---- time to tolerance (zero start)
+    tts = None
+    if not args.no_tts:
+        u = torch.zeros_like(g)
+        w0 = time.time()
+        status, its, rr, hist, secs = B.mg_solve(h, u, g, history_len=0, stream=st)
+        tts = {"status": {0: "converged", -4: "maxit", -5: "diverged"}.get(status, status), "iterations": its,
+               "rel_residual": rr, "device_seconds": secs, "wall_seconds": time.time() - w0, "tol": 1e-6}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hg = torch.from_numpy(inst.g).pin_memory()
+    hu = torch.zeros_like(hg).pin_memory()
+    e2e_steps = max(3, min(args.steps // 4, 20))
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.mg_solve_begin(h, hu, hg, stream=st)
+        B.mg_solve_steps(h, 1, stream=st)
+        B.mg_solve_end(h, hu, stream=st)
+    e2e_s = time.perf_counter() - w0
+    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 16,
+           "d2h_bytes_per_step": n * n * 16 + 8,
+           "note": "per step: H2D of u and g (complex128, pinned), FP64 residual, one outer step, "
+                   "D2H of u and the residual norm, all through mg_solve_begin/steps/end"}
+    B.mg_destroy(h)
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        dt = oracle_cycle_rate(2, 0)
+        scale = (N_SAMPLE / N_FULL) ** 2
+        cpu = {"value": scale / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2 oracle outer steps on the same recipe at n={N_SAMPLE}, omega={OMEGA_SAMPLE:g} "
+                         f"({dt:.2f} s each), scaled to n={N_FULL} by the point ratio {scale:.4f}"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n, omega), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "time_to_tolerance": tts, "rel_residual_after_timed_steps": rel_after,
+            "cycle_roofline": cycle_roofline, "kernels": kernels,
+            "setup_seconds": t_setup, "input_generation_seconds": t_inputs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--omega", type=float, default=OMEGA_FULL)
+    ap.add_argument("--tts-maxit", type=int, default=3000)
+    ap.add_argument("--no-tts", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -147,8 +147,38 @@ int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream
  * iteration.  Returns MG_OK, MG_ENOTCONV or MG_EDIVERGED (also in info). */
 int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_stream stream);
 
+/* Building blocks of mg_solve for callers that drive the outer iteration
+ * themselves (and for timing exactly K steps).
+ * mg_solve_begin: load the complex128 initial guess u and right-hand side g
+ *   and compute r = g - A u, ||r||, ||g|| in FP64 (asynchronous).
+ * mg_solve_steps: `nsteps` iterative-refinement steps
+ *   u <- u + ||r|| cycle(0, r/||r||), each followed by the FP64 residual
+ *   (Section 4.3.1 uses the cycle as the preconditioner of the outer
+ *   iteration); asynchronous, replayed as one CUDA graph per step when
+ *   use_graph is set.
+ * mg_solve_end: copy u back (if u != NULL) and return the largest relative
+ *   residual over the instances; synchronises `stream`. */
+int mg_solve_begin(mg_handle* h, const void* u, const void* g, mg_stream stream);
+int mg_solve_steps(mg_handle* h, int nsteps, mg_stream stream);
+int mg_solve_end(mg_handle* h, void* u, double* rel_residual, mg_stream stream);
+
 /* Free the workspace. */
 void mg_destroy(mg_handle* h);
+
+/* ------------------------------------------------------------------------
+ * Measurement.  mg_profile_steps runs `nsteps` outer steps (after
+ * mg_solve_begin) without the graph, brackets every kernel launch with CUDA
+ * events on `stream`, and accumulates per kernel kind k < nkinds: device
+ * milliseconds ms[k], algorithmic bytes bytes[k] (each input read once, each
+ * output written once) and launches[k].  nkinds must be >= MG_KERNEL_KINDS.
+ * mg_kernel_name gives the kind's name.  mg_step_launches: kernels of one
+ * outer step.
+ * ---------------------------------------------------------------------- */
+#define MG_KERNEL_KINDS 24
+int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* launches, int nkinds,
+                     mg_stream stream);
+const char* mg_kernel_name(int kind);
+int mg_step_launches(const mg_handle* h);
 
 /* ------------------------------------------------------------------------
  * Level operations: single-instance entry points into the same kernels the

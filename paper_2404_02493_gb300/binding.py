@@ -80,6 +80,12 @@ def load():
         "mg_coarse_solve": (ip, [vp, ip, ip, vp, vp, vp]),
         "mg_cycle_launches": (ip, [vp]),
         "mg_abi_sizes": (None, [ctypes.POINTER(ctypes.c_size_t)] * 3),
+        "mg_solve_begin": (ip, [vp, vp, vp, vp]),
+        "mg_solve_steps": (ip, [vp, ip, vp]),
+        "mg_solve_end": (ip, [vp, vp, ctypes.POINTER(dp), vp]),
+        "mg_profile_steps": (ip, [vp, ip, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
+        "mg_kernel_name": (ctypes.c_char_p, [ip]),
+        "mg_step_launches": (ip, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -94,7 +100,9 @@ def exported_symbols():
     return ["mg_default_params", "mg_last_error", "mg_setup", "mg_cycle", "mg_solve", "mg_destroy",
             "mg_num_levels", "mg_level_n", "mg_level_scalars", "mg_apply", "mg_residual",
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
-            "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes"]
+            "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
+            "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
+            "mg_step_launches"]
 
 
 class MgError(RuntimeError):
@@ -257,3 +265,33 @@ def mg_abi_sizes():
     a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
     load().mg_abi_sizes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return a.value, b.value, c.value
+
+
+MG_KERNEL_KINDS = 24
+
+
+def mg_solve_begin(h, u, g, stream=None):
+    _check(load().mg_solve_begin(h, _ptr(u), _ptr(g), _stream(stream)), "mg_solve_begin")
+
+
+def mg_solve_steps(h, nsteps, stream=None):
+    _check(load().mg_solve_steps(h, int(nsteps), _stream(stream)), "mg_solve_steps")
+
+
+def mg_solve_end(h, u=None, stream=None):
+    r = ctypes.c_double()
+    _check(load().mg_solve_end(h, _ptr(u), ctypes.byref(r), _stream(stream)), "mg_solve_end")
+    return r.value
+
+
+def mg_profile_steps(h, nsteps, stream=None):
+    """Per kernel kind: {name: (ms, algorithmic bytes, launches)} over nsteps."""
+    n = MG_KERNEL_KINDS
+    ms, by, la = (ctypes.c_double * n)(), (ctypes.c_double * n)(), (ctypes.c_int * n)()
+    _check(load().mg_profile_steps(h, int(nsteps), ms, by, la, n, _stream(stream)), "mg_profile_steps")
+    lib = load()
+    return {lib.mg_kernel_name(k).decode(): (ms[k], by[k], la[k]) for k in range(n) if la[k] > 0}
+
+
+def mg_step_launches(h):
+    return load().mg_step_launches(h)

@@ -83,20 +83,30 @@ struct LevelDesc {
     const void* mod;        // exp(+i w phi) (cplx<T>), level 2 only, or null
     const double2* inv_helm;  // coarsest level: dense inverse of A (FP64), N x N
     const double2* inv_adr;   // coarsest level: dense inverse of L_ADR (FP64)
-    double* scal;           // scalar area (see namespace S)
-    double2* part;          // reduction partials [max_blocks][MAXDOT]
+    void* scal;             // scalar area (see namespace S), working precision T
+    void* part;             // reduction partials [max_blocks][MAXDOT] of cplx<T>
     unsigned* counter;      // last-block counters [NCOUNTERS]
     int n, pitch;
     double h, inv_h2;
     double omega;           // scalar angular frequency (ADR)
     double shift;           // shifted Helmholtz coefficient (0: none)
+    double wh;              // omega / h
+    // the same constants in FP32, so FP32 kernels do no per-point FP64 work
+    float fh, fih2, fwh, fshift;
+    int has_shift;
     int bc;
     int inst;               // instance index
     int level;              // 1-based level
     int coarse;             // descriptor index of level+1 (same table), -1 if none
-    int pad_;
-    void* xvec;             // partner vectors in the other precision (outer <-> cycle level 1)
+    int krestart;           // outer: FGMRES restart length m
+    void* xvec;             // outer: the cycle's level-1 slots (cycle precision)
     long long xstride;
+    const void* xkf;        // outer: the cycle's level-1 k field (cycle precision)
+    const void* xsig;       // outer: the cycle's level-1 sponge term or null
+    void* kv;               // outer: Krylov vectors V_0..V_m, Z_0..Z_{m-1} (cycle precision)
+    double* fs;             // outer: FGMRES scalars
+    double2* fpart;         // outer: FGMRES reduction partials [MAXB][NVF]
+    double* est;            // outer: |gamma_{j+1}| of this instance (contiguous over instances)
 };
 
 struct Seg {
@@ -105,6 +115,24 @@ struct Seg {
     int blk1;     // one past the last block
     int pad;
 };
+
+template <typename T> struct LC;
+template <> struct LC<float> {
+    static __device__ __forceinline__ float h(const LevelDesc& d) { return d.fh; }
+    static __device__ __forceinline__ float ih2(const LevelDesc& d) { return d.fih2; }
+    static __device__ __forceinline__ float wh(const LevelDesc& d) { return d.fwh; }
+    static __device__ __forceinline__ float shift(const LevelDesc& d) { return d.fshift; }
+};
+template <> struct LC<double> {
+    static __device__ __forceinline__ double h(const LevelDesc& d) { return d.h; }
+    static __device__ __forceinline__ double ih2(const LevelDesc& d) { return d.inv_h2; }
+    static __device__ __forceinline__ double wh(const LevelDesc& d) { return d.wh; }
+    static __device__ __forceinline__ double shift(const LevelDesc& d) { return d.shift; }
+};
+template <typename T> __device__ __forceinline__ T* scalp(const LevelDesc& d) { return reinterpret_cast<T*>(d.scal); }
+template <typename T> __device__ __forceinline__ cplx<T>* partp(const LevelDesc& d) {
+    return reinterpret_cast<cplx<T>*>(d.part);
+}
 
 constexpr int MAXDOT = 8;        // complex partial sums per block
 constexpr int NCOUNTERS = 8;
@@ -131,6 +159,7 @@ constexpr int CHEB_N = 83;    // number of Chebyshev steps stored
 constexpr int CHEB_C1 = 84;   // d_m = c1[m] d_{m-1} + c2[m] s_m   (<= 16 steps)
 constexpr int CHEB_C2 = 100;
 constexpr int SCALE = 116;    // generic scale factor (outer loop)
+constexpr int SC2 = 117, SC3 = 118, SC4 = 119;  // GMRES vector pre-scales 1/|w_j|
 constexpr int SIZE = 128;
 }  // namespace S
 
@@ -151,7 +180,7 @@ template <typename T> __device__ __forceinline__ cplx<T>* slot(const LevelDesc& 
 //   - i shift h^2 k^2             [shifted Helmholtz]
 template <typename T>
 __device__ __forceinline__ cplx<T> helm_diag_h2(const LevelDesc& d, int i, int j, T k, T sig) {
-    T h = (T)d.h;
+    T h = LC<T>::h(d);
     T kh = k * h;
     T re = T(4) - kh * kh;
     T im = T(0);
@@ -162,7 +191,7 @@ __device__ __forceinline__ cplx<T> helm_diag_h2(const LevelDesc& d, int i, int j
     } else if (d.bc == BC_SPONGE) {
         im -= h * h * sig;
     }
-    if (d.shift != 0.0) im -= (T)d.shift * kh * kh;
+    if (d.has_shift) im -= LC<T>::shift(d) * kh * kh;
     return mk<T>(re, im);
 }
 
@@ -177,10 +206,14 @@ template <typename T> __device__ __forceinline__ cplx<T> helm_diag_at(const Leve
 }
 
 // --------------------------------------------------- deterministic reductions
-// Block-level sum of NV complex doubles in a fixed order (warp shuffle tree,
+// Element type E: float2 or double2 (complex partial sums).
+template <typename E> __device__ __forceinline__ E eadd(E a, E b) { E r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename E> __device__ __forceinline__ E ezero() { E r; r.x = 0; r.y = 0; return r; }
+
+// Block-level sum of NV complex values in a fixed order (warp shuffle tree,
 // then warps in index order).  Result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double2 (&v)[NV], double2* sh /* >= 8*NV */) {
+template <typename E, int NV>
+__device__ __forceinline__ void block_sum(E (&v)[NV], E* sh /* >= 8*NV */) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
@@ -201,25 +234,25 @@ __device__ __forceinline__ void block_sum(double2 (&v)[NV], double2* sh /* >= 8*
         const int nw = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double2 s = sh[k];
-            for (int w = 1; w < nw; ++w) s = dadd(s, sh[w * NV + k]);
+            E s = sh[k];
+            for (int w = 1; w < nw; ++w) s = eadd(s, sh[w * NV + k]);
             v[k] = s;
         }
     }
     __syncthreads();
 }
 
-// Publish this block's partials (thread 0 holds them) and return true in the
-// block that finishes last within its segment.
-template <int NV>
-__device__ __forceinline__ bool publish_partials(const LevelDesc& d, int lb, int nb, int ctr,
-                                                 const double2 (&v)[NV], int* flag_sh) {
+// Publish this block's partials (thread 0 holds them) into part[lb][stride]
+// and return true in the block that finishes last within its segment.
+template <typename E, int NV>
+__device__ __forceinline__ bool publish_partials(E* part, int stride, unsigned* counter, int lb, int nb,
+                                                 const E (&v)[NV], int* flag_sh) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) d.part[(long long)lb * MAXDOT + k] = v[k];
+        for (int k = 0; k < NV; ++k) part[(long long)lb * stride + k] = v[k];
         __threadfence();
-        unsigned prev = atomicAdd(&d.counter[ctr], 1u);
+        unsigned prev = atomicAdd(counter, 1u);
         *flag_sh = (prev == (unsigned)(nb - 1));
     }
     __syncthreads();
@@ -227,22 +260,22 @@ __device__ __forceinline__ bool publish_partials(const LevelDesc& d, int lb, int
 }
 
 // In the last block: sum the partials of blocks 0..nb-1 (thread t takes
-// blocks t, t+NT, ...; then the fixed block tree).  Result in out[0..NV) of
+// blocks t, t+NT, ...; then the fixed block tree).  Result in out[] of
 // thread 0.  Resets the counter for the next use.
-template <int NV>
-__device__ __forceinline__ void finish_partials(const LevelDesc& d, int nb, int ctr, double2 (&out)[NV],
-                                                double2* sh) {
+template <typename E, int NV>
+__device__ __forceinline__ void finish_partials(const E* part, int stride, unsigned* counter, int nb, E (&out)[NV],
+                                                E* sh) {
     __threadfence();
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nt = blockDim.x * blockDim.y;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < NV; ++k) out[k] = ezero<E>();
     for (int b = tid; b < nb; b += nt) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = dadd(out[k], __ldcg(&d.part[(long long)b * MAXDOT + k]));
+        for (int k = 0; k < NV; ++k) out[k] = eadd(out[k], __ldcg(&part[(long long)b * stride + k]));
     }
-    block_sum<NV>(out, sh);
-    if (tid == 0) d.counter[ctr] = 0u;
+    block_sum<E, NV>(out, sh);
+    if (tid == 0) *counter = 0u;
 }
 
 }  // namespace wadr

@@ -2,6 +2,10 @@
 // Emits Algorithm 1 as batched launches: at every level one launch covers all
 // instances that have that level (segment tables), so a batch of uneven grids
 // runs with the same number of launches as a single problem.
+//
+// Every launch goes through `go`, which counts it and, when the handle is in
+// profiling mode, brackets it with CUDA events and records its kernel kind
+// and algorithmic bytes (each input read once, each output written once).
 #pragma once
 #include <algorithm>
 #include <cstring>
@@ -9,6 +13,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "fgmres.cuh"
 #include "kernels.cuh"
 #include "setup_kernels.cuh"
 
@@ -16,9 +21,22 @@ namespace wadr {
 
 template <typename T>
 struct Engine : EngineBase {
-    static constexpr int kPts = 2048;   // points per block before capping
+    static constexpr int kPts = 256;    // one 32 x 8 tile per block until the 8-blocks-per-SM cap
+    static constexpr double C = 2.0 * sizeof(T);   // bytes of a complex value
+    static constexpr double R = sizeof(T);         // bytes of a real value
+    static constexpr double Q = 4.0 * sizeof(T);   // bytes of an ADR coefficient quad
 
-    static void count(Handle& H) { H.launches_cycle++; }
+    template <class F>
+    static void go(Handle& H, cudaStream_t st, int kind, double bytes, F&& f) {
+        if (H.prof) prof_begin(H, st);
+        f();
+        H.launches_cycle++;
+        if (H.prof) prof_end(H, st, kind, bytes);
+    }
+#define LAUNCH(kind, t, bpp, kern, ...)                                                              \
+    go(H, st, kind, (bpp) * (double)(t).pts, [&] {                                                    \
+        kern<<<(t).nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, (t).d, (t).nseg, __VA_ARGS__);            \
+    })
 
     std::vector<int> descs(Handle& H, int level, const std::vector<int>& I) {
         std::vector<int> d;
@@ -51,27 +69,29 @@ struct Engine : EngineBase {
         int cur = xin;
         int out = from_zero ? ((q & 1) ? SU : SX2) : (xin == SU ? SX2 : SU);
         for (int m = 0; m < q; ++m) {
-            int flags = (m == 0 && from_zero ? 1 : 0) | (m == q - 1 ? 2 : 0);
-            k_cheb_step<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, cur, out, m, flags);
-            count(H);
+            const bool xz = (m == 0 && from_zero), last = (m == q - 1);
+            const int flags = (xz ? 1 : 0) | (last ? 2 : 0);
+            // reads x (unless zero), g, k, d (m > 0); writes x, d (unless last)
+            const double bpp = (xz ? 0 : C) + C + R + (m > 0 ? C : 0) + C + (last ? 0 : C);
+            LAUNCH(KK_CHEB, t, bpp, k_cheb_step<T>, cur, out, m, flags);
             cur = out;
             out = (cur == SU) ? SX2 : SU;
         }
     }
 
     void gmres(Handle& H, const SegTable& t, int sr0, cudaStream_t st) {
-        dim3 bd(BX, BY);
-        k_gm_a1<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, sr0);
-        k_gm_a23<T, 2><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, sr0);
-        k_gm_a23<T, 3><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, sr0);
-        k_gm_b3<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, sr0);
-        count(H); count(H); count(H); count(H);
+        LAUNCH(KK_GM_A1, t, 2 * C + Q, k_gm_a1<T>, sr0);
+        LAUNCH(KK_GM_A2, t, 4 * C + Q, (k_gm_a23<T, 2>), sr0);
+        LAUNCH(KK_GM_A3, t, 5 * C + Q, (k_gm_a23<T, 3>), sr0);
+        LAUNCH(KK_GM_B3, t, 4 * C, k_gm_b3<T>, sr0);
     }
 
     void coarse_solve(Handle& H, const std::vector<int>& I, int level, int which, cudaStream_t st) {
         const SegTable& t = H.seg_rows(descs(H, level, I), NT / 32);
-        k_coarse<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, which);
-        count(H);
+        // the dense FP64 inverse is read once, plus the two vectors
+        go(H, st, KK_COARSE, 16.0 * (double)t.mat + 2 * C * (double)t.pts, [&] {
+            k_coarse<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, which);
+        });
     }
 
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
@@ -83,24 +103,19 @@ struct Engine : EngineBase {
         if (!co.empty()) coarse_solve(H, co, l, 1, st);
         if (rest.empty()) return;
         const SegTable& t = H.seg(descs(H, l, rest), false, kPts);
-        dim3 bd(BX, BY);
         gmres(H, t, SAB, st);   // pre-smoothing from x = 0: r0 = b
-        k_restrict<T, MODE_GMRES><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAX, SAB, SAB, 0);
-        count(H);
+        LAUNCH(KK_RESTRICT_GMRES, t, 5 * C + C / 4, (k_restrict<T, MODE_GMRES>), SAX, SAB, SAB, 0);
         adrv(H, l + 1, rest, false, st);
-        k_prolong<T, PMODE_ADR><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAX, SAX, SAB, SV1, SD, 0);
-        count(H);
+        LAUNCH(KK_PROLONG_ADR, t, 4 * C + C / 4 + Q, (k_prolong<T, PMODE_ADR>), SAX, SAX, SAB, SV1, SD, 0);
         gmres(H, t, SV1, st);   // post-smoothing from x' (r0 = b - L x')
-        k_gm_update<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SV1, SD, modulate ? 1 : 0);
-        count(H);
+        LAUNCH(KK_GM_UPDATE, t, modulate ? 7 * C : 5 * C, k_gm_update<T>, SV1, SD, modulate ? 1 : 0);
     }
 
     // Algorithm 1's ADR correction steps at level 2 (M times).
     void adr_corrections(Handle& H, const std::vector<int>& I, int M, cudaStream_t st) {
         const SegTable& t = H.seg(descs(H, 2, I), false, kPts);
         for (int m = 0; m < M; ++m) {
-            k_resdemod<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg);
-            count(H);
+            LAUNCH(KK_RESDEMOD, t, 4 * C + R, k_resdemod<T>, 0);
             adrv(H, 2, I, true, st);
         }
     }
@@ -119,21 +134,18 @@ struct Engine : EngineBase {
         }
         if (rest.empty()) return;
         const SegTable& t = H.seg(descs(H, l, rest), false, kPts);
-        dim3 bd(BX, BY);
         const int q = H.p.cheb_iters;
         const bool smooth = (l != 3);      // no smoothing on level 3 (Section 3.1.3)
         if (smooth) cheb_steps(H, t, q, SU, true, st);
-        k_restrict<T, MODE_HELM><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SG, SG, smooth ? 0 : 1);
-        count(H);
+        LAUNCH(KK_RESTRICT_HELM, t, smooth ? 2 * C + R + C / 4 : C + C / 4, (k_restrict<T, MODE_HELM>), SU, SG,
+               SG, smooth ? 0 : 1);
         wave(H, l + 1, rest, st);
         if (!smooth) {
-            k_prolong<T, PMODE_ADD><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SU, SG, SU, SU, 1);
-            count(H);
+            LAUNCH(KK_PROLONG_ADD, t, C + C / 4, (k_prolong<T, PMODE_ADD>), SU, SU, SG, SU, SU, 1);
             return;
         }
         const int out = (q & 1) ? SX2 : SU;
-        k_prolong<T, PMODE_ADD><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SU, SG, out, out, 0);
-        count(H);
+        LAUNCH(KK_PROLONG_ADD, t, 2 * C + C / 4, (k_prolong<T, PMODE_ADD>), SU, SU, SG, out, out, 0);
         cheb_steps(H, t, q, out, false, st);
         if (l == 2 && H.p.adr && H.p.M > 0) adr_corrections(H, rest, H.p.M, st);
     }
@@ -150,36 +162,91 @@ struct Engine : EngineBase {
         H.launches_cycle = 0;   // recounted on every emission
         std::vector<int> I = all(H);
         const SegTable& t = H.seg(descs(H, 1, I), false, kPts);
-        dim3 bd(BX, BY);
         if (uzero) {
-            k_restrict<T, MODE_JAC0><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SG, SG, 1);
-            count(H);
+            LAUNCH(KK_RESTRICT_JAC0, t, 2 * C + R + C / 4, (k_restrict<T, MODE_JAC0>), SU, SG, SG, 1);
         } else {
-            k_jacobi<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SX2, SG, SU, 0);
-            k_restrict<T, MODE_HELM><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SG, SG, 0);
-            count(H); count(H);
+            LAUNCH(KK_JACOBI, t, 3 * C + R, k_jacobi<T>, SX2, SG, SU, 0);
+            LAUNCH(KK_RESTRICT_HELM, t, 2 * C + R + C / 4, (k_restrict<T, MODE_HELM>), SU, SG, SG, 0);
         }
         wave(H, 2, I, st);
-        k_prolong<T, PMODE_JAC><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SU, SG, SD, SD, 0);
-        count(H);
+        LAUNCH(KK_PROLONG_JAC, t, 3 * C + C / 4 + R, (k_prolong<T, PMODE_JAC>), SU, SU, SG, SD, SD, 0);
+    }
+
+    const SegTable& outer_tab(Handle& H) {
+        std::vector<int> d;
+        for (auto& I : H.inst) d.push_back(I.outer_desc);
+        return H.seg(d, true, kPts);
     }
 
     void outer_residual(Handle& H, bool gnorm, cudaStream_t st) override {
-        std::vector<int> d;
-        for (auto& I : H.inst) d.push_back(I.outer_desc);
-        const SegTable& t = H.seg(d, true, kPts);
-        k_outer_residual<0><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, gnorm ? 1 : 0);
+        const SegTable& t = outer_tab(H);
+        go(H, st, KK_OUTER_RESIDUAL, (gnorm ? 64.0 : 56.0) * t.pts, [&] {
+            k_outer_residual<0><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, gnorm ? 1 : 0);
+        });
     }
 
     // u += ||r|| cycle(0, r/||r||); r = g - A u, ||r||  (iterative refinement)
     void ir_step(Handle& H, cudaStream_t st) override {
-        std::vector<int> d;
-        for (auto& I : H.inst) d.push_back(I.outer_desc);
-        const SegTable& t = H.seg(d, true, kPts);
-        k_outer_scale<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, SD);
+        const SegTable& t = outer_tab(H);
+        go(H, st, KK_OUTER_SCALE, (16.0 + C) * t.pts, [&] {
+            k_outer_scale<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, SD);
+        });
         cycle(H, true, st);
-        k_outer_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
-        k_outer_residual<0><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, 0);
+        const int cyc = H.launches_cycle;
+        go(H, st, KK_OUTER_UPDATE, (32.0 + C) * t.pts, [&] {
+            k_outer_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
+        });
+        outer_residual(H, false, st);
+        H.launches_cycle = cyc;
+        H.launches_step = cyc + 3;
+    }
+
+    // ------------------------------------------------------------ FGMRES
+    // Restart start: V_0 = r/||r|| from the FP64 residual.
+    void fg_start(Handle& H, cudaStream_t st) override {
+        const SegTable& t = outer_tab(H);
+        go(H, st, KK_FG_START, (16.0 + C) * t.pts, [&] {
+            k_fg_start<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
+        });
+        H.fg_j = 0;
+    }
+
+    // One inner iteration: z_j = cycle(0, V_j), W = A z_j, CGS2 against
+    // V_0..V_j, Hessenberg column and Givens rotation.
+    void fg_iter(Handle& H, cudaStream_t st) override {
+        const SegTable& t = outer_tab(H);
+        const int j = H.fg_j;
+        dim3 bd(BX, BY);
+        go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
+            k_fg_prep<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
+        });
+        cycle(H, true, st);
+        const int cyc = H.launches_cycle;
+        go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
+            k_fg_matvec<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
+        });
+        go(H, st, KK_FG_DOTS, (j + 2) * C * t.pts, [&] {
+            k_fg_dots<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
+        });
+        go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
+            k_fg_orth<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg, 1);
+        });
+        go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
+            k_fg_orth<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg, 2);
+        });
+        H.launches_cycle = cyc;
+        H.launches_step = cyc + 5;
+        H.fg_j = j + 1;
+    }
+
+    // Restart end: u += ||r|| Z y (FP64), r = g - A u (FP64).
+    void fg_finish(Handle& H, cudaStream_t st) override {
+        const SegTable& t = outer_tab(H);
+        go(H, st, KK_FG_UPDATE, (H.fg_j * C + 32.0) * t.pts, [&] {
+            k_fg_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
+        });
+        outer_residual(H, false, st);
+        H.fg_j = 0;
     }
 
     // ------------------------------------------------------------ level ops
@@ -232,7 +299,7 @@ struct Engine : EngineBase {
             adrv(H, level, I, false, st);
             return SAX;
         case OP_ADRCORR:
-            k_resdemod<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg);
+            k_resdemod<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, 0);
             adrv(H, level, I, true, st);
             return SU;
         case OP_COARSE:
@@ -241,6 +308,7 @@ struct Engine : EngineBase {
         }
         return -1;
     }
+#undef LAUNCH
 };
 
 }  // namespace wadr

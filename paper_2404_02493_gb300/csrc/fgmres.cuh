@@ -1,0 +1,336 @@
+// Flexible GMRES(m) around the Wave-ADR cycle (Section 4.3.1: the cycle is
+// used as the preconditioner of FGMRES with restart 20; Saad 1993).
+//
+// Mixed form: the Krylov vectors V_0..V_m and the preconditioned vectors
+// Z_0..Z_{m-1} are stored in the cycle precision TC; every restart solves
+// A e = r/||r|| from e = 0 and the solution update u += ||r|| Z y and the
+// residual r = g - A u are FP64 (iterative refinement around FGMRES).
+// Arnoldi: classical Gram-Schmidt with one re-orthogonalisation (CGS2),
+// FP64 reductions of per-thread partial sums, Givens rotations on the device.
+// The inner index j lives in device memory (fs[FS_J]) so one captured graph
+// serves every inner iteration.
+#pragma once
+#include "kernels.cuh"
+
+namespace wadr {
+
+constexpr int MAXR = 22;     // largest restart length
+constexpr int NVF = 24;      // dots per block partial (MAXR + norm, padded)
+
+namespace FS {
+constexpr int J = 0;         // current inner index
+constexpr int JDONE = 1;     // columns used by the last update
+constexpr int EST = 2;       // |gamma_{j+1}| (inner relative residual estimate)
+constexpr int HN = 4;        // HN[i]: norm of V_i before normalisation (i >= 1)
+constexpr int HC = 32;       // first-pass projections, NVF complex
+constexpr int CC = 80;       // second-pass projections, NVF complex
+constexpr int H = 128;       // Hessenberg (MAXR+1) x MAXR complex, row-major
+constexpr int CS = H + 2 * (MAXR + 1) * MAXR;
+constexpr int SN = CS + 2 * MAXR;
+constexpr int G = SN + 2 * MAXR;
+constexpr int Y = G + 2 * (MAXR + 1);
+constexpr int SIZE = ((Y + 2 * MAXR) + 63) / 64 * 64;
+}  // namespace FS
+
+// partials of the FGMRES reductions: [block][NVF], counter slot 2
+__device__ __forceinline__ bool publish_fpartials(const LevelDesc& d, int lb, int nb, const double2 (&v)[NVF], int nv,
+                                                  int* flag_sh) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
+        for (int k = 0; k < NVF; ++k)
+            if (k < nv || k == NVF - 1) d.fpart[(long long)lb * NVF + k] = v[k];
+        __threadfence();
+        unsigned prev = atomicAdd(&d.counter[2], 1u);
+        *flag_sh = (prev == (unsigned)(nb - 1));
+    }
+    __syncthreads();
+    return *flag_sh != 0;
+}
+__device__ __forceinline__ void finish_fpartials(const LevelDesc& d, int nb, double2 (&out)[NVF], double2* sh) {
+    __threadfence();
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+#pragma unroll
+    for (int k = 0; k < NVF; ++k) out[k] = make_double2(0.0, 0.0);
+    for (int b = tid; b < nb; b += nt) {
+#pragma unroll
+        for (int k = 0; k < NVF; ++k) out[k] = dadd(out[k], __ldcg(&d.fpart[(long long)b * NVF + k]));
+    }
+    block_sum<double2, NVF>(out, sh);
+    if (tid == 0) d.counter[2] = 0u;
+}
+
+__device__ __forceinline__ double2 sload2d(const double* s, int off) { return make_double2(s[off], s[off + 1]); }
+__device__ __forceinline__ void sstore2d(double* s, int off, double2 v) { s[off] = v.x; s[off + 1] = v.y; }
+
+template <typename TC>
+__device__ __forceinline__ cplx<TC>* kvec(const LevelDesc& d, int i) {
+    return reinterpret_cast<cplx<TC>*>(d.kv) + (long long)i * d.slot_stride;
+}
+// Z_i follows the m+1 V vectors
+template <typename TC>
+__device__ __forceinline__ cplx<TC>* zvec(const LevelDesc& d, int i) {
+    return kvec<TC>(d, d.krestart + 1 + i);
+}
+template <typename TC>
+__device__ __forceinline__ cplx<TC>* xslot(const LevelDesc& d, int s) {
+    return reinterpret_cast<cplx<TC>*>(d.xvec) + (long long)s * d.xstride;
+}
+
+// Start of a restart: V_0 = r/||r|| (r = outer SD, FP64), reset the
+// Hessenberg, gamma = e_1, j = 0.
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_fg_start(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                 int nseg) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const double2* r = slot<double>(d, SD);
+    cplx<TC>* v0 = kvec<TC>(d, 0);
+    const double sc = scalp<double>(d)[S::SCALE];
+    const TC inv = (TC)(sc > 0 ? 1.0 / sc : 0.0);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        const double2 rv = __ldg(r + p);
+        v0[p] = mk<TC>((TC)rv.x * inv, (TC)rv.y * inv);
+    }
+    if (c.lb == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        double* f = d.fs;
+        for (int q = FS::H; q < FS::SIZE; ++q) f[q] = 0.0;
+        f[FS::G] = 1.0;
+        f[FS::J] = 0.0;
+        f[FS::JDONE] = 0.0;
+        f[FS::EST] = 1.0;
+        *d.est = (sc > 0) ? 1.0 : 0.0;
+    }
+}
+
+// Cycle input: level-1 SG = V_j (normalising V_j in place first for j > 0).
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_fg_prep(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                int nseg) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int jj = (int)d.fs[FS::J];
+    cplx<TC>* v = kvec<TC>(d, jj);
+    cplx<TC>* g = xslot<TC>(d, SG);
+    const double hn = jj > 0 ? d.fs[FS::HN + jj] : 1.0;
+    const TC inv = (TC)(hn > 0 ? 1.0 / hn : 0.0);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<TC> x = v[p];
+        if (jj > 0) {
+            x = cscale<TC>(x, inv);
+            v[p] = x;
+        }
+        g[p] = x;
+    }
+}
+
+// Z_j = z (cycle output, level-1 SD); W = V_{j+1} = A z in the cycle
+// precision (5-point Helmholtz with the level-1 k of that precision).
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_fg_matvec(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                  int nseg) {
+    __shared__ LevelDesc d;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int jj = (int)d.fs[FS::J];
+    const cplx<TC>* z = xslot<TC>(d, SD);
+    cplx<TC>* zj = zvec<TC>(d, jj);
+    cplx<TC>* w = kvec<TC>(d, jj + 1);
+    const TC ih2 = LC<TC>::ih2(d);
+    const TC* kf = reinterpret_cast<const TC*>(d.xkf);
+    const TC* sg = reinterpret_cast<const TC*>(d.xsig);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        const cplx<TC> zc = __ldg(z + p);
+        const cplx<TC> s = nbr_sum<TC>(z, d.n, d.pitch, i, j, p);
+        const cplx<TC> dg = helm_diag_h2<TC>(d, i, j, __ldg(kf + p), sg ? __ldg(sg + p) : TC(0));
+        zj[p] = zc;
+        w[p] = cscale<TC>(csub<TC>(cmul<TC>(dg, zc), s), ih2);
+    }
+}
+
+// First Gram-Schmidt pass: projections <V_i, W>, i <= j  -> fs[HC].
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                int nseg) {
+    __shared__ LevelDesc d;
+    __shared__ double2 sh[8 * NVF];
+    __shared__ cplx<TC> shT[8 * NVF];
+    __shared__ int flag;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int jj = (int)d.fs[FS::J];
+    const cplx<TC>* w = kvec<TC>(d, jj + 1);
+    cplx<TC> ac[NVF];
+#pragma unroll
+    for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        const cplx<TC> wv = __ldg(w + p);
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q)
+            if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(__ldg(kvec<TC>(d, q) + p), wv));
+    }
+    block_sum<cplx<TC>, NVF>(ac, shT);
+    double2 acc[NVF];
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+        for (int q = 0; q < NVF; ++q) acc[q] = to_d(ac[q]);
+    }
+    if (publish_fpartials(d, c.lb, c.nb, acc, jj + 1, &flag)) {
+        double2 tot[NVF];
+        finish_fpartials(d, c.nb, tot, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            for (int q = 0; q <= jj; ++q) sstore2d(d.fs, FS::HC + 2 * q, tot[q]);
+    }
+}
+
+// W -= sum_i coef_i V_i (coef = fs[HC] in pass 1, fs[CC] in pass 2).  Pass
+// 1 also forms the second-pass projections <V_i, W'>; both passes form
+// ||W'||^2.  The last block of pass 2 completes column j of the Hessenberg,
+// applies the Givens rotations, stores |gamma_{j+1}| and advances j.
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_fg_orth(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                int nseg, int pass) {
+    __shared__ LevelDesc d;
+    __shared__ double2 sh[8 * NVF];
+    __shared__ cplx<TC> shT[8 * NVF];
+    __shared__ int flag;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int jj = (int)d.fs[FS::J];
+    cplx<TC>* w = kvec<TC>(d, jj + 1);
+    const int off = (pass == 1) ? FS::HC : FS::CC;
+    cplx<TC> coef[MAXR];
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q)
+        coef[q] = q <= jj ? mk<TC>((TC)d.fs[off + 2 * q], (TC)d.fs[off + 2 * q + 1]) : zero2<TC>();
+    cplx<TC> ac[NVF];
+#pragma unroll
+    for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        cplx<TC> vq[MAXR];
+        cplx<TC> wv = w[p];
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q)
+            if (q <= jj) {
+                vq[q] = __ldg(kvec<TC>(d, q) + p);
+                wv = csub<TC>(wv, cmul<TC>(coef[q], vq[q]));
+            }
+        w[p] = wv;
+        if (pass == 1) {
+#pragma unroll
+            for (int q = 0; q < MAXR; ++q)
+                if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(vq[q], wv));
+        }
+        ac[NVF - 1].x += cabs2<TC>(wv);
+    }
+    block_sum<cplx<TC>, NVF>(ac, shT);
+    double2 acc[NVF];
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+        for (int q = 0; q < NVF; ++q) acc[q] = to_d(ac[q]);
+    }
+    if (publish_fpartials(d, c.lb, c.nb, acc, NVF, &flag)) {
+        double2 tot[NVF];
+        finish_fpartials(d, c.nb, tot, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double* f = d.fs;
+            if (pass == 1) {
+                for (int q = 0; q <= jj; ++q) sstore2d(f, FS::CC + 2 * q, tot[q]);
+            } else {
+                const double hnext = sqrt(tot[NVF - 1].x);
+                f[FS::HN + jj + 1] = hnext;
+                // column j: h_ij = first + second pass projections
+                double2 col[MAXR + 1];
+                for (int q = 0; q <= jj; ++q) col[q] = dadd(sload2d(f, FS::HC + 2 * q), sload2d(f, FS::CC + 2 * q));
+                col[jj + 1] = make_double2(hnext, 0);
+                for (int q = 0; q <= jj + 1; ++q) sstore2d(f, FS::H + 2 * (q * MAXR + jj), col[q]);
+                // rotations G_i = [[conj(c) conj(s)], [-s c]]
+                for (int q = 0; q < jj; ++q) {
+                    const double2 cs = sload2d(f, FS::CS + 2 * q), sn = sload2d(f, FS::SN + 2 * q);
+                    const double2 a = col[q], b = col[q + 1];
+                    col[q] = dadd(dmulc(cs, a), dmulc(sn, b));
+                    col[q + 1] = dsub(dmul(cs, b), dmul(sn, a));
+                }
+                const double2 a = col[jj], b = col[jj + 1];
+                const double den = sqrt(dabs2(a) + dabs2(b));
+                double2 cs = make_double2(1, 0), sn = make_double2(0, 0);
+                if (den > 0) {
+                    cs = dsc(a, 1.0 / den);
+                    sn = dsc(b, 1.0 / den);
+                }
+                sstore2d(f, FS::CS + 2 * jj, cs);
+                sstore2d(f, FS::SN + 2 * jj, sn);
+                col[jj] = make_double2(den, 0);
+                // store the rotated (upper triangular) column in the R part
+                for (int q = 0; q <= jj; ++q) sstore2d(f, FS::H + 2 * (q * MAXR + jj), col[q]);
+                const double2 gj = sload2d(f, FS::G + 2 * jj);
+                sstore2d(f, FS::G + 2 * (jj + 1), dsc(dmul(sn, gj), -1.0));
+                sstore2d(f, FS::G + 2 * jj, dmulc(cs, gj));
+                const double est = sqrt(dabs2(sload2d(f, FS::G + 2 * (jj + 1))));
+                f[FS::EST] = est;
+                f[FS::J] = jj + 1;
+                f[FS::JDONE] = jj + 1;
+                *d.est = est;
+            }
+        }
+    }
+}
+
+// y = R^{-1} gamma (one thread per instance), then u += ||r|| sum_i y_i Z_i.
+template <typename TC>
+__global__ void __launch_bounds__(NT) k_fg_update(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                  int nseg) {
+    __shared__ LevelDesc d;
+    __shared__ double2 ysh[MAXR];
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int m = (int)d.fs[FS::JDONE];
+    if (tid == 0) {
+        // every block solves the (tiny) triangular system redundantly
+        const double* f = d.fs;
+        for (int q = m - 1; q >= 0; --q) {
+            double2 acc = sload2d(f, FS::G + 2 * q);
+            for (int r = q + 1; r < m; ++r) acc = dsub(acc, dmul(sload2d(f, FS::H + 2 * (q * MAXR + r)), ysh[r]));
+            const double2 rqq = sload2d(f, FS::H + 2 * (q * MAXR + q));
+            ysh[q] = dabs2(rqq) > 0 ? ddiv(acc, rqq) : make_double2(0, 0);
+        }
+    }
+    __syncthreads();
+    const double sc = scalp<double>(d)[S::SCALE];
+    cplx<TC> yq[MAXR];
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) yq[q] = q < m ? from_d<TC>(ysh[q]) : zero2<TC>();
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    double2* u = slot<double>(d, SU);
+    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
+        if (i >= d.n || j >= d.n) continue;
+        const long long p = (long long)j * d.pitch + i;
+        // e = Z y accumulated in the cycle precision over <= 22 terms,
+        // then added to the FP64 solution
+        cplx<TC> e = zero2<TC>();
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q)
+            if (q < m) e = cfma<TC>(yq[q], __ldg(zvec<TC>(d, q) + p), e);
+        u[p] = dadd(u[p], dsc(to_d(e), sc));
+    }
+}
+
+}  // namespace wadr

@@ -42,6 +42,7 @@ struct InstHost {
     std::vector<LevelHost> lv;      // lv[0] = level 1
     // outer FP64 level-1 vectors (slots SU, SG, SD, SX2)
     void* outer_vec = nullptr;
+    void* kv = nullptr;             // FGMRES Krylov vectors (cycle precision)
     size_t outer_stride = 0;
     int outer_desc = -1;
     long long off = 0;              // offset of this instance in user arrays (elements)
@@ -50,7 +51,18 @@ struct InstHost {
 struct SegTable {
     Seg* d = nullptr;
     int nseg = 0, nblocks = 0;
+    long long pts = 0;     // sum of n^2 over the segments
+    long long mat = 0;     // sum of (n^2)^2 (dense coarsest matrices)
 };
+
+// kernel kinds for the event profiler (names in kernel_kind_name)
+enum KernelKind : int {
+    KK_RESTRICT_JAC0 = 0, KK_RESTRICT_HELM, KK_RESTRICT_GMRES, KK_PROLONG_JAC, KK_PROLONG_ADD, KK_PROLONG_ADR,
+    KK_CHEB, KK_RESDEMOD, KK_GM_A1, KK_GM_A2, KK_GM_A3, KK_GM_B3, KK_GM_UPDATE, KK_COARSE, KK_OUTER_RESIDUAL,
+    KK_OUTER_SCALE, KK_OUTER_UPDATE, KK_JACOBI, KK_FG_START, KK_FG_PREP, KK_FG_MATVEC, KK_FG_DOTS, KK_FG_ORTH,
+    KK_FG_UPDATE, KK_COUNT
+};
+const char* kernel_kind_name(int k);
 
 struct Handle {
     mg_params p{};
@@ -73,6 +85,20 @@ struct Handle {
     cudaGraphExec_t g_irstep = nullptr;     // scale + cycle + update + residual
     cudaStream_t g_stream = nullptr;
     int launches_cycle = 0;                 // kernels of the last emitted cycle
+    int launches_step = 0;                  // kernels of the last emitted outer step
+    // event profiler (mg_profile_steps)
+    int prof = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> prof_kind;
+    std::vector<double> prof_bytes;
+    bool solve_ready = false;               // mg_solve_begin was called
+    // FGMRES
+    int fg_j = 0;                           // inner index of the current restart (host copy)
+    double* fs = nullptr;                   // [ninst][FS::SIZE]
+    double2* fpart = nullptr;               // [ninst][MAXB][NVF]
+    double* est = nullptr;                  // [ninst]
+    cudaGraphExec_t g_fgiter = nullptr;
     // pinned host scratch for scalars
     double* hpin = nullptr;
     std::string last_error;
@@ -95,6 +121,9 @@ struct EngineBase {
     virtual void cycle(Handle& H, bool uzero, cudaStream_t st) = 0;
     virtual void ir_step(Handle& H, cudaStream_t st) = 0;
     virtual void outer_residual(Handle& H, bool gnorm, cudaStream_t st) = 0;
+    virtual void fg_start(Handle& H, cudaStream_t st) = 0;
+    virtual void fg_iter(Handle& H, cudaStream_t st) = 0;
+    virtual void fg_finish(Handle& H, cudaStream_t st) = 0;
     // level operations (single instance) used by the parity tests
     virtual int level_op(Handle& H, int inst, int level, int what, int a0, int a1, cudaStream_t st) = 0;
 };
@@ -120,5 +149,7 @@ int setup_coarse_inverse(const double* k64, const double* phi64, const double* s
     } while (0)
 
 void set_error(const std::string& s);
+void prof_begin(Handle& H, cudaStream_t st);
+void prof_end(Handle& H, cudaStream_t st, int kind, double bytes);
 
 }  // namespace wadr

@@ -65,7 +65,7 @@ __device__ __forceinline__ cplx<T> helm_apply_pt(const LevelDesc& d, const cplx<
     if (HERM) dg.y = -dg.y;
     const cplx<T> s = nbr_sum<T>(u, d.n, d.pitch, i, j, p);
     const cplx<T> c = __ldg(u + p);
-    const T ih2 = (T)d.inv_h2;
+    const T ih2 = LC<T>::ih2(d);
     return cscale<T>(csub<T>(cmul<T>(dg, c), s), ih2);
 }
 
@@ -101,7 +101,7 @@ __device__ __forceinline__ cplx<T> adr_apply_pt(const LevelDesc& d, const cplx<T
     cplx<T> e = i < n - 1 ? __ldg(u + p + 1) : z;
     cplx<T> s = j > 0 ? __ldg(u + p - d.pitch) : z;
     cplx<T> nn = j < n - 1 ? __ldg(u + p + d.pitch) : z;
-    return adr_pt<T>(load_adr<T>(d, p), (T)d.inv_h2, (T)(d.omega / d.h), __ldg(u + p), w, e, s, nn);
+    return adr_pt<T>(load_adr<T>(d, p), LC<T>::ih2(d), LC<T>::wh(d), __ldg(u + p), w, e, s, nn);
 }
 
 // Transposed ADR stencil (L^T y)(i,j): each neighbour contributes with the
@@ -112,7 +112,7 @@ __device__ __forceinline__ cplx<T> adr_apply_t_pt(const LevelDesc& d, const cplx
                                                   int j) {
     const long long p = (long long)j * d.pitch + i;
     const int n = d.n;
-    const T ih2 = (T)d.inv_h2, wh = (T)(d.omega / d.h);
+    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
     quad<T> qc = load_adr<T>(d, p);
     auto ld = [&](long long pq) { cplx<T> v = __ldg(y + pq); if (CONJ) v.y = -v.y; return v; };
     cplx<T> r = cmul<T>(mk<T>(qc.z, qc.w), ld(p));
@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(NT) k_jacobi(const LevelDesc* __restrict__ D, 
     const cplx<T>* u = slot<T>(d, su);
     const cplx<T>* g = slot<T>(d, sg);
     cplx<T>* o = slot<T>(d, sout);
-    const T wj = (T)d.scal[S::OMEGA_J];
+    const T wj = scalp<T>(d)[S::OMEGA_J];
+    const T ih2 = LC<T>::ih2(d), h2 = LC<T>::h(d) * LC<T>::h(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
@@ -193,10 +194,9 @@ __global__ void __launch_bounds__(NT) k_jacobi(const LevelDesc* __restrict__ D, 
         cplx<T> uc = uzero ? zero2<T>() : __ldg(u + p);
         if (!uzero) {
             cplx<T> s = nbr_sum<T>(u, d.n, d.pitch, i, j, p);
-            rr = csub<T>(rr, cscale<T>(csub<T>(cmul<T>(dg, uc), s), (T)d.inv_h2));
+            rr = csub<T>(rr, cscale<T>(csub<T>(cmul<T>(dg, uc), s), ih2));
         }
         // D = dg / h^2  ->  D^{-1} rr = h^2 rr / dg
-        const T h2 = (T)(d.h * d.h);
         const T den = dg.x * dg.x + dg.y * dg.y;
         cplx<T> q = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
         o[p] = cadd<T>(uc, cscale<T>(q, wj * h2));
@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
     const cplx<T>* g = slot<T>(d, SG);
     cplx<T>* dd = slot<T>(d, SD);
     const bool xzero = flags & 1;
-    const T c1 = (T)d.scal[S::CHEB_C1 + m], c2 = (T)d.scal[S::CHEB_C2 + m];
-    const T ih2 = (T)d.inv_h2;
+    const T c1 = scalp<T>(d)[S::CHEB_C1 + m], c2 = scalp<T>(d)[S::CHEB_C2 + m];
+    const T ih2 = LC<T>::ih2(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int x0 = (t % ntx) * CTX, y0 = (t / ntx) * CTY;
         __syncthreads();
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
     __syncthreads();
     const int n = d.n, pitch = d.pitch, nc = dc.n;
     const int ntx = (nc + RCX - 1) / RCX, nty = (nc + RCY - 1) / RCY;
-    const T ih2 = (T)d.inv_h2;
+    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
     cplx<T>* xs = slot<T>(d, sx);
     const cplx<T>* bs = slot<T>(d, sb);
     cplx<T>* out = slot<T>(dc, sc);
@@ -325,11 +325,12 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
     const cplx<T>* w3 = slot<T>(d, SWA);
     cplx<T> cu[3], cr[4];
     if (MODE == MODE_GMRES) {
-        for (int q = 0; q < 3; ++q) cu[q] = from_d<T>(make_double2(d.scal[S::CUPD + 2 * q], d.scal[S::CUPD + 2 * q + 1]));
-        for (int q = 0; q < 4; ++q) cr[q] = from_d<T>(make_double2(d.scal[S::CRES + 2 * q], d.scal[S::CRES + 2 * q + 1]));
+        const T* sc = scalp<T>(d);
+        for (int q = 0; q < 3; ++q) cu[q] = mk<T>(sc[S::CUPD + 2 * q], sc[S::CUPD + 2 * q + 1]);
+        for (int q = 0; q < 4; ++q) cr[q] = mk<T>(sc[S::CRES + 2 * q], sc[S::CRES + 2 * q + 1]);
     }
-    const T wj = (MODE == MODE_JAC0) ? (T)d.scal[S::OMEGA_J] : T(0);
-    const T h2 = (T)(d.h * d.h);
+    const T wj = (MODE == MODE_JAC0) ? scalp<T>(d)[S::OMEGA_J] : T(0);
+    const T h2 = LC<T>::h(d) * LC<T>::h(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int I0 = (t % ntx) * RCX, J0 = (t / ntx) * RCY;
         const int fx0 = 2 * I0, fy0 = 2 * J0;   // footprint origin (fine)
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
                     if (!(uzero && MODE != MODE_JAC0)) {
                         const int b = (r + 1) * RHW + cc + 1;
                         if (MODE == MODE_ADR) {
-                            v = csub<T>(v, adr_pt<T>(load_adr<T>(d, p), ih2, (T)(d.omega / d.h), X[b], X[b - 1],
+                            v = csub<T>(v, adr_pt<T>(load_adr<T>(d, p), ih2, wh, X[b], X[b - 1],
                                                      X[b + 1], X[b - RHW], X[b + RHW]));
                         } else {
                             cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - RHW], X[b + RHW]));
@@ -441,7 +442,8 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
     const cplx<T>* ec = slot<T>(dc, sc);
     const cplx<T>* bs = slot<T>(d, sb);
     cplx<T>* os = slot<T>(d, sout);
-    const T ih2 = (T)d.inv_h2;
+    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
+    const T wjh2 = (MODE == PMODE_JAC) ? scalp<T>(d)[S::OMEGA_J] * LC<T>::h(d) * LC<T>::h(d) : T(0);
     const int halo = (MODE == PMODE_ADD) ? 0 : 1;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int x0 = (t % ntx) * PTX, y0 = (t / ntx) * PTY;
@@ -491,11 +493,10 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
                     cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - PHW], X[b + PHW]));
                     cplx<T> rr = csub<T>(__ldg(bs + p), cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
                     const T den = dg.x * dg.x + dg.y * dg.y;
-                    const T wj = (T)d.scal[S::OMEGA_J] * (T)(d.h * d.h);
                     cplx<T> q = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
-                    os[p] = cadd<T>(X[b], cscale<T>(q, wj));
+                    os[p] = cadd<T>(X[b], cscale<T>(q, wjh2));
                 } else {
-                    cplx<T> Lx = adr_pt<T>(load_adr<T>(d, p), ih2, (T)(d.omega / d.h), X[b], X[b - 1], X[b + 1],
+                    cplx<T> Lx = adr_pt<T>(load_adr<T>(d, p), ih2, wh, X[b], X[b - 1], X[b + 1],
                                            X[b - PHW], X[b + PHW]);
                     os[p] = csub<T>(__ldg(bs + p), Lx);
                     slot<T>(d, sxo)[p] = X[b];
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
 // in the exp(+i w phi) convention); result in slot SAB.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                 int nseg) {
+                                                 int nseg, int /*unused*/) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
@@ -530,51 +531,70 @@ __global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D
 // ----------------------------------------------------------- GMRES(3)
 // GMRES(3) smoother of the ADR V-cycle (Section 3.2.2), Arnoldi with
 // classical Gram-Schmidt and lagged normalisation:
-//   A1: w1 = L r0;                   dots |r0|^2, <r0,w1>, |w1|^2
-//   A2: u2 = w1 - c r0 (on the fly); w2 = L u2; dots |u2|^2, <r0,w2>, <u2,w2>, |w2|^2
-//   A3: u3 = w2 - c0 r0 - c1 u2;    w3 = L u3; dots |u3|^2, <r0,w3>, <u2,w3>, <u3,w3>, |w3|^2
-//   B3: u4 = w3 - c0 r0 - c1 u2 - c2 u3;  dot |u4|^2;  then the 4x3 least squares
-// with v1 = r0/beta, v2 = u2/|u2|, v3 = u3/|u3|, v4 = u4/|u4|.
-__device__ __forceinline__ double2 sload2(const double* s, int off) { return make_double2(s[off], s[off + 1]); }
-__device__ __forceinline__ void sstore2(double* s, int off, double2 v) { s[off] = v.x; s[off + 1] = v.y; }
-__device__ __forceinline__ double sinv(double v) { return v > 0.0 ? 1.0 / v : 0.0; }
+//   A1: w1 = L r0;                          dots |r0|^2, <r0,w1>, |w1|^2
+//   A2: u2 = s2 (w1 - c r0) (on the fly);   w2 = L u2; dots |u2|^2, <r0,w2>, <u2,w2>, |w2|^2
+//   A3: u3 = s3 (w2 - c0 r0 - c1 u2);       w3 = L u3; dots |u3|^2, <r0,w3>, <u2,w3>, <u3,w3>, |w3|^2
+//   B3: u4 = s4 (w3 - c0 r0 - c1 u2 - c2 u3);  dot |u4|^2;  then the 4x3 least squares
+// with v1 = r0/beta, v2 = u2/|u2|, v3 = u3/|u3|, v4 = u4/|u4|.  The scales
+// s_{j+1} = 1/|w_j| (known from the previous reduction) keep every stored
+// vector O(1): without them |w3| grows like ||L||^3 |r0| and its square
+// leaves the FP32 range on fine ADR levels (||L|| ~ 4/h^2).
+//
+// All scalar work (reductions, Hessenberg entries, the small least squares)
+// runs in the working precision T: on this GPU a dependent FP64 operation
+// costs ~14x an FP32 one and an FP64 divide or square root 200-350 ns, which
+// would dominate the small launches of the coarse ADR levels.
+template <typename T> __device__ __forceinline__ cplx<T> sload2(const T* s, int off) { return mk<T>(s[off], s[off + 1]); }
+template <typename T> __device__ __forceinline__ void sstore2(T* s, int off, cplx<T> v) { s[off] = v.x; s[off + 1] = v.y; }
+template <typename T> __device__ __forceinline__ T sinv(T v) { return v > T(0) ? T(1) / v : T(0); }
+template <typename T> __device__ __forceinline__ T cabs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
+template <typename T> __device__ __forceinline__ cplx<T> cdivT(cplx<T> a, cplx<T> b) {
+    const T den = b.x * b.x + b.y * b.y;
+    return mk<T>((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gm_a1(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                               int nseg, int sr0) {
     __shared__ LevelDesc d;
-    __shared__ double2 sh[8 * 3];
+    __shared__ cplx<T> sh[8 * 3];
     __shared__ int flag;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const cplx<T>* r0 = slot<T>(d, sr0);
     cplx<T>* w = slot<T>(d, SWA);
-    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
+    cplx<T> ac[3] = {zero2<T>(), zero2<T>(), zero2<T>()};
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
         const long long p = (long long)j * d.pitch + i;
-        cplx<T> wv = adr_apply_pt<T>(d, r0, i, j);
+        const cplx<T> z = zero2<T>();
+        const cplx<T> a = __ldg(r0 + p);
+        const cplx<T> wv = adr_pt<T>(load_adr<T>(d, p), ih2, wh, a, i > 0 ? __ldg(r0 + p - 1) : z,
+                                     i < d.n - 1 ? __ldg(r0 + p + 1) : z, j > 0 ? __ldg(r0 + p - d.pitch) : z,
+                                     j < d.n - 1 ? __ldg(r0 + p + d.pitch) : z);
         w[p] = wv;
-        double2 a = to_d(__ldg(r0 + p)), b = to_d(wv);
-        acc[0].x += dabs2(a);
-        acc[1] = dadd(acc[1], dmulc(a, b));
-        acc[2].x += dabs2(b);
+        ac[0].x += cabs2<T>(a);
+        ac[1] = cadd<T>(ac[1], cmulc<T>(a, wv));
+        ac[2].x += cabs2<T>(wv);
     }
-    block_sum<3>(acc, sh);
-    if (publish_partials<3>(d, c.lb, c.nb, 0, acc, &flag)) {
-        double2 tot[3];
-        finish_partials<3>(d, c.nb, 0, tot, sh);
+    block_sum<cplx<T>, 3>(ac, sh);
+    if (publish_partials<cplx<T>, 3>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
+        cplx<T> tot[3];
+        finish_partials<cplx<T>, 3>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            double* s = d.scal;
-            const double beta = sqrt(tot[0].x);
-            const double ib2 = sinv(tot[0].x);
+            T* s = scalp<T>(d);
+            const T beta = sqrt(tot[0].x);
+            const T ib2 = sinv<T>(tot[0].x);
             s[S::BETA] = beta;
-            const double2 h11 = dsc(tot[1], ib2);
-            for (int q = 0; q < 24; ++q) s[S::H + q] = 0.0;
-            sstore2(s, S::H + 0, h11);
-            s[S::WN1] = sqrt(tot[2].x) * sinv(beta);
-            sstore2(s, S::CA2, h11);
+            const cplx<T> h11 = cscale<T>(tot[1], ib2);
+            for (int q = 0; q < 24; ++q) s[S::H + q] = T(0);
+            sstore2<T>(s, S::H + 0, h11);
+            const T nw1 = sqrt(tot[2].x);
+            s[S::WN1] = nw1 * sinv<T>(beta);
+            sstore2<T>(s, S::CA2, h11);
+            s[S::SC2] = sinv<T>(nw1);   // 1/|w1|
         }
     }
 }
@@ -585,7 +605,7 @@ __global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, 
                                                int nseg, int sr0) {
     constexpr int NV = STEP == 2 ? 4 : 5;
     __shared__ LevelDesc d;
-    __shared__ double2 sh[8 * 5];
+    __shared__ cplx<T> sh[8 * 5];
     __shared__ int flag;
     __shared__ cplx<T> Ur[(BY + 2) * (BX + 2)];
     SegCtx c = seg_begin(D, Sg, nseg, d);
@@ -597,17 +617,19 @@ __global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, 
     const cplx<T>* u2 = slot<T>(d, SU2);
     cplx<T>* uout = slot<T>(d, STEP == 2 ? SU2 : SU3);
     cplx<T>* wout = slot<T>(d, STEP == 2 ? SWB : SWA);
+    const T* sc = scalp<T>(d);
     cplx<T> ca, cb = zero2<T>();
     if (STEP == 2) {
-        ca = from_d<T>(sload2(d.scal, S::CA2));
+        ca = sload2<T>(sc, S::CA2);
     } else {
-        ca = from_d<T>(sload2(d.scal, S::CA3));
-        cb = from_d<T>(sload2(d.scal, S::CA3 + 2));
+        ca = sload2<T>(sc, S::CA3);
+        cb = sload2<T>(sc, S::CA3 + 2);
     }
-    const T ih2 = (T)d.inv_h2, wh = (T)(d.omega / d.h);
-    double2 acc[NV];
+    const T scl = sc[STEP == 2 ? S::SC2 : S::SC3];
+    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
+    cplx<T> ac[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = make_double2(0, 0);
+    for (int k = 0; k < NV; ++k) ac[k] = zero2<T>();
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
         __syncthreads();
@@ -619,6 +641,7 @@ __global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, 
                 const long long p = (long long)gj * pitch + gi;
                 v = csub<T>(__ldg(win + p), cmul<T>(ca, __ldg(r0 + p)));
                 if (STEP == 3) v = csub<T>(v, cmul<T>(cb, __ldg(u2 + p)));
+                v = cscale<T>(v, scl);
             }
             Ur[e] = v;
         }
@@ -632,55 +655,59 @@ __global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, 
                                    Ur[b + (BX + 2)]);
             uout[p] = uc;
             wout[p] = wv;
-            double2 U = to_d(uc), W = to_d(wv), R0 = to_d(__ldg(r0 + p));
-            acc[0].x += dabs2(U);
-            acc[1] = dadd(acc[1], dmulc(R0, W));
+            const cplx<T> R0 = __ldg(r0 + p);
+            ac[0].x += cabs2<T>(uc);
+            ac[1] = cadd<T>(ac[1], cmulc<T>(R0, wv));
             if (STEP == 2) {
-                acc[2] = dadd(acc[2], dmulc(U, W));
-                acc[3].x += dabs2(W);
+                ac[2] = cadd<T>(ac[2], cmulc<T>(uc, wv));
+                ac[3].x += cabs2<T>(wv);
             } else {
-                acc[2] = dadd(acc[2], dmulc(to_d(__ldg(u2 + p)), W));
-                acc[3] = dadd(acc[3], dmulc(U, W));
-                acc[4].x += dabs2(W);
+                ac[2] = cadd<T>(ac[2], cmulc<T>(__ldg(u2 + p), wv));
+                ac[3] = cadd<T>(ac[3], cmulc<T>(uc, wv));
+                ac[4].x += cabs2<T>(wv);
             }
         }
     }
-    block_sum<NV>(acc, sh);
-    if (publish_partials<NV>(d, c.lb, c.nb, 0, acc, &flag)) {
-        double2 tot[NV];
-        finish_partials<NV>(d, c.nb, 0, tot, sh);
+    block_sum<cplx<T>, NV>(ac, sh);
+    if (publish_partials<cplx<T>, NV>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
+        cplx<T> tot[NV];
+        finish_partials<cplx<T>, NV>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
         if (tid == 0) {
-            double* s = d.scal;
-            const double beta = s[S::BETA];
+            T* s = scalp<T>(d);
+            const T beta = s[S::BETA];
             if (STEP == 2) {
-                const double nu2 = sqrt(tot[0].x);
+                const T nu2 = sqrt(tot[0].x);
                 s[S::NU2] = nu2;
-                const double in2 = sinv(nu2);
-                // h21 = nu2/beta, h12 = <r0,w2>/(beta nu2), h22 = <u2,w2>/nu2^2
-                sstore2(s, S::H + 2 * (1 * 3 + 0), make_double2(nu2 * sinv(beta), 0));
-                const double2 h12 = dsc(tot[1], sinv(beta) * in2);
-                const double2 h22 = dsc(tot[2], in2 * in2);
-                sstore2(s, S::H + 2 * (0 * 3 + 1), h12);
-                sstore2(s, S::H + 2 * (1 * 3 + 1), h22);
-                s[S::WN2] = sqrt(tot[3].x) * in2;
-                sstore2(s, S::CA3, dsc(h12, nu2 * sinv(beta)));
-                sstore2(s, S::CA3 + 2, h22);
+                const T in2 = sinv<T>(nu2);
+                // h21 = nu2/(s2 beta), h12 = <r0,w2>/(beta nu2), h22 = <u2,w2>/nu2^2
+                sstore2<T>(s, S::H + 2 * (1 * 3 + 0), mk<T>(nu2 * sinv<T>(s[S::SC2] * beta), T(0)));
+                const cplx<T> h12 = cscale<T>(tot[1], sinv<T>(beta) * in2);
+                const cplx<T> h22 = cscale<T>(tot[2], in2 * in2);
+                sstore2<T>(s, S::H + 2 * (0 * 3 + 1), h12);
+                sstore2<T>(s, S::H + 2 * (1 * 3 + 1), h22);
+                const T nw2 = sqrt(tot[3].x);
+                s[S::WN2] = nw2 * in2;
+                sstore2<T>(s, S::CA3, cscale<T>(h12, nu2 * sinv<T>(beta)));
+                sstore2<T>(s, S::CA3 + 2, h22);
+                s[S::SC3] = sinv<T>(nw2);   // 1/|w2|
             } else {
-                const double nu2 = s[S::NU2];
-                const double nu3 = sqrt(tot[0].x);
+                const T nu2 = s[S::NU2];
+                const T nu3 = sqrt(tot[0].x);
                 s[S::NU3] = nu3;
-                const double in3 = sinv(nu3);
-                sstore2(s, S::H + 2 * (2 * 3 + 1), make_double2(nu3 * sinv(nu2), 0));
-                const double2 h13 = dsc(tot[1], sinv(beta) * in3);
-                const double2 h23 = dsc(tot[2], sinv(nu2) * in3);
-                const double2 h33 = dsc(tot[3], in3 * in3);
-                sstore2(s, S::H + 2 * (0 * 3 + 2), h13);
-                sstore2(s, S::H + 2 * (1 * 3 + 2), h23);
-                sstore2(s, S::H + 2 * (2 * 3 + 2), h33);
-                s[S::WN3] = sqrt(tot[4].x) * in3;
-                sstore2(s, S::CB3 + 0, dsc(h13, nu3 * sinv(beta)));
-                sstore2(s, S::CB3 + 2, dsc(h23, nu3 * sinv(nu2)));
-                sstore2(s, S::CB3 + 4, h33);
+                const T in3 = sinv<T>(nu3);
+                sstore2<T>(s, S::H + 2 * (2 * 3 + 1), mk<T>(nu3 * sinv<T>(s[S::SC3] * nu2), T(0)));
+                const cplx<T> h13 = cscale<T>(tot[1], sinv<T>(beta) * in3);
+                const cplx<T> h23 = cscale<T>(tot[2], sinv<T>(nu2) * in3);
+                const cplx<T> h33 = cscale<T>(tot[3], in3 * in3);
+                sstore2<T>(s, S::H + 2 * (0 * 3 + 2), h13);
+                sstore2<T>(s, S::H + 2 * (1 * 3 + 2), h23);
+                sstore2<T>(s, S::H + 2 * (2 * 3 + 2), h33);
+                const T nw3 = sqrt(tot[4].x);
+                s[S::WN3] = nw3 * in3;
+                s[S::SC4] = sinv<T>(nw3);   // 1/|w3|
+                sstore2<T>(s, S::CB3 + 0, cscale<T>(h13, nu3 * sinv<T>(beta)));
+                sstore2<T>(s, S::CB3 + 2, cscale<T>(h23, nu3 * sinv<T>(nu2)));
+                sstore2<T>(s, S::CB3 + 4, h33);
             }
         }
     }
@@ -689,47 +716,48 @@ __global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, 
 // Small dense least squares min || beta e1 - H y ||, H (m+1) x m upper
 // Hessenberg (row-major 4 x 3), by complex Givens rotations; also returns the
 // residual coefficients c = beta e1 - H y.
-__device__ inline void hess_lsq(const double* Hm, double beta, int m, double2* y, double2* cres) {
-    double2 R[4][3], g[4];
+template <typename T>
+__device__ inline void hess_lsq(const T* Hm, T beta, int m, cplx<T>* y, cplx<T>* cres) {
+    cplx<T> R[4][3], g[4];
     for (int r = 0; r < 4; ++r)
-        for (int q = 0; q < 3; ++q) R[r][q] = make_double2(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]);
-    for (int r = 0; r < 4; ++r) g[r] = make_double2(0, 0);
+        for (int q = 0; q < 3; ++q) R[r][q] = mk<T>(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]);
+    for (int r = 0; r < 4; ++r) g[r] = zero2<T>();
     g[0].x = beta;
-    double2 cs[3], sn[3];
+    cplx<T> cs[3], sn[3];
     for (int j = 0; j < m; ++j) {
         for (int i = 0; i < j; ++i) {
-            double2 a = R[i][j], b = R[i + 1][j];
-            double2 t = dadd(dmulc(cs[i], a), dmulc(sn[i], b));
-            R[i + 1][j] = dsub(dmul(cs[i], b), dmul(sn[i], a));
+            cplx<T> a = R[i][j], b = R[i + 1][j];
+            cplx<T> t = cadd<T>(cmulc<T>(cs[i], a), cmulc<T>(sn[i], b));
+            R[i + 1][j] = csub<T>(cmul<T>(cs[i], b), cmul<T>(sn[i], a));
             R[i][j] = t;
         }
-        double2 a = R[j][j], b = R[j + 1][j];
-        double den = sqrt(dabs2(a) + dabs2(b));
-        if (den > 0) {
-            cs[j] = dsc(a, 1.0 / den);
-            sn[j] = dsc(b, 1.0 / den);
+        cplx<T> a = R[j][j], b = R[j + 1][j];
+        T den = sqrt(cabs2<T>(a) + cabs2<T>(b));
+        if (den > T(0)) {
+            const T id = T(1) / den;
+            cs[j] = cscale<T>(a, id);
+            sn[j] = cscale<T>(b, id);
         } else {
-            cs[j] = make_double2(1, 0);
-            sn[j] = make_double2(0, 0);
+            cs[j] = mk<T>(T(1), T(0));
+            sn[j] = zero2<T>();
         }
-        R[j][j] = make_double2(den, 0);
-        R[j + 1][j] = make_double2(0, 0);
-        double2 gj = g[j];
-        g[j + 1] = dsc(dmul(sn[j], gj), -1.0);
-        g[j] = dmulc(cs[j], gj);
+        R[j][j] = mk<T>(den, T(0));
+        R[j + 1][j] = zero2<T>();
+        cplx<T> gj = g[j];
+        g[j + 1] = cscale<T>(cmul<T>(sn[j], gj), T(-1));
+        g[j] = cmulc<T>(cs[j], gj);
     }
-    for (int q = 0; q < 3; ++q) y[q] = make_double2(0, 0);
+    for (int q = 0; q < 3; ++q) y[q] = zero2<T>();
     for (int j = m - 1; j >= 0; --j) {
-        double2 acc = g[j];
-        for (int q = j + 1; q < m; ++q) acc = dsub(acc, dmul(R[j][q], y[q]));
-        y[j] = (dabs2(R[j][j]) > 0) ? ddiv(acc, R[j][j]) : make_double2(0, 0);
+        cplx<T> acc = g[j];
+        for (int q = j + 1; q < m; ++q) acc = csub<T>(acc, cmul<T>(R[j][q], y[q]));
+        y[j] = (cabs2<T>(R[j][j]) > T(0)) ? cdivT<T>(acc, R[j][j]) : zero2<T>();
     }
     // c = beta e1 - H y with the original H
     for (int r = 0; r < 4; ++r) {
-        double2 acc = make_double2(r == 0 ? beta : 0.0, 0);
-        for (int q = 0; q < m; ++q)
-            acc = dsub(acc, dmul(make_double2(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]), y[q]));
-        cres[r] = (r <= m) ? acc : make_double2(0, 0);
+        cplx<T> acc = mk<T>(r == 0 ? beta : T(0), T(0));
+        for (int q = 0; q < m; ++q) acc = csub<T>(acc, cmul<T>(mk<T>(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]), y[q]));
+        cres[r] = (r <= m) ? acc : zero2<T>();
     }
 }
 
@@ -737,7 +765,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_gm_b3(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                               int nseg, int sr0) {
     __shared__ LevelDesc d;
-    __shared__ double2 sh[8];
+    __shared__ cplx<T> sh[8];
     __shared__ int flag;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
@@ -745,9 +773,10 @@ __global__ void __launch_bounds__(NT) k_gm_b3(const LevelDesc* __restrict__ D, c
     const cplx<T>* u2 = slot<T>(d, SU2);
     const cplx<T>* u3 = slot<T>(d, SU3);
     const cplx<T>* w3 = slot<T>(d, SWA);
-    const cplx<T> c0 = from_d<T>(sload2(d.scal, S::CB3)), c1 = from_d<T>(sload2(d.scal, S::CB3 + 2)),
-                  c2 = from_d<T>(sload2(d.scal, S::CB3 + 4));
-    double2 acc[1] = {{0, 0}};
+    const T* sc = scalp<T>(d);
+    const cplx<T> c0 = sload2<T>(sc, S::CB3), c1 = sload2<T>(sc, S::CB3 + 2), c2 = sload2<T>(sc, S::CB3 + 4);
+    const T s4 = sc[S::SC4];
+    cplx<T> ac[1] = {zero2<T>()};
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
@@ -756,40 +785,41 @@ __global__ void __launch_bounds__(NT) k_gm_b3(const LevelDesc* __restrict__ D, c
         v = csub<T>(v, cmul<T>(c0, __ldg(r0 + p)));
         v = csub<T>(v, cmul<T>(c1, __ldg(u2 + p)));
         v = csub<T>(v, cmul<T>(c2, __ldg(u3 + p)));
-        acc[0].x += dabs2(to_d(v));
+        v = cscale<T>(v, s4);
+        ac[0].x += cabs2<T>(v);
     }
-    block_sum<1>(acc, sh);
-    if (publish_partials<1>(d, c.lb, c.nb, 0, acc, &flag)) {
-        double2 tot[1];
-        finish_partials<1>(d, c.nb, 0, tot, sh);
+    block_sum<cplx<T>, 1>(ac, sh);
+    if (publish_partials<cplx<T>, 1>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
+        cplx<T> tot[1];
+        finish_partials<cplx<T>, 1>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            double* s = d.scal;
-            const double beta = s[S::BETA], nu2 = s[S::NU2], nu3 = s[S::NU3];
-            const double nu4 = sqrt(tot[0].x);
+            T* s = scalp<T>(d);
+            const T beta = s[S::BETA], nu2 = s[S::NU2], nu3 = s[S::NU3];
+            const T nu4 = sqrt(tot[0].x);
             s[S::NU4] = nu4;
-            sstore2(s, S::H + 2 * (3 * 3 + 2), make_double2(nu4 * sinv(nu3), 0));
+            sstore2<T>(s, S::H + 2 * (3 * 3 + 2), mk<T>(nu4 * sinv<T>(s[S::SC4] * nu3), T(0)));
             // Krylov dimension: stop at an (almost) invariant subspace
-            const double eps = 1e-12;
+            const T eps = T(1e-12);
             int m = 3;
-            if (!(beta > 0)) m = 0;
+            if (!(beta > T(0))) m = 0;
             else if (!(s[S::H + 2 * (1 * 3 + 0)] > eps * s[S::WN1])) m = 1;
             else if (!(s[S::H + 2 * (2 * 3 + 1)] > eps * s[S::WN2])) m = 2;
-            s[S::M] = m;
-            double2 y[3], cr[4];
-            hess_lsq(s + S::H, beta, m, y, cr);
-            for (int q = 0; q < 3; ++q) sstore2(s, S::Y + 2 * q, y[q]);
-            const double inv[3] = {sinv(beta), sinv(nu2), sinv(nu3)};
-            for (int q = 0; q < 3; ++q) sstore2(s, S::CUPD + 2 * q, dsc(y[q], inv[q]));
-            // r = sum_i c_i v_i; v4 = (w3 - CB3.(r0,u2,u3))/nu4
-            const double2 cb[3] = {sload2(s, S::CB3), sload2(s, S::CB3 + 2), sload2(s, S::CB3 + 4)};
-            const double i4 = sinv(nu4);
-            const double2 c4 = (m == 3) ? dsc(cr[3], i4) : make_double2(0, 0);
+            s[S::M] = (T)m;
+            cplx<T> y[3], cr[4];
+            hess_lsq<T>(s + S::H, beta, m, y, cr);
+            for (int q = 0; q < 3; ++q) sstore2<T>(s, S::Y + 2 * q, y[q]);
+            const T inv[3] = {sinv<T>(beta), sinv<T>(nu2), sinv<T>(nu3)};
+            for (int q = 0; q < 3; ++q) sstore2<T>(s, S::CUPD + 2 * q, cscale<T>(y[q], inv[q]));
+            // r = sum_i c_i v_i; v4 = s4 (w3 - CB3.(r0,u2,u3))/nu4
+            const cplx<T> cb[3] = {sload2<T>(s, S::CB3), sload2<T>(s, S::CB3 + 2), sload2<T>(s, S::CB3 + 4)};
+            const T i4 = sinv<T>(nu4) * s[S::SC4];
+            const cplx<T> c4 = (m == 3) ? cscale<T>(cr[3], i4) : zero2<T>();
             for (int q = 0; q < 3; ++q) {
-                double2 v = (q <= m) ? dsc(cr[q], inv[q]) : make_double2(0, 0);
-                v = dsub(v, dmul(c4, cb[q]));
-                sstore2(s, S::CRES + 2 * q, v);
+                cplx<T> v = (q <= m) ? cscale<T>(cr[q], inv[q]) : zero2<T>();
+                v = csub<T>(v, cmul<T>(c4, cb[q]));
+                sstore2<T>(s, S::CRES + 2 * q, v);
             }
-            sstore2(s, S::CRES + 6, c4);
+            sstore2<T>(s, S::CRES + 6, c4);
         }
     }
 }
@@ -810,8 +840,8 @@ __global__ void __launch_bounds__(NT) k_gm_update(const LevelDesc* __restrict__ 
     cplx<T>* xout = slot<T>(d, SAX);
     cplx<T>* u = slot<T>(d, SU);
     const cplx<T>* mod = reinterpret_cast<const cplx<T>*>(d.mod);
-    const cplx<T> c0 = from_d<T>(sload2(d.scal, S::CUPD)), c1 = from_d<T>(sload2(d.scal, S::CUPD + 2)),
-                  c2 = from_d<T>(sload2(d.scal, S::CUPD + 4));
+    const T* sc = scalp<T>(d);
+    const cplx<T> c0 = sload2<T>(sc, S::CUPD), c1 = sload2<T>(sc, S::CUPD + 2), c2 = sload2<T>(sc, S::CUPD + 4);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
@@ -884,6 +914,7 @@ __global__ void __launch_bounds__(NT) k_outer_residual(const LevelDesc* __restri
     const double2* g = slot<double>(d, SG);
     double2* r = slot<double>(d, SD);
     double2 acc[2] = {{0, 0}, {0, 0}};
+    double* sc = scalp<double>(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
@@ -894,15 +925,15 @@ __global__ void __launch_bounds__(NT) k_outer_residual(const LevelDesc* __restri
         acc[0].x += dabs2(v);
         if (with_gnorm) acc[1].x += dabs2(gv);
     }
-    block_sum<2>(acc, sh);
-    if (publish_partials<2>(d, c.lb, c.nb, 0, acc, &flag)) {
+    block_sum<double2, 2>(acc, sh);
+    if (publish_partials<double2, 2>(partp<double>(d), MAXDOT, d.counter, c.lb, c.nb, acc, &flag)) {
         double2 tot[2];
-        finish_partials<2>(d, c.nb, 0, tot, sh);
+        finish_partials<double2, 2>(partp<double>(d), MAXDOT, d.counter, c.nb, tot, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            d.scal[S::NORM] = tot[0].x;
-            if (with_gnorm) d.scal[S::NORM + 1] = tot[1].x;
+            sc[S::NORM] = tot[0].x;
+            if (with_gnorm) sc[S::NORM + 1] = tot[1].x;
             const double nr = sqrt(tot[0].x);
-            d.scal[S::SCALE] = nr;   // IR: e = ||r|| cycle(0, r/||r||)
+            sc[S::SCALE] = nr;   // IR: e = ||r|| cycle(0, r/||r||)
         }
     }
 }
@@ -916,13 +947,14 @@ __global__ void __launch_bounds__(NT) k_outer_scale(const LevelDesc* __restrict_
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const double2* r = slot<double>(d, src_slot);
     cplx<TC>* out = reinterpret_cast<cplx<TC>*>(d.xvec) + (long long)SG * d.xstride;
-    const double sc = d.scal[S::SCALE];
-    const double inv = sc > 0 ? 1.0 / sc : 0.0;
+    const double sc = scalp<double>(d)[S::SCALE];
+    const TC inv = (TC)(sc > 0 ? 1.0 / sc : 0.0);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
         const long long p = (long long)j * d.pitch + i;
-        out[p] = from_d<TC>(dsc(__ldg(r + p), inv));
+        const double2 rv = __ldg(r + p);
+        out[p] = mk<TC>((TC)rv.x * inv, (TC)rv.y * inv);
     }
 }
 
@@ -935,7 +967,7 @@ __global__ void __launch_bounds__(NT) k_outer_update(const LevelDesc* __restrict
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     double2* u = slot<double>(d, SU);
     const cplx<TC>* e = reinterpret_cast<const cplx<TC>*>(d.xvec) + (long long)SD * d.xstride;
-    const double sc = d.scal[S::SCALE];
+    const double sc = scalp<double>(d)[S::SCALE];
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;

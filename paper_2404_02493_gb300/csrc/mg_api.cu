@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "fgmres.cuh"
 #include "kernels.cuh"
 
 struct mg_handle {
@@ -19,6 +20,31 @@ namespace wadr {
 
 static thread_local std::string g_err = "";
 void set_error(const std::string& s) { g_err = s; }
+
+const char* kernel_kind_name(int k) {
+    static const char* names[KK_COUNT] = {
+        "restrict_jacobi0", "restrict_helmholtz", "restrict_gmres_update", "prolong_jacobi", "prolong_add",
+        "prolong_adr_residual", "chebyshev_step", "residual_demodulate", "gmres_a1", "gmres_a2", "gmres_a3",
+        "gmres_b3_lsq", "gmres_update", "coarse_lu_apply", "outer_residual_fp64", "outer_scale",
+        "outer_update_fp64", "jacobi", "fgmres_start", "fgmres_prep", "fgmres_matvec", "fgmres_dots",
+        "fgmres_orth", "fgmres_update"};
+    return (k >= 0 && k < KK_COUNT) ? names[k] : "unknown";
+}
+
+static cudaEvent_t next_event(Handle& H) {
+    if (H.ev_used == H.ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        H.ev_pool.push_back(e);
+    }
+    return H.ev_pool[H.ev_used++];
+}
+void prof_begin(Handle& H, cudaStream_t st) { cudaEventRecord(next_event(H), st); }
+void prof_end(Handle& H, cudaStream_t st, int kind, double bytes) {
+    cudaEventRecord(next_event(H), st);
+    H.prof_kind.push_back(kind);
+    H.prof_bytes.push_back(bytes);
+}
 
 void* Handle::alloc(size_t bytes) {
     void* p = nullptr;
@@ -53,6 +79,10 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
     SegTable t;
     t.nseg = (int)h.size();
     t.nblocks = blk;
+    for (int i : ids) {
+        const LevelDesc& d = outer ? houter[i] : hdesc[i];
+        t.pts += (long long)d.n * d.n;
+    }
     t.d = (Seg*)alloc(sizeof(Seg) * h.size());
     cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
     return segs[key] = t;
@@ -78,6 +108,11 @@ const SegTable& Handle::seg_rows(const std::vector<int>& ids, int rows_per_block
     SegTable t;
     t.nseg = (int)h.size();
     t.nblocks = blk;
+    for (int i : ids) {
+        const long long N = (long long)hdesc[i].n * hdesc[i].n;
+        t.pts += N;
+        t.mat += N * N;
+    }
     t.d = (Seg*)alloc(sizeof(Seg) * h.size());
     cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
     return segs[key] = t;
@@ -199,6 +234,12 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         I.outer_vec = H.alloc(npt1 * 4 * 16);
         if (!I.outer_vec) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
         cudaMemsetAsync(I.outer_vec, 0, npt1 * 4 * 16, st);
+        if (p.outer == MG_OUTER_FGMRES) {
+            const size_t nk = (size_t)(2 * p.restart + 1) * npt1 * esz(prec);
+            I.kv = H.alloc(nk);
+            if (!I.kv) { set_error("mg_setup: out of device memory (Krylov vectors)"); return MG_ENOMEM; }
+            cudaMemsetAsync(I.kv, 0, nk, st);
+        }
     }
     H.total_elems = off;
     // --- FP64 fields by injection
@@ -238,7 +279,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.mod = lv.mod;
             d.inv_helm = lv.inv_helm;
             d.inv_adr = lv.inv_adr;
-            d.scal = H.scal + (size_t)S::SIZE * di;
+            d.scal = H.scal + (size_t)S::SIZE * di;   // holds T values
             d.part = H.part + (size_t)MAXB * MAXDOT * di;
             d.counter = H.counter + (size_t)NCOUNTERS * di;
             d.n = lv.n;
@@ -247,6 +288,12 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.inv_h2 = 1.0 / (lv.h * lv.h);
             d.omega = I.omega;
             d.shift = H.p.shift;
+            d.wh = I.omega / lv.h;
+            d.fh = (float)d.h;
+            d.fih2 = (float)d.inv_h2;
+            d.fwh = (float)d.wh;
+            d.fshift = (float)d.shift;
+            d.has_shift = d.shift != 0.0;
             d.bc = I.bc;
             d.inst = b;
             d.level = l;
@@ -294,6 +341,13 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         }
     }
     // outer descriptors (FP64, level-1 geometry)
+    if (p.outer == MG_OUTER_FGMRES) {
+        H.fs = (double*)H.alloc(sizeof(double) * FS::SIZE * ninst);
+        H.fpart = (double2*)H.alloc(sizeof(double2) * (size_t)MAXB * NVF * ninst);
+        H.est = (double*)H.alloc(sizeof(double) * ninst);
+        if (!H.fs || !H.fpart || !H.est) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
+        cudaMemsetAsync(H.fs, 0, sizeof(double) * FS::SIZE * ninst, st);
+    }
     for (int b = 0; b < ninst; ++b) {
         InstHost& I = H.inst[b];
         LevelHost& l1 = I.lv[0];
@@ -310,6 +364,15 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         d.coarse = -1;
         d.xvec = l1.vec;
         d.xstride = (long long)l1.slot_stride;
+        d.xkf = l1.kf;
+        d.xsig = l1.sig;
+        d.krestart = p.restart;
+        if (p.outer == MG_OUTER_FGMRES) {
+            d.kv = I.kv;
+            d.fs = H.fs + (size_t)FS::SIZE * b;
+            d.fpart = H.fpart + (size_t)MAXB * NVF * b;
+            d.est = H.est + b;
+        }
         I.outer_desc = b;
         H.houter.push_back(d);
     }
@@ -317,7 +380,17 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
     H.douter = (LevelDesc*)H.alloc(sizeof(LevelDesc) * H.houter.size());
     cudaMemcpy(H.ddesc, H.hdesc.data(), sizeof(LevelDesc) * H.hdesc.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(H.douter, H.houter.data(), sizeof(LevelDesc) * H.houter.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(H.scal, hs.data(), sizeof(double) * hs.size(), cudaMemcpyHostToDevice);
+    if (prec == MG_PREC_MIXED) {
+        // the cycle descriptors hold FP32 scalars (first half of each block)
+        std::vector<float> hf((size_t)S::SIZE * 2 * nd, 0.0f);
+        for (int q = 0; q < nd; ++q)
+            for (int k = 0; k < S::SIZE; ++k) hf[(size_t)q * 2 * S::SIZE + k] = (float)hs[(size_t)q * S::SIZE + k];
+        cudaMemcpy(H.scal, hf.data(), sizeof(double) * S::SIZE * nd, cudaMemcpyHostToDevice);
+        cudaMemcpy(H.scal + (size_t)S::SIZE * nd, hs.data() + (size_t)S::SIZE * nd, sizeof(double) * S::SIZE * ninst,
+                   cudaMemcpyHostToDevice);
+    } else {
+        cudaMemcpy(H.scal, hs.data(), sizeof(double) * hs.size(), cudaMemcpyHostToDevice);
+    }
     if (cudaMallocHost(&H.hpin, sizeof(double) * S::SIZE * nslots) != cudaSuccess) H.hpin = nullptr;
     if (cudaStreamCreateWithFlags(&H.g_stream, cudaStreamNonBlocking) != cudaSuccess) return MG_ECUDA;
     cudaError_t e = cudaStreamSynchronize(st);
@@ -326,9 +399,31 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
     return MG_OK;
 }
 
+// Capture `emit` into a graph on the handle's stream (after one plain run
+// on the zeroed workspace that builds every segment table).
+template <class F>
+static int capture(Handle& H, cudaGraphExec_t* out, F emit) {
+    emit(H.g_stream);
+    cudaError_t e = cudaStreamSynchronize(H.g_stream);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    cudaGraph_t g;
+    e = cudaStreamBeginCapture(H.g_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    emit(H.g_stream);
+    e = cudaStreamEndCapture(H.g_stream, &g);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+    return MG_OK;
+}
+
 static void free_all(Handle& H) {
+    for (cudaEvent_t e : H.ev_pool) cudaEventDestroy(e);
+    H.ev_pool.clear();
     if (H.g_cycle0) cudaGraphExecDestroy(H.g_cycle0);
     if (H.g_irstep) cudaGraphExecDestroy(H.g_irstep);
+    if (H.g_fgiter) cudaGraphExecDestroy(H.g_fgiter);
     if (H.g_stream) cudaStreamDestroy(H.g_stream);
     for (void* p : H.allocs) cudaFree(p);
     if (H.hpin) cudaFreeHost(H.hpin);
@@ -348,23 +443,58 @@ static void* slot_ptr(const Handle& H, const LevelHost& lv, int s) {
     return (char*)lv.vec + (size_t)s * lv.slot_stride * esz(H.prec);
 }
 
-// Capture `emit` into a graph on the handle's stream (after one plain run
-// that builds every segment table).
-template <class F>
-static int capture(Handle& H, cudaGraphExec_t* out, F emit) {
-    emit(H.g_stream);
-    cudaError_t e = cudaStreamSynchronize(H.g_stream);
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
-    cudaGraph_t g;
-    e = cudaStreamBeginCapture(H.g_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
-    emit(H.g_stream);
-    e = cudaStreamEndCapture(H.g_stream, &g);
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
-    e = cudaGraphInstantiate(out, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+static int ensure_graph(mg_handle* h) {
+    Handle& H = h->H;
+    if (!H.p.use_graph) return MG_OK;
+    if (H.p.outer == MG_OUTER_FGMRES) {
+        if (H.g_fgiter) return MG_OK;
+        // plain run of start / iteration / finish on the zeroed workspace
+        h->eng->fg_start(H, H.g_stream);
+        int rc = capture(H, &H.g_fgiter, [&](cudaStream_t s) { h->eng->fg_iter(H, s); });
+        h->eng->fg_finish(H, H.g_stream);
+        cudaError_t e = cudaStreamSynchronize(H.g_stream);
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MG_ECUDA; }
+        return rc;
+    }
+    if (H.g_irstep) return MG_OK;
+    return capture(H, &H.g_irstep, [&](cudaStream_t s) { h->eng->ir_step(H, s); });
+}
+
+// one inner FGMRES iteration (graph replay or plain emission)
+static int fg_iter_launch(mg_handle* h, cudaStream_t st) {
+    Handle& H = h->H;
+    if (H.p.use_graph) {
+        WADR_CHECK(cudaGraphLaunch(H.g_fgiter, st));
+        H.fg_j++;
+    } else {
+        h->eng->fg_iter(H, st);
+    }
     return MG_OK;
+}
+
+// per-instance ||r||, ||g|| of the outer loop -> host (synchronises st)
+static int read_outer_norms(Handle& H, cudaStream_t st, std::vector<double>& rn, std::vector<double>* gn) {
+    const int ni = (int)H.inst.size();
+    const double* outer_scal = H.scal + (size_t)S::SIZE * H.hdesc.size();
+    WADR_CHECK(cudaMemcpyAsync(H.hpin, outer_scal, sizeof(double) * S::SIZE * ni, cudaMemcpyDeviceToHost, st));
+    WADR_CHECK(cudaStreamSynchronize(st));
+    rn.resize(ni);
+    if (gn) gn->resize(ni);
+    for (int b = 0; b < ni; ++b) {
+        rn[b] = std::sqrt(H.hpin[(size_t)S::SIZE * b + S::NORM]);
+        if (gn) (*gn)[b] = std::sqrt(H.hpin[(size_t)S::SIZE * b + S::NORM + 1]);
+    }
+    return MG_OK;
+}
+
+static double max_rel(const std::vector<double>& rn, const std::vector<double>& gn) {
+    double m = 0;
+    for (size_t b = 0; b < rn.size(); ++b) {
+        const double v = gn[b] > 0 ? rn[b] / gn[b] : rn[b];
+        if (!std::isfinite(v)) return v;
+        m = std::max(m, v);
+    }
+    return m;
 }
 
 }  // namespace wadr
@@ -387,7 +517,7 @@ void mg_default_params(mg_params* p) {
     p->adr = 1;
     p->omega_jacobi = 0.0;
     for (int i = 0; i < MG_MAX_LEVELS; ++i) p->alpha[i] = 0.0;
-    p->outer = MG_OUTER_IR;
+    p->outer = MG_OUTER_FGMRES;
     p->restart = 20;
     p->maxit = 500;
     p->tol = 1e-6;
@@ -400,8 +530,9 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     *out = nullptr;
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) { set_error("mg_setup: precision"); return MG_EINVAL; }
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
-        p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1) {
-        set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1)");
+        p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
+        p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES) {
+        set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }
     for (int b = 0; b < ninst; ++b) {
@@ -527,97 +658,130 @@ int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream
     return MG_OK;
 }
 
-int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_stream stream) {
-    if (!h || !u || !g) { set_error("mg_solve: bad argument"); return MG_EINVAL; }
+int mg_solve_begin(mg_handle* h, const void* u, const void* g, mg_stream stream) {
+    if (!h || !u || !g) { set_error("mg_solve_begin: bad argument"); return MG_EINVAL; }
     Handle& H = h->H;
-    if (H.p.outer == MG_OUTER_FGMRES) { set_error("mg_solve: FGMRES outer not available in this build"); return MG_EUNSUPPORTED; }
-    cudaStream_t st = H.g_stream;
-    cudaStream_t ust = (cudaStream_t)stream;
-    // order after the caller's stream
-    cudaEvent_t ev0, ev1, evu;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventCreateWithFlags(&evu, cudaEventDisableTiming);
-    cudaEventRecord(evu, ust);
-    cudaStreamWaitEvent(st, evu, 0);
-    const int ni = (int)H.inst.size();
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
     for (auto& I : H.inst) {
         LevelHost& l1 = I.lv[0];
         char* ov = (char*)I.outer_vec;
         WADR_CHECK(copy_in(g, I.off, 16, ov + (size_t)SG * I.outer_stride * 16, l1.n, l1.pitch, st));
         WADR_CHECK(copy_in(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
     }
-    const int nd = (int)H.hdesc.size();
-    const double* outer_scal = H.scal + (size_t)S::SIZE * nd;
-    std::vector<double> gn(ni), rn(ni);
-    auto read_norms = [&](bool g2) -> int {
-        WADR_CHECK(cudaMemcpyAsync(H.hpin, outer_scal, sizeof(double) * S::SIZE * ni, cudaMemcpyDeviceToHost, st));
-        WADR_CHECK(cudaStreamSynchronize(st));
-        for (int b = 0; b < ni; ++b) {
-            rn[b] = std::sqrt(H.hpin[(size_t)S::SIZE * b + S::NORM]);
-            if (g2) gn[b] = std::sqrt(H.hpin[(size_t)S::SIZE * b + S::NORM + 1]);
-        }
-        return MG_OK;
-    };
     h->eng->outer_residual(H, true, st);
-    int rc = read_norms(true);
-    if (rc) return rc;
-    auto relres = [&]() {
-        double m = 0;
-        for (int b = 0; b < ni; ++b) {
-            double v = gn[b] > 0 ? rn[b] / gn[b] : rn[b];
-            if (!std::isfinite(v)) return v;
-            m = std::max(m, v);
-        }
-        return m;
-    };
-    double rel = relres(), rel0 = rel;
-    int it = 0, nh = 0;
-    if (info && info->history && info->history_len > 0) info->history[nh++] = rel;
-    if (H.p.use_graph && !H.g_irstep) {
-        rc = capture(H, &H.g_irstep, [&](cudaStream_t s) { h->eng->ir_step(H, s); });
-        if (rc) return rc;
-        // the capture's plain run already performed one step: restart from u
-        for (auto& I : H.inst) {
-            LevelHost& l1 = I.lv[0];
-            char* ov = (char*)I.outer_vec;
-            WADR_CHECK(copy_in(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
-        }
-        h->eng->outer_residual(H, true, st);
-        rc = read_norms(true);
-        if (rc) return rc;
-    }
-    cudaEventRecord(ev0, st);
-    int status = MG_OK;
-    while (rel >= H.p.tol && it < H.p.maxit) {
-        if (H.p.use_graph) {
+    if (H.p.outer == MG_OUTER_FGMRES) h->eng->fg_start(H, st);
+    WADR_CHECK(cudaGetLastError());
+    H.solve_ready = true;
+    return MG_OK;
+}
+
+int mg_solve_steps(mg_handle* h, int nsteps, mg_stream stream) {
+    if (!h || nsteps < 0) { set_error("mg_solve_steps: bad argument"); return MG_EINVAL; }
+    Handle& H = h->H;
+    if (!H.solve_ready) { set_error("mg_solve_steps: call mg_solve_begin first"); return MG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < nsteps; ++i) {
+        if (H.p.outer == MG_OUTER_FGMRES) {
+            if (H.fg_j == H.p.restart) {   // restart: FP64 update and residual
+                h->eng->fg_finish(H, st);
+                h->eng->fg_start(H, st);
+            }
+            int rc = fg_iter_launch(h, st);
+            if (rc) return rc;
+        } else if (H.p.use_graph) {
             WADR_CHECK(cudaGraphLaunch(H.g_irstep, st));
         } else {
             h->eng->ir_step(H, st);
         }
-        ++it;
-        rc = read_norms(false);
+    }
+    WADR_CHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+int mg_solve_end(mg_handle* h, void* u, double* rel_residual, mg_stream stream) {
+    if (!h) { set_error("mg_solve_end: bad argument"); return MG_EINVAL; }
+    Handle& H = h->H;
+    if (!H.solve_ready) { set_error("mg_solve_end: call mg_solve_begin first"); return MG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (H.p.outer == MG_OUTER_FGMRES && H.fg_j > 0) {
+        h->eng->fg_finish(H, st);   // apply the pending Krylov update
+        h->eng->fg_start(H, st);
+    }
+    if (u) {
+        for (auto& I : H.inst) {
+            LevelHost& l1 = I.lv[0];
+            const char* ov = (const char*)I.outer_vec;
+            WADR_CHECK(copy_out(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
+        }
+    }
+    std::vector<double> rn, gn;
+    int rc = read_outer_norms(H, st, rn, &gn);
+    if (rc) return rc;
+    if (rel_residual) *rel_residual = max_rel(rn, gn);
+    return MG_OK;
+}
+
+int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_stream stream) {
+    if (!h || !u || !g) { set_error("mg_solve: bad argument"); return MG_EINVAL; }
+    Handle& H = h->H;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = mg_solve_begin(h, u, g, stream);
+    if (rc) return rc;
+    std::vector<double> rn, gn;
+    rc = read_outer_norms(H, st, rn, &gn);
+    if (rc) return rc;
+    double rel = max_rel(rn, gn), rel0 = rel;
+    int it = 0, nh = 0;
+    if (info && info->history && info->history_len > 0) info->history[nh++] = rel;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, st);
+    int status = MG_OK;
+    const int ni = (int)H.inst.size();
+    std::vector<double> est(ni);
+    while (rel >= H.p.tol && it < H.p.maxit) {
+        if (H.p.outer == MG_OUTER_FGMRES) {
+            // one restart: inner iterations until the estimate meets tol
+            for (int j = 0; j < H.p.restart && it < H.p.maxit; ++j) {
+                rc = fg_iter_launch(h, st);
+                if (rc) return rc;
+                ++it;
+                WADR_CHECK(cudaMemcpyAsync(H.hpin, H.est, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+                WADR_CHECK(cudaStreamSynchronize(st));
+                double e = 0;
+                for (int b = 0; b < ni; ++b) {
+                    const double v = H.hpin[b] * (gn[b] > 0 ? rn[b] / gn[b] : rn[b]);
+                    e = std::isfinite(v) ? std::max(e, v) : v;
+                }
+                if (info && info->history && nh < info->history_len) info->history[nh++] = e;
+                if (!(e >= H.p.tol)) break;
+            }
+            h->eng->fg_finish(H, st);
+            h->eng->fg_start(H, st);
+        } else {
+            rc = mg_solve_steps(h, 1, stream);
+            if (rc) return rc;
+            ++it;
+        }
+        rc = read_outer_norms(H, st, rn, nullptr);
         if (rc) return rc;
-        rel = relres();
-        if (info && info->history && nh < info->history_len) info->history[nh++] = rel;
+        rel = max_rel(rn, gn);
+        if (info && info->history && nh > 0 && H.p.outer == MG_OUTER_FGMRES) info->history[nh - 1] = rel;
+        else if (info && info->history && nh < info->history_len) info->history[nh++] = rel;
         if (!std::isfinite(rel) || rel > 1e3 * std::max(rel0, 1.0)) { status = MG_EDIVERGED; break; }
     }
     cudaEventRecord(ev1, st);
     cudaEventSynchronize(ev1);
     float ms = 0;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    if (status == MG_OK && rel >= H.p.tol) status = MG_ENOTCONV;
-    for (auto& I : H.inst) {
-        LevelHost& l1 = I.lv[0];
-        char* ov = (char*)I.outer_vec;
-        WADR_CHECK(copy_out(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
-    }
-    cudaEventRecord(evu, st);
-    cudaStreamWaitEvent(ust, evu, 0);
-    WADR_CHECK(cudaStreamSynchronize(st));
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    cudaEventDestroy(evu);
+    if (status == MG_OK && rel >= H.p.tol) status = MG_ENOTCONV;
+    rc = mg_solve_end(h, u, nullptr, stream);
+    if (rc) return rc;
     if (info) {
         info->iterations = it;
         info->status = status;
@@ -626,6 +790,48 @@ int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_strea
         info->seconds = ms * 1e-3;
     }
     return status;
+}
+
+int mg_step_launches(const mg_handle* h) { return h ? h->H.launches_step : MG_EINVAL; }
+
+const char* mg_kernel_name(int kind) { return kernel_kind_name(kind); }
+
+int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* launches, int nkinds,
+                     mg_stream stream) {
+    if (!h || nsteps < 1 || !ms || !bytes || !launches || nkinds < KK_COUNT) {
+        set_error("mg_profile_steps: bad argument");
+        return MG_EINVAL;
+    }
+    Handle& H = h->H;
+    if (!H.solve_ready) { set_error("mg_profile_steps: call mg_solve_begin first"); return MG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < nkinds; ++k) { ms[k] = 0; bytes[k] = 0; launches[k] = 0; }
+    for (int s = 0; s < nsteps; ++s) {
+        H.prof = 1;
+        H.ev_used = 0;
+        H.prof_kind.clear();
+        H.prof_bytes.clear();
+        if (H.p.outer == MG_OUTER_FGMRES) {
+            if (H.fg_j == H.p.restart) {
+                h->eng->fg_finish(H, st);
+                h->eng->fg_start(H, st);
+            }
+            h->eng->fg_iter(H, st);
+        } else {
+            h->eng->ir_step(H, st);
+        }
+        H.prof = 0;
+        WADR_CHECK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < H.prof_kind.size(); ++i) {
+            float t = 0;
+            WADR_CHECK(cudaEventElapsedTime(&t, H.ev_pool[2 * i], H.ev_pool[2 * i + 1]));
+            const int k = H.prof_kind[i];
+            ms[k] += t;
+            bytes[k] += H.prof_bytes[i];
+            launches[k] += 1;
+        }
+    }
+    return MG_OK;
 }
 
 // ------------------------------------------------------------ level ops

@@ -48,4 +48,4 @@ def test_struct_layouts_match(lib):
 def test_default_params_are_the_papers(lib):
     p = binding.default_params()
     assert (p.jacobi_iters, p.cheb_iters, p.coarse_cheb_iters, p.M, p.restart) == (1, 5, 10, 8, 20)
-    assert p.tol == 1e-6 and p.adr == 1 and p.n_cmax == 15
+    assert p.tol == 1e-6 and p.adr == 1 and p.n_cmax == 15 and p.outer == binding.MG_OUTER['fgmres']

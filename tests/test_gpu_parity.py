@@ -189,8 +189,8 @@ def test_cycle_fp64(pair):
 def test_solve_ir_fp64_matches_oracle():
     I = inst_const(128, 40.0)
     H = oracle_hier(I, n_cmax=16)
-    _, it_o, hist_o = oracle.solve_ir(H, I.g, tol=1e-8, maxit=80)
-    h = lib_handle([I], "fp64", n_cmax=16, tol=1e-8, maxit=80)
+    _, it_o, hist_o = oracle.solve_ir(H, I.g, tol=1e-8, maxit=150)
+    h = lib_handle([I], "fp64", n_cmax=16, tol=1e-8, maxit=150, outer="ir")
     u = np.zeros_like(I.g)
     st, it, rr, hist, sec = B.mg_solve(h, u, I.g.copy(), history_len=100)
     B.mg_destroy(h)
@@ -201,25 +201,60 @@ def test_solve_ir_fp64_matches_oracle():
     assert rel(helmholtz_apply(H.lev(1), u), I.g) < 1e-8
 
 
+@pytest.mark.parametrize("case", ["even128", "odd127_medium", "ragged100", "sponge63"])
+def test_fgmres_fp64_matches_oracle(case):
+    """FGMRES(20) preconditioned by the FP64 cycle (Section 4.3.1): same
+    iteration count as the oracle's FGMRES +-1, residual history within
+    1e-6 relative, and a true FP64 residual below 1e-6."""
+    I, ncm = CASES[case]()
+    H = oracle_hier(I, n_cmax=ncm)
+    _, it_o, hist_o = oracle.solve_fgmres(H, I.g, tol=1e-6, maxit=300)
+    h = lib_handle([I], "fp64", n_cmax=ncm, tol=1e-6, maxit=300)
+    u = np.zeros_like(I.g)
+    st, it, rr, hist, sec = B.mg_solve(h, u, I.g.copy(), history_len=400)
+    B.mg_destroy(h)
+    assert st == B.MG_OK and rr < 1e-6
+    assert abs(it - it_o) <= 1, (it, it_o)
+    n = min(len(hist), len(hist_o)) - 1
+    assert np.allclose(hist[:n], hist_o[:n], rtol=1e-6)
+    assert rel(helmholtz_apply(H.lev(1), u), I.g) < 1e-6
+
+
 @pytest.mark.parametrize("case", ["even128", "odd127_medium", "ragged100"])
 def test_mixed_cycle_and_solve(case):
     """Complex-FP32 cycle against the FP64 oracle: 1e-5 per cycle; the mixed
-    IR solve reaches 1e-6 with the oracle's iteration count +-1."""
+    FGMRES solve (FP32 Krylov vectors, FP64 residual and update) reaches a
+    true FP64 residual below 1e-6 with the oracle's iteration count +-1."""
     I, ncm = CASES[case]()
     H = oracle_hier(I, n_cmax=ncm)
-    h = lib_handle([I], "mixed", n_cmax=ncm, tol=1e-6, maxit=120)
+    h = lib_handle([I], "mixed", n_cmax=ncm, tol=1e-6, maxit=300)
     g32 = (I.g / np.linalg.norm(I.g)).astype(np.complex64)
     u32 = np.zeros_like(g32)
     B.mg_cycle(h, u32, g32, 1)
     ref = H.cycle(np.zeros_like(I.g), g32.astype(np.complex128))
     assert rel(u32.astype(np.complex128), ref) < 1e-5, rel(u32, ref)
     u = np.zeros_like(I.g)
-    st, it, rr, hist, sec = B.mg_solve(h, u, I.g.copy(), history_len=200)
+    st, it, rr, hist, sec = B.mg_solve(h, u, I.g.copy(), history_len=400)
     B.mg_destroy(h)
-    _, it_o, _ = oracle.solve_ir(H, I.g, tol=1e-6, maxit=120)
+    _, it_o, _ = oracle.solve_fgmres(H, I.g, tol=1e-6, maxit=300)
     assert st == B.MG_OK and rr < 1e-6
     assert abs(it - it_o) <= 1, (it, it_o)
     assert rel(helmholtz_apply(H.lev(1), u), I.g) < 1e-6
+
+
+def test_mixed_ir_matches_oracle_ir():
+    """The mixed form with iterative refinement as the outer loop (FP64
+    residual and update around FP32 cycles) on the constant medium, where the
+    stationary iteration converges."""
+    I = inst_const(128, 40.0)
+    H = oracle_hier(I, n_cmax=16)
+    _, it_o, _ = oracle.solve_ir(H, I.g, tol=1e-6, maxit=150)
+    h = lib_handle([I], "mixed", n_cmax=16, tol=1e-6, maxit=150, outer="ir")
+    u = np.zeros_like(I.g)
+    st, it, rr, hist, sec = B.mg_solve(h, u, I.g.copy(), history_len=200)
+    B.mg_destroy(h)
+    assert st == B.MG_OK and rr < 1e-6
+    assert abs(it - it_o) <= 1, (it, it_o)
 
 
 def test_batched_uneven_instances_match_single():
