@@ -232,6 +232,32 @@ int mg_cycle_launches(const mg_handle* h);
  * binding check its struct layout.  Needs no GPU. */
 void mg_abi_sizes(size_t* params, size_t* instance, size_t* info);
 
+/* ------------------------------------------------------------------------
+ * Residual without allocation.  The paper has no counterpart of this entry
+ * point; it exists for callers that may not allocate device memory: a plugin
+ * inside a host program that owns the whole device through its own caching
+ * allocator, or a latency-bound loop that must not pay for cudaMalloc /
+ * cudaFree (which can synchronise the device).  It needs no handle.
+ *
+ * Computes r = g - A u (the FP64 5-point Helmholtz operator of Section 2 on
+ * an n x n grid, h = 1/(n+1), boundary `bc`; the sponge term, if any, is
+ * evaluated from the node position with the reference frequency `omega`)
+ * and writes ||r||^2 to *norm2.  k (FP64), u, g, r (complex128) and norm2
+ * are DEVICE pointers, dense row-major; the call is asynchronous on
+ * `stream`.
+ *
+ * Scratch: 1216 complex partial sums and a counter held in fixed
+ * __device__ arrays of the library (about 20 KB, kept by every GPU that
+ * loads the library until the process exits).  The grid size does not
+ * change the scratch; n must be in 1..32768 (MG_EINVAL otherwise).  The
+ * first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same scratch and
+ * clears its counter first, so two calls that overlap on the GPU (for
+ * example on two streams) race and must be ordered by the caller. */
+int mg_residual_norm_noalloc(int n, double omega, const double* k, int bc, const void* u, const void* g, void* r,
+                             double* norm2, mg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ def load():
         "mg_profile_steps": (ip, [vp, ip, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
         "mg_kernel_name": (ctypes.c_char_p, [ip]),
         "mg_step_launches": (ip, [vp]),
+        "mg_residual_norm_noalloc": (ip, [ip, dp, vp, ip, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -102,7 +103,7 @@ def exported_symbols():
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
-            "mg_step_launches"]
+            "mg_step_launches", "mg_residual_norm_noalloc"]
 
 
 class MgError(RuntimeError):
@@ -295,3 +296,10 @@ def mg_profile_steps(h, nsteps, stream=None):
 
 def mg_step_launches(h):
     return load().mg_step_launches(h)
+
+
+def mg_residual_norm_noalloc(n, omega, k, bc, u, g, r, norm2, stream=None):
+    """r = g - A u and ||r||^2 -> norm2 (all device arrays); allocates nothing."""
+    bc = MG_BC[bc] if isinstance(bc, str) else int(bc)
+    _check(load().mg_residual_norm_noalloc(int(n), float(omega), _ptr(k), bc, _ptr(u), _ptr(g), _ptr(r),
+                                           _ptr(norm2), _stream(stream)), "mg_residual_norm_noalloc")
