@@ -179,6 +179,11 @@ int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* l
                      mg_stream stream);
 const char* mg_kernel_name(int kind);
 int mg_step_launches(const mg_handle* h);
+/* The same measurement kept apart per (kernel kind, points of the launch):
+ * fills up to maxrec records and returns their number (or a negative
+ * error). */
+int mg_profile_records(mg_handle* h, int nsteps, int* kind, long long* pts, double* ms, double* bytes,
+                       int* launches, int maxrec, mg_stream stream);
 
 /* ------------------------------------------------------------------------
  * Level operations: single-instance entry points into the same kernels the

@@ -87,6 +87,8 @@ def load():
         "mg_kernel_name": (ctypes.c_char_p, [ip]),
         "mg_step_launches": (ip, [vp]),
         "mg_residual_norm_noalloc": (ip, [ip, dp, vp, ip, vp, vp, vp, vp, vp]),
+        "mg_profile_records": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -103,7 +105,7 @@ def exported_symbols():
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
-            "mg_step_launches", "mg_residual_norm_noalloc"]
+            "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records"]
 
 
 class MgError(RuntimeError):
@@ -303,3 +305,14 @@ def mg_residual_norm_noalloc(n, omega, k, bc, u, g, r, norm2, stream=None):
     bc = MG_BC[bc] if isinstance(bc, str) else int(bc)
     _check(load().mg_residual_norm_noalloc(int(n), float(omega), _ptr(k), bc, _ptr(u), _ptr(g), _ptr(r),
                                            _ptr(norm2), _stream(stream)), "mg_residual_norm_noalloc")
+
+
+def mg_profile_records(h, nsteps, stream=None, maxrec=256):
+    """[(kernel name, points per launch, ms, algorithmic bytes, launches)] over nsteps."""
+    kd, pt = (ctypes.c_int * maxrec)(), (ctypes.c_longlong * maxrec)()
+    ms, by, la = (ctypes.c_double * maxrec)(), (ctypes.c_double * maxrec)(), (ctypes.c_int * maxrec)()
+    lib = load()
+    nr = lib.mg_profile_records(h, int(nsteps), kd, pt, ms, by, la, maxrec, _stream(stream))
+    if nr < 0:
+        _check(nr, "mg_profile_records")
+    return [(lib.mg_kernel_name(kd[i]).decode(), pt[i], ms[i], by[i], la[i]) for i in range(nr)]

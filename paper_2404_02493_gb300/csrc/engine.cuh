@@ -27,16 +27,16 @@ struct Engine : EngineBase {
     static constexpr double Q = 4.0 * sizeof(T);   // bytes of an ADR coefficient quad
 
     template <class F>
-    static void go(Handle& H, cudaStream_t st, int kind, double bytes, F&& f) {
+    static void go(Handle& H, cudaStream_t st, int kind, double bytes, F&& f, long long pts = 0) {
         if (H.prof) prof_begin(H, st);
         f();
         H.launches_cycle++;
-        if (H.prof) prof_end(H, st, kind, bytes);
+        if (H.prof) prof_end(H, st, kind, bytes, pts);
     }
 #define LAUNCH(kind, t, bpp, kern, ...)                                                              \
     go(H, st, kind, (bpp) * (double)(t).pts, [&] {                                                    \
         kern<<<(t).nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, (t).d, (t).nseg, __VA_ARGS__);            \
-    })
+    }, (t).pts)
 
     std::vector<int> descs(Handle& H, int level, const std::vector<int>& I) {
         std::vector<int> d;
@@ -91,7 +91,7 @@ struct Engine : EngineBase {
         // the dense FP64 inverse is read once, plus the two vectors
         go(H, st, KK_COARSE, 16.0 * (double)t.mat + 2 * C * (double)t.pts, [&] {
             k_coarse<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, which);
-        });
+        }, t.pts);
     }
 
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
@@ -182,7 +182,7 @@ struct Engine : EngineBase {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_OUTER_RESIDUAL, (gnorm ? 64.0 : 56.0) * t.pts, [&] {
             k_outer_residual<0><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, gnorm ? 1 : 0);
-        });
+        }, t.pts);
     }
 
     // u += ||r|| cycle(0, r/||r||); r = g - A u, ||r||  (iterative refinement)
@@ -190,12 +190,12 @@ struct Engine : EngineBase {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_OUTER_SCALE, (16.0 + C) * t.pts, [&] {
             k_outer_scale<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, SD);
-        });
+        }, t.pts);
         cycle(H, true, st);
         const int cyc = H.launches_cycle;
         go(H, st, KK_OUTER_UPDATE, (32.0 + C) * t.pts, [&] {
             k_outer_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
-        });
+        }, t.pts);
         outer_residual(H, false, st);
         H.launches_cycle = cyc;
         H.launches_step = cyc + 3;
@@ -207,7 +207,7 @@ struct Engine : EngineBase {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_START, (16.0 + C) * t.pts, [&] {
             k_fg_start<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
-        });
+        }, t.pts);
         H.fg_j = 0;
     }
 
@@ -219,21 +219,21 @@ struct Engine : EngineBase {
         dim3 bd(BX, BY);
         go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
             k_fg_prep<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
-        });
+        }, t.pts);
         cycle(H, true, st);
         const int cyc = H.launches_cycle;
         go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
             k_fg_matvec<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
-        });
+        }, t.pts);
         go(H, st, KK_FG_DOTS, (j + 2) * C * t.pts, [&] {
             k_fg_dots<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
-        });
+        }, t.pts);
         go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
             k_fg_orth<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg, 1);
-        });
+        }, t.pts);
         go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
             k_fg_orth<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg, 2);
-        });
+        }, t.pts);
         H.launches_cycle = cyc;
         H.launches_step = cyc + 5;
         H.fg_j = j + 1;
@@ -244,7 +244,7 @@ struct Engine : EngineBase {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_UPDATE, (H.fg_j * C + 32.0) * t.pts, [&] {
             k_fg_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
-        });
+        }, t.pts);
         outer_residual(H, false, st);
         H.fg_j = 0;
     }

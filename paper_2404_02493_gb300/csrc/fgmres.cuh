@@ -33,12 +33,13 @@ constexpr int SIZE = ((Y + 2 * MAXR) + 63) / 64 * 64;
 }  // namespace FS
 
 // partials of the FGMRES reductions: [block][NVF], counter slot 2
-__device__ __forceinline__ bool publish_fpartials(const LevelDesc& d, int lb, int nb, const double2 (&v)[NVF], int nv,
+template <typename E>
+__device__ __forceinline__ bool publish_fpartials(const LevelDesc& d, int lb, int nb, const E (&v)[NVF], int nv,
                                                   int* flag_sh) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) {
         for (int k = 0; k < NVF; ++k)
-            if (k < nv || k == NVF - 1) d.fpart[(long long)lb * NVF + k] = v[k];
+            if (k < nv || k == NVF - 1) d.fpart[(long long)lb * NVF + k] = to_d(v[k]);
         __threadfence();
         unsigned prev = atomicAdd(&d.counter[2], 1u);
         *flag_sh = (prev == (unsigned)(nb - 1));
@@ -46,18 +47,25 @@ __device__ __forceinline__ bool publish_fpartials(const LevelDesc& d, int lb, in
     __syncthreads();
     return *flag_sh != 0;
 }
-__device__ __forceinline__ void finish_fpartials(const LevelDesc& d, int nb, double2 (&out)[NVF], double2* sh) {
+// In the last block: value k = tid % 32 (< NVF) of block group g = tid / 32
+// sums blocks g, g+8, ...; the 8 group sums are added in order.  Totals land
+// in tot[0..NVF) (shared).  One value per thread keeps registers low.
+__device__ __forceinline__ void finish_fpartials(const LevelDesc& d, int nb, double2* tot, double2* grp /* 8*32 */) {
     __threadfence();
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int nt = blockDim.x * blockDim.y;
-#pragma unroll
-    for (int k = 0; k < NVF; ++k) out[k] = make_double2(0.0, 0.0);
-    for (int b = tid; b < nb; b += nt) {
-#pragma unroll
-        for (int k = 0; k < NVF; ++k) out[k] = dadd(out[k], __ldcg(&d.fpart[(long long)b * NVF + k]));
+    const int k = tid & 31, g = tid >> 5;
+    double2 s = make_double2(0.0, 0.0);
+    if (k < NVF)
+        for (int b = g; b < nb; b += 8) s = dadd(s, __ldcg(&d.fpart[(long long)b * NVF + k]));
+    grp[g * 32 + k] = s;
+    __syncthreads();
+    if (tid < NVF) {
+        double2 t = grp[tid];
+        for (int q = 1; q < 8; ++q) t = dadd(t, grp[q * 32 + tid]);
+        tot[tid] = t;
     }
-    block_sum<double2, NVF>(out, sh);
     if (tid == 0) d.counter[2] = 0u;
+    __syncthreads();
 }
 
 __device__ __forceinline__ double2 sload2d(const double* s, int off) { return make_double2(s[off], s[off + 1]); }
@@ -164,7 +172,8 @@ template <typename TC>
 __global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                 int nseg) {
     __shared__ LevelDesc d;
-    __shared__ double2 sh[8 * NVF];
+    __shared__ double2 grp[8 * 32];
+    __shared__ double2 tot[NVF];
     __shared__ cplx<TC> shT[8 * NVF];
     __shared__ int flag;
     SegCtx c = seg_begin(D, Sg, nseg, d);
@@ -184,14 +193,8 @@ __global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D,
             if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(__ldg(kvec<TC>(d, q) + p), wv));
     }
     block_sum<cplx<TC>, NVF>(ac, shT);
-    double2 acc[NVF];
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-        for (int q = 0; q < NVF; ++q) acc[q] = to_d(ac[q]);
-    }
-    if (publish_fpartials(d, c.lb, c.nb, acc, jj + 1, &flag)) {
-        double2 tot[NVF];
-        finish_fpartials(d, c.nb, tot, sh);
+    if (publish_fpartials(d, c.lb, c.nb, ac, jj + 1, &flag)) {
+        finish_fpartials(d, c.nb, tot, grp);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             for (int q = 0; q <= jj; ++q) sstore2d(d.fs, FS::HC + 2 * q, tot[q]);
     }
@@ -205,18 +208,19 @@ template <typename TC>
 __global__ void __launch_bounds__(NT) k_fg_orth(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                 int nseg, int pass) {
     __shared__ LevelDesc d;
-    __shared__ double2 sh[8 * NVF];
+    __shared__ double2 grp[8 * 32];
+    __shared__ double2 tot[NVF];
     __shared__ cplx<TC> shT[8 * NVF];
+    __shared__ cplx<TC> coef[MAXR];
     __shared__ int flag;
     SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const int jj = (int)d.fs[FS::J];
     cplx<TC>* w = kvec<TC>(d, jj + 1);
     const int off = (pass == 1) ? FS::HC : FS::CC;
-    cplx<TC> coef[MAXR];
-#pragma unroll
-    for (int q = 0; q < MAXR; ++q)
-        coef[q] = q <= jj ? mk<TC>((TC)d.fs[off + 2 * q], (TC)d.fs[off + 2 * q + 1]) : zero2<TC>();
+    if (tid < MAXR) coef[tid] = tid <= jj ? mk<TC>((TC)d.fs[off + 2 * tid], (TC)d.fs[off + 2 * tid + 1]) : zero2<TC>();
+    __syncthreads();
     cplx<TC> ac[NVF];
 #pragma unroll
     for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
@@ -224,31 +228,20 @@ __global__ void __launch_bounds__(NT) k_fg_orth(const LevelDesc* __restrict__ D,
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
         if (i >= d.n || j >= d.n) continue;
         const long long p = (long long)j * d.pitch + i;
-        cplx<TC> vq[MAXR];
         cplx<TC> wv = w[p];
-#pragma unroll
-        for (int q = 0; q < MAXR; ++q)
-            if (q <= jj) {
-                vq[q] = __ldg(kvec<TC>(d, q) + p);
-                wv = csub<TC>(wv, cmul<TC>(coef[q], vq[q]));
-            }
+        for (int q = 0; q <= jj; ++q) wv = csub<TC>(wv, cmul<TC>(coef[q], __ldg(kvec<TC>(d, q) + p)));
         w[p] = wv;
         if (pass == 1) {
+            // second-pass projections; V_q is read again (mostly from L1)
 #pragma unroll
             for (int q = 0; q < MAXR; ++q)
-                if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(vq[q], wv));
+                if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(__ldg(kvec<TC>(d, q) + p), wv));
         }
         ac[NVF - 1].x += cabs2<TC>(wv);
     }
     block_sum<cplx<TC>, NVF>(ac, shT);
-    double2 acc[NVF];
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-        for (int q = 0; q < NVF; ++q) acc[q] = to_d(ac[q]);
-    }
-    if (publish_fpartials(d, c.lb, c.nb, acc, NVF, &flag)) {
-        double2 tot[NVF];
-        finish_fpartials(d, c.nb, tot, sh);
+    if (publish_fpartials(d, c.lb, c.nb, ac, NVF, &flag)) {
+        finish_fpartials(d, c.nb, tot, grp);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             double* f = d.fs;
             if (pass == 1) {

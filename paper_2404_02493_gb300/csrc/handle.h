@@ -92,6 +92,7 @@ struct Handle {
     size_t ev_used = 0;
     std::vector<int> prof_kind;
     std::vector<double> prof_bytes;
+    std::vector<long long> prof_pts;        // points of each profiled launch
     bool solve_ready = false;               // mg_solve_begin was called
     // FGMRES
     int fg_j = 0;                           // inner index of the current restart (host copy)
@@ -150,6 +151,6 @@ int setup_coarse_inverse(const double* k64, const double* phi64, const double* s
 
 void set_error(const std::string& s);
 void prof_begin(Handle& H, cudaStream_t st);
-void prof_end(Handle& H, cudaStream_t st, int kind, double bytes);
+void prof_end(Handle& H, cudaStream_t st, int kind, double bytes, long long pts);
 
 }  // namespace wadr

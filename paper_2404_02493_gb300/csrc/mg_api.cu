@@ -40,10 +40,11 @@ static cudaEvent_t next_event(Handle& H) {
     return H.ev_pool[H.ev_used++];
 }
 void prof_begin(Handle& H, cudaStream_t st) { cudaEventRecord(next_event(H), st); }
-void prof_end(Handle& H, cudaStream_t st, int kind, double bytes) {
+void prof_end(Handle& H, cudaStream_t st, int kind, double bytes, long long pts) {
     cudaEventRecord(next_event(H), st);
     H.prof_kind.push_back(kind);
     H.prof_bytes.push_back(bytes);
+    H.prof_pts.push_back(pts);
 }
 
 void* Handle::alloc(size_t bytes) {
@@ -796,6 +797,54 @@ int mg_step_launches(const mg_handle* h) { return h ? h->H.launches_step : MG_EI
 
 const char* mg_kernel_name(int kind) { return kernel_kind_name(kind); }
 
+int mg_profile_records(mg_handle* h, int nsteps, int* kind, long long* pts, double* ms, double* bytes,
+                       int* launches, int maxrec, mg_stream stream) {
+    if (!h || nsteps < 1 || !kind || !pts || !ms || !bytes || !launches || maxrec < 1) {
+        set_error("mg_profile_records: bad argument");
+        return MG_EINVAL;
+    }
+    Handle& H = h->H;
+    if (!H.solve_ready) { set_error("mg_profile_records: call mg_solve_begin first"); return MG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    int nrec = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        H.prof = 1;
+        H.ev_used = 0;
+        H.prof_kind.clear();
+        H.prof_bytes.clear();
+        H.prof_pts.clear();
+        if (H.p.outer == MG_OUTER_FGMRES) {
+            if (H.fg_j == H.p.restart) {
+                h->eng->fg_finish(H, st);
+                h->eng->fg_start(H, st);
+            }
+            h->eng->fg_iter(H, st);
+        } else {
+            h->eng->ir_step(H, st);
+        }
+        H.prof = 0;
+        WADR_CHECK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < H.prof_kind.size(); ++i) {
+            float t = 0;
+            WADR_CHECK(cudaEventElapsedTime(&t, H.ev_pool[2 * i], H.ev_pool[2 * i + 1]));
+            int r = 0;
+            while (r < nrec && !(kind[r] == H.prof_kind[i] && pts[r] == H.prof_pts[i])) ++r;
+            if (r == nrec) {
+                if (nrec == maxrec) continue;
+                kind[r] = H.prof_kind[i];
+                pts[r] = H.prof_pts[i];
+                ms[r] = bytes[r] = 0;
+                launches[r] = 0;
+                ++nrec;
+            }
+            ms[r] += t;
+            bytes[r] += H.prof_bytes[i];
+            launches[r] += 1;
+        }
+    }
+    return nrec;
+}
+
 int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* launches, int nkinds,
                      mg_stream stream) {
     if (!h || nsteps < 1 || !ms || !bytes || !launches || nkinds < KK_COUNT) {
@@ -811,6 +860,7 @@ int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* l
         H.ev_used = 0;
         H.prof_kind.clear();
         H.prof_bytes.clear();
+        H.prof_pts.clear();
         if (H.p.outer == MG_OUTER_FGMRES) {
             if (H.fg_j == H.p.restart) {
                 h->eng->fg_finish(H, st);
