@@ -165,6 +165,24 @@ int mg_solve_end(mg_handle* h, void* u, double* rel_residual, mg_stream stream);
 /* Free the workspace. */
 void mg_destroy(mg_handle* h);
 
+/* Adjoint of K cycles from u0 (Section 3.3 trains through K cycles with the
+ * loss eq. loss; Algorithm 2 back-propagates through them).  For the map
+ * u_K = cycle^K(u0, g) with the handle's phi and smoother weights, and a
+ * cotangent gbar_uK of u_K, ACCUMULATES (+=):
+ *   grad_phi[n*n per instance]           d/d phi on the fine grid (FP64);
+ *   grad_weights[MG_MAX_LEVELS per inst] [0] = d/d omega_J, [l-1] = d/d alpha_l
+ *                                        for the Chebyshev levels l;
+ *   grad_u0 (complex128, may be NULL)    d/d u0.
+ * Complex cotangents follow the real-loss convention
+ * v_bar = d loss/d Re v + i d loss/d Im v.  Each cycle is recomputed from a
+ * checkpoint and swept backwards with the transposed operators (A^H, L^H,
+ * R^T = P/4, P^T = 4R), the reversed Chebyshev recurrence and GMRES(3)
+ * differentiated through its least-squares definition.  FP64 handles with
+ * the LU coarsest level only (MG_EUNSUPPORTED otherwise).  Pointers may be
+ * host or device memory; synchronises `stream`. */
+int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const void* gbar_uK, double* grad_phi,
+                      double* grad_weights, void* grad_u0, mg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Measurement.  mg_profile_steps runs `nsteps` outer steps (after
  * mg_solve_begin) without the graph, brackets every kernel launch with CUDA

@@ -89,6 +89,7 @@ def load():
         "mg_residual_norm_noalloc": (ip, [ip, dp, vp, ip, vp, vp, vp, vp, vp]),
         "mg_profile_records": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
+        "mg_cycle_backward": (ip, [vp, vp, vp, ip, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -105,7 +106,7 @@ def exported_symbols():
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
-            "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records"]
+            "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward"]
 
 
 class MgError(RuntimeError):
@@ -316,3 +317,10 @@ def mg_profile_records(h, nsteps, stream=None, maxrec=256):
     if nr < 0:
         _check(nr, "mg_profile_records")
     return [(lib.mg_kernel_name(kd[i]).decode(), pt[i], ms[i], by[i], la[i]) for i in range(nr)]
+
+
+def mg_cycle_backward(h, u0, g, K, gbar_uK, grad_phi=None, grad_weights=None, grad_u0=None, stream=None):
+    """Accumulate d/d phi, d/d weights ([ninst][16]: omega_J, alpha_l at l-1)
+    and d/d u0 of K cycles for the cotangent gbar_uK of u_K."""
+    _check(load().mg_cycle_backward(h, _ptr(u0), _ptr(g), int(K), _ptr(gbar_uK), _ptr(grad_phi),
+                                    _ptr(grad_weights), _ptr(grad_u0), _stream(stream)), "mg_cycle_backward")

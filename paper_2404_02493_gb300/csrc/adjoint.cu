@@ -1,0 +1,1057 @@
+// Hand-written adjoint of K Wave-ADR cycles (FP64 handles).
+//
+// Reverse mode with per-cycle checkpoints: the forward K cycles run on the
+// regular schedule and keep u_0..u_{K-1}; then, for k = K-1 .. 0, cycle k is
+// run again with a tape (every intermediate the reverse sweep needs) and
+// swept backwards.  Gradients follow the convention of a real loss:
+// v_bar = d loss/d Re v + i d loss/d Im v, so y = M x gives x_bar += M^H y_bar.
+//
+// Pieces (Algorithm 1 in reverse):
+//   Jacobi (eq. sjac)      u' = u + w D^{-1}(g - A u)
+//   Chebyshev (eq. cheb)   x_{m+1} = x_m + d_m, d_m = c1_m d_{m-1} + c2_m A^*(g - A x_m);
+//                          c1_m, c2_m depend on alpha through the interval
+//   transfers              R^T = P/4, P^T = 4 R
+//   ADR correction         b = conj(m) r, u += m a, m = exp(i w phi_2)
+//   GMRES(3)               x = x0 + K c, K = [r0, s L r0, s^2 L^2 r0] (s a fixed
+//                          level constant), W = L K, c = (W^H W)^{-1} W^H r0,
+//                          the least-squares definition of GMRES(3)
+//   coarsest solves        x = A^{-1} b: b_bar = A^{-H} x_bar; for the ADR
+//                          inverse also L_bar = -b_bar x^H
+//   ADR coefficients       every y = L a adds (y_bar, a) to the gradients of
+//                          (phix, phiy, d) of that level; these are chained to
+//                          phi by the transposed finite differences and the
+//                          transposed injection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "kernels.cuh"
+
+namespace wadr {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------ kernels (FP64)
+constexpr int ANT = 256;
+
+__device__ __forceinline__ bool ij_of(long long q, int n, int& i, int& j) {
+    if (q >= (long long)n * n) return false;
+    j = (int)(q / n);
+    i = (int)(q - (long long)j * n);
+    return true;
+}
+
+// out (+)= sum_t c_t x_t   (up to 4 terms; null pointers skipped)
+__global__ void ka_lincomb(int n, int pitch, double2* out, int acc, const double2* x0, double2 c0, const double2* x1,
+                           double2 c1, const double2* x2, double2 c2, const double2* x3, double2 c3) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, i, j)) return;
+    const long long p = (long long)j * pitch + i;
+    double2 v = acc ? out[p] : make_double2(0, 0);
+    if (x0) v = dadd(v, dmul(c0, x0[p]));
+    if (x1) v = dadd(v, dmul(c1, x1[p]));
+    if (x2) v = dadd(v, dmul(c2, x2[p]));
+    if (x3) v = dadd(v, dmul(c3, x3[p]));
+    out[p] = v;
+}
+
+// y (+)= s op(x), op: 0 A, 1 A^H, 2 L, 4 L^H
+__global__ void ka_apply(LevelDesc d, int op, const double2* x, double2* y, double2 s, int acc) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    double2 r;
+    if (op == 0) r = helm_apply_pt<double, false>(d, x, i, j);
+    else if (op == 1) r = helm_apply_pt<double, true>(d, x, i, j);
+    else if (op == 2) r = adr_apply_pt<double>(d, x, i, j);
+    else r = adr_apply_t_pt<double, true>(d, x, i, j);
+    r = dmul(s, r);
+    y[p] = acc ? dadd(y[p], r) : r;
+}
+
+// y (+)= s D^{-1} x  or  s D^{-H} x  (D = Helmholtz diagonal)
+__global__ void ka_diag(LevelDesc d, const double2* x, double2* y, int herm, double s, int acc) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    double2 dg = helm_diag_at<double>(d, i, j);
+    dg = dsc(dg, d.inv_h2);
+    if (herm) dg.y = -dg.y;
+    double2 r = dsc(ddiv(x[p], dg), s);
+    y[p] = acc ? dadd(y[p], r) : r;
+}
+
+// y_coarse (+)= s R x_fine   (full weighting)
+__global__ void ka_restrict(int nf, int pf, int nc, int pc, const double2* x, double2* y, double s, int acc) {
+    int I, J;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, nc, I, J)) return;
+    double2 v = make_double2(0, 0);
+    const double w[3] = {1, 2, 1};
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const int i = 2 * I + a, j = 2 * J + b;   // fine index 2I+1+(a-1)
+            if (i < nf && j < nf) v = dadd(v, dsc(x[(long long)j * pf + i], w[a] * w[b] / 16.0));
+        }
+    v = dsc(v, s);
+    const long long q = (long long)J * pc + I;
+    y[q] = acc ? dadd(y[q], v) : v;
+}
+
+// y_fine (+)= s P e_coarse  (bilinear)
+__global__ void ka_prolong(int nf, int pf, int nc, int pc, const double2* e, double2* y, double s, int acc) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, nf, i, j)) return;
+    int ia[2], ja[2];
+    double wa[2], wb[2];
+    int na, nb;
+    if (i & 1) { ia[0] = (i - 1) / 2; wa[0] = 1; na = 1; } else { ia[0] = i / 2 - 1; ia[1] = i / 2; wa[0] = wa[1] = 0.5; na = 2; }
+    if (j & 1) { ja[0] = (j - 1) / 2; wb[0] = 1; nb = 1; } else { ja[0] = j / 2 - 1; ja[1] = j / 2; wb[0] = wb[1] = 0.5; nb = 2; }
+    double2 v = make_double2(0, 0);
+    for (int q = 0; q < nb; ++q)
+        for (int r = 0; r < na; ++r)
+            if (ia[r] >= 0 && ia[r] < nc && ja[q] >= 0 && ja[q] < nc)
+                v = dadd(v, dsc(e[(long long)ja[q] * pc + ia[r]], wa[r] * wb[q]));
+    v = dsc(v, s);
+    const long long p = (long long)j * pf + i;
+    y[p] = acc ? dadd(y[p], v) : v;
+}
+
+// block partials of up to 8 dot products sum conj(x_k) y_k
+__global__ void ka_dots(int n, int pitch, int npair, const double2* const* xs, const double2* const* ys,
+                        double2* part) {
+    __shared__ double2 sh[8 * 8];
+    double2 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_double2(0, 0);
+    const long long N = (long long)n * n;
+    for (long long q = (long long)blockIdx.x * ANT + threadIdx.x; q < N; q += (long long)gridDim.x * ANT) {
+        const int j = (int)(q / n), i = (int)(q - (long long)j * n);
+        const long long p = (long long)j * pitch + i;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < npair) acc[k] = dadd(acc[k], dmulc(xs[k][p], ys[k][p]));
+    }
+    block_sum<double2, 8>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) part[blockIdx.x * 8 + k] = acc[k];
+}
+
+// ADR coefficient gradients of y = s L a with cotangent ybar:
+// qbar = (phix_bar, phiy_bar, d_bar.re, d_bar.im) per node.
+__global__ void ka_adr_grad(LevelDesc d, const double2* ybar, const double2* a, double s, double* qbar) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    const int n = d.n;
+    const double2 yb = dsc(ybar[p], s);
+    const double2 z = make_double2(0, 0);
+    const double2 aW = i > 0 ? a[p - 1] : z, aE = i < n - 1 ? a[p + 1] : z;
+    const double2 aS = j > 0 ? a[p - d.pitch] : z, aN = j < n - 1 ? a[p + d.pitch] : z;
+    const quad<double> q = reinterpret_cast<const quad<double>*>(d.adr)[p];
+    const double sx = (q.x > 0) - (q.x < 0), sy = (q.y > 0) - (q.y < 0);
+    const double wh = d.wh;
+    // d(La)/d phix = i wh [(1+sx) aW - (1-sx) aE]
+    double2 tx = dsub(dsc(aW, 1 + sx), dsc(aE, 1 - sx));
+    tx = make_double2(-wh * tx.y, wh * tx.x);
+    double2 ty = dsub(dsc(aS, 1 + sy), dsc(aN, 1 - sy));
+    ty = make_double2(-wh * ty.y, wh * ty.x);
+    const double2 ac = a[p];
+    double* o = qbar + 4 * ((long long)j * n + i);
+    o[0] += yb.x * tx.x + yb.y * tx.y;        // Re(conj(yb) tx)
+    o[1] += yb.x * ty.x + yb.y * ty.y;
+    const double2 db = dmulc(ac, yb);          // conj(a) ybar
+    o[2] += db.x;
+    o[3] += db.y;
+}
+
+// demodulation b = conj(m) r:      rbar += m bbar,    mbar += r conj(bbar)
+// modulated update u += m a:       abar  = conj(m) ubar, mbar += conj(a) ubar
+__global__ void ka_mod(LevelDesc d, int mode, const double2* x, const double2* xbar, double2* ybar, double2* mbar) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    const double2 m = reinterpret_cast<const double2*>(d.mod)[p];
+    const long long q = (long long)j * d.n + i;
+    if (mode == 0) {
+        const double2 bb = xbar[p];
+        ybar[p] = dadd(ybar[p], dmul(m, bb));
+        mbar[q] = dadd(mbar[q], dmul(x[p], make_double2(bb.x, -bb.y)));
+    } else {
+        const double2 ub = xbar[p];
+        ybar[p] = dmulc(m, ub);
+        mbar[q] = dadd(mbar[q], dmulc(x[p], ub));
+    }
+}
+
+// forward modulation: mode 0: out = conj(m) x ; mode 1: out = u + m x
+__global__ void ka_apply_mod(LevelDesc d, int mode, const double2* x, const double2* u, double2* out) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    const double2 m = reinterpret_cast<const double2*>(d.mod)[p];
+    if (mode == 0) out[p] = dmulc(m, x[p]);
+    else out[p] = dadd(u[p], dmul(m, x[p]));
+}
+
+// y (+)= M x or M^H x with a dense FP64 n^2 x n^2 matrix (coarsest level)
+__global__ void ka_gemv(int n, int pitch, const double2* M, const double2* x, double2* y, int herm, int acc) {
+    const int row = blockIdx.x * ANT + threadIdx.x;
+    const int N = n * n;
+    if (row >= N) return;
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < N; ++c) {
+        const int i = c % n, j = c / n;
+        const double2 xv = x[(long long)j * pitch + i];
+        if (herm) s = dadd(s, dmulc(M[(long long)c * N + row], xv));
+        else s = dadd(s, dmul(M[(long long)row * N + c], xv));
+    }
+    const int i = row % n, j = row / n;
+    const long long p = (long long)j * pitch + i;
+    y[p] = acc ? dadd(y[p], s) : s;
+}
+
+// ------------------------------------------------------------ host side
+struct Vec {
+    double2* p = nullptr;
+};
+
+struct AdjLevel {
+    LevelDesc d;          // host copy (device pointers)
+    int n = 0, pitch = 0;
+    size_t sz = 0;        // elements per vector
+    std::vector<double2*> pool;   // free vectors
+    std::vector<double2*> owned;  // every vector of this level
+    double* qbar = nullptr;       // ADR coefficient gradients (4 per node)
+    double2* mbar = nullptr;      // modulation gradient (level 2)
+    double kscale = 1.0;          // fixed Krylov basis scale of this level
+    double cbar1[16], cbar2[16];  // Chebyshev coefficient gradients
+};
+
+struct Adjoint {
+    Handle& H;
+    InstHost& I;
+    cudaStream_t st;
+    std::vector<AdjLevel> lv;
+    std::vector<double2*> all;
+    double2* part = nullptr;
+    const double2** dptrs = nullptr;
+    double2* hpart = nullptr;
+    double wj_bar = 0;
+    int err = 0;
+
+    Adjoint(Handle& h, InstHost& inst, cudaStream_t s) : H(h), I(inst), st(s) {}
+    ~Adjoint() {
+        for (auto* p : all) cudaFree(p);
+        for (auto& L : lv) {
+            cudaFree(L.qbar);
+            cudaFree(L.mbar);
+        }
+        cudaFree(part);
+        cudaFree((void*)dptrs);
+        cudaFreeHost(hpart);
+    }
+
+    int blocks(int n) const { return (int)(((long long)n * n + ANT - 1) / ANT); }
+
+    int init() {
+        lv.resize(I.L + 1);
+        for (int l = 1; l <= I.L; ++l) {
+            AdjLevel& L = lv[l];
+            L.d = H.hdesc[I.lv[l - 1].desc];
+            L.n = L.d.n;
+            L.pitch = L.d.pitch;
+            L.sz = (size_t)L.pitch * L.n;
+            if (L.d.adr) {
+                if (cudaMalloc(&L.qbar, sizeof(double) * 4 * L.n * L.n) != cudaSuccess) return MG_ENOMEM;
+                cudaMemsetAsync(L.qbar, 0, sizeof(double) * 4 * L.n * L.n, st);
+                // fixed Krylov scale: 1 / (Gershgorin bound of L)
+                L.kscale = 1.0 / (8.0 * L.d.inv_h2 + 4.0 * I.omega * I.omega + 8.0 * L.d.wh);
+            }
+            if (L.d.mod) {
+                if (cudaMalloc(&L.mbar, sizeof(double2) * L.n * L.n) != cudaSuccess) return MG_ENOMEM;
+                cudaMemsetAsync(L.mbar, 0, sizeof(double2) * L.n * L.n, st);
+            }
+            for (int m = 0; m < 16; ++m) L.cbar1[m] = L.cbar2[m] = 0;
+        }
+        if (cudaMalloc(&part, sizeof(double2) * 8 * 1024) != cudaSuccess) return MG_ENOMEM;
+        if (cudaMalloc((void**)&dptrs, sizeof(double2*) * 16) != cudaSuccess) return MG_ENOMEM;
+        if (cudaMallocHost(&hpart, sizeof(double2) * 8 * 1024) != cudaSuccess) return MG_ENOMEM;
+        return MG_OK;
+    }
+
+    double2* get(int l) {
+        AdjLevel& L = lv[l];
+        if (!L.pool.empty()) {
+            double2* p = L.pool.back();
+            L.pool.pop_back();
+            return p;
+        }
+        double2* p = nullptr;
+        if (cudaMalloc(&p, sizeof(double2) * L.sz) != cudaSuccess) {
+            err = MG_ENOMEM;
+            return nullptr;
+        }
+        cudaMemsetAsync(p, 0, sizeof(double2) * L.sz, st);
+        all.push_back(p);
+        L.owned.push_back(p);
+        return p;
+    }
+    void put(int l, double2* p) {
+        if (p) lv[l].pool.push_back(p);
+    }
+    // after one cycle's reverse sweep every vector is free again
+    void reset() {
+        for (auto& L : lv) L.pool = L.owned;
+        for (void* t : tapes) delete_tape(t);
+        tapes.clear();
+        tape_kind.clear();
+    }
+    std::vector<int> tape_kind;
+    void delete_tape(void* t);
+
+    // ----- building blocks
+    void lin(int l, double2* out, bool acc, const double2* x0, cd c0, const double2* x1 = nullptr, cd c1 = 0,
+             const double2* x2 = nullptr, cd c2 = 0, const double2* x3 = nullptr, cd c3 = 0) {
+        AdjLevel& L = lv[l];
+        ka_lincomb<<<blocks(L.n), ANT, 0, st>>>(L.n, L.pitch, out, acc, x0, make_double2(c0.real(), c0.imag()), x1,
+                                                make_double2(c1.real(), c1.imag()), x2,
+                                                make_double2(c2.real(), c2.imag()), x3,
+                                                make_double2(c3.real(), c3.imag()));
+    }
+    void apply(int l, int op, const double2* x, double2* y, cd s = 1.0, bool acc = false) {
+        AdjLevel& L = lv[l];
+        ka_apply<<<blocks(L.n), ANT, 0, st>>>(L.d, op, x, y, make_double2(s.real(), s.imag()), acc);
+    }
+    void diag(int l, const double2* x, double2* y, bool herm, double s, bool acc) {
+        AdjLevel& L = lv[l];
+        ka_diag<<<blocks(L.n), ANT, 0, st>>>(L.d, x, y, herm, s, acc);
+    }
+    void restrict_(int l, const double2* xf, double2* yc, double s, bool acc) {
+        AdjLevel &F = lv[l], &Cc = lv[l + 1];
+        ka_restrict<<<blocks(Cc.n), ANT, 0, st>>>(F.n, F.pitch, Cc.n, Cc.pitch, xf, yc, s, acc);
+    }
+    void prolong_(int l, const double2* ec, double2* yf, double s, bool acc) {
+        AdjLevel &F = lv[l], &Cc = lv[l + 1];
+        ka_prolong<<<blocks(F.n), ANT, 0, st>>>(F.n, F.pitch, Cc.n, Cc.pitch, ec, yf, s, acc);
+    }
+    void adr_grad(int l, const double2* ybar, const double2* a, double s) {
+        AdjLevel& L = lv[l];
+        ka_adr_grad<<<blocks(L.n), ANT, 0, st>>>(L.d, ybar, a, s, L.qbar);
+    }
+    // conj(x_k)^T y_k for up to 8 pairs (synchronises)
+    std::vector<cd> dots(int l, std::vector<std::pair<const double2*, const double2*>> pr) {
+        AdjLevel& L = lv[l];
+        const int np = (int)pr.size();
+        const double2* h[16];
+        for (int k = 0; k < 8; ++k) {
+            h[k] = k < np ? pr[k].first : pr[0].first;
+            h[8 + k] = k < np ? pr[k].second : pr[0].second;
+        }
+        cudaMemcpyAsync((void*)dptrs, h, sizeof(h), cudaMemcpyHostToDevice, st);
+        const int nb = std::min(blocks(L.n), 1024);
+        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, dptrs, dptrs + 8, part);
+        cudaMemcpyAsync(hpart, part, sizeof(double2) * 8 * nb, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        std::vector<cd> out(np, 0.0);
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < np; ++k) out[k] += cd(hpart[b * 8 + k].x, hpart[b * 8 + k].y);
+        return out;
+    }
+
+    // ----- Chebyshev coefficients and their alpha-derivatives (dual numbers)
+    void cheb_coeffs(int l, double alpha, int q, double* c1, double* c2, double* dc1, double* dc2) {
+        const double lam = I.lv[l - 1].lam_max;
+        // a = lam/alpha, b = lam; derivatives w.r.t. alpha
+        const double a = lam / alpha, da = -lam / (alpha * alpha), b = lam;
+        const double th = 0.5 * (a + b), dth = 0.5 * da, de = 0.5 * (b - a), dde = -0.5 * da;
+        const double sg = th / de, dsg = (dth * de - th * dde) / (de * de);
+        double rho = 1.0 / sg, drho = -dsg / (sg * sg);
+        c1[0] = 0;
+        dc1[0] = 0;
+        c2[0] = 1.0 / th;
+        dc2[0] = -dth / (th * th);
+        for (int m = 1; m < q; ++m) {
+            const double den = 2 * sg - rho, dden = 2 * dsg - drho;
+            const double rn = 1.0 / den, drn = -dden / (den * den);
+            c1[m] = rn * rho;
+            dc1[m] = drn * rho + rn * drho;
+            c2[m] = 2.0 * rn / de;
+            dc2[m] = 2.0 * (drn * de - rn * dde) / (de * de);
+            rho = rn;
+            drho = drn;
+        }
+    }
+
+    // ============================================================ tapes
+    struct ChebTape {
+        std::vector<double2*> x;   // x_0 .. x_q (x_0 may be null = zero)
+        double2* g = nullptr;
+    };
+    struct GmTape {
+        double2 *r0 = nullptr, *x0 = nullptr, *b = nullptr;   // x0 null: from zero (r0 = b)
+        double2 *k[3] = {nullptr, nullptr, nullptr}, *w[3] = {nullptr, nullptr, nullptr};
+        cd c[3] = {0, 0, 0};
+        cd G[3][3];
+        cd z[3];
+        bool zero = false;
+    };
+    struct AdrTape {
+        int l;
+        double2* b;
+        GmTape pre, post;
+        double2 *x1, *x2, *x3, *rc;
+        AdrTape* child = nullptr;
+        double2* coarse_x = nullptr;   // l == L
+    };
+    struct WaveTape {
+        int l;
+        double2 *g, *u_in, *u_out;
+        ChebTape pre, post;
+        double2 *v1 = nullptr, *u1 = nullptr, *u2 = nullptr, *v2 = nullptr;  // level 1
+        double2* rc = nullptr;
+        WaveTape* child = nullptr;
+        std::vector<double2*> corr_u, corr_r;   // level 2: u before each correction, residuals
+        std::vector<AdrTape*> corr_adr;
+    };
+    std::vector<void*> tapes;
+
+    // ----- GMRES(3) through its least-squares definition
+    void gm_forward(int l, GmTape& T, double2* b, double2* x0, double2* x) {
+        AdjLevel& L = lv[l];
+        T.b = b;
+        T.x0 = x0;
+        T.r0 = get(l);
+        if (x0) {
+            apply(l, 2, x0, T.r0, 1.0);
+            lin(l, T.r0, false, b, 1.0, T.r0, -1.0);
+        } else {
+            lin(l, T.r0, false, b, 1.0);
+        }
+        const double s = L.kscale;
+        for (int q = 0; q < 3; ++q) {
+            T.k[q] = get(l);
+            T.w[q] = get(l);
+        }
+        lin(l, T.k[0], false, T.r0, 1.0);
+        apply(l, 2, T.k[0], T.w[0], 1.0);
+        lin(l, T.k[1], false, T.w[0], s);
+        apply(l, 2, T.k[1], T.w[1], 1.0);
+        lin(l, T.k[2], false, T.w[1], s);
+        apply(l, 2, T.k[2], T.w[2], 1.0);
+        auto d1 = dots(l, {{T.w[0], T.w[0]}, {T.w[0], T.w[1]}, {T.w[0], T.w[2]}, {T.w[1], T.w[1]},
+                           {T.w[1], T.w[2]}, {T.w[2], T.w[2]}, {T.w[0], T.r0}, {T.w[1], T.r0}});
+        auto d2 = dots(l, {{T.w[2], T.r0}});
+        T.G[0][0] = d1[0]; T.G[0][1] = d1[1]; T.G[0][2] = d1[2];
+        T.G[1][1] = d1[3]; T.G[1][2] = d1[4]; T.G[2][2] = d1[5];
+        T.G[1][0] = std::conj(T.G[0][1]); T.G[2][0] = std::conj(T.G[0][2]); T.G[2][1] = std::conj(T.G[1][2]);
+        T.z[0] = d1[6]; T.z[1] = d1[7]; T.z[2] = d2[0];
+        T.zero = !(std::abs(T.G[0][0]) > 0);
+        if (!T.zero) solve3(T.G, T.z, T.c);
+        // x = x0 + K c
+        lin(l, x, false, T.k[0], T.c[0], T.k[1], T.c[1], T.k[2], T.c[2], x0, 1.0);
+    }
+
+    static void solve3(const cd G[3][3], const cd* z, cd* c) {
+        cd M[3][4];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) M[i][j] = G[i][j];
+            M[i][3] = z[i];
+        }
+        for (int k = 0; k < 3; ++k) {
+            int pv = k;
+            for (int i = k + 1; i < 3; ++i)
+                if (std::abs(M[i][k]) > std::abs(M[pv][k])) pv = i;
+            for (int j = 0; j < 4; ++j) std::swap(M[k][j], M[pv][j]);
+            for (int i = k + 1; i < 3; ++i) {
+                const cd f = M[i][k] / M[k][k];
+                for (int j = k; j < 4; ++j) M[i][j] -= f * M[k][j];
+            }
+        }
+        for (int i = 2; i >= 0; --i) {
+            cd s = M[i][3];
+            for (int j = i + 1; j < 3; ++j) s -= M[i][j] * c[j];
+            c[i] = s / M[i][i];
+        }
+    }
+
+    // reverse of gm_forward: xbar given; adds to bbar, x0bar (if x0), ADR gradients
+    void gm_backward(int l, GmTape& T, double2* xbar, double2* bbar, double2* x0bar) {
+        if (T.zero) {
+            if (x0bar) lin(l, x0bar, true, xbar, 1.0);
+            return;
+        }
+        AdjLevel& L = lv[l];
+        const double s = L.kscale;
+        // x = x0 + K c
+        auto cb = dots(l, {{T.k[0], xbar}, {T.k[1], xbar}, {T.k[2], xbar}});
+        // c = G^{-1} z: zbar = G^{-H} cbar, Gbar = -zbar c^H
+        cd GH[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) GH[i][j] = std::conj(T.G[j][i]);
+        cd zb[3];
+        solve3(GH, cb.data(), zb);
+        cd Gb[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Gb[i][j] = -zb[i] * std::conj(T.c[j]);
+        double2* r0b = get(l);
+        double2* kb[3];
+        double2* wb[3];
+        for (int q = 0; q < 3; ++q) {
+            kb[q] = get(l);
+            wb[q] = get(l);
+        }
+        // kbar_j = conj(c_j) xbar
+        for (int q = 0; q < 3; ++q) lin(l, kb[q], false, xbar, std::conj(T.c[q]));
+        // z_i = w_i^H r0: r0bar += sum_i w_i zbar_i ; wbar_i += r0 conj(zbar_i)
+        lin(l, r0b, false, T.w[0], zb[0], T.w[1], zb[1], T.w[2], zb[2]);
+        // G_ij = w_i^H w_j: wbar_j += sum_i w_i Gbar_ij ; wbar_i += sum_j w_j conj(Gbar_ij)
+        for (int q = 0; q < 3; ++q) {
+            cd a0 = Gb[0][q] + std::conj(Gb[q][0]);
+            cd a1 = Gb[1][q] + std::conj(Gb[q][1]);
+            cd a2 = Gb[2][q] + std::conj(Gb[q][2]);
+            lin(l, wb[q], false, T.w[0], a0, T.w[1], a1, T.w[2], a2, T.r0, std::conj(zb[q]));
+        }
+        // w_q = L k_q
+        for (int q = 0; q < 3; ++q) {
+            apply(l, 4, wb[q], kb[q], 1.0, true);
+            adr_grad(l, wb[q], T.k[q], 1.0);
+        }
+        // k_2 = s L k_1, k_1 = s L k_0
+        apply(l, 4, kb[2], kb[1], s, true);
+        adr_grad(l, kb[2], T.k[1], s);
+        apply(l, 4, kb[1], kb[0], s, true);
+        adr_grad(l, kb[1], T.k[0], s);
+        lin(l, r0b, true, kb[0], 1.0);
+        // r0 = b - L x0 (or b)
+        lin(l, bbar, true, r0b, 1.0);
+        if (T.x0) {
+            lin(l, x0bar, true, xbar, 1.0);
+            apply(l, 4, r0b, x0bar, -1.0, true);
+            adr_grad(l, r0b, T.x0, -1.0);
+        }
+        put(l, r0b);
+        for (int q = 0; q < 3; ++q) {
+            put(l, kb[q]);
+            put(l, wb[q]);
+        }
+    }
+
+    // ----- ADR V-cycle
+    AdrTape* adr_forward(int l, double2* b, double2* x_out) {
+        AdrTape* T = new AdrTape();
+        tapes.push_back(T);
+        tape_kind.push_back(0);
+        T->l = l;
+        T->b = b;
+        if (l == I.L) {
+            AdjLevel& L = lv[l];
+            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, b, x_out, 0, 0);
+            T->coarse_x = x_out;
+            return T;
+        }
+        T->x1 = get(l);
+        gm_forward(l, T->pre, b, nullptr, T->x1);
+        double2* r = get(l);
+        apply(l, 2, T->x1, r, 1.0);
+        lin(l, r, false, b, 1.0, r, -1.0);
+        T->rc = get(l + 1);
+        restrict_(l, r, T->rc, 1.0, false);
+        put(l, r);
+        double2* ec = get(l + 1);
+        T->child = adr_forward(l + 1, T->rc, ec);
+        T->x2 = get(l);
+        lin(l, T->x2, false, T->x1, 1.0);
+        prolong_(l, ec, T->x2, 1.0, true);
+        gm_forward(l, T->post, b, T->x2, x_out);
+        T->x3 = x_out;
+        return T;
+    }
+
+    void adr_backward(AdrTape* T, double2* xbar, double2* bbar) {
+        const int l = T->l;
+        if (l == I.L) {
+            AdjLevel& L = lv[l];
+            // x = X b: bbar += X^H xbar ; L_bar = -bbar_new x^H
+            double2* bb = get(l);
+            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
+            lin(l, bbar, true, bb, 1.0);
+            adr_grad(l, bb, T->coarse_x, -1.0);
+            put(l, bb);
+            return;
+        }
+        double2* x2b = get(l);
+        lin(l, x2b, false, nullptr, 0.0);
+        gm_backward(l, T->post, xbar, bbar, x2b);
+        // x2 = x1 + P ec
+        double2* x1b = get(l);
+        lin(l, x1b, false, x2b, 1.0);
+        double2* ecb = get(l + 1);
+        restrict_(l, x2b, ecb, 4.0, false);       // P^T = 4 R
+        double2* rcb = get(l + 1);
+        lin(l + 1, rcb, false, nullptr, 0.0);
+        adr_backward(T->child, ecb, rcb);
+        // rc = R r, r = b - L x1
+        double2* rb = get(l);
+        prolong_(l, rcb, rb, 0.25, false);        // R^T = P/4
+        lin(l, bbar, true, rb, 1.0);
+        apply(l, 4, rb, x1b, -1.0, true);
+        adr_grad(l, rb, T->x1, -1.0);
+        gm_backward(l, T->pre, x1b, bbar, nullptr);
+        put(l, x2b);
+        put(l, x1b);
+        put(l + 1, ecb);
+        put(l + 1, rcb);
+        put(l, rb);
+    }
+
+    // ----- Chebyshev
+    void cheb_forward(int l, ChebTape& T, double2* x0, double2* g, int q, double2* xout) {
+        T.g = g;
+        double c1[16], c2[16], d1[16], d2[16];
+        cheb_coeffs(l, I.lv[l - 1].alpha, q, c1, c2, d1, d2);
+        T.x.assign(q + 1, nullptr);
+        T.x[0] = x0;
+        double2* d = get(l);
+        double2* s = get(l);
+        double2* t = get(l);
+        for (int m = 0; m < q; ++m) {
+            // s = A^H (g - A x_m)
+            if (T.x[m]) {
+                apply(l, 0, T.x[m], t, 1.0);
+                lin(l, t, false, g, 1.0, t, -1.0);
+            } else {
+                lin(l, t, false, g, 1.0);
+            }
+            apply(l, 1, t, s, 1.0);
+            lin(l, d, false, s, c2[m], m > 0 ? d : nullptr, c1[m]);
+            double2* xn = (m == q - 1) ? xout : get(l);
+            lin(l, xn, false, d, 1.0, T.x[m], 1.0);
+            T.x[m + 1] = xn;
+        }
+        put(l, d);
+        put(l, s);
+        put(l, t);
+    }
+
+    void cheb_backward(int l, ChebTape& T, double2* xbar /* in: x_q bar, out: x_0 bar */, double2* gbar) {
+        const int q = (int)T.x.size() - 1;
+        double c1[16], c2[16], d1[16], d2[16];
+        cheb_coeffs(l, I.lv[l - 1].alpha, q, c1, c2, d1, d2);
+        AdjLevel& L = lv[l];
+        double2* db = get(l);      // d_m bar
+        double2* dprev = get(l);   // d_{m-1} (recomputed)
+        double2* s = get(l);
+        double2* t = get(l);
+        double2* sb = get(l);
+        lin(l, db, false, nullptr, 0.0);
+        for (int m = q - 1; m >= 0; --m) {
+            // x_{m+1} = x_m + d_m: d_m bar += x_{m+1} bar; x_m bar = x_{m+1} bar (kept in xbar)
+            lin(l, db, true, xbar, 1.0);
+            // s_m = A^H (g - A x_m)
+            if (T.x[m]) {
+                apply(l, 0, T.x[m], t, 1.0);
+                lin(l, t, false, T.g, 1.0, t, -1.0);
+            } else {
+                lin(l, t, false, T.g, 1.0);
+            }
+            apply(l, 1, t, s, 1.0);
+            // d_m = c1 d_{m-1} + c2 s_m
+            auto dd = dots(l, {{s, db}});
+            L.cbar2[m] += dd[0].real();
+            if (m > 0) {
+                // d_{m-1} = x_m - x_{m-1}
+                lin(l, dprev, false, T.x[m], 1.0, T.x[m - 1], -1.0);
+                auto d2v = dots(l, {{dprev, db}});
+                L.cbar1[m] += d2v[0].real();
+            }
+            lin(l, sb, false, db, c2[m]);
+            // s = A^H t, t = g - A x_m: t_bar = A s_bar
+            apply(l, 0, sb, t, 1.0);
+            lin(l, gbar, true, t, 1.0);
+            if (T.x[m]) apply(l, 1, t, xbar, -1.0, true);
+            // d_{m-1} bar = c1 d_m bar
+            if (m > 0) lin(l, db, false, db, c1[m]);
+        }
+        // alpha gradient from the coefficient gradients
+        double ab = 0;
+        for (int m = 0; m < q; ++m) ab += L.cbar1[m] * d1[m] + L.cbar2[m] * d2[m];
+        alpha_bar[l] += ab;
+        for (int m = 0; m < 16; ++m) L.cbar1[m] = L.cbar2[m] = 0;
+        put(l, db);
+        put(l, dprev);
+        put(l, s);
+        put(l, t);
+        put(l, sb);
+    }
+    double alpha_bar[MG_MAX_LEVELS + 1] = {0};
+
+    // ----- wave cycle
+    bool is_cheb(int l) const { return I.lv[l - 1].cheb; }
+
+    WaveTape* wave_forward(int l, double2* u_in, double2* g, double2* u_out) {
+        WaveTape* T = new WaveTape();
+        tapes.push_back(T);
+        tape_kind.push_back(1);
+        T->l = l;
+        T->g = g;
+        T->u_in = u_in;
+        T->u_out = u_out;
+        AdjLevel& L = lv[l];
+        if (l == I.L) {
+            // from zero: u = A^{-1} g
+            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, g, u_out, 0, 0);
+            return T;
+        }
+        const double wj = I.omega_j;
+        double2* u;   // current iterate
+        double2* t = get(l);
+        if (l == 1) {
+            T->v1 = get(l);
+            apply(l, 0, u_in, t, 1.0);
+            lin(l, t, false, g, 1.0, t, -1.0);
+            diag(l, t, T->v1, false, 1.0, false);
+            T->u1 = get(l);
+            lin(l, T->u1, false, u_in, 1.0, T->v1, wj);
+            u = T->u1;
+        } else if (l == 3) {
+            u = nullptr;
+        } else {
+            u = get(l);
+            cheb_forward(l, T->pre, nullptr, g, H.p.cheb_iters, u);
+        }
+        // rc = R (g - A u)
+        if (u) {
+            apply(l, 0, u, t, 1.0);
+            lin(l, t, false, g, 1.0, t, -1.0);
+        } else {
+            lin(l, t, false, g, 1.0);
+        }
+        T->rc = get(l + 1);
+        restrict_(l, t, T->rc, 1.0, false);
+        double2* ec = get(l + 1);
+        T->child = wave_forward(l + 1, nullptr, T->rc, ec);
+        double2* u2 = get(l);
+        if (u) lin(l, u2, false, u, 1.0);
+        else lin(l, u2, false, nullptr, 0.0);
+        prolong_(l, ec, u2, 1.0, true);
+        if (l == 1) {
+            T->u2 = u2;
+            T->v2 = get(l);
+            apply(l, 0, u2, t, 1.0);
+            lin(l, t, false, g, 1.0, t, -1.0);
+            diag(l, t, T->v2, false, 1.0, false);
+            lin(l, u_out, false, u2, 1.0, T->v2, wj);
+        } else if (l == 3) {
+            lin(l, u_out, false, u2, 1.0);
+        } else {
+            const bool adr = (l == 2 && H.p.adr && H.p.M > 0 && lv[2].d.adr);
+            double2* y = adr ? get(l) : u_out;
+            cheb_forward(l, T->post, u2, g, H.p.cheb_iters, y);
+            if (y != u_out) {
+                // ADR corrections (Algorithm 1, level 2), M times
+                double2* cur = y;
+                for (int m = 0; m < H.p.M; ++m) {
+                    double2* r = get(l);
+                    apply(l, 0, cur, r, 1.0);
+                    lin(l, r, false, g, 1.0, r, -1.0);
+                    double2* b = get(l);
+                    // b = conj(m) r  (pointwise via the modulation field)
+                    ka_mod_demod(l, r, b);
+                    double2* a = get(l);
+                    AdrTape* at = adr_forward(2, b, a);
+                    double2* nx = (m == H.p.M - 1) ? u_out : get(l);
+                    ka_mod_update(l, cur, a, nx);
+                    T->corr_u.push_back(cur);
+                    T->corr_r.push_back(r);
+                    T->corr_adr.push_back(at);
+                    cur = nx;
+                }
+            }
+        }
+        put(l, t);
+        return T;
+    }
+
+    void ka_mod_demod(int l, const double2* r, double2* b);
+    void ka_mod_update(int l, const double2* u, const double2* a, double2* out);
+
+    // ubar_out given; produces ubar_in (if u_in) and adds to gbar
+    void wave_backward(WaveTape* T, double2* uob, double2* uib, double2* gbar) {
+        const int l = T->l;
+        AdjLevel& L = lv[l];
+        if (l == I.L) {
+            double2* gb = get(l);
+            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, uob, gb, 1, 0);
+            lin(l, gbar, true, gb, 1.0);
+            put(l, gb);
+            return;
+        }
+        const double wj = I.omega_j;
+        double2* u2b = get(l);
+        double2* t = get(l);
+        if (l == 1) {
+            // u_out = u2 + wj v2, v2 = D^{-1}(g - A u2)
+            auto dv = dots(l, {{T->v2, uob}});
+            wj_bar += dv[0].real();
+            lin(l, u2b, false, uob, 1.0);
+            diag(l, uob, t, true, wj, false);        // t = wj D^{-H} ubar
+            lin(l, gbar, true, t, 1.0);
+            apply(l, 1, t, u2b, -1.0, true);
+        } else if (l == 3) {
+            lin(l, u2b, false, uob, 1.0);
+        } else {
+            double2* yb = get(l);
+            lin(l, yb, false, uob, 1.0);
+            if (!T->corr_adr.empty()) {
+                double2* curb = yb;   // bar of the iterate after correction m
+                for (int m = (int)T->corr_adr.size() - 1; m >= 0; --m) {
+                    // nx = cur + mod a  -> cur_bar = nx_bar, a_bar = conj(mod) nx_bar, mod_bar
+                    double2* ab = get(l);
+                    ka_mod_update_back(l, T->corr_adr[m]->x3, curb, ab);
+                    double2* bb = get(l);
+                    lin(l, bb, false, nullptr, 0.0);
+                    adr_backward(T->corr_adr[m], ab, bb);
+                    // b = conj(mod) r -> r_bar = mod b_bar, mod_bar += r conj(b_bar)
+                    double2* rb = get(l);
+                    lin(l, rb, false, nullptr, 0.0);
+                    ka_mod_demod_back(l, T->corr_r[m], bb, rb);
+                    // r = g - A cur
+                    lin(l, gbar, true, rb, 1.0);
+                    apply(l, 1, rb, curb, -1.0, true);
+                    put(l, ab);
+                    put(l, bb);
+                    put(l, rb);
+                }
+            }
+            cheb_backward(l, T->post, yb, gbar);   // yb becomes u2 bar
+            lin(l, u2b, false, yb, 1.0);
+            put(l, yb);
+        }
+        // u2 = u + P ec
+        double2* ecb = get(l + 1);
+        restrict_(l, u2b, ecb, 4.0, false);
+        double2* rcb = get(l + 1);
+        lin(l + 1, rcb, false, nullptr, 0.0);
+        wave_backward(T->child, ecb, nullptr, rcb);
+        // rc = R (g - A u)
+        double2* rb = get(l);
+        prolong_(l, rcb, rb, 0.25, false);
+        lin(l, gbar, true, rb, 1.0);
+        double2* ub = u2b;    // bar of the pre-smoothed iterate u
+        if (l == 3) {
+            // u = 0 on entry
+        } else {
+            apply(l, 1, rb, ub, -1.0, true);
+            if (l == 1) {
+                // u1 = u_in + wj v1, v1 = D^{-1}(g - A u_in)
+                auto dv = dots(l, {{T->v1, ub}});
+                wj_bar += dv[0].real();
+                if (uib) lin(l, uib, true, ub, 1.0);
+                diag(l, ub, t, true, wj, false);
+                lin(l, gbar, true, t, 1.0);
+                if (uib) apply(l, 1, t, uib, -1.0, true);
+            } else {
+                cheb_backward(l, T->pre, ub, gbar);   // from zero: no x_0 bar
+            }
+        }
+        put(l, u2b);
+        put(l, t);
+        put(l + 1, ecb);
+        put(l + 1, rcb);
+        put(l, rb);
+    }
+
+    void ka_mod_update_back(int l, const double2* a, const double2* nxb, double2* ab);
+    void ka_mod_demod_back(int l, const double2* r, const double2* bb, double2* rb);
+};
+
+void Adjoint::delete_tape(void* t) {
+    (void)t;   // the tapes hold only pointers into the level pools
+}
+
+// d loss/d phi on the fine grid from the per-level ADR coefficient
+// gradients and the level-2 modulation gradient (host, FP64):
+//   d = 4/h^2 - 2 i w (|px|+|py|)/h - i w lap + w^2 (px^2 + py^2 - s^2) [+ phi-free terms]
+//   px, py, lap: central differences with linear ghost extrapolation
+//   m = exp(i w phi_2);  phi_l = injection of phi.
+static void chain_to_phi(const InstHost& I, const std::vector<AdjLevel>& lv, cudaStream_t st, double* grad_phi_host) {
+    const int n1 = I.n;
+    const double w = I.omega;
+    for (int l = 2; l <= I.L; ++l) {
+        const AdjLevel& L = lv[l];
+        if (!L.qbar) continue;
+        const int n = L.n, pitch = L.pitch;
+        const double h = I.lv[l - 1].h;
+        std::vector<double> qb((size_t)4 * n * n), quads((size_t)4 * pitch * n);
+        cudaMemcpyAsync(qb.data(), L.qbar, sizeof(double) * qb.size(), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(quads.data(), L.d.adr, sizeof(double) * quads.size(), cudaMemcpyDeviceToHost, st);
+        std::vector<double> mb;
+        std::vector<double> mod;
+        if (L.mbar) {
+            mb.resize((size_t)2 * n * n);
+            mod.resize((size_t)2 * pitch * n);
+            cudaMemcpyAsync(mb.data(), L.mbar, sizeof(double) * mb.size(), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(mod.data(), L.d.mod, sizeof(double) * mod.size(), cudaMemcpyDeviceToHost, st);
+        }
+        cudaStreamSynchronize(st);
+        std::vector<double> gphi((size_t)n * n, 0.0);
+        auto G = [&](int i, int j) -> double& { return gphi[(size_t)j * n + i]; };
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                const size_t q = (size_t)j * n + i, pq = (size_t)j * pitch + i;
+                const double px = quads[4 * pq], py = quads[4 * pq + 1];
+                const double sx = (px > 0) - (px < 0), sy = (py > 0) - (py < 0);
+                const double dre = qb[4 * q + 2], dim = qb[4 * q + 3];
+                const double gx = qb[4 * q] + dre * 2 * w * w * px + dim * (-2 * w * sx / h);
+                const double gy = qb[4 * q + 1] + dre * 2 * w * w * py + dim * (-2 * w * sy / h);
+                const double gl = dim * (-w);
+                // px = (E - W)/(2h), py = (N - S)/(2h), lap = (E + W + N + S - 4 c)/h^2
+                const double ax = gx / (2 * h), ay = gy / (2 * h), al = gl / (h * h);
+                auto addE = [&](double v) { if (i < n - 1) G(i + 1, j) += v; else { G(n - 1, j) += 2 * v; G(n - 2, j) -= v; } };
+                auto addW = [&](double v) { if (i > 0) G(i - 1, j) += v; else { G(0, j) += 2 * v; G(1, j) -= v; } };
+                auto addN = [&](double v) { if (j < n - 1) G(i, j + 1) += v; else { G(i, n - 1) += 2 * v; G(i, n - 2) -= v; } };
+                auto addS = [&](double v) { if (j > 0) G(i, j - 1) += v; else { G(i, 0) += 2 * v; G(i, 1) -= v; } };
+                addE(ax + al);
+                addW(-ax + al);
+                addN(ay + al);
+                addS(-ay + al);
+                G(i, j) += -4 * al;
+                if (L.mbar) {
+                    const double a = mb[2 * q], b = mb[2 * q + 1];
+                    const double c = mod[2 * pq], s = mod[2 * pq + 1];
+                    G(i, j) += a * (-w * s) + b * (w * c);   // Re(conj(mbar) i w m)
+                }
+            }
+        const long long f = 1LL << (l - 1);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+                grad_phi_host[(f * (j + 1) - 1) * n1 + (f * (i + 1) - 1)] += G(i, j);
+    }
+}
+
+void Adjoint::ka_mod_demod(int l, const double2* r, double2* b) {
+    // b = conj(m) r
+    AdjLevel& L = lv[l];
+    ka_apply_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 0, r, nullptr, b);
+}
+void Adjoint::ka_mod_update(int l, const double2* u, const double2* a, double2* out) {
+    AdjLevel& L = lv[l];
+    ka_apply_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 1, a, u, out);
+}
+void Adjoint::ka_mod_update_back(int l, const double2* a, const double2* nxb, double2* ab) {
+    AdjLevel& L = lv[l];
+    ka_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 1, a, nxb, ab, L.mbar);
+}
+void Adjoint::ka_mod_demod_back(int l, const double2* r, const double2* bb, double2* rb) {
+    AdjLevel& L = lv[l];
+    ka_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 0, r, bb, rb, L.mbar);
+}
+
+}  // namespace wadr
+
+using namespace wadr;
+
+extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const void* gbar_uK,
+                                 double* grad_phi, double* grad_weights, void* grad_u0, mg_stream stream) {
+    if (!h || !u0 || !g || !gbar_uK || K < 1) { set_error("mg_cycle_backward: bad argument"); return MG_EINVAL; }
+    Handle& H = h->H;
+    if (H.prec != MG_PREC_FP64) { set_error("mg_cycle_backward: the adjoint needs an FP64 handle"); return MG_EUNSUPPORTED; }
+    if (H.p.coarse != MG_COARSE_LU) { set_error("mg_cycle_backward: coarsest level must be the dense LU"); return MG_EUNSUPPORTED; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ni = (int)H.inst.size();
+    auto cp2d = [&](void* dst, size_t dpitch, const void* src, size_t spitch, int n) {
+        return cudaMemcpy2DAsync(dst, dpitch * 16, src, spitch * 16, (size_t)n * 16, n, cudaMemcpyDefault, st);
+    };
+    // ---- checkpoints u_0 .. u_{K-1} (pitched level-1 layout) by the regular forward
+    std::vector<std::vector<double2*>> ck(ni);
+    std::vector<void*> owned;
+    auto dalloc = [&](size_t bytes) -> double2* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        owned.push_back(p);
+        cudaMemsetAsync(p, 0, bytes, st);
+        return (double2*)p;
+    };
+    auto cleanup = [&]() { cudaStreamSynchronize(st); for (void* p : owned) cudaFree(p); };
+    for (int b = 0; b < ni; ++b) {
+        InstHost& I = H.inst[b];
+        LevelHost& l1 = I.lv[0];
+        ck[b].resize(K);
+        for (int k = 0; k < K; ++k) {
+            ck[b][k] = dalloc(sizeof(double2) * l1.slot_stride);
+            if (!ck[b][k]) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return MG_ENOMEM; }
+        }
+        WADR_CHECK(cp2d(ck[b][0], l1.pitch, (const char*)u0 + I.off * 16, l1.n, l1.n));
+        WADR_CHECK(cp2d((char*)l1.vec + (size_t)SG * l1.slot_stride * 16, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n));
+        WADR_CHECK(cudaMemcpyAsync((char*)l1.vec + (size_t)SX2 * l1.slot_stride * 16, ck[b][0], l1.slot_stride * 16,
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+    for (int k = 1; k < K; ++k) {
+        h->eng->cycle(H, false, st);
+        for (int b = 0; b < ni; ++b) {
+            LevelHost& l1 = H.inst[b].lv[0];
+            const char* sd = (const char*)l1.vec + (size_t)SD * l1.slot_stride * 16;
+            WADR_CHECK(cudaMemcpyAsync(ck[b][k], sd, l1.slot_stride * 16, cudaMemcpyDeviceToDevice, st));
+            WADR_CHECK(cudaMemcpyAsync((char*)l1.vec + (size_t)SX2 * l1.slot_stride * 16, sd, l1.slot_stride * 16,
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    // ---- reverse sweep per instance
+    for (int b = 0; b < ni; ++b) {
+        InstHost& I = H.inst[b];
+        LevelHost& l1 = I.lv[0];
+        Adjoint A(H, I, st);
+        int rc = A.init();
+        if (rc) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return rc; }
+        double2* ub = dalloc(sizeof(double2) * l1.slot_stride);
+        double2* ubin = dalloc(sizeof(double2) * l1.slot_stride);
+        double2* gd = dalloc(sizeof(double2) * l1.slot_stride);
+        double2* gbar = dalloc(sizeof(double2) * l1.slot_stride);
+        double2* uout = dalloc(sizeof(double2) * l1.slot_stride);
+        if (!ub || !ubin || !gd || !gbar || !uout) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return MG_ENOMEM; }
+        WADR_CHECK(cp2d(ub, l1.pitch, (const char*)gbar_uK + I.off * 16, l1.n, l1.n));
+        WADR_CHECK(cp2d(gd, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n));
+        for (int k = K - 1; k >= 0; --k) {
+            Adjoint::WaveTape* T = A.wave_forward(1, ck[b][k], gd, uout);
+            WADR_CHECK(cudaMemsetAsync(ubin, 0, sizeof(double2) * l1.slot_stride, st));
+            A.wave_backward(T, ub, ubin, gbar);
+            std::swap(ub, ubin);
+            if (A.err) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return A.err; }
+            WADR_CHECK(cudaGetLastError());
+            A.reset();
+        }
+        if (grad_u0) {
+            // grad_u0 += ub
+            std::vector<double2> hu((size_t)l1.n * l1.n), hg((size_t)l1.n * l1.n);
+            WADR_CHECK(cudaMemcpy2DAsync(hu.data(), (size_t)l1.n * 16, ub, (size_t)l1.pitch * 16, (size_t)l1.n * 16,
+                                         l1.n, cudaMemcpyDeviceToHost, st));
+            WADR_CHECK(cudaMemcpyAsync(hg.data(), (const char*)grad_u0 + I.off * 16, hg.size() * 16, cudaMemcpyDefault, st));
+            WADR_CHECK(cudaStreamSynchronize(st));
+            for (size_t q = 0; q < hu.size(); ++q) { hg[q].x += hu[q].x; hg[q].y += hu[q].y; }
+            WADR_CHECK(cudaMemcpyAsync((char*)grad_u0 + I.off * 16, hg.data(), hg.size() * 16, cudaMemcpyDefault, st));
+        }
+        if (grad_weights) {
+            double* gw = grad_weights + (size_t)b * MG_MAX_LEVELS;
+            gw[0] += A.wj_bar;
+            for (int l = 2; l <= I.L; ++l) gw[l - 1] += A.alpha_bar[l];
+        }
+        if (grad_phi) {
+            std::vector<double> gp((size_t)I.n * I.n);
+            WADR_CHECK(cudaMemcpyAsync(gp.data(), grad_phi + I.off, gp.size() * 8, cudaMemcpyDefault, st));
+            WADR_CHECK(cudaStreamSynchronize(st));
+            chain_to_phi(I, A.lv, st, gp.data());
+            WADR_CHECK(cudaMemcpyAsync(grad_phi + I.off, gp.data(), gp.size() * 8, cudaMemcpyDefault, st));
+        }
+        WADR_CHECK(cudaStreamSynchronize(st));
+    }
+    cleanup();
+    WADR_CHECK(cudaGetLastError());
+    return MG_OK;
+}

@@ -154,3 +154,8 @@ void prof_begin(Handle& H, cudaStream_t st);
 void prof_end(Handle& H, cudaStream_t st, int kind, double bytes, long long pts);
 
 }  // namespace wadr
+
+struct mg_handle {
+    wadr::Handle H;
+    wadr::EngineBase* eng = nullptr;
+};

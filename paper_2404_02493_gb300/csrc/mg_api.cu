@@ -11,10 +11,6 @@
 #include "fgmres.cuh"
 #include "kernels.cuh"
 
-struct mg_handle {
-    wadr::Handle H;
-    wadr::EngineBase* eng = nullptr;
-};
 
 namespace wadr {
 
