@@ -68,6 +68,7 @@ enum { MG_OUTER_STATIONARY = 0, MG_OUTER_IR = 1, MG_OUTER_FGMRES = 2 };
 enum { MG_COARSE_LU = 0, MG_COARSE_CHEB = 1 };
 
 #define MG_MAX_LEVELS 16
+#define MG_TILE_CANDIDATES 4   /* halo-tile shape candidates per ADR GMRES kernel */
 
 /* Schedule constants.  mg_default_params fills the paper's values:
  * Algorithm 1 (1 Jacobi sweep on level 1; 5 Chebyshev steps before and after
@@ -92,6 +93,10 @@ typedef struct mg_params {
     double tol;             /* relative residual ||g - A u|| / ||g|| */
     double shift;           /* shifted Helmholtz: adds -i*shift*k^2 (Section 4.3.2; 0 = off) */
     int use_graph;          /* 1: replay the cycle as a captured CUDA graph */
+    int autotune;           /* 1: time the halo-tile candidates of the ADR GMRES kernels per launch at
+                               setup and keep the fastest (default); 0: default tile shapes */
+    int tile_candidate;     /* -1 (default); 0..MG_TILE_CANDIDATES-1: use that candidate for every ADR
+                               GMRES kernel (overrides autotune; for testing each shape) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */
@@ -192,7 +197,7 @@ int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const 
  * mg_kernel_name gives the kind's name.  mg_step_launches: kernels of one
  * outer step.
  * ---------------------------------------------------------------------- */
-#define MG_KERNEL_KINDS 24
+#define MG_KERNEL_KINDS 21
 int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* launches, int nkinds,
                      mg_stream stream);
 const char* mg_kernel_name(int kind);
@@ -246,6 +251,15 @@ int mg_adr_correction(mg_handle* h, int inst, void* u, const void* g, mg_stream 
 /* x = A_L^{-1} b (which = 0, Helmholtz) or L_L^{-1} b (which = 1, ADR) on
  * the coarsest level, with the dense FP64 LU factors. */
 int mg_coarse_solve(mg_handle* h, int inst, int which, const void* b, void* x, mg_stream stream);
+
+/* Halo-tile shapes used by the ADR GMRES(3) kernels of `level` (2 <= level
+ * < coarsest) in the launch that covers instance `inst`: out[6] = gram pass
+ * tile (x, y fine nodes), pre-smoothing tile (x, y coarse nodes; fine
+ * footprint 2x+1 by 2y+1), post-smoothing tile (x, y fine nodes), as chosen
+ * by the setup-time autotuner (mg_params.autotune) or the defaults.  The
+ * paper has no counterpart (its kernels are library convolutions).
+ * Errors: MG_EINVAL (no such ADR level). */
+int mg_tile_shapes(const mg_handle* h, int inst, int level, int* out);
 
 /* Number of kernel launches of one cycle (counted when the schedule is
  * emitted). */

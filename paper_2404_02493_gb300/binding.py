@@ -22,6 +22,7 @@ MG_OUTER = {"stationary": 0, "ir": 1, "fgmres": 2}
 MG_COARSE_LU, MG_COARSE_CHEB = 0, 1
 MG_OP = {"A": 0, "AH": 1, "L": 2, "LT": 3, "LH": 4}
 MG_MAX_LEVELS = 16
+MG_TILE_CANDIDATES = 4
 
 
 class MgParams(ctypes.Structure):
@@ -31,7 +32,7 @@ class MgParams(ctypes.Structure):
         ("M", ctypes.c_int), ("adr", ctypes.c_int), ("omega_jacobi", ctypes.c_double),
         ("alpha", ctypes.c_double * MG_MAX_LEVELS), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("shift", ctypes.c_double),
-        ("use_graph", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("tile_candidate", ctypes.c_int),
     ]
 
 
@@ -90,6 +91,7 @@ def load():
         "mg_profile_records": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
         "mg_cycle_backward": (ip, [vp, vp, vp, ip, vp, vp, vp, vp, vp]),
+        "mg_tile_shapes": (ip, [vp, ip, ip, ctypes.POINTER(ip)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -106,7 +108,8 @@ def exported_symbols():
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
-            "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward"]
+            "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
+            "mg_tile_shapes"]
 
 
 class MgError(RuntimeError):
@@ -219,6 +222,14 @@ def mg_level_scalars(h, inst, level):
     return {"lam_max": out[0], "alpha": out[1], "omega_j": out[2], "h": out[3]}
 
 
+def mg_tile_shapes(h, inst, level):
+    """Halo tiles of the ADR GMRES kernels of `level`: {'gram': (x, y),
+    'pre': (x, y) coarse nodes, 'post': (x, y)}."""
+    out = (ctypes.c_int * 6)()
+    _check(load().mg_tile_shapes(h, inst, level, out), "mg_tile_shapes")
+    return {"gram": (out[0], out[1]), "pre": (out[2], out[3]), "post": (out[4], out[5])}
+
+
 def mg_apply(h, inst, level, op, x, y, stream=None):
     op = MG_OP[op] if isinstance(op, str) else op
     _check(load().mg_apply(h, inst, level, op, _ptr(x), _ptr(y), _stream(stream)), "mg_apply")
@@ -271,7 +282,7 @@ def mg_abi_sizes():
     return a.value, b.value, c.value
 
 
-MG_KERNEL_KINDS = 24
+MG_KERNEL_KINDS = 21
 
 
 def mg_solve_begin(h, u, g, stream=None):

@@ -15,7 +15,8 @@ LIB = os.path.join(HERE, "libwaveadr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["mg_api.cu", "setup.cu", "engine_f32.cu", "engine_f64.cu", "noalloc.cu", "adjoint.cu"]
-HEADERS = ["common.cuh", "kernels.cuh", "engine.cuh", "handle.h", "setup_kernels.cuh", "fgmres.cuh"]
+HEADERS = ["common.cuh", "kernels.cuh", "engine.cuh", "handle.h", "setup_kernels.cuh", "fgmres.cuh",
+           "gmres_sstep.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 

@@ -93,6 +93,8 @@ struct LevelDesc {
     double wh;              // omega / h
     // the same constants in FP32, so FP32 kernels do no per-point FP64 work
     float fh, fih2, fwh, fshift;
+    double gs;              // ADR levels: power of two s with ||s L||_inf <= 1 (s-step GMRES basis)
+    float fgs;
     int has_shift;
     int bc;
     int inst;               // instance index
@@ -122,12 +124,14 @@ template <> struct LC<float> {
     static __device__ __forceinline__ float ih2(const LevelDesc& d) { return d.fih2; }
     static __device__ __forceinline__ float wh(const LevelDesc& d) { return d.fwh; }
     static __device__ __forceinline__ float shift(const LevelDesc& d) { return d.fshift; }
+    static __device__ __forceinline__ float gs(const LevelDesc& d) { return d.fgs; }
 };
 template <> struct LC<double> {
     static __device__ __forceinline__ double h(const LevelDesc& d) { return d.h; }
     static __device__ __forceinline__ double ih2(const LevelDesc& d) { return d.inv_h2; }
     static __device__ __forceinline__ double wh(const LevelDesc& d) { return d.wh; }
     static __device__ __forceinline__ double shift(const LevelDesc& d) { return d.shift; }
+    static __device__ __forceinline__ double gs(const LevelDesc& d) { return d.gs; }
 };
 template <typename T> __device__ __forceinline__ T* scalp(const LevelDesc& d) { return reinterpret_cast<T*>(d.scal); }
 template <typename T> __device__ __forceinline__ cplx<T>* partp(const LevelDesc& d) {
@@ -142,24 +146,14 @@ constexpr int BX = 32, BY = 8;   // block shape
 // scalar area layout (doubles) of an (instance, level)
 namespace S {
 constexpr int DOT = 0;        // 2*MAXDOT: raw reduced dots of the last reduction
-constexpr int BETA = 16;      // ||r0||
-constexpr int NU2 = 17, NU3 = 18, NU4 = 19;
-constexpr int H = 20;         // 4x3 complex Hessenberg, row-major: 24 doubles
-constexpr int Y = 44;         // 3 complex
-constexpr int CA2 = 50;       // u2 = w1 - c r0                     (1 complex)
-constexpr int CA3 = 52;       // u3 = w2 - c0 r0 - c1 u2            (2 complex)
-constexpr int CB3 = 56;       // u4 = w3 - c0 r0 - c1 u2 - c2 u3    (3 complex)
-constexpr int CUPD = 62;      // x += c0 r0 + c1 u2 + c2 u3         (3 complex)
-constexpr int CRES = 68;      // r = c0 r0 + c1 u2 + c2 u3 + c3 w3  (4 complex)
-constexpr int M = 76;         // Krylov dimension used
-constexpr int WN1 = 77, WN2 = 78, WN3 = 79;  // ||L v_j|| for the breakdown test
+constexpr int GC = 44;        // s-step GMRES(3) coefficients c0..c2 (3 complex)
+constexpr int M = 76;         // Krylov dimension used by the last GMRES(3) sweep
 constexpr int NORM = 80;      // generic norm^2 result
 constexpr int OMEGA_J = 82;   // Jacobi weight (level 1)
 constexpr int CHEB_N = 83;    // number of Chebyshev steps stored
 constexpr int CHEB_C1 = 84;   // d_m = c1[m] d_{m-1} + c2[m] s_m   (<= 16 steps)
 constexpr int CHEB_C2 = 100;
 constexpr int SCALE = 116;    // generic scale factor (outer loop)
-constexpr int SC2 = 117, SC3 = 118, SC4 = 119;  // GMRES vector pre-scales 1/|w_j|
 constexpr int SIZE = 128;
 }  // namespace S
 

@@ -10,11 +10,13 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "handle.h"
 #include "fgmres.cuh"
 #include "kernels.cuh"
+#include "gmres_sstep.cuh"
 #include "setup_kernels.cuh"
 
 namespace wadr {
@@ -79,11 +81,150 @@ struct Engine : EngineBase {
         }
     }
 
-    void gmres(Handle& H, const SegTable& t, int sr0, cudaStream_t st) {
-        LAUNCH(KK_GM_A1, t, 2 * C + Q, k_gm_a1<T>, sr0);
-        LAUNCH(KK_GM_A2, t, 4 * C + Q, (k_gm_a23<T, 2>), sr0);
-        LAUNCH(KK_GM_A3, t, 5 * C + Q, (k_gm_a23<T, 3>), sr0);
-        LAUNCH(KK_GM_B3, t, 4 * C, k_gm_b3<T>, sr0);
+    // ------------------------------------------------------------ s-step GMRES(3)
+    // Per (kernel, candidate): dynamic shared memory opt-in and the resident
+    // blocks per SM, so that a launch has at most one wave of persistent
+    // blocks per segment (blocks loop over tiles).
+    static int& gs_cap_slot(int which, int cand) {
+        static int cap[3][GS_NCAND] = {};
+        return cap[which][cand];
+    }
+    template <class K>
+    static int gs_prepare(K kern, int smem, int which, int cand) {
+        int& cap = gs_cap_slot(which, cand);
+        if (cap == 0) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            int nb = 0, dev = 0, nsm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem);
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cap = std::max(1, nb) * std::max(1, nsm);
+        }
+        return cap;
+    }
+    template <class F>
+    static void gs_dispatch(int cand, F&& f) {
+        switch (cand) {
+        case 0: f(std::integral_constant<int, 0>{}); break;
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        default: f(std::integral_constant<int, 3>{}); break;
+        }
+    }
+    static TileChoice tiles_of(Handle& H, const std::vector<int>& ds) {
+        TileChoice tc;
+        if (H.p.tile_candidate >= 0) {
+            tc.gram = tc.pre = tc.post = H.p.tile_candidate;
+        } else {
+            auto it = H.tiles.find(desc_key(ds));
+            if (it != H.tiles.end()) tc = it->second;
+        }
+        if (tc.gram < 0) tc.gram = GS_DEFAULT_GRAM;
+        if (tc.pre < 0) tc.pre = GS_DEFAULT_PRE;
+        if (tc.post < 0) tc.post = GS_DEFAULT_POST;
+        return tc;
+    }
+
+    // Gram pass of r0 in slot sr0 (reads r0 and the coefficients once).
+    void gs_gram(Handle& H, const std::vector<int>& ds, int cand, int sr0, cudaStream_t st) {
+        gs_dispatch(cand, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            constexpr GsShape sh = gs_gram_shape(I);
+            auto kern = k_gs_gram<T, sh.x, sh.y>;
+            const int smem = gs_gram_smem<T>(I);
+            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 0, I));
+            go(H, st, KK_GS_GRAM, (C + Q) * (double)t.pts, [&] {
+                kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sr0);
+            }, t.pts);
+        });
+    }
+    // Pre-smoothing update from zero, fused with the restriction of the
+    // residual to slot SAB of the next level; x to SAX.
+    void gs_pre(Handle& H, const std::vector<int>& ds, int cand, cudaStream_t st) {
+        gs_dispatch(cand, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            constexpr GsShape sh = gs_pre_shape(I);
+            auto kern = k_gs_pre<T, sh.x, sh.y>;
+            const int smem = gs_pre_smem<T>(I);
+            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, true, gs_prepare(kern, smem, 1, I));
+            go(H, st, KK_GS_PRE, (2 * C + Q + C / 4) * (double)t.pts, [&] {
+                kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, SAB, SAX, SAB);
+            }, t.pts);
+        });
+    }
+    // Post-smoothing update x = x' + z (flags: 1 x' = 0, 2 modulate into u).
+    void gs_post(Handle& H, const std::vector<int>& ds, int cand, int sr0, int sxo, int flags, cudaStream_t st) {
+        gs_dispatch(cand, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            constexpr GsShape sh = gs_post_shape(I);
+            auto kern = k_gs_post<T, sh.x, sh.y>;
+            const int smem = gs_post_smem<T>(I);
+            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 2, I));
+            const double bpp = (flags & 2) ? 5 * C + Q : ((flags & 1) ? 2 * C + Q : 3 * C + Q);
+            go(H, st, KK_GS_POST, bpp * (double)t.pts, [&] {
+                kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sr0, sxo, flags);
+            }, t.pts);
+        });
+    }
+
+    // Autotuner: for every ADR launch of the cycle (level l over the
+    // instances that have l < L) time each halo-tile candidate of the three
+    // GMRES kernels on the handle's workspace and keep the fastest.  The
+    // kernels only read and write workspace here (x to SAX, the restricted
+    // residual to the next level's SAB, scalars), all of which every cycle
+    // rewrites before use.
+    int autotune(Handle& H, cudaStream_t st) override {
+        for (int w = 0; w < 3; ++w)
+            for (int c = 0; c < GS_NCAND; ++c) {
+                gs_dispatch(c, [&](auto ic) {
+                    constexpr int I = decltype(ic)::value;
+                    if (w == 0) gs_prepare(k_gs_gram<T, gs_gram_shape(I).x, gs_gram_shape(I).y>, gs_gram_smem<T>(I), 0, I);
+                    if (w == 1) gs_prepare(k_gs_pre<T, gs_pre_shape(I).x, gs_pre_shape(I).y>, gs_pre_smem<T>(I), 1, I);
+                    if (w == 2) gs_prepare(k_gs_post<T, gs_post_shape(I).x, gs_post_shape(I).y>, gs_post_smem<T>(I), 2, I);
+                });
+            }
+        if (!H.p.adr || H.p.M <= 0 || !H.p.autotune || H.p.tile_candidate >= 0) return MG_OK;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const int saved = H.launches_cycle;
+        for (int l = 2; l <= H.Lmax; ++l) {
+            std::vector<int> rest;
+            for (size_t b = 0; b < H.inst.size(); ++b)
+                if (H.inst[b].L > l) rest.push_back((int)b);
+            if (rest.empty()) continue;
+            const std::vector<int> ds = descs(H, l, rest);
+            TileChoice tc;
+            for (int w = 0; w < 3; ++w) {
+                float best = 1e30f;
+                int arg = -1;
+                for (int c = 0; c < GS_NCAND; ++c) {
+                    auto run = [&] {
+                        if (w == 0) gs_gram(H, ds, c, SAB, st);
+                        else if (w == 1) gs_pre(H, ds, c, st);
+                        else gs_post(H, ds, c, SV1, SD, 0, st);
+                    };
+                    run();   // warm-up (also builds the segment table)
+                    float tmin = 1e30f;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        cudaEventRecord(e0, st);
+                        run();
+                        cudaEventRecord(e1, st);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tmin = std::min(tmin, ms);
+                    }
+                    if (tmin < best) { best = tmin; arg = c; }
+                }
+                (w == 0 ? tc.gram : w == 1 ? tc.pre : tc.post) = arg;
+            }
+            H.tiles[desc_key(ds)] = tc;
+        }
+        H.launches_cycle = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ECUDA;
     }
 
     void coarse_solve(Handle& H, const std::vector<int>& I, int level, int which, cudaStream_t st) {
@@ -102,13 +243,15 @@ struct Engine : EngineBase {
         for (int b : I) (H.inst[b].L == l ? co : rest).push_back(b);
         if (!co.empty()) coarse_solve(H, co, l, 1, st);
         if (rest.empty()) return;
-        const SegTable& t = H.seg(descs(H, l, rest), false, kPts);
-        gmres(H, t, SAB, st);   // pre-smoothing from x = 0: r0 = b
-        LAUNCH(KK_RESTRICT_GMRES, t, 5 * C + C / 4, (k_restrict<T, MODE_GMRES>), SAX, SAB, SAB, 0);
+        const std::vector<int> ds = descs(H, l, rest);
+        const SegTable& t = H.seg(ds, false, kPts);
+        const TileChoice tc = tiles_of(H, ds);
+        gs_gram(H, ds, tc.gram, SAB, st);   // pre-smoothing from x = 0: r0 = b
+        gs_pre(H, ds, tc.pre, st);          // x to SAX, restricted residual to SAB of l+1
         adrv(H, l + 1, rest, false, st);
         LAUNCH(KK_PROLONG_ADR, t, 4 * C + C / 4 + Q, (k_prolong<T, PMODE_ADR>), SAX, SAX, SAB, SV1, SD, 0);
-        gmres(H, t, SV1, st);   // post-smoothing from x' (r0 = b - L x')
-        LAUNCH(KK_GM_UPDATE, t, modulate ? 7 * C : 5 * C, k_gm_update<T>, SV1, SD, modulate ? 1 : 0);
+        gs_gram(H, ds, tc.gram, SV1, st);   // post-smoothing from x' (r0 = b - L x')
+        gs_post(H, ds, tc.post, SV1, SD, modulate ? 2 : 0, st);
     }
 
     // Algorithm 1's ADR correction steps at level 2 (M times).
@@ -281,20 +424,22 @@ struct Engine : EngineBase {
             }
             return cur;
         }
-        case OP_GMRES:
+        case OP_GMRES: {
+            const std::vector<int> ds = descs(H, level, I);
+            const TileChoice tc = tiles_of(H, ds);
             if (a0) {
                 // r0 = b - L x  (x in SAX, b in SAB)
-                k_apply<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, 2, SAX, SWB);
-                k_sub<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAB, SWB, SV1);
-                gmres(H, t, SV1, st);
+                k_apply<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, 2, SAX, STMP);
+                k_sub<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAB, STMP, SV1);
                 k_copy<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAX, SD);
-                k_gm_update<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SV1, SD, 0);
+                gs_gram(H, ds, tc.gram, SV1, st);
+                gs_post(H, ds, tc.post, SV1, SD, 0, st);
             } else {
-                gmres(H, t, SAB, st);
-                k_zero<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SD);
-                k_gm_update<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAB, SD, 0);
+                gs_gram(H, ds, tc.gram, SAB, st);
+                gs_post(H, ds, tc.post, SAB, SD, 1, st);
             }
             return SAX;
+        }
         case OP_ADRV:
             adrv(H, level, I, false, st);
             return SAX;

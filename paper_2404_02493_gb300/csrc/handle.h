@@ -57,12 +57,18 @@ struct SegTable {
 
 // kernel kinds for the event profiler (names in kernel_kind_name)
 enum KernelKind : int {
-    KK_RESTRICT_JAC0 = 0, KK_RESTRICT_HELM, KK_RESTRICT_GMRES, KK_PROLONG_JAC, KK_PROLONG_ADD, KK_PROLONG_ADR,
-    KK_CHEB, KK_RESDEMOD, KK_GM_A1, KK_GM_A2, KK_GM_A3, KK_GM_B3, KK_GM_UPDATE, KK_COARSE, KK_OUTER_RESIDUAL,
-    KK_OUTER_SCALE, KK_OUTER_UPDATE, KK_JACOBI, KK_FG_START, KK_FG_PREP, KK_FG_MATVEC, KK_FG_DOTS, KK_FG_ORTH,
-    KK_FG_UPDATE, KK_COUNT
+    KK_RESTRICT_JAC0 = 0, KK_RESTRICT_HELM, KK_GS_PRE, KK_PROLONG_JAC, KK_PROLONG_ADD, KK_PROLONG_ADR,
+    KK_CHEB, KK_RESDEMOD, KK_GS_GRAM, KK_GS_POST, KK_COARSE, KK_OUTER_RESIDUAL, KK_OUTER_SCALE, KK_OUTER_UPDATE,
+    KK_JACOBI, KK_FG_START, KK_FG_PREP, KK_FG_MATVEC, KK_FG_DOTS, KK_FG_ORTH, KK_FG_UPDATE, KK_COUNT
 };
 const char* kernel_kind_name(int k);
+
+// halo-tile candidates (index into the gs_*_shape tables) of one ADR launch
+struct TileChoice {
+    int gram = -1, pre = -1, post = -1;   // -1: default shape
+};
+
+std::string desc_key(const std::vector<int>& descs);
 
 struct Handle {
     mg_params p{};
@@ -78,6 +84,7 @@ struct Handle {
     double2* part = nullptr;        // [ndesc + ninst][MAXB][MAXDOT]
     unsigned* counter = nullptr;    // [ndesc + ninst][NCOUNTERS]
     std::map<std::string, SegTable> segs;
+    std::map<std::string, TileChoice> tiles;  // per ADR launch (desc_key), from the autotuner
     std::vector<void*> allocs;      // everything cudaMalloc'ed
     long long total_elems = 0;      // sum of n^2 over instances
     // graphs
@@ -107,6 +114,8 @@ struct Handle {
     void* alloc(size_t bytes);
     const SegTable& seg(const std::vector<int>& descs, bool outer, int pts_per_block);
     const SegTable& seg_rows(const std::vector<int>& descs, int rows_per_block);
+    // one block per tile of tx x ty nodes (of the next level when `coarse`), at most cap per segment
+    const SegTable& seg_tiles(const std::vector<int>& descs, int tx, int ty, bool coarse, int cap);
 };
 
 // level operations of EngineBase::level_op
@@ -127,6 +136,8 @@ struct EngineBase {
     virtual void fg_finish(Handle& H, cudaStream_t st) = 0;
     // level operations (single instance) used by the parity tests
     virtual int level_op(Handle& H, int inst, int level, int what, int a0, int a1, cudaStream_t st) = 0;
+    // halo-tile autotuner of the ADR launches (fills Handle::tiles)
+    virtual int autotune(Handle& H, cudaStream_t st) = 0;
 };
 
 EngineBase* make_engine_f32();
@@ -137,6 +148,8 @@ void setup_inject(const double* k_fine, const double* phi_fine, int n1, double o
                   double* k64, double* phi64, double* sig64, int n, int pitch, cudaStream_t st);
 double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
                         double* dscratch, cudaStream_t st);
+double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                       double omega, int bc, double shift, double* dscratch, cudaStream_t st);
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
                          double omega, int bc, double shift, int which, double2* inv, cudaStream_t st);
 

@@ -18,11 +18,8 @@ enum Slot : int {
     SAX = 4,  // ADR iterate
     SAB = 5,  // ADR right-hand side
     SV1 = 6,  // GMRES r0 of the post-smoother
-    SU2 = 7,  // GMRES unnormalised Krylov vectors
-    SU3 = 8,
-    SWA = 9,  // GMRES L-images (ping-pong)
-    SWB = 10,
-    NSLOT = 11,
+    STMP = 7, // scratch of the level operations
+    NSLOT = 8,
     NSLOT_L1 = 4
 };
 
@@ -217,6 +214,54 @@ __device__ __forceinline__ void load_region(cplx<T>* sm, const cplx<T>* __restri
     }
 }
 
+// ----------------------------------------------------------- asynchronous tiles
+// cp.async copies global -> shared memory (no register staging); an
+// out-of-grid element is zero-filled (source size 0, nothing is read).  A
+// tile's copies are issued together and waited for as one commit group, so
+// the next tile of a block can stream in while the current one is computed.
+template <int B>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, bool ok) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    if (B == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 8 : 0));
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename E>
+__device__ __forceinline__ void cp_async_elem(E* sdst, const E* gsrc, bool ok) {
+    static_assert(sizeof(E) == 8 || sizeof(E) == 16 || sizeof(E) == 32, "element size");
+    if constexpr (sizeof(E) == 8) {
+        cp_async<8>(sdst, gsrc, ok);
+    } else if constexpr (sizeof(E) == 16) {
+        cp_async<16>(sdst, gsrc, ok);
+    } else {
+        cp_async<16>(sdst, gsrc, ok);
+        cp_async<16>(reinterpret_cast<char*>(sdst) + 16, reinterpret_cast<const char*>(gsrc) + 16, ok);
+    }
+}
+
+// Issue the copies of rows [y0, y0+H) x cols [x0, x0+W) of an n x n grid
+// array (row pitch `pitch`) into sm (row stride W).
+template <typename E, int W, int H>
+__device__ __forceinline__ void async_region(E* sm, const E* __restrict__ g, int n, int pitch, int x0, int y0) {
+    constexpr int NE = W * H;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+#pragma unroll
+    for (int k = 0; k < (NE + NT - 1) / NT; ++k) {
+        const int e = tid + k * NT;
+        if (NE % NT == 0 || e < NE) {
+            const int r = e / W, cc = e - r * W;
+            const int gi = x0 + cc, gj = y0 + r;
+            const bool ok = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n;
+            cp_async_elem<E>(sm + e, ok ? g + (long long)gj * pitch + gi : g, ok);
+        }
+    }
+}
+
 // ----------------------------------------------------------- Chebyshev step
 // One step of the Chebyshev semi-iteration on A^*A x = A^*g (eq. cheb),
 // three-term form: s = A^*(g - A x);  d = c1[m] d + c2[m] s;  x += d.
@@ -295,9 +340,8 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
 // MODE_HELM:  r = g - A u          (uzero flag: r = g)
 // MODE_JAC0:  u1 = w D^{-1} g (written to slot su), r = g - A u1
 // MODE_ADR:   r = b - L x          (ADR operator, slots sx/sb)
-// MODE_GMRES: x = CUPD.(r0,u2,u3) written to SAX, r = CRES.(r0,u2,u3,w3)
 // The coarse result goes to slot `sc` of the next level.
-enum RMode : int { MODE_HELM = 0, MODE_JAC0 = 1, MODE_ADR = 2, MODE_GMRES = 3 };
+enum RMode : int { MODE_HELM = 0, MODE_JAC0 = 1, MODE_ADR = 2 };
 constexpr int RCX = 32, RCY = 8;
 constexpr int RFW = 2 * RCX + 1, RFH = 2 * RCY + 1;   // footprint
 constexpr int RHW = RFW + 2, RHH = RFH + 2;            // footprint + ring
@@ -319,16 +363,6 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
     cplx<T>* xs = slot<T>(d, sx);
     const cplx<T>* bs = slot<T>(d, sb);
     cplx<T>* out = slot<T>(dc, sc);
-    const cplx<T>* r0 = slot<T>(d, sb);     // MODE_GMRES: r0 slot passed as sb
-    const cplx<T>* u2 = slot<T>(d, SU2);
-    const cplx<T>* u3 = slot<T>(d, SU3);
-    const cplx<T>* w3 = slot<T>(d, SWA);
-    cplx<T> cu[3], cr[4];
-    if (MODE == MODE_GMRES) {
-        const T* sc = scalp<T>(d);
-        for (int q = 0; q < 3; ++q) cu[q] = mk<T>(sc[S::CUPD + 2 * q], sc[S::CUPD + 2 * q + 1]);
-        for (int q = 0; q < 4; ++q) cr[q] = mk<T>(sc[S::CRES + 2 * q], sc[S::CRES + 2 * q + 1]);
-    }
     const T wj = (MODE == MODE_JAC0) ? scalp<T>(d)[S::OMEGA_J] : T(0);
     const T h2 = LC<T>::h(d) * LC<T>::h(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
@@ -365,19 +399,7 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
             cplx<T> v = zero2<T>();
             if (gi < n && gj < n) {
                 const long long p = (long long)gj * pitch + gi;
-                if (MODE == MODE_GMRES) {
-                    cplx<T> a = __ldg(r0 + p), b2 = __ldg(u2 + p), b3 = __ldg(u3 + p);
-                    v = cmul<T>(cr[0], a);
-                    v = cfma<T>(cr[1], b2, v);
-                    v = cfma<T>(cr[2], b3, v);
-                    v = cfma<T>(cr[3], __ldg(w3 + p), v);
-                    if (gi < ox1 && gj < oy1) {
-                        cplx<T> xv = cmul<T>(cu[0], a);
-                        xv = cfma<T>(cu[1], b2, xv);
-                        xv = cfma<T>(cu[2], b3, xv);
-                        xs[p] = xv;   // sx = SAX
-                    }
-                } else {
+                {
                     v = __ldg(bs + p);
                     if (!(uzero && MODE != MODE_JAC0)) {
                         const int b = (r + 1) * RHW + cc + 1;
@@ -528,332 +550,10 @@ __global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D
     }
 }
 
-// ----------------------------------------------------------- GMRES(3)
-// GMRES(3) smoother of the ADR V-cycle (Section 3.2.2), Arnoldi with
-// classical Gram-Schmidt and lagged normalisation:
-//   A1: w1 = L r0;                          dots |r0|^2, <r0,w1>, |w1|^2
-//   A2: u2 = s2 (w1 - c r0) (on the fly);   w2 = L u2; dots |u2|^2, <r0,w2>, <u2,w2>, |w2|^2
-//   A3: u3 = s3 (w2 - c0 r0 - c1 u2);       w3 = L u3; dots |u3|^2, <r0,w3>, <u2,w3>, <u3,w3>, |w3|^2
-//   B3: u4 = s4 (w3 - c0 r0 - c1 u2 - c2 u3);  dot |u4|^2;  then the 4x3 least squares
-// with v1 = r0/beta, v2 = u2/|u2|, v3 = u3/|u3|, v4 = u4/|u4|.  The scales
-// s_{j+1} = 1/|w_j| (known from the previous reduction) keep every stored
-// vector O(1): without them |w3| grows like ||L||^3 |r0| and its square
-// leaves the FP32 range on fine ADR levels (||L|| ~ 4/h^2).
-//
-// All scalar work (reductions, Hessenberg entries, the small least squares)
-// runs in the working precision T: on this GPU a dependent FP64 operation
-// costs ~14x an FP32 one and an FP64 divide or square root 200-350 ns, which
-// would dominate the small launches of the coarse ADR levels.
+// ----------------------------------------------------------- scalar helpers
 template <typename T> __device__ __forceinline__ cplx<T> sload2(const T* s, int off) { return mk<T>(s[off], s[off + 1]); }
 template <typename T> __device__ __forceinline__ void sstore2(T* s, int off, cplx<T> v) { s[off] = v.x; s[off + 1] = v.y; }
-template <typename T> __device__ __forceinline__ T sinv(T v) { return v > T(0) ? T(1) / v : T(0); }
 template <typename T> __device__ __forceinline__ T cabs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
-template <typename T> __device__ __forceinline__ cplx<T> cdivT(cplx<T> a, cplx<T> b) {
-    const T den = b.x * b.x + b.y * b.y;
-    return mk<T>((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT) k_gm_a1(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                              int nseg, int sr0) {
-    __shared__ LevelDesc d;
-    __shared__ cplx<T> sh[8 * 3];
-    __shared__ int flag;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
-    const cplx<T>* r0 = slot<T>(d, sr0);
-    cplx<T>* w = slot<T>(d, SWA);
-    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
-    cplx<T> ac[3] = {zero2<T>(), zero2<T>(), zero2<T>()};
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
-        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
-        const long long p = (long long)j * d.pitch + i;
-        const cplx<T> z = zero2<T>();
-        const cplx<T> a = __ldg(r0 + p);
-        const cplx<T> wv = adr_pt<T>(load_adr<T>(d, p), ih2, wh, a, i > 0 ? __ldg(r0 + p - 1) : z,
-                                     i < d.n - 1 ? __ldg(r0 + p + 1) : z, j > 0 ? __ldg(r0 + p - d.pitch) : z,
-                                     j < d.n - 1 ? __ldg(r0 + p + d.pitch) : z);
-        w[p] = wv;
-        ac[0].x += cabs2<T>(a);
-        ac[1] = cadd<T>(ac[1], cmulc<T>(a, wv));
-        ac[2].x += cabs2<T>(wv);
-    }
-    block_sum<cplx<T>, 3>(ac, sh);
-    if (publish_partials<cplx<T>, 3>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
-        cplx<T> tot[3];
-        finish_partials<cplx<T>, 3>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            T* s = scalp<T>(d);
-            const T beta = sqrt(tot[0].x);
-            const T ib2 = sinv<T>(tot[0].x);
-            s[S::BETA] = beta;
-            const cplx<T> h11 = cscale<T>(tot[1], ib2);
-            for (int q = 0; q < 24; ++q) s[S::H + q] = T(0);
-            sstore2<T>(s, S::H + 0, h11);
-            const T nw1 = sqrt(tot[2].x);
-            s[S::WN1] = nw1 * sinv<T>(beta);
-            sstore2<T>(s, S::CA2, h11);
-            s[S::SC2] = sinv<T>(nw1);   // 1/|w1|
-        }
-    }
-}
-
-// region-based stencil of the on-the-fly combination
-template <typename T, int STEP>
-__global__ void __launch_bounds__(NT) k_gm_a23(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                               int nseg, int sr0) {
-    constexpr int NV = STEP == 2 ? 4 : 5;
-    __shared__ LevelDesc d;
-    __shared__ cplx<T> sh[8 * 5];
-    __shared__ int flag;
-    __shared__ cplx<T> Ur[(BY + 2) * (BX + 2)];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + BX - 1) / BX, nty = (n + BY - 1) / BY;
-    const cplx<T>* r0 = slot<T>(d, sr0);
-    const cplx<T>* win = slot<T>(d, STEP == 2 ? SWA : SWB);
-    const cplx<T>* u2 = slot<T>(d, SU2);
-    cplx<T>* uout = slot<T>(d, STEP == 2 ? SU2 : SU3);
-    cplx<T>* wout = slot<T>(d, STEP == 2 ? SWB : SWA);
-    const T* sc = scalp<T>(d);
-    cplx<T> ca, cb = zero2<T>();
-    if (STEP == 2) {
-        ca = sload2<T>(sc, S::CA2);
-    } else {
-        ca = sload2<T>(sc, S::CA3);
-        cb = sload2<T>(sc, S::CA3 + 2);
-    }
-    const T scl = sc[STEP == 2 ? S::SC2 : S::SC3];
-    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
-    cplx<T> ac[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) ac[k] = zero2<T>();
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
-        const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
-        __syncthreads();
-        for (int e = tid; e < (BX + 2) * (BY + 2); e += NT) {
-            const int r = e / (BX + 2), cc = e - r * (BX + 2);
-            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
-            cplx<T> v = zero2<T>();
-            if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
-                const long long p = (long long)gj * pitch + gi;
-                v = csub<T>(__ldg(win + p), cmul<T>(ca, __ldg(r0 + p)));
-                if (STEP == 3) v = csub<T>(v, cmul<T>(cb, __ldg(u2 + p)));
-                v = cscale<T>(v, scl);
-            }
-            Ur[e] = v;
-        }
-        __syncthreads();
-        const int gi = x0 + threadIdx.x, gj = y0 + threadIdx.y;
-        if (gi < n && gj < n) {
-            const long long p = (long long)gj * pitch + gi;
-            const int b = (threadIdx.y + 1) * (BX + 2) + threadIdx.x + 1;
-            const cplx<T> uc = Ur[b];
-            cplx<T> wv = adr_pt<T>(load_adr<T>(d, p), ih2, wh, uc, Ur[b - 1], Ur[b + 1], Ur[b - (BX + 2)],
-                                   Ur[b + (BX + 2)]);
-            uout[p] = uc;
-            wout[p] = wv;
-            const cplx<T> R0 = __ldg(r0 + p);
-            ac[0].x += cabs2<T>(uc);
-            ac[1] = cadd<T>(ac[1], cmulc<T>(R0, wv));
-            if (STEP == 2) {
-                ac[2] = cadd<T>(ac[2], cmulc<T>(uc, wv));
-                ac[3].x += cabs2<T>(wv);
-            } else {
-                ac[2] = cadd<T>(ac[2], cmulc<T>(__ldg(u2 + p), wv));
-                ac[3] = cadd<T>(ac[3], cmulc<T>(uc, wv));
-                ac[4].x += cabs2<T>(wv);
-            }
-        }
-    }
-    block_sum<cplx<T>, NV>(ac, sh);
-    if (publish_partials<cplx<T>, NV>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
-        cplx<T> tot[NV];
-        finish_partials<cplx<T>, NV>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
-        if (tid == 0) {
-            T* s = scalp<T>(d);
-            const T beta = s[S::BETA];
-            if (STEP == 2) {
-                const T nu2 = sqrt(tot[0].x);
-                s[S::NU2] = nu2;
-                const T in2 = sinv<T>(nu2);
-                // h21 = nu2/(s2 beta), h12 = <r0,w2>/(beta nu2), h22 = <u2,w2>/nu2^2
-                sstore2<T>(s, S::H + 2 * (1 * 3 + 0), mk<T>(nu2 * sinv<T>(s[S::SC2] * beta), T(0)));
-                const cplx<T> h12 = cscale<T>(tot[1], sinv<T>(beta) * in2);
-                const cplx<T> h22 = cscale<T>(tot[2], in2 * in2);
-                sstore2<T>(s, S::H + 2 * (0 * 3 + 1), h12);
-                sstore2<T>(s, S::H + 2 * (1 * 3 + 1), h22);
-                const T nw2 = sqrt(tot[3].x);
-                s[S::WN2] = nw2 * in2;
-                sstore2<T>(s, S::CA3, cscale<T>(h12, nu2 * sinv<T>(beta)));
-                sstore2<T>(s, S::CA3 + 2, h22);
-                s[S::SC3] = sinv<T>(nw2);   // 1/|w2|
-            } else {
-                const T nu2 = s[S::NU2];
-                const T nu3 = sqrt(tot[0].x);
-                s[S::NU3] = nu3;
-                const T in3 = sinv<T>(nu3);
-                sstore2<T>(s, S::H + 2 * (2 * 3 + 1), mk<T>(nu3 * sinv<T>(s[S::SC3] * nu2), T(0)));
-                const cplx<T> h13 = cscale<T>(tot[1], sinv<T>(beta) * in3);
-                const cplx<T> h23 = cscale<T>(tot[2], sinv<T>(nu2) * in3);
-                const cplx<T> h33 = cscale<T>(tot[3], in3 * in3);
-                sstore2<T>(s, S::H + 2 * (0 * 3 + 2), h13);
-                sstore2<T>(s, S::H + 2 * (1 * 3 + 2), h23);
-                sstore2<T>(s, S::H + 2 * (2 * 3 + 2), h33);
-                const T nw3 = sqrt(tot[4].x);
-                s[S::WN3] = nw3 * in3;
-                s[S::SC4] = sinv<T>(nw3);   // 1/|w3|
-                sstore2<T>(s, S::CB3 + 0, cscale<T>(h13, nu3 * sinv<T>(beta)));
-                sstore2<T>(s, S::CB3 + 2, cscale<T>(h23, nu3 * sinv<T>(nu2)));
-                sstore2<T>(s, S::CB3 + 4, h33);
-            }
-        }
-    }
-}
-
-// Small dense least squares min || beta e1 - H y ||, H (m+1) x m upper
-// Hessenberg (row-major 4 x 3), by complex Givens rotations; also returns the
-// residual coefficients c = beta e1 - H y.
-template <typename T>
-__device__ inline void hess_lsq(const T* Hm, T beta, int m, cplx<T>* y, cplx<T>* cres) {
-    cplx<T> R[4][3], g[4];
-    for (int r = 0; r < 4; ++r)
-        for (int q = 0; q < 3; ++q) R[r][q] = mk<T>(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]);
-    for (int r = 0; r < 4; ++r) g[r] = zero2<T>();
-    g[0].x = beta;
-    cplx<T> cs[3], sn[3];
-    for (int j = 0; j < m; ++j) {
-        for (int i = 0; i < j; ++i) {
-            cplx<T> a = R[i][j], b = R[i + 1][j];
-            cplx<T> t = cadd<T>(cmulc<T>(cs[i], a), cmulc<T>(sn[i], b));
-            R[i + 1][j] = csub<T>(cmul<T>(cs[i], b), cmul<T>(sn[i], a));
-            R[i][j] = t;
-        }
-        cplx<T> a = R[j][j], b = R[j + 1][j];
-        T den = sqrt(cabs2<T>(a) + cabs2<T>(b));
-        if (den > T(0)) {
-            const T id = T(1) / den;
-            cs[j] = cscale<T>(a, id);
-            sn[j] = cscale<T>(b, id);
-        } else {
-            cs[j] = mk<T>(T(1), T(0));
-            sn[j] = zero2<T>();
-        }
-        R[j][j] = mk<T>(den, T(0));
-        R[j + 1][j] = zero2<T>();
-        cplx<T> gj = g[j];
-        g[j + 1] = cscale<T>(cmul<T>(sn[j], gj), T(-1));
-        g[j] = cmulc<T>(cs[j], gj);
-    }
-    for (int q = 0; q < 3; ++q) y[q] = zero2<T>();
-    for (int j = m - 1; j >= 0; --j) {
-        cplx<T> acc = g[j];
-        for (int q = j + 1; q < m; ++q) acc = csub<T>(acc, cmul<T>(R[j][q], y[q]));
-        y[j] = (cabs2<T>(R[j][j]) > T(0)) ? cdivT<T>(acc, R[j][j]) : zero2<T>();
-    }
-    // c = beta e1 - H y with the original H
-    for (int r = 0; r < 4; ++r) {
-        cplx<T> acc = mk<T>(r == 0 ? beta : T(0), T(0));
-        for (int q = 0; q < m; ++q) acc = csub<T>(acc, cmul<T>(mk<T>(Hm[2 * (r * 3 + q)], Hm[2 * (r * 3 + q) + 1]), y[q]));
-        cres[r] = (r <= m) ? acc : zero2<T>();
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT) k_gm_b3(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                              int nseg, int sr0) {
-    __shared__ LevelDesc d;
-    __shared__ cplx<T> sh[8];
-    __shared__ int flag;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
-    const cplx<T>* r0 = slot<T>(d, sr0);
-    const cplx<T>* u2 = slot<T>(d, SU2);
-    const cplx<T>* u3 = slot<T>(d, SU3);
-    const cplx<T>* w3 = slot<T>(d, SWA);
-    const T* sc = scalp<T>(d);
-    const cplx<T> c0 = sload2<T>(sc, S::CB3), c1 = sload2<T>(sc, S::CB3 + 2), c2 = sload2<T>(sc, S::CB3 + 4);
-    const T s4 = sc[S::SC4];
-    cplx<T> ac[1] = {zero2<T>()};
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
-        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
-        const long long p = (long long)j * d.pitch + i;
-        cplx<T> v = __ldg(w3 + p);
-        v = csub<T>(v, cmul<T>(c0, __ldg(r0 + p)));
-        v = csub<T>(v, cmul<T>(c1, __ldg(u2 + p)));
-        v = csub<T>(v, cmul<T>(c2, __ldg(u3 + p)));
-        v = cscale<T>(v, s4);
-        ac[0].x += cabs2<T>(v);
-    }
-    block_sum<cplx<T>, 1>(ac, sh);
-    if (publish_partials<cplx<T>, 1>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
-        cplx<T> tot[1];
-        finish_partials<cplx<T>, 1>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            T* s = scalp<T>(d);
-            const T beta = s[S::BETA], nu2 = s[S::NU2], nu3 = s[S::NU3];
-            const T nu4 = sqrt(tot[0].x);
-            s[S::NU4] = nu4;
-            sstore2<T>(s, S::H + 2 * (3 * 3 + 2), mk<T>(nu4 * sinv<T>(s[S::SC4] * nu3), T(0)));
-            // Krylov dimension: stop at an (almost) invariant subspace
-            const T eps = T(1e-12);
-            int m = 3;
-            if (!(beta > T(0))) m = 0;
-            else if (!(s[S::H + 2 * (1 * 3 + 0)] > eps * s[S::WN1])) m = 1;
-            else if (!(s[S::H + 2 * (2 * 3 + 1)] > eps * s[S::WN2])) m = 2;
-            s[S::M] = (T)m;
-            cplx<T> y[3], cr[4];
-            hess_lsq<T>(s + S::H, beta, m, y, cr);
-            for (int q = 0; q < 3; ++q) sstore2<T>(s, S::Y + 2 * q, y[q]);
-            const T inv[3] = {sinv<T>(beta), sinv<T>(nu2), sinv<T>(nu3)};
-            for (int q = 0; q < 3; ++q) sstore2<T>(s, S::CUPD + 2 * q, cscale<T>(y[q], inv[q]));
-            // r = sum_i c_i v_i; v4 = s4 (w3 - CB3.(r0,u2,u3))/nu4
-            const cplx<T> cb[3] = {sload2<T>(s, S::CB3), sload2<T>(s, S::CB3 + 2), sload2<T>(s, S::CB3 + 4)};
-            const T i4 = sinv<T>(nu4) * s[S::SC4];
-            const cplx<T> c4 = (m == 3) ? cscale<T>(cr[3], i4) : zero2<T>();
-            for (int q = 0; q < 3; ++q) {
-                cplx<T> v = (q <= m) ? cscale<T>(cr[q], inv[q]) : zero2<T>();
-                v = csub<T>(v, cmul<T>(c4, cb[q]));
-                sstore2<T>(s, S::CRES + 2 * q, v);
-            }
-            sstore2<T>(s, S::CRES + 6, c4);
-        }
-    }
-}
-
-// Post-smoother update SAX = x[sx] + V y (pointwise).  With `mod` (level 2) the
-// ADR result is modulated into the Helmholtz iterate instead:
-// u += exp(+i w phi) (x + V y)   (Algorithm 1's u <- u + e).
-template <typename T>
-__global__ void __launch_bounds__(NT) k_gm_update(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                  int nseg, int sr0, int sx, int modulate) {
-    __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
-    const cplx<T>* r0 = slot<T>(d, sr0);
-    const cplx<T>* u2 = slot<T>(d, SU2);
-    const cplx<T>* u3 = slot<T>(d, SU3);
-    const cplx<T>* x = slot<T>(d, sx);
-    cplx<T>* xout = slot<T>(d, SAX);
-    cplx<T>* u = slot<T>(d, SU);
-    const cplx<T>* mod = reinterpret_cast<const cplx<T>*>(d.mod);
-    const T* sc = scalp<T>(d);
-    const cplx<T> c0 = sload2<T>(sc, S::CUPD), c1 = sload2<T>(sc, S::CUPD + 2), c2 = sload2<T>(sc, S::CUPD + 4);
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
-        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
-        const long long p = (long long)j * d.pitch + i;
-        cplx<T> v = __ldg(x + p);
-        v = cfma<T>(c0, __ldg(r0 + p), v);
-        v = cfma<T>(c1, __ldg(u2 + p), v);
-        v = cfma<T>(c2, __ldg(u3 + p), v);
-        if (modulate) u[p] = cfma<T>(__ldg(mod + p), v, __ldg(u + p));
-        else xout[p] = v;
-    }
-}
 
 // ----------------------------------------------------------- coarsest level
 // x = A^{-1} b with the dense FP64 inverse formed at setup from the LU

@@ -10,6 +10,7 @@
 #include "handle.h"
 #include "fgmres.cuh"
 #include "kernels.cuh"
+#include "gmres_sstep.cuh"
 
 
 namespace wadr {
@@ -19,11 +20,10 @@ void set_error(const std::string& s) { g_err = s; }
 
 const char* kernel_kind_name(int k) {
     static const char* names[KK_COUNT] = {
-        "restrict_jacobi0", "restrict_helmholtz", "restrict_gmres_update", "prolong_jacobi", "prolong_add",
-        "prolong_adr_residual", "chebyshev_step", "residual_demodulate", "gmres_a1", "gmres_a2", "gmres_a3",
-        "gmres_b3_lsq", "gmres_update", "coarse_lu_apply", "outer_residual_fp64", "outer_scale",
-        "outer_update_fp64", "jacobi", "fgmres_start", "fgmres_prep", "fgmres_matvec", "fgmres_dots",
-        "fgmres_orth", "fgmres_update"};
+        "restrict_jacobi0", "restrict_helmholtz", "gmres_pre_restrict", "prolong_jacobi", "prolong_add",
+        "prolong_adr_residual", "chebyshev_step", "residual_demodulate", "gmres_gram", "gmres_post_update",
+        "coarse_lu_apply", "outer_residual_fp64", "outer_scale", "outer_update_fp64", "jacobi", "fgmres_start",
+        "fgmres_prep", "fgmres_matvec", "fgmres_dots", "fgmres_orth", "fgmres_update"};
     return (k >= 0 && k < KK_COUNT) ? names[k] : "unknown";
 }
 
@@ -80,6 +80,40 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
         const LevelDesc& d = outer ? houter[i] : hdesc[i];
         t.pts += (long long)d.n * d.n;
     }
+    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
+    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    return segs[key] = t;
+}
+
+std::string desc_key(const std::vector<int>& ids) {
+    std::string key;
+    for (int i : ids) key += "," + std::to_string(i);
+    return key;
+}
+
+const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, bool coarse, int cap) {
+    std::string key = "t" + std::to_string(tx) + "x" + std::to_string(ty) + (coarse ? "c" : "f") +
+                      std::to_string(cap) + desc_key(ids);
+    auto it = segs.find(key);
+    if (it != segs.end()) return it->second;
+    std::vector<Seg> h;
+    SegTable t;
+    int blk = 0;
+    for (int i : ids) {
+        const LevelDesc& d = hdesc[i];
+        const int n = coarse ? hdesc[d.coarse].n : d.n;
+        const long long ntiles = (long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty);
+        Seg s;
+        s.desc = i;
+        s.blk0 = blk;
+        blk += (int)std::max(1LL, std::min(ntiles, (long long)std::min(cap, MAXB)));
+        s.blk1 = blk;
+        s.pad = 0;
+        h.push_back(s);
+        t.pts += (long long)d.n * d.n;
+    }
+    t.nseg = (int)h.size();
+    t.nblocks = blk;
     t.d = (Seg*)alloc(sizeof(Seg) * h.size());
     cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
     return segs[key] = t;
@@ -291,6 +325,10 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.fwh = (float)d.wh;
             d.fshift = (float)d.shift;
             d.has_shift = d.shift != 0.0;
+            d.gs = lv.adr ? setup_adr_scale(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
+                                            dscr, st)
+                          : 1.0;
+            d.fgs = (float)d.gs;
             d.bc = I.bc;
             d.inst = b;
             d.level = l;
@@ -520,6 +558,8 @@ void mg_default_params(mg_params* p) {
     p->tol = 1e-6;
     p->shift = 0.0;
     p->use_graph = 1;
+    p->autotune = 1;
+    p->tile_candidate = -1;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -528,7 +568,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) { set_error("mg_setup: precision"); return MG_EINVAL; }
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
-        p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES) {
+        p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
+        p->tile_candidate >= MG_TILE_CANDIDATES) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }
@@ -570,6 +611,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         }
     }
     int rc = build(mh, staged.data(), ninst, st0);
+    if (!rc) rc = mh->eng->autotune(mh->H, st0);
     cudaStreamSynchronize(st0);
     for (void* q : tmp) cudaFree(q);
     if (rc) {
@@ -610,6 +652,29 @@ int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int n
     int k = std::min(nout, 4);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
+}
+
+int mg_tile_shapes(const mg_handle* h, int inst, int level, int* out) {
+    if (!h || !out || inst < 0 || inst >= (int)h->H.inst.size()) return MG_EINVAL;
+    const Handle& H = h->H;
+    if (level < 2 || level >= H.inst[inst].L || !H.inst[inst].lv[level - 1].adr) return MG_EINVAL;
+    // the ADR launch of this level covers every instance that has a finer-than-coarsest level l
+    std::vector<int> ds;
+    for (const InstHost& I : H.inst)
+        if (I.L > level) ds.push_back(I.lv[level - 1].desc);
+    TileChoice tc;
+    auto it = H.tiles.find(desc_key(ds));
+    if (it != H.tiles.end()) tc = it->second;
+    if (H.p.tile_candidate >= 0) tc.gram = tc.pre = tc.post = H.p.tile_candidate;
+    const int g = tc.gram >= 0 ? tc.gram : GS_DEFAULT_GRAM, pr = tc.pre >= 0 ? tc.pre : GS_DEFAULT_PRE,
+              po = tc.post >= 0 ? tc.post : GS_DEFAULT_POST;
+    out[0] = gs_gram_shape(g).x;
+    out[1] = gs_gram_shape(g).y;
+    out[2] = gs_pre_shape(pr).x;
+    out[3] = gs_pre_shape(pr).y;
+    out[4] = gs_post_shape(po).x;
+    out[5] = gs_post_shape(po).y;
+    return MG_OK;
 }
 
 int mg_cycle_launches(const mg_handle* h) { return h ? h->H.launches_cycle : MG_EINVAL; }

@@ -3,6 +3,7 @@
 // These run once per mg_setup; none is on the per-cycle path.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "handle.h"
@@ -81,6 +82,38 @@ double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch
     double r;
     memcpy(&r, &v, sizeof(r));
     return r * r;
+}
+
+// max over nodes of the absolute row sum of the ADR operator |d| + sum |c_dir|
+__global__ void k_adr_rowmax(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
+                             double h, double omega, int bc, double shift, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j);
+    const double v = sqrt(dabs2(c.d)) + sqrt(dabs2(c.cw)) + sqrt(dabs2(c.ce)) + sqrt(dabs2(c.cs)) +
+                     sqrt(dabs2(c.cn));
+    atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+// Scale of the s-step GMRES basis of an ADR level: the power of two s with
+// s * (max row sum of |L|) in (1/2, 1], so that ||s L||_inf <= 1 and the
+// basis vectors (s L)^j r0 stay O(|r0|) without rounding from s itself.
+double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                       double omega, int bc, double shift, double* dscratch, cudaStream_t st) {
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
+    cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
+    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
+    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, shift, o);
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    double r;
+    memcpy(&r, &v, sizeof(r));
+    if (!(r > 0.0)) return 1.0;
+    int e;
+    std::frexp(r, &e);          // r = f 2^e, f in [1/2, 1)
+    return std::ldexp(1.0, -e);
 }
 
 // ---------------------------------------------------------------- dense LU

@@ -1,0 +1,87 @@
+"""Halo-tile candidates and the setup-time autotuner of the ADR GMRES(3)
+kernels: every candidate shape gives the oracle's cycle (ragged and even
+grid sizes included), and the autotuner only picks listed candidates."""
+import numpy as np
+import pytest
+
+from gpu_util import lib_handle, oracle_hier, rel, rnd
+from paper_2404_02493_gb300 import binding as B
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GRAM = [(32, 8), (32, 16), (64, 8), (64, 16)]
+PRE = [(16, 8), (32, 8), (16, 16), (32, 4)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_02493_gb300 import build
+    build.build()
+    B.load()
+
+
+def _inst(n, omega, seed):
+    return synth.config_lognormal(n=n, omega=omega, seed=seed)
+
+
+@pytest.mark.parametrize("cand", range(B.MG_TILE_CANDIDATES))
+@pytest.mark.parametrize("n", [100, 127])
+def test_every_tile_candidate_matches_oracle_fp64(cand, n):
+    I = _inst(n, 0.4 * n * np.pi / 5, 40 + n)
+    h = lib_handle([I], "fp64", n_cmax=12, tile_candidate=cand, autotune=0)
+    H = oracle_hier(I, n_cmax=12)
+    try:
+        u = rnd(I.g.shape, 7) * 1e-3
+        uu = u.copy()
+        B.mg_cycle(h, uu, I.g.copy(), 1)
+        ref = H.cycle(u, I.g)
+        assert rel(uu, ref) < 1e-12, (cand, n, rel(uu, ref))
+        sh = B.mg_tile_shapes(h, 0, 2)
+        assert sh["gram"] == GRAM[cand] and sh["pre"] == PRE[cand] and sh["post"] == GRAM[cand]
+    finally:
+        B.mg_destroy(h)
+
+
+@pytest.mark.parametrize("cand", range(B.MG_TILE_CANDIDATES))
+def test_every_tile_candidate_mixed_within_tolerance(cand):
+    I = _inst(255, 100.0, 5)
+    h = lib_handle([I], "mixed", n_cmax=15, tile_candidate=cand, autotune=0)
+    H = oracle_hier(I, n_cmax=15)
+    try:
+        g32 = (I.g / np.linalg.norm(I.g)).astype(np.complex64)
+        u32 = np.zeros_like(g32)
+        B.mg_cycle(h, u32, g32, 1)
+        ref = H.cycle(np.zeros_like(I.g), g32.astype(np.complex128))
+        assert rel(u32.astype(np.complex128), ref) < 1e-5, (cand, rel(u32, ref))
+    finally:
+        B.mg_destroy(h)
+
+
+def test_autotuner_picks_listed_candidates():
+    """Autotuned handle (default) vs default tiles: shapes are candidates on
+    every ADR level below the coarsest, and the two cycles agree to the FP32
+    rounding of a different reduction order."""
+    insts = [_inst(255, 100.0, 8), _inst(511, 200.0, 9)]
+    ha = lib_handle(insts, "mixed", n_cmax=15)              # autotune = 1
+    hd = lib_handle(insts, "mixed", n_cmax=15, autotune=0)
+    try:
+        for b, I in enumerate(insts):
+            L = B.mg_num_levels(ha, b)
+            for l in range(2, L):
+                sh = B.mg_tile_shapes(ha, b, l)
+                assert sh["gram"] in GRAM and sh["post"] in GRAM and sh["pre"] in PRE
+            with pytest.raises(B.MgError):
+                B.mg_tile_shapes(ha, b, L)
+        g = np.concatenate([(I.g / np.linalg.norm(I.g)).ravel() for I in insts]).astype(np.complex64)
+        ua = np.zeros_like(g)
+        ud = np.zeros_like(g)
+        B.mg_cycle(ha, ua, g, 2)
+        B.mg_cycle(hd, ud, g, 2)
+        assert rel(ua.astype(np.complex128), ud.astype(np.complex128)) < 1e-5
+    finally:
+        B.mg_destroy(ha)
+        B.mg_destroy(hd)
