@@ -253,12 +253,13 @@ int mg_adr_correction(mg_handle* h, int inst, void* u, const void* g, mg_stream 
 int mg_coarse_solve(mg_handle* h, int inst, int which, const void* b, void* x, mg_stream stream);
 
 /* Halo-tile shapes used by the ADR GMRES(3) kernels of `level` (2 <= level
- * < coarsest) in the launch that covers instance `inst`: out[6] = gram pass
- * tile (x, y fine nodes), pre-smoothing tile (x, y coarse nodes; fine
- * footprint 2x+1 by 2y+1), post-smoothing tile (x, y fine nodes), as chosen
- * by the setup-time autotuner (mg_params.autotune) or the defaults.  The
- * paper has no counterpart (its kernels are library convolutions).
- * Errors: MG_EINVAL (no such ADR level). */
+ * < coarsest) in the launch that covers instance `inst`, as chosen by the
+ * setup-time autotuner (mg_params.autotune) or the defaults: out[0..1] gram
+ * pass tile (x, y fine nodes; for the warp-streaming variant x = 56 result
+ * columns per strip and y the band height), out[2..3] pre-smoothing tile (x,
+ * y coarse nodes; fine footprint 2x+1 by 2y+1), out[4] = 1 when the gram
+ * pass is the streaming variant.  The paper has no counterpart (its kernels
+ * are library convolutions).  Errors: MG_EINVAL (no such ADR level). */
 int mg_tile_shapes(const mg_handle* h, int inst, int level, int* out);
 
 /* Number of kernel launches of one cycle (counted when the schedule is

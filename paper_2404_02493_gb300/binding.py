@@ -224,10 +224,10 @@ def mg_level_scalars(h, inst, level):
 
 def mg_tile_shapes(h, inst, level):
     """Halo tiles of the ADR GMRES kernels of `level`: {'gram': (x, y),
-    'pre': (x, y) coarse nodes, 'post': (x, y)}."""
+    'pre': (x, y) coarse nodes, 'streaming': bool (gram variant)}."""
     out = (ctypes.c_int * 6)()
     _check(load().mg_tile_shapes(h, inst, level, out), "mg_tile_shapes")
-    return {"gram": (out[0], out[1]), "pre": (out[2], out[3]), "post": (out[4], out[5])}
+    return {"gram": (out[0], out[1]), "pre": (out[2], out[3]), "streaming": bool(out[4])}
 
 
 def mg_apply(h, inst, level, op, x, y, stream=None):

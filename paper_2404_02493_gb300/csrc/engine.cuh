@@ -90,12 +90,12 @@ struct Engine : EngineBase {
         return cap[which][cand];
     }
     template <class K>
-    static int gs_prepare(K kern, int smem, int which, int cand) {
+    static int gs_prepare(K kern, int smem, int which, int cand, int threads) {
         int& cap = gs_cap_slot(which, cand);
         if (cap == 0) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             int nb = 0, dev = 0, nsm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
             cap = std::max(1, nb) * std::max(1, nsm);
@@ -114,28 +114,36 @@ struct Engine : EngineBase {
     static TileChoice tiles_of(Handle& H, const std::vector<int>& ds) {
         TileChoice tc;
         if (H.p.tile_candidate >= 0) {
-            tc.gram = tc.pre = tc.post = H.p.tile_candidate;
+            tc.gram = tc.pre = H.p.tile_candidate;
         } else {
             auto it = H.tiles.find(desc_key(ds));
             if (it != H.tiles.end()) tc = it->second;
         }
         if (tc.gram < 0) tc.gram = GS_DEFAULT_GRAM;
         if (tc.pre < 0) tc.pre = GS_DEFAULT_PRE;
-        if (tc.post < 0) tc.post = GS_DEFAULT_POST;
         return tc;
     }
 
-    // Gram pass of r0 in slot sr0 (reads r0 and the coefficients once).
+    // Gram pass of r0 in slot sr0 (reads r0 and the coefficients once,
+    // writes K1 and K2).
     void gs_gram(Handle& H, const std::vector<int>& ds, int cand, int sr0, cudaStream_t st) {
         gs_dispatch(cand, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             constexpr GsShape sh = gs_gram_shape(I);
-            auto kern = k_gs_gram<T, sh.x, sh.y>;
             const int smem = gs_gram_smem<T>(I);
-            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 0, I));
-            go(H, st, KK_GS_GRAM, (C + Q) * (double)t.pts, [&] {
-                kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sr0);
-            }, t.pts);
+            if constexpr (gs_gram_streaming(I)) {
+                auto kern = k_gs_gram_stream<T, sh.y>;
+                const SegTable& t = H.seg_tiles(ds, sh.x, sh.y * GS_WPB, false, gs_prepare(kern, smem, 0, I, 32 * GS_WPB));
+                go(H, st, KK_GS_GRAM, (3 * C + Q) * (double)t.pts, [&] {
+                    kern<<<t.nblocks, dim3(32, GS_WPB), smem, st>>>(H.ddesc, t.d, t.nseg, sr0);
+                }, t.pts);
+            } else {
+                auto kern = k_gs_gram_tile<T, sh.x, sh.y>;
+                const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 0, I, NT));
+                go(H, st, KK_GS_GRAM, (3 * C + Q) * (double)t.pts, [&] {
+                    kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sr0);
+                }, t.pts);
+            }
         });
     }
     // Pre-smoothing update from zero, fused with the restriction of the
@@ -146,25 +154,19 @@ struct Engine : EngineBase {
             constexpr GsShape sh = gs_pre_shape(I);
             auto kern = k_gs_pre<T, sh.x, sh.y>;
             const int smem = gs_pre_smem<T>(I);
-            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, true, gs_prepare(kern, smem, 1, I));
-            go(H, st, KK_GS_PRE, (2 * C + Q + C / 4) * (double)t.pts, [&] {
+            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, true, gs_prepare(kern, smem, 1, I, NT));
+            go(H, st, KK_GS_PRE, (4 * C + Q + C / 4) * (double)t.pts, [&] {
                 kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, SAB, SAX, SAB);
             }, t.pts);
         });
     }
     // Post-smoothing update x = x' + z (flags: 1 x' = 0, 2 modulate into u).
-    void gs_post(Handle& H, const std::vector<int>& ds, int cand, int sr0, int sxo, int flags, cudaStream_t st) {
-        gs_dispatch(cand, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            constexpr GsShape sh = gs_post_shape(I);
-            auto kern = k_gs_post<T, sh.x, sh.y>;
-            const int smem = gs_post_smem<T>(I);
-            const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 2, I));
-            const double bpp = (flags & 2) ? 5 * C + Q : ((flags & 1) ? 2 * C + Q : 3 * C + Q);
-            go(H, st, KK_GS_POST, bpp * (double)t.pts, [&] {
-                kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sr0, sxo, flags);
-            }, t.pts);
-        });
+    void gs_post(Handle& H, const std::vector<int>& ds, int sr0, int sxo, int flags, cudaStream_t st) {
+        const SegTable& t = H.seg(ds, false, 2 * NT);
+        const double bpp = (flags & 2) ? 7 * C : ((flags & 1) ? 4 * C : 5 * C);
+        go(H, st, KK_GS_POST, bpp * (double)t.pts, [&] {
+            k_gs_post<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, sr0, sxo, flags);
+        }, t.pts);
     }
 
     // Autotuner: for every ADR launch of the cycle (level l over the
@@ -174,15 +176,17 @@ struct Engine : EngineBase {
     // residual to the next level's SAB, scalars), all of which every cycle
     // rewrites before use.
     int autotune(Handle& H, cudaStream_t st) override {
-        for (int w = 0; w < 3; ++w)
-            for (int c = 0; c < GS_NCAND; ++c) {
-                gs_dispatch(c, [&](auto ic) {
-                    constexpr int I = decltype(ic)::value;
-                    if (w == 0) gs_prepare(k_gs_gram<T, gs_gram_shape(I).x, gs_gram_shape(I).y>, gs_gram_smem<T>(I), 0, I);
-                    if (w == 1) gs_prepare(k_gs_pre<T, gs_pre_shape(I).x, gs_pre_shape(I).y>, gs_pre_smem<T>(I), 1, I);
-                    if (w == 2) gs_prepare(k_gs_post<T, gs_post_shape(I).x, gs_post_shape(I).y>, gs_post_smem<T>(I), 2, I);
-                });
-            }
+        for (int c = 0; c < GS_NCAND; ++c) {
+            gs_dispatch(c, [&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                if constexpr (gs_gram_streaming(I))
+                    gs_prepare(k_gs_gram_stream<T, gs_gram_shape(I).y>, gs_gram_smem<T>(I), 0, I, 32 * GS_WPB);
+                else
+                    gs_prepare(k_gs_gram_tile<T, gs_gram_shape(I).x, gs_gram_shape(I).y>, gs_gram_smem<T>(I), 0, I,
+                               NT);
+                gs_prepare(k_gs_pre<T, gs_pre_shape(I).x, gs_pre_shape(I).y>, gs_pre_smem<T>(I), 1, I, NT);
+            });
+        }
         if (!H.p.adr || H.p.M <= 0 || !H.p.autotune || H.p.tile_candidate >= 0) return MG_OK;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -195,14 +199,13 @@ struct Engine : EngineBase {
             if (rest.empty()) continue;
             const std::vector<int> ds = descs(H, l, rest);
             TileChoice tc;
-            for (int w = 0; w < 3; ++w) {
+            for (int w = 0; w < 2; ++w) {
                 float best = 1e30f;
                 int arg = -1;
                 for (int c = 0; c < GS_NCAND; ++c) {
                     auto run = [&] {
                         if (w == 0) gs_gram(H, ds, c, SAB, st);
-                        else if (w == 1) gs_pre(H, ds, c, st);
-                        else gs_post(H, ds, c, SV1, SD, 0, st);
+                        else gs_pre(H, ds, c, st);
                     };
                     run();   // warm-up (also builds the segment table)
                     float tmin = 1e30f;
@@ -217,7 +220,7 @@ struct Engine : EngineBase {
                     }
                     if (tmin < best) { best = tmin; arg = c; }
                 }
-                (w == 0 ? tc.gram : w == 1 ? tc.pre : tc.post) = arg;
+                (w == 0 ? tc.gram : tc.pre) = arg;
             }
             H.tiles[desc_key(ds)] = tc;
         }
@@ -251,7 +254,7 @@ struct Engine : EngineBase {
         adrv(H, l + 1, rest, false, st);
         LAUNCH(KK_PROLONG_ADR, t, 4 * C + C / 4 + Q, (k_prolong<T, PMODE_ADR>), SAX, SAX, SAB, SV1, SD, 0);
         gs_gram(H, ds, tc.gram, SV1, st);   // post-smoothing from x' (r0 = b - L x')
-        gs_post(H, ds, tc.post, SV1, SD, modulate ? 2 : 0, st);
+        gs_post(H, ds, SV1, SD, modulate ? 2 : 0, st);
     }
 
     // Algorithm 1's ADR correction steps at level 2 (M times).
@@ -372,10 +375,10 @@ struct Engine : EngineBase {
             k_fg_dots<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
         }, t.pts);
         go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
-            k_fg_orth<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg, 1);
+            k_fg_orth<T, 1><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
         }, t.pts);
         go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
-            k_fg_orth<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg, 2);
+            k_fg_orth<T, 2><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
         }, t.pts);
         H.launches_cycle = cyc;
         H.launches_step = cyc + 5;
@@ -433,10 +436,10 @@ struct Engine : EngineBase {
                 k_sub<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAB, STMP, SV1);
                 k_copy<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAX, SD);
                 gs_gram(H, ds, tc.gram, SV1, st);
-                gs_post(H, ds, tc.post, SV1, SD, 0, st);
+                gs_post(H, ds, SV1, SD, 0, st);
             } else {
                 gs_gram(H, ds, tc.gram, SAB, st);
-                gs_post(H, ds, tc.post, SAB, SD, 1, st);
+                gs_post(H, ds, SAB, SD, 1, st);
             }
             return SAX;
         }

@@ -167,6 +167,53 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const LevelDesc* __restrict__ 
     }
 }
 
+// The Gram-Schmidt kernels stream the level-1 vectors two complex values
+// per thread (one 16-byte load for complex64): W and V_0..V_j at the same
+// positions, so that every thread keeps j + 2 independent loads in flight.
+// Pairs run along rows; when n is odd the last pair of a row has one node
+// past the grid (row padding, zero in every vector) which is masked.
+template <typename TC>
+struct V2 {
+    cplx<TC> a, b;
+};
+template <typename TC>
+__device__ __forceinline__ V2<TC> ld2(const cplx<TC>* p) {
+    if constexpr (sizeof(cplx<TC>) == 8) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        return V2<TC>{mk<TC>(v.x, v.y), mk<TC>(v.z, v.w)};
+    } else {
+        return V2<TC>{__ldg(p), __ldg(p + 1)};
+    }
+}
+template <typename TC>
+__device__ __forceinline__ V2<TC> ld2cg(const cplx<TC>* p) {   // vector written by this kernel family
+    if constexpr (sizeof(cplx<TC>) == 8) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+        return V2<TC>{mk<TC>(v.x, v.y), mk<TC>(v.z, v.w)};
+    } else {
+        return V2<TC>{__ldcg(p), __ldcg(p + 1)};
+    }
+}
+template <typename TC>
+__device__ __forceinline__ void st2(cplx<TC>* p, const V2<TC>& v, bool two) {
+    if constexpr (sizeof(cplx<TC>) == 8) {
+        if (two) {
+            *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+            return;
+        }
+        p[0] = v.a;
+    } else {
+        p[0] = v.a;
+        if (two) p[1] = v.b;
+    }
+}
+// pair index e -> element offset of its first node, and whether both exist
+__device__ __forceinline__ long long pair_pos(int e, int npr, int pitch, int n, bool& two) {
+    const int r = e / npr, q = e - r * npr;
+    two = 2 * q + 1 < n;
+    return (long long)r * pitch + 2 * q;
+}
+
 // First Gram-Schmidt pass: projections <V_i, W>, i <= j  -> fs[HC].
 template <typename TC>
 __global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
@@ -177,20 +224,26 @@ __global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D,
     __shared__ cplx<TC> shT[8 * NVF];
     __shared__ int flag;
     SegCtx c = seg_begin(D, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
     const int jj = (int)d.fs[FS::J];
     const cplx<TC>* w = kvec<TC>(d, jj + 1);
+    const cplx<TC>* v0 = kvec<TC>(d, 0);
+    const long long vs = d.slot_stride;
     cplx<TC> ac[NVF];
 #pragma unroll
     for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
-        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
-        const long long p = (long long)j * d.pitch + i;
-        const cplx<TC> wv = __ldg(w + p);
+    for (int e = c.lb * NT + tid; e < npairs; e += c.nb * NT) {
+        bool two;
+        const long long p = pair_pos(e, npr, pitch, n, two);
+        V2<TC> wv = ld2cg<TC>(w + p);
+        if (!two) wv.b = zero2<TC>();
 #pragma unroll
         for (int q = 0; q < MAXR; ++q)
-            if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(__ldg(kvec<TC>(d, q) + p), wv));
+            if (q <= jj) {
+                const V2<TC> v = ld2<TC>(v0 + q * vs + p);
+                ac[q] = cadd<TC>(ac[q], cadd<TC>(cmulc<TC>(v.a, wv.a), cmulc<TC>(v.b, wv.b)));
+            }
     }
     block_sum<cplx<TC>, NVF>(ac, shT);
     if (publish_fpartials(d, c.lb, c.nb, ac, jj + 1, &flag)) {
@@ -204,9 +257,9 @@ __global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D,
 // 1 also forms the second-pass projections <V_i, W'>; both passes form
 // ||W'||^2.  The last block of pass 2 completes column j of the Hessenberg,
 // applies the Givens rotations, stores |gamma_{j+1}| and advances j.
-template <typename TC>
-__global__ void __launch_bounds__(NT) k_fg_orth(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                int nseg, int pass) {
+template <typename TC, int pass>
+__global__ void __launch_bounds__(NT, 2) k_fg_orth(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                   int nseg) {
     __shared__ LevelDesc d;
     __shared__ double2 grp[8 * 32];
     __shared__ double2 tot[NVF];
@@ -215,30 +268,52 @@ __global__ void __launch_bounds__(NT) k_fg_orth(const LevelDesc* __restrict__ D,
     __shared__ int flag;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
     const int jj = (int)d.fs[FS::J];
     cplx<TC>* w = kvec<TC>(d, jj + 1);
+    const cplx<TC>* v0 = kvec<TC>(d, 0);
+    const long long vs = d.slot_stride;
     const int off = (pass == 1) ? FS::HC : FS::CC;
     if (tid < MAXR) coef[tid] = tid <= jj ? mk<TC>((TC)d.fs[off + 2 * tid], (TC)d.fs[off + 2 * tid + 1]) : zero2<TC>();
     __syncthreads();
+    constexpr int NA = (pass == 1) ? NVF : 1;   // pass 2 keeps only ||W''||^2
     cplx<TC> ac[NVF];
 #pragma unroll
     for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
-        const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
-        const long long p = (long long)j * d.pitch + i;
-        cplx<TC> wv = w[p];
-        for (int q = 0; q <= jj; ++q) wv = csub<TC>(wv, cmul<TC>(coef[q], __ldg(kvec<TC>(d, q) + p)));
-        w[p] = wv;
+    cplx<TC> nrm = zero2<TC>();
+    for (int e = c.lb * NT + tid; e < npairs; e += c.nb * NT) {
+        bool two;
+        const long long p = pair_pos(e, npr, pitch, n, two);
+        V2<TC> wv = ld2cg<TC>(w + p);
+        // chunks of 8 vectors: 8 loads in flight per thread, bounded registers
+#pragma unroll 1
+        for (int q0 = 0; q0 <= jj; q0 += 8) {
+#pragma unroll
+            for (int dq = 0; dq < 8; ++dq) {
+                const int q = q0 + dq;
+                if (q <= jj) {
+                    const V2<TC> v = ld2<TC>(v0 + q * vs + p);
+                    const cplx<TC> cq = coef[q];
+                    wv.a = csub<TC>(wv.a, cmul<TC>(cq, v.a));
+                    wv.b = csub<TC>(wv.b, cmul<TC>(cq, v.b));
+                }
+            }
+        }
+        if (!two) wv.b = zero2<TC>();
+        st2<TC>(w + p, wv, two);
         if (pass == 1) {
             // second-pass projections; V_q is read again (mostly from L1)
 #pragma unroll
             for (int q = 0; q < MAXR; ++q)
-                if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(__ldg(kvec<TC>(d, q) + p), wv));
+                if (q <= jj) {
+                    const V2<TC> v = ld2<TC>(v0 + q * vs + p);
+                    ac[q] = cadd<TC>(ac[q], cadd<TC>(cmulc<TC>(v.a, wv.a), cmulc<TC>(v.b, wv.b)));
+                }
         }
-        ac[NVF - 1].x += cabs2<TC>(wv);
+        nrm.x += cabs2<TC>(wv.a) + cabs2<TC>(wv.b);
     }
+    (void)NA;
+    ac[NVF - 1] = nrm;
     block_sum<cplx<TC>, NVF>(ac, shT);
     if (publish_fpartials(d, c.lb, c.nb, ac, NVF, &flag)) {
         finish_fpartials(d, c.nb, tot, grp);

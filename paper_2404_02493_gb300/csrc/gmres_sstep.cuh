@@ -6,75 +6,48 @@
 // basis K_j = (s L)^j r0, j = 0..3, gives z = s (c0 K0 + c1 K1 + c2 K2) and
 // r = r0 - (c0 K1 + c1 K2 + c2 K3), where c solves the 3 x 3 normal equations
 //   G[1:,1:] c = G[1:,0],   G_ab = <K_a, K_b>.
-// One sweep is therefore two passes over the level instead of an Arnoldi
-// process with a reduction per basis vector:
-//   gram pass:  K1..K3 recomputed on chip from a halo-3 tile of r0, the ten
-//               distinct entries of G reduced (fixed order), and the small
-//               system solved by the last block (Jacobi-scaled Cholesky);
-//   update pass: K1, K2 (and K3 for the residual) recomputed from a halo tile
-//               of r0; pre-smoothing also forms the residual and restricts it
-//               (full weighting) to the next level, post-smoothing adds z to
-//               x' (or, at level 2, adds exp(+i w phi) (x' + z) to the wave
-//               iterate).
+// One sweep is two passes over the level instead of an Arnoldi process with
+// a reduction per basis vector:
+//   gram pass:  K1, K2 formed on chip from a halo-3 neighbourhood of r0 and
+//               stored, K3 formed at the node, the ten distinct entries of G
+//               reduced in a fixed order, the small system solved by the last
+//               block (Jacobi-scaled Cholesky);
+//   update:     pre-smoothing (from x0 = 0): x, and the residual (K3 again,
+//               one stencil on the stored K2) restricted by full weighting to
+//               the next level; post-smoothing: x = x' + z, pointwise (at
+//               level 2 added to the wave iterate as exp(+i w phi) x).
 // The same minimiser as the Arnoldi form; in the working precision the Gram
 // form loses accuracy like cond(K)^2, which the small block-tree reductions
 // keep below the Arnoldi form's error on the ADR levels of the cycle.
 //
-// Tiles: every kernel is templated on its tile shape; a setup-time autotuner
-// times the candidate shapes per level and launch (GsShapes).
+// The gram pass exists as a shared-memory tile kernel (two tile shapes) and
+// as a warp-streaming kernel (two band heights); the pre-smoothing update as
+// a footprint tile kernel (four shapes).  A setup-time autotuner times the
+// candidates per level and launch.
 #pragma once
-#include "kernels.cuh"
+#include "stream.cuh"
 
 namespace wadr {
 
-// ------------------------------------------------------------ tile shapes
-// Candidates (the autotuner picks one index per kernel and launch).
+// ------------------------------------------------------------ candidates
 constexpr int GS_NCAND = 4;
+constexpr int GS_WPB = 4;            // warps per block of the streaming kernel
 struct GsShape { int x, y; };
-// gram and post: fine tile TX x TY; pre: coarse tile CX x CY (fine footprint 2C+1)
+// gram: 0, 1 = tiles of x * y fine nodes; 2, 3 = streaming strips of 56
+// result columns by y rows
 __host__ __device__ constexpr GsShape gs_gram_shape(int i) {
-    return i == 0 ? GsShape{32, 8} : i == 1 ? GsShape{32, 16} : i == 2 ? GsShape{64, 8} : GsShape{64, 16};
+    return i == 0 ? GsShape{32, 8} : i == 1 ? GsShape{32, 16} : i == 2 ? GsShape{SW_OUT, 32} : GsShape{SW_OUT, 64};
 }
+__host__ __device__ constexpr bool gs_gram_streaming(int i) { return i >= 2; }
+// pre: tiles of x * y coarse nodes (fine footprint 2x+1 by 2y+1)
 __host__ __device__ constexpr GsShape gs_pre_shape(int i) {
     return i == 0 ? GsShape{16, 8} : i == 1 ? GsShape{32, 8} : i == 2 ? GsShape{16, 16} : GsShape{32, 4};
 }
-__host__ __device__ constexpr GsShape gs_post_shape(int i) { return gs_gram_shape(i); }
-constexpr int GS_DEFAULT_GRAM = 1, GS_DEFAULT_PRE = 0, GS_DEFAULT_POST = 1;
+constexpr int GS_DEFAULT_GRAM = 1, GS_DEFAULT_PRE = 0;
 
 template <typename T> struct GsEps;
 template <> struct GsEps<float> { static constexpr float tau = 32.0f * 1.1920929e-7f; };
 template <> struct GsEps<double> { static constexpr double tau = 32.0 * 2.220446049250313e-16; };
-
-// s L at an on-chip point b of a region of row stride W, with the point's
-// coefficient quad q; zero outside the grid is carried by the region itself
-// (ADR ghost values are zero).
-template <typename T>
-__device__ __forceinline__ cplx<T> sl_q(const quad<T>& q, const cplx<T>* __restrict__ Sr, int b, int W, T ih2,
-                                        T wh, T s) {
-    return cscale<T>(adr_pt<T>(q, ih2, wh, Sr[b], Sr[b - 1], Sr[b + 1], Sr[b - W], Sr[b + W]), s);
-}
-
-// Sout (WO x HO nodes from global (ox, oy)) = s L Sin, with Sin of stride
-// WO + 2 from (ox - 1, oy - 1) and coefficients Q of stride WQ from
-// (ox - QO, oy - QO); zero outside the grid.
-template <typename T, int WO, int HO, int WQ, int QO>
-__device__ __forceinline__ void sl_stage(int n, const cplx<T>* __restrict__ Sin, cplx<T>* __restrict__ Sout,
-                                         const quad<T>* __restrict__ Q, int ox, int oy, T ih2, T wh, T s) {
-    constexpr int WI = WO + 2, NE = WO * HO;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-#pragma unroll
-    for (int k = 0; k < (NE + NT - 1) / NT; ++k) {
-        const int e = tid + k * NT;
-        if (NE % NT == 0 || e < NE) {
-            const int r = e / WO, cc = e - r * WO;
-            const int gi = ox + cc, gj = oy + r;
-            cplx<T> v = zero2<T>();
-            if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n)
-                v = sl_q<T>(Q[(r + QO) * WQ + cc + QO], Sin, (r + 1) * WI + cc + 1, WI, ih2, wh, s);
-            Sout[e] = v;
-        }
-    }
-}
 
 // Normal equations of the s-step GMRES(3) in the last block (thread 0).
 // G[0] = (|K0|^2, |K1|^2), G[1] = (|K2|^2, |K3|^2), G[2..4] = <K0, K1..K3>,
@@ -132,14 +105,71 @@ __device__ inline void gs_solve(const cplx<T> (&G)[8], T* sc) {
     sc[S::NORM] = rr;
 }
 
-// ------------------------------------------------------------ gram pass
-// r0 in slot sr0; G reduced per (instance, level), c stored in S::GC.
-// Double-buffered: the r0 halo tile (halo 3) and the coefficient tile (halo
-// 2) of a block's next tile are copied asynchronously while the current one
-// is computed.
+// s L at an on-chip point b of a region of row stride W, with the point's
+// coefficient quad q; zero outside the grid is carried by the region itself
+// (ADR ghost values are zero).
+template <typename T>
+__device__ __forceinline__ cplx<T> sl_q(const quad<T>& q, const cplx<T>* __restrict__ Sr, int b, int W, T ih2,
+                                        T wh, T s) {
+    return cscale<T>(adr_pt<T>(q, ih2, wh, Sr[b], Sr[b - 1], Sr[b + 1], Sr[b - W], Sr[b + W]), s);
+}
+
+// Sout (WO x HO nodes from global (ox, oy)) = s L Sin, with Sin of stride
+// WO + 2 from (ox - 1, oy - 1) and coefficients Q of stride WQ from
+// (ox - QO, oy - QO); zero outside the grid.
+template <typename T, int WO, int HO, int WQ, int QO>
+__device__ __forceinline__ void sl_stage(int n, const cplx<T>* __restrict__ Sin, cplx<T>* __restrict__ Sout,
+                                         const quad<T>* __restrict__ Q, int ox, int oy, T ih2, T wh, T s) {
+    constexpr int WI = WO + 2, NE = WO * HO;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+#pragma unroll
+    for (int k = 0; k < (NE + NT - 1) / NT; ++k) {
+        const int e = tid + k * NT;
+        if (NE % NT == 0 || e < NE) {
+            const int r = e / WO, cc = e - r * WO;
+            const int gi = ox + cc, gj = oy + r;
+            cplx<T> v = zero2<T>();
+            if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n)
+                v = sl_q<T>(Q[(r + QO) * WQ + cc + QO], Sin, (r + 1) * WI + cc + 1, WI, ih2, wh, s);
+            Sout[e] = v;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void gram_acc(cplx<T> (&ac)[8], cplx<T> k0, cplx<T> k1, cplx<T> k2, cplx<T> k3) {
+    ac[0].x += cabs2<T>(k0);
+    ac[0].y += cabs2<T>(k1);
+    ac[1].x += cabs2<T>(k2);
+    ac[1].y += cabs2<T>(k3);
+    ac[2] = cadd<T>(ac[2], cmulc<T>(k0, k1));
+    ac[3] = cadd<T>(ac[3], cmulc<T>(k0, k2));
+    ac[4] = cadd<T>(ac[4], cmulc<T>(k0, k3));
+    ac[5] = cadd<T>(ac[5], cmulc<T>(k1, k2));
+    ac[6] = cadd<T>(ac[6], cmulc<T>(k1, k3));
+    ac[7] = cadd<T>(ac[7], cmulc<T>(k2, k3));
+}
+
+// reduction of the Gram entries of a launch and the small solve
+template <typename T>
+__device__ __forceinline__ void gram_finish(const LevelDesc& d, const SegCtx& c, cplx<T> (&ac)[8], cplx<T>* sh,
+                                            int* flag) {
+    block_sum<cplx<T>, 8>(ac, sh);
+    if (publish_partials<cplx<T>, 8>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, flag)) {
+        cplx<T> tot[8];
+        finish_partials<cplx<T>, 8>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) gs_solve<T>(tot, scalp<T>(d));
+    }
+}
+
+// ------------------------------------------------------------ gram pass (tiles)
+// r0 in slot sr0; K1, K2 to SK1, SK2; G reduced per (instance, level), c in
+// S::GC.  Double-buffered: the r0 halo tile (halo 3) and the coefficient tile
+// (halo 2) of a block's next tile stream in while the current one is
+// computed.
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(NT) k_gs_gram(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                int nseg, int sr0) {
+__global__ void __launch_bounds__(NT) k_gs_gram_tile(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                     int nseg, int sr0) {
     constexpr int W0 = TX + 6, H0 = TY + 6, W1 = TX + 4, H1 = TY + 4, W2 = TX + 2, H2 = TY + 2;
     static_assert((TX * TY) % NT == 0, "tile");
     extern __shared__ __align__(16) unsigned char gs_smem[];
@@ -155,6 +185,8 @@ __global__ void __launch_bounds__(NT) k_gs_gram(const LevelDesc* __restrict__ D,
     const int n = d.n, pitch = d.pitch;
     const int ntx = (n + TX - 1) / TX, ntiles = ntx * ((n + TY - 1) / TY);
     const cplx<T>* r0 = slot<T>(d, sr0);
+    cplx<T>* k1o = slot<T>(d, SK1);
+    cplx<T>* k2o = slot<T>(d, SK2);
     const quad<T>* coef = reinterpret_cast<const quad<T>*>(d.adr);
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
     auto issue = [&](int t, int b) {
@@ -188,66 +220,148 @@ __global__ void __launch_bounds__(NT) k_gs_gram(const LevelDesc* __restrict__ D,
                 const int b2 = (r + 1) * W2 + cc + 1;
                 const cplx<T> k0 = S0[(r + 3) * W0 + cc + 3], k1 = S1[(r + 2) * W1 + cc + 2], k2 = S2[b2];
                 const cplx<T> k3 = sl_q<T>(Q[(r + 2) * W1 + cc + 2], S2, b2, W2, ih2, wh, s);
-                ac[0].x += cabs2<T>(k0);
-                ac[0].y += cabs2<T>(k1);
-                ac[1].x += cabs2<T>(k2);
-                ac[1].y += cabs2<T>(k3);
-                ac[2] = cadd<T>(ac[2], cmulc<T>(k0, k1));
-                ac[3] = cadd<T>(ac[3], cmulc<T>(k0, k2));
-                ac[4] = cadd<T>(ac[4], cmulc<T>(k0, k3));
-                ac[5] = cadd<T>(ac[5], cmulc<T>(k1, k2));
-                ac[6] = cadd<T>(ac[6], cmulc<T>(k1, k3));
-                ac[7] = cadd<T>(ac[7], cmulc<T>(k2, k3));
+                const long long p = (long long)(y0 + r) * pitch + x0 + cc;
+                k1o[p] = k1;
+                k2o[p] = k2;
+                gram_acc<T>(ac, k0, k1, k2, k3);
             }
         }
         __syncthreads();
         buf ^= 1;
     }
     cp_async_wait<0>();
-    block_sum<cplx<T>, 8>(ac, sh);
-    if (publish_partials<cplx<T>, 8>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, &flag)) {
-        cplx<T> tot[8];
-        finish_partials<cplx<T>, 8>(partp<T>(d), MAXDOT, d.counter, c.nb, tot, sh);
-        if (tid == 0) gs_solve<T>(tot, scalp<T>(d));
+    gram_finish<T>(d, c, ac, sh, &flag);
+}
+
+// ------------------------------------------------------------ gram pass (streaming)
+// The same pass as warp-streaming strips (stream.cuh).  March of a unit:
+// input row j, K1 at j-1, K2 at j-2, K3 and the Gram terms at j-3.
+template <typename T> constexpr int gs_ring_bytes(int nq, int nc) {
+    return (int)((nq * sizeof(quad<T>) + nc * sizeof(cplx<T>)) * GS_WPB * SW_DEP * SW_COLS);
+}
+template <typename T, int RH>
+__global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const LevelDesc* __restrict__ D,
+                                                                const Seg* __restrict__ Sg, int nseg, int sr0) {
+    extern __shared__ __align__(16) unsigned char gs_smem[];
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    quad<T>* Qr = reinterpret_cast<quad<T>*>(gs_smem) + warp * SW_DEP * SW_COLS;
+    cplx<T>* Kr = reinterpret_cast<cplx<T>*>(reinterpret_cast<quad<T>*>(gs_smem) + GS_WPB * SW_DEP * SW_COLS) +
+                  warp * SW_DEP * SW_COLS;
+    __shared__ LevelDesc d;
+    __shared__ cplx<T> sh[8 * 8];
+    __shared__ int flag;
+    SegCtx c = seg_begin(D, Sg, nseg, d);
+    const int n = d.n, pitch = d.pitch;
+    const int nstrips = (n + SW_OUT - 1) / SW_OUT, nunits = nstrips * ((n + RH - 1) / RH);
+    const cplx<T>* r0 = slot<T>(d, sr0);
+    cplx<T>* k1o = slot<T>(d, SK1);
+    cplx<T>* k2o = slot<T>(d, SK2);
+    const quad<T>* coef = reinterpret_cast<const quad<T>*>(d.adr);
+    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
+    cplx<T> ac[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ac[k] = zero2<T>();
+    for (int u = c.lb * GS_WPB + warp; u < nunits; u += c.nb * GS_WPB) {
+        const StripGeo gg = strip_geo(u, nstrips, RH, n);
+        const int j0 = gg.y0 - 3, j1 = gg.y1 + 2;
+        const int col = gg.X0 + 2 * lane;
+        const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
+        const bool own = lane >= 2 && lane < 30;
+        auto issue = [&](int r) {
+            ring_issue<cplx<T>>(Kr, r0, n, pitch, gg.X0, r, lane);
+            ring_issue<quad<T>>(Qr, coef, n, pitch, gg.X0, r, lane);
+        };
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (j0 + r <= j1) issue(j0 + r);
+            cp_async_commit();
+        }
+        P2<T> a0 = p2zero<T>(), a1 = p2zero<T>(), a2 = p2zero<T>();
+        P2<T> b0 = p2zero<T>(), b1 = p2zero<T>(), c0w = p2zero<T>(), c1w = p2zero<T>();
+        for (int j = j0; j <= j1; ++j) {
+            if (j + 4 <= j1) issue(j + 4);
+            cp_async_commit();
+            cp_async_wait<4>();
+            P2<T> a3;
+            ring_read<cplx<T>>(Kr, j, lane, a3.v0, a3.v1);
+            quad<T> q0, q1;
+            ring_read<quad<T>>(Qr, j - 1, lane, q0, q1);
+            const bool r1 = (unsigned)(j - 1) < (unsigned)n;
+            const P2<T> k1 = sl_row<T>(q0, q1, a2, a1, a3, ih2, wh, s, r1 && cin0, r1 && cin1);
+            ring_read<quad<T>>(Qr, j - 2, lane, q0, q1);
+            const bool r2 = (unsigned)(j - 2) < (unsigned)n;
+            const P2<T> k2 = sl_row<T>(q0, q1, b1, b0, k1, ih2, wh, s, r2 && cin0, r2 && cin1);
+            ring_read<quad<T>>(Qr, j - 3, lane, q0, q1);
+            const bool r3 = j - 3 >= gg.y0 && j - 3 < gg.y1;
+            const P2<T> k3 = sl_row<T>(q0, q1, c1w, c0w, k2, ih2, wh, s, r3 && cin0, r3 && cin1);
+            if (own) {
+                if (j - 1 >= gg.y0 && j - 1 < gg.y1) {
+                    const long long p = (long long)(j - 1) * pitch + col;
+                    if (cin0) k1o[p] = k1.v0;
+                    if (cin1) k1o[p + 1] = k1.v1;
+                }
+                if (j - 2 >= gg.y0 && j - 2 < gg.y1) {
+                    const long long p = (long long)(j - 2) * pitch + col;
+                    if (cin0) k2o[p] = k2.v0;
+                    if (cin1) k2o[p + 1] = k2.v1;
+                }
+                if (r3) {
+                    if (cin0) gram_acc<T>(ac, a0.v0, b0.v0, c1w.v0, k3.v0);
+                    if (cin1) gram_acc<T>(ac, a0.v1, b0.v1, c1w.v1, k3.v1);
+                }
+            }
+            a0 = a1; a1 = a2; a2 = a3;
+            b0 = b1; b1 = k1;
+            c0w = c1w; c1w = k2;
+        }
+        cp_async_wait<0>();
+        __syncwarp();
     }
+    gram_finish<T>(d, c, ac, sh, &flag);
 }
 
 // ------------------------------------------------------------ pre-smoothing update
-// From x0 = 0 with r0 = b in slot sb: x = s (c0 K0 + c1 K1 + c2 K2) to slot
-// sx; r = K0 - c0 K1 - c1 K2 - c2 K3 restricted by full weighting to slot
-// sc of the next level.  Tiles are CX x CY coarse nodes; the fine footprint
-// of a tile is (2CX+1) x (2CY+1) from fine node (2 I0, 2 J0).
+// From x0 = 0 with r0 = b in slot sb (= K0) and K1, K2 from the gram pass:
+// x = s (c0 K0 + c1 K1 + c2 K2) to slot sx; r = K0 - c0 K1 - c1 K2 - c2 K3
+// with K3 = s L K2 formed here, restricted by full weighting to slot sc of
+// the next level.  Tiles are CX x CY coarse nodes; the fine footprint of a
+// tile is (2CX+1) x (2CY+1) from fine node (2 I0, 2 J0); K2 is staged with a
+// one-node ring.  Double-buffered like the gram tiles.
 template <typename T, int CX, int CY>
 __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                int nseg, int sb, int sx, int sc) {
-    constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1;
-    constexpr int W0 = FW + 6, H0 = FH + 6, W1 = FW + 4, H1 = FH + 4, W2 = FW + 2, H2 = FH + 2;
+    constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1, W2 = FW + 2, H2 = FH + 2;
+    constexpr int NF = FW * FH;
     extern __shared__ __align__(16) unsigned char gs_smem[];
-    quad<T>* Qb = reinterpret_cast<quad<T>*>(gs_smem);            // [2][W1 H1]
-    cplx<T>* S0b = reinterpret_cast<cplx<T>*>(Qb + 2 * W1 * H1);   // [2][W0 H0]
-    cplx<T>* S1 = S0b + 2 * W0 * H0;
-    cplx<T>* S2 = S1 + W1 * H1;
-    cplx<T>* R = S2 + W2 * H2;
+    quad<T>* Qb = reinterpret_cast<quad<T>*>(gs_smem);            // [2][NF]
+    cplx<T>* K2b = reinterpret_cast<cplx<T>*>(Qb + 2 * NF);        // [2][W2 H2]
+    cplx<T>* K0b = K2b + 2 * W2 * H2;                              // [2][NF]
+    cplx<T>* K1b = K0b + 2 * NF;                                   // [2][NF]
+    cplx<T>* R = K1b + 2 * NF;                                     // [NF]
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) dc = D[d.coarse];
     __syncthreads();
-    const int n = d.n, pitch = d.pitch, nc = dc.n;
+    const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
     const int ntx = (nc + CX - 1) / CX, ntiles = ntx * ((nc + CY - 1) / CY);
-    const cplx<T>* r0 = slot<T>(d, sb);
+    const cplx<T>* k0g = slot<T>(d, sb);
+    const cplx<T>* k1g = slot<T>(d, SK1);
+    const cplx<T>* k2g = slot<T>(d, SK2);
     const quad<T>* coef = reinterpret_cast<const quad<T>*>(d.adr);
     cplx<T>* xs = slot<T>(d, sx);
     cplx<T>* out = slot<T>(dc, sc);
-    const int cpitch = dc.pitch;
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
     const T* scl = scalp<T>(d);
     const cplx<T> c0 = sload2<T>(scl, S::GC), c1 = sload2<T>(scl, S::GC + 2), c2 = sload2<T>(scl, S::GC + 4);
+    const cplx<T> sc0 = cscale<T>(c0, s), sc1 = cscale<T>(c1, s), sc2 = cscale<T>(c2, s);
     auto issue = [&](int t, int b) {
         const int fx0 = 2 * (t % ntx) * CX, fy0 = 2 * (t / ntx) * CY;
-        async_region<cplx<T>, W0, H0>(S0b + b * W0 * H0, r0, n, pitch, fx0 - 3, fy0 - 3);
-        async_region<quad<T>, W1, H1>(Qb + b * W1 * H1, coef, n, pitch, fx0 - 2, fy0 - 2);
+        async_region<cplx<T>, W2, H2>(K2b + b * W2 * H2, k2g, n, pitch, fx0 - 1, fy0 - 1);
+        async_region<cplx<T>, FW, FH>(K0b + b * NF, k0g, n, pitch, fx0, fy0);
+        async_region<cplx<T>, FW, FH>(K1b + b * NF, k1g, n, pitch, fx0, fy0);
+        async_region<quad<T>, FW, FH>(Qb + b * NF, coef, n, pitch, fx0, fy0);
     };
     int buf = 0;
     if (c.lb < ntiles) issue(c.lb, 0);
@@ -257,37 +371,31 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        const cplx<T>* S0 = S0b + buf * W0 * H0;
-        const quad<T>* Q = Qb + buf * W1 * H1;
+        const cplx<T>* K2s = K2b + buf * W2 * H2;
+        const cplx<T>* K0s = K0b + buf * NF;
+        const cplx<T>* K1s = K1b + buf * NF;
+        const quad<T>* Q = Qb + buf * NF;
         const int I0 = (t % ntx) * CX, J0 = (t / ntx) * CY;
         const int fx0 = 2 * I0, fy0 = 2 * J0;
         // fine nodes this tile writes (the last tile in a direction takes the rest)
         const int ox1 = (I0 + CX >= nc) ? n : 2 * (I0 + CX);
         const int oy1 = (J0 + CY >= nc) ? n : 2 * (J0 + CY);
-        sl_stage<T, W1, H1, W1, 0>(n, S0, S1, Q, fx0 - 2, fy0 - 2, ih2, wh, s);
-        __syncthreads();
-        sl_stage<T, W2, H2, W1, 1>(n, S1, S2, Q, fx0 - 1, fy0 - 1, ih2, wh, s);
-        __syncthreads();
 #pragma unroll
-        for (int k = 0; k < (FW * FH + NT - 1) / NT; ++k) {
+        for (int k = 0; k < (NF + NT - 1) / NT; ++k) {
             const int e = tid + k * NT;
-            if (e < FW * FH) {
+            if (e < NF) {
                 const int r = e / FW, cc = e - r * FW;
                 const int gi = fx0 + cc, gj = fy0 + r;
                 cplx<T> v = zero2<T>();
                 if (gi < n && gj < n) {
                     const int b2 = (r + 1) * W2 + cc + 1;
-                    const cplx<T> k0 = S0[(r + 3) * W0 + cc + 3], k1 = S1[(r + 2) * W1 + cc + 2], k2 = S2[b2];
-                    const cplx<T> k3 = sl_q<T>(Q[(r + 2) * W1 + cc + 2], S2, b2, W2, ih2, wh, s);
+                    const cplx<T> k0 = K0s[e], k1 = K1s[e], k2 = K2s[b2];
+                    const cplx<T> k3 = sl_q<T>(Q[e], K2s, b2, W2, ih2, wh, s);
                     v = csub<T>(k0, cmul<T>(c0, k1));
                     v = csub<T>(v, cmul<T>(c1, k2));
                     v = csub<T>(v, cmul<T>(c2, k3));
-                    if (gi < ox1 && gj < oy1) {
-                        cplx<T> xv = cmul<T>(c0, k0);
-                        xv = cfma<T>(c1, k1, xv);
-                        xv = cfma<T>(c2, k2, xv);
-                        xs[(long long)gj * pitch + gi] = cscale<T>(xv, s);
-                    }
+                    if (gi < ox1 && gj < oy1)
+                        xs[(long long)gj * pitch + gi] = cfma<T>(sc2, k2, cfma<T>(sc1, k1, cmul<T>(sc0, k0)));
                 }
                 R[e] = v;
             }
@@ -317,112 +425,61 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
 }
 
 // ------------------------------------------------------------ post-smoothing update
-// x = x' + s (c0 K0 + c1 K1 + c2 K2), r0 = K0 in slot sr0, x' in slot sxo
-// (flags & 1: x' = 0).  flags & 2 (level 2): u += exp(+i w phi) x instead of
-// writing x to SAX (Algorithm 1's u <- u + e after the ADR cycle).
-template <typename T, int TX, int TY>
+// x = x' + s (c0 K0 + c1 K1 + c2 K2) pointwise, K0 = r0 in slot sr0, x' in
+// slot sxo (flags & 1: x' = 0).  flags & 2 (level 2): u += exp(+i w phi) x
+// instead of writing x to SAX (Algorithm 1's u <- u + e after the ADR cycle).
+// Two nodes of a row per thread.
+template <typename T>
 __global__ void __launch_bounds__(NT) k_gs_post(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                 int nseg, int sr0, int sxo, int flags) {
-    constexpr int W0 = TX + 4, H0 = TY + 4, W1 = TX + 2, H1 = TY + 2;
-    static_assert((TX * TY) % NT == 0, "tile");
-    extern __shared__ __align__(16) unsigned char gs_smem[];
-    quad<T>* Qb = reinterpret_cast<quad<T>*>(gs_smem);            // [2][W1 H1]
-    cplx<T>* S0b = reinterpret_cast<cplx<T>*>(Qb + 2 * W1 * H1);   // [2][W0 H0]
-    cplx<T>* S1 = S0b + 2 * W0 * H0;
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + TX - 1) / TX, ntiles = ntx * ((n + TY - 1) / TY);
-    const cplx<T>* r0 = slot<T>(d, sr0);
-    const quad<T>* coef = reinterpret_cast<const quad<T>*>(d.adr);
+    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
+    const cplx<T>* k0 = slot<T>(d, sr0);
+    const cplx<T>* k1 = slot<T>(d, SK1);
+    const cplx<T>* k2 = slot<T>(d, SK2);
     const cplx<T>* xo = slot<T>(d, sxo);
     cplx<T>* xout = slot<T>(d, SAX);
     cplx<T>* u = slot<T>(d, SU);
     const cplx<T>* mod = reinterpret_cast<const cplx<T>*>(d.mod);
-    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
+    const T s = LC<T>::gs(d);
     const T* scl = scalp<T>(d);
     const cplx<T> c0 = cscale<T>(sload2<T>(scl, S::GC), s), c1 = cscale<T>(sload2<T>(scl, S::GC + 2), s),
                   c2 = cscale<T>(sload2<T>(scl, S::GC + 4), s);
     const bool xzero = flags & 1, modulate = flags & 2;
-    auto issue = [&](int t, int b) {
-        const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-        async_region<cplx<T>, W0, H0>(S0b + b * W0 * H0, r0, n, pitch, x0 - 2, y0 - 2);
-        async_region<quad<T>, W1, H1>(Qb + b * W1 * H1, coef, n, pitch, x0 - 1, y0 - 1);
-    };
-    int buf = 0;
-    if (c.lb < ntiles) issue(c.lb, 0);
-    cp_async_commit();
-    for (int t = c.lb; t < ntiles; t += c.nb) {
-        if (t + c.nb < ntiles) issue(t + c.nb, buf ^ 1);
-        cp_async_commit();
-        const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-        // pointwise operands of this tile, loaded while the tile copies land
-        cplx<T> xv[TX * TY / NT], uv[TX * TY / NT], mv[TX * TY / NT];
+    for (int e = c.lb * NT + tid; e < npairs; e += c.nb * NT) {
+        const int r = e / npr, q = e - r * npr;
+        const long long p = (long long)r * pitch + 2 * q;
+        const bool two = 2 * q + 1 < n;
+        const int m = two ? 2 : 1;
 #pragma unroll
-        for (int k = 0; k < TX * TY / NT; ++k) {
-            const int e = tid + k * NT;
-            const int r = e / TX, cc = e - r * TX;
-            const int gi = x0 + cc, gj = y0 + r;
-            xv[k] = uv[k] = mv[k] = zero2<T>();
-            if (gi < n && gj < n) {
-                const long long p = (long long)gj * pitch + gi;
-                if (!xzero) xv[k] = __ldg(xo + p);
-                if (modulate) {
-                    uv[k] = u[p];
-                    mv[k] = __ldg(mod + p);
-                }
+        for (int v = 0; v < 2; ++v) {
+            if (v < m) {
+                cplx<T> x = xzero ? zero2<T>() : __ldg(xo + p + v);
+                x = cfma<T>(c0, __ldg(k0 + p + v), x);
+                x = cfma<T>(c1, __ldg(k1 + p + v), x);
+                x = cfma<T>(c2, __ldg(k2 + p + v), x);
+                if (modulate) u[p + v] = cfma<T>(__ldg(mod + p + v), x, u[p + v]);
+                else xout[p + v] = x;
             }
         }
-        cp_async_wait<1>();
-        __syncthreads();
-        const cplx<T>* S0 = S0b + buf * W0 * H0;
-        const quad<T>* Q = Qb + buf * W1 * H1;
-        sl_stage<T, W1, H1, W1, 0>(n, S0, S1, Q, x0 - 1, y0 - 1, ih2, wh, s);
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < TX * TY / NT; ++k) {
-            const int e = tid + k * NT;
-            const int r = e / TX, cc = e - r * TX;
-            const int gi = x0 + cc, gj = y0 + r;
-            if (gi < n && gj < n) {
-                const long long p = (long long)gj * pitch + gi;
-                const int b1 = (r + 1) * W1 + cc + 1;
-                const cplx<T> k0 = S0[(r + 2) * W0 + cc + 2], k1 = S1[b1];
-                const cplx<T> k2 = sl_q<T>(Q[(r + 1) * W1 + cc + 1], S1, b1, W1, ih2, wh, s);
-                cplx<T> v = xv[k];
-                v = cfma<T>(c0, k0, v);
-                v = cfma<T>(c1, k1, v);
-                v = cfma<T>(c2, k2, v);
-                if (modulate) u[p] = cfma<T>(mv[k], v, uv[k]);
-                else xout[p] = v;
-            }
-        }
-        __syncthreads();
-        buf ^= 1;
     }
-    cp_async_wait<0>();
 }
 
-// dynamic shared memory of each kernel and candidate (two buffers of the
-// streamed tiles plus the on-chip stencil stages)
+// dynamic shared memory of each kernel and candidate
 template <typename T> constexpr int gs_gram_smem(int i) {
-    return (int)(sizeof(quad<T>) * 2 * (gs_gram_shape(i).x + 4) * (gs_gram_shape(i).y + 4) +
-                 sizeof(cplx<T>) * (2 * (gs_gram_shape(i).x + 6) * (gs_gram_shape(i).y + 6) +
-                                    (gs_gram_shape(i).x + 4) * (gs_gram_shape(i).y + 4) +
-                                    (gs_gram_shape(i).x + 2) * (gs_gram_shape(i).y + 2)));
+    return gs_gram_streaming(i)
+               ? gs_ring_bytes<T>(1, 1)
+               : (int)(sizeof(quad<T>) * 2 * (gs_gram_shape(i).x + 4) * (gs_gram_shape(i).y + 4) +
+                       sizeof(cplx<T>) * (2 * (gs_gram_shape(i).x + 6) * (gs_gram_shape(i).y + 6) +
+                                          (gs_gram_shape(i).x + 4) * (gs_gram_shape(i).y + 4) +
+                                          (gs_gram_shape(i).x + 2) * (gs_gram_shape(i).y + 2)));
 }
 template <typename T> constexpr int gs_pre_smem(int i) {
-    return (int)(sizeof(quad<T>) * 2 * (2 * gs_pre_shape(i).x + 5) * (2 * gs_pre_shape(i).y + 5) +
-                 sizeof(cplx<T>) * (2 * (2 * gs_pre_shape(i).x + 7) * (2 * gs_pre_shape(i).y + 7) +
-                                    (2 * gs_pre_shape(i).x + 5) * (2 * gs_pre_shape(i).y + 5) +
-                                    (2 * gs_pre_shape(i).x + 3) * (2 * gs_pre_shape(i).y + 3) +
-                                    (2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1)));
-}
-template <typename T> constexpr int gs_post_smem(int i) {
-    return (int)(sizeof(quad<T>) * 2 * (gs_post_shape(i).x + 2) * (gs_post_shape(i).y + 2) +
-                 sizeof(cplx<T>) * (2 * (gs_post_shape(i).x + 4) * (gs_post_shape(i).y + 4) +
-                                    (gs_post_shape(i).x + 2) * (gs_post_shape(i).y + 2)));
+    return (int)(sizeof(quad<T>) * 2 * (2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1) +
+                 sizeof(cplx<T>) * (2 * (2 * gs_pre_shape(i).x + 3) * (2 * gs_pre_shape(i).y + 3) +
+                                    5 * (2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1)));
 }
 
 }  // namespace wadr

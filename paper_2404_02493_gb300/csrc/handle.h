@@ -65,7 +65,7 @@ const char* kernel_kind_name(int k);
 
 // halo-tile candidates (index into the gs_*_shape tables) of one ADR launch
 struct TileChoice {
-    int gram = -1, pre = -1, post = -1;   // -1: default shape
+    int gram = -1, pre = -1;   // -1: default shape
 };
 
 std::string desc_key(const std::vector<int>& descs);

@@ -18,8 +18,10 @@ enum Slot : int {
     SAX = 4,  // ADR iterate
     SAB = 5,  // ADR right-hand side
     SV1 = 6,  // GMRES r0 of the post-smoother
-    STMP = 7, // scratch of the level operations
-    NSLOT = 8,
+    SK1 = 7,  // GMRES basis vectors K1 = s L r0, K2 = (s L)^2 r0
+    SK2 = 8,
+    STMP = 9, // scratch of the level operations
+    NSLOT = 10,
     NSLOT_L1 = 4
 };
 
@@ -81,6 +83,25 @@ __device__ __forceinline__ cplx<T> adr_pt(const quad<T>& q, T ih2, T wh, cplx<T>
     cplx<T> r = cmul<T>(dg, c);
     r.x += -ih2 * lap.x - wh * adv.y;
     r.y += -ih2 * lap.y + wh * adv.x;
+    return r;
+}
+
+// FP32: the same stencil in packed FP32x2 instructions (sm_100+), each
+// component rounded as the scalar operation.
+template <>
+__device__ __forceinline__ float2 adr_pt<float>(const quad<float>& q, float ih2, float wh, float2 c, float2 w,
+                                                float2 e, float2 s, float2 nn) {
+    const float aw = 2.f * fmaxf(q.x, 0.f), ae = -2.f * fminf(q.x, 0.f);
+    const float as = 2.f * fmaxf(q.y, 0.f), an = -2.f * fminf(q.y, 0.f);
+    const float2 lap = __fadd2_rn(__fadd2_rn(w, e), __fadd2_rn(s, nn));
+    float2 adv = __fmul2_rn(make_float2(aw, aw), w);
+    adv = __ffma2_rn(make_float2(ae, ae), e, adv);
+    adv = __ffma2_rn(make_float2(as, as), s, adv);
+    adv = __ffma2_rn(make_float2(an, an), nn, adv);
+    float2 r = __fmul2_rn(make_float2(q.z, q.z), c);
+    r = __ffma2_rn(make_float2(-q.w, q.w), make_float2(c.y, c.x), r);
+    r = __ffma2_rn(make_float2(-ih2, -ih2), lap, r);
+    r = __ffma2_rn(make_float2(-wh, wh), make_float2(adv.y, adv.x), r);
     return r;
 }
 

@@ -665,15 +665,13 @@ int mg_tile_shapes(const mg_handle* h, int inst, int level, int* out) {
     TileChoice tc;
     auto it = H.tiles.find(desc_key(ds));
     if (it != H.tiles.end()) tc = it->second;
-    if (H.p.tile_candidate >= 0) tc.gram = tc.pre = tc.post = H.p.tile_candidate;
-    const int g = tc.gram >= 0 ? tc.gram : GS_DEFAULT_GRAM, pr = tc.pre >= 0 ? tc.pre : GS_DEFAULT_PRE,
-              po = tc.post >= 0 ? tc.post : GS_DEFAULT_POST;
+    if (H.p.tile_candidate >= 0) tc.gram = tc.pre = H.p.tile_candidate;
+    const int g = tc.gram >= 0 ? tc.gram : GS_DEFAULT_GRAM, pr = tc.pre >= 0 ? tc.pre : GS_DEFAULT_PRE;
     out[0] = gs_gram_shape(g).x;
     out[1] = gs_gram_shape(g).y;
     out[2] = gs_pre_shape(pr).x;
     out[3] = gs_pre_shape(pr).y;
-    out[4] = gs_post_shape(po).x;
-    out[5] = gs_post_shape(po).y;
+    out[4] = gs_gram_streaming(g) ? 1 : 0;
     return MG_OK;
 }
 

@@ -1,6 +1,8 @@
 """Halo-tile candidates and the setup-time autotuner of the ADR GMRES(3)
-kernels: every candidate shape gives the oracle's cycle (ragged and even
-grid sizes included), and the autotuner only picks listed candidates."""
+kernels (shared-memory tiles and warp-streaming strips of the gram pass,
+footprint tiles of the pre-smoothing update): every candidate gives the
+oracle's cycle (ragged and even grid sizes, strips and tiles larger than the
+grid included), and the autotuner only picks listed candidates."""
 import numpy as np
 import pytest
 
@@ -10,7 +12,9 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-GRAM = [(32, 8), (32, 16), (64, 8), (64, 16)]
+# gram pass: shared-memory tiles (32 x 8, 32 x 16 nodes) or warp-streaming
+# strips of 56 result columns by 32 / 64 rows; pre-smoothing: coarse tiles
+GRAM = [(32, 8), (32, 16), (56, 32), (56, 64)]
 PRE = [(16, 8), (32, 8), (16, 16), (32, 4)]
 
 
@@ -41,7 +45,7 @@ def test_every_tile_candidate_matches_oracle_fp64(cand, n):
         ref = H.cycle(u, I.g)
         assert rel(uu, ref) < 1e-12, (cand, n, rel(uu, ref))
         sh = B.mg_tile_shapes(h, 0, 2)
-        assert sh["gram"] == GRAM[cand] and sh["pre"] == PRE[cand] and sh["post"] == GRAM[cand]
+        assert sh["gram"] == GRAM[cand] and sh["pre"] == PRE[cand] and sh["streaming"] == (cand >= 2)
     finally:
         B.mg_destroy(h)
 
@@ -73,7 +77,7 @@ def test_autotuner_picks_listed_candidates():
             L = B.mg_num_levels(ha, b)
             for l in range(2, L):
                 sh = B.mg_tile_shapes(ha, b, l)
-                assert sh["gram"] in GRAM and sh["post"] in GRAM and sh["pre"] in PRE
+                assert sh["gram"] in GRAM and sh["pre"] in PRE
             with pytest.raises(B.MgError):
                 B.mg_tile_shapes(ha, b, L)
         g = np.concatenate([(I.g / np.linalg.norm(I.g)).ravel() for I in insts]).astype(np.complex64)
