@@ -59,6 +59,8 @@ enum {
     MG_ENOMEM = -3,      /* device allocation failed */
     MG_ENOTCONV = -4,    /* mg_solve reached maxit */
     MG_EDIVERGED = -5,   /* residual not finite or grew by > 1e3 */
+    MG_ETIMEOUT = -6,    /* a device-side wait of a tile kernel expired (reported at the next
+                            synchronising call: mg_cycle with host buffers, mg_solve, mg_solve_end) */
     MG_EUNSUPPORTED = -7 /* option not implemented for this handle */
 };
 

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-MG_OK, MG_EINVAL, MG_ECUDA, MG_ENOMEM, MG_ENOTCONV, MG_EDIVERGED, MG_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -7
+MG_OK, MG_EINVAL, MG_ECUDA, MG_ENOMEM, MG_ENOTCONV, MG_EDIVERGED, MG_ETIMEOUT, MG_EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 MG_BC = {"dirichlet": 0, "abc1": 1, "sponge": 2}
 MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_OUTER = {"stationary": 0, "ir": 1, "fgmres": 2}

@@ -109,6 +109,8 @@ struct LevelDesc {
     double* fs;             // outer: FGMRES scalars
     double2* fpart;         // outer: FGMRES reduction partials [MAXB][NVF]
     double* est;            // outer: |gamma_{j+1}| of this instance (contiguous over instances)
+    const void* tm;         // tensor maps of the tile kernels (MapId order, 128 B each)
+    unsigned* err;          // handle error word (device-side wait expiry)
 };
 
 struct Seg {

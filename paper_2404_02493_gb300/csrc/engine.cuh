@@ -40,6 +40,51 @@ struct Engine : EngineBase {
         kern<<<(t).nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, (t).d, (t).nseg, __VA_ARGS__);            \
     }, (t).pts)
 
+    // Dynamic shared memory opt-in and resident blocks per SM x SM count of a
+    // tile kernel (cached per kernel): the block count of its launches, so
+    // that one wave of blocks loops over the tiles (double-buffered).
+    template <class K>
+    static int occ_cap(K kern, int smem, int threads = NT) {
+        static std::map<const void*, int> caps;
+        auto it = caps.find((const void*)kern);
+        if (it != caps.end()) return it->second;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int nb = 0, dev = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        return caps[(const void*)kern] = std::max(1, nb) * std::max(1, nsm);
+    }
+    void launch_cheb(Handle& H, const std::vector<int>& ds, double bpp, int sin, int sout, int m, int flags,
+                     cudaStream_t st) {
+        auto kern = k_cheb_step<T>;
+        const int smem = cheb_smem<T>();
+        const SegTable& t = H.seg_tiles(ds, CTX, CTY, false, occ_cap(kern, smem));
+        go(H, st, KK_CHEB, bpp * (double)t.pts, [&] {
+            kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sin, sout, m, flags);
+        }, t.pts);
+    }
+    template <int MODE>
+    void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
+                         cudaStream_t st) {
+        auto kern = k_restrict<T, MODE>;
+        const int smem = restrict_smem<T>();
+        const SegTable& t = H.seg_tiles(ds, RCX, RCY, true, occ_cap(kern, smem));
+        go(H, st, kind, bpp * (double)t.pts, [&] {
+            kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sx, sb, sc, uzero);
+        }, t.pts);
+    }
+    template <int MODE>
+    void launch_prolong(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sc, int sb, int sout,
+                        int sxo, int xzero, cudaStream_t st) {
+        auto kern = k_prolong<T, MODE>;
+        const int smem = prolong_smem<T, MODE>();
+        const SegTable& t = H.seg_tiles(ds, PTX, PTY, false, occ_cap(kern, smem));
+        go(H, st, kind, bpp * (double)t.pts, [&] {
+            kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sx, sc, sb, sout, sxo, xzero);
+        }, t.pts);
+    }
+
     std::vector<int> descs(Handle& H, int level, const std::vector<int>& I) {
         std::vector<int> d;
         for (int b : I) d.push_back(H.inst[b].lv[level - 1].desc);
@@ -67,7 +112,7 @@ struct Engine : EngineBase {
     // ------------------------------------------------------------ pieces
     // q Chebyshev steps; from_zero: the first step starts from x = 0.  The
     // output slots alternate so that the final iterate lands in SU.
-    void cheb_steps(Handle& H, const SegTable& t, int q, int xin, bool from_zero, cudaStream_t st) {
+    void cheb_steps(Handle& H, const std::vector<int>& ds, int q, int xin, bool from_zero, cudaStream_t st) {
         int cur = xin;
         int out = from_zero ? ((q & 1) ? SU : SX2) : (xin == SU ? SX2 : SU);
         for (int m = 0; m < q; ++m) {
@@ -75,7 +120,7 @@ struct Engine : EngineBase {
             const int flags = (xz ? 1 : 0) | (last ? 2 : 0);
             // reads x (unless zero), g, k, d (m > 0); writes x, d (unless last)
             const double bpp = (xz ? 0 : C) + C + R + (m > 0 ? C : 0) + C + (last ? 0 : C);
-            LAUNCH(KK_CHEB, t, bpp, k_cheb_step<T>, cur, out, m, flags);
+            launch_cheb(H, ds, bpp, cur, out, m, flags, st);
             cur = out;
             out = (cur == SU) ? SX2 : SU;
         }
@@ -247,12 +292,11 @@ struct Engine : EngineBase {
         if (!co.empty()) coarse_solve(H, co, l, 1, st);
         if (rest.empty()) return;
         const std::vector<int> ds = descs(H, l, rest);
-        const SegTable& t = H.seg(ds, false, kPts);
         const TileChoice tc = tiles_of(H, ds);
         gs_gram(H, ds, tc.gram, SAB, st);   // pre-smoothing from x = 0: r0 = b
         gs_pre(H, ds, tc.pre, st);          // x to SAX, restricted residual to SAB of l+1
         adrv(H, l + 1, rest, false, st);
-        LAUNCH(KK_PROLONG_ADR, t, 4 * C + C / 4 + Q, (k_prolong<T, PMODE_ADR>), SAX, SAX, SAB, SV1, SD, 0);
+        launch_prolong<PMODE_ADR>(H, ds, KK_PROLONG_ADR, 4 * C + C / 4 + Q, SAX, SAX, SAB, SV1, SD, 0, st);
         gs_gram(H, ds, tc.gram, SV1, st);   // post-smoothing from x' (r0 = b - L x')
         gs_post(H, ds, SV1, SD, modulate ? 2 : 0, st);
     }
@@ -274,25 +318,24 @@ struct Engine : EngineBase {
             if (H.p.coarse == MG_COARSE_LU) {
                 coarse_solve(H, co, l, 0, st);
             } else {
-                const SegTable& tc = H.seg(descs(H, l, co), false, kPts);
-                cheb_steps(H, tc, H.p.coarse_cheb_iters, SU, true, st);
+                cheb_steps(H, descs(H, l, co), H.p.coarse_cheb_iters, SU, true, st);
             }
         }
         if (rest.empty()) return;
-        const SegTable& t = H.seg(descs(H, l, rest), false, kPts);
+        const std::vector<int> ds = descs(H, l, rest);
         const int q = H.p.cheb_iters;
         const bool smooth = (l != 3);      // no smoothing on level 3 (Section 3.1.3)
-        if (smooth) cheb_steps(H, t, q, SU, true, st);
-        LAUNCH(KK_RESTRICT_HELM, t, smooth ? 2 * C + R + C / 4 : C + C / 4, (k_restrict<T, MODE_HELM>), SU, SG,
-               SG, smooth ? 0 : 1);
+        if (smooth) cheb_steps(H, ds, q, SU, true, st);
+        launch_restrict<MODE_HELM>(H, ds, KK_RESTRICT_HELM, smooth ? 2 * C + R + C / 4 : C + C / 4, SU, SG,
+                                   SG, smooth ? 0 : 1, st);
         wave(H, l + 1, rest, st);
         if (!smooth) {
-            LAUNCH(KK_PROLONG_ADD, t, C + C / 4, (k_prolong<T, PMODE_ADD>), SU, SU, SG, SU, SU, 1);
+            launch_prolong<PMODE_ADD>(H, ds, KK_PROLONG_ADD, C + C / 4, SU, SU, SG, SU, SU, 1, st);
             return;
         }
         const int out = (q & 1) ? SX2 : SU;
-        LAUNCH(KK_PROLONG_ADD, t, 2 * C + C / 4, (k_prolong<T, PMODE_ADD>), SU, SU, SG, out, out, 0);
-        cheb_steps(H, t, q, out, false, st);
+        launch_prolong<PMODE_ADD>(H, ds, KK_PROLONG_ADD, 2 * C + C / 4, SU, SU, SG, out, out, 0, st);
+        cheb_steps(H, ds, q, out, false, st);
         if (l == 2 && H.p.adr && H.p.M > 0) adr_corrections(H, rest, H.p.M, st);
     }
 
@@ -307,15 +350,16 @@ struct Engine : EngineBase {
     void cycle(Handle& H, bool uzero, cudaStream_t st) override {
         H.launches_cycle = 0;   // recounted on every emission
         std::vector<int> I = all(H);
-        const SegTable& t = H.seg(descs(H, 1, I), false, kPts);
+        const std::vector<int> ds1 = descs(H, 1, I);
+        const SegTable& t = H.seg(ds1, false, kPts);
         if (uzero) {
-            LAUNCH(KK_RESTRICT_JAC0, t, 2 * C + R + C / 4, (k_restrict<T, MODE_JAC0>), SU, SG, SG, 1);
+            launch_restrict<MODE_JAC0>(H, ds1, KK_RESTRICT_JAC0, 2 * C + R + C / 4, SU, SG, SG, 1, st);
         } else {
             LAUNCH(KK_JACOBI, t, 3 * C + R, k_jacobi<T>, SX2, SG, SU, 0);
-            LAUNCH(KK_RESTRICT_HELM, t, 2 * C + R + C / 4, (k_restrict<T, MODE_HELM>), SU, SG, SG, 0);
+            launch_restrict<MODE_HELM>(H, ds1, KK_RESTRICT_HELM, 2 * C + R + C / 4, SU, SG, SG, 0, st);
         }
         wave(H, 2, I, st);
-        LAUNCH(KK_PROLONG_JAC, t, 3 * C + C / 4 + R, (k_prolong<T, PMODE_JAC>), SU, SU, SG, SD, SD, 0);
+        launch_prolong<PMODE_JAC>(H, ds1, KK_PROLONG_JAC, 3 * C + C / 4 + R, SU, SU, SG, SD, SD, 0, st);
     }
 
     const SegTable& outer_tab(Handle& H) {
@@ -408,10 +452,10 @@ struct Engine : EngineBase {
             k_residual<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SG, SD, 0);
             return SD;
         case OP_RESTRICT:
-            k_restrict<T, MODE_HELM><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SG, SG, 0);
+            launch_restrict<MODE_HELM>(H, descs(H, level, I), KK_RESTRICT_HELM, 0, SU, SG, SG, 0, st);
             return SG;   // on level+1
         case OP_PROLONG:
-            k_prolong<T, PMODE_ADD><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SU, SG, SD, SD, 0);
+            launch_prolong<PMODE_ADD>(H, descs(H, level, I), KK_PROLONG_ADD, 0, SU, SU, SG, SD, SD, 0, st);
             return SD;
         case OP_JACOBI:
             k_jacobi<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SX2, SG, SU, 0);
@@ -421,7 +465,7 @@ struct Engine : EngineBase {
             int cur = SU, out = SX2;
             for (int m = 0; m < a0; ++m) {
                 int flags = (m == a0 - 1 ? 2 : 0);
-                k_cheb_step<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, cur, out, m, flags);
+                launch_cheb(H, descs(H, level, I), 0, cur, out, m, flags, st);
                 cur = out;
                 out = (cur == SU) ? SX2 : SU;
             }

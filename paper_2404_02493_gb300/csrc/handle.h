@@ -83,6 +83,8 @@ struct Handle {
     double* scal = nullptr;         // [ndesc + ninst][S::SIZE]
     double2* part = nullptr;        // [ndesc + ninst][MAXB][MAXDOT]
     unsigned* counter = nullptr;    // [ndesc + ninst][NCOUNTERS]
+    void* tmaps = nullptr;          // [ndesc][NMAP] tensor maps of the tile kernels
+    unsigned* err = nullptr;        // device error word (bounded waits that expired)
     std::map<std::string, SegTable> segs;
     std::map<std::string, TileChoice> tiles;  // per ADR launch (desc_key), from the autotuner
     std::vector<void*> allocs;      // everything cudaMalloc'ed
@@ -109,6 +111,7 @@ struct Handle {
     cudaGraphExec_t g_fgiter = nullptr;
     // pinned host scratch for scalars
     double* hpin = nullptr;
+    unsigned* herr = nullptr;               // pinned copy of the device error word
     std::string last_error;
 
     void* alloc(size_t bytes);

@@ -5,6 +5,7 @@
 // slots of the (instance, level) its block belongs to.  Blocks are 32 x 8.
 #pragma once
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace wadr {
 
@@ -243,7 +244,9 @@ __device__ __forceinline__ void load_region(cplx<T>* sm, const cplx<T>* __restri
 template <int B>
 __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, bool ok) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    if (B == 8)
+    if (B == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 4 : 0));
+    else if (B == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 8 : 0));
     else
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 16 : 0));
@@ -254,8 +257,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <typename E>
 __device__ __forceinline__ void cp_async_elem(E* sdst, const E* gsrc, bool ok) {
-    static_assert(sizeof(E) == 8 || sizeof(E) == 16 || sizeof(E) == 32, "element size");
-    if constexpr (sizeof(E) == 8) {
+    static_assert(sizeof(E) == 4 || sizeof(E) == 8 || sizeof(E) == 16 || sizeof(E) == 32, "element size");
+    if constexpr (sizeof(E) == 4) {
+        cp_async<4>(sdst, gsrc, ok);
+    } else if constexpr (sizeof(E) == 8) {
         cp_async<8>(sdst, gsrc, ok);
     } else if constexpr (sizeof(E) == 16) {
         cp_async<16>(sdst, gsrc, ok);
@@ -283,74 +288,154 @@ __device__ __forceinline__ void async_region(E* sm, const E* __restrict__ g, int
     }
 }
 
+// Double-buffered tile loop of a block: issue(t, b) issues the copies of
+// tile t into buffer b, body(t, b) computes tile t once its copies landed;
+// the next tile's copies are in flight meanwhile.
+template <class Issue, class Body>
+__device__ __forceinline__ void tile_loop(int lb, int nb, int ntiles, Issue&& issue, Body&& body) {
+    int buf = 0;
+    if (lb < ntiles) issue(lb, 0);
+    cp_async_commit();
+    for (int t = lb; t < ntiles; t += nb) {
+        if (t + nb < ntiles) issue(t + nb, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        body(t, buf);
+        __syncthreads();
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// Carve typed arrays out of a dynamic shared-memory block (16-byte aligned
+// pieces).
+struct SmemCarve {
+    unsigned char* p;
+    template <typename E>
+    __device__ __forceinline__ E* take(int count) {
+        E* r = reinterpret_cast<E*>(p);
+        p += ((size_t)count * sizeof(E) + 15) / 16 * 16;
+        return r;
+    }
+};
+template <typename E> __host__ __device__ constexpr int smem_piece(int count) {
+    return (int)(((size_t)count * sizeof(E) + 15) / 16 * 16);
+}
+
 // ----------------------------------------------------------- Chebyshev step
 // One step of the Chebyshev semi-iteration on A^*A x = A^*g (eq. cheb),
 // three-term form: s = A^*(g - A x);  d = c1[m] d + c2[m] s;  x += d.
 // Flags: 1 = x is zero on entry (first pre-smoothing step from zero),
 //        2 = do not write d (last step).
+// Tiles of CTX x CTY nodes; x (2-node halo), g, k, the sponge term (1-node
+// halo) and d arrive by TMA into two alternating buffers.
 constexpr int CTX = 32, CTY = 16;
+constexpr int CXW = CTX + 4, CXH = CTY + 4;     // x box, from (x0-2, y0-2)
+constexpr int CGW = CTX + 4, CGH = CTY + 2;     // g box, from (x0-2, y0-1)
+constexpr int CKW = CTX + 8, CKH = CTY + 2;     // k box, from (x0-4, y0-1)
+constexpr int CRW = CTX + 2, CRH = CTY + 2;     // residual ring region
+template <typename T> __host__ __device__ constexpr int cheb_smem() {
+    return 128 + 2 * (tma_piece<cplx<T>>(CXW * CXH) + tma_piece<cplx<T>>(CGW * CGH) + 2 * tma_piece<T>(CKW * CKH) +
+                      tma_piece<cplx<T>>(CTX * CTY)) +
+           tma_piece<cplx<T>>(CRW * CRH);
+}
 template <typename T>
 __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                   int nseg, int sxin, int sxout, int m, int flags) {
+    extern __shared__ unsigned char wk_smem[];
+    TmaCarve cv(wk_smem);
+    cplx<T>* Xb[2]; cplx<T>* Gb[2]; T* Kb[2]; T* Sb[2]; cplx<T>* Db[2];
+    for (int b = 0; b < 2; ++b) {
+        Xb[b] = cv.take<cplx<T>>(CXW * CXH);
+        Gb[b] = cv.take<cplx<T>>(CGW * CGH);
+        Kb[b] = cv.take<T>(CKW * CKH);
+        Sb[b] = cv.take<T>(CKW * CKH);
+        Db[b] = cv.take<cplx<T>>(CTX * CTY);
+    }
+    cplx<T>* Tt = cv.take<cplx<T>>(CRW * CRH);
     __shared__ LevelDesc d;
-    __shared__ cplx<T> X[(CTY + 4) * (CTX + 4)];
-    __shared__ cplx<T> Tt[(CTY + 2) * (CTX + 2)];
-    __shared__ T K[(CTY + 2) * (CTX + 2)];
+    __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
+    TmaPipe pipe;
+    pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + CTX - 1) / CTX, nty = (n + CTY - 1) / CTY;
-    const cplx<T>* x = slot<T>(d, sxin);
+    const int ntx = (n + CTX - 1) / CTX, ntiles = ntx * ((n + CTY - 1) / CTY);
     cplx<T>* xo_ = slot<T>(d, sxout);
-    const cplx<T>* g = slot<T>(d, SG);
     cplx<T>* dd = slot<T>(d, SD);
+    const bool hs = d.sig != nullptr;
     const bool xzero = flags & 1;
     const T c1 = scalp<T>(d)[S::CHEB_C1 + m], c2 = scalp<T>(d)[S::CHEB_C2 + m];
     const T ih2 = LC<T>::ih2(d);
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+    const unsigned bytes = (xzero ? 0u : (unsigned)(CXW * CXH * sizeof(cplx<T>))) +
+                           (unsigned)(CGW * CGH * sizeof(cplx<T>)) + (unsigned)(CKW * CKH * sizeof(T)) * (hs ? 2u : 1u) +
+                           (c1 != T(0) ? (unsigned)(CTX * CTY * sizeof(cplx<T>)) : 0u);
+    auto issue = [&](int t, int b) {
+        if (tid != 0) return;
         const int x0 = (t % ntx) * CTX, y0 = (t / ntx) * CTY;
-        __syncthreads();
-        if (!xzero) load_region<T>(X, x, n, pitch, x0 - 2, y0 - 2, CTX + 4, CTY + 4);
-        for (int e = tid; e < (CTX + 2) * (CTY + 2); e += NT) {
-            const int r = e / (CTX + 2), cc = e - r * (CTX + 2);
-            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
-            K[e] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? load_k<T>(d, gi, gj) : T(0);
-        }
-        __syncthreads();
-        // t = g - A x on the tile plus a one-node ring
-        for (int e = tid; e < (CTX + 2) * (CTY + 2); e += NT) {
-            const int r = e / (CTX + 2), cc = e - r * (CTX + 2);
-            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
-            cplx<T> tv = zero2<T>();
-            if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
-                tv = __ldg(g + (long long)gj * pitch + gi);
-                if (!xzero) {
-                    const int b = (r + 1) * (CTX + 4) + cc + 1;
-                    cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - (CTX + 4)], X[b + (CTX + 4)]));
-                    cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[e], load_sig<T>(d, gi, gj));
-                    tv = csub<T>(tv, cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
+        pipe.expect(b, bytes);
+        if (!xzero) tma_load_3d(Xb[b], tmap(d, MC_CHEB_X), 2 * (x0 - 2), y0 - 2, sxin, &bars[b]);
+        tma_load_3d(Gb[b], tmap(d, MC_CHEB_G), 2 * (x0 - 2), y0 - 1, SG, &bars[b]);
+        tma_load_2d(Kb[b], tmap(d, MK_CHEB), x0 - 4, y0 - 1, &bars[b]);
+        if (hs) tma_load_2d(Sb[b], tmap(d, MS_CHEB), x0 - 4, y0 - 1, &bars[b]);
+        if (c1 != T(0)) tma_load_3d(Db[b], tmap(d, MC_CHEB_D), 2 * x0, y0, SD, &bars[b]);
+    };
+    int buf = 0;
+    if (c.lb < ntiles) issue(c.lb, 0);
+    for (int t = c.lb; t < ntiles; t += c.nb) {
+        if (t + c.nb < ntiles) issue(t + c.nb, buf ^ 1);
+        if (!pipe.wait(buf, d.err)) return;
+        const int x0 = (t % ntx) * CTX, y0 = (t / ntx) * CTY;
+        const cplx<T>* X = Xb[buf];
+        const T* K = Kb[buf];
+        const T* Sg2 = Sb[buf];
+        // t = g - A x on the tile plus a one-node ring (ring node (r, cc)
+        // is x box (r+1, cc+1), g box (r, cc+1), k box (r, cc+3))
+#pragma unroll
+        for (int k = 0; k < (CRW * CRH + NT - 1) / NT; ++k) {
+            const int e = tid + k * NT;
+            if (e < CRW * CRH) {
+                const int r = e / CRW, cc = e - r * CRW;
+                const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
+                cplx<T> tv = zero2<T>();
+                if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+                    tv = Gb[buf][r * CGW + cc + 1];
+                    if (!xzero) {
+                        const int q = (r + 1) * CXW + cc + 1;
+                        const cplx<T> sn = cadd<T>(cadd<T>(X[q - 1], X[q + 1]), cadd<T>(X[q - CXW], X[q + CXW]));
+                        const int qk = r * CKW + cc + 3;
+                        const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[qk], hs ? Sg2[qk] : T(0));
+                        tv = csub<T>(tv, cscale<T>(csub<T>(cmul<T>(dg, X[q]), sn), ih2));
+                    }
                 }
+                Tt[e] = tv;
             }
-            Tt[e] = tv;
         }
         __syncthreads();
         // s = A^H t, update d and x on the tile
-        for (int e = tid; e < CTX * CTY; e += NT) {
+#pragma unroll
+        for (int k = 0; k < CTX * CTY / NT; ++k) {
+            const int e = tid + k * NT;
             const int r = e / CTX, cc = e - r * CTX;
             const int gi = x0 + cc, gj = y0 + r;
-            if (gi >= n || gj >= n) continue;
-            const int b = (r + 1) * (CTX + 2) + cc + 1;
-            cplx<T> s = cadd<T>(cadd<T>(Tt[b - 1], Tt[b + 1]), cadd<T>(Tt[b - (CTX + 2)], Tt[b + (CTX + 2)]));
-            cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[b], load_sig<T>(d, gi, gj));
-            dg.y = -dg.y;
-            cplx<T> sv = cscale<T>(csub<T>(cmul<T>(dg, Tt[b]), s), ih2);
-            const long long p = (long long)gj * pitch + gi;
-            cplx<T> dn = cscale<T>(sv, c2);
-            if (c1 != T(0)) dn = cadd<T>(dn, cscale<T>(__ldg(dd + p), c1));
-            cplx<T> xo = xzero ? zero2<T>() : X[(r + 2) * (CTX + 4) + cc + 2];
-            xo_[p] = cadd<T>(xo, dn);
-            if (!(flags & 2)) dd[p] = dn;
+            if (gi < n && gj < n) {
+                const int q = (r + 1) * CRW + cc + 1;
+                const cplx<T> sn = cadd<T>(cadd<T>(Tt[q - 1], Tt[q + 1]), cadd<T>(Tt[q - CRW], Tt[q + CRW]));
+                const int qk = (r + 1) * CKW + cc + 4;
+                cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[qk], hs ? Sg2[qk] : T(0));
+                dg.y = -dg.y;
+                const cplx<T> sv = cscale<T>(csub<T>(cmul<T>(dg, Tt[q]), sn), ih2);
+                const long long p = (long long)gj * pitch + gi;
+                cplx<T> dn = cscale<T>(sv, c2);
+                if (c1 != T(0)) dn = cadd<T>(dn, cscale<T>(Db[buf][e], c1));
+                const cplx<T> xv = xzero ? zero2<T>() : X[(r + 2) * CXW + cc + 2];
+                xo_[p] = cadd<T>(xv, dn);
+                if (!(flags & 2)) dd[p] = dn;
+            }
         }
+        __syncthreads();
+        buf ^= 1;
     }
 }
 
@@ -360,96 +445,145 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
 //
 // MODE_HELM:  r = g - A u          (uzero flag: r = g)
 // MODE_JAC0:  u1 = w D^{-1} g (written to slot su), r = g - A u1
-// MODE_ADR:   r = b - L x          (ADR operator, slots sx/sb)
-// The coarse result goes to slot `sc` of the next level.
-enum RMode : int { MODE_HELM = 0, MODE_JAC0 = 1, MODE_ADR = 2 };
+// The coarse result goes to slot `sc` of the next level.  u, g, k (and the
+// sponge term) on the footprint plus a one-node ring arrive by TMA into two
+// alternating buffers.
+enum RMode : int { MODE_HELM = 0, MODE_JAC0 = 1 };
 constexpr int RCX = 32, RCY = 8;
 constexpr int RFW = 2 * RCX + 1, RFH = 2 * RCY + 1;   // footprint
 constexpr int RHW = RFW + 2, RHH = RFH + 2;            // footprint + ring
+constexpr int RXW = RFW + 3, RKW = RFW + 7;            // boxes from (fx0-2, fy0-1), (fx0-4, fy0-1)
+template <typename T> __host__ __device__ constexpr int restrict_smem() {
+    return 128 + 2 * (2 * tma_piece<cplx<T>>(RXW * RHH) + 2 * tma_piece<T>(RKW * RHH)) + tma_piece<cplx<T>>(RHW * RHH) +
+           tma_piece<cplx<T>>(RFW * RFH);
+}
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                  int nseg, int sx, int sb, int sc, int uzero) {
+    extern __shared__ unsigned char wk_smem[];
+    TmaCarve cv(wk_smem);
+    cplx<T>* Xb[2]; cplx<T>* Bb[2]; T* Kb[2]; T* Sb[2];
+    for (int b = 0; b < 2; ++b) {
+        Xb[b] = cv.take<cplx<T>>(RXW * RHH);
+        Bb[b] = cv.take<cplx<T>>(RXW * RHH);
+        Kb[b] = cv.take<T>(RKW * RHH);
+        Sb[b] = cv.take<T>(RKW * RHH);
+    }
+    cplx<T>* U = cv.take<cplx<T>>(RHW * RHH);
+    cplx<T>* R = cv.take<cplx<T>>(RFW * RFH);
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
-    __shared__ cplx<T> X[RHW * RHH];
-    __shared__ cplx<T> R[RFW * RFH];
+    __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) dc = D[d.coarse];
-    __syncthreads();
+    TmaPipe pipe;
+    pipe.init(bars);
     const int n = d.n, pitch = d.pitch, nc = dc.n;
-    const int ntx = (nc + RCX - 1) / RCX, nty = (nc + RCY - 1) / RCY;
-    const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
+    const int ntx = (nc + RCX - 1) / RCX, ntiles = ntx * ((nc + RCY - 1) / RCY);
+    const T ih2 = LC<T>::ih2(d);
     cplx<T>* xs = slot<T>(d, sx);
-    const cplx<T>* bs = slot<T>(d, sb);
     cplx<T>* out = slot<T>(dc, sc);
+    const bool hs = d.sig != nullptr;
     const T wj = (MODE == MODE_JAC0) ? scalp<T>(d)[S::OMEGA_J] : T(0);
     const T h2 = LC<T>::h(d) * LC<T>::h(d);
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+    const bool needx = (MODE == MODE_HELM) && !uzero;
+    const bool needk = needx || MODE == MODE_JAC0;
+    const unsigned bytes = (unsigned)(RXW * RHH * sizeof(cplx<T>)) * (needx ? 2u : 1u) +
+                           (needk ? (unsigned)(RKW * RHH * sizeof(T)) * (hs ? 2u : 1u) : 0u);
+    auto issue = [&](int t, int b) {
+        if (tid != 0) return;
+        const int fx0 = 2 * (t % ntx) * RCX, fy0 = 2 * (t / ntx) * RCY;
+        pipe.expect(b, bytes);
+        if (needx) tma_load_3d(Xb[b], tmap(d, MC_RESTR), 2 * (fx0 - 2), fy0 - 1, sx, &bars[b]);
+        tma_load_3d(Bb[b], tmap(d, MC_RESTR), 2 * (fx0 - 2), fy0 - 1, sb, &bars[b]);
+        if (needk) {
+            tma_load_2d(Kb[b], tmap(d, MK_RESTR), fx0 - 4, fy0 - 1, &bars[b]);
+            if (hs) tma_load_2d(Sb[b], tmap(d, MS_RESTR), fx0 - 4, fy0 - 1, &bars[b]);
+        }
+    };
+    int buf = 0;
+    if (c.lb < ntiles) issue(c.lb, 0);
+    for (int t = c.lb; t < ntiles; t += c.nb) {
+        if (t + c.nb < ntiles) issue(t + c.nb, buf ^ 1);
+        if (!pipe.wait(buf, d.err)) return;
         const int I0 = (t % ntx) * RCX, J0 = (t / ntx) * RCY;
-        const int fx0 = 2 * I0, fy0 = 2 * J0;   // footprint origin (fine)
+        const int fx0 = 2 * I0, fy0 = 2 * J0;
         // own fine rows/cols for writes of the fine iterate
         const int ox1 = (I0 + RCX >= nc) ? n : 2 * (I0 + RCX);
         const int oy1 = (J0 + RCY >= nc) ? n : 2 * (J0 + RCY);
-        __syncthreads();
-        if (MODE == MODE_HELM || MODE == MODE_ADR) {
-            if (!uzero) load_region<T>(X, xs, n, pitch, fx0 - 1, fy0 - 1, RHW, RHH);
-        } else if (MODE == MODE_JAC0) {
+        // ring node (r, cc) (origin fx0-1, fy0-1): complex box (r, cc+1), real box (r, cc+3)
+        const cplx<T>* X = Xb[buf];
+        int xw = RXW, xo = 1;
+        const cplx<T>* Bv = Bb[buf];
+        const T* K = Kb[buf];
+        const T* Sg2 = Sb[buf];
+        if (MODE == MODE_JAC0) {
             // u1 = w D^{-1} g on footprint + ring
-            for (int e = tid; e < RHW * RHH; e += NT) {
-                const int r = e / RHW, cc = e - r * RHW;
-                const int gi = fx0 - 1 + cc, gj = fy0 - 1 + r;
-                cplx<T> v = zero2<T>();
-                if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
-                    const long long p = (long long)gj * pitch + gi;
-                    cplx<T> gv = __ldg(bs + p);
-                    cplx<T> dg = helm_diag_at<T>(d, gi, gj);
-                    const T den = dg.x * dg.x + dg.y * dg.y;
-                    v = cscale<T>(mk<T>((gv.x * dg.x + gv.y * dg.y) / den, (gv.y * dg.x - gv.x * dg.y) / den), wj * h2);
-                    if (gi >= fx0 && gi < ox1 && gj >= fy0 && gj < oy1) xs[p] = v;
+#pragma unroll
+            for (int k = 0; k < (RHW * RHH + NT - 1) / NT; ++k) {
+                const int e = tid + k * NT;
+                if (e < RHW * RHH) {
+                    const int r = e / RHW, cc = e - r * RHW;
+                    const int gi = fx0 - 1 + cc, gj = fy0 - 1 + r;
+                    cplx<T> v = zero2<T>();
+                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+                        const cplx<T> gv = Bv[r * RXW + cc + 1];
+                        const int qk = r * RKW + cc + 3;
+                        const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[qk], hs ? Sg2[qk] : T(0));
+                        const T den = dg.x * dg.x + dg.y * dg.y;
+                        v = cscale<T>(mk<T>((gv.x * dg.x + gv.y * dg.y) / den, (gv.y * dg.x - gv.x * dg.y) / den),
+                                      wj * h2);
+                        if (gi >= fx0 && gi < ox1 && gj >= fy0 && gj < oy1) xs[(long long)gj * pitch + gi] = v;
+                    }
+                    U[e] = v;
                 }
-                X[e] = v;
             }
+            __syncthreads();
+            X = U;
+            xw = RHW;
+            xo = 0;
         }
-        __syncthreads();
         // fine residual on the footprint
-        for (int e = tid; e < RFW * RFH; e += NT) {
-            const int r = e / RFW, cc = e - r * RFW;
-            const int gi = fx0 + cc, gj = fy0 + r;
-            cplx<T> v = zero2<T>();
-            if (gi < n && gj < n) {
-                const long long p = (long long)gj * pitch + gi;
-                {
-                    v = __ldg(bs + p);
-                    if (!(uzero && MODE != MODE_JAC0)) {
-                        const int b = (r + 1) * RHW + cc + 1;
-                        if (MODE == MODE_ADR) {
-                            v = csub<T>(v, adr_pt<T>(load_adr<T>(d, p), ih2, wh, X[b], X[b - 1],
-                                                     X[b + 1], X[b - RHW], X[b + RHW]));
-                        } else {
-                            cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - RHW], X[b + RHW]));
-                            cplx<T> dg = helm_diag_at<T>(d, gi, gj);
-                            v = csub<T>(v, cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
-                        }
+#pragma unroll
+        for (int k = 0; k < (RFW * RFH + NT - 1) / NT; ++k) {
+            const int e = tid + k * NT;
+            if (e < RFW * RFH) {
+                const int r = e / RFW, cc = e - r * RFW;
+                const int gi = fx0 + cc, gj = fy0 + r;
+                cplx<T> v = zero2<T>();
+                if (gi < n && gj < n) {
+                    v = Bv[(r + 1) * RXW + cc + 2];
+                    if (needk) {
+                        const int q = (r + 1) * xw + cc + 1 + xo;
+                        const cplx<T> sn = cadd<T>(cadd<T>(X[q - 1], X[q + 1]), cadd<T>(X[q - xw], X[q + xw]));
+                        const int qk = (r + 1) * RKW + cc + 4;
+                        const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[qk], hs ? Sg2[qk] : T(0));
+                        v = csub<T>(v, cscale<T>(csub<T>(cmul<T>(dg, X[q]), sn), ih2));
                     }
                 }
+                R[e] = v;
             }
-            R[e] = v;
         }
         __syncthreads();
         // full weighting
-        {
-            const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+#pragma unroll
+        for (int k = 0; k < RCX * RCY / NT; ++k) {
+            const int e = tid + k * NT;
+            const int ty = e / RCX, tx = e - ty * RCX;
+            const int I = I0 + tx, J = J0 + ty;
             if (I < nc && J < nc) {
-                const int b = (2 * threadIdx.y + 1) * RFW + 2 * threadIdx.x + 1;
-                cplx<T> s4 = R[b];
-                cplx<T> s2 = cadd<T>(cadd<T>(R[b - 1], R[b + 1]), cadd<T>(R[b - RFW], R[b + RFW]));
-                cplx<T> s1 = cadd<T>(cadd<T>(R[b - RFW - 1], R[b - RFW + 1]), cadd<T>(R[b + RFW - 1], R[b + RFW + 1]));
-                cplx<T> v = cadd<T>(cadd<T>(cscale<T>(s4, T(4)), cscale<T>(s2, T(2))), s1);
+                const int q = (2 * ty + 1) * RFW + 2 * tx + 1;
+                const cplx<T> s4 = R[q];
+                const cplx<T> s2 = cadd<T>(cadd<T>(R[q - 1], R[q + 1]), cadd<T>(R[q - RFW], R[q + RFW]));
+                const cplx<T> s1 = cadd<T>(cadd<T>(R[q - RFW - 1], R[q - RFW + 1]), cadd<T>(R[q + RFW - 1], R[q + RFW + 1]));
+                const cplx<T> v = cadd<T>(cadd<T>(cscale<T>(s4, T(4)), cscale<T>(s2, T(2))), s1);
                 out[(long long)J * dc.pitch + I] = cscale<T>(v, T(0.0625));
             }
         }
+        __syncthreads();
+        buf ^= 1;
     }
 }
 
@@ -459,11 +593,26 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
 //   PMODE_ADD:  x[sout] = x[sx] + P e  (pointwise; sout may equal sx)
 //   PMODE_JAC:  u = x[sx] + P e;  x[sout] = u + w D^{-1}(g - A u)   (level 1 post)
 //   PMODE_ADR:  x' = x[sx] + P e written to sxo;  r0 = b[sb] - L x' to sout
-// The output slots always differ from the slots read with a halo.
+// The output slots always differ from the slots read with a halo.  Tiles of
+// PTX x PTY fine nodes; the coarse tile, x (with a ring for the stencil
+// modes), b / g, the coefficients and k arrive by TMA into two alternating
+// buffers.
 enum PMode : int { PMODE_ADD = 0, PMODE_JAC = 1, PMODE_ADR = 2 };
-constexpr int PTX = 32, PTY = 8;
-constexpr int PHW = PTX + 2, PHH = PTY + 2;
+constexpr int PTX = 32, PTY = 16;
 constexpr int PCW = PTX / 2 + 3, PCH = PTY / 2 + 3;
+constexpr int PEW = PCW + 1;                           // coarse box, from (cx0-1, cy0)
+template <int MODE> struct PGeo {
+    static constexpr int HAL = MODE == PMODE_ADD ? 0 : 1;
+    static constexpr int XW = PTX + 2 * HAL, XH = PTY + 2 * HAL, NX = XW * XH, NP = PTX * PTY;
+    static constexpr int BXW = MODE == PMODE_ADD ? PTX : PTX + 4;   // x box width (from x0 or x0-2)
+};
+template <typename T, int MODE> __host__ __device__ constexpr int prolong_smem() {
+    using G = PGeo<MODE>;
+    return 128 + 2 * (tma_piece<cplx<T>>(PEW * PCH) + tma_piece<cplx<T>>(G::BXW * G::XH) + tma_piece<cplx<T>>(G::NP) +
+                      (MODE == PMODE_ADR ? tma_piece<quad<T>>(G::NP) : 0) +
+                      (MODE == PMODE_JAC ? 2 * tma_piece<T>(G::NP) : 0)) +
+           tma_piece<cplx<T>>(G::NX);
+}
 
 template <typename T>
 __device__ __forceinline__ int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
@@ -471,81 +620,125 @@ __device__ __forceinline__ int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                 int nseg, int sx, int sc, int sb, int sout, int sxo, int xzero) {
+    using G = PGeo<MODE>;
+    constexpr int HAL = G::HAL, XW = G::XW, NX = G::NX, NP = G::NP, BXW = G::BXW, XH = G::XH;
+    extern __shared__ unsigned char wk_smem[];
+    TmaCarve cv(wk_smem);
+    cplx<T>* Eb[2]; cplx<T>* Xb[2]; cplx<T>* Bb[2]; quad<T>* Qb[2]; T* Kb[2]; T* Sb[2];
+    for (int b = 0; b < 2; ++b) {
+        Eb[b] = cv.take<cplx<T>>(PEW * PCH);
+        Xb[b] = cv.take<cplx<T>>(BXW * XH);
+        Bb[b] = cv.take<cplx<T>>(NP);
+        Qb[b] = MODE == PMODE_ADR ? cv.take<quad<T>>(NP) : nullptr;
+        Kb[b] = MODE == PMODE_JAC ? cv.take<T>(NP) : nullptr;
+        Sb[b] = MODE == PMODE_JAC ? cv.take<T>(NP) : nullptr;
+    }
+    cplx<T>* U = cv.take<cplx<T>>(NX);
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
-    __shared__ cplx<T> E[PCW * PCH];
-    __shared__ cplx<T> X[PHW * PHH];
+    __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) dc = D[d.coarse];
-    __syncthreads();
-    const int n = d.n, pitch = d.pitch, nc = dc.n;
-    const int ntx = (n + PTX - 1) / PTX, nty = (n + PTY - 1) / PTY;
-    const cplx<T>* xs = slot<T>(d, sx);
-    const cplx<T>* ec = slot<T>(dc, sc);
-    const cplx<T>* bs = slot<T>(d, sb);
+    TmaPipe pipe;
+    pipe.init(bars);
+    const int n = d.n, pitch = d.pitch;
+    const int ntx = (n + PTX - 1) / PTX, ntiles = ntx * ((n + PTY - 1) / PTY);
     cplx<T>* os = slot<T>(d, sout);
+    cplx<T>* xo = slot<T>(d, sxo);
+    const bool hs = d.sig != nullptr;
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
     const T wjh2 = (MODE == PMODE_JAC) ? scalp<T>(d)[S::OMEGA_J] * LC<T>::h(d) * LC<T>::h(d) : T(0);
-    const int halo = (MODE == PMODE_ADD) ? 0 : 1;
-    for (int t = c.lb; t < ntx * nty; t += c.nb) {
+    const unsigned bytes = (unsigned)(PEW * PCH * sizeof(cplx<T>)) +
+                           (xzero ? 0u : (unsigned)(BXW * XH * sizeof(cplx<T>))) +
+                           (MODE != PMODE_ADD ? (unsigned)(NP * sizeof(cplx<T>)) : 0u) +
+                           (MODE == PMODE_ADR ? (unsigned)(NP * sizeof(quad<T>)) : 0u) +
+                           (MODE == PMODE_JAC ? (unsigned)(NP * sizeof(T)) * (hs ? 2u : 1u) : 0u);
+    auto issue = [&](int t, int b) {
+        if (tid != 0) return;
         const int x0 = (t % ntx) * PTX, y0 = (t / ntx) * PTY;
-        // coarse index range feeding fine [x0-1, x0+PTX]
-        const int cx0 = fdiv2<T>(x0 - 2), cy0 = fdiv2<T>(y0 - 2);
-        __syncthreads();
-        load_region<T>(E, ec, nc, dc.pitch, cx0, cy0, PCW, PCH);
-        __syncthreads();
-        // u = x + P e on tile (+ ring)
-        for (int e = tid; e < PHW * PHH; e += NT) {
-            const int r = e / PHW, cc = e - r * PHW;
-            const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
-            cplx<T> v = zero2<T>();
-            const bool inner = cc >= 1 && cc <= PTX && r >= 1 && r <= PTY;
-            if ((halo || inner) && gi >= 0 && gi < n && gj >= 0 && gj < n) {
-                // 1D weights: odd fine index = coincident coarse node (gi-1)/2
-                T acc_re = 0, acc_im = 0;
-                int ia[2], ja[2];
-                T wa[2], wb[2];
-                int na, nb2;
-                if (gi & 1) { ia[0] = (gi - 1) / 2; wa[0] = T(1); na = 1; }
-                else { ia[0] = gi / 2 - 1; ia[1] = gi / 2; wa[0] = wa[1] = T(0.5); na = 2; }
-                if (gj & 1) { ja[0] = (gj - 1) / 2; wb[0] = T(1); nb2 = 1; }
-                else { ja[0] = gj / 2 - 1; ja[1] = gj / 2; wb[0] = wb[1] = T(0.5); nb2 = 2; }
-                for (int q = 0; q < nb2; ++q)
-                    for (int pp = 0; pp < na; ++pp) {
-                        cplx<T> ev = E[(ja[q] - cy0) * PCW + (ia[pp] - cx0)];
-                        acc_re += wa[pp] * wb[q] * ev.x;
-                        acc_im += wa[pp] * wb[q] * ev.y;
-                    }
-                v = mk<T>(acc_re, acc_im);
-                if (!xzero) v = cadd<T>(__ldg(xs + (long long)gj * pitch + gi), v);
-            }
-            X[e] = v;
+        pipe.expect(b, bytes);
+        // coarse nodes from x0/2 - 2 (even) and y0/2 - 1
+        tma_load_3d(Eb[b], tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, sc, &bars[b]);
+        if (!xzero) {
+            if (MODE == PMODE_ADD) tma_load_3d(Xb[b], tmap(d, MC_PROL_T), 2 * x0, y0, sx, &bars[b]);
+            else tma_load_3d(Xb[b], tmap(d, MC_PROL_X), 2 * (x0 - 2), y0 - 1, sx, &bars[b]);
         }
-        __syncthreads();
-        {
-            const int cc = threadIdx.x, r = threadIdx.y;
-            const int gi = x0 + cc, gj = y0 + r;
-            if (gi < n && gj < n) {
-                const long long p = (long long)gj * pitch + gi;
-                const int b = (r + 1) * PHW + cc + 1;
+        if (MODE != PMODE_ADD) tma_load_3d(Bb[b], tmap(d, MC_PROL_T), 2 * x0, y0, sb, &bars[b]);
+        if (MODE == PMODE_ADR) tma_load_3d(Qb[b], tmap(d, MQ_PROL), 0, x0, y0, &bars[b]);
+        if (MODE == PMODE_JAC) {
+            tma_load_2d(Kb[b], tmap(d, MK_PROL), x0, y0, &bars[b]);
+            if (hs) tma_load_2d(Sb[b], tmap(d, MS_PROL), x0, y0, &bars[b]);
+        }
+    };
+    int buf = 0;
+    if (c.lb < ntiles) issue(c.lb, 0);
+    for (int t = c.lb; t < ntiles; t += c.nb) {
+        if (t + c.nb < ntiles) issue(t + c.nb, buf ^ 1);
+        if (!pipe.wait(buf, d.err)) return;
+        const int x0 = (t % ntx) * PTX, y0 = (t / ntx) * PTY;
+        const int ex0 = x0 / 2 - 2, ey0 = y0 / 2 - 1;   // coarse box origin
+        const cplx<T>* E = Eb[buf];
+        // u = x + P e on the tile (+ ring); ring node (r, cc) from
+        // (x0-HAL, y0-HAL) is x box (r, cc + 2*HAL - HAL) = (r, cc + HAL)
+#pragma unroll
+        for (int k = 0; k < (NX + NT - 1) / NT; ++k) {
+            const int e = tid + k * NT;
+            if (e < NX) {
+                const int r = e / XW, cc = e - r * XW;
+                const int gi = x0 - HAL + cc, gj = y0 - HAL + r;
+                cplx<T> v = zero2<T>();
+                const bool in = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n;
+                if (in) {
+                    // 1D weights: odd fine index = coincident coarse node (gi-1)/2
+                    const int ia = (gi & 1) ? (gi - 1) / 2 : gi / 2 - 1;
+                    const int ja = (gj & 1) ? (gj - 1) / 2 : gj / 2 - 1;
+                    const int qb = (ja - ey0) * PEW + (ia - ex0);
+                    if (gi & 1) {
+                        if (gj & 1) v = E[qb];
+                        else v = cscale<T>(cadd<T>(E[qb], E[qb + PEW]), T(0.5));
+                    } else {
+                        if (gj & 1) v = cscale<T>(cadd<T>(E[qb], E[qb + 1]), T(0.5));
+                        else v = cscale<T>(cadd<T>(cadd<T>(E[qb], E[qb + 1]), cadd<T>(E[qb + PEW], E[qb + PEW + 1])),
+                                           T(0.25));
+                    }
+                    if (!xzero) v = cadd<T>(Xb[buf][r * BXW + cc + HAL], v);
+                }
                 if (MODE == PMODE_ADD) {
-                    os[p] = X[b];
-                } else if (MODE == PMODE_JAC) {
-                    cplx<T> dg = helm_diag_at<T>(d, gi, gj);
-                    cplx<T> s = cadd<T>(cadd<T>(X[b - 1], X[b + 1]), cadd<T>(X[b - PHW], X[b + PHW]));
-                    cplx<T> rr = csub<T>(__ldg(bs + p), cscale<T>(csub<T>(cmul<T>(dg, X[b]), s), ih2));
-                    const T den = dg.x * dg.x + dg.y * dg.y;
-                    cplx<T> q = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
-                    os[p] = cadd<T>(X[b], cscale<T>(q, wjh2));
+                    if (in) os[(long long)gj * pitch + gi] = v;
                 } else {
-                    cplx<T> Lx = adr_pt<T>(load_adr<T>(d, p), ih2, wh, X[b], X[b - 1], X[b + 1],
-                                           X[b - PHW], X[b + PHW]);
-                    os[p] = csub<T>(__ldg(bs + p), Lx);
-                    slot<T>(d, sxo)[p] = X[b];
+                    U[e] = v;
                 }
             }
         }
+        if (MODE != PMODE_ADD) {
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < NP / NT; ++k) {
+                const int e = tid + k * NT;
+                const int r = e / PTX, cc = e - r * PTX;
+                const int gi = x0 + cc, gj = y0 + r;
+                if (gi < n && gj < n) {
+                    const long long p = (long long)gj * pitch + gi;
+                    const int q = (r + 1) * XW + cc + 1;
+                    if (MODE == PMODE_JAC) {
+                        const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, Kb[buf][e], hs ? Sb[buf][e] : T(0));
+                        const cplx<T> sn = cadd<T>(cadd<T>(U[q - 1], U[q + 1]), cadd<T>(U[q - XW], U[q + XW]));
+                        const cplx<T> rr = csub<T>(Bb[buf][e], cscale<T>(csub<T>(cmul<T>(dg, U[q]), sn), ih2));
+                        const T den = dg.x * dg.x + dg.y * dg.y;
+                        const cplx<T> qv = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
+                        os[p] = cadd<T>(U[q], cscale<T>(qv, wjh2));
+                    } else {
+                        const cplx<T> Lx =
+                            adr_pt<T>(Qb[buf][e], ih2, wh, U[q], U[q - 1], U[q + 1], U[q - XW], U[q + XW]);
+                        os[p] = csub<T>(Bb[buf][e], Lx);
+                        xo[p] = U[q];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
     }
 }
 

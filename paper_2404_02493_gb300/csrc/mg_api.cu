@@ -7,6 +7,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "handle.h"
 #include "fgmres.cuh"
 #include "kernels.cuh"
@@ -206,6 +209,65 @@ static size_t esz(int prec) { return prec == MG_PREC_FP64 ? 16 : 8; }   // compl
 static size_t rsz(int prec) { return prec == MG_PREC_FP64 ? 8 : 4; }    // real element
 
 static int round_pitch(int n) { return (n + 31) / 32 * 32; }
+
+// ------------------------------------------------------------ tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// The tensor maps of one (instance, level) in MapId order (see tma.cuh):
+// complex slot maps 3D (2n reals, n rows, slots), quads 3D (4, n, n), reals
+// 2D (n, n); box (W, H) nodes as the tile kernels use them.
+static int build_tmaps_desc(const LevelDesc& d, int nslot, int prec, CUtensorMap* m) {
+    auto enc = encode_fn();
+    if (!enc) { set_error("mg_setup: cuTensorMapEncodeTiled unavailable"); return MG_ECUDA; }
+    const CUtensorMapDataType dt = prec == MG_PREC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t es = prec == MG_PREC_FP64 ? 8 : 4;
+    const cuuint64_t n = (cuuint64_t)d.n, pitch = (cuuint64_t)d.pitch;
+    const cuuint32_t one[3] = {1, 1, 1};
+    auto cplx_map = [&](int id, int W, int H) -> bool {
+        const cuuint64_t dims[3] = {2 * n, n, (cuuint64_t)nslot};
+        const cuuint64_t str[2] = {2 * pitch * es, 2 * (cuuint64_t)d.slot_stride * es};
+        const cuuint32_t box[3] = {(cuuint32_t)(2 * W), (cuuint32_t)H, 1};
+        return enc(&m[id], dt, 3, d.vec, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    auto quad_map = [&](int id, int W, int H) -> bool {
+        const cuuint64_t dims[3] = {4, n, n};
+        const cuuint64_t str[2] = {4 * es, 4 * pitch * es};
+        const cuuint32_t box[3] = {4, (cuuint32_t)W, (cuuint32_t)H};
+        return enc(&m[id], dt, 3, const_cast<void*>(d.adr), dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    auto real_map = [&](int id, const void* base, int W, int H) -> bool {
+        const cuuint64_t dims[2] = {n, n};
+        const cuuint64_t str[1] = {pitch * es};
+        const cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)H};
+        return enc(&m[id], dt, 2, const_cast<void*>(base), dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    bool ok = cplx_map(MC_CHEB_X, CXW, CXH) && cplx_map(MC_CHEB_G, CGW, CGH) && cplx_map(MC_CHEB_D, CTX, CTY) &&
+              real_map(MK_CHEB, d.kf, CKW, CKH) && cplx_map(MC_RESTR, RXW, RHH) && real_map(MK_RESTR, d.kf, RKW, RHH) &&
+              cplx_map(MC_PROL_E, PEW, PCH) && cplx_map(MC_PROL_X, PTX + 4, PTY + 2) && cplx_map(MC_PROL_T, PTX, PTY) &&
+              real_map(MK_PROL, d.kf, PTX, PTY);
+    if (ok && d.sig)
+        ok = real_map(MS_CHEB, d.sig, CKW, CKH) && real_map(MS_RESTR, d.sig, RKW, RHH) &&
+             real_map(MS_PROL, d.sig, PTX, PTY);
+    if (ok && d.adr) ok = quad_map(MQ_PROL, PTX, PTY);
+    if (!ok) { set_error("mg_setup: tensor map encoding failed"); return MG_ECUDA; }
+    return MG_OK;
+}
 
 static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t st) {
     Handle& H = mh->H;
@@ -411,6 +473,26 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         I.outer_desc = b;
         H.houter.push_back(d);
     }
+    // tensor maps of the tile kernels and the device error word
+    {
+        const size_t nd2 = H.hdesc.size();
+        std::vector<CUtensorMap> maps(nd2 * NMAP);
+        memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+        H.tmaps = H.alloc(maps.size() * sizeof(CUtensorMap));
+        H.err = (unsigned*)H.alloc(sizeof(unsigned));
+        if (!H.tmaps || !H.err) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
+        cudaMemsetAsync(H.err, 0, sizeof(unsigned), st);
+        for (size_t q = 0; q < nd2; ++q) {
+            LevelDesc& d = H.hdesc[q];
+            const int rc2 = build_tmaps_desc(d, d.level == 1 ? NSLOT_L1 : NSLOT, prec, &maps[q * NMAP]);
+            if (rc2) return rc2;
+            d.tm = (const unsigned char*)H.tmaps + q * NMAP * sizeof(CUtensorMap);
+            d.err = H.err;
+        }
+        for (LevelDesc& d : H.houter) d.err = H.err;
+        cudaMemcpy(H.tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    }
+    static_assert(sizeof(CUtensorMap) == TMAP_BYTES, "tensor map size");
     H.ddesc = (LevelDesc*)H.alloc(sizeof(LevelDesc) * H.hdesc.size());
     H.douter = (LevelDesc*)H.alloc(sizeof(LevelDesc) * H.houter.size());
     cudaMemcpy(H.ddesc, H.hdesc.data(), sizeof(LevelDesc) * H.hdesc.size(), cudaMemcpyHostToDevice);
@@ -427,6 +509,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         cudaMemcpy(H.scal, hs.data(), sizeof(double) * hs.size(), cudaMemcpyHostToDevice);
     }
     if (cudaMallocHost(&H.hpin, sizeof(double) * S::SIZE * nslots) != cudaSuccess) H.hpin = nullptr;
+    if (cudaMallocHost(&H.herr, sizeof(unsigned)) != cudaSuccess) H.herr = nullptr;
     if (cudaStreamCreateWithFlags(&H.g_stream, cudaStreamNonBlocking) != cudaSuccess) return MG_ECUDA;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -462,6 +545,7 @@ static void free_all(Handle& H) {
     if (H.g_stream) cudaStreamDestroy(H.g_stream);
     for (void* p : H.allocs) cudaFree(p);
     if (H.hpin) cudaFreeHost(H.hpin);
+    if (H.herr) cudaFreeHost(H.herr);
     H.allocs.clear();
 }
 
@@ -503,6 +587,20 @@ static int fg_iter_launch(mg_handle* h, cudaStream_t st) {
         H.fg_j++;
     } else {
         h->eng->fg_iter(H, st);
+    }
+    return MG_OK;
+}
+
+// Device error word (a bounded wait of a tile kernel expired) -> MG_ETIMEOUT;
+// synchronises st.  The word is cleared after it was reported.
+static int check_device_error(Handle& H, cudaStream_t st) {
+    if (!H.err || !H.herr) return MG_OK;
+    WADR_CHECK(cudaMemcpyAsync(H.herr, H.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    WADR_CHECK(cudaStreamSynchronize(st));
+    if (*H.herr) {
+        cudaMemsetAsync(H.err, 0, sizeof(unsigned), st);
+        set_error("device-side wait expired (a tile kernel gave up; results are invalid)");
+        return MG_ETIMEOUT;
     }
     return MG_OK;
 }
@@ -714,7 +812,7 @@ int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream
         WADR_CHECK(copy_out(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.pitch, st));
     }
     WADR_CHECK(cudaGetLastError());
-    if (is_host_ptr(u)) WADR_CHECK(cudaStreamSynchronize(st));   // host result must be complete on return
+    if (is_host_ptr(u)) return check_device_error(H, st);   // synchronises: host result complete on return
     return MG_OK;
 }
 
@@ -778,6 +876,8 @@ int mg_solve_end(mg_handle* h, void* u, double* rel_residual, mg_stream stream) 
     }
     std::vector<double> rn, gn;
     int rc = read_outer_norms(H, st, rn, &gn);
+    if (rc) return rc;
+    rc = check_device_error(H, st);
     if (rc) return rc;
     if (rel_residual) *rel_residual = max_rel(rn, gn);
     return MG_OK;
