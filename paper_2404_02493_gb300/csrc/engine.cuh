@@ -415,15 +415,27 @@ struct Engine : EngineBase {
         go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
             k_fg_matvec<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
         }, t.pts);
-        go(H, st, KK_FG_DOTS, (j + 2) * C * t.pts, [&] {
-            k_fg_dots<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
-        }, t.pts);
-        go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
-            k_fg_orth<T, 1><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
-        }, t.pts);
-        go(H, st, KK_FG_ORTH, (j + 3) * C * t.pts, [&] {
-            k_fg_orth<T, 2><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
-        }, t.pts);
+        {
+            std::vector<int> od;
+            for (auto& I : H.inst) od.push_back(I.outer_desc);
+            auto k0 = k_fg_gs<T, 0>;
+            auto k1 = k_fg_gs<T, 1>;
+            auto k2 = k_fg_gs<T, 2>;
+            const int smem = fg_smem<T>();
+            const int cap = occ_cap(k0, smem);
+            occ_cap(k1, smem);
+            occ_cap(k2, smem);
+            const SegTable& tg = H.seg_outer_chunks(od, fg_chunk<T>(), cap);
+            go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
+                k0<<<tg.nblocks, bd, smem, st>>>(H.douter, tg.d, tg.nseg);
+            }, tg.pts);
+            go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
+                k1<<<tg.nblocks, bd, smem, st>>>(H.douter, tg.d, tg.nseg);
+            }, tg.pts);
+            go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
+                k2<<<tg.nblocks, bd, smem, st>>>(H.douter, tg.d, tg.nseg);
+            }, tg.pts);
+        }
         H.launches_cycle = cyc;
         H.launches_step = cyc + 5;
         H.fg_j = j + 1;

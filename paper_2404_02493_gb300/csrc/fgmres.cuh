@@ -11,6 +11,7 @@
 // serves every inner iteration.
 #pragma once
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace wadr {
 
@@ -167,159 +168,112 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const LevelDesc* __restrict__ 
     }
 }
 
-// The Gram-Schmidt kernels stream the level-1 vectors two complex values
-// per thread (one 16-byte load for complex64): W and V_0..V_j at the same
-// positions, so that every thread keeps j + 2 independent loads in flight.
-// Pairs run along rows; when n is odd the last pair of a row has one node
-// past the grid (row padding, zero in every vector) which is masked.
-template <typename TC>
-struct V2 {
-    cplx<TC> a, b;
-};
-template <typename TC>
-__device__ __forceinline__ V2<TC> ld2(const cplx<TC>* p) {
-    if constexpr (sizeof(cplx<TC>) == 8) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        return V2<TC>{mk<TC>(v.x, v.y), mk<TC>(v.z, v.w)};
-    } else {
-        return V2<TC>{__ldg(p), __ldg(p + 1)};
-    }
-}
-template <typename TC>
-__device__ __forceinline__ V2<TC> ld2cg(const cplx<TC>* p) {   // vector written by this kernel family
-    if constexpr (sizeof(cplx<TC>) == 8) {
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
-        return V2<TC>{mk<TC>(v.x, v.y), mk<TC>(v.z, v.w)};
-    } else {
-        return V2<TC>{__ldcg(p), __ldcg(p + 1)};
-    }
-}
-template <typename TC>
-__device__ __forceinline__ void st2(cplx<TC>* p, const V2<TC>& v, bool two) {
-    if constexpr (sizeof(cplx<TC>) == 8) {
-        if (two) {
-            *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
-            return;
-        }
-        p[0] = v.a;
-    } else {
-        p[0] = v.a;
-        if (two) p[1] = v.b;
-    }
-}
-// pair index e -> element offset of its first node, and whether both exist
-__device__ __forceinline__ long long pair_pos(int e, int npr, int pitch, int n, bool& two) {
-    const int r = e / npr, q = e - r * npr;
-    two = 2 * q + 1 < n;
-    return (long long)r * pitch + 2 * q;
+// Gram-Schmidt passes of FGMRES over the level-1 vectors.  The padded
+// vectors are contiguous (pitch * n values, zero in the row padding), so a
+// pass treats them as flat arrays cut into chunks of FG_CHUNK values: for
+// each chunk the block streams W and V_0..V_j in by 1D bulk copies into one
+// of two shared-memory stages (the next chunk's copies are in flight while
+// the current chunk is computed), and every thread works on its values of
+// the chunk from shared memory.
+//   PASS 0: projections <V_i, W>, i <= j             -> fs[HC]
+//   PASS 1: W -= sum_i h1_i V_i; <V_i, W'>, ||W'||^2  -> fs[CC]
+//   PASS 2: W -= sum_i h2_i V_i; ||W''||^2; the last block completes column
+//           j of the Hessenberg, applies the Givens rotations, stores
+//           |gamma_{j+1}| and advances j.
+template <typename TC> __host__ __device__ constexpr int fg_chunk() { return sizeof(cplx<TC>) == 8 ? 512 : 256; }
+template <typename TC> __host__ __device__ constexpr int fg_smem() {
+    return 128 + 2 * (MAXR + 1) * tma_piece<cplx<TC>>(fg_chunk<TC>());
 }
 
-// First Gram-Schmidt pass: projections <V_i, W>, i <= j  -> fs[HC].
-template <typename TC>
-__global__ void __launch_bounds__(NT) k_fg_dots(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                int nseg) {
-    __shared__ LevelDesc d;
-    __shared__ double2 grp[8 * 32];
-    __shared__ double2 tot[NVF];
-    __shared__ cplx<TC> shT[8 * NVF];
-    __shared__ int flag;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
-    const int jj = (int)d.fs[FS::J];
-    const cplx<TC>* w = kvec<TC>(d, jj + 1);
-    const cplx<TC>* v0 = kvec<TC>(d, 0);
-    const long long vs = d.slot_stride;
-    cplx<TC> ac[NVF];
-#pragma unroll
-    for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
-    for (int e = c.lb * NT + tid; e < npairs; e += c.nb * NT) {
-        bool two;
-        const long long p = pair_pos(e, npr, pitch, n, two);
-        V2<TC> wv = ld2cg<TC>(w + p);
-        if (!two) wv.b = zero2<TC>();
-#pragma unroll
-        for (int q = 0; q < MAXR; ++q)
-            if (q <= jj) {
-                const V2<TC> v = ld2<TC>(v0 + q * vs + p);
-                ac[q] = cadd<TC>(ac[q], cadd<TC>(cmulc<TC>(v.a, wv.a), cmulc<TC>(v.b, wv.b)));
-            }
-    }
-    block_sum<cplx<TC>, NVF>(ac, shT);
-    if (publish_fpartials(d, c.lb, c.nb, ac, jj + 1, &flag)) {
-        finish_fpartials(d, c.nb, tot, grp);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            for (int q = 0; q <= jj; ++q) sstore2d(d.fs, FS::HC + 2 * q, tot[q]);
-    }
-}
-
-// W -= sum_i coef_i V_i (coef = fs[HC] in pass 1, fs[CC] in pass 2).  Pass
-// 1 also forms the second-pass projections <V_i, W'>; both passes form
-// ||W'||^2.  The last block of pass 2 completes column j of the Hessenberg,
-// applies the Givens rotations, stores |gamma_{j+1}| and advances j.
-template <typename TC, int pass>
-__global__ void __launch_bounds__(NT, 2) k_fg_orth(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                   int nseg) {
+template <typename TC, int PASS>
+__global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+                                                 int nseg) {
+    constexpr int P = fg_chunk<TC>();
+    extern __shared__ unsigned char fg_raw[];
+    TmaCarve cv(fg_raw);
+    // [stage][V_0..V_{MAXR-1}, W][P]; P values = 4 KB, so every piece stays 128-byte aligned
+    static_assert(P * sizeof(cplx<TC>) % 128 == 0, "chunk size");
+    cplx<TC>* const stg0 = cv.take<cplx<TC>>(2 * (MAXR + 1) * P);
+    auto stg = [&](int b, int q) { return stg0 + (b * (MAXR + 1) + q) * P; };
     __shared__ LevelDesc d;
     __shared__ double2 grp[8 * 32];
     __shared__ double2 tot[NVF];
     __shared__ cplx<TC> shT[8 * NVF];
     __shared__ cplx<TC> coef[MAXR];
     __shared__ int flag;
+    __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
+    TmaPipe pipe;
+    pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
+    const long long N = (long long)d.n * d.pitch;
+    const int nchunks = (int)((N + P - 1) / P);
     const int jj = (int)d.fs[FS::J];
     cplx<TC>* w = kvec<TC>(d, jj + 1);
-    const cplx<TC>* v0 = kvec<TC>(d, 0);
-    const long long vs = d.slot_stride;
-    const int off = (pass == 1) ? FS::HC : FS::CC;
-    if (tid < MAXR) coef[tid] = tid <= jj ? mk<TC>((TC)d.fs[off + 2 * tid], (TC)d.fs[off + 2 * tid + 1]) : zero2<TC>();
+    if (PASS > 0) {
+        const int off = (PASS == 1) ? FS::HC : FS::CC;
+        if (tid < MAXR) coef[tid] = tid <= jj ? mk<TC>((TC)d.fs[off + 2 * tid], (TC)d.fs[off + 2 * tid + 1]) : zero2<TC>();
+    }
     __syncthreads();
-    constexpr int NA = (pass == 1) ? NVF : 1;   // pass 2 keeps only ||W''||^2
-    cplx<TC> ac[NVF];
+    auto issue = [&](int k, int b) {
+        if (tid != 0) return;
+        const long long e0 = (long long)k * P;
+        const unsigned bytes = (unsigned)(min((long long)P, N - e0) * (long long)sizeof(cplx<TC>));
+        pipe.expect(b, bytes * (unsigned)(jj + 2));
+        for (int q = 0; q <= jj; ++q) bulk_load(stg(b, q), kvec<TC>(d, q) + e0, bytes, &bars[b]);
+        bulk_load(stg(b, MAXR), w + e0, bytes, &bars[b]);
+    };
+    constexpr int NA = (PASS == 2) ? 1 : NVF;
+    cplx<TC> ac[NA];
 #pragma unroll
-    for (int q = 0; q < NVF; ++q) ac[q] = zero2<TC>();
-    cplx<TC> nrm = zero2<TC>();
-    for (int e = c.lb * NT + tid; e < npairs; e += c.nb * NT) {
-        bool two;
-        const long long p = pair_pos(e, npr, pitch, n, two);
-        V2<TC> wv = ld2cg<TC>(w + p);
-        // chunks of 8 vectors: 8 loads in flight per thread, bounded registers
-#pragma unroll 1
-        for (int q0 = 0; q0 <= jj; q0 += 8) {
+    for (int q = 0; q < NA; ++q) ac[q] = zero2<TC>();
+    TC nrm = TC(0);
+    int buf = 0;
+    if (c.lb < nchunks) issue(c.lb, 0);
+    for (int k = c.lb; k < nchunks; k += c.nb) {
+        if (k + c.nb < nchunks) issue(k + c.nb, buf ^ 1);
+        if (!pipe.wait(buf, d.err)) return;
+        const long long e0 = (long long)k * P;
+        const int cnt = (int)min((long long)P, N - e0);
 #pragma unroll
-            for (int dq = 0; dq < 8; ++dq) {
-                const int q = q0 + dq;
-                if (q <= jj) {
-                    const V2<TC> v = ld2<TC>(v0 + q * vs + p);
-                    const cplx<TC> cq = coef[q];
-                    wv.a = csub<TC>(wv.a, cmul<TC>(cq, v.a));
-                    wv.b = csub<TC>(wv.b, cmul<TC>(cq, v.b));
+        for (int r = 0; r < P / NT; ++r) {
+            const int e = tid + r * NT;
+            if (e < cnt) {
+                const cplx<TC>* sv = stg(buf, 0);
+                cplx<TC> wv = sv[MAXR * P + e];
+                if (PASS == 0) {
+#pragma unroll
+                    for (int q = 0; q < MAXR; ++q)
+                        if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * P + e], wv));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < MAXR; ++q)
+                        if (q <= jj) wv = csub<TC>(wv, cmul<TC>(coef[q], sv[q * P + e]));
+                    w[e0 + e] = wv;
+                    if (PASS == 1) {
+#pragma unroll
+                        for (int q = 0; q < MAXR; ++q)
+                            if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * P + e], wv));
+                    }
+                    nrm += cabs2<TC>(wv);
                 }
             }
         }
-        if (!two) wv.b = zero2<TC>();
-        st2<TC>(w + p, wv, two);
-        if (pass == 1) {
-            // second-pass projections; V_q is read again (mostly from L1)
-#pragma unroll
-            for (int q = 0; q < MAXR; ++q)
-                if (q <= jj) {
-                    const V2<TC> v = ld2<TC>(v0 + q * vs + p);
-                    ac[q] = cadd<TC>(ac[q], cadd<TC>(cmulc<TC>(v.a, wv.a), cmulc<TC>(v.b, wv.b)));
-                }
-        }
-        nrm.x += cabs2<TC>(wv.a) + cabs2<TC>(wv.b);
+        __syncthreads();
+        buf ^= 1;
     }
-    (void)NA;
-    ac[NVF - 1] = nrm;
-    block_sum<cplx<TC>, NVF>(ac, shT);
-    if (publish_fpartials(d, c.lb, c.nb, ac, NVF, &flag)) {
+    cplx<TC> red[NVF];
+#pragma unroll
+    for (int q = 0; q < NVF; ++q) red[q] = (q < NA && PASS != 2) ? ac[q < NA ? q : 0] : zero2<TC>();
+    red[NVF - 1] = mk<TC>(nrm, TC(0));
+    block_sum<cplx<TC>, NVF>(red, shT);
+    if (publish_fpartials(d, c.lb, c.nb, red, PASS == 0 ? jj + 1 : NVF, &flag)) {
         finish_fpartials(d, c.nb, tot, grp);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             double* f = d.fs;
-            if (pass == 1) {
+            if (PASS == 0) {
+                for (int q = 0; q <= jj; ++q) sstore2d(f, FS::HC + 2 * q, tot[q]);
+            } else if (PASS == 1) {
                 for (int q = 0; q <= jj; ++q) sstore2d(f, FS::CC + 2 * q, tot[q]);
             } else {
                 const double hnext = sqrt(tot[NVF - 1].x);

@@ -119,6 +119,8 @@ struct Handle {
     const SegTable& seg_rows(const std::vector<int>& descs, int rows_per_block);
     // one block per tile of tx x ty nodes (of the next level when `coarse`), at most cap per segment
     const SegTable& seg_tiles(const std::vector<int>& descs, int tx, int ty, bool coarse, int cap);
+    // outer descriptors: one block per `chunk` values of the padded level-1 array, at most cap per segment
+    const SegTable& seg_outer_chunks(const std::vector<int>& descs, int chunk, int cap);
 };
 
 // level operations of EngineBase::level_op

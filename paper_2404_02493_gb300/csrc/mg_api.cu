@@ -122,6 +122,32 @@ const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, b
     return segs[key] = t;
 }
 
+const SegTable& Handle::seg_outer_chunks(const std::vector<int>& ids, int chunk, int cap) {
+    std::string key = "oc" + std::to_string(chunk) + "x" + std::to_string(cap) + desc_key(ids);
+    auto it = segs.find(key);
+    if (it != segs.end()) return it->second;
+    std::vector<Seg> h;
+    SegTable t;
+    int blk = 0;
+    for (int i : ids) {
+        const LevelDesc& d = houter[i];
+        const long long nch = ((long long)d.n * d.pitch + chunk - 1) / chunk;
+        Seg s;
+        s.desc = i;
+        s.blk0 = blk;
+        blk += (int)std::max(1LL, std::min(nch, (long long)std::min(cap, MAXB)));
+        s.blk1 = blk;
+        s.pad = 0;
+        h.push_back(s);
+        t.pts += (long long)d.n * d.n;
+    }
+    t.nseg = (int)h.size();
+    t.nblocks = blk;
+    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
+    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    return segs[key] = t;
+}
+
 const SegTable& Handle::seg_rows(const std::vector<int>& ids, int rows_per_block) {
     std::string key = "r" + std::to_string(rows_per_block);
     for (int i : ids) key += "," + std::to_string(i);

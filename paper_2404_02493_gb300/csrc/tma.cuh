@@ -77,6 +77,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, i
         : "memory");
 }
 
+// 1D bulk copy of `bytes` contiguous bytes (16-byte aligned addresses, size a
+// multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+
 // Operand kinds of the tile kernels.  Complex slot maps are 3D over
 // (2n reals, n rows, slots) of the level's slot allocation; quad maps are 3D
 // over (4 components, n, n); real maps (k, sponge term) are 2D over (n, n).
