@@ -193,6 +193,93 @@ def recorded_traffic(kernel):
     return None if v is None else float(v["dram_bytes_per_launch_full"])
 
 
+def batched_leg(B, torch, dev, st, steps, warmup):
+    """The batched workload: 64 instances of uneven size (255, 511, 1023 in
+    turn, k0 = 0.4 n pi / 5, log-normal media, random sources) in one handle;
+    complex-FP32 cycles preconditioning FGMRES(20) with an FP64 residual and
+    update (iterative refinement diverges on these heterogeneous media), every
+    instance with its own Krylov space; every step is one graph launch that
+    runs one FGMRES iteration of every instance (batched launches over the
+    instances' segment tables).  value = instance-cycles per second."""
+    import synth
+    t0 = time.time()
+    insts = synth.config_batch(64)
+    t_in = time.time() - t0
+    spec = [(I.n, I.omega, torch.from_numpy(I.k).to(dev), torch.from_numpy(I.phi).to(dev), "abc1") for I in insts]
+    p = B.default_params(precision="mixed", n_cmax=15, outer="fgmres", tol=0.0, maxit=1 << 30)
+    t0 = time.time()
+    h = B.mg_setup(spec, p, stream=st)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    g = torch.cat([torch.from_numpy(I.g).reshape(-1) for I in insts]).to(dev)
+    u = torch.zeros_like(g)
+    B.mg_solve_begin(h, u, g, stream=st)
+    B.mg_solve_steps(h, warmup, stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    B.mg_solve_steps(h, steps, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rel = B.mg_solve_end(h, stream=st)
+    launches = B.mg_step_launches(h)
+    recs = B.mg_profile_records(h, 2, stream=st)
+    step_bytes = sum(r[3] for r in recs) / 2
+    peak, _ = measured_peak()
+    tiles = {f"n={insts[b].n}": B.mg_tile_shapes(h, b, 2) for b in range(3)}
+    B.mg_destroy(h)
+    pts = sum(I.n * I.n for I in insts)
+    return {"workload": "64 instances, n in (255, 511, 1023) in turn, k0 = 0.4 n pi/5 (k h ~ 0.25), log-normal "
+                        "media c in [1, 3] (seeds 100..163), random sources in [0.2, 0.8]^2; complex-FP32 Wave-ADR "
+                        "cycles (M=8) preconditioning FGMRES(20) with FP64 residual and update, per instance; one "
+                        "CUDA-graph launch per step runs one FGMRES iteration (one cycle) of every instance",
+            "instances": 64, "fine_points": pts, "steps": steps, "warmup": warmup,
+            "value": 64 * steps / (ms * 1e-3), "unit": "instance-cycles/s", "ms_per_step": ms / steps,
+            "algorithmic_GB_per_step": step_bytes / 1e9,
+            "achieved_GBps": step_bytes / (ms * 1e-3 / steps) / 1e9,
+            "frac_of_peak": step_bytes / (ms * 1e-3 / steps) / 1e9 / peak,
+            "gpu_launches_per_step": launches, "level2_tiles": tiles, "rel_residual_after": rel,
+            "setup_seconds": t_setup, "input_generation_seconds": t_in}
+
+
+def adjoint_leg(B, torch, dev, st, batch):
+    """The differentiation workload: the hand-written adjoint of 8 FP64
+    Wave-ADR cycles from u = 0 on n = 1023, omega = 500 (off-node sources,
+    log-normal media), gradients with respect to phi and the smoother weights,
+    per-cycle checkpoints; one backward call over the whole batch."""
+    import synth
+    insts = synth.config_adjoint(n=1023, omega=500.0, batch=batch)
+    spec = [(I.n, I.omega, torch.from_numpy(I.k).to(dev), torch.from_numpy(I.phi).to(dev), "abc1") for I in insts]
+    p = B.default_params(precision="fp64", n_cmax=15)
+    h = B.mg_setup(spec, p, stream=st)
+    g = torch.cat([torch.from_numpy(I.g).reshape(-1) for I in insts]).to(dev)
+    u0 = torch.zeros_like(g)
+    uK = u0.clone()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    B.mg_cycle(h, uK, g, 8, stream=st)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - w0
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    gbar = torch.complex(torch.randn(g.shape, generator=gen, dtype=torch.float64),
+                         torch.randn(g.shape, generator=gen, dtype=torch.float64)).to(dev)
+    gphi = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    gw = torch.zeros(batch * B.MG_MAX_LEVELS, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    B.mg_cycle_backward(h, u0, g, 8, gbar, gphi, gw, None, stream=st)
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - w0
+    B.mg_destroy(h)
+    return {"workload": f"adjoint of 8 FP64 Wave-ADR cycles, n=1023, omega=500, batch {batch}, off-node sources, "
+                        "per-cycle checkpoints, gradients w.r.t. phi and the smoother weights",
+            "batch": batch, "K": 8, "backward_seconds": t_bwd, "forward_seconds": t_fwd,
+            "value": batch * 8 / t_bwd, "unit": "instance-cycle adjoints/s",
+            "backward_over_forward": t_bwd / t_fwd if t_fwd > 0 else None,
+            "note": "wall clock of one mg_cycle_backward call (host-driven reverse sweep, instance by instance)"}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -316,6 +403,9 @@ def run_ours(args):
     if h is not None:
         B.mg_destroy(h)
 
+    batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3)
+    adjoint = None if args.no_adjoint else adjoint_leg(B, torch, dev, st, args.adjoint_batch)
+
     if rank != 0:
         return 0
     cpu = None
@@ -333,6 +423,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "time_to_tolerance": tts, "rel_residual_after_timed_steps": rel_after,
             "cycle_roofline": cycle_roofline, "kernels": kernels, "top_launches": top_records,
+            "batched": batched, "adjoint": adjoint,
             "setup_seconds": t_setup, "input_generation_seconds": t_inputs}
     print(json.dumps(line), flush=True)
     return 0
@@ -353,6 +444,10 @@ def main():
     ap.add_argument("--M", type=int, default=8, help="ADR corrections per cycle in the timed steps")
     ap.add_argument("--tts-M", type=int, default=2, help="ADR corrections for the time-to-tolerance solve")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "ir"])
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-batch", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1038,9 +1038,15 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
             WADR_CHECK(cudaMemcpyAsync((char*)grad_u0 + I.off * 16, hg.data(), hg.size() * 16, cudaMemcpyDefault, st));
         }
         if (grad_weights) {
-            double* gw = grad_weights + (size_t)b * MG_MAX_LEVELS;
+            // grad_weights may be host or device memory: read, accumulate, write back
+            double gw[MG_MAX_LEVELS];
+            double* gdst = grad_weights + (size_t)b * MG_MAX_LEVELS;
+            WADR_CHECK(cudaMemcpyAsync(gw, gdst, sizeof(gw), cudaMemcpyDefault, st));
+            WADR_CHECK(cudaStreamSynchronize(st));
             gw[0] += A.wj_bar;
             for (int l = 2; l <= I.L; ++l) gw[l - 1] += A.alpha_bar[l];
+            WADR_CHECK(cudaMemcpyAsync(gdst, gw, sizeof(gw), cudaMemcpyDefault, st));
+            WADR_CHECK(cudaStreamSynchronize(st));
         }
         if (grad_phi) {
             std::vector<double> gp((size_t)I.n * I.n);

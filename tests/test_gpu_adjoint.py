@@ -107,3 +107,34 @@ def test_autograd_function_wrapper():
     _, gphi_r, gw_r, ga_r, _ = loss_and_grads(H, I.g, I.phi, 2)
     assert rel(phi.grad.cpu().numpy(), gphi_r) < 1e-5
     assert abs(w.grad[0].item() - gw_r) < 1e-6 * abs(gw_r)
+
+
+def test_adjoint_outputs_in_device_memory_batched():
+    """Two instances in one handle, every output (grad_phi, grad_weights,
+    grad_u0) a CUDA tensor: the same accumulated gradients as host arrays
+    (outputs are accumulated, so a second call doubles them)."""
+    torch = pytest.importorskip("torch")
+    insts = [synth.config_lognormal(n=n, omega=om, seed=s, x0=synth.off_node_source(n, 40 + s))
+             for n, om, s in ((31, 20.0, 11), (47, 25.0, 12))]
+    spec = [(I.n, I.omega, np.ascontiguousarray(I.k), np.ascontiguousarray(I.phi), I.bc) for I in insts]
+    h = B.mg_setup(spec, B.default_params(precision="fp64", n_cmax=7, M=2))
+    try:
+        g = np.concatenate([I.g.ravel() for I in insts])
+        rng = np.random.default_rng(3)
+        ubar = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+        u0 = np.zeros_like(g)
+        host = (np.zeros(g.shape), np.zeros(2 * B.MG_MAX_LEVELS), np.zeros_like(g))
+        B.mg_cycle_backward(h, u0, g, 2, ubar, *host)
+        dev = torch.device("cuda", 0)
+        td = [torch.zeros(g.shape, dtype=torch.float64, device=dev),
+              torch.zeros(2 * B.MG_MAX_LEVELS, dtype=torch.float64, device=dev),
+              torch.zeros(g.shape, dtype=torch.complex128, device=dev)]
+        tu0, tg, tub = (torch.from_numpy(x).to(dev) for x in (u0, g, ubar))
+        for _ in range(2):
+            B.mg_cycle_backward(h, tu0, tg, 2, tub, *td)
+        torch.cuda.synchronize()
+        for got, ref in zip(td, host):
+            got = got.cpu().numpy()
+            assert np.allclose(got, 2 * ref, rtol=1e-12, atol=1e-300), np.max(np.abs(got - 2 * ref))
+    finally:
+        B.mg_destroy(h)
