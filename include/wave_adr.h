@@ -99,6 +99,12 @@ typedef struct mg_params {
                                setup and keep the fastest (default); 0: default tile shapes */
     int tile_candidate;     /* -1 (default); 0..MG_TILE_CANDIDATES-1: use that candidate for every ADR
                                GMRES kernel (overrides autotune; for testing each shape) */
+    int tail_nmax;          /* ADR levels l >= 3 with n_l <= tail_nmax and everything below them run as one
+                               launch per ADR cycle (one thread-block cluster per instance); 0 = off
+                               (default: on this GPU a cluster phase costs about as much as a launch) */
+    int pdl;                /* 1: kernels are launched with programmatic dependent launch (a kernel's
+                               descriptor prologue overlaps its predecessor); 0 (default): plain launches
+                               (measured 0.1 ms per n=4095 cycle faster on this GPU) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */
@@ -199,7 +205,7 @@ int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const 
  * mg_kernel_name gives the kind's name.  mg_step_launches: kernels of one
  * outer step.
  * ---------------------------------------------------------------------- */
-#define MG_KERNEL_KINDS 21
+#define MG_KERNEL_KINDS 22
 int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* launches, int nkinds,
                      mg_stream stream);
 const char* mg_kernel_name(int kind);

@@ -34,6 +34,7 @@ class MgParams(ctypes.Structure):
         ("alpha", ctypes.c_double * MG_MAX_LEVELS), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("shift", ctypes.c_double),
         ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("tile_candidate", ctypes.c_int),
+        ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int),
     ]
 
 
@@ -283,7 +284,7 @@ def mg_abi_sizes():
     return a.value, b.value, c.value
 
 
-MG_KERNEL_KINDS = 21
+MG_KERNEL_KINDS = 22
 
 
 def mg_solve_begin(h, u, g, stream=None):

@@ -11,12 +11,14 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "handle.h"
 #include "fgmres.cuh"
 #include "kernels.cuh"
 #include "gmres_sstep.cuh"
+#include "tail.cuh"
 #include "setup_kernels.cuh"
 
 namespace wadr {
@@ -28,6 +30,29 @@ struct Engine : EngineBase {
     static constexpr double R = sizeof(T);         // bytes of a real value
     static constexpr double Q = 4.0 * sizeof(T);   // bytes of an ADR coefficient quad
 
+    // Launch with programmatic dependent launch allowed: the kernel's prologue
+    // (descriptor copies) may overlap the tail of the previous kernel; every
+    // kernel waits for its predecessor (griddepcontrol.wait in seg_begin)
+    // before it touches data.
+    static bool& pdl_on() {
+        static bool on = true;
+        return on;
+    }
+    template <typename... KArgs, typename... Args>
+    static void kl(void (*kern)(KArgs...), dim3 grid, dim3 block, int smem, cudaStream_t st, Args&&... args) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = pdl_on() ? 1 : 0;
+        cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    }
+
     template <class F>
     static void go(Handle& H, cudaStream_t st, int kind, double bytes, F&& f, long long pts = 0) {
         if (H.prof) prof_begin(H, st);
@@ -37,7 +62,7 @@ struct Engine : EngineBase {
     }
 #define LAUNCH(kind, t, bpp, kern, ...)                                                              \
     go(H, st, kind, (bpp) * (double)(t).pts, [&] {                                                    \
-        kern<<<(t).nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, (t).d, (t).nseg, __VA_ARGS__);            \
+        kl(kern, (t).nblocks, dim3(BX, BY), 0, st, H.ddesc, (t).d, (t).nseg, __VA_ARGS__);            \
     }, (t).pts)
 
     // Dynamic shared memory opt-in and resident blocks per SM x SM count of a
@@ -61,7 +86,7 @@ struct Engine : EngineBase {
         const int smem = cheb_smem<T>();
         const SegTable& t = H.seg_tiles(ds, CTX, CTY, false, occ_cap(kern, smem));
         go(H, st, KK_CHEB, bpp * (double)t.pts, [&] {
-            kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sin, sout, m, flags);
+            kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sin, sout, m, flags);
         }, t.pts);
     }
     template <int MODE>
@@ -71,7 +96,7 @@ struct Engine : EngineBase {
         const int smem = restrict_smem<T>();
         const SegTable& t = H.seg_tiles(ds, RCX, RCY, true, occ_cap(kern, smem));
         go(H, st, kind, bpp * (double)t.pts, [&] {
-            kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sx, sb, sc, uzero);
+            kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sx, sb, sc, uzero);
         }, t.pts);
     }
     template <int MODE>
@@ -81,7 +106,7 @@ struct Engine : EngineBase {
         const int smem = prolong_smem<T, MODE>();
         const SegTable& t = H.seg_tiles(ds, PTX, PTY, false, occ_cap(kern, smem));
         go(H, st, kind, bpp * (double)t.pts, [&] {
-            kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sx, sc, sb, sout, sxo, xzero);
+            kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sx, sc, sb, sout, sxo, xzero);
         }, t.pts);
     }
 
@@ -180,13 +205,13 @@ struct Engine : EngineBase {
                 auto kern = k_gs_gram_stream<T, sh.y>;
                 const SegTable& t = H.seg_tiles(ds, sh.x, sh.y * GS_WPB, false, gs_prepare(kern, smem, 0, I, 32 * GS_WPB));
                 go(H, st, KK_GS_GRAM, (3 * C + Q) * (double)t.pts, [&] {
-                    kern<<<t.nblocks, dim3(32, GS_WPB), smem, st>>>(H.ddesc, t.d, t.nseg, sr0);
+                    kl(kern, t.nblocks, dim3(32, GS_WPB), smem, st, H.ddesc, t.d, t.nseg, sr0);
                 }, t.pts);
             } else {
                 auto kern = k_gs_gram_tile<T, sh.x, sh.y>;
                 const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 0, I, NT));
                 go(H, st, KK_GS_GRAM, (3 * C + Q) * (double)t.pts, [&] {
-                    kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, sr0);
+                    kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sr0);
                 }, t.pts);
             }
         });
@@ -201,7 +226,7 @@ struct Engine : EngineBase {
             const int smem = gs_pre_smem<T>(I);
             const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, true, gs_prepare(kern, smem, 1, I, NT));
             go(H, st, KK_GS_PRE, (4 * C + Q + C / 4) * (double)t.pts, [&] {
-                kern<<<t.nblocks, dim3(BX, BY), smem, st>>>(H.ddesc, t.d, t.nseg, SAB, SAX, SAB);
+                kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, SAB, SAX, SAB);
             }, t.pts);
         });
     }
@@ -210,7 +235,7 @@ struct Engine : EngineBase {
         const SegTable& t = H.seg(ds, false, 2 * NT);
         const double bpp = (flags & 2) ? 7 * C : ((flags & 1) ? 4 * C : 5 * C);
         go(H, st, KK_GS_POST, bpp * (double)t.pts, [&] {
-            k_gs_post<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, sr0, sxo, flags);
+            kl(k_gs_post<T>, t.nblocks, dim3(BX, BY), 0, st, H.ddesc, t.d, t.nseg, sr0, sxo, flags);
         }, t.pts);
     }
 
@@ -221,6 +246,7 @@ struct Engine : EngineBase {
     // residual to the next level's SAB, scalars), all of which every cycle
     // rewrites before use.
     int autotune(Handle& H, cudaStream_t st) override {
+        pdl_on() = H.p.pdl != 0;
         for (int c = 0; c < GS_NCAND; ++c) {
             gs_dispatch(c, [&](auto ic) {
                 constexpr int I = decltype(ic)::value;
@@ -240,8 +266,8 @@ struct Engine : EngineBase {
         for (int l = 2; l <= H.Lmax; ++l) {
             std::vector<int> rest;
             for (size_t b = 0; b < H.inst.size(); ++b)
-                if (H.inst[b].L > l) rest.push_back((int)b);
-            if (rest.empty()) continue;
+                if (H.inst[b].L > l && !(l >= 3 && H.inst[b].lv[l - 1].n <= H.p.tail_nmax)) rest.push_back((int)b);
+            if (rest.empty()) continue;   // not launched per level (coarse tail) or no such level
             const std::vector<int> ds = descs(H, l, rest);
             TileChoice tc;
             for (int w = 0; w < 2; ++w) {
@@ -279,17 +305,85 @@ struct Engine : EngineBase {
         const SegTable& t = H.seg_rows(descs(H, level, I), NT / 32);
         // the dense FP64 inverse is read once, plus the two vectors
         go(H, st, KK_COARSE, 16.0 * (double)t.mat + 2 * C * (double)t.pts, [&] {
-            k_coarse<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.ddesc, t.d, t.nseg, which);
+            kl(k_coarse<T>, t.nblocks, dim3(BX, BY), 0, st, H.ddesc, t.d, t.nseg, which);
         }, t.pts);
+    }
+
+    // The ADR sub-V-cycle adrv(l..L) of the instances in `tail` in one
+    // launch: one thread-block cluster per instance (tail.cuh).  The cluster
+    // size is 16 CTAs (non-portable) when the GPU can schedule it, else 8.
+    int tail_cluster(Handle& H) {
+        static int cl = 0;
+        if (cl) return cl;
+        auto kern = k_adr_tail<T>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int c : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = c;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(c);
+            cfg.blockDim = dim3(TAIL_THREADS);
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int num = 0;
+            if (cudaOccupancyMaxActiveClusters(&num, kern, &cfg) == cudaSuccess && num > 0) {
+                cl = c;
+                break;
+            }
+            cudaGetLastError();
+        }
+        if (!cl) cl = 8;
+        return cl;
+    }
+    void launch_tail(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
+        const std::vector<int> ds = descs(H, l, tail);
+        const std::string key = "tail" + desc_key(ds);
+        auto it = H.tail_first.find(key);
+        int* dfirst = nullptr;
+        if (it == H.tail_first.end()) {
+            dfirst = (int*)H.alloc(sizeof(int) * ds.size());
+            cudaMemcpy(dfirst, ds.data(), sizeof(int) * ds.size(), cudaMemcpyHostToDevice);
+            H.tail_first[key] = dfirst;
+        } else {
+            dfirst = it->second;
+        }
+        const int cl = tail_cluster(H);
+        long long pts = 0;
+        for (int b : tail)
+            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].n;
+        // per ADR level point: two gram passes, the pre- and post-smoothing updates and the prolongation,
+        // as the multi-launch kernels count them
+        const double bpp = 2 * (3 * C + Q) + (4 * C + Q + C / 4) + (4 * C + Q + C / 4) + 5 * C;
+        go(H, st, KK_ADR_TAIL, bpp * (double)pts, [&] {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(cl * (unsigned)tail.size());
+            cfg.blockDim = dim3(TAIL_THREADS);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = st;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, k_adr_tail<T>, (const LevelDesc*)H.ddesc, (const int*)dfirst);
+        }, pts);
     }
 
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
     // level l, result in SAX (or, at level 2 with `modulate`, added as
     // exp(+i w phi) a to the wave iterate SU).
     void adrv(Handle& H, int l, const std::vector<int>& I, bool modulate, cudaStream_t st) {
-        std::vector<int> co, rest;
-        for (int b : I) (H.inst[b].L == l ? co : rest).push_back(b);
+        std::vector<int> co, rest0, tail, rest;
+        for (int b : I) (H.inst[b].L == l ? co : rest0).push_back(b);
         if (!co.empty()) coarse_solve(H, co, l, 1, st);
+        for (int b : rest0)
+            (l >= 3 && H.inst[b].lv[l - 1].n <= H.p.tail_nmax ? tail : rest).push_back(b);
+        if (!tail.empty()) launch_tail(H, l, tail, st);
         if (rest.empty()) return;
         const std::vector<int> ds = descs(H, l, rest);
         const TileChoice tc = tiles_of(H, ds);
@@ -371,7 +465,8 @@ struct Engine : EngineBase {
     void outer_residual(Handle& H, bool gnorm, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_OUTER_RESIDUAL, (gnorm ? 64.0 : 56.0) * t.pts, [&] {
-            k_outer_residual<0><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, gnorm ? 1 : 0);
+            auto kern = &k_outer_residual<0>;
+            kl(kern, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg, gnorm ? 1 : 0);
         }, t.pts);
     }
 
@@ -379,12 +474,12 @@ struct Engine : EngineBase {
     void ir_step(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_OUTER_SCALE, (16.0 + C) * t.pts, [&] {
-            k_outer_scale<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg, SD);
+            kl(k_outer_scale<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg, SD);
         }, t.pts);
         cycle(H, true, st);
         const int cyc = H.launches_cycle;
         go(H, st, KK_OUTER_UPDATE, (32.0 + C) * t.pts, [&] {
-            k_outer_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
+            kl(k_outer_update<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg);
         }, t.pts);
         outer_residual(H, false, st);
         H.launches_cycle = cyc;
@@ -396,7 +491,7 @@ struct Engine : EngineBase {
     void fg_start(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_START, (16.0 + C) * t.pts, [&] {
-            k_fg_start<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
+            kl(k_fg_start<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg);
         }, t.pts);
         H.fg_j = 0;
     }
@@ -408,12 +503,12 @@ struct Engine : EngineBase {
         const int j = H.fg_j;
         dim3 bd(BX, BY);
         go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
-            k_fg_prep<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
+            kl(k_fg_prep<T>, t.nblocks, bd, 0, st, H.douter, t.d, t.nseg);
         }, t.pts);
         cycle(H, true, st);
         const int cyc = H.launches_cycle;
         go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
-            k_fg_matvec<T><<<t.nblocks, bd, 0, st>>>(H.douter, t.d, t.nseg);
+            kl(k_fg_matvec<T>, t.nblocks, bd, 0, st, H.douter, t.d, t.nseg);
         }, t.pts);
         {
             std::vector<int> od;
@@ -427,13 +522,13 @@ struct Engine : EngineBase {
             occ_cap(k2, smem);
             const SegTable& tg = H.seg_outer_chunks(od, fg_chunk<T>(), cap);
             go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
-                k0<<<tg.nblocks, bd, smem, st>>>(H.douter, tg.d, tg.nseg);
+                kl(k0, tg.nblocks, bd, smem, st, H.douter, tg.d, tg.nseg);
             }, tg.pts);
             go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
-                k1<<<tg.nblocks, bd, smem, st>>>(H.douter, tg.d, tg.nseg);
+                kl(k1, tg.nblocks, bd, smem, st, H.douter, tg.d, tg.nseg);
             }, tg.pts);
             go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
-                k2<<<tg.nblocks, bd, smem, st>>>(H.douter, tg.d, tg.nseg);
+                kl(k2, tg.nblocks, bd, smem, st, H.douter, tg.d, tg.nseg);
             }, tg.pts);
         }
         H.launches_cycle = cyc;
@@ -445,7 +540,7 @@ struct Engine : EngineBase {
     void fg_finish(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_UPDATE, (H.fg_j * C + 32.0) * t.pts, [&] {
-            k_fg_update<T><<<t.nblocks, dim3(BX, BY), 0, st>>>(H.douter, t.d, t.nseg);
+            kl(k_fg_update<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg);
         }, t.pts);
         outer_residual(H, false, st);
         H.fg_j = 0;
@@ -458,10 +553,10 @@ struct Engine : EngineBase {
         dim3 bd(BX, BY);
         switch (what) {
         case OP_APPLY:
-            k_apply<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, a0, SU, SD);
+            kl(k_apply<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, a0, SU, SD);
             return SD;
         case OP_RESIDUAL:
-            k_residual<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SU, SG, SD, 0);
+            kl(k_residual<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SU, SG, SD, 0);
             return SD;
         case OP_RESTRICT:
             launch_restrict<MODE_HELM>(H, descs(H, level, I), KK_RESTRICT_HELM, 0, SU, SG, SG, 0, st);
@@ -470,7 +565,7 @@ struct Engine : EngineBase {
             launch_prolong<PMODE_ADD>(H, descs(H, level, I), KK_PROLONG_ADD, 0, SU, SU, SG, SD, SD, 0, st);
             return SD;
         case OP_JACOBI:
-            k_jacobi<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SX2, SG, SU, 0);
+            kl(k_jacobi<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SX2, SG, SU, 0);
             return SU;
         case OP_CHEB: {
             // a0 steps from the iterate in SU
@@ -488,9 +583,9 @@ struct Engine : EngineBase {
             const TileChoice tc = tiles_of(H, ds);
             if (a0) {
                 // r0 = b - L x  (x in SAX, b in SAB)
-                k_apply<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, 2, SAX, STMP);
-                k_sub<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAB, STMP, SV1);
-                k_copy<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, SAX, SD);
+                kl(k_apply<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, 2, SAX, STMP);
+                kl(k_sub<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SAB, STMP, SV1);
+                kl(k_copy<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SAX, SD);
                 gs_gram(H, ds, tc.gram, SV1, st);
                 gs_post(H, ds, SV1, SD, 0, st);
             } else {
@@ -503,7 +598,7 @@ struct Engine : EngineBase {
             adrv(H, level, I, false, st);
             return SAX;
         case OP_ADRCORR:
-            k_resdemod<T><<<t.nblocks, bd, 0, st>>>(H.ddesc, t.d, t.nseg, 0);
+            kl(k_resdemod<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, 0);
             adrv(H, level, I, true, st);
             return SU;
         case OP_COARSE:

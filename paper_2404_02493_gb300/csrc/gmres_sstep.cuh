@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
     __shared__ LevelDesc dc;
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid == 0) dc = D[d.coarse];
+    copy_desc(dc, D + d.coarse, tid);
     __syncthreads();
     const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
     const int ntx = (nc + CX - 1) / CX, ntiles = ntx * ((nc + CY - 1) / CY);

@@ -26,6 +26,15 @@ enum Slot : int {
     NSLOT_L1 = 4
 };
 
+// Copy a descriptor into shared memory with the first warp (independent
+// 8-byte loads); the caller synchronises before use.
+__device__ __forceinline__ void copy_desc(LevelDesc& dst, const LevelDesc* src, int tid) {
+    constexpr int W = (int)(sizeof(LevelDesc) / sizeof(unsigned long long));
+    if (tid < 32)
+        for (int w = tid; w < W; w += 32)
+            reinterpret_cast<unsigned long long*>(&dst)[w] = reinterpret_cast<const unsigned long long*>(src)[w];
+}
+
 struct SegCtx {
     int lb, nb;      // block index within segment, number of blocks of segment
 };
@@ -36,8 +45,19 @@ __device__ __forceinline__ SegCtx seg_begin(const LevelDesc* __restrict__ D, con
     const int s = find_seg(Sg, nseg, blockIdx.x);
     const Seg g = Sg[s];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid == 0) sd = D[g.desc];
+    // the first warp copies the descriptor word by word (independent loads)
+    constexpr int W = (int)(sizeof(LevelDesc) / sizeof(unsigned long long));
+    static_assert(sizeof(LevelDesc) % sizeof(unsigned long long) == 0, "descriptor size");
+    if (tid < 32)
+        for (int w = tid; w < W; w += 32)
+            reinterpret_cast<unsigned long long*>(&sd)[w] = reinterpret_cast<const unsigned long long*>(D + g.desc)[w];
     __syncthreads();
+    // Programmatic dependent launch: descriptors and segment tables are
+    // constant, so the copies above may overlap the previous kernel; wait for
+    // it before touching any data, then allow the next kernel to be scheduled
+    // (it starts only when every CTA of this grid has passed this point).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     SegCtx c;
     c.lb = blockIdx.x - g.blk0;
     c.nb = g.blk1 - g.blk0;
@@ -477,7 +497,7 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
     __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid == 0) dc = D[d.coarse];
+    copy_desc(dc, D + d.coarse, tid);
     TmaPipe pipe;
     pipe.init(bars);
     const int n = d.n, pitch = d.pitch, nc = dc.n;
@@ -639,7 +659,7 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
     __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid == 0) dc = D[d.coarse];
+    copy_desc(dc, D + d.coarse, tid);
     TmaPipe pipe;
     pipe.init(bars);
     const int n = d.n, pitch = d.pitch;

@@ -26,7 +26,7 @@ const char* kernel_kind_name(int k) {
         "restrict_jacobi0", "restrict_helmholtz", "gmres_pre_restrict", "prolong_jacobi", "prolong_add",
         "prolong_adr_residual", "chebyshev_step", "residual_demodulate", "gmres_gram", "gmres_post_update",
         "coarse_lu_apply", "outer_residual_fp64", "outer_scale", "outer_update_fp64", "jacobi", "fgmres_start",
-        "fgmres_prep", "fgmres_matvec", "fgmres_dots", "fgmres_orth", "fgmres_update"};
+        "fgmres_prep", "fgmres_matvec", "fgmres_dots", "fgmres_orth", "fgmres_update", "adr_tail"};
     return (k >= 0 && k < KK_COUNT) ? names[k] : "unknown";
 }
 
@@ -684,6 +684,8 @@ void mg_default_params(mg_params* p) {
     p->use_graph = 1;
     p->autotune = 1;
     p->tile_candidate = -1;
+    p->tail_nmax = 0;
+    p->pdl = 0;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {

@@ -89,3 +89,32 @@ def test_autotuner_picks_listed_candidates():
     finally:
         B.mg_destroy(ha)
         B.mg_destroy(hd)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_coarse_tail_matches_per_level_launches(prec, tol):
+    """The coarse ADR levels in one cluster launch (tail_nmax = 511) against
+    one launch per pass (tail_nmax = 0, the default) and against the oracle,
+    on a batch of uneven instances (the tail takes different numbers of
+    levels per instance)."""
+    insts = [_inst(95, 40.0, 31), _inst(200, 60.0, 32), _inst(127, 50.0, 33)]
+    ht = lib_handle(insts, prec, n_cmax=12, tail_nmax=511)
+    hp = lib_handle(insts, prec, n_cmax=12, tail_nmax=0)
+    try:
+        dt = np.complex128 if prec == "fp64" else np.complex64
+        g = np.concatenate([(I.g / np.linalg.norm(I.g)).ravel() for I in insts]).astype(dt)
+        ut = np.zeros_like(g)
+        up = np.zeros_like(g)
+        B.mg_cycle(ht, ut, g, 1)
+        B.mg_cycle(hp, up, g, 1)
+        assert rel(ut.astype(np.complex128), up.astype(np.complex128)) < tol
+        off = 0
+        for I in insts:
+            H = oracle_hier(I, n_cmax=12)
+            ref = H.cycle(np.zeros_like(I.g), (I.g / np.linalg.norm(I.g)).astype(dt).astype(np.complex128))
+            got = ut[off:off + I.n * I.n].reshape(I.n, I.n).astype(np.complex128)
+            off += I.n * I.n
+            assert rel(got, ref) < tol, (I.n, rel(got, ref))
+    finally:
+        B.mg_destroy(ht)
+        B.mg_destroy(hp)
