@@ -280,6 +280,33 @@ def adjoint_leg(B, torch, dev, st, batch):
             "note": "wall clock of one mg_cycle_backward call (host-driven reverse sweep, instance by instance)"}
 
 
+def precision_leg(B, torch, dev, st, n=1023, omega=500.0):
+    """Time to 1e-6 relative residual of the same problem (the layered recipe
+    at n=1023, omega=500, M=8, FGMRES(20), zero start) with complex-FP32
+    cycles in FP64 refinement and with plain FP64 cycles; every solve reports
+    its final FP64 residual."""
+    import synth
+    inst = synth.config_layered(n=n, omega=omega, seed=5)
+    k = torch.from_numpy(inst.k).to(dev)
+    phi = torch.from_numpy(inst.phi).to(dev)
+    g = torch.from_numpy(inst.g).to(dev)
+    out = {"workload": f"layered medium n={n} omega={omega:g}, M=8, FGMRES(20) to 1e-6 from u=0", "solves": {}}
+    for prec in ("mixed", "fp64"):
+        p = B.default_params(precision=prec, n_cmax=15, tol=1e-6, maxit=2000, M=8)
+        h = B.mg_setup([(n, omega, k, phi, "abc1")], p, stream=st)
+        u = torch.zeros_like(g)
+        w0 = time.time()
+        status, its, rr, hist, secs = B.mg_solve(h, u, g, history_len=0, stream=st)
+        wall = time.time() - w0
+        B.mg_destroy(h)
+        out["solves"][prec] = {"status": {0: "converged", -4: "maxit", -5: "diverged"}.get(status, status),
+                               "iterations": its, "rel_residual_fp64": rr, "device_seconds": secs,
+                               "wall_seconds": wall, "ms_per_iteration": 1e3 * secs / max(its, 1)}
+    m, f = out["solves"]["mixed"], out["solves"]["fp64"]
+    out["fp64_over_mixed_time"] = f["device_seconds"] / m["device_seconds"] if m["device_seconds"] > 0 else None
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -404,6 +431,7 @@ def run_ours(args):
         B.mg_destroy(h)
 
     batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3)
+    precision = None if args.no_precision else precision_leg(B, torch, dev, st)
     adjoint = None if args.no_adjoint else adjoint_leg(B, torch, dev, st, args.adjoint_batch)
 
     if rank != 0:
@@ -423,7 +451,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "time_to_tolerance": tts, "rel_residual_after_timed_steps": rel_after,
             "cycle_roofline": cycle_roofline, "kernels": kernels, "top_launches": top_records,
-            "batched": batched, "adjoint": adjoint,
+            "batched": batched, "adjoint": adjoint, "precision_comparison": precision,
             "setup_seconds": t_setup, "input_generation_seconds": t_inputs}
     print(json.dumps(line), flush=True)
     return 0
@@ -447,6 +475,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--adjoint-batch", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -70,7 +70,7 @@ enum { MG_OUTER_STATIONARY = 0, MG_OUTER_IR = 1, MG_OUTER_FGMRES = 2 };
 enum { MG_COARSE_LU = 0, MG_COARSE_CHEB = 1 };
 
 #define MG_MAX_LEVELS 16
-#define MG_TILE_CANDIDATES 4   /* halo-tile shape candidates per ADR GMRES kernel */
+#define MG_TILE_CANDIDATES 5   /* halo-tile shape candidates per ADR GMRES kernel */
 
 /* Schedule constants.  mg_default_params fills the paper's values:
  * Algorithm 1 (1 Jacobi sweep on level 1; 5 Chebyshev steps before and after
@@ -105,6 +105,8 @@ typedef struct mg_params {
     int pdl;                /* 1: kernels are launched with programmatic dependent launch (a kernel's
                                descriptor prologue overlaps its predecessor); 0 (default): plain launches
                                (measured 0.1 ms per n=4095 cycle faster on this GPU) */
+    int tail_cluster;       /* CTAs per instance of the coarse tail (1..16); 0 (default): 16 if the GPU can
+                               schedule such clusters, else 8 */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */

@@ -23,7 +23,7 @@ MG_OUTER = {"stationary": 0, "ir": 1, "fgmres": 2}
 MG_COARSE_LU, MG_COARSE_CHEB = 0, 1
 MG_OP = {"A": 0, "AH": 1, "L": 2, "LT": 3, "LH": 4}
 MG_MAX_LEVELS = 16
-MG_TILE_CANDIDATES = 4
+MG_TILE_CANDIDATES = 5
 
 
 class MgParams(ctypes.Structure):
@@ -34,7 +34,7 @@ class MgParams(ctypes.Structure):
         ("alpha", ctypes.c_double * MG_MAX_LEVELS), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("shift", ctypes.c_double),
         ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("tile_candidate", ctypes.c_int),
-        ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int),
+        ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int), ("tail_cluster", ctypes.c_int),
     ]
 
 

@@ -74,6 +74,7 @@ struct Engine : EngineBase {
         auto it = caps.find((const void*)kern);
         if (it != caps.end()) return it->second;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         int nb = 0, dev = 0, nsm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
         cudaGetDevice(&dev);
@@ -164,6 +165,7 @@ struct Engine : EngineBase {
         int& cap = gs_cap_slot(which, cand);
         if (cap == 0) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
             int nb = 0, dev = 0, nsm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
             cudaGetDevice(&dev);
@@ -178,7 +180,8 @@ struct Engine : EngineBase {
         case 0: f(std::integral_constant<int, 0>{}); break;
         case 1: f(std::integral_constant<int, 1>{}); break;
         case 2: f(std::integral_constant<int, 2>{}); break;
-        default: f(std::integral_constant<int, 3>{}); break;
+        case 3: f(std::integral_constant<int, 3>{}); break;
+        default: f(std::integral_constant<int, 4>{}); break;
         }
     }
     static TileChoice tiles_of(Handle& H, const std::vector<int>& ds) {
@@ -313,6 +316,7 @@ struct Engine : EngineBase {
     // launch: one thread-block cluster per instance (tail.cuh).  The cluster
     // size is 16 CTAs (non-portable) when the GPU can schedule it, else 8.
     int tail_cluster(Handle& H) {
+        if (H.p.tail_cluster > 0) return H.p.tail_cluster;
         static int cl = 0;
         if (cl) return cl;
         auto kern = k_adr_tail<T>;

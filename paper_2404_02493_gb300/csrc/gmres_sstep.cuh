@@ -30,18 +30,26 @@
 namespace wadr {
 
 // ------------------------------------------------------------ candidates
-constexpr int GS_NCAND = 4;
+constexpr int GS_NCAND = 5;
 constexpr int GS_WPB = 4;            // warps per block of the streaming kernel
 struct GsShape { int x, y; };
-// gram: 0, 1 = tiles of x * y fine nodes; 2, 3 = streaming strips of 56
+// gram: 0, 1 = tiles of x * y fine nodes; 2, 3, 4 = streaming strips of 56
 // result columns by y rows
 __host__ __device__ constexpr GsShape gs_gram_shape(int i) {
-    return i == 0 ? GsShape{32, 8} : i == 1 ? GsShape{32, 16} : i == 2 ? GsShape{SW_OUT, 32} : GsShape{SW_OUT, 64};
+    return i == 0 ? GsShape{32, 8}
+         : i == 1 ? GsShape{32, 16}
+         : i == 2 ? GsShape{SW_OUT, 16}
+         : i == 3 ? GsShape{SW_OUT, 32}
+                  : GsShape{SW_OUT, 64};
 }
 __host__ __device__ constexpr bool gs_gram_streaming(int i) { return i >= 2; }
 // pre: tiles of x * y coarse nodes (fine footprint 2x+1 by 2y+1)
 __host__ __device__ constexpr GsShape gs_pre_shape(int i) {
-    return i == 0 ? GsShape{16, 8} : i == 1 ? GsShape{32, 8} : i == 2 ? GsShape{16, 16} : GsShape{32, 4};
+    return i == 0 ? GsShape{16, 8}
+         : i == 1 ? GsShape{32, 8}
+         : i == 2 ? GsShape{16, 16}
+         : i == 3 ? GsShape{32, 4}
+                  : GsShape{16, 4};
 }
 constexpr int GS_DEFAULT_GRAM = 1, GS_DEFAULT_PRE = 0;
 
@@ -136,24 +144,64 @@ __device__ __forceinline__ void sl_stage(int n, const cplx<T>* __restrict__ Sin,
     }
 }
 
+// Running Gram terms of one thread: nrm[i] holds the two halves of |K_i|^2,
+// crs[] the six <K_a, K_b> (a < b) as sums of conj(a) b.  FP32 uses packed
+// FP32x2 instructions (two per cross term, one per norm).
 template <typename T>
-__device__ __forceinline__ void gram_acc(cplx<T> (&ac)[8], cplx<T> k0, cplx<T> k1, cplx<T> k2, cplx<T> k3) {
-    ac[0].x += cabs2<T>(k0);
-    ac[0].y += cabs2<T>(k1);
-    ac[1].x += cabs2<T>(k2);
-    ac[1].y += cabs2<T>(k3);
-    ac[2] = cadd<T>(ac[2], cmulc<T>(k0, k1));
-    ac[3] = cadd<T>(ac[3], cmulc<T>(k0, k2));
-    ac[4] = cadd<T>(ac[4], cmulc<T>(k0, k3));
-    ac[5] = cadd<T>(ac[5], cmulc<T>(k1, k2));
-    ac[6] = cadd<T>(ac[6], cmulc<T>(k1, k3));
-    ac[7] = cadd<T>(ac[7], cmulc<T>(k2, k3));
+struct GramAcc {
+    cplx<T> nrm[4], crs[6];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nrm[k] = zero2<T>();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) crs[k] = zero2<T>();
+    }
+    // the entries in the reduction layout of gs_solve
+    __device__ __forceinline__ void to_layout(cplx<T> (&ac)[8]) const {
+        ac[0] = mk<T>(nrm[0].x + nrm[0].y, nrm[1].x + nrm[1].y);
+        ac[1] = mk<T>(nrm[2].x + nrm[2].y, nrm[3].x + nrm[3].y);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ac[2 + k] = crs[k];
+    }
+};
+template <typename T>
+__device__ __forceinline__ void gacc_norm(cplx<T>& acc, cplx<T> a) {
+    acc.x += a.x * a.x;
+    acc.y += a.y * a.y;
+}
+template <typename T>
+__device__ __forceinline__ void gacc_cross(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+    acc = cadd<T>(acc, cmulc<T>(a, b));
+}
+template <>
+__device__ __forceinline__ void gacc_norm<float>(float2& acc, float2 a) {
+    acc = __ffma2_rn(a, a, acc);
+}
+template <>
+__device__ __forceinline__ void gacc_cross<float>(float2& acc, float2 a, float2 b) {
+    acc = __ffma2_rn(make_float2(a.x, a.x), b, acc);
+    acc = __ffma2_rn(make_float2(a.y, -a.y), make_float2(b.y, b.x), acc);
+}
+template <typename T>
+__device__ __forceinline__ void gram_acc(GramAcc<T>& g, cplx<T> k0, cplx<T> k1, cplx<T> k2, cplx<T> k3) {
+    gacc_norm<T>(g.nrm[0], k0);
+    gacc_norm<T>(g.nrm[1], k1);
+    gacc_norm<T>(g.nrm[2], k2);
+    gacc_norm<T>(g.nrm[3], k3);
+    gacc_cross<T>(g.crs[0], k0, k1);
+    gacc_cross<T>(g.crs[1], k0, k2);
+    gacc_cross<T>(g.crs[2], k0, k3);
+    gacc_cross<T>(g.crs[3], k1, k2);
+    gacc_cross<T>(g.crs[4], k1, k3);
+    gacc_cross<T>(g.crs[5], k2, k3);
 }
 
 // reduction of the Gram entries of a launch and the small solve
 template <typename T>
-__device__ __forceinline__ void gram_finish(const LevelDesc& d, const SegCtx& c, cplx<T> (&ac)[8], cplx<T>* sh,
+__device__ __forceinline__ void gram_finish(const LevelDesc& d, const SegCtx& c, const GramAcc<T>& g, cplx<T>* sh,
                                             int* flag) {
+    cplx<T> ac[8];
+    g.to_layout(ac);
     block_sum<cplx<T>, 8>(ac, sh);
     if (publish_partials<cplx<T>, 8>(partp<T>(d), MAXDOT, d.counter, c.lb, c.nb, ac, flag)) {
         cplx<T> tot[8];
@@ -194,9 +242,8 @@ __global__ void __launch_bounds__(NT) k_gs_gram_tile(const LevelDesc* __restrict
         async_region<cplx<T>, W0, H0>(S0b + b * W0 * H0, r0, n, pitch, x0 - 3, y0 - 3);
         async_region<quad<T>, W1, H1>(Qb + b * W1 * H1, coef, n, pitch, x0 - 2, y0 - 2);
     };
-    cplx<T> ac[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ac[k] = zero2<T>();
+    GramAcc<T> ac;
+    ac.zero();
     int buf = 0;
     if (c.lb < ntiles) issue(c.lb, 0);
     cp_async_commit();
@@ -258,9 +305,8 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const LevelDesc*
     cplx<T>* k2o = slot<T>(d, SK2);
     const quad<T>* coef = reinterpret_cast<const quad<T>*>(d.adr);
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
-    cplx<T> ac[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ac[k] = zero2<T>();
+    GramAcc<T> ac;
+    ac.zero();
     for (int u = c.lb * GS_WPB + warp; u < nunits; u += c.nb * GS_WPB) {
         const StripGeo gg = strip_geo(u, nstrips, RH, n);
         const int j0 = gg.y0 - 3, j1 = gg.y1 + 2;

@@ -710,18 +710,14 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
                 cplx<T> v = zero2<T>();
                 const bool in = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n;
                 if (in) {
-                    // 1D weights: odd fine index = coincident coarse node (gi-1)/2
-                    const int ia = (gi & 1) ? (gi - 1) / 2 : gi / 2 - 1;
-                    const int ja = (gj & 1) ? (gj - 1) / 2 : gj / 2 - 1;
+                    // bilinear weights without branches: coarse node (gi-1) >> 1 and the next one
+                    // get (1, 0) for odd gi (coincident node) and (1/2, 1/2) for even gi
+                    const int ia = (gi - 1) >> 1, ja = (gj - 1) >> 1;
+                    const T wa0 = (gi & 1) ? T(1) : T(0.5), wa1 = T(1) - wa0;
+                    const T wb0 = (gj & 1) ? T(1) : T(0.5), wb1 = T(1) - wb0;
                     const int qb = (ja - ey0) * PEW + (ia - ex0);
-                    if (gi & 1) {
-                        if (gj & 1) v = E[qb];
-                        else v = cscale<T>(cadd<T>(E[qb], E[qb + PEW]), T(0.5));
-                    } else {
-                        if (gj & 1) v = cscale<T>(cadd<T>(E[qb], E[qb + 1]), T(0.5));
-                        else v = cscale<T>(cadd<T>(cadd<T>(E[qb], E[qb + 1]), cadd<T>(E[qb + PEW], E[qb + PEW + 1])),
-                                           T(0.25));
-                    }
+                    v = cscale<T>(cadd<T>(cscale<T>(E[qb], wa0), cscale<T>(E[qb + 1], wa1)), wb0);
+                    v = cadd<T>(v, cscale<T>(cadd<T>(cscale<T>(E[qb + PEW], wa0), cscale<T>(E[qb + PEW + 1], wa1)), wb1));
                     if (!xzero) v = cadd<T>(Xb[buf][r * BXW + cc + HAL], v);
                 }
                 if (MODE == PMODE_ADD) {

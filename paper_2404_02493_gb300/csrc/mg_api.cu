@@ -686,6 +686,7 @@ void mg_default_params(mg_params* p) {
     p->tile_candidate = -1;
     p->tail_nmax = 0;
     p->pdl = 0;
+    p->tail_cluster = 0;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -695,7 +696,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
-        p->tile_candidate >= MG_TILE_CANDIDATES) {
+        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }

@@ -107,14 +107,15 @@ __device__ void tail_gram(const LevelDesc& d, int s0, const TailCtx& t, cplx<T>*
     const cplx<T>* k0 = slot<T>(d, s0);
     const cplx<T>* k1 = slot<T>(d, SK1);
     const cplx<T>* k2 = slot<T>(d, SK2);
-    cplx<T> ac[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ac[k] = zero2<T>();
+    GramAcc<T> g;
+    g.zero();
     for (int q = t.gt; q < N; q += t.gn) {
         const int j = q / n, i = q - j * n;
         const long long p = (long long)j * pitch + i;
-        gram_acc<T>(ac, __ldcg(k0 + p), __ldcg(k1 + p), __ldcg(k2 + p), tail_k3<T>(d, k2, i, j, p));
+        gram_acc<T>(g, __ldcg(k0 + p), __ldcg(k1 + p), __ldcg(k2 + p), tail_k3<T>(d, k2, i, j, p));
     }
+    cplx<T> ac[8];
+    g.to_layout(ac);
     block_sum<cplx<T>, 8>(ac, sh);
     cplx<T>* part = partp<T>(d);
     if (threadIdx.x == 0) {

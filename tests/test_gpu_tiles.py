@@ -13,9 +13,9 @@ import synth
 pytestmark = pytest.mark.gpu
 
 # gram pass: shared-memory tiles (32 x 8, 32 x 16 nodes) or warp-streaming
-# strips of 56 result columns by 32 / 64 rows; pre-smoothing: coarse tiles
-GRAM = [(32, 8), (32, 16), (56, 32), (56, 64)]
-PRE = [(16, 8), (32, 8), (16, 16), (32, 4)]
+# strips of 56 result columns by 16 / 32 / 64 rows; pre-smoothing: coarse tiles
+GRAM = [(32, 8), (32, 16), (56, 16), (56, 32), (56, 64)]
+PRE = [(16, 8), (32, 8), (16, 16), (32, 4), (16, 4)]
 
 
 @pytest.fixture(scope="module", autouse=True)
