@@ -15,8 +15,6 @@ LIB = os.path.join(HERE, "libwaveadr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["mg_api.cu", "setup.cu", "engine_f32.cu", "engine_f64.cu", "noalloc.cu", "adjoint.cu"]
-HEADERS = ["common.cuh", "kernels.cuh", "engine.cuh", "handle.h", "setup_kernels.cuh", "fgmres.cuh",
-           "gmres_sstep.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 
@@ -29,7 +27,8 @@ def nvcc() -> str:
 
 
 def _newest_input() -> float:
-    files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
+    # every source and header of the library (headers include one another)
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "wave_adr.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)

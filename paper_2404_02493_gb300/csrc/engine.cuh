@@ -225,7 +225,7 @@ struct Engine : EngineBase {
         gs_dispatch(cand, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             constexpr GsShape sh = gs_pre_shape(I);
-            auto kern = k_gs_pre<T, sh.x, sh.y>;
+            auto kern = k_gs_pre<T, sh.x, sh.y, I>;
             const int smem = gs_pre_smem<T>(I);
             const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, true, gs_prepare(kern, smem, 1, I, NT));
             go(H, st, KK_GS_PRE, (4 * C + Q + C / 4) * (double)t.pts, [&] {
@@ -258,7 +258,7 @@ struct Engine : EngineBase {
                 else
                     gs_prepare(k_gs_gram_tile<T, gs_gram_shape(I).x, gs_gram_shape(I).y>, gs_gram_smem<T>(I), 0, I,
                                NT);
-                gs_prepare(k_gs_pre<T, gs_pre_shape(I).x, gs_pre_shape(I).y>, gs_pre_smem<T>(I), 1, I, NT);
+                gs_prepare(k_gs_pre<T, gs_pre_shape(I).x, gs_pre_shape(I).y, I>, gs_pre_smem<T>(I), 1, I, NT);
             });
         }
         if (!H.p.adr || H.p.M <= 0 || !H.p.autotune || H.p.tile_candidate >= 0) return MG_OK;

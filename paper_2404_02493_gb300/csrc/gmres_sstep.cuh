@@ -52,6 +52,8 @@ __host__ __device__ constexpr GsShape gs_pre_shape(int i) {
                   : GsShape{16, 4};
 }
 constexpr int GS_DEFAULT_GRAM = 1, GS_DEFAULT_PRE = 0;
+static_assert(MC_PRE_K01 - MC_PRE_K2 == GS_NCAND && MQ_PRE - MC_PRE_K01 == GS_NCAND && NMAP - MQ_PRE == GS_NCAND,
+              "one tensor map per pre-smoothing candidate");
 
 template <typename T> struct GsEps;
 template <> struct GsEps<float> { static constexpr float tau = 32.0f * 1.1920929e-7f; };
@@ -371,56 +373,63 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const LevelDesc*
 // x = s (c0 K0 + c1 K1 + c2 K2) to slot sx; r = K0 - c0 K1 - c1 K2 - c2 K3
 // with K3 = s L K2 formed here, restricted by full weighting to slot sc of
 // the next level.  Tiles are CX x CY coarse nodes; the fine footprint of a
-// tile is (2CX+1) x (2CY+1) from fine node (2 I0, 2 J0); K2 is staged with a
-// one-node ring.  Double-buffered like the gram tiles.
-template <typename T, int CX, int CY>
+// tile is (2CX+1) x (2CY+1) from fine node (2 I0, 2 J0).  K2 (with a
+// one-node ring), K0, K1 and the coefficient quads arrive by TMA in two
+// alternating buffers (tensor maps MC_PRE_K2 / MC_PRE_K01 / MQ_PRE + CAND).
+template <int CX, int CY>
+struct PreGeo {
+    static constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1, NF = FW * FH;
+    static constexpr int KW = FW + 3, KH = FH + 2;   // K2 box from (fx0 - 2, fy0 - 1)
+    static constexpr int AW = FW + 1;                // K0 / K1 box from (fx0, fy0), FH rows
+};
+template <typename T, int CX, int CY, int CAND>
 __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                int nseg, int sb, int sx, int sc) {
-    constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1, W2 = FW + 2, H2 = FH + 2;
-    constexpr int NF = FW * FH;
-    extern __shared__ __align__(16) unsigned char gs_smem[];
-    quad<T>* Qb = reinterpret_cast<quad<T>*>(gs_smem);            // [2][NF]
-    cplx<T>* K2b = reinterpret_cast<cplx<T>*>(Qb + 2 * NF);        // [2][W2 H2]
-    cplx<T>* K0b = K2b + 2 * W2 * H2;                              // [2][NF]
-    cplx<T>* K1b = K0b + 2 * NF;                                   // [2][NF]
-    cplx<T>* R = K1b + 2 * NF;                                     // [NF]
+    using G = PreGeo<CX, CY>;
+    constexpr int FW = G::FW, FH = G::FH, NF = G::NF, KW = G::KW, KH = G::KH, AW = G::AW;
+    // per buffer: quads | K2 | K0 | K1 (128-byte aligned pieces); then R
+    constexpr int OQ = 0, OK2 = OQ + tma_piece<quad<T>>(NF), OK0 = OK2 + tma_piece<cplx<T>>(KW * KH),
+                  OK1 = OK0 + tma_piece<cplx<T>>(AW * FH), BUFB = OK1 + tma_piece<cplx<T>>(AW * FH);
+    extern __shared__ unsigned char gs_smem[];
+    unsigned char* const sm0 = reinterpret_cast<unsigned char*>(((uintptr_t)gs_smem + 127) & ~(uintptr_t)127);
+    cplx<T>* R = reinterpret_cast<cplx<T>*>(sm0 + 2 * BUFB);
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
+    __shared__ alignas(8) uint64_t bars[2];
     SegCtx c = seg_begin(D, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     copy_desc(dc, D + d.coarse, tid);
-    __syncthreads();
+    TmaPipe pipe;
+    pipe.init(bars);
     const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
     const int ntx = (nc + CX - 1) / CX, ntiles = ntx * ((nc + CY - 1) / CY);
-    const cplx<T>* k0g = slot<T>(d, sb);
-    const cplx<T>* k1g = slot<T>(d, SK1);
-    const cplx<T>* k2g = slot<T>(d, SK2);
-    const quad<T>* coef = reinterpret_cast<const quad<T>*>(d.adr);
     cplx<T>* xs = slot<T>(d, sx);
     cplx<T>* out = slot<T>(dc, sc);
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
     const T* scl = scalp<T>(d);
     const cplx<T> c0 = sload2<T>(scl, S::GC), c1 = sload2<T>(scl, S::GC + 2), c2 = sload2<T>(scl, S::GC + 4);
     const cplx<T> sc0 = cscale<T>(c0, s), sc1 = cscale<T>(c1, s), sc2 = cscale<T>(c2, s);
+    constexpr unsigned bytes = (unsigned)(NF * sizeof(quad<T>) + (KW * KH + 2 * AW * FH) * sizeof(cplx<T>));
     auto issue = [&](int t, int b) {
-        const int fx0 = 2 * (t % ntx) * CX, fy0 = 2 * (t / ntx) * CY;
-        async_region<cplx<T>, W2, H2>(K2b + b * W2 * H2, k2g, n, pitch, fx0 - 1, fy0 - 1);
-        async_region<cplx<T>, FW, FH>(K0b + b * NF, k0g, n, pitch, fx0, fy0);
-        async_region<cplx<T>, FW, FH>(K1b + b * NF, k1g, n, pitch, fx0, fy0);
-        async_region<quad<T>, FW, FH>(Qb + b * NF, coef, n, pitch, fx0, fy0);
+        if (tid != 0) return;
+        const int fx0 = 2 * (t % ntx) * CX, fy0 = 2 * (t / ntx) * CY;   // even: 16-byte aligned x
+        unsigned char* bp = sm0 + b * BUFB;
+        pipe.expect(b, bytes);
+        tma_load_3d(bp + OK2, tmap(d, MC_PRE_K2 + CAND), 2 * (fx0 - 2), fy0 - 1, SK2, &bars[b]);
+        tma_load_3d(bp + OK0, tmap(d, MC_PRE_K01 + CAND), 2 * fx0, fy0, sb, &bars[b]);
+        tma_load_3d(bp + OK1, tmap(d, MC_PRE_K01 + CAND), 2 * fx0, fy0, SK1, &bars[b]);
+        tma_load_3d(bp + OQ, tmap(d, MQ_PRE + CAND), 0, fx0, fy0, &bars[b]);
     };
     int buf = 0;
     if (c.lb < ntiles) issue(c.lb, 0);
-    cp_async_commit();
     for (int t = c.lb; t < ntiles; t += c.nb) {
         if (t + c.nb < ntiles) issue(t + c.nb, buf ^ 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const cplx<T>* K2s = K2b + buf * W2 * H2;
-        const cplx<T>* K0s = K0b + buf * NF;
-        const cplx<T>* K1s = K1b + buf * NF;
-        const quad<T>* Q = Qb + buf * NF;
+        if (!pipe.wait(buf, d.err)) return;
+        const unsigned char* bp = sm0 + buf * BUFB;
+        const cplx<T>* K2s = reinterpret_cast<const cplx<T>*>(bp + OK2);
+        const cplx<T>* K0s = reinterpret_cast<const cplx<T>*>(bp + OK0);
+        const cplx<T>* K1s = reinterpret_cast<const cplx<T>*>(bp + OK1);
+        const quad<T>* Q = reinterpret_cast<const quad<T>*>(bp + OQ);
         const int I0 = (t % ntx) * CX, J0 = (t / ntx) * CY;
         const int fx0 = 2 * I0, fy0 = 2 * J0;
         // fine nodes this tile writes (the last tile in a direction takes the rest)
@@ -434,9 +443,9 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
                 const int gi = fx0 + cc, gj = fy0 + r;
                 cplx<T> v = zero2<T>();
                 if (gi < n && gj < n) {
-                    const int b2 = (r + 1) * W2 + cc + 1;
-                    const cplx<T> k0 = K0s[e], k1 = K1s[e], k2 = K2s[b2];
-                    const cplx<T> k3 = sl_q<T>(Q[e], K2s, b2, W2, ih2, wh, s);
+                    const int b2 = (r + 1) * KW + cc + 2, a = r * AW + cc;
+                    const cplx<T> k0 = K0s[a], k1 = K1s[a], k2 = K2s[b2];
+                    const cplx<T> k3 = sl_q<T>(Q[e], K2s, b2, KW, ih2, wh, s);
                     v = csub<T>(k0, cmul<T>(c0, k1));
                     v = csub<T>(v, cmul<T>(c1, k2));
                     v = csub<T>(v, cmul<T>(c2, k3));
@@ -467,7 +476,6 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
         __syncthreads();
         buf ^= 1;
     }
-    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------ post-smoothing update
@@ -523,9 +531,10 @@ template <typename T> constexpr int gs_gram_smem(int i) {
                                           (gs_gram_shape(i).x + 2) * (gs_gram_shape(i).y + 2)));
 }
 template <typename T> constexpr int gs_pre_smem(int i) {
-    return (int)(sizeof(quad<T>) * 2 * (2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1) +
-                 sizeof(cplx<T>) * (2 * (2 * gs_pre_shape(i).x + 3) * (2 * gs_pre_shape(i).y + 3) +
-                                    5 * (2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1)));
+    return 128 + 2 * (tma_piece<quad<T>>((2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1)) +
+                      tma_piece<cplx<T>>((2 * gs_pre_shape(i).x + 4) * (2 * gs_pre_shape(i).y + 3)) +
+                      2 * tma_piece<cplx<T>>((2 * gs_pre_shape(i).x + 2) * (2 * gs_pre_shape(i).y + 1))) +
+           tma_piece<cplx<T>>((2 * gs_pre_shape(i).x + 1) * (2 * gs_pre_shape(i).y + 1));
 }
 
 }  // namespace wadr

@@ -291,6 +291,12 @@ static int build_tmaps_desc(const LevelDesc& d, int nslot, int prec, CUtensorMap
         ok = real_map(MS_CHEB, d.sig, CKW, CKH) && real_map(MS_RESTR, d.sig, RKW, RHH) &&
              real_map(MS_PROL, d.sig, PTX, PTY);
     if (ok && d.adr) ok = quad_map(MQ_PROL, PTX, PTY);
+    if (ok && d.adr)
+        for (int c = 0; c < GS_NCAND && ok; ++c) {
+            const int FW = 2 * gs_pre_shape(c).x + 1, FH = 2 * gs_pre_shape(c).y + 1;
+            ok = cplx_map(MC_PRE_K2 + c, FW + 3, FH + 2) && cplx_map(MC_PRE_K01 + c, FW + 1, FH) &&
+                 quad_map(MQ_PRE + c, FW, FH);
+        }
     if (!ok) { set_error("mg_setup: tensor map encoding failed"); return MG_ECUDA; }
     return MG_OK;
 }

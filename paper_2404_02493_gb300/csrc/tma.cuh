@@ -106,7 +106,10 @@ enum MapId : int {
     MQ_PROL,         // quads,   PTX x PTY
     MK_PROL,         // k,       PTX x PTY
     MS_PROL,
-    NMAP
+    MC_PRE_K2,                            // complex, (2CX+4) x (2CY+3)  from (fx0-2, fy0-1), per pre candidate
+    MC_PRE_K01 = MC_PRE_K2 + 5,           // complex, (2CX+2) x (2CY+1)  from (fx0, fy0)
+    MQ_PRE = MC_PRE_K01 + 5,              // quads,   (2CX+1) x (2CY+1)  from (fx0, fy0)
+    NMAP = MQ_PRE + 5
 };
 constexpr int TMAP_BYTES = 128;   // sizeof(CUtensorMap)
 
