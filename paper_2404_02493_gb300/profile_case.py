@@ -2,6 +2,7 @@
 
     python -m paper_2404_02493_gb300.profile_case --n 2047 --cycles 1 --tile 3
     python -m paper_2404_02493_gb300.profile_case --n 2047 --fgmres 8
+    python -m paper_2404_02493_gb300.profile_case --n 1023 --param tail_nmax=127
 
 Sets up one layered-medium instance (the benchmark's recipe at a smaller n,
 omega scaled to keep k h), optionally a fixed halo-tile candidate instead of
@@ -27,6 +28,8 @@ def main(argv=None):
     ap.add_argument("--tile", type=int, default=-1, help="force halo-tile candidate (default: autotune)")
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--fgmres", type=int, default=0, help="run K FGMRES iterations instead of cycles")
+    ap.add_argument("--param", action="append", default=[], metavar="NAME=INT",
+                    help="set an integer field of mg_params (e.g. tail_nmax=127); repeatable")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -39,8 +42,9 @@ def main(argv=None):
     dev = torch.device("cuda", 0)
     k = torch.from_numpy(inst.k).to(dev)
     phi = torch.from_numpy(inst.phi).to(dev)
+    extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in a.param}
     p = B.default_params(precision=a.precision, n_cmax=15, outer="fgmres" if a.fgmres else "ir", use_graph=0,
-                         autotune=0 if a.tile >= 0 else 1, tile_candidate=a.tile)
+                         autotune=0 if a.tile >= 0 else 1, tile_candidate=a.tile, **extra)
     st = torch.cuda.current_stream()
     h = B.mg_setup([(n, omega, k, phi, "abc1")], p, stream=st)
     dt = torch.complex64 if a.precision == "mixed" else torch.complex128
