@@ -191,10 +191,12 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
     constexpr int P = fg_chunk<TC>();
     extern __shared__ unsigned char fg_raw[];
     TmaCarve cv(fg_raw);
-    // [stage][V_0..V_{MAXR-1}, W][P]; P values = 4 KB, so every piece stays 128-byte aligned
+    // a stage holds (MAXR + 1) * P values; with j + 2 vectors to stream the
+    // chunk is PJ = P * floor((MAXR + 1) / (j + 2)) values long, so a stage
+    // is (nearly) full at every j: [stage][V_0..V_j, W][PJ].  P values =
+    // 4 KB, so every piece stays 128-byte aligned.
     static_assert(P * sizeof(cplx<TC>) % 128 == 0, "chunk size");
     cplx<TC>* const stg0 = cv.take<cplx<TC>>(2 * (MAXR + 1) * P);
-    auto stg = [&](int b, int q) { return stg0 + (b * (MAXR + 1) + q) * P; };
     __shared__ LevelDesc d;
     __shared__ double2 grp[8 * 32];
     __shared__ double2 tot[NVF];
@@ -207,8 +209,10 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
     pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const long long N = (long long)d.n * d.pitch;
-    const int nchunks = (int)((N + P - 1) / P);
     const int jj = (int)d.fs[FS::J];
+    const int PJ = P * ((MAXR + 1) / (jj + 2));
+    const int nchunks = (int)((N + PJ - 1) / PJ);
+    auto stg = [&](int b, int q) { return stg0 + b * (MAXR + 1) * P + q * PJ; };
     cplx<TC>* w = kvec<TC>(d, jj + 1);
     if (PASS > 0) {
         const int off = (PASS == 1) ? FS::HC : FS::CC;
@@ -217,11 +221,11 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
     __syncthreads();
     auto issue = [&](int k, int b) {
         if (tid != 0) return;
-        const long long e0 = (long long)k * P;
-        const unsigned bytes = (unsigned)(min((long long)P, N - e0) * (long long)sizeof(cplx<TC>));
+        const long long e0 = (long long)k * PJ;
+        const unsigned bytes = (unsigned)(min((long long)PJ, N - e0) * (long long)sizeof(cplx<TC>));
         pipe.expect(b, bytes * (unsigned)(jj + 2));
         for (int q = 0; q <= jj; ++q) bulk_load(stg(b, q), kvec<TC>(d, q) + e0, bytes, &bars[b]);
-        bulk_load(stg(b, MAXR), w + e0, bytes, &bars[b]);
+        bulk_load(stg(b, jj + 1), w + e0, bytes, &bars[b]);
     };
     constexpr int NA = (PASS == 2) ? 1 : NVF;
     cplx<TC> ac[NA];
@@ -233,30 +237,26 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
     for (int k = c.lb; k < nchunks; k += c.nb) {
         if (k + c.nb < nchunks) issue(k + c.nb, buf ^ 1);
         if (!pipe.wait(buf, d.err)) return;
-        const long long e0 = (long long)k * P;
-        const int cnt = (int)min((long long)P, N - e0);
+        const long long e0 = (long long)k * PJ;
+        const int cnt = (int)min((long long)PJ, N - e0);
+        const cplx<TC>* sv = stg(buf, 0);
+        for (int e = tid; e < cnt; e += NT) {
+            cplx<TC> wv = sv[(jj + 1) * PJ + e];
+            if (PASS == 0) {
 #pragma unroll
-        for (int r = 0; r < P / NT; ++r) {
-            const int e = tid + r * NT;
-            if (e < cnt) {
-                const cplx<TC>* sv = stg(buf, 0);
-                cplx<TC> wv = sv[MAXR * P + e];
-                if (PASS == 0) {
+                for (int q = 0; q < MAXR; ++q)
+                    if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * PJ + e], wv));
+            } else {
+#pragma unroll
+                for (int q = 0; q < MAXR; ++q)
+                    if (q <= jj) wv = csub<TC>(wv, cmul<TC>(coef[q], sv[q * PJ + e]));
+                w[e0 + e] = wv;
+                if (PASS == 1) {
 #pragma unroll
                     for (int q = 0; q < MAXR; ++q)
-                        if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * P + e], wv));
-                } else {
-#pragma unroll
-                    for (int q = 0; q < MAXR; ++q)
-                        if (q <= jj) wv = csub<TC>(wv, cmul<TC>(coef[q], sv[q * P + e]));
-                    w[e0 + e] = wv;
-                    if (PASS == 1) {
-#pragma unroll
-                        for (int q = 0; q < MAXR; ++q)
-                            if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * P + e], wv));
-                    }
-                    nrm += cabs2<TC>(wv);
+                        if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * PJ + e], wv));
                 }
+                nrm += cabs2<TC>(wv);
             }
         }
         __syncthreads();

@@ -809,8 +809,17 @@ __global__ void __launch_bounds__(NT) k_coarse(const LevelDesc* __restrict__ D, 
     const int lane = tid & 31, wid = tid >> 5;
     for (int row = c.lb * (NT / 32) + wid; row < N; row += c.nb * (NT / 32)) {
         const double2* a = Ainv + (long long)row * N;
+        // four fused multiply-adds per complex term; unrolled so that the
+        // loads of a row are in flight together
         double2 acc = make_double2(0, 0);
-        for (int q = lane; q < N; q += 32) acc = dadd(acc, dmul(__ldg(a + q), bsh[q]));
+#pragma unroll 4
+        for (int q = lane; q < N; q += 32) {
+            const double2 av = __ldg(a + q), bv = bsh[q];
+            acc.x = fma(av.x, bv.x, acc.x);
+            acc.x = fma(-av.y, bv.y, acc.x);
+            acc.y = fma(av.x, bv.y, acc.y);
+            acc.y = fma(av.y, bv.x, acc.y);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);

@@ -94,6 +94,23 @@ std::string desc_key(const std::vector<int>& ids) {
     return key;
 }
 
+// Blocks of a persistent launch over several segments (instances): one wave
+// of `cap` blocks shared in proportion to each segment's work units (tiles
+// or chunks), so that every block loops over several units and its copy
+// pipeline stays busy.  Each segment gets at least one block and at most
+// min(units, MAXB); a single segment gets min(units, cap, MAXB).
+static std::vector<int> share_blocks(const std::vector<long long>& units, int cap) {
+    long long tot = 0;
+    for (long long u : units) tot += u;
+    std::vector<int> nb(units.size());
+    for (size_t q = 0; q < units.size(); ++q) {
+        long long b = units[q];
+        if (tot > cap) b = (long long)((double)cap * (double)units[q] / (double)tot);
+        nb[q] = (int)std::max(1LL, std::min({b, units[q], (long long)MAXB}));
+    }
+    return nb;
+}
+
 const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, bool coarse, int cap) {
     std::string key = "t" + std::to_string(tx) + "x" + std::to_string(ty) + (coarse ? "c" : "f") +
                       std::to_string(cap) + desc_key(ids);
@@ -101,19 +118,23 @@ const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, b
     if (it != segs.end()) return it->second;
     std::vector<Seg> h;
     SegTable t;
-    int blk = 0;
+    std::vector<long long> units;
     for (int i : ids) {
         const LevelDesc& d = hdesc[i];
         const int n = coarse ? hdesc[d.coarse].n : d.n;
-        const long long ntiles = (long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty);
+        units.push_back((long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty));
+        t.pts += (long long)d.n * d.n;
+    }
+    const std::vector<int> nb = share_blocks(units, cap);
+    int blk = 0;
+    for (size_t q = 0; q < ids.size(); ++q) {
         Seg s;
-        s.desc = i;
+        s.desc = ids[q];
         s.blk0 = blk;
-        blk += (int)std::max(1LL, std::min(ntiles, (long long)std::min(cap, MAXB)));
+        blk += nb[q];
         s.blk1 = blk;
         s.pad = 0;
         h.push_back(s);
-        t.pts += (long long)d.n * d.n;
     }
     t.nseg = (int)h.size();
     t.nblocks = blk;
@@ -128,18 +149,22 @@ const SegTable& Handle::seg_outer_chunks(const std::vector<int>& ids, int chunk,
     if (it != segs.end()) return it->second;
     std::vector<Seg> h;
     SegTable t;
-    int blk = 0;
+    std::vector<long long> units;
     for (int i : ids) {
         const LevelDesc& d = houter[i];
-        const long long nch = ((long long)d.n * d.pitch + chunk - 1) / chunk;
+        units.push_back(((long long)d.n * d.pitch + chunk - 1) / chunk);
+        t.pts += (long long)d.n * d.n;
+    }
+    const std::vector<int> nb = share_blocks(units, cap);
+    int blk = 0;
+    for (size_t q = 0; q < ids.size(); ++q) {
         Seg s;
-        s.desc = i;
+        s.desc = ids[q];
         s.blk0 = blk;
-        blk += (int)std::max(1LL, std::min(nch, (long long)std::min(cap, MAXB)));
+        blk += nb[q];
         s.blk1 = blk;
         s.pad = 0;
         h.push_back(s);
-        t.pts += (long long)d.n * d.n;
     }
     t.nseg = (int)h.size();
     t.nblocks = blk;
