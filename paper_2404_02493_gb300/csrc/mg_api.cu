@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -54,6 +55,37 @@ void* Handle::alloc(size_t bytes) {
     return p;
 }
 
+// Blocks of a persistent launch over several segments (instances): one wave
+// of `cap` blocks shared among the segments so that the largest number of
+// work units (tiles, chunks) a block of any segment loops over is as small
+// as possible (greedy: every segment starts with one block, each further
+// block goes to the segment with the largest units per block).  A segment
+// gets at most min(units, MAXB) blocks; a single segment gets
+// min(units, cap, MAXB).  Blocks that loop over several units keep their
+// copy pipelines busy and pay the descriptor set-up once.
+static std::vector<int> share_blocks(const std::vector<long long>& units, int cap) {
+    const size_t ns = units.size();
+    std::vector<int> nb(ns, 1);
+    long long tot = 0;
+    for (long long u : units) tot += u;
+    auto limit = [&](size_t q) { return (int)std::min(std::max(units[q], 1LL), (long long)MAXB); };
+    if (tot <= cap) {
+        for (size_t q = 0; q < ns; ++q) nb[q] = limit(q);
+        return nb;
+    }
+    auto load = [&](size_t q) { return (units[q] + nb[q] - 1) / nb[q]; };
+    std::priority_queue<std::pair<long long, size_t>> pq;
+    for (size_t q = 0; q < ns; ++q)
+        if (nb[q] < limit(q)) pq.push({load(q), q});
+    for (long long left = (long long)cap - (long long)ns; left > 0 && !pq.empty(); --left) {
+        const size_t q = pq.top().second;
+        pq.pop();
+        ++nb[q];
+        if (nb[q] < limit(q)) pq.push({load(q), q});
+    }
+    return nb;
+}
+
 static int blocks_for(long long pts, int per) {
     long long b = (pts + per - 1) / per;
     return (int)std::max(1LL, std::min(b, 1216LL));
@@ -65,13 +97,18 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
     auto it = segs.find(key);
     if (it != segs.end()) return it->second;
     std::vector<Seg> h;
-    int blk = 0;
+    std::vector<long long> units;
     for (int i : ids) {
         const LevelDesc& d = outer ? houter[i] : hdesc[i];
+        units.push_back(((long long)d.n * d.n + pts - 1) / pts);
+    }
+    const std::vector<int> nb = share_blocks(units, 1216);
+    int blk = 0;
+    for (size_t q = 0; q < ids.size(); ++q) {
         Seg s;
-        s.desc = i;
+        s.desc = ids[q];
         s.blk0 = blk;
-        blk += blocks_for((long long)d.n * d.n, pts);
+        blk += nb[q];
         s.blk1 = blk;
         s.pad = 0;
         h.push_back(s);
@@ -92,23 +129,6 @@ std::string desc_key(const std::vector<int>& ids) {
     std::string key;
     for (int i : ids) key += "," + std::to_string(i);
     return key;
-}
-
-// Blocks of a persistent launch over several segments (instances): one wave
-// of `cap` blocks shared in proportion to each segment's work units (tiles
-// or chunks), so that every block loops over several units and its copy
-// pipeline stays busy.  Each segment gets at least one block and at most
-// min(units, MAXB); a single segment gets min(units, cap, MAXB).
-static std::vector<int> share_blocks(const std::vector<long long>& units, int cap) {
-    long long tot = 0;
-    for (long long u : units) tot += u;
-    std::vector<int> nb(units.size());
-    for (size_t q = 0; q < units.size(); ++q) {
-        long long b = units[q];
-        if (tot > cap) b = (long long)((double)cap * (double)units[q] / (double)tot);
-        nb[q] = (int)std::max(1LL, std::min({b, units[q], (long long)MAXB}));
-    }
-    return nb;
 }
 
 const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, bool coarse, int cap) {
