@@ -378,25 +378,41 @@ struct Engine : EngineBase {
         }, pts);
     }
 
+    // Instance b runs levels l.. of the ADR V-cycle with per-level launches
+    // (not the coarsest level, not in the coarse tail).
+    static bool adr_per_level(Handle& H, int b, int l) {
+        return H.inst[b].L > l && !(l >= 3 && H.inst[b].lv[l - 1].n <= H.p.tail_nmax);
+    }
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
     // level l, result in SAX (or, at level 2 with `modulate`, added as
-    // exp(+i w phi) a to the wave iterate SU).
-    void adrv(Handle& H, int l, const std::vector<int>& I, bool modulate, cudaStream_t st) {
+    // exp(+i w phi) a to the wave iterate SU).  With `defer` (a recursive
+    // call) the post-smoothing update of the per-level instances is left to
+    // the caller's prolongation (PMODE_ADRF), which forms the result on the
+    // fly; SAX of this level is then not written.
+    void adrv(Handle& H, int l, const std::vector<int>& I, bool modulate, cudaStream_t st, bool defer = false) {
         std::vector<int> co, rest0, tail, rest;
         for (int b : I) (H.inst[b].L == l ? co : rest0).push_back(b);
         if (!co.empty()) coarse_solve(H, co, l, 1, st);
-        for (int b : rest0)
-            (l >= 3 && H.inst[b].lv[l - 1].n <= H.p.tail_nmax ? tail : rest).push_back(b);
+        for (int b : rest0) (adr_per_level(H, b, l) ? rest : tail).push_back(b);
         if (!tail.empty()) launch_tail(H, l, tail, st);
         if (rest.empty()) return;
         const std::vector<int> ds = descs(H, l, rest);
         const TileChoice tc = tiles_of(H, ds);
         gs_gram(H, ds, tc.gram, SAB, st);   // pre-smoothing from x = 0: r0 = b
         gs_pre(H, ds, tc.pre, st);          // x to SAX, restricted residual to SAB of l+1
-        adrv(H, l + 1, rest, false, st);
-        launch_prolong<PMODE_ADR>(H, ds, KK_PROLONG_ADR, 4 * C + C / 4 + Q, SAX, SAX, SAB, SV1, SD, 0, st);
+        adrv(H, l + 1, rest, false, st, true);
+        // x' = x + P e, r0 = b - L x'; e is the coarse SAX (coarsest level or
+        // coarse tail) or the coarse post-smoothing result formed here
+        std::vector<int> plain, fused;
+        for (int b : rest) (adr_per_level(H, b, l + 1) ? fused : plain).push_back(b);
+        if (!plain.empty())
+            launch_prolong<PMODE_ADR>(H, descs(H, l, plain), KK_PROLONG_ADR, 4 * C + C / 4 + Q, SAX, SAX, SAB, SV1, SD,
+                                      0, st);
+        if (!fused.empty())
+            launch_prolong<PMODE_ADRF>(H, descs(H, l, fused), KK_PROLONG_ADR, 4 * C + C + Q, SAX, SAX, SAB, SV1, SD,
+                                       0, st);
         gs_gram(H, ds, tc.gram, SV1, st);   // post-smoothing from x' (r0 = b - L x')
-        gs_post(H, ds, SV1, SD, modulate ? 2 : 0, st);
+        if (!defer) gs_post(H, ds, SV1, SD, modulate ? 2 : 0, st);
     }
 
     // Algorithm 1's ADR correction steps at level 2 (M times).

@@ -607,17 +607,27 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
     }
 }
 
+// ----------------------------------------------------------- scalar helpers
+template <typename T> __device__ __forceinline__ cplx<T> sload2(const T* s, int off) { return mk<T>(s[off], s[off + 1]); }
+template <typename T> __device__ __forceinline__ void sstore2(T* s, int off, cplx<T> v) { s[off] = v.x; s[off + 1] = v.y; }
+template <typename T> __device__ __forceinline__ T cabs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
+
 // ----------------------------------------------------------- prolongation tile
 // Bilinear interpolation P = 4 R^T of the coarse correction (slot `sc` of
 // the next level), fused with the step that consumes it:
 //   PMODE_ADD:  x[sout] = x[sx] + P e  (pointwise; sout may equal sx)
 //   PMODE_JAC:  u = x[sx] + P e;  x[sout] = u + w D^{-1}(g - A u)   (level 1 post)
 //   PMODE_ADR:  x' = x[sx] + P e written to sxo;  r0 = b[sb] - L x' to sout
+//   PMODE_ADRF: as PMODE_ADR, with the coarse level's GMRES(3) post-smoothing
+//               update folded in: e = x'_c + s (c0 r0_c + c1 K1_c + c2 K2_c)
+//               formed on the coarse box from the coarse slots SD, SV1, SK1,
+//               SK2 and the coarse level's coefficients (the coarse x itself
+//               is not stored)
 // The output slots always differ from the slots read with a halo.  Tiles of
 // PTX x PTY fine nodes; the coarse tile, x (with a ring for the stencil
 // modes), b / g, the coefficients and k arrive by TMA into two alternating
 // buffers.
-enum PMode : int { PMODE_ADD = 0, PMODE_JAC = 1, PMODE_ADR = 2 };
+enum PMode : int { PMODE_ADD = 0, PMODE_JAC = 1, PMODE_ADR = 2, PMODE_ADRF = 3 };
 constexpr int PTX = 32, PTY = 16;
 constexpr int PCW = PTX / 2 + 3, PCH = PTY / 2 + 3;
 constexpr int PEW = PCW + 1;                           // coarse box, from (cx0-1, cy0)
@@ -628,8 +638,9 @@ template <int MODE> struct PGeo {
 };
 template <typename T, int MODE> __host__ __device__ constexpr int prolong_smem() {
     using G = PGeo<MODE>;
-    return 128 + 2 * (tma_piece<cplx<T>>(PEW * PCH) + tma_piece<cplx<T>>(G::BXW * G::XH) + tma_piece<cplx<T>>(G::NP) +
-                      (MODE == PMODE_ADR ? tma_piece<quad<T>>(G::NP) : 0) +
+    return 128 + 2 * ((MODE == PMODE_ADRF ? 4 : 1) * tma_piece<cplx<T>>(PEW * PCH) +
+                      tma_piece<cplx<T>>(G::BXW * G::XH) + tma_piece<cplx<T>>(G::NP) +
+                      (MODE >= PMODE_ADR ? tma_piece<quad<T>>(G::NP) : 0) +
                       (MODE == PMODE_JAC ? 2 * tma_piece<T>(G::NP) : 0)) +
            tma_piece<cplx<T>>(G::NX);
 }
@@ -642,18 +653,24 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
                                                 int nseg, int sx, int sc, int sb, int sout, int sxo, int xzero) {
     using G = PGeo<MODE>;
     constexpr int HAL = G::HAL, XW = G::XW, NX = G::NX, NP = G::NP, BXW = G::BXW, XH = G::XH;
+    constexpr bool ADR = MODE >= PMODE_ADR, FUSED = MODE == PMODE_ADRF;
+    // per buffer (128-byte aligned pieces): coarse boxes (e, or x', r0, K1,
+    // K2 of the coarse level when FUSED) | x | b / g | quads | k | sponge;
+    // then the stencil input U
+    constexpr int EP = tma_piece<cplx<T>>(PEW * PCH);
+    constexpr int OE = 0, OX = OE + (FUSED ? 4 : 1) * EP, OB = OX + tma_piece<cplx<T>>(BXW * XH),
+                  OQ = OB + tma_piece<cplx<T>>(NP), OK = OQ + (ADR ? tma_piece<quad<T>>(NP) : 0),
+                  OS = OK + (MODE == PMODE_JAC ? tma_piece<T>(NP) : 0),
+                  BUFB = OS + (MODE == PMODE_JAC ? tma_piece<T>(NP) : 0);
     extern __shared__ unsigned char wk_smem[];
-    TmaCarve cv(wk_smem);
-    cplx<T>* Eb[2]; cplx<T>* Xb[2]; cplx<T>* Bb[2]; quad<T>* Qb[2]; T* Kb[2]; T* Sb[2];
-    for (int b = 0; b < 2; ++b) {
-        Eb[b] = cv.take<cplx<T>>(PEW * PCH);
-        Xb[b] = cv.take<cplx<T>>(BXW * XH);
-        Bb[b] = cv.take<cplx<T>>(NP);
-        Qb[b] = MODE == PMODE_ADR ? cv.take<quad<T>>(NP) : nullptr;
-        Kb[b] = MODE == PMODE_JAC ? cv.take<T>(NP) : nullptr;
-        Sb[b] = MODE == PMODE_JAC ? cv.take<T>(NP) : nullptr;
-    }
-    cplx<T>* U = cv.take<cplx<T>>(NX);
+    unsigned char* const sm0 = reinterpret_cast<unsigned char*>(((uintptr_t)wk_smem + 127) & ~(uintptr_t)127);
+    auto Ebox = [&](int b, int q) { return reinterpret_cast<cplx<T>*>(sm0 + b * BUFB + OE + q * EP); };
+    auto Xbuf = [&](int b) { return reinterpret_cast<cplx<T>*>(sm0 + b * BUFB + OX); };
+    auto Bbuf = [&](int b) { return reinterpret_cast<cplx<T>*>(sm0 + b * BUFB + OB); };
+    auto Qbuf = [&](int b) { return reinterpret_cast<quad<T>*>(sm0 + b * BUFB + OQ); };
+    auto Kbuf = [&](int b) { return reinterpret_cast<T*>(sm0 + b * BUFB + OK); };
+    auto Sbuf = [&](int b) { return reinterpret_cast<T*>(sm0 + b * BUFB + OS); };
+    cplx<T>* U = reinterpret_cast<cplx<T>*>(sm0 + 2 * BUFB);
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
     __shared__ alignas(8) uint64_t bars[2];
@@ -669,26 +686,41 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
     const bool hs = d.sig != nullptr;
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d);
     const T wjh2 = (MODE == PMODE_JAC) ? scalp<T>(d)[S::OMEGA_J] * LC<T>::h(d) * LC<T>::h(d) : T(0);
-    const unsigned bytes = (unsigned)(PEW * PCH * sizeof(cplx<T>)) +
+    cplx<T> pc0 = zero2<T>(), pc1 = zero2<T>(), pc2 = zero2<T>();
+    if (FUSED) {
+        const T* cscl = scalp<T>(dc);
+        const T sgc = LC<T>::gs(dc);
+        pc0 = cscale<T>(sload2<T>(cscl, S::GC), sgc);
+        pc1 = cscale<T>(sload2<T>(cscl, S::GC + 2), sgc);
+        pc2 = cscale<T>(sload2<T>(cscl, S::GC + 4), sgc);
+    }
+    const unsigned bytes = (unsigned)(PEW * PCH * sizeof(cplx<T>)) * (FUSED ? 4u : 1u) +
                            (xzero ? 0u : (unsigned)(BXW * XH * sizeof(cplx<T>))) +
                            (MODE != PMODE_ADD ? (unsigned)(NP * sizeof(cplx<T>)) : 0u) +
-                           (MODE == PMODE_ADR ? (unsigned)(NP * sizeof(quad<T>)) : 0u) +
+                           (ADR ? (unsigned)(NP * sizeof(quad<T>)) : 0u) +
                            (MODE == PMODE_JAC ? (unsigned)(NP * sizeof(T)) * (hs ? 2u : 1u) : 0u);
     auto issue = [&](int t, int b) {
         if (tid != 0) return;
         const int x0 = (t % ntx) * PTX, y0 = (t / ntx) * PTY;
         pipe.expect(b, bytes);
         // coarse nodes from x0/2 - 2 (even) and y0/2 - 1
-        tma_load_3d(Eb[b], tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, sc, &bars[b]);
-        if (!xzero) {
-            if (MODE == PMODE_ADD) tma_load_3d(Xb[b], tmap(d, MC_PROL_T), 2 * x0, y0, sx, &bars[b]);
-            else tma_load_3d(Xb[b], tmap(d, MC_PROL_X), 2 * (x0 - 2), y0 - 1, sx, &bars[b]);
+        if (FUSED) {
+            tma_load_3d(Ebox(b, 0), tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, SD, &bars[b]);
+            tma_load_3d(Ebox(b, 1), tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, SV1, &bars[b]);
+            tma_load_3d(Ebox(b, 2), tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, SK1, &bars[b]);
+            tma_load_3d(Ebox(b, 3), tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, SK2, &bars[b]);
+        } else {
+            tma_load_3d(Ebox(b, 0), tmap(dc, MC_PROL_E), 2 * (x0 / 2 - 2), y0 / 2 - 1, sc, &bars[b]);
         }
-        if (MODE != PMODE_ADD) tma_load_3d(Bb[b], tmap(d, MC_PROL_T), 2 * x0, y0, sb, &bars[b]);
-        if (MODE == PMODE_ADR) tma_load_3d(Qb[b], tmap(d, MQ_PROL), 0, x0, y0, &bars[b]);
+        if (!xzero) {
+            if (MODE == PMODE_ADD) tma_load_3d(Xbuf(b), tmap(d, MC_PROL_T), 2 * x0, y0, sx, &bars[b]);
+            else tma_load_3d(Xbuf(b), tmap(d, MC_PROL_X), 2 * (x0 - 2), y0 - 1, sx, &bars[b]);
+        }
+        if (MODE != PMODE_ADD) tma_load_3d(Bbuf(b), tmap(d, MC_PROL_T), 2 * x0, y0, sb, &bars[b]);
+        if (ADR) tma_load_3d(Qbuf(b), tmap(d, MQ_PROL), 0, x0, y0, &bars[b]);
         if (MODE == PMODE_JAC) {
-            tma_load_2d(Kb[b], tmap(d, MK_PROL), x0, y0, &bars[b]);
-            if (hs) tma_load_2d(Sb[b], tmap(d, MS_PROL), x0, y0, &bars[b]);
+            tma_load_2d(Kbuf(b), tmap(d, MK_PROL), x0, y0, &bars[b]);
+            if (hs) tma_load_2d(Sbuf(b), tmap(d, MS_PROL), x0, y0, &bars[b]);
         }
     };
     int buf = 0;
@@ -698,7 +730,21 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
         if (!pipe.wait(buf, d.err)) return;
         const int x0 = (t % ntx) * PTX, y0 = (t / ntx) * PTY;
         const int ex0 = x0 / 2 - 2, ey0 = y0 / 2 - 1;   // coarse box origin
-        const cplx<T>* E = Eb[buf];
+        cplx<T>* E = Ebox(buf, 0);
+        if (FUSED) {
+            // e = x' + s (c0 r0 + c1 K1 + c2 K2) in place of x' (zero outside the coarse grid)
+            const cplx<T>* R0 = Ebox(buf, 1);
+            const cplx<T>* K1 = Ebox(buf, 2);
+            const cplx<T>* K2 = Ebox(buf, 3);
+            for (int q = tid; q < PEW * PCH; q += NT)
+                E[q] = cfma<T>(pc2, K2[q], cfma<T>(pc1, K1[q], cfma<T>(pc0, R0[q], E[q])));
+            __syncthreads();
+        }
+        const cplx<T>* Xs = Xbuf(buf);
+        const cplx<T>* Bs = Bbuf(buf);
+        const quad<T>* Qs = Qbuf(buf);
+        const T* Ks = Kbuf(buf);
+        const T* Ss = Sbuf(buf);
         // u = x + P e on the tile (+ ring); ring node (r, cc) from
         // (x0-HAL, y0-HAL) is x box (r, cc + 2*HAL - HAL) = (r, cc + HAL)
 #pragma unroll
@@ -718,7 +764,7 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
                     const int qb = (ja - ey0) * PEW + (ia - ex0);
                     v = cscale<T>(cadd<T>(cscale<T>(E[qb], wa0), cscale<T>(E[qb + 1], wa1)), wb0);
                     v = cadd<T>(v, cscale<T>(cadd<T>(cscale<T>(E[qb + PEW], wa0), cscale<T>(E[qb + PEW + 1], wa1)), wb1));
-                    if (!xzero) v = cadd<T>(Xb[buf][r * BXW + cc + HAL], v);
+                    if (!xzero) v = cadd<T>(Xs[r * BXW + cc + HAL], v);
                 }
                 if (MODE == PMODE_ADD) {
                     if (in) os[(long long)gj * pitch + gi] = v;
@@ -738,16 +784,16 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
                     const long long p = (long long)gj * pitch + gi;
                     const int q = (r + 1) * XW + cc + 1;
                     if (MODE == PMODE_JAC) {
-                        const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, Kb[buf][e], hs ? Sb[buf][e] : T(0));
+                        const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, Ks[e], hs ? Ss[e] : T(0));
                         const cplx<T> sn = cadd<T>(cadd<T>(U[q - 1], U[q + 1]), cadd<T>(U[q - XW], U[q + XW]));
-                        const cplx<T> rr = csub<T>(Bb[buf][e], cscale<T>(csub<T>(cmul<T>(dg, U[q]), sn), ih2));
+                        const cplx<T> rr = csub<T>(Bs[e], cscale<T>(csub<T>(cmul<T>(dg, U[q]), sn), ih2));
                         const T den = dg.x * dg.x + dg.y * dg.y;
                         const cplx<T> qv = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
                         os[p] = cadd<T>(U[q], cscale<T>(qv, wjh2));
                     } else {
                         const cplx<T> Lx =
-                            adr_pt<T>(Qb[buf][e], ih2, wh, U[q], U[q - 1], U[q + 1], U[q - XW], U[q + XW]);
-                        os[p] = csub<T>(Bb[buf][e], Lx);
+                            adr_pt<T>(Qs[e], ih2, wh, U[q], U[q - 1], U[q + 1], U[q - XW], U[q + XW]);
+                        os[p] = csub<T>(Bs[e], Lx);
                         xo[p] = U[q];
                     }
                 }
@@ -780,10 +826,6 @@ __global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D
     }
 }
 
-// ----------------------------------------------------------- scalar helpers
-template <typename T> __device__ __forceinline__ cplx<T> sload2(const T* s, int off) { return mk<T>(s[off], s[off + 1]); }
-template <typename T> __device__ __forceinline__ void sstore2(T* s, int off, cplx<T> v) { s[off] = v.x; s[off + 1] = v.y; }
-template <typename T> __device__ __forceinline__ T cabs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
 
 // ----------------------------------------------------------- coarsest level
 // x = A^{-1} b with the dense FP64 inverse formed at setup from the LU
