@@ -343,6 +343,14 @@ template <typename E> __host__ __device__ constexpr int smem_piece(int count) {
     return (int)(((size_t)count * sizeof(E) + 15) / 16 * 16);
 }
 
+// Pointer of double-buffer b from the buffer-0 pointer: the second buffer's
+// pieces follow the first's at a constant byte stride (no pointer arrays,
+// which would live in local memory when indexed by the running buffer).
+template <typename P>
+__device__ __forceinline__ P* bufp(P* p0, int b, int stride) {
+    return reinterpret_cast<P*>(reinterpret_cast<unsigned char*>(p0) + (size_t)b * stride);
+}
+
 // ----------------------------------------------------------- Chebyshev step
 // One step of the Chebyshev semi-iteration on A^*A x = A^*g (eq. cheb),
 // three-term form: s = A^*(g - A x);  d = c1[m] d + c2[m] s;  x += d.
@@ -365,14 +373,14 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
                                                   int nseg, int sxin, int sxout, int m, int flags) {
     extern __shared__ unsigned char wk_smem[];
     TmaCarve cv(wk_smem);
-    cplx<T>* Xb[2]; cplx<T>* Gb[2]; T* Kb[2]; T* Sb[2]; cplx<T>* Db[2];
-    for (int b = 0; b < 2; ++b) {
-        Xb[b] = cv.take<cplx<T>>(CXW * CXH);
-        Gb[b] = cv.take<cplx<T>>(CGW * CGH);
-        Kb[b] = cv.take<T>(CKW * CKH);
-        Sb[b] = cv.take<T>(CKW * CKH);
-        Db[b] = cv.take<cplx<T>>(CTX * CTY);
-    }
+    constexpr int BUFB = tma_piece<cplx<T>>(CXW * CXH) + tma_piece<cplx<T>>(CGW * CGH) + 2 * tma_piece<T>(CKW * CKH) +
+                         tma_piece<cplx<T>>(CTX * CTY);
+    cplx<T>* const X0 = cv.take<cplx<T>>(CXW * CXH);
+    cplx<T>* const G0 = cv.take<cplx<T>>(CGW * CGH);
+    T* const K0 = cv.take<T>(CKW * CKH);
+    T* const S0 = cv.take<T>(CKW * CKH);
+    cplx<T>* const D0 = cv.take<cplx<T>>(CTX * CTY);
+    cv.p += BUFB;   // second buffer
     cplx<T>* Tt = cv.take<cplx<T>>(CRW * CRH);
     __shared__ LevelDesc d;
     __shared__ alignas(8) uint64_t bars[2];
@@ -395,11 +403,11 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
         if (tid != 0) return;
         const int x0 = (t % ntx) * CTX, y0 = (t / ntx) * CTY;
         pipe.expect(b, bytes);
-        if (!xzero) tma_load_3d(Xb[b], tmap(d, MC_CHEB_X), 2 * (x0 - 2), y0 - 2, sxin, &bars[b]);
-        tma_load_3d(Gb[b], tmap(d, MC_CHEB_G), 2 * (x0 - 2), y0 - 1, SG, &bars[b]);
-        tma_load_2d(Kb[b], tmap(d, MK_CHEB), x0 - 4, y0 - 1, &bars[b]);
-        if (hs) tma_load_2d(Sb[b], tmap(d, MS_CHEB), x0 - 4, y0 - 1, &bars[b]);
-        if (c1 != T(0)) tma_load_3d(Db[b], tmap(d, MC_CHEB_D), 2 * x0, y0, SD, &bars[b]);
+        if (!xzero) tma_load_3d(bufp(X0, b, BUFB), tmap(d, MC_CHEB_X), 2 * (x0 - 2), y0 - 2, sxin, &bars[b]);
+        tma_load_3d(bufp(G0, b, BUFB), tmap(d, MC_CHEB_G), 2 * (x0 - 2), y0 - 1, SG, &bars[b]);
+        tma_load_2d(bufp(K0, b, BUFB), tmap(d, MK_CHEB), x0 - 4, y0 - 1, &bars[b]);
+        if (hs) tma_load_2d(bufp(S0, b, BUFB), tmap(d, MS_CHEB), x0 - 4, y0 - 1, &bars[b]);
+        if (c1 != T(0)) tma_load_3d(bufp(D0, b, BUFB), tmap(d, MC_CHEB_D), 2 * x0, y0, SD, &bars[b]);
     };
     int buf = 0;
     if (c.lb < ntiles) issue(c.lb, 0);
@@ -407,9 +415,9 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
         if (t + c.nb < ntiles) issue(t + c.nb, buf ^ 1);
         if (!pipe.wait(buf, d.err)) return;
         const int x0 = (t % ntx) * CTX, y0 = (t / ntx) * CTY;
-        const cplx<T>* X = Xb[buf];
-        const T* K = Kb[buf];
-        const T* Sg2 = Sb[buf];
+        const cplx<T>* X = bufp(X0, buf, BUFB);
+        const T* K = bufp(K0, buf, BUFB);
+        const T* Sg2 = bufp(S0, buf, BUFB);
         // t = g - A x on the tile plus a one-node ring (ring node (r, cc)
         // is x box (r+1, cc+1), g box (r, cc+1), k box (r, cc+3))
 #pragma unroll
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
                 const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
                 cplx<T> tv = zero2<T>();
                 if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
-                    tv = Gb[buf][r * CGW + cc + 1];
+                    tv = bufp(G0, buf, BUFB)[r * CGW + cc + 1];
                     if (!xzero) {
                         const int q = (r + 1) * CXW + cc + 1;
                         const cplx<T> sn = cadd<T>(cadd<T>(X[q - 1], X[q + 1]), cadd<T>(X[q - CXW], X[q + CXW]));
@@ -448,7 +456,7 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
                 const cplx<T> sv = cscale<T>(csub<T>(cmul<T>(dg, Tt[q]), sn), ih2);
                 const long long p = (long long)gj * pitch + gi;
                 cplx<T> dn = cscale<T>(sv, c2);
-                if (c1 != T(0)) dn = cadd<T>(dn, cscale<T>(Db[buf][e], c1));
+                if (c1 != T(0)) dn = cadd<T>(dn, cscale<T>(bufp(D0, buf, BUFB)[e], c1));
                 const cplx<T> xv = xzero ? zero2<T>() : X[(r + 2) * CXW + cc + 2];
                 xo_[p] = cadd<T>(xv, dn);
                 if (!(flags & 2)) dd[p] = dn;
@@ -483,13 +491,12 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
                                                  int nseg, int sx, int sb, int sc, int uzero) {
     extern __shared__ unsigned char wk_smem[];
     TmaCarve cv(wk_smem);
-    cplx<T>* Xb[2]; cplx<T>* Bb[2]; T* Kb[2]; T* Sb[2];
-    for (int b = 0; b < 2; ++b) {
-        Xb[b] = cv.take<cplx<T>>(RXW * RHH);
-        Bb[b] = cv.take<cplx<T>>(RXW * RHH);
-        Kb[b] = cv.take<T>(RKW * RHH);
-        Sb[b] = cv.take<T>(RKW * RHH);
-    }
+    constexpr int BUFB = 2 * tma_piece<cplx<T>>(RXW * RHH) + 2 * tma_piece<T>(RKW * RHH);
+    cplx<T>* const X0 = cv.take<cplx<T>>(RXW * RHH);
+    cplx<T>* const B0 = cv.take<cplx<T>>(RXW * RHH);
+    T* const K0 = cv.take<T>(RKW * RHH);
+    T* const S0 = cv.take<T>(RKW * RHH);
+    cv.p += BUFB;   // second buffer
     cplx<T>* U = cv.take<cplx<T>>(RHW * RHH);
     cplx<T>* R = cv.take<cplx<T>>(RFW * RFH);
     __shared__ LevelDesc d;
@@ -516,11 +523,11 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
         if (tid != 0) return;
         const int fx0 = 2 * (t % ntx) * RCX, fy0 = 2 * (t / ntx) * RCY;
         pipe.expect(b, bytes);
-        if (needx) tma_load_3d(Xb[b], tmap(d, MC_RESTR), 2 * (fx0 - 2), fy0 - 1, sx, &bars[b]);
-        tma_load_3d(Bb[b], tmap(d, MC_RESTR), 2 * (fx0 - 2), fy0 - 1, sb, &bars[b]);
+        if (needx) tma_load_3d(bufp(X0, b, BUFB), tmap(d, MC_RESTR), 2 * (fx0 - 2), fy0 - 1, sx, &bars[b]);
+        tma_load_3d(bufp(B0, b, BUFB), tmap(d, MC_RESTR), 2 * (fx0 - 2), fy0 - 1, sb, &bars[b]);
         if (needk) {
-            tma_load_2d(Kb[b], tmap(d, MK_RESTR), fx0 - 4, fy0 - 1, &bars[b]);
-            if (hs) tma_load_2d(Sb[b], tmap(d, MS_RESTR), fx0 - 4, fy0 - 1, &bars[b]);
+            tma_load_2d(bufp(K0, b, BUFB), tmap(d, MK_RESTR), fx0 - 4, fy0 - 1, &bars[b]);
+            if (hs) tma_load_2d(bufp(S0, b, BUFB), tmap(d, MS_RESTR), fx0 - 4, fy0 - 1, &bars[b]);
         }
     };
     int buf = 0;
@@ -534,11 +541,11 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
         const int ox1 = (I0 + RCX >= nc) ? n : 2 * (I0 + RCX);
         const int oy1 = (J0 + RCY >= nc) ? n : 2 * (J0 + RCY);
         // ring node (r, cc) (origin fx0-1, fy0-1): complex box (r, cc+1), real box (r, cc+3)
-        const cplx<T>* X = Xb[buf];
+        const cplx<T>* X = bufp(X0, buf, BUFB);
         int xw = RXW, xo = 1;
-        const cplx<T>* Bv = Bb[buf];
-        const T* K = Kb[buf];
-        const T* Sg2 = Sb[buf];
+        const cplx<T>* Bv = bufp(B0, buf, BUFB);
+        const T* K = bufp(K0, buf, BUFB);
+        const T* Sg2 = bufp(S0, buf, BUFB);
         if (MODE == MODE_JAC0) {
             // u1 = w D^{-1} g on footprint + ring
 #pragma unroll
@@ -552,9 +559,9 @@ __global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D
                         const cplx<T> gv = Bv[r * RXW + cc + 1];
                         const int qk = r * RKW + cc + 3;
                         const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[qk], hs ? Sg2[qk] : T(0));
-                        const T den = dg.x * dg.x + dg.y * dg.y;
-                        v = cscale<T>(mk<T>((gv.x * dg.x + gv.y * dg.y) / den, (gv.y * dg.x - gv.x * dg.y) / den),
-                                      wj * h2);
+                        // w h^2 g / (h^2 D): one division per node
+                        const T sc = wj * h2 / (dg.x * dg.x + dg.y * dg.y);
+                        v = mk<T>((gv.x * dg.x + gv.y * dg.y) * sc, (gv.y * dg.x - gv.x * dg.y) * sc);
                         if (gi >= fx0 && gi < ox1 && gj >= fy0 && gj < oy1) xs[(long long)gj * pitch + gi] = v;
                     }
                     U[e] = v;
@@ -787,9 +794,8 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
                         const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, Ks[e], hs ? Ss[e] : T(0));
                         const cplx<T> sn = cadd<T>(cadd<T>(U[q - 1], U[q + 1]), cadd<T>(U[q - XW], U[q + XW]));
                         const cplx<T> rr = csub<T>(Bs[e], cscale<T>(csub<T>(cmul<T>(dg, U[q]), sn), ih2));
-                        const T den = dg.x * dg.x + dg.y * dg.y;
-                        const cplx<T> qv = mk<T>((rr.x * dg.x + rr.y * dg.y) / den, (rr.y * dg.x - rr.x * dg.y) / den);
-                        os[p] = cadd<T>(U[q], cscale<T>(qv, wjh2));
+                        const T sc = wjh2 / (dg.x * dg.x + dg.y * dg.y);   // one division per node
+                        os[p] = cadd<T>(U[q], mk<T>((rr.x * dg.x + rr.y * dg.y) * sc, (rr.y * dg.x - rr.x * dg.y) * sc));
                     } else {
                         const cplx<T> Lx =
                             adr_pt<T>(Qs[e], ih2, wh, U[q], U[q - 1], U[q + 1], U[q - XW], U[q + XW]);
