@@ -94,7 +94,7 @@ struct Engine : EngineBase {
     void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
                          cudaStream_t st) {
         auto kern = k_restrict<T, MODE>;
-        const int smem = restrict_smem<T>();
+        const int smem = restrict_smem<T, MODE>();
         const SegTable& t = H.seg_tiles(ds, RCX, RCY, true, occ_cap(kern, smem));
         go(H, st, kind, bpp * (double)t.pts, [&] {
             kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sx, sb, sc, uzero);

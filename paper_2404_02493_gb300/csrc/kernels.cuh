@@ -481,23 +481,26 @@ constexpr int RCX = 32, RCY = 8;
 constexpr int RFW = 2 * RCX + 1, RFH = 2 * RCY + 1;   // footprint
 constexpr int RHW = RFW + 2, RHH = RFH + 2;            // footprint + ring
 constexpr int RXW = RFW + 3, RKW = RFW + 7;            // boxes from (fx0-2, fy0-1), (fx0-4, fy0-1)
-template <typename T> __host__ __device__ constexpr int restrict_smem() {
-    return 128 + 2 * (2 * tma_piece<cplx<T>>(RXW * RHH) + 2 * tma_piece<T>(RKW * RHH)) + tma_piece<cplx<T>>(RHW * RHH) +
-           tma_piece<cplx<T>>(RFW * RFH);
+// per buffer: x box (MODE_HELM only), b / g box, k, sponge; then the Jacobi
+// iterate U (MODE_JAC0 only) and the fine residual R
+template <typename T, int MODE> __host__ __device__ constexpr int restrict_smem() {
+    return 128 + 2 * ((MODE == MODE_HELM ? 2 : 1) * tma_piece<cplx<T>>(RXW * RHH) + 2 * tma_piece<T>(RKW * RHH)) +
+           (MODE == MODE_JAC0 ? tma_piece<cplx<T>>(RHW * RHH) : 0) + tma_piece<cplx<T>>(RFW * RFH);
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NT) k_restrict(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                                 int nseg, int sx, int sb, int sc, int uzero) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const LevelDesc* __restrict__ D,
+                                                                         const Seg* __restrict__ Sg, int nseg, int sx,
+                                                                         int sb, int sc, int uzero) {
     extern __shared__ unsigned char wk_smem[];
     TmaCarve cv(wk_smem);
-    constexpr int BUFB = 2 * tma_piece<cplx<T>>(RXW * RHH) + 2 * tma_piece<T>(RKW * RHH);
-    cplx<T>* const X0 = cv.take<cplx<T>>(RXW * RHH);
+    constexpr int BUFB = (MODE == MODE_HELM ? 2 : 1) * tma_piece<cplx<T>>(RXW * RHH) + 2 * tma_piece<T>(RKW * RHH);
+    cplx<T>* const X0 = MODE == MODE_HELM ? cv.take<cplx<T>>(RXW * RHH) : nullptr;
     cplx<T>* const B0 = cv.take<cplx<T>>(RXW * RHH);
     T* const K0 = cv.take<T>(RKW * RHH);
     T* const S0 = cv.take<T>(RKW * RHH);
     cv.p += BUFB;   // second buffer
-    cplx<T>* U = cv.take<cplx<T>>(RHW * RHH);
+    cplx<T>* U = MODE == MODE_JAC0 ? cv.take<cplx<T>>(RHW * RHH) : nullptr;
     cplx<T>* R = cv.take<cplx<T>>(RFW * RFH);
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
