@@ -95,9 +95,9 @@ template <typename T>
 __device__ __forceinline__ cplx<T> adr_pt(const quad<T>& q, T ih2, T wh, cplx<T> c, cplx<T> w, cplx<T> e,
                                           cplx<T> s, cplx<T> nn) {
     // d c - ih2 (w+e+s+n) + i wh [ 2max(px,0) w - 2min(px,0) e + 2max(py,0) s - 2min(py,0) n ]
-    const T px = q.x, py = q.y;
-    const T aw = T(2) * fmax(px, T(0)), ae = T(-2) * fmin(px, T(0));
-    const T as = T(2) * fmax(py, T(0)), an = T(-2) * fmin(py, T(0));
+    // 2 max(p, 0) = p + |p| and -2 min(p, 0) = |p| - p, exactly
+    const T px = q.x, py = q.y, ax = fabs(px), ay = fabs(py);
+    const T aw = px + ax, ae = ax - px, as = py + ay, an = ay - py;
     cplx<T> adv = mk<T>(aw * w.x + ae * e.x + as * s.x + an * nn.x, aw * w.y + ae * e.y + as * s.y + an * nn.y);
     cplx<T> lap = mk<T>(w.x + e.x + s.x + nn.x, w.y + e.y + s.y + nn.y);
     cplx<T> dg = mk<T>(q.z, q.w);
@@ -112,8 +112,8 @@ __device__ __forceinline__ cplx<T> adr_pt(const quad<T>& q, T ih2, T wh, cplx<T>
 template <>
 __device__ __forceinline__ float2 adr_pt<float>(const quad<float>& q, float ih2, float wh, float2 c, float2 w,
                                                 float2 e, float2 s, float2 nn) {
-    const float aw = 2.f * fmaxf(q.x, 0.f), ae = -2.f * fminf(q.x, 0.f);
-    const float as = 2.f * fmaxf(q.y, 0.f), an = -2.f * fminf(q.y, 0.f);
+    const float ax = fabsf(q.x), ay = fabsf(q.y);
+    const float aw = q.x + ax, ae = ax - q.x, as = q.y + ay, an = ay - q.y;   // exact, as above
     const float2 lap = __fadd2_rn(__fadd2_rn(w, e), __fadd2_rn(s, nn));
     float2 adv = __fmul2_rn(make_float2(aw, aw), w);
     adv = __ffma2_rn(make_float2(ae, ae), e, adv);

@@ -82,9 +82,11 @@ __device__ __forceinline__ P2<T> sl_row(const quad<T>& q0, const quad<T>& q1, co
                                         const P2<T>& nn, T ih2, T wh, T sc, bool ok0, bool ok1) {
     const cplx<T> w0 = shfl_up1<T>(c.v1);
     const cplx<T> e1 = shfl_dn1<T>(c.v0);
+    // the zero outside the grid comes with the scale (the operands there are
+    // zero-filled, so the product is finite)
     P2<T> o;
-    o.v0 = ok0 ? cscale<T>(adr_pt<T>(q0, ih2, wh, c.v0, w0, c.v1, s.v0, nn.v0), sc) : zero2<T>();
-    o.v1 = ok1 ? cscale<T>(adr_pt<T>(q1, ih2, wh, c.v1, c.v0, e1, s.v1, nn.v1), sc) : zero2<T>();
+    o.v0 = cscale<T>(adr_pt<T>(q0, ih2, wh, c.v0, w0, c.v1, s.v0, nn.v0), ok0 ? sc : T(0));
+    o.v1 = cscale<T>(adr_pt<T>(q1, ih2, wh, c.v1, c.v0, e1, s.v1, nn.v1), ok1 ? sc : T(0));
     return o;
 }
 
