@@ -68,6 +68,36 @@ def test_plane_wave_zero_residual():
 
 
 # ------------------------------------------------------------------ P2
+def test_shifted_plane_wave_zero_residual():
+    """Shifted Helmholtz (Section 4.3.2, k^2 -> k^2 (1 + i beta) in the
+    spec convention): a plane wave whose second wavenumber is the
+    complex root of 4 sin^2(k1 h/2) + 4 sin^2(k2 h/2) = k^2 h^2 (1 + i beta)
+    is annihilated by the shifted stencil (Dirichlet ghosts moved to g).  The
+    opposite sign of the shift, or no shift, leaves an O(1) residual."""
+    import dataclasses
+    n, k, beta = 63, 30.0, 0.01
+    h = 1.0 / (n + 1)
+    k1 = 11.0
+    rhs = k * k * h * h * (1 + 1j * beta) / 4 - np.sin(k1 * h / 2) ** 2
+    k2 = (2 / h) * np.arcsin(np.sqrt(rhs + 0j))
+    xs = (np.arange(-1, n + 1) + 1) * h
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    full = np.exp(1j * (k1 * X + k2 * Y))
+    u = full[1:-1, 1:-1]
+    ghost = np.zeros((n, n), complex)
+    ghost[:, 0] += full[1:-1, 0]
+    ghost[:, -1] += full[1:-1, -1]
+    ghost[0, :] += full[0, 1:-1]
+    ghost[-1, :] += full[-1, 1:-1]
+    g = ghost / (h * h)
+    lev = dataclasses.replace(const_level(n, k), shift=beta)
+    r = oracle.helmholtz_residual(lev, u, g)
+    assert np.linalg.norm(r) / np.linalg.norm(g) < 1e-12
+    for wrong in (0.0, -beta):
+        r2 = oracle.helmholtz_residual(dataclasses.replace(lev, shift=wrong), u, g)
+        assert np.linalg.norm(r2) / np.linalg.norm(g) > 1e-3
+
+
 def test_helmholtz_eigenpairs():
     """A v_pq = lambda_pq v_pq with the tensor-product form of eq. eigs /
     eq. eigvec."""
