@@ -10,6 +10,7 @@
 // The inner index j lives in device memory (fs[FS_J]) so one captured graph
 // serves every inner iteration.
 #pragma once
+#include <type_traits>
 #include "kernels.cuh"
 #include "tma.cuh"
 
@@ -185,6 +186,40 @@ template <typename TC> __host__ __device__ constexpr int fg_smem() {
     return 128 + 2 * (MAXR + 1) * tma_piece<cplx<TC>>(fg_chunk<TC>());
 }
 
+// One chunk of a Gram-Schmidt pass with the inner index j known at compile
+// time (J), so that exactly J + 1 projection terms are unrolled.
+template <typename TC, int PASS, int J, int NA>
+__device__ __forceinline__ void fg_chunk(const cplx<TC>* __restrict__ sv, int PJ, int cnt, cplx<TC>* __restrict__ w,
+                                         const cplx<TC>* coef, cplx<TC> (&ac)[NA], TC& nrm, int tid) {
+    for (int e = tid; e < cnt; e += NT) {
+        cplx<TC> wv = sv[(J + 1) * PJ + e];
+        if (PASS == 0) {
+#pragma unroll
+            for (int q = 0; q <= J; ++q) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * PJ + e], wv));
+        } else {
+#pragma unroll
+            for (int q = 0; q <= J; ++q) wv = csub<TC>(wv, cmul<TC>(coef[q], sv[q * PJ + e]));
+            w[e] = wv;
+            if (PASS == 1) {
+#pragma unroll
+                for (int q = 0; q <= J; ++q) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * PJ + e], wv));
+            }
+            nrm += cabs2<TC>(wv);
+        }
+    }
+}
+// f(std::integral_constant<int, v>) for a runtime v in [0, N)
+template <int N, class F>
+__device__ __forceinline__ void fg_dispatch(int v, F&& f) {
+    if constexpr (N > 1) {
+        if (v < N - 1) {
+            fg_dispatch<N - 1>(v, f);
+            return;
+        }
+    }
+    f(std::integral_constant<int, N - 1>{});
+}
+
 template <typename TC, int PASS>
 __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                                  int nseg) {
@@ -240,25 +275,9 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
         const long long e0 = (long long)k * PJ;
         const int cnt = (int)min((long long)PJ, N - e0);
         const cplx<TC>* sv = stg(buf, 0);
-        for (int e = tid; e < cnt; e += NT) {
-            cplx<TC> wv = sv[(jj + 1) * PJ + e];
-            if (PASS == 0) {
-#pragma unroll
-                for (int q = 0; q < MAXR; ++q)
-                    if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * PJ + e], wv));
-            } else {
-#pragma unroll
-                for (int q = 0; q < MAXR; ++q)
-                    if (q <= jj) wv = csub<TC>(wv, cmul<TC>(coef[q], sv[q * PJ + e]));
-                w[e0 + e] = wv;
-                if (PASS == 1) {
-#pragma unroll
-                    for (int q = 0; q < MAXR; ++q)
-                        if (q <= jj) ac[q] = cadd<TC>(ac[q], cmulc<TC>(sv[q * PJ + e], wv));
-                }
-                nrm += cabs2<TC>(wv);
-            }
-        }
+        fg_dispatch<MAXR>(jj, [&](auto J) {
+            fg_chunk<TC, PASS, decltype(J)::value>(sv, PJ, cnt, w + e0, coef, ac, nrm, tid);
+        });
         __syncthreads();
         buf ^= 1;
     }
