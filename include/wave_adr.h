@@ -99,14 +99,19 @@ typedef struct mg_params {
                                setup and keep the fastest (default); 0: default tile shapes */
     int tile_candidate;     /* -1 (default); 0..MG_TILE_CANDIDATES-1: use that candidate for every ADR
                                GMRES kernel (overrides autotune; for testing each shape) */
-    int tail_nmax;          /* ADR levels l >= 3 with n_l <= tail_nmax and everything below them run as one
-                               launch per ADR cycle (one thread-block cluster per instance); 0 = off
-                               (default: on this GPU a cluster phase costs about as much as a launch) */
+    int tail_nmax;          /* ADR levels l >= 3 with n_l <= tail_nmax and everything below them form the
+                               coarse tail of an instance, run without per-level launches (see tail_cluster);
+                               0 = off; -1 (default): 31 for a handle with one instance and the shared-
+                               memory tail, else 0 (measured fastest on this GPU) */
     int pdl;                /* 1: kernels are launched with programmatic dependent launch (a kernel's
                                descriptor prologue overlaps its predecessor); 0 (default): plain launches
                                (measured 0.1 ms per n=4095 cycle faster on this GPU) */
-    int tail_cluster;       /* CTAs per instance of the coarse tail (1..16); 0 (default): 16 if the GPU can
-                               schedule such clusters, else 8 */
+    int tail_cluster;       /* 0 (default): shared-memory tail -- one block per instance runs the pre-smoothing
+                               chain down to the coarsest level, the FP64 coarsest solve follows, one block per
+                               instance runs the post-smoothing chain up (3 launches per ADR cycle; a level
+                               joins the tail only if its vectors fit in one block's shared memory);
+                               1..16: one thread-block cluster of that many CTAs per instance runs the whole
+                               tail in one launch, data through L2 (slower on this GPU) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */

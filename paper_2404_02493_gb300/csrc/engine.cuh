@@ -19,6 +19,7 @@
 #include "kernels.cuh"
 #include "gmres_sstep.cuh"
 #include "tail.cuh"
+#include "tail_smem.cuh"
 #include "setup_kernels.cuh"
 
 namespace wadr {
@@ -269,7 +270,7 @@ struct Engine : EngineBase {
         for (int l = 2; l <= H.Lmax; ++l) {
             std::vector<int> rest;
             for (size_t b = 0; b < H.inst.size(); ++b)
-                if (H.inst[b].L > l && !(l >= 3 && H.inst[b].lv[l - 1].n <= H.p.tail_nmax)) rest.push_back((int)b);
+                if (adr_per_level(H, (int)b, l)) rest.push_back((int)b);
             if (rest.empty()) continue;   // not launched per level (coarse tail) or no such level
             const std::vector<int> ds = descs(H, l, rest);
             TileChoice tc;
@@ -316,11 +317,16 @@ struct Engine : EngineBase {
     // launch: one thread-block cluster per instance (tail.cuh).  The cluster
     // size is 16 CTAs (non-portable) when the GPU can schedule it, else 8.
     int tail_cluster(Handle& H) {
+        auto kern = k_adr_tail<T>;
+        static bool nonportable = false;   // clusters of more than 8 CTAs need the opt-in
+        if (!nonportable) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaGetLastError();
+            nonportable = true;
+        }
         if (H.p.tail_cluster > 0) return H.p.tail_cluster;
         static int cl = 0;
         if (cl) return cl;
-        auto kern = k_adr_tail<T>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         for (int c : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
@@ -342,7 +348,71 @@ struct Engine : EngineBase {
         if (!cl) cl = 8;
         return cl;
     }
+    // Shared-memory tail (tail_smem.cuh): the largest dynamic shared memory
+    // its kernels may use (opt-in limit minus their static shared memory),
+    // set on both kernels once.
+    static long long ts_smem_limit() {
+        static long long lim = -1;
+        if (lim >= 0) return lim;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes a1 = {}, a2 = {};
+        cudaFuncGetAttributes(&a1, k_adr_down<T>);
+        cudaFuncGetAttributes(&a2, k_adr_up<T>);
+        lim = (long long)optin - (long long)std::max(a1.sharedSizeBytes, a2.sharedSizeBytes) - 256;
+        if (lim < 0) lim = 0;
+        cudaFuncSetAttribute(k_adr_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        cudaFuncSetAttribute(k_adr_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        cudaGetLastError();
+        return lim;
+    }
+    // The shared-memory tail holds the vectors of its first level n x n.
+    static bool ts_fits(int n) {
+        return n <= TS_MAXN && ts_up_smem<T>(n) <= ts_smem_limit() && ts_down_smem<T>(n) <= ts_smem_limit();
+    }
+
+    // Down / coarsest / up launches of the shared-memory tail for the
+    // instances in `tail` (their level l is the first tail level).
+    void launch_tail_smem(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
+        const std::vector<int> ds = descs(H, l, tail);
+        const std::string key = "tsm" + desc_key(ds);
+        auto it = H.tail_first.find(key);
+        int* dfirst = nullptr;
+        if (it == H.tail_first.end()) {
+            dfirst = (int*)H.alloc(sizeof(int) * ds.size());
+            cudaMemcpy(dfirst, ds.data(), sizeof(int) * ds.size(), cudaMemcpyHostToDevice);
+            H.tail_first[key] = dfirst;
+        } else {
+            dfirst = it->second;
+        }
+        long long sd = 0, su = 0, pts = 0;
+        for (int b : tail) {
+            const int n = H.inst[b].lv[l - 1].n;
+            sd = std::max(sd, ts_down_smem<T>(n));
+            su = std::max(su, ts_up_smem<T>(n));
+            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].n;
+        }
+        ts_smem_limit();
+        const unsigned nb = (unsigned)tail.size();
+        // per tail-level point, as the multi-launch kernels count them: down = gram pass and pre-smoothing
+        // update, up = prolongation, gram pass and post-smoothing update
+        go(H, st, KK_ADR_TAIL, ((3 * C + Q) + (4 * C + Q + C / 4)) * (double)pts, [&] {
+            k_adr_down<T><<<nb, TS_THREADS, (size_t)sd, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst);
+        }, pts);
+        std::map<int, std::vector<int>> byL;
+        for (int b : tail) byL[H.inst[b].L].push_back(b);
+        for (auto& g : byL) coarse_solve(H, g.second, g.first, 1, st);
+        go(H, st, KK_ADR_TAIL, ((4 * C + Q + C) + (3 * C + Q) + 5 * C) * (double)pts, [&] {
+            k_adr_up<T><<<nb, TS_THREADS, (size_t)su, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst);
+        }, pts);
+    }
+
     void launch_tail(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
+        if (H.p.tail_cluster == 0) {
+            launch_tail_smem(H, l, tail, st);
+            return;
+        }
         const std::vector<int> ds = descs(H, l, tail);
         const std::string key = "tail" + desc_key(ds);
         auto it = H.tail_first.find(key);
@@ -381,7 +451,14 @@ struct Engine : EngineBase {
     // Instance b runs levels l.. of the ADR V-cycle with per-level launches
     // (not the coarsest level, not in the coarse tail).
     static bool adr_per_level(Handle& H, int b, int l) {
-        return H.inst[b].L > l && !(l >= 3 && H.inst[b].lv[l - 1].n <= H.p.tail_nmax);
+        return H.inst[b].L > l && !in_tail(H, b, l);
+    }
+    // Level l (not the coarsest) of instance b starts or lies in the coarse
+    // tail: l >= 3, n_l <= tail_nmax and, for the shared-memory tail
+    // (tail_cluster == 0), its vectors fit in one block's shared memory.
+    static bool in_tail(Handle& H, int b, int l) {
+        const int n = H.inst[b].lv[l - 1].n;
+        return l >= 3 && n <= H.p.tail_nmax && (H.p.tail_cluster > 0 || ts_fits(n));
     }
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
     // level l, result in SAX (or, at level 2 with `modulate`, added as

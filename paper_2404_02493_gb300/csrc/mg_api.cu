@@ -735,7 +735,7 @@ void mg_default_params(mg_params* p) {
     p->use_graph = 1;
     p->autotune = 1;
     p->tile_candidate = -1;
-    p->tail_nmax = 0;
+    p->tail_nmax = -1;   // automatic (mg_setup)
     p->pdl = 0;
     p->tail_cluster = 0;
 }
@@ -747,7 +747,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
-        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16) {
+        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }
@@ -760,6 +760,11 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     }
     mg_handle* mh = new mg_handle();
     mh->H.p = *p;
+    // automatic coarse tail: the shared-memory tail of the levels with n <= 31
+    // pays off for a single instance (one block per instance runs those
+    // levels); with many instances the per-level launches spread the work
+    // over more SMs
+    if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = (ninst == 1 && mh->H.p.tail_cluster == 0) ? 31 : 0;
     mh->H.prec = p->precision;
     mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();
     // k and phi may be host memory: stage them on the device for the setup kernels
