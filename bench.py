@@ -193,17 +193,24 @@ def recorded_traffic(kernel):
     return None if v is None else float(v["dram_bytes_per_launch_full"])
 
 
-def batched_leg(B, torch, dev, st, steps, warmup):
+def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0):
     """The batched workload: 64 instances of uneven size (255, 511, 1023 in
     turn, k0 = 0.4 n pi / 5, log-normal media, random sources) in one handle;
     complex-FP32 cycles preconditioning FGMRES(20) with an FP64 residual and
     update (iterative refinement diverges on these heterogeneous media), every
     instance with its own Krylov space; every step is one graph launch that
     runs one FGMRES iteration of every instance (batched launches over the
-    instances' segment tables).  value = instance-cycles per second."""
+    instances' segment tables).  value = instance-cycles per second.  With
+    several ranks every rank takes a contiguous range of the 64 instances
+    balanced by grid points (no collective on the data path; the step time is
+    the maximum over ranks, the per-instance results are gathered on the
+    host)."""
     import synth
+    from paper_2404_02493_gb300.shard import gather_to_host, my_shard
     t0 = time.time()
-    insts = synth.config_batch(64)
+    all_insts = synth.config_batch(64)
+    mine = list(my_shard([I.n * I.n for I in all_insts], rank, ws))
+    insts = [all_insts[i] for i in mine]
     t_in = time.time() - t0
     spec = [(I.n, I.omega, torch.from_numpy(I.k).to(dev), torch.from_numpy(I.phi).to(dev), "abc1") for I in insts]
     p = B.default_params(precision="mixed", n_cmax=15, outer="fgmres", tol=0.0, maxit=1 << 30)
@@ -227,9 +234,17 @@ def batched_leg(B, torch, dev, st, steps, warmup):
     recs = B.mg_profile_records(h, 2, stream=st)
     step_bytes = sum(r[3] for r in recs) / 2
     peak, _ = measured_peak()
-    tiles = {f"n={insts[b].n}": B.mg_tile_shapes(h, b, 2) for b in range(3)}
+    tiles = {f"n={insts[b].n}": B.mg_tile_shapes(h, b, 2) for b in range(min(3, len(insts)))}
     B.mg_destroy(h)
-    pts = sum(I.n * I.n for I in insts)
+    if ws > 1:
+        t = torch.tensor([ms, step_bytes], device=dev, dtype=torch.float64)
+        tm, tb = t[0:1].clone(), t[1:2].clone()
+        torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tb, op=torch.distributed.ReduceOp.SUM)
+        ms, step_bytes = float(tm.item()), float(tb.item())
+    rels = gather_to_host({i: rel for i in mine}, ws)
+    rel = max(rels.values())
+    pts = sum(I.n * I.n for I in all_insts)
     return {"workload": "64 instances, n in (255, 511, 1023) in turn, k0 = 0.4 n pi/5 (k h ~ 0.25), log-normal "
                         "media c in [1, 3] (seeds 100..163), random sources in [0.2, 0.8]^2; complex-FP32 Wave-ADR "
                         "cycles (M=8) preconditioning FGMRES(20) with FP64 residual and update, per instance; one "
@@ -240,7 +255,9 @@ def batched_leg(B, torch, dev, st, steps, warmup):
             "achieved_GBps": step_bytes / (ms * 1e-3 / steps) / 1e9,
             "frac_of_peak": step_bytes / (ms * 1e-3 / steps) / 1e9 / peak,
             "gpu_launches_per_step": launches, "level2_tiles": tiles, "rel_residual_after": rel,
-            "setup_seconds": t_setup, "input_generation_seconds": t_in}
+            "setup_seconds": t_setup, "input_generation_seconds": t_in, "ranks": ws,
+            "instances_per_rank": [len(my_shard([I.n * I.n for I in all_insts], r, ws)) for r in range(ws)],
+            "scaling": "strong: the 64 instances are split over the ranks" if ws > 1 else None}
 
 
 def adjoint_leg(B, torch, dev, st, batch):
@@ -430,7 +447,7 @@ def run_ours(args):
     if h is not None:
         B.mg_destroy(h)
 
-    batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3)
+    batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3, ws, rank)
     precision = None if args.no_precision else precision_leg(B, torch, dev, st)
     adjoint = None if args.no_adjoint else adjoint_leg(B, torch, dev, st, args.adjoint_batch)
 
