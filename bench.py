@@ -177,9 +177,10 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel sources."""
+def recorded_traffic(kernel, shape=None):
+    """DRAM bytes per launch of `kernel` (for the halo-tile shape the
+    autotuner picked, when the kernel has several) from the committed ncu
+    summary, if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -190,7 +191,14 @@ def recorded_traffic(kernel):
     if d.get("source_hash") != h.hexdigest()[:16]:
         return None
     v = d.get("kernels", {}).get(kernel)
-    return None if v is None else float(v["dram_bytes_per_launch_full"])
+    if v is None:
+        return None
+    if "dram_bytes_per_launch" in v:
+        return float(v["dram_bytes_per_launch"])
+    if shape is None:
+        return None
+    v = v.get(f"{shape[0]}x{shape[1]}")
+    return None if v is None else float(v)
 
 
 def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0):
@@ -390,9 +398,10 @@ def run_ours(args):
     dkey = f"{dname}@{dpts}"
     achieved = d_bytes / (d_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = recorded_traffic(dkey)
+    shapes = B.mg_tile_shapes(h, 0, 2)
+    traffic = recorded_traffic(dkey, {"gmres_gram": shapes["gram"], "gmres_pre_restrict": shapes["pre"]}.get(dname))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dkey, "peak_source": peak_kind,
+                "traffic": traffic, "kernel": dkey, "level2_tiles": shapes, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": d_bytes / d_launch, "ms_per_launch": d_ms / d_launch,
                 "launches_per_step": d_launch / 2, "share_of_step": d_ms / tot_ms}
     step_bytes = sum(r[3] for r in recs) / 2
