@@ -147,8 +147,8 @@ __device__ __forceinline__ void sl_stage(int n, const cplx<T>* __restrict__ Sin,
 }
 
 // Running Gram terms of one thread: nrm[i] holds the two halves of |K_i|^2,
-// crs[] the six <K_a, K_b> (a < b) as sums of conj(a) b.  FP32 uses packed
-// FP32x2 instructions (two per cross term, one per norm).
+// crs[] the six <K_a, K_b> (a < b) as sums of conj(a) b.  In FP32 a norm is
+// one packed FP32x2 FMA, a cross term four scalar FMAs.
 template <typename T>
 struct GramAcc {
     cplx<T> nrm[4], crs[6];
@@ -179,10 +179,14 @@ template <>
 __device__ __forceinline__ void gacc_norm<float>(float2& acc, float2 a) {
     acc = __ffma2_rn(a, a, acc);
 }
+// the cross terms as four scalar FMAs: a packed form needs broadcast and
+// swapped operand pairs, which cost more register moves than it saves
 template <>
 __device__ __forceinline__ void gacc_cross<float>(float2& acc, float2 a, float2 b) {
-    acc = __ffma2_rn(make_float2(a.x, a.x), b, acc);
-    acc = __ffma2_rn(make_float2(a.y, -a.y), make_float2(b.y, b.x), acc);
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(-a.y, b.x, acc.y);
 }
 template <typename T>
 __device__ __forceinline__ void gram_acc(GramAcc<T>& g, cplx<T> k0, cplx<T> k1, cplx<T> k2, cplx<T> k3) {
