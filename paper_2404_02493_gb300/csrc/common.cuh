@@ -160,12 +160,6 @@ constexpr int SIZE = 128;
 }  // namespace S
 
 // ------------------------------------------------------------ helpers
-__device__ __forceinline__ int find_seg(const Seg* __restrict__ segs, int nseg, int b) {
-    int s = 0;
-    while (s + 1 < nseg && __ldg(&segs[s + 1].blk0) <= b) ++s;
-    return s;
-}
-
 template <typename T> __device__ __forceinline__ cplx<T>* slot(const LevelDesc& d, int s) {
     return reinterpret_cast<cplx<T>*>(d.vec) + (long long)s * d.slot_stride;
 }

@@ -42,8 +42,16 @@ struct SegCtx {
 // Copy this block's descriptor into shared memory.
 __device__ __forceinline__ SegCtx seg_begin(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
                                             int nseg, LevelDesc& sd) {
-    const int s = find_seg(Sg, nseg, blockIdx.x);
-    const Seg g = Sg[s];
+    // the block's segment: one table entry per block, or (nseg < 0) the only
+    // segment, descriptor -nseg - 1, passed with the launch
+    Seg g;
+    if (nseg < 0) {
+        g.desc = -nseg - 1;
+        g.blk0 = 0;
+        g.blk1 = (int)gridDim.x;
+    } else {
+        g = Sg[blockIdx.x];
+    }
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     // the first warp copies the descriptor word by word (independent loads)
     constexpr int W = (int)(sizeof(LevelDesc) / sizeof(unsigned long long));

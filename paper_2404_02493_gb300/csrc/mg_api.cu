@@ -86,6 +86,19 @@ static std::vector<int> share_blocks(const std::vector<long long>& units, int ca
     return nb;
 }
 
+// Upload a segment table as one entry per block (the block's segment, read
+// with one load); a launch over a single segment needs no table at all: its
+// nseg is passed as -(descriptor + 1).
+static void finish_table(Handle& H, const std::vector<Seg>& h, SegTable& t) {
+    std::vector<Seg> per;
+    per.reserve((size_t)t.nblocks);
+    for (const Seg& g : h)
+        for (int b = g.blk0; b < g.blk1; ++b) per.push_back(g);
+    t.nseg = h.size() == 1 ? -(h[0].desc + 1) : (int)h.size();
+    t.d = (Seg*)H.alloc(sizeof(Seg) * std::max<size_t>(per.size(), 1));
+    if (!per.empty()) cudaMemcpy(t.d, per.data(), sizeof(Seg) * per.size(), cudaMemcpyHostToDevice);
+}
+
 static int blocks_for(long long pts, int per) {
     long long b = (pts + per - 1) / per;
     return (int)std::max(1LL, std::min(b, 1216LL));
@@ -114,14 +127,12 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
         h.push_back(s);
     }
     SegTable t;
-    t.nseg = (int)h.size();
     t.nblocks = blk;
     for (int i : ids) {
         const LevelDesc& d = outer ? houter[i] : hdesc[i];
         t.pts += (long long)d.n * d.n;
     }
-    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
-    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    finish_table(*this, h, t);
     return segs[key] = t;
 }
 
@@ -156,10 +167,8 @@ const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, b
         s.pad = 0;
         h.push_back(s);
     }
-    t.nseg = (int)h.size();
     t.nblocks = blk;
-    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
-    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    finish_table(*this, h, t);
     return segs[key] = t;
 }
 
@@ -186,10 +195,8 @@ const SegTable& Handle::seg_outer_chunks(const std::vector<int>& ids, int chunk,
         s.pad = 0;
         h.push_back(s);
     }
-    t.nseg = (int)h.size();
     t.nblocks = blk;
-    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
-    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    finish_table(*this, h, t);
     return segs[key] = t;
 }
 
@@ -211,15 +218,13 @@ const SegTable& Handle::seg_rows(const std::vector<int>& ids, int rows_per_block
         h.push_back(s);
     }
     SegTable t;
-    t.nseg = (int)h.size();
     t.nblocks = blk;
     for (int i : ids) {
         const long long N = (long long)hdesc[i].n * hdesc[i].n;
         t.pts += N;
         t.mat += N * N;
     }
-    t.d = (Seg*)alloc(sizeof(Seg) * h.size());
-    cudaMemcpy(t.d, h.data(), sizeof(Seg) * h.size(), cudaMemcpyHostToDevice);
+    finish_table(*this, h, t);
     return segs[key] = t;
 }
 
