@@ -113,6 +113,15 @@ struct LevelDesc {
     unsigned* err;          // handle error word (device-side wait expiry)
 };
 
+// First argument of every segment-table kernel: the descriptor table and,
+// for a launch over a single segment (nseg < 0), that segment's descriptor
+// and the one of its next coarser level by value, so that the kernel starts
+// without a dependent load of either.
+struct KDesc {
+    const LevelDesc* table;
+    LevelDesc d, dc;
+};
+
 struct Seg {
     int desc;     // index into the descriptor table
     int blk0;     // first block of this segment

@@ -39,6 +39,19 @@ struct Engine : EngineBase {
         static bool on = true;
         return on;
     }
+    // Launch argument carrying the descriptor table and, for a
+    // single-segment table, the segment's descriptors by value.
+    static KDesc kd(Handle& H, const SegTable& t) {
+        KDesc k;
+        std::memset(&k, 0, sizeof(k));
+        k.table = t.outer ? H.douter : H.ddesc;
+        if (t.nseg < 0) {
+            const LevelDesc& d = (t.outer ? H.houter : H.hdesc)[-t.nseg - 1];
+            k.d = d;
+            if (!t.outer && d.coarse >= 0) k.dc = H.hdesc[d.coarse];
+        }
+        return k;
+    }
     template <typename... KArgs, typename... Args>
     static void kl(void (*kern)(KArgs...), dim3 grid, dim3 block, int smem, cudaStream_t st, Args&&... args) {
         cudaLaunchConfig_t cfg = {};
@@ -63,7 +76,7 @@ struct Engine : EngineBase {
     }
 #define LAUNCH(kind, t, bpp, kern, ...)                                                              \
     go(H, st, kind, (bpp) * (double)(t).pts, [&] {                                                    \
-        kl(kern, (t).nblocks, dim3(BX, BY), 0, st, H.ddesc, (t).d, (t).nseg, __VA_ARGS__);            \
+        kl(kern, (t).nblocks, dim3(BX, BY), 0, st, kd(H, (t)), (t).d, (t).nseg, __VA_ARGS__);            \
     }, (t).pts)
 
     // Dynamic shared memory opt-in and resident blocks per SM x SM count of a
@@ -88,7 +101,7 @@ struct Engine : EngineBase {
         const int smem = cheb_smem<T>();
         const SegTable& t = H.seg_tiles(ds, CTX, CTY, false, occ_cap(kern, smem));
         go(H, st, KK_CHEB, bpp * (double)t.pts, [&] {
-            kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sin, sout, m, flags);
+            kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sin, sout, m, flags);
         }, t.pts);
     }
     template <int MODE>
@@ -98,7 +111,7 @@ struct Engine : EngineBase {
         const int smem = restrict_smem<T, MODE>();
         const SegTable& t = H.seg_tiles(ds, RCX, RCY, true, occ_cap(kern, smem));
         go(H, st, kind, bpp * (double)t.pts, [&] {
-            kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sx, sb, sc, uzero);
+            kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sx, sb, sc, uzero);
         }, t.pts);
     }
     template <int MODE>
@@ -108,7 +121,7 @@ struct Engine : EngineBase {
         const int smem = prolong_smem<T, MODE>();
         const SegTable& t = H.seg_tiles(ds, PTX, PTY, false, occ_cap(kern, smem));
         go(H, st, kind, bpp * (double)t.pts, [&] {
-            kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sx, sc, sb, sout, sxo, xzero);
+            kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sx, sc, sb, sout, sxo, xzero);
         }, t.pts);
     }
 
@@ -209,13 +222,13 @@ struct Engine : EngineBase {
                 auto kern = k_gs_gram_stream<T, sh.y>;
                 const SegTable& t = H.seg_tiles(ds, sh.x, sh.y * GS_WPB, false, gs_prepare(kern, smem, 0, I, 32 * GS_WPB));
                 go(H, st, KK_GS_GRAM, (3 * C + Q) * (double)t.pts, [&] {
-                    kl(kern, t.nblocks, dim3(32, GS_WPB), smem, st, H.ddesc, t.d, t.nseg, sr0);
+                    kl(kern, t.nblocks, dim3(32, GS_WPB), smem, st, kd(H, t), t.d, t.nseg, sr0);
                 }, t.pts);
             } else {
                 auto kern = k_gs_gram_tile<T, sh.x, sh.y>;
                 const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, false, gs_prepare(kern, smem, 0, I, NT));
                 go(H, st, KK_GS_GRAM, (3 * C + Q) * (double)t.pts, [&] {
-                    kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, sr0);
+                    kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sr0);
                 }, t.pts);
             }
         });
@@ -230,7 +243,7 @@ struct Engine : EngineBase {
             const int smem = gs_pre_smem<T>(I);
             const SegTable& t = H.seg_tiles(ds, sh.x, sh.y, true, gs_prepare(kern, smem, 1, I, NT));
             go(H, st, KK_GS_PRE, (4 * C + Q + C / 4) * (double)t.pts, [&] {
-                kl(kern, t.nblocks, dim3(BX, BY), smem, st, H.ddesc, t.d, t.nseg, SAB, SAX, SAB);
+                kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, SAB, SAX, SAB);
             }, t.pts);
         });
     }
@@ -239,7 +252,7 @@ struct Engine : EngineBase {
         const SegTable& t = H.seg(ds, false, 2 * NT);
         const double bpp = (flags & 2) ? 7 * C : ((flags & 1) ? 4 * C : 5 * C);
         go(H, st, KK_GS_POST, bpp * (double)t.pts, [&] {
-            kl(k_gs_post<T>, t.nblocks, dim3(BX, BY), 0, st, H.ddesc, t.d, t.nseg, sr0, sxo, flags);
+            kl(k_gs_post<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, sr0, sxo, flags);
         }, t.pts);
     }
 
@@ -309,7 +322,7 @@ struct Engine : EngineBase {
         const SegTable& t = H.seg_rows(descs(H, level, I), NT / 32);
         // the dense FP64 inverse is read once, plus the two vectors
         go(H, st, KK_COARSE, 16.0 * (double)t.mat + 2 * C * (double)t.pts, [&] {
-            kl(k_coarse<T>, t.nblocks, dim3(BX, BY), 0, st, H.ddesc, t.d, t.nseg, which);
+            kl(k_coarse<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, which);
         }, t.pts);
     }
 
@@ -563,7 +576,7 @@ struct Engine : EngineBase {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_OUTER_RESIDUAL, (gnorm ? 64.0 : 56.0) * t.pts, [&] {
             auto kern = &k_outer_residual<0>;
-            kl(kern, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg, gnorm ? 1 : 0);
+            kl(kern, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, gnorm ? 1 : 0);
         }, t.pts);
     }
 
@@ -571,12 +584,12 @@ struct Engine : EngineBase {
     void ir_step(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_OUTER_SCALE, (16.0 + C) * t.pts, [&] {
-            kl(k_outer_scale<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg, SD);
+            kl(k_outer_scale<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, SD);
         }, t.pts);
         cycle(H, true, st);
         const int cyc = H.launches_cycle;
         go(H, st, KK_OUTER_UPDATE, (32.0 + C) * t.pts, [&] {
-            kl(k_outer_update<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg);
+            kl(k_outer_update<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
         outer_residual(H, false, st);
         H.launches_cycle = cyc;
@@ -588,7 +601,7 @@ struct Engine : EngineBase {
     void fg_start(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_START, (16.0 + C) * t.pts, [&] {
-            kl(k_fg_start<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg);
+            kl(k_fg_start<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
         H.fg_j = 0;
     }
@@ -600,12 +613,12 @@ struct Engine : EngineBase {
         const int j = H.fg_j;
         dim3 bd(BX, BY);
         go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
-            kl(k_fg_prep<T>, t.nblocks, bd, 0, st, H.douter, t.d, t.nseg);
+            kl(k_fg_prep<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
         cycle(H, true, st);
         const int cyc = H.launches_cycle;
         go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
-            kl(k_fg_matvec<T>, t.nblocks, bd, 0, st, H.douter, t.d, t.nseg);
+            kl(k_fg_matvec<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
         {
             std::vector<int> od;
@@ -619,13 +632,13 @@ struct Engine : EngineBase {
             occ_cap(k2, smem);
             const SegTable& tg = H.seg_outer_chunks(od, fg_chunk<T>(), cap);
             go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
-                kl(k0, tg.nblocks, bd, smem, st, H.douter, tg.d, tg.nseg);
+                kl(k0, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
             }, tg.pts);
             go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
-                kl(k1, tg.nblocks, bd, smem, st, H.douter, tg.d, tg.nseg);
+                kl(k1, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
             }, tg.pts);
             go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
-                kl(k2, tg.nblocks, bd, smem, st, H.douter, tg.d, tg.nseg);
+                kl(k2, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
             }, tg.pts);
         }
         H.launches_cycle = cyc;
@@ -637,7 +650,7 @@ struct Engine : EngineBase {
     void fg_finish(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_UPDATE, (H.fg_j * C + 32.0) * t.pts, [&] {
-            kl(k_fg_update<T>, t.nblocks, dim3(BX, BY), 0, st, H.douter, t.d, t.nseg);
+            kl(k_fg_update<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
         outer_residual(H, false, st);
         H.fg_j = 0;
@@ -650,10 +663,10 @@ struct Engine : EngineBase {
         dim3 bd(BX, BY);
         switch (what) {
         case OP_APPLY:
-            kl(k_apply<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, a0, SU, SD);
+            kl(k_apply<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, a0, SU, SD);
             return SD;
         case OP_RESIDUAL:
-            kl(k_residual<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SU, SG, SD, 0);
+            kl(k_residual<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, SU, SG, SD, 0);
             return SD;
         case OP_RESTRICT:
             launch_restrict<MODE_HELM>(H, descs(H, level, I), KK_RESTRICT_HELM, 0, SU, SG, SG, 0, st);
@@ -662,7 +675,7 @@ struct Engine : EngineBase {
             launch_prolong<PMODE_ADD>(H, descs(H, level, I), KK_PROLONG_ADD, 0, SU, SU, SG, SD, SD, 0, st);
             return SD;
         case OP_JACOBI:
-            kl(k_jacobi<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SX2, SG, SU, 0);
+            kl(k_jacobi<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, SX2, SG, SU, 0);
             return SU;
         case OP_CHEB: {
             // a0 steps from the iterate in SU
@@ -680,9 +693,9 @@ struct Engine : EngineBase {
             const TileChoice tc = tiles_of(H, ds);
             if (a0) {
                 // r0 = b - L x  (x in SAX, b in SAB)
-                kl(k_apply<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, 2, SAX, STMP);
-                kl(k_sub<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SAB, STMP, SV1);
-                kl(k_copy<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, SAX, SD);
+                kl(k_apply<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, 2, SAX, STMP);
+                kl(k_sub<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, SAB, STMP, SV1);
+                kl(k_copy<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, SAX, SD);
                 gs_gram(H, ds, tc.gram, SV1, st);
                 gs_post(H, ds, SV1, SD, 0, st);
             } else {
@@ -695,7 +708,7 @@ struct Engine : EngineBase {
             adrv(H, level, I, false, st);
             return SAX;
         case OP_ADRCORR:
-            kl(k_resdemod<T>, t.nblocks, bd, 0, st, H.ddesc, t.d, t.nseg, 0);
+            kl(k_resdemod<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, 0);
             adrv(H, level, I, true, st);
             return SU;
         case OP_COARSE:

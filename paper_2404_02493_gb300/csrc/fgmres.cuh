@@ -90,10 +90,10 @@ __device__ __forceinline__ cplx<TC>* xslot(const LevelDesc& d, int s) {
 // Start of a restart: V_0 = r/||r|| (r = outer SD, FP64), reset the
 // Hessenberg, gamma = e_1, j = 0.
 template <typename TC>
-__global__ void __launch_bounds__(NT) k_fg_start(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_fg_start(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                  int nseg) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const double2* r = slot<double>(d, SD);
     cplx<TC>* v0 = kvec<TC>(d, 0);
@@ -119,10 +119,10 @@ __global__ void __launch_bounds__(NT) k_fg_start(const LevelDesc* __restrict__ D
 
 // Cycle input: level-1 SG = V_j (normalising V_j in place first for j > 0).
 template <typename TC>
-__global__ void __launch_bounds__(NT) k_fg_prep(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_fg_prep(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                 int nseg) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const int jj = (int)d.fs[FS::J];
     cplx<TC>* v = kvec<TC>(d, jj);
@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(NT) k_fg_prep(const LevelDesc* __restrict__ D,
 // Z_j = z (cycle output, level-1 SD); W = V_{j+1} = A z in the cycle
 // precision (5-point Helmholtz with the level-1 k of that precision).
 template <typename TC>
-__global__ void __launch_bounds__(NT) k_fg_matvec(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_fg_matvec(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                   int nseg) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const int jj = (int)d.fs[FS::J];
     const cplx<TC>* z = xslot<TC>(d, SD);
@@ -221,7 +221,7 @@ __device__ __forceinline__ void fg_dispatch(int v, F&& f) {
 }
 
 template <typename TC, int PASS>
-__global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT, 1) k_fg_gs(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                  int nseg) {
     constexpr int P = fg_chunk<TC>();
     extern __shared__ unsigned char fg_raw[];
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
     __shared__ cplx<TC> coef[MAXR];
     __shared__ int flag;
     __shared__ alignas(8) uint64_t bars[2];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     TmaPipe pipe;
     pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -336,11 +336,11 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const LevelDesc* __restrict__ D
 
 // y = R^{-1} gamma (one thread per instance), then u += ||r|| sum_i y_i Z_i.
 template <typename TC>
-__global__ void __launch_bounds__(NT) k_fg_update(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_fg_update(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                   int nseg) {
     __shared__ LevelDesc d;
     __shared__ double2 ysh[MAXR];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int m = (int)d.fs[FS::JDONE];
     if (tid == 0) {

@@ -222,7 +222,7 @@ __device__ __forceinline__ void gram_finish(const LevelDesc& d, const SegCtx& c,
 // (halo 2) of a block's next tile stream in while the current one is
 // computed.
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(NT) k_gs_gram_tile(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_gs_gram_tile(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                      int nseg, int sr0) {
     constexpr int W0 = TX + 6, H0 = TY + 6, W1 = TX + 4, H1 = TY + 4, W2 = TX + 2, H2 = TY + 2;
     static_assert((TX * TY) % NT == 0, "tile");
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT) k_gs_gram_tile(const LevelDesc* __restrict
     __shared__ LevelDesc d;
     __shared__ cplx<T> sh[8 * 8];
     __shared__ int flag;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int n = d.n, pitch = d.pitch;
     const int ntx = (n + TX - 1) / TX, ntiles = ntx * ((n + TY - 1) / TY);
@@ -293,7 +293,7 @@ template <typename T> constexpr int gs_ring_bytes(int nq, int nc) {
     return (int)((nq * sizeof(quad<T>) + nc * sizeof(cplx<T>)) * GS_WPB * SW_DEP * SW_COLS);
 }
 template <typename T, int RH>
-__global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const LevelDesc* __restrict__ D,
+__global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_constant__ KDesc A,
                                                                 const Seg* __restrict__ Sg, int nseg, int sr0) {
     extern __shared__ __align__(16) unsigned char gs_smem[];
     const int lane = threadIdx.x, warp = threadIdx.y;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const LevelDesc*
     __shared__ LevelDesc d;
     __shared__ cplx<T> sh[8 * 8];
     __shared__ int flag;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int n = d.n, pitch = d.pitch;
     const int nstrips = (n + SW_OUT - 1) / SW_OUT, nunits = nstrips * ((n + RH - 1) / RH);
     const cplx<T>* r0 = slot<T>(d, sr0);
@@ -387,7 +387,7 @@ struct PreGeo {
     static constexpr int AW = FW + 1;                // K0 / K1 box from (fx0, fy0), FH rows
 };
 template <typename T, int CX, int CY, int CAND>
-__global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_gs_pre(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                int nseg, int sb, int sx, int sc) {
     using G = PreGeo<CX, CY>;
     constexpr int FW = G::FW, FH = G::FH, NF = G::NF, KW = G::KW, KH = G::KH, AW = G::AW;
@@ -400,9 +400,9 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
     __shared__ alignas(8) uint64_t bars[2];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    copy_desc(dc, D + d.coarse, tid);
+    coarse_desc(A, nseg, d, dc, tid);
     TmaPipe pipe;
     pipe.init(bars);
     const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
@@ -488,10 +488,10 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const LevelDesc* __restrict__ D, 
 // instead of writing x to SAX (Algorithm 1's u <- u + e after the ADR cycle).
 // Two nodes of a row per thread.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_gs_post(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_gs_post(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                 int nseg, int sr0, int sxo, int flags) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
     const cplx<T>* k0 = slot<T>(d, sr0);

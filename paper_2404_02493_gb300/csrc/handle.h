@@ -50,7 +50,8 @@ struct InstHost {
 
 struct SegTable {
     Seg* d = nullptr;
-    int nseg = 0, nblocks = 0;
+    int nseg = 0, nblocks = 0;     // nseg < 0: a single segment, descriptor -nseg - 1
+    bool outer = false;            // descriptors of the outer (FP64) table
     long long pts = 0;     // sum of n^2 over the segments
     long long mat = 0;     // sum of (n^2)^2 (dense coarsest matrices)
 };

@@ -35,13 +35,18 @@ __device__ __forceinline__ void copy_desc(LevelDesc& dst, const LevelDesc* src, 
             reinterpret_cast<unsigned long long*>(&dst)[w] = reinterpret_cast<const unsigned long long*>(src)[w];
 }
 
+// The descriptor of the next coarser level of d into shared memory dc.
+__device__ __forceinline__ void coarse_desc(const KDesc& A, int nseg, const LevelDesc& d, LevelDesc& dc, int tid) {
+    copy_desc(dc, nseg < 0 ? &A.dc : A.table + d.coarse, tid);
+}
+
 struct SegCtx {
     int lb, nb;      // block index within segment, number of blocks of segment
 };
 
-// Copy this block's descriptor into shared memory.
-__device__ __forceinline__ SegCtx seg_begin(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
-                                            int nseg, LevelDesc& sd) {
+// Copy this block's descriptor into shared memory (from the launch
+// arguments for a single-segment launch, else from the table).
+__device__ __forceinline__ SegCtx seg_begin(const KDesc& A, const Seg* __restrict__ Sg, int nseg, LevelDesc& sd) {
     // the block's segment: one table entry per block, or (nseg < 0) the only
     // segment, descriptor -nseg - 1, passed with the launch
     Seg g;
@@ -53,12 +58,7 @@ __device__ __forceinline__ SegCtx seg_begin(const LevelDesc* __restrict__ D, con
         g = Sg[blockIdx.x];
     }
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    // the first warp copies the descriptor word by word (independent loads)
-    constexpr int W = (int)(sizeof(LevelDesc) / sizeof(unsigned long long));
-    static_assert(sizeof(LevelDesc) % sizeof(unsigned long long) == 0, "descriptor size");
-    if (tid < 32)
-        for (int w = tid; w < W; w += 32)
-            reinterpret_cast<unsigned long long*>(&sd)[w] = reinterpret_cast<const unsigned long long*>(D + g.desc)[w];
+    copy_desc(sd, nseg < 0 ? &A.d : A.table + g.desc, tid);
     __syncthreads();
     // Programmatic dependent launch: descriptors and segment tables are
     // constant, so the copies above may overlap the previous kernel; wait for
@@ -180,10 +180,10 @@ __device__ __forceinline__ cplx<T> adr_apply_t_pt(const LevelDesc& d, const cplx
 // ----------------------------------------------------------- generic ops
 // op: 0 A, 1 A^H, 2 L (ADR), 3 L^T, 4 L^H
 template <typename T>
-__global__ void __launch_bounds__(NT) k_apply(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_apply(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                               int nseg, int op, int sx, int sy) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const cplx<T>* x = slot<T>(d, sx);
     cplx<T>* y = slot<T>(d, sy);
@@ -202,10 +202,10 @@ __global__ void __launch_bounds__(NT) k_apply(const LevelDesc* __restrict__ D, c
 
 // r = g - A u (uzero: r = g)
 template <typename T>
-__global__ void __launch_bounds__(NT) k_residual(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                  int nseg, int su, int sg, int sr, int uzero) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const cplx<T>* u = slot<T>(d, su);
     const cplx<T>* g = slot<T>(d, sg);
@@ -222,10 +222,10 @@ __global__ void __launch_bounds__(NT) k_residual(const LevelDesc* __restrict__ D
 
 // Damped Jacobi: out = u + w D^{-1} (g - A u)   (eq. sjac)
 template <typename T>
-__global__ void __launch_bounds__(NT) k_jacobi(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_jacobi(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                int nseg, int su, int sg, int sout, int uzero) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const cplx<T>* u = slot<T>(d, su);
     const cplx<T>* g = slot<T>(d, sg);
@@ -377,7 +377,7 @@ template <typename T> __host__ __device__ constexpr int cheb_smem() {
            tma_piece<cplx<T>>(CRW * CRH);
 }
 template <typename T>
-__global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_cheb_step(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                   int nseg, int sxin, int sxout, int m, int flags) {
     extern __shared__ unsigned char wk_smem[];
     TmaCarve cv(wk_smem);
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const LevelDesc* __restrict__ 
     cplx<T>* Tt = cv.take<cplx<T>>(CRW * CRH);
     __shared__ LevelDesc d;
     __shared__ alignas(8) uint64_t bars[2];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     TmaPipe pipe;
     pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -497,7 +497,7 @@ template <typename T, int MODE> __host__ __device__ constexpr int restrict_smem(
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const LevelDesc* __restrict__ D,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const __grid_constant__ KDesc A,
                                                                          const Seg* __restrict__ Sg, int nseg, int sx,
                                                                          int sb, int sc, int uzero) {
     extern __shared__ unsigned char wk_smem[];
@@ -513,9 +513,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const L
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
     __shared__ alignas(8) uint64_t bars[2];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    copy_desc(dc, D + d.coarse, tid);
+    coarse_desc(A, nseg, d, dc, tid);
     TmaPipe pipe;
     pipe.init(bars);
     const int n = d.n, pitch = d.pitch, nc = dc.n;
@@ -667,7 +667,7 @@ template <typename T>
 __device__ __forceinline__ int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_prolong(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                 int nseg, int sx, int sc, int sb, int sout, int sxo, int xzero) {
     using G = PGeo<MODE>;
     constexpr int HAL = G::HAL, XW = G::XW, NX = G::NX, NP = G::NP, BXW = G::BXW, XH = G::XH;
@@ -692,9 +692,9 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
     __shared__ LevelDesc d;
     __shared__ LevelDesc dc;
     __shared__ alignas(8) uint64_t bars[2];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    copy_desc(dc, D + d.coarse, tid);
+    coarse_desc(A, nseg, d, dc, tid);
     TmaPipe pipe;
     pipe.init(bars);
     const int n = d.n, pitch = d.pitch;
@@ -825,10 +825,10 @@ __global__ void __launch_bounds__(NT) k_prolong(const LevelDesc* __restrict__ D,
 // b = exp(-i w phi) (g - A u)  at level 2 (eq. Rytov: r_hat = r e^{-i w phi}
 // in the exp(+i w phi) convention); result in slot SAB.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_resdemod(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                  int nseg, int /*unused*/) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const cplx<T>* u = slot<T>(d, SU);
     const cplx<T>* g = slot<T>(d, SG);
@@ -850,11 +850,11 @@ __global__ void __launch_bounds__(NT) k_resdemod(const LevelDesc* __restrict__ D
 // memory (n_L^2 <= 1024).  which: 0 Helmholtz (SG -> SU), 1 ADR (SAB -> SAX).
 constexpr int MAXCOARSE = 1024;
 template <typename T>
-__global__ void __launch_bounds__(NT) k_coarse(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_coarse(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                int nseg, int which) {
     __shared__ LevelDesc d;
     __shared__ double2 bsh[MAXCOARSE];
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int n = d.n, N = n * n;
     const cplx<T>* b = slot<T>(d, which ? SAB : SG);
@@ -901,12 +901,12 @@ namespace wadr {
 
 // r = g - A u in FP64 (slot SD) and ||r||^2 -> S::NORM; optionally ||g||^2 -> S::NORM+1.
 template <int V = 0>
-__global__ void __launch_bounds__(NT) k_outer_residual(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_outer_residual(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                        int nseg, int with_gnorm) {
     __shared__ LevelDesc d;
     __shared__ double2 sh[8 * 2];
     __shared__ int flag;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const double2* u = slot<double>(d, SU);
     const double2* g = slot<double>(d, SG);
@@ -938,10 +938,10 @@ __global__ void __launch_bounds__(NT) k_outer_residual(const LevelDesc* __restri
 
 // cycle level-1 SG (precision TC) = r / ||r||
 template <typename TC>
-__global__ void __launch_bounds__(NT) k_outer_scale(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_outer_scale(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                     int nseg, int src_slot) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     const double2* r = slot<double>(d, src_slot);
     cplx<TC>* out = reinterpret_cast<cplx<TC>*>(d.xvec) + (long long)SG * d.xstride;
@@ -958,10 +958,10 @@ __global__ void __launch_bounds__(NT) k_outer_scale(const LevelDesc* __restrict_
 
 // u += ||r|| e   (e = cycle level-1 SD, precision TC)
 template <typename TC>
-__global__ void __launch_bounds__(NT) k_outer_update(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg,
+__global__ void __launch_bounds__(NT) k_outer_update(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                      int nseg) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     double2* u = slot<double>(d, SU);
     const cplx<TC>* e = reinterpret_cast<const cplx<TC>*>(d.xvec) + (long long)SD * d.xstride;
@@ -979,10 +979,10 @@ __global__ void __launch_bounds__(NT) k_outer_update(const LevelDesc* __restrict
 namespace wadr {
 // ----------------------------------------------------------- small utilities
 template <typename T>
-__global__ void __launch_bounds__(NT) k_sub(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg, int nseg,
+__global__ void __launch_bounds__(NT) k_sub(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg, int nseg,
                                             int sa, int sb, int sc) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
@@ -992,10 +992,10 @@ __global__ void __launch_bounds__(NT) k_sub(const LevelDesc* __restrict__ D, con
     }
 }
 template <typename T>
-__global__ void __launch_bounds__(NT) k_copy(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg, int nseg,
+__global__ void __launch_bounds__(NT) k_copy(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg, int nseg,
                                              int sa, int sb) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
@@ -1005,10 +1005,10 @@ __global__ void __launch_bounds__(NT) k_copy(const LevelDesc* __restrict__ D, co
     }
 }
 template <typename T>
-__global__ void __launch_bounds__(NT) k_zero(const LevelDesc* __restrict__ D, const Seg* __restrict__ Sg, int nseg,
+__global__ void __launch_bounds__(NT) k_zero(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg, int nseg,
                                              int sa) {
     __shared__ LevelDesc d;
-    SegCtx c = seg_begin(D, Sg, nseg, d);
+    SegCtx c = seg_begin(A, Sg, nseg, d);
     const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;

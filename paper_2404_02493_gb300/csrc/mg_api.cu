@@ -128,6 +128,7 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
     }
     SegTable t;
     t.nblocks = blk;
+    t.outer = outer;
     for (int i : ids) {
         const LevelDesc& d = outer ? houter[i] : hdesc[i];
         t.pts += (long long)d.n * d.n;
@@ -196,6 +197,7 @@ const SegTable& Handle::seg_outer_chunks(const std::vector<int>& ids, int chunk,
         h.push_back(s);
     }
     t.nblocks = blk;
+    t.outer = true;
     finish_table(*this, h, t);
     return segs[key] = t;
 }
