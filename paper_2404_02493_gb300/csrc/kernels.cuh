@@ -868,17 +868,25 @@ __global__ void __launch_bounds__(NT) k_coarse(const __grid_constant__ KDesc A, 
     const int lane = tid & 31, wid = tid >> 5;
     for (int row = c.lb * (NT / 32) + wid; row < N; row += c.nb * (NT / 32)) {
         const double2* a = Ainv + (long long)row * N;
-        // four fused multiply-adds per complex term; unrolled so that the
-        // loads of a row are in flight together
-        double2 acc = make_double2(0, 0);
-#pragma unroll 4
-        for (int q = lane; q < N; q += 32) {
-            const double2 av = __ldg(a + q), bv = bsh[q];
-            acc.x = fma(av.x, bv.x, acc.x);
-            acc.x = fma(-av.y, bv.y, acc.x);
-            acc.y = fma(av.x, bv.y, acc.y);
-            acc.y = fma(av.y, bv.x, acc.y);
+        // four fused multiply-adds per complex term into four independent
+        // accumulators (columns q mod 128 in four groups of 32): a dependent
+        // FP64 FMA is slow on this GPU, so one chain per lane would set the
+        // time
+        double2 ac[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+        for (int q0 = lane; q0 < N; q0 += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + 32 * u;
+                if (q < N) {
+                    const double2 av = __ldg(a + q), bv = bsh[q];
+                    ac[u].x = fma(av.x, bv.x, ac[u].x);
+                    ac[u].x = fma(-av.y, bv.y, ac[u].x);
+                    ac[u].y = fma(av.x, bv.y, ac[u].y);
+                    ac[u].y = fma(av.y, bv.x, ac[u].y);
+                }
+            }
         }
+        double2 acc = dadd(dadd(ac[0], ac[1]), dadd(ac[2], ac[3]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
