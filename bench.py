@@ -355,6 +355,29 @@ def shifted_leg(B, torch, dev, st, n=1023, omega=500.0, beta=0.01):
     return out
 
 
+def ray_leg(B, torch, dev, st, n=1023, omega=500.0):
+    """Wave-Ray corrections (Section 3.2: the M corrections use the plane-wave
+    phases of directions theta_m = 2 pi (m-1) / M) against Wave-ADR (the
+    eikonal phase of the input) on the layered recipe at n=1023, omega=500,
+    M=8: mixed-form FGMRES(20) to 1e-6 from zero."""
+    import synth
+    inst = synth.config_layered(n=n, omega=omega, seed=5)
+    k = torch.from_numpy(inst.k).to(dev)
+    phi = torch.from_numpy(inst.phi).to(dev)
+    g = torch.from_numpy(inst.g).to(dev)
+    out = {"workload": f"layered medium n={n} omega={omega:g}, M=8, mixed FGMRES(20) to 1e-6 from u=0, "
+                       "Wave-Ray plane-wave corrections vs Wave-ADR (eikonal phase)", "solves": {}}
+    for name, ray in (("wave_ray", 1), ("wave_adr", 0)):
+        p = B.default_params(precision="mixed", n_cmax=15, tol=1e-6, maxit=3000, M=8, ray=ray)
+        h = B.mg_setup([(n, omega, k, phi, "abc1")], p, stream=st)
+        u = torch.zeros_like(g)
+        status, its, rr, hist, secs = B.mg_solve(h, u, g, history_len=0, stream=st)
+        B.mg_destroy(h)
+        out["solves"][name] = {"status": {0: "converged", -4: "maxit", -5: "diverged"}.get(status, status),
+                               "iterations": its, "rel_residual_fp64": rr, "device_seconds": secs}
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -482,6 +505,7 @@ def run_ours(args):
     batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3, ws, rank)
     precision = None if args.no_precision else precision_leg(B, torch, dev, st)
     shifted = None if args.no_shifted else shifted_leg(B, torch, dev, st)
+    ray = None if args.no_ray else ray_leg(B, torch, dev, st)
     adjoint = None if args.no_adjoint else adjoint_leg(B, torch, dev, st, args.adjoint_batch)
 
     if rank != 0:
@@ -501,7 +525,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "time_to_tolerance": tts, "rel_residual_after_timed_steps": rel_after,
             "cycle_roofline": cycle_roofline, "kernels": kernels, "top_launches": top_records,
-            "batched": batched, "adjoint": adjoint, "precision_comparison": precision, "shifted": shifted,
+            "batched": batched, "adjoint": adjoint, "precision_comparison": precision, "shifted": shifted, "wave_ray": ray,
             "setup_seconds": t_setup, "input_generation_seconds": t_inputs}
     print(json.dumps(line), flush=True)
     return 0
@@ -527,6 +551,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-shifted", action="store_true")
+    ap.add_argument("--no-ray", action="store_true")
     ap.add_argument("--adjoint-batch", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:

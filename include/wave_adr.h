@@ -112,6 +112,11 @@ typedef struct mg_params {
                                joins the tail only if its vectors fit in one block's shared memory);
                                1..16: one thread-block cluster of that many CTAs per instance runs the whole
                                tail in one launch, data through L2 (slower on this GPU) */
+    int ray;                /* 0 (default): the M ADR corrections use the input phase phi (Wave-ADR);
+                               1: Wave-Ray (the ray equations of Section 3.2): correction m = 1..M uses the
+                               plane-wave phase phi_m = cos(theta_m) x + sin(theta_m) y, theta_m =
+                               (m-1) 2 pi / M, instead
+                               (the input phi is not used; mg_cycle_backward is not available) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */

@@ -1,6 +1,7 @@
 """Oracle Wave-ADR cycle (Algorithm 1) with the ADR V-cycle correction."""
 from __future__ import annotations
 
+import dataclasses
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -31,6 +32,7 @@ class CycleParams:
     adr: bool = True               # False: plain wave cycle
     omega_jacobi: float | None = None      # None: (4-kappa)/(5-kappa)
     alphas: dict = field(default_factory=dict)  # level -> alpha; missing: spectral
+    ray: bool = False              # Wave-Ray: correction m uses the plane-wave phase of direction m
 
 
 def build_sizes(n: int, n_cmax: int):
@@ -115,15 +117,32 @@ class Hierarchy:
                     l, alpha_spectral(lev.n, lev.h, float(np.max(lev.k))))
         self.adr = {}
         self.mod = None
-        if self.p.adr and self.L >= 3:
-            for l in range(2, self.L + 1):
-                self.adr[l] = adr_coefficients(self.levels[l - 1])
-            lv2 = self.levels[1]
-            self.mod = np.exp(1j * conv * omega * lv2.phi)   # e^{+i conv w phi_2}
         cl = self.levels[-1]
         self.lu_helm = scipy.linalg.lu_factor(helmholtz_sparse(cl).toarray())
-        self.lu_adr = (scipy.linalg.lu_factor(adr_sparse(cl).toarray())
-                       if self.adr else None)
+        self.lu_adr = None
+        # ADR sets of the corrections: one (the input phase) for Wave-ADR; for
+        # Wave-Ray one per plane-wave direction theta_m = 2 pi m / M
+        self.adr_sets = []
+        if self.p.adr and self.L >= 3:
+            if self.p.ray:
+                X, Y = np.meshgrid((np.arange(n) + 1) / (n + 1), (np.arange(n) + 1) / (n + 1), indexing="xy")
+                phases = []
+                for m in range(self.p.M):
+                    th = m * 2.0 * np.pi / self.p.M
+                    phases.append(np.cos(th) * X + np.sin(th) * Y)
+            else:
+                phases = [np.asarray(phi, float)]
+            for ph in phases:
+                levs, pl = [], ph
+                for l in range(1, self.L + 1):
+                    if l > 1:
+                        pl = inject(pl)
+                    levs.append(dataclasses.replace(self.levels[l - 1], phi=pl))
+                coefs = {l: adr_coefficients(levs[l - 1]) for l in range(2, self.L + 1)}
+                mod = np.exp(1j * conv * omega * levs[1].phi)   # e^{+i conv w phi_2}
+                lu = scipy.linalg.lu_factor(adr_sparse(levs[-1]).toarray())
+                self.adr_sets.append((coefs, mod, lu))
+            self.adr, self.mod, self.lu_adr = self.adr_sets[0]
 
     # ------------------------------------------------------------ roles
     def _uses_cheb(self, l: int) -> bool:
@@ -152,17 +171,19 @@ class Hierarchy:
             return u + scipy.linalg.lu_solve(self.lu_helm, r.ravel()).reshape(r.shape)
         return self.cheb(self.L, u, g, self.p.coarse_cheb_iters)
 
-    def adr_vcycle(self, l: int, b: np.ndarray) -> np.ndarray:
+    def adr_vcycle(self, l: int, b: np.ndarray, m: int = 0) -> np.ndarray:
         """ADR cycle (Section 3.2.2): one V-cycle on the upwind ADR operator
         from level l down to L, one GMRES(3) sweep before and after the
-        coarse-grid correction, exact solve on the coarsest level."""
+        coarse-grid correction, exact solve on the coarsest level.  m: the
+        ADR set (Wave-Ray direction)."""
+        coefs, _, lu = self.adr_sets[m]
         if l == self.L:
-            return scipy.linalg.lu_solve(self.lu_adr, b.ravel()).reshape(b.shape)
-        c = self.adr[l]
+            return scipy.linalg.lu_solve(lu, b.ravel()).reshape(b.shape)
+        c = coefs[l]
         op = lambda v: adr_apply(c, v)
         x = gmres(op, b, None, self.p.gmres_m)
         r = b - op(x)
-        ec = self.adr_vcycle(l + 1, restrict(r))
+        ec = self.adr_vcycle(l + 1, restrict(r), m)
         x = x + prolong(ec, self.lev(l).n)
         x = gmres(op, b, x, self.p.gmres_m)
         return x
@@ -170,12 +191,16 @@ class Hierarchy:
     def adr_correction(self, u2: np.ndarray, g2: np.ndarray) -> np.ndarray:
         """Algorithm 1's ADR correction at level 2, repeated M times
         (Section 4.2): r = g - A u; r_hat = r e^{-i conv w phi};
-        a = ADR cycle(r_hat); u <- u + a e^{+i conv w phi}."""
+        a = ADR cycle(r_hat); u <- u + a e^{+i conv w phi}.  Wave-Ray
+        (Section 3.2): correction m uses the ray equation of plane wave m,
+        i.e. phi_m = cos(theta_m) x + sin(theta_m) y."""
         lev = self.lev(2)
-        for _ in range(self.p.M):
+        for m in range(self.p.M):
+            k = m if self.p.ray else 0
+            mod = self.adr_sets[k][1]
             r = g2 - helmholtz_apply(lev, u2)
-            a = self.adr_vcycle(2, np.conj(self.mod) * r)
-            u2 = u2 + self.mod * a
+            a = self.adr_vcycle(2, np.conj(mod) * r, k)
+            u2 = u2 + mod * a
         return u2
 
     def cycle(self, u: np.ndarray, g: np.ndarray, l: int = 1) -> np.ndarray:

@@ -130,6 +130,17 @@ struct Engine : EngineBase {
         for (int b : I) d.push_back(H.inst[b].lv[level - 1].desc);
         return d;
     }
+    // Descriptors of the ADR levels: those of the Wave-Ray correction being
+    // emitted (H.cur_var > 0), else the base levels.
+    std::vector<int> adescs(Handle& H, int level, const std::vector<int>& I) {
+        std::vector<int> d;
+        for (int b : I) {
+            const InstHost& In = H.inst[b];
+            d.push_back(H.cur_var > 0 && !In.rv.empty() ? In.rv[(size_t)H.cur_var - 1][level - 1].desc
+                                                        : In.lv[level - 1].desc);
+        }
+        return d;
+    }
 
     // ------------------------------------------------------------ setup
     int setup_fields(Handle& H, const mg_instance* in, cudaStream_t st) override {
@@ -145,6 +156,16 @@ struct Engine : EngineBase {
                 if (lv.mod)
                     k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.pitch, I.omega, (cplx<T>*)lv.mod);
             }
+            // Wave-Ray corrections 2..M: their own ADR quads and modulation
+            for (auto& vl : I.rv)
+                for (int l = 2; l <= I.L; ++l) {
+                    LevelHost& lv = vl[l - 1];
+                    dim3 bb(32, 8), gg((lv.n + 31) / 32, (lv.n + 7) / 8);
+                    k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega,
+                                                      I.bc, H.p.shift, (quad<T>*)lv.adr);
+                    if (lv.mod)
+                        k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.pitch, I.omega, (cplx<T>*)lv.mod);
+                }
         }
         return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ECUDA;
     }
@@ -203,7 +224,10 @@ struct Engine : EngineBase {
         if (H.p.tile_candidate >= 0) {
             tc.gram = tc.pre = H.p.tile_candidate;
         } else {
-            auto it = H.tiles.find(desc_key(ds));
+            // Wave-Ray variants share the tile choice of their base levels
+            std::vector<int> base(ds.size());
+            for (size_t q = 0; q < ds.size(); ++q) base[q] = H.base_of.empty() ? ds[q] : H.base_of[(size_t)ds[q]];
+            auto it = H.tiles.find(desc_key(base));
             if (it != H.tiles.end()) tc = it->second;
         }
         if (tc.gram < 0) tc.gram = GS_DEFAULT_GRAM;
@@ -319,7 +343,7 @@ struct Engine : EngineBase {
     }
 
     void coarse_solve(Handle& H, const std::vector<int>& I, int level, int which, cudaStream_t st) {
-        const SegTable& t = H.seg_rows(descs(H, level, I), NT / 32);
+        const SegTable& t = H.seg_rows(which ? adescs(H, level, I) : descs(H, level, I), NT / 32);
         // the dense FP64 inverse is read once, plus the two vectors
         go(H, st, KK_COARSE, 16.0 * (double)t.mat + 2 * C * (double)t.pts, [&] {
             kl(k_coarse<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, which);
@@ -388,7 +412,7 @@ struct Engine : EngineBase {
     // Down / coarsest / up launches of the shared-memory tail for the
     // instances in `tail` (their level l is the first tail level).
     void launch_tail_smem(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
-        const std::vector<int> ds = descs(H, l, tail);
+        const std::vector<int> ds = adescs(H, l, tail);
         const std::string key = "tsm" + desc_key(ds);
         auto it = H.tail_first.find(key);
         int* dfirst = nullptr;
@@ -426,7 +450,7 @@ struct Engine : EngineBase {
             launch_tail_smem(H, l, tail, st);
             return;
         }
-        const std::vector<int> ds = descs(H, l, tail);
+        const std::vector<int> ds = adescs(H, l, tail);
         const std::string key = "tail" + desc_key(ds);
         auto it = H.tail_first.find(key);
         int* dfirst = nullptr;
@@ -486,7 +510,7 @@ struct Engine : EngineBase {
         for (int b : rest0) (adr_per_level(H, b, l) ? rest : tail).push_back(b);
         if (!tail.empty()) launch_tail(H, l, tail, st);
         if (rest.empty()) return;
-        const std::vector<int> ds = descs(H, l, rest);
+        const std::vector<int> ds = adescs(H, l, rest);
         const TileChoice tc = tiles_of(H, ds);
         gs_gram(H, ds, tc.gram, SAB, st);   // pre-smoothing from x = 0: r0 = b
         gs_pre(H, ds, tc.pre, st);          // x to SAX, restricted residual to SAB of l+1
@@ -496,22 +520,25 @@ struct Engine : EngineBase {
         std::vector<int> plain, fused;
         for (int b : rest) (adr_per_level(H, b, l + 1) ? fused : plain).push_back(b);
         if (!plain.empty())
-            launch_prolong<PMODE_ADR>(H, descs(H, l, plain), KK_PROLONG_ADR, 4 * C + C / 4 + Q, SAX, SAX, SAB, SV1, SD,
+            launch_prolong<PMODE_ADR>(H, adescs(H, l, plain), KK_PROLONG_ADR, 4 * C + C / 4 + Q, SAX, SAX, SAB, SV1, SD,
                                       0, st);
         if (!fused.empty())
-            launch_prolong<PMODE_ADRF>(H, descs(H, l, fused), KK_PROLONG_ADR, 4 * C + C + Q, SAX, SAX, SAB, SV1, SD,
+            launch_prolong<PMODE_ADRF>(H, adescs(H, l, fused), KK_PROLONG_ADR, 4 * C + C + Q, SAX, SAX, SAB, SV1, SD,
                                        0, st);
         gs_gram(H, ds, tc.gram, SV1, st);   // post-smoothing from x' (r0 = b - L x')
         if (!defer) gs_post(H, ds, SV1, SD, modulate ? 2 : 0, st);
     }
 
     // Algorithm 1's ADR correction steps at level 2 (M times).
+    // Wave-Ray (H.p.ray): correction m uses the ADR levels of plane wave m.
     void adr_corrections(Handle& H, const std::vector<int>& I, int M, cudaStream_t st) {
-        const SegTable& t = H.seg(descs(H, 2, I), false, kPts);
         for (int m = 0; m < M; ++m) {
+            H.cur_var = H.p.ray ? m : 0;
+            const SegTable& t = H.seg(adescs(H, 2, I), false, kPts);
             LAUNCH(KK_RESDEMOD, t, 4 * C + R, k_resdemod<T>, 0);
             adrv(H, 2, I, true, st);
         }
+        H.cur_var = 0;
     }
 
     // Wave cycle on level l >= 2 from u = 0, right-hand side SG, result SU.

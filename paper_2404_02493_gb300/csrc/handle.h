@@ -46,6 +46,10 @@ struct InstHost {
     size_t outer_stride = 0;
     int outer_desc = -1;
     long long off = 0;              // offset of this instance in user arrays (elements)
+    // Wave-Ray: the ADR levels of corrections m = 2..M (rv[m-2][l-1], l >= 2):
+    // own phase, ADR quads, level-2 modulation, coarsest inverse and
+    // descriptor; slots and k shared with lv.  Correction 1 uses lv itself.
+    std::vector<std::vector<LevelHost>> rv;
 };
 
 struct SegTable {
@@ -77,7 +81,9 @@ struct Handle {
     std::vector<InstHost> inst;
     int Lmax = 0;
     // descriptor tables (device) and host copies
-    std::vector<LevelDesc> hdesc;   // cycle levels of all instances
+    std::vector<LevelDesc> hdesc;   // cycle levels of all instances (Wave-Ray variants after the base levels)
+    std::vector<int> base_of;       // descriptor -> the base descriptor of its (instance, level)
+    int cur_var = 0;                // Wave-Ray: correction whose ADR descriptors the engine emits
     LevelDesc* ddesc = nullptr;
     std::vector<LevelDesc> houter;  // outer FP64 level-1 descriptors
     LevelDesc* douter = nullptr;
@@ -151,6 +157,7 @@ EngineBase* make_engine_f32();
 EngineBase* make_engine_f64();
 
 // setup helpers shared by the engines (setup.cu)
+void setup_plane_phase(double* phi64, int n, int pitch, double h1, int scale, double cx, double cy, cudaStream_t st);
 void setup_inject(const double* k_fine, const double* phi_fine, int n1, double omega, int bc, int level,
                   double* k64, double* phi64, double* sig64, int n, int pitch, cudaStream_t st);
 double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,

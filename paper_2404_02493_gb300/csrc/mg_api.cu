@@ -406,6 +406,34 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             if (!lv.vec || !lv.kf || !lv.k64 || !lv.phi64) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
             cudaMemsetAsync(lv.vec, 0, npt * lv.nslot * esz(prec), st);
         }
+        if (adr && p.ray) {
+            // Wave-Ray corrections 2..M: own phase, ADR quads, modulation and coarsest inverse
+            I.rv.assign((size_t)(p.M - 1), std::vector<LevelHost>((size_t)I.L));
+            for (auto& vl : I.rv)
+                for (int l = 2; l <= I.L; ++l) {
+                    const LevelHost& base = I.lv[l - 1];
+                    LevelHost& v = vl[l - 1];
+                    v.n = base.n;
+                    v.pitch = base.pitch;
+                    v.h = base.h;
+                    v.slot_stride = base.slot_stride;
+                    v.nslot = base.nslot;
+                    v.vec = base.vec;
+                    v.kf = base.kf;
+                    v.sig = base.sig;
+                    v.k64 = base.k64;
+                    v.sig64 = base.sig64;
+                    const size_t npt = v.slot_stride;
+                    v.phi64 = (double*)H.alloc(npt * 8);
+                    v.adr = H.alloc(npt * 2 * esz(prec));
+                    if (l == 2) v.mod = H.alloc(npt * esz(prec));
+                    if (l == I.L) v.inv_adr = (double2*)H.alloc((size_t)v.n * v.n * v.n * v.n * sizeof(double2));
+                    if (!v.phi64 || !v.adr || (l == 2 && !v.mod) || (l == I.L && !v.inv_adr)) {
+                        set_error("mg_setup: out of device memory (Wave-Ray levels)");
+                        return MG_ENOMEM;
+                    }
+                }
+        }
         const size_t npt1 = I.lv[0].slot_stride;
         I.outer_stride = npt1;
         I.outer_vec = H.alloc(npt1 * 4 * 16);
@@ -426,13 +454,29 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             LevelHost& lv = I.lv[l - 1];
             setup_inject(in[b].k, in[b].phi, I.n, I.omega, I.bc, l, lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, st);
         }
+        if (p.ray && I.lv.size() >= 2 && I.lv[1].adr) {
+            // Wave-Ray: correction m (0-based here) uses phi_m = cos(theta) x + sin(theta) y,
+            // theta = 2 pi m / M, on every ADR level; correction 0 uses the base levels
+            for (int m = 0; m < p.M; ++m) {
+                const double th = (double)m * 2.0 * M_PI / (double)p.M;
+                const double cx = std::cos(th), cy = std::sin(th);
+                for (int l = 2; l <= I.L; ++l) {
+                    LevelHost& lv = (m == 0) ? I.lv[l - 1] : I.rv[(size_t)m - 1][l - 1];
+                    setup_plane_phase(lv.phi64, lv.n, lv.pitch, I.lv[0].h, 1 << (l - 1), cx, cy, st);
+                }
+            }
+        }
     }
     int rc = mh->eng->setup_fields(H, in, st);
     if (rc) return rc;
     // --- descriptor tables and scalar arenas
-    int nd = 0;
-    for (auto& I : H.inst) nd += I.L;
-    const int nslots = nd + ninst;
+    int nd = 0, nvd = 0;
+    for (auto& I : H.inst) {
+        nd += I.L;
+        nvd += (int)I.rv.size() * (I.L - 1);
+    }
+    const int ndc = nd + nvd;   // cycle descriptors: base levels, then Wave-Ray variants
+    const int nslots = ndc + ninst;
     H.scal = (double*)H.alloc(sizeof(double) * S::SIZE * nslots);
     H.part = (double2*)H.alloc(sizeof(double2) * (size_t)MAXB * MAXDOT * nslots);
     H.counter = (unsigned*)H.alloc(sizeof(unsigned) * NCOUNTERS * nslots);
@@ -521,6 +565,37 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             ++di;
         }
     }
+    // Wave-Ray variant descriptors (levels 2..L of corrections 2..M): the base
+    // level's descriptor with the variant's ADR fields, scale and arenas
+    H.base_of.resize((size_t)ndc);
+    for (int q = 0; q < nd; ++q) H.base_of[(size_t)q] = q;
+    for (int b = 0; b < ninst; ++b) {
+        InstHost& I = H.inst[b];
+        for (auto& vl : I.rv)
+            for (int l = 2; l <= I.L; ++l) {
+                LevelHost& v = vl[l - 1];
+                const int base = I.lv[l - 1].desc;
+                LevelDesc d = H.hdesc[(size_t)base];
+                v.desc = di;
+                d.adr = v.adr;
+                d.mod = v.mod;
+                d.inv_adr = v.inv_adr;
+                d.scal = H.scal + (size_t)S::SIZE * di;
+                d.part = H.part + (size_t)MAXB * MAXDOT * di;
+                d.counter = H.counter + (size_t)NCOUNTERS * di;
+                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, dscr, st);
+                d.fgs = (float)d.gs;
+                d.coarse = (l < I.L) ? di + 1 : -1;
+                if (l == I.L) {
+                    int r = setup_coarse_inverse(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, 1,
+                                                 v.inv_adr, st);
+                    if (r) return r;
+                }
+                H.hdesc.push_back(d);
+                H.base_of[(size_t)di] = base;
+                ++di;
+            }
+    }
     // outer descriptors (FP64, level-1 geometry)
     if (p.outer == MG_OUTER_FGMRES) {
         H.fs = (double*)H.alloc(sizeof(double) * FS::SIZE * ninst);
@@ -539,9 +614,9 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         d.sig = l1.sig64;
         d.adr = nullptr;
         d.mod = nullptr;
-        d.scal = H.scal + (size_t)S::SIZE * (nd + b);
-        d.part = H.part + (size_t)MAXB * MAXDOT * (nd + b);
-        d.counter = H.counter + (size_t)NCOUNTERS * (nd + b);
+        d.scal = H.scal + (size_t)S::SIZE * (ndc + b);
+        d.part = H.part + (size_t)MAXB * MAXDOT * (ndc + b);
+        d.counter = H.counter + (size_t)NCOUNTERS * (ndc + b);
         d.coarse = -1;
         d.xvec = l1.vec;
         d.xstride = (long long)l1.slot_stride;
@@ -583,11 +658,11 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
     cudaMemcpy(H.douter, H.houter.data(), sizeof(LevelDesc) * H.houter.size(), cudaMemcpyHostToDevice);
     if (prec == MG_PREC_MIXED) {
         // the cycle descriptors hold FP32 scalars (first half of each block)
-        std::vector<float> hf((size_t)S::SIZE * 2 * nd, 0.0f);
-        for (int q = 0; q < nd; ++q)
+        std::vector<float> hf((size_t)S::SIZE * 2 * ndc, 0.0f);
+        for (int q = 0; q < ndc; ++q)
             for (int k = 0; k < S::SIZE; ++k) hf[(size_t)q * 2 * S::SIZE + k] = (float)hs[(size_t)q * S::SIZE + k];
-        cudaMemcpy(H.scal, hf.data(), sizeof(double) * S::SIZE * nd, cudaMemcpyHostToDevice);
-        cudaMemcpy(H.scal + (size_t)S::SIZE * nd, hs.data() + (size_t)S::SIZE * nd, sizeof(double) * S::SIZE * ninst,
+        cudaMemcpy(H.scal, hf.data(), sizeof(double) * S::SIZE * ndc, cudaMemcpyHostToDevice);
+        cudaMemcpy(H.scal + (size_t)S::SIZE * ndc, hs.data() + (size_t)S::SIZE * ndc, sizeof(double) * S::SIZE * ninst,
                    cudaMemcpyHostToDevice);
     } else {
         cudaMemcpy(H.scal, hs.data(), sizeof(double) * hs.size(), cudaMemcpyHostToDevice);
@@ -745,6 +820,7 @@ void mg_default_params(mg_params* p) {
     p->tail_nmax = -1;   // automatic (mg_setup)
     p->pdl = 0;
     p->tail_cluster = 0;
+    p->ray = 0;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -754,7 +830,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
-        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1) {
+        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1 || p->ray < 0 ||
+        p->ray > 1) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }

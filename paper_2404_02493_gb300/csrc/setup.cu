@@ -43,6 +43,13 @@ void setup_inject(const double* k_fine, const double* phi_fine, int n1, double o
     k_inject<<<g, b, 0, st>>>(k_fine, phi_fine, n1, omega, bc, level, k64, phi64, sig64, n, pitch);
 }
 
+// Wave-Ray plane-wave phase cx x + cy y on level l (scale = 2^(l-1), h1 the
+// level-1 spacing), as injection of the level-1 phase places it
+void setup_plane_phase(double* phi64, int n, int pitch, double h1, int scale, double cx, double cy, cudaStream_t st) {
+    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
+    k_plane_phase<<<g, b, 0, st>>>(phi64, n, pitch, h1, scale, cx, cy);
+}
+
 // max over nodes of the absolute row sum |A_pp| + (in-grid neighbours)/h^2
 __device__ __forceinline__ double helm_row_sum(const double* k64, const double* sig64, int n, int pitch,
                                                double h, int bc, double shift, int i, int j) {

@@ -5,6 +5,17 @@
 
 namespace wadr {
 
+// Wave-Ray plane-wave phase phi = cx x + cy y at the nodes of level l: node
+// i of level l is level-1 node 2^(l-1) (i+1) - 1, at x = 2^(l-1) (i+1) h1,
+// exactly the value injection of the level-1 phase gives.  Products and the
+// sum are rounded separately (no contraction).
+__global__ inline void k_plane_phase(double* phi64, int n, int pitch, double h1, int scale, double cx, double cy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const double x = __dmul_rn((double)(scale * (i + 1)), h1), y = __dmul_rn((double)(scale * (j + 1)), h1);
+    phi64[(long long)j * pitch + i] = __dadd_rn(__dmul_rn(cx, x), __dmul_rn(cy, y));
+}
+
 struct AdrCoef {
     double2 d, cw, ce, cs, cn;
     double px, py;

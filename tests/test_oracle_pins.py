@@ -486,3 +486,43 @@ def test_more_adr_corrections_converge_faster(cfg1):
         _, it, hist = oracle.solve_fgmres(H, inst.g, tol=1e-6, maxit=80)
         res[M] = it
     assert res[8] < res[2]
+
+
+def test_wave_ray_sets_have_unit_plane_wave_gradients():
+    """Wave-Ray (Section 3.2): correction m solves the ray equation of the
+    plane wave exp(i w k_m . x), k_m = (cos theta_m, sin theta_m), theta_m =
+    2 pi (m-1) / M.  The oracle's ADR coefficients of every direction and
+    level must therefore carry grad phi = k_m (central differences of a
+    linear phase, also at the extrapolated boundary ghosts) and Lap phi = 0,
+    and the modulation at level 2 must be the plane wave itself."""
+    from oracle.cycle import CycleParams, Hierarchy
+    I = synth.config_lognormal(n=63, omega=30.0, seed=7)
+    M = 8
+    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=7, M=M, ray=True))
+    assert len(H.adr_sets) == M
+    for m, (coefs, mod, lu) in enumerate(H.adr_sets):
+        th = 2 * np.pi * m / M
+        for l, c in coefs.items():
+            assert np.allclose(c.phix, np.cos(th), atol=1e-11, rtol=0)
+            assert np.allclose(c.phiy, np.sin(th), atol=1e-11, rtol=0)
+            # rounding noise of the second difference only (eps / h^2 scale)
+            assert np.abs(c.lap).max() < 1e-9 * (H.lev(l).n + 1) ** 2
+        n2 = H.lev(2).n
+        nf = H.lev(1).n
+        # level-2 node I sits on fine node 2I+1 at x = (2I+2) / (nf+1)
+        X = (2 * np.arange(n2) + 2) / (nf + 1)
+        XX, YY = np.meshgrid(X, X, indexing="xy")
+        assert np.allclose(mod, np.exp(1j * I.omega * (np.cos(th) * XX + np.sin(th) * YY)), atol=1e-12)
+
+
+def test_wave_ray_single_direction_is_wave_adr_with_phase_x():
+    """With M = 1 the only ray direction is theta = 0, so a Wave-Ray cycle is
+    the Wave-ADR cycle whose input phase is phi = x (bit for bit)."""
+    from oracle.cycle import CycleParams, Hierarchy
+    I = synth.config_lognormal(n=47, omega=25.0, seed=8)
+    n = I.n
+    X, _ = np.meshgrid((np.arange(n) + 1) / (n + 1), (np.arange(n) + 1) / (n + 1), indexing="xy")
+    Hr = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=7, M=1, ray=True))
+    Ha = Hierarchy(I.n, I.k, 1.0 * X, I.omega, I.bc, CycleParams(n_cmax=7, M=1, ray=False))
+    u = np.zeros_like(I.g)
+    assert np.array_equal(Hr.cycle(u, I.g), Ha.cycle(u, I.g))
