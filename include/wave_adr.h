@@ -290,6 +290,15 @@ int mg_cycle_launches(const mg_handle* h);
  * binding check its struct layout.  Needs no GPU. */
 void mg_abi_sizes(size_t* params, size_t* instance, size_t* info);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).  One
+ * block arms an mbarrier for 16 bytes that no copy will deliver and waits on
+ * it with the same bounded wait as the tile kernels: after the wait limit
+ * (100 ms of wall clock) the block records the expiry in a device word and
+ * leaves.  Returns MG_ETIMEOUT when the expiry was recorded (the expected
+ * outcome), MG_OK if the wait completed (it cannot), MG_ECUDA on a CUDA
+ * error.  Synchronises `stream`; the CUDA context stays usable. */
+int mg_selftest_wait_timeout(mg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Residual without allocation.  The paper has no counterpart of this entry
  * point; it exists for callers that may not allocate device memory: a plugin

@@ -94,6 +94,7 @@ def load():
                                     ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
         "mg_cycle_backward": (ip, [vp, vp, vp, ip, vp, vp, vp, vp, vp]),
         "mg_tile_shapes": (ip, [vp, ip, ip, ctypes.POINTER(ip)]),
+        "mg_selftest_wait_timeout": (ip, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -111,7 +112,7 @@ def exported_symbols():
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
             "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
-            "mg_tile_shapes"]
+            "mg_tile_shapes", "mg_selftest_wait_timeout"]
 
 
 class MgError(RuntimeError):
@@ -337,3 +338,8 @@ def mg_cycle_backward(h, u0, g, K, gbar_uK, grad_phi=None, grad_weights=None, gr
     and d/d u0 of K cycles for the cotangent gbar_uK of u_K."""
     _check(load().mg_cycle_backward(h, _ptr(u0), _ptr(g), int(K), _ptr(gbar_uK), _ptr(grad_phi),
                                     _ptr(grad_weights), _ptr(grad_u0), _stream(stream)), "mg_cycle_backward")
+
+
+def mg_selftest_wait_timeout(stream=None):
+    """Bounded-wait self-test: returns the library status (MG_ETIMEOUT expected)."""
+    return load().mg_selftest_wait_timeout(_stream(stream))

@@ -1316,3 +1316,38 @@ int mg_coarse_solve(mg_handle* h, int inst, int which, const void* b, void* x, m
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ bounded-wait self-test
+namespace wadr {
+__global__ void k_selftest_wait(unsigned* err) {
+    __shared__ alignas(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);   // 16 bytes that no copy delivers
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0);                // bounded: TMA_WAIT_NS
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1u);
+}
+}  // namespace wadr
+
+extern "C" int mg_selftest_wait_timeout(mg_stream stream) {
+    using namespace wadr;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned* derr = nullptr;
+    if (cudaMalloc(&derr, sizeof(unsigned)) != cudaSuccess) { set_error("mg_selftest_wait_timeout: cudaMalloc"); return MG_ECUDA; }
+    unsigned herr = 0;
+    cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 32, 0, st>>>(derr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(derr);
+    if (e != cudaSuccess) { set_error(std::string("mg_selftest_wait_timeout: ") + cudaGetErrorString(e)); return MG_ECUDA; }
+    if (herr) { set_error("mg_selftest_wait_timeout: the bounded wait expired (expected)"); return MG_ETIMEOUT; }
+    return MG_OK;
+}
