@@ -117,6 +117,10 @@ typedef struct mg_params {
                                plane-wave phase phi_m = cos(theta_m) x + sin(theta_m) y, theta_m =
                                (m-1) 2 pi / M, instead
                                (the input phi is not used; mg_cycle_backward is not available) */
+    int fgmres_passes;      /* Gram-Schmidt passes over the Krylov vectors per FGMRES iteration: 3 = CGS2
+                               (projection, re-orthogonalisation, norm); 2 (default) = the same CGS2 with the
+                               re-orthogonalisation of each new basis vector done in the next iteration's passes
+                               (one pass over all Krylov vectors less per iteration) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */

@@ -650,26 +650,42 @@ struct Engine : EngineBase {
         {
             std::vector<int> od;
             for (auto& I : H.inst) od.push_back(I.outer_desc);
-            auto k0 = k_fg_gs<T, 0>;
-            auto k1 = k_fg_gs<T, 1>;
-            auto k2 = k_fg_gs<T, 2>;
             const int smem = fg_smem<T>();
-            const int cap = occ_cap(k0, smem);
-            occ_cap(k1, smem);
-            occ_cap(k2, smem);
-            const SegTable& tg = H.seg_outer_chunks(od, fg_chunk<T>(), cap);
-            go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
-                kl(k0, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
-            }, tg.pts);
-            go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
-                kl(k1, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
-            }, tg.pts);
-            go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
-                kl(k2, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
-            }, tg.pts);
+            if (H.p.fgmres_passes == 2) {
+                // two passes: dots (V_0..V_j, W), then the lagged re-orthogonalisation
+                // of V_j and the projection of W (writes V_j and W)
+                auto a = k_fg_lag<T, 0>;
+                auto b = k_fg_lag<T, 1>;
+                const int cap = occ_cap(a, smem);
+                occ_cap(b, smem);
+                const SegTable& tg = H.seg_outer_chunks(od, fg_chunk<T>(), cap);
+                go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
+                    kl(a, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
+                }, tg.pts);
+                go(H, st, KK_FG_ORTH, (j + 4) * C * tg.pts, [&] {
+                    kl(b, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
+                }, tg.pts);
+            } else {
+                auto k0 = k_fg_gs<T, 0>;
+                auto k1 = k_fg_gs<T, 1>;
+                auto k2 = k_fg_gs<T, 2>;
+                const int cap = occ_cap(k0, smem);
+                occ_cap(k1, smem);
+                occ_cap(k2, smem);
+                const SegTable& tg = H.seg_outer_chunks(od, fg_chunk<T>(), cap);
+                go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
+                    kl(k0, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
+                }, tg.pts);
+                go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
+                    kl(k1, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
+                }, tg.pts);
+                go(H, st, KK_FG_ORTH, (j + 3) * C * tg.pts, [&] {
+                    kl(k2, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg);
+                }, tg.pts);
+            }
         }
         H.launches_cycle = cyc;
-        H.launches_step = cyc + 5;
+        H.launches_step = cyc + (H.p.fgmres_passes == 2 ? 4 : 5);
         H.fg_j = j + 1;
     }
 
@@ -677,7 +693,10 @@ struct Engine : EngineBase {
     void fg_finish(Handle& H, cudaStream_t st) override {
         const SegTable& t = outer_tab(H);
         go(H, st, KK_FG_UPDATE, (H.fg_j * C + 32.0) * t.pts, [&] {
-            kl(k_fg_update<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg);
+            if (H.p.fgmres_passes == 2)
+                kl(k_fg_update<T, true>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg);
+            else
+                kl(k_fg_update<T, false>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
         outer_residual(H, false, st);
         H.fg_j = 0;

@@ -18,11 +18,13 @@ namespace wadr {
 
 constexpr int MAXR = 22;     // largest restart length
 constexpr int NVF = 24;      // dots per block partial (MAXR + norm, padded)
+constexpr int NVL = 48;      // dots per block partial of the two-pass scheme (2 MAXR + 2, padded)
 
 namespace FS {
 constexpr int J = 0;         // current inner index
 constexpr int JDONE = 1;     // columns used by the last update
 constexpr int EST = 2;       // |gamma_{j+1}| (inner relative residual estimate)
+constexpr int BETA = 3;      // two-pass scheme: norm of the new basis vector's orthogonal part
 constexpr int HN = 4;        // HN[i]: norm of V_i before normalisation (i >= 1)
 constexpr int HC = 32;       // first-pass projections, NVF complex
 constexpr int CC = 80;       // second-pass projections, NVF complex
@@ -334,8 +336,247 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const __grid_constant__ KDesc A
     }
 }
 
+// ------------------------------------------------------------ two-pass Gram-Schmidt
+// Two passes over the Krylov vectors per inner iteration instead of three
+// (the option `fgmres_passes = 2`).  The basis vector V_j enters step j as
+// Vt_j = W1_{j-1} / ||W1_{j-1}||, orthogonalised once (the cycle is applied
+// to it); its second orthogonalisation is done lazily in step j:
+//   pass A: S1_q = <V_q, Vt_j>, S2_q = <V_q, W> (q < j), s3 = <Vt_j, W>,
+//           ||Vt_j||^2; then V_j = (Vt_j - V S1) / beta with
+//           beta^2 = ||Vt_j||^2 - ||S1||^2, and <V_j, W> = (s3 - S1^H S2) / beta.
+//           The Hessenberg column j-1 becomes final: since
+//           W1_{j-1} = ||W1_{j-1}|| (beta V_j + V S1), its rows q < j gain
+//           ||W1_{j-1}|| S1_q and row j is ||W1_{j-1}|| beta; the column is
+//           then rotated and the Givens recursion advances.
+//   pass B: V_j written corrected, W1_j = W - V_{<j} h - h_j V_j and
+//           ||W1_j||; column j is stored unrotated (pending) and a
+//           provisional rotation of it gives the residual estimate.
+// A Z = V H holds with the final V (flexible GMRES only needs W = A z_j in
+// the orthonormal basis), so the method is CGS2 with the re-orthogonalisation
+// of each new vector moved to the next step.  At the end of a restart the
+// pending column enters the update with its provisional rotation.
+template <typename TC, int J>
+__device__ __forceinline__ void fg_lag_dots(const cplx<TC>* __restrict__ sv, int PJ, int cnt, cplx<TC> (&s1)[MAXR],
+                                            cplx<TC> (&s2)[MAXR], cplx<TC>& s3, TC& nv, int tid) {
+    for (int e = tid; e < cnt; e += NT) {
+        const cplx<TC> vt = sv[J * PJ + e], w = sv[(J + 1) * PJ + e];
+#pragma unroll
+        for (int q = 0; q < J; ++q) {
+            const cplx<TC> vq = sv[q * PJ + e];
+            s1[q] = cadd<TC>(s1[q], cmulc<TC>(vq, vt));
+            s2[q] = cadd<TC>(s2[q], cmulc<TC>(vq, w));
+        }
+        s3 = cadd<TC>(s3, cmulc<TC>(vt, w));
+        nv += cabs2<TC>(vt);
+    }
+}
+template <typename TC, int J>
+__device__ __forceinline__ void fg_lag_update(const cplx<TC>* __restrict__ sv, int PJ, int cnt,
+                                              cplx<TC>* __restrict__ vout, cplx<TC>* __restrict__ wout,
+                                              const cplx<TC>* s1c, const cplx<TC>* hc, TC ibeta, TC& nrm, int tid) {
+    for (int e = tid; e < cnt; e += NT) {
+        cplx<TC> v = sv[J * PJ + e], w = sv[(J + 1) * PJ + e];
+#pragma unroll
+        for (int q = 0; q < J; ++q) {
+            const cplx<TC> vq = sv[q * PJ + e];
+            v = csub<TC>(v, cmul<TC>(s1c[q], vq));
+            w = csub<TC>(w, cmul<TC>(hc[q], vq));
+        }
+        v = cscale<TC>(v, ibeta);
+        w = csub<TC>(w, cmul<TC>(hc[J], v));
+        if (J > 0) vout[e] = v;
+        wout[e] = w;
+        nrm += cabs2<TC>(w);
+    }
+}
+
+// Apply the committed rotations 0..j-1 to col[0..j+1] (rows of column j).
+__device__ __forceinline__ void fg_rotate(const double* f, int j, double2* col) {
+    for (int q = 0; q < j; ++q) {
+        const double2 cs = sload2d(f, FS::CS + 2 * q), sn = sload2d(f, FS::SN + 2 * q);
+        const double2 a = col[q], b = col[q + 1];
+        col[q] = dadd(dmulc(cs, a), dmulc(sn, b));
+        col[q + 1] = dsub(dmul(cs, b), dmul(sn, a));
+    }
+}
+
+template <typename TC, int PASS>
+__global__ void __launch_bounds__(NT, 1) k_fg_lag(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
+                                                  int nseg) {
+    constexpr int P = fg_chunk<TC>();
+    extern __shared__ unsigned char fg_raw[];
+    TmaCarve cv(fg_raw);
+    cplx<TC>* const stg0 = cv.take<cplx<TC>>(2 * (MAXR + 1) * P);
+    __shared__ LevelDesc d;
+    __shared__ double2 grp[4 * 64];
+    __shared__ double2 tot[NVL];
+    __shared__ cplx<TC> shT[8 * NVL];
+    __shared__ cplx<TC> s1c[MAXR], hc[MAXR];
+    __shared__ TC ibeta_sh;
+    __shared__ int flag;
+    __shared__ alignas(8) uint64_t bars[2];
+    SegCtx c = seg_begin(A, Sg, nseg, d);
+    TmaPipe pipe;
+    pipe.init(bars);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const long long N = (long long)d.n * d.pitch;
+    const int jj = (int)d.fs[FS::J];
+    const int PJ = P * ((MAXR + 1) / (jj + 2));
+    const int nchunks = (int)((N + PJ - 1) / PJ);
+    auto stg = [&](int b, int q) { return stg0 + b * (MAXR + 1) * P + q * PJ; };
+    cplx<TC>* vj = kvec<TC>(d, jj);
+    cplx<TC>* w = kvec<TC>(d, jj + 1);
+    if (PASS == 1) {
+        if (tid < MAXR) {
+            s1c[tid] = tid < jj ? mk<TC>((TC)d.fs[FS::CC + 2 * tid], (TC)d.fs[FS::CC + 2 * tid + 1]) : zero2<TC>();
+            hc[tid] = tid <= jj ? mk<TC>((TC)d.fs[FS::HC + 2 * tid], (TC)d.fs[FS::HC + 2 * tid + 1]) : zero2<TC>();
+        }
+        if (tid == 0) ibeta_sh = (TC)(1.0 / d.fs[FS::BETA]);
+    }
+    __syncthreads();
+    auto issue = [&](int k, int b) {
+        if (tid != 0) return;
+        const long long e0 = (long long)k * PJ;
+        const unsigned bytes = (unsigned)(min((long long)PJ, N - e0) * (long long)sizeof(cplx<TC>));
+        pipe.expect(b, bytes * (unsigned)(jj + 2));
+        for (int q = 0; q <= jj; ++q) bulk_load(stg(b, q), kvec<TC>(d, q) + e0, bytes, &bars[b]);
+        bulk_load(stg(b, jj + 1), w + e0, bytes, &bars[b]);
+    };
+    cplx<TC> s1[MAXR], s2[MAXR], s3 = zero2<TC>();
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) s1[q] = s2[q] = zero2<TC>();
+    TC nv = TC(0), nrm = TC(0);
+    const TC ibeta = PASS == 1 ? ibeta_sh : TC(1);
+    int buf = 0;
+    if (c.lb < nchunks) issue(c.lb, 0);
+    for (int k = c.lb; k < nchunks; k += c.nb) {
+        if (k + c.nb < nchunks) issue(k + c.nb, buf ^ 1);
+        if (!pipe.wait(buf, d.err)) return;
+        const long long e0 = (long long)k * PJ;
+        const int cnt = (int)min((long long)PJ, N - e0);
+        const cplx<TC>* sv = stg(buf, 0);
+        fg_dispatch<MAXR>(jj, [&](auto Jc) {
+            constexpr int JJ = decltype(Jc)::value;
+            if (PASS == 0) fg_lag_dots<TC, JJ>(sv, PJ, cnt, s1, s2, s3, nv, tid);
+            else fg_lag_update<TC, JJ>(sv, PJ, cnt, vj + e0, w + e0, s1c, hc, ibeta, nrm, tid);
+        });
+        __syncthreads();
+        buf ^= 1;
+    }
+    // block sums -> per-block partials -> the last block of the segment
+    cplx<TC> red[NVL];
+#pragma unroll
+    for (int q = 0; q < NVL; ++q) red[q] = zero2<TC>();
+    if (PASS == 0) {
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q) {
+            red[q] = s1[q];
+            red[MAXR + q] = s2[q];
+        }
+        red[2 * MAXR] = s3;
+        red[2 * MAXR + 1] = mk<TC>(nv, TC(0));
+    } else {
+        red[0] = mk<TC>(nrm, TC(0));
+    }
+    block_sum<cplx<TC>, NVL>(red, shT);
+    if (tid == 0) {
+        for (int q = 0; q < NVL; ++q) d.fpart[(long long)c.lb * NVL + q] = to_d(red[q]);
+        __threadfence();
+        const unsigned prev = atomicAdd(&d.counter[2], 1u);
+        flag = (prev == (unsigned)(c.nb - 1));
+    }
+    __syncthreads();
+    if (!flag) return;
+    __threadfence();
+    {
+        // value k = tid % 64 (< NVL) of block group g = tid / 64 sums blocks g, g+4, ...;
+        // the 4 group sums are added in order
+        const int k = tid & 63, g = tid >> 6;
+        double2 sacc = make_double2(0.0, 0.0);
+        if (k < NVL)
+            for (int b = g; b < c.nb; b += 4) sacc = dadd(sacc, __ldcg(&d.fpart[(long long)b * NVL + k]));
+        grp[g * 64 + k] = sacc;
+        __syncthreads();
+        if (tid < NVL) {
+            double2 t = grp[tid];
+            for (int q = 1; q < 4; ++q) t = dadd(t, grp[q * 64 + tid]);
+            tot[tid] = t;
+        }
+        if (tid == 0) d.counter[2] = 0u;
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    double* f = d.fs;
+    const int j = jj;
+    if (PASS == 0) {
+        double2 S1[MAXR], S2[MAXR];
+        double ss = 0.0;
+        for (int q = 0; q < j; ++q) {
+            S1[q] = tot[q];
+            S2[q] = tot[MAXR + q];
+            ss += dabs2(S1[q]);
+        }
+        const double2 s3d = tot[2 * MAXR];
+        const double nvd = tot[2 * MAXR + 1].x;
+        // V_0 comes normalised from the restart; later vectors lose their projections
+        const double b2 = j == 0 ? 1.0 : nvd - ss;
+        const double beta = b2 > 0.0 ? sqrt(b2) : 1e-300;
+        if (j >= 1) {
+            // column j-1 final: rows q < j gain ||W1_{j-1}|| S1_q, row j is ||W1_{j-1}|| beta
+            const double hn = f[FS::HN + j];
+            double2 col[MAXR + 1];
+            for (int q = 0; q < j; ++q) col[q] = dadd(sload2d(f, FS::H + 2 * (q * MAXR + (j - 1))), dsc(S1[q], hn));
+            col[j] = make_double2(hn * beta, 0.0);
+            fg_rotate(f, j - 1, col);
+            const double2 a = col[j - 1], b = col[j];
+            const double den = sqrt(dabs2(a) + dabs2(b));
+            double2 cs = make_double2(1, 0), sn = make_double2(0, 0);
+            if (den > 0) {
+                cs = dsc(a, 1.0 / den);
+                sn = dsc(b, 1.0 / den);
+            }
+            sstore2d(f, FS::CS + 2 * (j - 1), cs);
+            sstore2d(f, FS::SN + 2 * (j - 1), sn);
+            col[j - 1] = make_double2(den, 0);
+            for (int q = 0; q < j; ++q) sstore2d(f, FS::H + 2 * (q * MAXR + (j - 1)), col[q]);
+            const double2 gj = sload2d(f, FS::G + 2 * (j - 1));
+            sstore2d(f, FS::G + 2 * j, dsc(dmul(sn, gj), -1.0));
+            sstore2d(f, FS::G + 2 * (j - 1), dmulc(cs, gj));
+        }
+        // column j, rows 0..j (pending until step j+1): h_q = S2_q, h_j = (s3 - S1^H S2) / beta
+        double2 hj = s3d;
+        for (int q = 0; q < j; ++q) hj = dsub(hj, dmulc(S1[q], S2[q]));
+        hj = dsc(hj, 1.0 / beta);
+        for (int q = 0; q < j; ++q) {
+            sstore2d(f, FS::HC + 2 * q, S2[q]);
+            sstore2d(f, FS::CC + 2 * q, S1[q]);
+            sstore2d(f, FS::H + 2 * (q * MAXR + j), S2[q]);
+        }
+        sstore2d(f, FS::HC + 2 * j, hj);
+        sstore2d(f, FS::H + 2 * (j * MAXR + j), hj);
+        f[FS::BETA] = beta;
+    } else {
+        const double hn = sqrt(tot[0].x);
+        f[FS::HN + j + 1] = hn;
+        sstore2d(f, FS::H + 2 * ((j + 1) * MAXR + j), make_double2(hn, 0.0));
+        // provisional rotation of the pending column j: the residual estimate
+        double2 col[MAXR + 1];
+        for (int q = 0; q <= j; ++q) col[q] = sload2d(f, FS::H + 2 * (q * MAXR + j));
+        col[j + 1] = make_double2(hn, 0.0);
+        fg_rotate(f, j, col);
+        const double den = sqrt(dabs2(col[j]) + hn * hn);
+        const double est = den > 0 ? hn / den * sqrt(dabs2(sload2d(f, FS::G + 2 * j))) : 0.0;
+        f[FS::EST] = est;
+        f[FS::J] = j + 1;
+        f[FS::JDONE] = j + 1;
+        *d.est = est;
+    }
+}
+
 // y = R^{-1} gamma (one thread per instance), then u += ||r|| sum_i y_i Z_i.
-template <typename TC>
+// LAG (two-pass scheme): the last column is still pending (unrotated); it
+// enters with its provisional rotation.
+template <typename TC, bool LAG>
 __global__ void __launch_bounds__(NT) k_fg_update(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                   int nseg) {
     __shared__ LevelDesc d;
@@ -346,10 +587,24 @@ __global__ void __launch_bounds__(NT) k_fg_update(const __grid_constant__ KDesc 
     if (tid == 0) {
         // every block solves the (tiny) triangular system redundantly
         const double* f = d.fs;
+        double2 rl[MAXR + 1];
+        double2 gl = m > 0 ? sload2d(f, FS::G + 2 * (m - 1)) : make_double2(0, 0);
+        if (LAG && m > 0) {
+            for (int q = 0; q <= m; ++q) rl[q] = sload2d(f, FS::H + 2 * (q * MAXR + (m - 1)));
+            fg_rotate(f, m - 1, rl);
+            const double2 a = rl[m - 1], b = rl[m];
+            const double den = sqrt(dabs2(a) + dabs2(b));
+            const double2 cs = den > 0 ? dsc(a, 1.0 / den) : make_double2(1, 0);
+            rl[m - 1] = make_double2(den, 0);
+            gl = dmulc(cs, gl);
+        }
+        auto Rq = [&](int q, int r) {
+            return (LAG && r == m - 1) ? rl[q] : sload2d(f, FS::H + 2 * (q * MAXR + r));
+        };
         for (int q = m - 1; q >= 0; --q) {
-            double2 acc = sload2d(f, FS::G + 2 * q);
-            for (int r = q + 1; r < m; ++r) acc = dsub(acc, dmul(sload2d(f, FS::H + 2 * (q * MAXR + r)), ysh[r]));
-            const double2 rqq = sload2d(f, FS::H + 2 * (q * MAXR + q));
+            double2 acc = (q == m - 1) ? gl : sload2d(f, FS::G + 2 * q);
+            for (int r = q + 1; r < m; ++r) acc = dsub(acc, dmul(Rq(q, r), ysh[r]));
+            const double2 rqq = Rq(q, q);
             ysh[q] = dabs2(rqq) > 0 ? ddiv(acc, rqq) : make_double2(0, 0);
         }
     }

@@ -114,7 +114,7 @@ struct Handle {
     // FGMRES
     int fg_j = 0;                           // inner index of the current restart (host copy)
     double* fs = nullptr;                   // [ninst][FS::SIZE]
-    double2* fpart = nullptr;               // [ninst][MAXB][NVF]
+    double2* fpart = nullptr;               // [ninst][MAXB][NVL]
     double* est = nullptr;                  // [ninst]
     cudaGraphExec_t g_fgiter = nullptr;
     // pinned host scratch for scalars

@@ -599,7 +599,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
     // outer descriptors (FP64, level-1 geometry)
     if (p.outer == MG_OUTER_FGMRES) {
         H.fs = (double*)H.alloc(sizeof(double) * FS::SIZE * ninst);
-        H.fpart = (double2*)H.alloc(sizeof(double2) * (size_t)MAXB * NVF * ninst);
+        H.fpart = (double2*)H.alloc(sizeof(double2) * (size_t)MAXB * NVL * ninst);
         H.est = (double*)H.alloc(sizeof(double) * ninst);
         if (!H.fs || !H.fpart || !H.est) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
         cudaMemsetAsync(H.fs, 0, sizeof(double) * FS::SIZE * ninst, st);
@@ -626,7 +626,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         if (p.outer == MG_OUTER_FGMRES) {
             d.kv = I.kv;
             d.fs = H.fs + (size_t)FS::SIZE * b;
-            d.fpart = H.fpart + (size_t)MAXB * NVF * b;
+            d.fpart = H.fpart + (size_t)MAXB * NVL * b;
             d.est = H.est + b;
         }
         I.outer_desc = b;
@@ -821,6 +821,7 @@ void mg_default_params(mg_params* p) {
     p->pdl = 0;
     p->tail_cluster = 0;
     p->ray = 0;
+    p->fgmres_passes = 2;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -831,7 +832,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
         p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1 || p->ray < 0 ||
-        p->ray > 1) {
+        p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }

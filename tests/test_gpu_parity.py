@@ -291,3 +291,25 @@ def test_degenerate_inputs():
     B.mg_gmres3(P.h, 0, l, b, x, 1)
     assert rel(x, x0) < 1e-12
     P.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_pass_gram_schmidt_matches_three_pass(prec):
+    """FGMRES with the re-orthogonalisation of each basis vector moved to the
+    next iteration (fgmres_passes = 2, default) against plain CGS2 (3 passes):
+    the same iteration count +-1, both below tolerance, solutions within the
+    tolerance of each other, and the same oracle count +-1."""
+    I, ncm = CASES["odd127_medium"]()
+    H = oracle_hier(I, n_cmax=ncm)
+    _, it_o, _ = oracle.solve_fgmres(H, I.g, tol=1e-6, maxit=300)
+    res = {}
+    for passes in (2, 3):
+        h = lib_handle([I], prec, n_cmax=ncm, tol=1e-6, maxit=300, fgmres_passes=passes)
+        u = np.zeros_like(I.g)
+        st, it, rr, hist, sec = B.mg_solve(h, u, I.g.copy(), history_len=400)
+        B.mg_destroy(h)
+        assert st == B.MG_OK and rr < 1e-6
+        assert abs(it - it_o) <= 1, (passes, it, it_o)
+        res[passes] = (it, u)
+    assert abs(res[2][0] - res[3][0]) <= 1
+    assert rel(res[2][1], res[3][1]) < 1e-5
