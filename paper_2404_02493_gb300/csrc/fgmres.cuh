@@ -173,9 +173,9 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const __grid_constant__ KDesc 
 
 // Gram-Schmidt passes of FGMRES over the level-1 vectors.  The padded
 // vectors are contiguous (pitch * n values, zero in the row padding), so a
-// pass treats them as flat arrays cut into chunks of FG_CHUNK values: for
-// each chunk the block streams W and V_0..V_j in by 1D bulk copies into one
-// of two shared-memory stages (the next chunk's copies are in flight while
+// pass treats them as flat arrays cut into chunks: for each chunk the block
+// streams W and V_0..V_j in by 1D bulk copies into one stage of a ring of
+// shared-memory stages (the copies of the next chunks are in flight while
 // the current chunk is computed), and every thread works on its values of
 // the chunk from shared memory.
 //   PASS 0: projections <V_i, W>, i <= j             -> fs[HC]
@@ -183,15 +183,24 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const __grid_constant__ KDesc 
 //   PASS 2: W -= sum_i h2_i V_i; ||W''||^2; the last block completes column
 //           j of the Hessenberg, applies the Givens rotations, stores
 //           |gamma_{j+1}| and advances j.
-template <typename TC> __host__ __device__ constexpr int fg_chunk() { return sizeof(cplx<TC>) == 8 ? 512 : 256; }
-template <typename TC> __host__ __device__ constexpr int fg_smem() {
-    return 128 + 2 * (MAXR + 1) * tma_piece<cplx<TC>>(fg_chunk<TC>());
+//
+// Ring geometry: a stage holds (MAXR + 1) pw values; with j + 2 vectors to
+// stream, the chunk is the largest multiple PJ of 32 values with
+// (j + 2) PJ <= (MAXR + 1) pw, so a stage is nearly full at every j:
+// [V_0..V_j, W][PJ].  32 values and pw values are multiples of 128 bytes,
+// so every piece stays 128-byte aligned (bulk copies want 16).
+constexpr int FG_MAXNS = 8;
+struct FgGeom {
+    int pw, ns;      // piece length (values), stages
+};
+template <typename TC> __host__ __device__ constexpr int fg_smem(FgGeom g) {
+    return 128 + g.ns * (MAXR + 1) * g.pw * (int)sizeof(cplx<TC>);
 }
 
 // One chunk of a Gram-Schmidt pass with the inner index j known at compile
 // time (J), so that exactly J + 1 projection terms are unrolled.
 template <typename TC, int PASS, int J, int NA>
-__device__ __forceinline__ void fg_chunk(const cplx<TC>* __restrict__ sv, int PJ, int cnt, cplx<TC>* __restrict__ w,
+__device__ __forceinline__ void fg_gs_chunk(const cplx<TC>* __restrict__ sv, int PJ, int cnt, cplx<TC>* __restrict__ w,
                                          const cplx<TC>* coef, cplx<TC> (&ac)[NA], TC& nrm, int tid) {
     for (int e = tid; e < cnt; e += NT) {
         cplx<TC> wv = sv[(J + 1) * PJ + e];
@@ -222,67 +231,99 @@ __device__ __forceinline__ void fg_dispatch(int v, F&& f) {
     f(std::integral_constant<int, N - 1>{});
 }
 
+// The chunks k = lb, lb + nb, ... of a block through the ring of ns stages:
+// the copies of the block's next ns - 1 chunks are in flight while one is
+// computed; body(sv, PJ, cnt, e0) works on the chunk of cnt values from
+// flat index e0 at sv ([V_0..V_j, W][PJ]).  The j + 2 copies of a chunk are
+// issued by as many lanes of warp 0 at once (one thread issuing them in turn
+// held the whole block at the next barrier).  One block barrier per chunk:
+// every thread waits for the stage's copies itself, and the barrier after
+// the chunk also makes a wait that expired known to all.  Returns false
+// (block-uniform) in that case: the error word is set and the copies still
+// in flight are awaited (bounded) first.
+template <typename TC, class Body>
+__device__ __forceinline__ bool fg_stream(const LevelDesc& d, const SegCtx& c, int jj, const cplx<TC>* w,
+                                          cplx<TC>* stg0, FgGeom g, uint64_t* bars, Body&& body) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const long long N = (long long)d.n * d.pitch;
+    const int PJ = (MAXR + 1) * g.pw / (jj + 2) / 32 * 32;
+    const long long nchunks = (N + PJ - 1) / PJ;
+    const int nmine = c.lb < nchunks ? (int)((nchunks - 1 - c.lb) / c.nb + 1) : 0;
+    const int sstride = (MAXR + 1) * g.pw;
+    if (tid == 0) {
+        for (int s = 0; s < g.ns; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto first = [&](int i) { return (long long)(c.lb + (long long)i * c.nb) * PJ; };
+    // warp 0: the copies of the block's chunk i into stage i % ns, vector q
+    // (V_0..V_j, then W = V_{j+1}) by lane q; the expected bytes are posted
+    // before any copy is issued
+    auto issue = [&](int i) {
+        const long long e0 = first(i);
+        const unsigned bytes = (unsigned)(min((long long)PJ, N - e0) * (long long)sizeof(cplx<TC>));
+        cplx<TC>* st = stg0 + (i % g.ns) * sstride;
+        uint64_t* b = &bars[i % g.ns];
+        if (tid == 0) mbar_expect_tx(b, bytes * (unsigned)(jj + 2));
+        __syncwarp();
+        for (int q = tid; q <= jj + 1; q += 32)
+            bulk_load(st + q * PJ, (q <= jj ? (const cplx<TC>*)kvec<TC>(d, q) : w) + e0, bytes, b);
+    };
+    if (tid < 32)
+        for (int i = 0; i < min(g.ns - 1, nmine); ++i) issue(i);
+    for (int i = 0; i < nmine; ++i) {
+        // stage (i - 1) % ns was released by the barrier that ended chunk i - 1
+        if (tid < 32 && i + g.ns - 1 < nmine) issue(i + g.ns - 1);
+        const bool landed = mbar_wait(&bars[i % g.ns], (unsigned)((i / g.ns) & 1));
+        const long long e0 = first(i);
+        // a thread whose wait expired skips the chunk; the others' results are dropped below
+        if (landed) body((const cplx<TC>*)(stg0 + (i % g.ns) * sstride), PJ, (int)min((long long)PJ, N - e0), e0);
+        if (__syncthreads_or(landed ? 0 : 1) != 0) {
+            if (tid == 0) {
+                if (d.err) atomicExch(d.err, 1u);
+                for (int q = i + 1; q < min(i + g.ns, nmine); ++q) mbar_wait(&bars[q % g.ns], (unsigned)((q / g.ns) & 1));
+            }
+            __syncthreads();
+            return false;
+        }
+    }
+    return true;
+}
+
 template <typename TC, int PASS>
 __global__ void __launch_bounds__(NT, 1) k_fg_gs(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
-                                                 int nseg) {
-    constexpr int P = fg_chunk<TC>();
+                                                 int nseg, FgGeom g) {
     extern __shared__ unsigned char fg_raw[];
     TmaCarve cv(fg_raw);
-    // a stage holds (MAXR + 1) * P values; with j + 2 vectors to stream the
-    // chunk is PJ = P * floor((MAXR + 1) / (j + 2)) values long, so a stage
-    // is (nearly) full at every j: [stage][V_0..V_j, W][PJ].  P values =
-    // 4 KB, so every piece stays 128-byte aligned.
-    static_assert(P * sizeof(cplx<TC>) % 128 == 0, "chunk size");
-    cplx<TC>* const stg0 = cv.take<cplx<TC>>(2 * (MAXR + 1) * P);
+    cplx<TC>* const stg0 = cv.take<cplx<TC>>(g.ns * (MAXR + 1) * g.pw);
     __shared__ LevelDesc d;
     __shared__ double2 grp[8 * 32];
     __shared__ double2 tot[NVF];
     __shared__ cplx<TC> shT[8 * NVF];
     __shared__ cplx<TC> coef[MAXR];
     __shared__ int flag;
-    __shared__ alignas(8) uint64_t bars[2];
+    __shared__ alignas(8) uint64_t bars[FG_MAXNS];
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    TmaPipe pipe;
-    pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const long long N = (long long)d.n * d.pitch;
     const int jj = (int)d.fs[FS::J];
-    const int PJ = P * ((MAXR + 1) / (jj + 2));
-    const int nchunks = (int)((N + PJ - 1) / PJ);
-    auto stg = [&](int b, int q) { return stg0 + b * (MAXR + 1) * P + q * PJ; };
     cplx<TC>* w = kvec<TC>(d, jj + 1);
     if (PASS > 0) {
         const int off = (PASS == 1) ? FS::HC : FS::CC;
         if (tid < MAXR) coef[tid] = tid <= jj ? mk<TC>((TC)d.fs[off + 2 * tid], (TC)d.fs[off + 2 * tid + 1]) : zero2<TC>();
     }
     __syncthreads();
-    auto issue = [&](int k, int b) {
-        if (tid != 0) return;
-        const long long e0 = (long long)k * PJ;
-        const unsigned bytes = (unsigned)(min((long long)PJ, N - e0) * (long long)sizeof(cplx<TC>));
-        pipe.expect(b, bytes * (unsigned)(jj + 2));
-        for (int q = 0; q <= jj; ++q) bulk_load(stg(b, q), kvec<TC>(d, q) + e0, bytes, &bars[b]);
-        bulk_load(stg(b, jj + 1), w + e0, bytes, &bars[b]);
-    };
     constexpr int NA = (PASS == 2) ? 1 : NVF;
     cplx<TC> ac[NA];
 #pragma unroll
     for (int q = 0; q < NA; ++q) ac[q] = zero2<TC>();
     TC nrm = TC(0);
-    int buf = 0;
-    if (c.lb < nchunks) issue(c.lb, 0);
-    for (int k = c.lb; k < nchunks; k += c.nb) {
-        if (k + c.nb < nchunks) issue(k + c.nb, buf ^ 1);
-        if (!pipe.wait(buf, d.err)) return;
-        const long long e0 = (long long)k * PJ;
-        const int cnt = (int)min((long long)PJ, N - e0);
-        const cplx<TC>* sv = stg(buf, 0);
+    const bool ok = fg_stream<TC>(d, c, jj, w, stg0, g, bars,
+                                  [&](const cplx<TC>* sv, int PJ, int cnt, long long e0) {
         fg_dispatch<MAXR>(jj, [&](auto J) {
-            fg_chunk<TC, PASS, decltype(J)::value>(sv, PJ, cnt, w + e0, coef, ac, nrm, tid);
+            fg_gs_chunk<TC, PASS, decltype(J)::value>(sv, PJ, cnt, w + e0, coef, ac, nrm, tid);
         });
-        __syncthreads();
-        buf ^= 1;
-    }
+    });
+    if (!ok) return;
     cplx<TC> red[NVF];
 #pragma unroll
     for (int q = 0; q < NVF; ++q) red[q] = (q < NA && PASS != 2) ? ac[q < NA ? q : 0] : zero2<TC>();
@@ -402,11 +443,10 @@ __device__ __forceinline__ void fg_rotate(const double* f, int j, double2* col) 
 
 template <typename TC, int PASS>
 __global__ void __launch_bounds__(NT, 1) k_fg_lag(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
-                                                  int nseg) {
-    constexpr int P = fg_chunk<TC>();
+                                                  int nseg, FgGeom g) {
     extern __shared__ unsigned char fg_raw[];
     TmaCarve cv(fg_raw);
-    cplx<TC>* const stg0 = cv.take<cplx<TC>>(2 * (MAXR + 1) * P);
+    cplx<TC>* const stg0 = cv.take<cplx<TC>>(g.ns * (MAXR + 1) * g.pw);
     __shared__ LevelDesc d;
     __shared__ double2 grp[4 * 64];
     __shared__ double2 tot[NVL];
@@ -414,16 +454,10 @@ __global__ void __launch_bounds__(NT, 1) k_fg_lag(const __grid_constant__ KDesc 
     __shared__ cplx<TC> s1c[MAXR], hc[MAXR];
     __shared__ TC ibeta_sh;
     __shared__ int flag;
-    __shared__ alignas(8) uint64_t bars[2];
+    __shared__ alignas(8) uint64_t bars[FG_MAXNS];
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    TmaPipe pipe;
-    pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const long long N = (long long)d.n * d.pitch;
     const int jj = (int)d.fs[FS::J];
-    const int PJ = P * ((MAXR + 1) / (jj + 2));
-    const int nchunks = (int)((N + PJ - 1) / PJ);
-    auto stg = [&](int b, int q) { return stg0 + b * (MAXR + 1) * P + q * PJ; };
     cplx<TC>* vj = kvec<TC>(d, jj);
     cplx<TC>* w = kvec<TC>(d, jj + 1);
     if (PASS == 1) {
@@ -434,35 +468,20 @@ __global__ void __launch_bounds__(NT, 1) k_fg_lag(const __grid_constant__ KDesc 
         if (tid == 0) ibeta_sh = (TC)(1.0 / d.fs[FS::BETA]);
     }
     __syncthreads();
-    auto issue = [&](int k, int b) {
-        if (tid != 0) return;
-        const long long e0 = (long long)k * PJ;
-        const unsigned bytes = (unsigned)(min((long long)PJ, N - e0) * (long long)sizeof(cplx<TC>));
-        pipe.expect(b, bytes * (unsigned)(jj + 2));
-        for (int q = 0; q <= jj; ++q) bulk_load(stg(b, q), kvec<TC>(d, q) + e0, bytes, &bars[b]);
-        bulk_load(stg(b, jj + 1), w + e0, bytes, &bars[b]);
-    };
     cplx<TC> s1[MAXR], s2[MAXR], s3 = zero2<TC>();
 #pragma unroll
     for (int q = 0; q < MAXR; ++q) s1[q] = s2[q] = zero2<TC>();
     TC nv = TC(0), nrm = TC(0);
     const TC ibeta = PASS == 1 ? ibeta_sh : TC(1);
-    int buf = 0;
-    if (c.lb < nchunks) issue(c.lb, 0);
-    for (int k = c.lb; k < nchunks; k += c.nb) {
-        if (k + c.nb < nchunks) issue(k + c.nb, buf ^ 1);
-        if (!pipe.wait(buf, d.err)) return;
-        const long long e0 = (long long)k * PJ;
-        const int cnt = (int)min((long long)PJ, N - e0);
-        const cplx<TC>* sv = stg(buf, 0);
+    const bool ok = fg_stream<TC>(d, c, jj, w, stg0, g, bars,
+                                  [&](const cplx<TC>* sv, int PJ, int cnt, long long e0) {
         fg_dispatch<MAXR>(jj, [&](auto Jc) {
             constexpr int JJ = decltype(Jc)::value;
             if (PASS == 0) fg_lag_dots<TC, JJ>(sv, PJ, cnt, s1, s2, s3, nv, tid);
             else fg_lag_update<TC, JJ>(sv, PJ, cnt, vj + e0, w + e0, s1c, hc, ibeta, nrm, tid);
         });
-        __syncthreads();
-        buf ^= 1;
-    }
+    });
+    if (!ok) return;
     // block sums -> per-block partials -> the last block of the segment
     cplx<TC> red[NVL];
 #pragma unroll

@@ -185,7 +185,25 @@ const SegTable& Handle::seg_outer_chunks(const std::vector<int>& ids, int chunk,
         units.push_back(((long long)d.n * d.pitch + chunk - 1) / chunk);
         t.pts += (long long)d.n * d.n;
     }
-    const std::vector<int> nb = share_blocks(units, cap);
+    // Several segments: when one wave of blocks (cap) leaves the largest
+    // per-block share more than 10% above the mean, the grid is a few waves
+    // of the resident count; blocks of a later wave start as earlier ones
+    // end, so the loads of the SMs even out.
+    long long tot = 0;
+    for (long long u : units) tot += u;
+    int waves = 1;
+    if (ids.size() > 1) {
+        double best = 1e300;
+        for (int m = 1; m <= 4; ++m) {
+            const std::vector<int> nbm = share_blocks(units, m * cap);
+            long long mx = 0;
+            for (size_t q = 0; q < units.size(); ++q) mx = std::max(mx, (units[q] + nbm[q] - 1) / nbm[q]);
+            const double ratio = (double)mx * (double)(m * cap) / (double)std::max(tot, 1LL);
+            if (ratio < best - 1e-9) { best = ratio; waves = m; }
+            if (ratio <= 1.1) break;
+        }
+    }
+    const std::vector<int> nb = share_blocks(units, waves * cap);
     int blk = 0;
     for (size_t q = 0; q < ids.size(); ++q) {
         Seg s;
