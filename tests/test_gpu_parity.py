@@ -276,6 +276,43 @@ def test_batched_uneven_instances_match_single():
     B.mg_destroy(h)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_batched_fgmres_steps_match_single_solves(prec, tol):
+    """25 FGMRES iterations (one restart) of a batch of four instances in one
+    handle against the same iterations of each instance alone.  The sizes
+    (63, 127, 255, 383) make the Gram-Schmidt passes' chunk table take three
+    waves of blocks (one wave would leave the largest block share a third
+    above the mean), so blocks of later waves pick up segments that earlier
+    blocks did not finish.  Only the summation order of the reductions
+    differs between the two runs."""
+    insts = [inst_medium(n, 0.5 * n, seed=50 + n % 7) for n in (63, 127, 255, 383)]
+    K = 25
+
+    def run(group):
+        h = lib_handle(group, prec, n_cmax=15, tol=0.0, maxit=1 << 30)
+        u = np.zeros(sum(I.n * I.n for I in group), dtype=np.complex128)
+        g = np.concatenate([I.g.ravel() for I in group])
+        try:
+            B.mg_solve_begin(h, u, g)
+            B.mg_solve_steps(h, K)
+            B.mg_solve_end(h, u)
+        finally:
+            B.mg_destroy(h)
+        return u
+
+    ub = run(insts)
+    off = 0
+    for I in insts:
+        us = run([I])
+        got = ub[off:off + I.n * I.n]
+        off += I.n * I.n
+        assert np.all(np.isfinite(got))
+        assert rel(got, us) < tol, (I.n, rel(got, us))
+        # the iterations did work: the residual fell well below its start
+        H = oracle_hier(I, n_cmax=15)
+        assert rel(helmholtz_apply(H.lev(1), got.reshape(I.n, I.n)), I.g) < 0.5
+
+
 def test_degenerate_inputs():
     """Zero right-hand side and zero iterate stay zero; GMRES with b = L x
     returns x (r0 = 0)."""
