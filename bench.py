@@ -467,6 +467,26 @@ def run_ours(args):
                     "GBps": r[3] / (r[2] * 1e-3) / 1e9 if r[2] > 0 else None}
                    for r in sorted(recs, key=lambda r: -r[2])[:12]]
 
+    # ---- end to end through the C ABI with pinned host buffers, on the timed handle (M corrections)
+    hg = torch.from_numpy(inst.g).pin_memory()
+    hu = torch.zeros_like(hg).pin_memory()
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps // 4, 20))
+    if e2e_steps:   # one untimed pass (first use of the pinned buffers)
+        B.mg_solve_begin(h, hu, hg, stream=st)
+        B.mg_solve_steps(h, 1, stream=st)
+        B.mg_solve_end(h, hu, stream=st)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.mg_solve_begin(h, hu, hg, stream=st)
+        B.mg_solve_steps(h, 1, stream=st)
+        B.mg_solve_end(h, hu, stream=st)
+    e2e_s = time.perf_counter() - w0
+    e2e = {"value": ws * e2e_steps / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 16,
+           "d2h_bytes_per_step": n * n * 16 + 8,
+           "note": "per step: H2D of u and g (complex128, pinned), FP64 residual, one outer step, "
+                   "D2H of u and the residual norm, all through mg_solve_begin/steps/end"}
+
     # ---- time to tolerance (zero start) on a handle with args.tts_M ADR corrections
     tts = None
     if not args.no_tts:
@@ -484,21 +504,6 @@ def run_ours(args):
                        "first-arrival eikonal phase, in FP64 as well; M=2 converges"}
         h = h2
 
-    # ---- end to end through the C ABI with pinned host buffers
-    hg = torch.from_numpy(inst.g).pin_memory()
-    hu = torch.zeros_like(hg).pin_memory()
-    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps // 4, 20))
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        B.mg_solve_begin(h, hu, hg, stream=st)
-        B.mg_solve_steps(h, 1, stream=st)
-        B.mg_solve_end(h, hu, stream=st)
-    e2e_s = time.perf_counter() - w0
-    e2e = {"value": ws * e2e_steps / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 16,
-           "d2h_bytes_per_step": n * n * 16 + 8,
-           "note": "per step: H2D of u and g (complex128, pinned), FP64 residual, one outer step, "
-                   "D2H of u and the residual norm, all through mg_solve_begin/steps/end"}
     if h is not None:
         B.mg_destroy(h)
 
