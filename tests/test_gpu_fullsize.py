@@ -10,13 +10,11 @@ inputs of the library, widened):
 - one GMRES(3) sweep and one Chebyshev smoothing (q = 5) at level 2: 1e-5;
 - one full Wave-ADR cycle from zero: the per-cycle tolerance 1e-5 of the mixed
   form at n = 1023 (the same recipe, omega scaled to keep k h).  At n = 2047
-  and n = 4095 the measured deviation is 1.1e-5 and 1.2-2.7e-5 (it depends on
-  the tile shapes the autotuner picks, which set the summation order), and
-  the bounds are 5e-5 and 1e-4: the cycle turns the FP32 rounding of the
-  GMRES(3) Gram sums into that deviation.  A complex64 emulation of the
-  oracle cycle at n = 4095 gives 2.4e-5 for FP32 Gram sums, 6.4e-5 for an FP32
-  Arnoldi GMRES(3), and 4.7e-7 only if the products and sums of the rounded
-  vectors were exact (FP64 products on every node);
+  and n = 4095 the measured deviation is up to 1.1e-5 and 1.2-3.8e-5 (it
+  depends on the tile shapes the autotuner picks), and the bounds are 5e-5
+  and 1e-4.  The deviation comes from the FP32 state of the ADR corrections:
+  without them (M = 0) the mixed cycle deviates 1e-7, and each correction
+  adds about 1e-6 at n = 1023; the cycle's amplification grows with n;
 - 25 FGMRES iterations (one restart) through mg_solve_begin/steps/end: the
   relative residual the library reports equals the oracle's FP64 residual of
   the returned iterate to 1e-9 (with M = 8 on this medium the residual
