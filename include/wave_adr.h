@@ -102,7 +102,10 @@ typedef struct mg_params {
     int tail_nmax;          /* ADR levels l >= 3 with n_l <= tail_nmax and everything below them form the
                                coarse tail of an instance, run without per-level launches (see tail_cluster);
                                0 = off; -1 (default): 31 for a handle with one instance and the shared-
-                               memory tail, else 0 (measured fastest on this GPU) */
+                               memory tail, else 0 (measured fastest on this GPU).  The same bound, when
+                               set, selects the wave-cycle levels l >= 4 that run as a shared-memory tail
+                               (Chebyshev smoothing and transfers in one block per instance); -1: n_l <= 63
+                               for one instance, else off */
     int pdl;                /* 1: kernels are launched with programmatic dependent launch (a kernel's
                                descriptor prologue overlaps its predecessor); 0 (default): plain launches
                                (measured 0.1 ms per n=4095 cycle faster on this GPU) */
@@ -221,7 +224,7 @@ int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const 
  * mg_kernel_name gives the kind's name.  mg_step_launches: kernels of one
  * outer step.
  * ---------------------------------------------------------------------- */
-#define MG_KERNEL_KINDS 22
+#define MG_KERNEL_KINDS 23
 int mg_profile_steps(mg_handle* h, int nsteps, double* ms, double* bytes, int* launches, int nkinds,
                      mg_stream stream);
 const char* mg_kernel_name(int kind);

@@ -286,7 +286,7 @@ def mg_abi_sizes():
     return a.value, b.value, c.value
 
 
-MG_KERNEL_KINDS = 22
+MG_KERNEL_KINDS = 23
 
 
 def mg_solve_begin(h, u, g, stream=None):

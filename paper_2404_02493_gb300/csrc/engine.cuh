@@ -20,6 +20,7 @@
 #include "gmres_sstep.cuh"
 #include "tail.cuh"
 #include "tail_smem.cuh"
+#include "tail_wave.cuh"
 #include "setup_kernels.cuh"
 
 namespace wadr {
@@ -445,6 +446,67 @@ struct Engine : EngineBase {
         }, pts);
     }
 
+    // Shared-memory tail of the wave cycle (tail_wave.cuh): opt-in dynamic
+    // shared memory of its two kernels, set once.
+    static long long wt_smem_limit() {
+        static long long lim = -1;
+        if (lim >= 0) return lim;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes a1 = {}, a2 = {};
+        cudaFuncGetAttributes(&a1, k_wave_down<T>);
+        cudaFuncGetAttributes(&a2, k_wave_up<T>);
+        lim = (long long)optin - (long long)std::max(a1.sharedSizeBytes, a2.sharedSizeBytes) - 256;
+        if (lim < 0) lim = 0;
+        cudaFuncSetAttribute(k_wave_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        cudaFuncSetAttribute(k_wave_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        cudaGetLastError();
+        return lim;
+    }
+    // Level l (smoothed, l >= 4, not the coarsest) of instance b starts the
+    // wave tail: n_l within the bound and its vectors fit one block.
+    static bool in_wave_tail(Handle& H, int b, int l) {
+        const int n = H.inst[b].lv[l - 1].n;
+        return l >= 4 && H.inst[b].L > l && n <= H.wave_tail_nmax && n <= WT_MAXN && wt_smem<T>(n) <= wt_smem_limit();
+    }
+    // Down / coarsest / up launches of the wave tail for the instances in
+    // `tail` (their level l is the first tail level).
+    void launch_wave_tail(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
+        const std::vector<int> ds = descs(H, l, tail);
+        const std::string key = "wt" + desc_key(ds);
+        auto it = H.tail_first.find(key);
+        int* dfirst = nullptr;
+        if (it == H.tail_first.end()) {
+            dfirst = (int*)H.alloc(sizeof(int) * ds.size());
+            cudaMemcpy(dfirst, ds.data(), sizeof(int) * ds.size(), cudaMemcpyHostToDevice);
+            H.tail_first[key] = dfirst;
+        } else {
+            dfirst = it->second;
+        }
+        long long sm = 0, pts = 0;
+        for (int b : tail) {
+            sm = std::max(sm, wt_smem<T>(H.inst[b].lv[l - 1].n));
+            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].n;
+        }
+        wt_smem_limit();
+        const unsigned nb = (unsigned)tail.size();
+        const int q = H.p.cheb_iters;
+        // per tail-level point, as the multi-launch kernels count them: q Chebyshev steps (the first from zero,
+        // the last without writing d) and the restriction / the prolongation
+        const double cheb_zero = (C + R + C) + (q - 2) * (5 * C + R) + (4 * C + R);
+        const double cheb_x = (2 * C + R + C) + (q - 2) * (5 * C + R) + (4 * C + R);
+        go(H, st, KK_WAVE_TAIL, (cheb_zero + 2 * C + R + C / 4) * (double)pts, [&] {
+            k_wave_down<T><<<nb, WT_THREADS, (size_t)sm, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst, q);
+        }, pts);
+        std::map<int, std::vector<int>> byL;
+        for (int b : tail) byL[H.inst[b].L].push_back(b);
+        for (auto& g : byL) coarse_solve(H, g.second, g.first, 0, st);
+        go(H, st, KK_WAVE_TAIL, (2 * C + C / 4 + cheb_x) * (double)pts, [&] {
+            k_wave_up<T><<<nb, WT_THREADS, (size_t)sm, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst, q);
+        }, pts);
+    }
+
     void launch_tail(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
         if (H.p.tail_cluster == 0) {
             launch_tail_smem(H, l, tail, st);
@@ -553,6 +615,14 @@ struct Engine : EngineBase {
             }
         }
         if (rest.empty()) return;
+        if (l >= 4 && H.wave_tail_nmax > 0 && H.p.cheb_iters >= 2) {
+            bool all = true;
+            for (int b : rest) all = all && in_wave_tail(H, b, l);
+            if (all) {
+                launch_wave_tail(H, l, rest, st);
+                return;
+            }
+        }
         const std::vector<int> ds = descs(H, l, rest);
         const int q = H.p.cheb_iters;
         const bool smooth = (l != 3);      // no smoothing on level 3 (Section 3.1.3)

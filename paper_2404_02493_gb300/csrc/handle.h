@@ -64,7 +64,7 @@ struct SegTable {
 enum KernelKind : int {
     KK_RESTRICT_JAC0 = 0, KK_RESTRICT_HELM, KK_GS_PRE, KK_PROLONG_JAC, KK_PROLONG_ADD, KK_PROLONG_ADR,
     KK_CHEB, KK_RESDEMOD, KK_GS_GRAM, KK_GS_POST, KK_COARSE, KK_OUTER_RESIDUAL, KK_OUTER_SCALE, KK_OUTER_UPDATE,
-    KK_JACOBI, KK_FG_START, KK_FG_PREP, KK_FG_MATVEC, KK_FG_DOTS, KK_FG_ORTH, KK_FG_UPDATE, KK_ADR_TAIL, KK_COUNT
+    KK_JACOBI, KK_FG_START, KK_FG_PREP, KK_FG_MATVEC, KK_FG_DOTS, KK_FG_ORTH, KK_FG_UPDATE, KK_ADR_TAIL, KK_WAVE_TAIL, KK_COUNT
 };
 const char* kernel_kind_name(int k);
 
@@ -95,6 +95,7 @@ struct Handle {
     std::map<std::string, SegTable> segs;
     std::map<std::string, TileChoice> tiles;  // per ADR launch (desc_key), from the autotuner
     std::map<std::string, int*> tail_first;   // per coarse-tail launch: first-level descriptors (device)
+    int wave_tail_nmax = 0;                    // wave-cycle levels l >= 4 with n_l <= this run as the shared-memory tail
     std::vector<void*> allocs;      // everything cudaMalloc'ed
     long long total_elems = 0;      // sum of n^2 over instances
     // graphs

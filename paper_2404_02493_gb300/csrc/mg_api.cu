@@ -27,7 +27,7 @@ const char* kernel_kind_name(int k) {
         "restrict_jacobi0", "restrict_helmholtz", "gmres_pre_restrict", "prolong_jacobi", "prolong_add",
         "prolong_adr_residual", "chebyshev_step", "residual_demodulate", "gmres_gram", "gmres_post_update",
         "coarse_lu_apply", "outer_residual_fp64", "outer_scale", "outer_update_fp64", "jacobi", "fgmres_start",
-        "fgmres_prep", "fgmres_matvec", "fgmres_dots", "fgmres_orth", "fgmres_update", "adr_tail"};
+        "fgmres_prep", "fgmres_matvec", "fgmres_dots", "fgmres_orth", "fgmres_update", "adr_tail", "wave_tail"};
     return (k >= 0 && k < KK_COUNT) ? names[k] : "unknown";
 }
 
@@ -867,6 +867,9 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     // pays off for a single instance (one block per instance runs those
     // levels); with many instances the per-level launches spread the work
     // over more SMs
+    // the wave-cycle tail (tail_wave.cuh) follows an explicit tail_nmax; automatic: levels with n <= 63 for a
+    // single instance
+    mh->H.wave_tail_nmax = mh->H.p.tail_nmax >= 0 ? mh->H.p.tail_nmax : (ninst == 1 ? 63 : 0);
     if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = (ninst == 1 && mh->H.p.tail_cluster == 0) ? 31 : 0;
     mh->H.prec = p->precision;
     mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();

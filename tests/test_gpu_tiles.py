@@ -121,3 +121,34 @@ def test_coarse_tail_matches_per_level_launches(prec, tol, cluster):
     finally:
         B.mg_destroy(ht)
         B.mg_destroy(hp)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_wave_tail_matches_per_level_launches(prec, tol):
+    """One instance of n = 511 (levels 511 .. 15).  With the default bound
+    the wave levels from n = 63 down (mixed; FP64 from n = 31, since its
+    n = 63 vectors do not fit one block) run as the shared-memory wave tail:
+    Chebyshev smoothing and transfers in one block, the FP64 coarsest solve
+    between.  Against tail_nmax = 0 (one launch per pass) and against the
+    oracle, for two cycles; the tail handle needs fewer launches."""
+    I = _inst(511, 200.0, 34)
+    ht = lib_handle([I], prec, n_cmax=15)
+    hp = lib_handle([I], prec, n_cmax=15, tail_nmax=0)
+    H = oracle_hier(I, n_cmax=15)
+    try:
+        dt = np.complex128 if prec == "fp64" else np.complex64
+        g = (I.g / np.linalg.norm(I.g)).astype(dt)
+        ut, up = np.zeros_like(g), np.zeros_like(g)
+        B.mg_cycle(ht, ut, g, 1)
+        B.mg_cycle(hp, up, g, 1)
+        assert B.mg_cycle_launches(ht) < B.mg_cycle_launches(hp)
+        g64 = g.astype(np.complex128)
+        ref = H.cycle(np.zeros_like(g64), g64)
+        assert rel(ut.astype(np.complex128), ref) < tol, rel(ut, ref)
+        assert rel(ut.astype(np.complex128), up.astype(np.complex128)) < tol
+        B.mg_cycle(ht, ut, g, 1)
+        ref2 = H.cycle(ref, g64)
+        assert rel(ut.astype(np.complex128), ref2) < tol * (10 if prec == "mixed" else 1), rel(ut, ref2)
+    finally:
+        B.mg_destroy(ht)
+        B.mg_destroy(hp)
