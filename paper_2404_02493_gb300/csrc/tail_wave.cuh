@@ -26,7 +26,6 @@
 namespace wadr {
 
 constexpr int WT_THREADS = 1024;
-constexpr int WT_MAXL = 8;
 constexpr int WT_MAXN = 64;   // nodes map to threads as 64 columns x 16 rows
 
 // for (j, i) over an n x n level (n <= WT_MAXN), this thread's nodes
@@ -95,37 +94,15 @@ __device__ void wt_cheb(const LevelDesc& d, int q, bool xzero, cplx<T>* X, const
     }
 }
 
-__device__ __forceinline__ int wt_chain(const LevelDesc* __restrict__ D, const int* __restrict__ first, LevelDesc* Lv,
-                                        int* didx, int* nlev) {
-    if (threadIdx.x == 0) {
-        int di = first[blockIdx.x];
-        int k = 0;
-        while (di >= 0 && k < WT_MAXL) {
-            didx[k++] = di;
-            di = D[di].coarse;
-        }
-        *nlev = k;
-    }
-    __syncthreads();
-    constexpr int W = (int)(sizeof(LevelDesc) / sizeof(unsigned long long));
-    const int nl = *nlev;
-    for (int e = threadIdx.x; e < nl * W; e += blockDim.x) {
-        const int k = e / W, w = e - k * W;
-        reinterpret_cast<unsigned long long*>(&Lv[k])[w] = reinterpret_cast<const unsigned long long*>(D + didx[k])[w];
-    }
-    __syncthreads();
-    return nl;
-}
-
 // ------------------------------------------------------------ down
 template <typename T>
 __global__ void __launch_bounds__(WT_THREADS, 1) k_wave_down(const LevelDesc* __restrict__ D,
                                                              const int* __restrict__ first, int q) {
     extern __shared__ __align__(16) unsigned char wt_smem_raw[];
-    __shared__ LevelDesc Lv[WT_MAXL];
-    __shared__ int didx[WT_MAXL];
+    __shared__ LevelDesc Lv[TS_MAXL];
+    __shared__ int didx[TS_MAXL];
     __shared__ int nlev;
-    const int nl = wt_chain(D, first, Lv, didx, &nlev);
+    const int nl = ts_chain(D, first, Lv, didx, &nlev);
     const int n0 = Lv[0].n, N0 = n0 * n0;
     cplx<T>* X = reinterpret_cast<cplx<T>*>(wt_smem_raw);
     cplx<T>* Dv = X + N0;
@@ -186,10 +163,10 @@ template <typename T>
 __global__ void __launch_bounds__(WT_THREADS, 1) k_wave_up(const LevelDesc* __restrict__ D,
                                                            const int* __restrict__ first, int q) {
     extern __shared__ __align__(16) unsigned char wt_smem_raw[];
-    __shared__ LevelDesc Lv[WT_MAXL];
-    __shared__ int didx[WT_MAXL];
+    __shared__ LevelDesc Lv[TS_MAXL];
+    __shared__ int didx[TS_MAXL];
     __shared__ int nlev;
-    const int nl = wt_chain(D, first, Lv, didx, &nlev);
+    const int nl = ts_chain(D, first, Lv, didx, &nlev);
     const int n0 = Lv[0].n, N0 = n0 * n0;
     cplx<T>* XA = reinterpret_cast<cplx<T>*>(wt_smem_raw);   // x of levels l0, l0+2, ...
     cplx<T>* Dv = XA + N0;
