@@ -104,8 +104,7 @@ typedef struct mg_params {
                                0 = off; -1 (default): 31 for a handle with one instance and the shared-
                                memory tail, else 0 (measured fastest on this GPU).  The same bound, when
                                set, selects the wave-cycle levels l >= 4 that run as a shared-memory tail
-                               (Chebyshev smoothing and transfers in one block per instance); -1: n_l <= 63
-                               for one instance, else off */
+                               (Chebyshev smoothing and transfers in one block per instance); -1: n_l <= 63 */
     int pdl;                /* 1: kernels are launched with programmatic dependent launch (a kernel's
                                descriptor prologue overlaps its predecessor); 0 (default): plain launches
                                (measured 0.1 ms per n=4095 cycle faster on this GPU) */

@@ -867,9 +867,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     // pays off for a single instance (one block per instance runs those
     // levels); with many instances the per-level launches spread the work
     // over more SMs
-    // the wave-cycle tail (tail_wave.cuh) follows an explicit tail_nmax; automatic: levels with n <= 63 for a
-    // single instance
-    mh->H.wave_tail_nmax = mh->H.p.tail_nmax >= 0 ? mh->H.p.tail_nmax : (ninst == 1 ? 63 : 0);
+    // the wave-cycle tail (tail_wave.cuh) follows an explicit tail_nmax; automatic: levels with n <= 63
+    mh->H.wave_tail_nmax = mh->H.p.tail_nmax >= 0 ? mh->H.p.tail_nmax : 63;
     if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = (ninst == 1 && mh->H.p.tail_cluster == 0) ? 31 : 0;
     mh->H.prec = p->precision;
     mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();
