@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from gpu_util import lib_handle, oracle_hier, rel, rnd
+from oracle.cycle import CycleParams, Hierarchy
 from paper_2404_02493_gb300 import binding as B
 import synth
 
@@ -123,21 +124,22 @@ def test_coarse_tail_matches_per_level_launches(prec, tol, cluster):
         B.mg_destroy(hp)
 
 
-@pytest.mark.parametrize("bc", ["abc1", "sponge"])
+@pytest.mark.parametrize("bc,shift", [("abc1", 0.0), ("sponge", 0.0), ("abc1", 0.01)])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
-def test_wave_tail_matches_per_level_launches(prec, tol, bc):
+def test_wave_tail_matches_per_level_launches(prec, tol, bc, shift):
     """One instance of n = 511 (levels 511 .. 15).  With the default bound
     the wave levels from n = 63 down (mixed; FP64 from n = 31, since its
     n = 63 vectors do not fit one block) run as the shared-memory wave tail:
     Chebyshev smoothing and transfers in one block, the FP64 coarsest solve
     between.  Against tail_nmax = 0 (one launch per pass) and against the
     oracle, for two cycles; the tail handle needs fewer launches.  Both
-    boundary closures (the sponge term enters the tail's diagonal)."""
+    boundary closures and the shifted operator (the sponge term and the shift
+    enter the tail's diagonal)."""
     I = _inst(511, 200.0, 34)
     I.bc = bc
-    ht = lib_handle([I], prec, n_cmax=15)
-    hp = lib_handle([I], prec, n_cmax=15, tail_nmax=0)
-    H = oracle_hier(I, n_cmax=15)
+    ht = lib_handle([I], prec, n_cmax=15, shift=shift)
+    hp = lib_handle([I], prec, n_cmax=15, tail_nmax=0, shift=shift)
+    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=15), shift=shift)
     try:
         dt = np.complex128 if prec == "fp64" else np.complex64
         g = (I.g / np.linalg.norm(I.g)).astype(dt)
