@@ -49,3 +49,15 @@ def test_default_params_are_the_papers(lib):
     p = binding.default_params()
     assert (p.jacobi_iters, p.cheb_iters, p.coarse_cheb_iters, p.M, p.restart) == (1, 5, 10, 8, 20)
     assert p.tol == 1e-6 and p.adr == 1 and p.n_cmax == 15 and p.outer == binding.MG_OUTER['fgmres']
+
+
+def test_kernel_kind_table_matches_the_header(lib):
+    """MG_KERNEL_KINDS in the header and the binding, and one name per kind
+    in the library (host-side lookup only)."""
+    m = re.search(r"#define\s+MG_KERNEL_KINDS\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == binding.MG_KERNEL_KINDS
+    lib.mg_kernel_name.restype = ctypes.c_char_p
+    names = [lib.mg_kernel_name(k).decode() for k in range(binding.MG_KERNEL_KINDS)]
+    assert "unknown" not in names and len(set(names)) == len(names), names
+    assert lib.mg_kernel_name(binding.MG_KERNEL_KINDS).decode() == "unknown"
+    assert {"gmres_gram", "chebyshev_step", "adr_tail", "wave_tail", "fgmres_dots"} <= set(names)
