@@ -36,7 +36,7 @@ tests/test_oracle_*.py against closed forms, printed values, brute force or
 library routines (see each test's docstring).
 """
 from .operators import (Level, helmholtz_apply, helmholtz_apply_h, helmholtz_diag,
-                        helmholtz_residual, adr_coefficients, adr_apply,
+                        helmholtz_residual, adr_coefficients, adr_apply, peclet_number,
                         adr_apply_t, restrict, prolong, sponge_gamma)
 from .smoothers import (jacobi, chebyshev, chebyshev_product, lambda_max_gershgorin,
                         alpha_spectral, alpha_spectral_1d, jacobi_weight_default,
@@ -46,7 +46,7 @@ from .solve import solve_stationary, solve_ir, solve_fgmres
 
 __all__ = [
     "Level", "helmholtz_apply", "helmholtz_apply_h", "helmholtz_diag",
-    "helmholtz_residual", "adr_coefficients", "adr_apply", "adr_apply_t",
+    "helmholtz_residual", "adr_coefficients", "peclet_number", "adr_apply", "adr_apply_t",
     "restrict", "prolong", "sponge_gamma", "jacobi", "chebyshev",
     "chebyshev_product", "lambda_max_gershgorin", "alpha_spectral",
     "alpha_spectral_1d", "jacobi_weight_default", "gmres", "Hierarchy",

@@ -7,6 +7,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from .operators import (Level, adr_apply, adr_coefficients, coarse_size,
                         helmholtz_apply, helmholtz_diag, inject, prolong, restrict,
@@ -33,6 +34,9 @@ class CycleParams:
     omega_jacobi: float | None = None      # None: (4-kappa)/(5-kappa)
     alphas: dict = field(default_factory=dict)  # level -> alpha; missing: spectral
     ray: bool = False              # Wave-Ray: correction m uses the plane-wave phase of direction m
+    adr_bc: str = "zero"           # ADR boundary closure: "zero" ghost | "abc" (absorbing, carried through)
+    adr_scheme: str = "upwind"     # ADR convection: "upwind" (eq. upwind) | "central" (Fig. discremethod)
+    adr_solver: str = "vcycle"     # ADR system: one V-cycle (Section 3.2.2) | "direct" (Fig. discremethod)
 
 
 def build_sizes(n: int, n_cmax: int):
@@ -69,9 +73,9 @@ def helmholtz_sparse(lev: Level) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(n * n, n * n), dtype=np.complex128)
 
 
-def adr_sparse(lev: Level) -> sp.csr_matrix:
-    """Assembly of the upwind ADR matrix from its coefficients."""
-    c = adr_coefficients(lev)
+def adr_sparse(lev: Level, closure: str = "zero", scheme: str = "upwind") -> sp.csr_matrix:
+    """Assembly of the ADR matrix from its coefficients."""
+    c = adr_coefficients(lev, closure, scheme)
     n = lev.n
     rows, cols, vals = [], [], []
     for j in range(n):
@@ -138,11 +142,14 @@ class Hierarchy:
                     if l > 1:
                         pl = inject(pl)
                     levs.append(dataclasses.replace(self.levels[l - 1], phi=pl))
-                coefs = {l: adr_coefficients(levs[l - 1]) for l in range(2, self.L + 1)}
+                pa = self.p
+                coefs = {l: adr_coefficients(levs[l - 1], pa.adr_bc, pa.adr_scheme) for l in range(2, self.L + 1)}
                 mod = np.exp(1j * conv * omega * levs[1].phi)   # e^{+i conv w phi_2}
-                lu = scipy.linalg.lu_factor(adr_sparse(levs[-1]).toarray())
-                self.adr_sets.append((coefs, mod, lu))
-            self.adr, self.mod, self.lu_adr = self.adr_sets[0]
+                lu = scipy.linalg.lu_factor(adr_sparse(levs[-1], pa.adr_bc, pa.adr_scheme).toarray())
+                direct = (spla.splu(adr_sparse(levs[1], pa.adr_bc, pa.adr_scheme).tocsc())
+                          if pa.adr_solver == "direct" else None)
+                self.adr_sets.append((coefs, mod, lu, direct))
+            self.adr, self.mod, self.lu_adr = self.adr_sets[0][:3]
 
     # ------------------------------------------------------------ roles
     def _uses_cheb(self, l: int) -> bool:
@@ -176,7 +183,9 @@ class Hierarchy:
         from level l down to L, one GMRES(3) sweep before and after the
         coarse-grid correction, exact solve on the coarsest level.  m: the
         ADR set (Wave-Ray direction)."""
-        coefs, _, lu = self.adr_sets[m]
+        coefs, _, lu, direct = self.adr_sets[m]
+        if direct is not None and l == 2:
+            return direct.solve(b.ravel()).reshape(b.shape)
         if l == self.L:
             return scipy.linalg.lu_solve(lu, b.ravel()).reshape(b.shape)
         c = coefs[l]

@@ -131,7 +131,7 @@ def phase_derivatives(phi: np.ndarray, h: float):
     return phix, phiy, lap
 
 
-def adr_coefficients(lev: Level) -> ADRCoefficients:
+def adr_coefficients(lev: Level, closure: str = "zero", scheme: str = "upwind") -> ADRCoefficients:
     """Discrete ADR operator obtained by substituting v = a exp(i conv w phi)
     into the Helmholtz equation (eq. Rytov, eq. ADR):
 
@@ -143,10 +143,26 @@ def adr_coefficients(lev: Level) -> ADRCoefficients:
     eq. upwind, whose 5-point form (Section 3.3) is
       (1/2h)[ 2(|px|+|py|) a_c + (-px-|px|) a_W + (px-|px|) a_E
               + (-py-|py|) a_S + (py-|py|) a_N ].
-    The ADR unknown has a zero ghost (Dirichlet) on every side."""
+    scheme="central" replaces the upwind convection by the central
+    difference (1/2h)[px (a_E - a_W) + py (a_N - a_S)], the discretisation
+    Section 3.2.2 compares against (Fig. discremethod).
+    Boundary closure of the ADR unknown (the paper states none):
+      closure="zero": zero ghost a_g = 0 on every side;
+      closure="abc" (first-order absorbing Helmholtz boundary only): the
+        Helmholtz ghost u_g = (1 + i conv k h) u_b written for
+        u = a exp(i conv w phi), with the ghost phase extrapolated linearly as
+        for the derivatives: a_g = (1 + i conv k h)
+        exp(-i conv w (phi_b - phi_in)) a_b; the ghost term enters the
+        diagonal of the boundary node.  Other boundaries keep the zero ghost
+        (u = 0 on the boundary gives a = 0)."""
     h, w = lev.h, lev.omega
     phix, phiy, lap = phase_derivatives(lev.phi, h)
-    ax, ay = np.abs(phix), np.abs(phiy)
+    if scheme == "upwind":
+        ax, ay = np.abs(phix), np.abs(phiy)
+    elif scheme == "central":
+        ax, ay = np.zeros_like(phix), np.zeros_like(phiy)   # no one-sided part
+    else:
+        raise ValueError(scheme)
     s2 = (lev.k / w) ** 2
     ic = 1j * lev.conv
     d = (4.0 / (h * h) - ic * 2 * w * (ax + ay) / h - ic * w * lap
@@ -160,8 +176,32 @@ def adr_coefficients(lev: Level) -> ADRCoefficients:
     cE = -inv_h2 - ic * w * (phix - ax) / h
     cS = -inv_h2 + ic * w * (phiy + ay) / h
     cN = -inv_h2 - ic * w * (phiy - ay) / h
+    if closure == "abc" and lev.bc == "abc1":
+        phi, k = lev.phi, lev.k
+        d = d.copy()
+
+        def ghost(sl, coef, inner):
+            rho = (1.0 + ic * k[sl] * h) * np.exp(-ic * w * (phi[sl] - phi[inner]))
+            d[sl] += coef[sl] * rho
+
+        ghost((slice(None), 0), cW, (slice(None), 1))      # west ghost, inner neighbour i = 1
+        ghost((slice(None), -1), cE, (slice(None), -2))
+        ghost((0, slice(None)), cS, (1, slice(None)))
+        ghost((-1, slice(None)), cN, (-2, slice(None)))
+    elif closure not in ("zero", "abc"):
+        raise ValueError(closure)
     return ADRCoefficients(d=d, cW=cW, cE=cE, cS=cS, cN=cN, phix=phix, phiy=phiy,
                            lap=lap)
+
+
+def peclet_number(lev: Level) -> float:
+    """Peclet number of the ADR operator on a level (Section 3.2.2: the
+    central-difference ADR discretisation needs
+    2 omega h max(|phi_x|, |phi_y|) <= 2): the maximum over nodes of
+    omega h max(|phi_x|, |phi_y|), with the phase derivatives of the ADR
+    coefficients.  The condition holds where the value is <= 1."""
+    phix, phiy, _ = phase_derivatives(lev.phi, lev.h)
+    return float(lev.omega * lev.h * np.max(np.maximum(np.abs(phix), np.abs(phiy))))
 
 
 def adr_apply(c: ADRCoefficients, a: np.ndarray) -> np.ndarray:

@@ -526,3 +526,26 @@ def test_wave_ray_single_direction_is_wave_adr_with_phase_x():
     Ha = Hierarchy(I.n, I.k, 1.0 * X, I.omega, I.bc, CycleParams(n_cmax=7, M=1, ray=False))
     u = np.zeros_like(I.g)
     assert np.array_equal(Hr.cycle(u, I.g), Ha.cycle(u, I.g))
+
+
+def test_peclet_number_closed_form():
+    """Peclet number (Section 3.2.2): for phi = |x - x0| with the source on a
+    node, the row through the source is linear in x, so its central (and
+    extrapolated one-sided) differences are exactly +-1 and
+    max(|phi_x|, |phi_y|) = 1: the Peclet number is omega h.  At the level
+    with omega h ~ 1 (the paper's ADR level) the condition holds; on the
+    next coarser level it fails, which is why the paper uses upwinding."""
+    from oracle.operators import Level, peclet_number
+    n = 255
+    omega = 0.98 * (n + 1) / 2          # omega h = 0.98 on the level of 127 nodes
+    for nl in (127, 63, 31):
+        h = 1.0 / (nl + 1)
+        x = (np.arange(nl) + 1) * h
+        X, Y = np.meshgrid(x, x, indexing="xy")
+        lev = Level(n=nl, h=h, k=np.full((nl, nl), omega), phi=np.hypot(X - 0.5, Y - 0.5),
+                    gamma=np.zeros((nl, nl)), omega=omega, bc="abc1")
+        assert abs(peclet_number(lev) - omega * h) < 1e-12 * omega * h
+    lev2 = Level(n=127, h=1 / 128, k=np.full((127, 127), omega),
+                 phi=np.hypot(*[g - 0.5 for g in np.meshgrid((np.arange(127) + 1) / 128, (np.arange(127) + 1) / 128)]),
+                 gamma=np.zeros((127, 127)), omega=omega, bc="abc1")
+    assert peclet_number(lev2) <= 1.0
