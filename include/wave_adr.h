@@ -68,6 +68,8 @@ enum { MG_BC_DIRICHLET = 0, MG_BC_ABC1 = 1, MG_BC_SPONGE = 2 };
 enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 };
 enum { MG_OUTER_STATIONARY = 0, MG_OUTER_IR = 1, MG_OUTER_FGMRES = 2 };
 enum { MG_COARSE_LU = 0, MG_COARSE_CHEB = 1 };
+/* Boundary closure of the ADR unknown a (the paper states none; see mg_params.adr_bc). */
+enum { MG_ADR_BC_ZERO = 0, MG_ADR_BC_ABC = 1 };
 
 #define MG_MAX_LEVELS 16
 #define MG_TILE_CANDIDATES 5   /* halo-tile shape candidates per ADR GMRES kernel */
@@ -123,6 +125,14 @@ typedef struct mg_params {
                                (projection, re-orthogonalisation, norm); 2 (default) = the same CGS2 with the
                                re-orthogonalisation of each new basis vector done in the next iteration's passes
                                (one pass over all Krylov vectors less per iteration) */
+    int adr_bc;             /* MG_ADR_BC_ZERO (default): zero ghost of the ADR unknown on every side;
+                               MG_ADR_BC_ABC: for MG_BC_ABC1 instances, the absorbing condition of the Helmholtz
+                               problem carried through v = a exp(i omega phi): ghost a_g = (1 + i k h)
+                               exp(-i omega (phi_b - phi_in)) a_b, phi_in the inner neighbour (other boundary
+                               kinds keep the zero ghost, which is what u = 0 on the boundary gives) */
+    long long workspace_limit; /* 0 (default): none; > 0: mg_setup fails with MG_ENOMEM, freeing what it
+                               had allocated, when the handle's device workspace would exceed this many bytes
+                               (for callers that share the GPU; mg_workspace_bytes reports the size) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */
@@ -196,6 +206,11 @@ int mg_solve_end(mg_handle* h, void* u, double* rel_residual, mg_stream stream);
 /* Free the workspace. */
 void mg_destroy(mg_handle* h);
 
+/* Bytes of device memory the handle's workspace holds (levels, coefficient
+ * fields, coarsest-level inverses, Krylov vectors, scalars), or MG_EINVAL
+ * for a null handle.  Needs no synchronisation. */
+long long mg_workspace_bytes(const mg_handle* h);
+
 /* Adjoint of K cycles from u0 (Section 3.3 trains through K cycles with the
  * loss eq. loss; Algorithm 2 back-propagates through them).  For the map
  * u_K = cycle^K(u0, g) with the handle's phi and smoother weights, and a
@@ -241,13 +256,37 @@ int mg_profile_records(mg_handle* h, int nsteps, int* kind, long long* pts, doub
  * 1-based.  Synchronous with respect to `stream` only through copies.
  * ---------------------------------------------------------------------- */
 
+/* Level roles (Algorithm 1): MG_ROLE_JACOBI (level 1: damped Jacobi),
+ * MG_ROLE_CHEB_ADR (level 2: Chebyshev, then the M ADR corrections),
+ * MG_ROLE_NONE (level 3: no smoothing, Section 3.1.3), MG_ROLE_CHEB (levels
+ * >= 4: Chebyshev), MG_ROLE_COARSE_LU / MG_ROLE_COARSE_CHEB (level L: dense
+ * FP64 LU, or Algorithm 1's q = 10 Chebyshev steps). */
+enum { MG_ROLE_JACOBI = 0, MG_ROLE_CHEB = 1, MG_ROLE_NONE = 2, MG_ROLE_CHEB_ADR = 3, MG_ROLE_COARSE_LU = 4,
+       MG_ROLE_COARSE_CHEB = 5 };
+/* The hierarchy mg_setup builds for an n x n instance with the schedule p,
+ * without a handle or a GPU: writes n_l to sizes[l-1] and the role of level
+ * l to roles[l-1] for l = 1..min(L, maxl) and returns L (or MG_EINVAL).  The
+ * coarsest level's role takes precedence (for L <= 3). */
+int mg_level_roles(int n, const mg_params* p, int* sizes, int* roles, int maxl);
+
 /* Number of levels L of an instance (Algorithm 1's max-level). */
 int mg_num_levels(const mg_handle* h, int inst);
 /* n_l of level `level`. */
 int mg_level_n(const mg_handle* h, int inst, int level);
 /* Setup scalars of a level: out[0] = lambda_max (Gershgorin bound of A^*A),
- * out[1] = alpha, out[2] = Jacobi weight, out[3] = h.  Returns count. */
+ * out[1] = alpha, out[2] = Jacobi weight, out[3] = h, out[4] = Peclet
+ * number omega h max(|phi_x|, |phi_y|) of the ADR operator (0 on levels
+ * without one).  Writes min(nout, 5) values and returns that count. */
 int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int nout);
+
+/* Peclet warning flags (Section 3.2.2: a central-difference ADR
+ * discretisation needs 2 omega h max(|phi_x|, |phi_y|) <= 2; the paper uses
+ * the upwind stencil because coarse levels violate it).  Bit l-1 is set when
+ * ADR level l violates the condition, i.e. its Peclet number (the maximum
+ * over nodes of omega h max(|phi_x|, |phi_y|), phase derivatives as in the
+ * ADR coefficients) exceeds 1.  Informational: the upwind operator is used
+ * on every level regardless.  Returns the bit mask (>= 0) or MG_EINVAL. */
+int mg_peclet_flags(const mg_handle* h, int inst);
 
 enum { MG_OP_A = 0, MG_OP_AH = 1, MG_OP_L = 2, MG_OP_LT = 3, MG_OP_LH = 4 };
 /* y = op(x): A (5-point Helmholtz, Section 2), A^* (eq. cheb), L (upwind ADR
@@ -312,10 +351,13 @@ int mg_selftest_wait_timeout(mg_stream stream);
  * allocator, or a latency-bound loop that must not pay for cudaMalloc /
  * cudaFree (which can synchronise the device).  It needs no handle.
  *
- * Computes r = g - A u (the FP64 5-point Helmholtz operator of Section 2 on
- * an n x n grid, h = 1/(n+1), boundary `bc`; the sponge term, if any, is
- * evaluated from the node position with the reference frequency `omega`)
- * and writes ||r||^2 to *norm2.  k (FP64), u, g, r (complex128) and norm2
+ * Computes r = g - A u, A the FP64 5-point Helmholtz operator on an n x n
+ * grid: h = 1/(n+1), diagonal (4 - h^2 k^2)/h^2 and -1/h^2 to each in-grid
+ * neighbour; boundary `bc`: MG_BC_DIRICHLET (zero ghosts), MG_BC_ABC1 (ghost
+ * (1 + i k h) u_b per missing neighbour, folded into the diagonal) or
+ * MG_BC_SPONGE (zero ghosts plus the damping term -i omega gamma s^2, gamma
+ * evaluated from the node position with the reference frequency `omega`,
+ * the same profile as mg_setup uses), and writes ||r||^2 to *norm2.  k (FP64), u, g, r (complex128) and norm2
  * are DEVICE pointers, dense row-major; the call is asynchronous on
  * `stream`.
  *
@@ -324,8 +366,11 @@ int mg_selftest_wait_timeout(mg_stream stream);
  * loads the library until the process exits).  The grid size does not
  * change the scratch; n must be in 1..32768 (MG_EINVAL otherwise).  The
  * first call on each device looks up the scratch's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call reuses the same scratch and
+ * (cudaGetSymbolAddress) with that device current and keeps it for later
+ * calls; make that first call before any stream capture.  The kept address
+ * belongs to the device's current context: a caller that destroys that
+ * context (cudaDeviceReset) must not call this entry point again in the
+ * same process.  Every call reuses the same scratch and
  * clears its counter first, so two calls that overlap on the GPU (for
  * example on two streams) race and must be ordered by the caller. */
 int mg_residual_norm_noalloc(int n, double omega, const double* k, int bc, const void* u, const void* g, void* r,

@@ -16,33 +16,43 @@ import torch
 from . import binding as B
 
 
-def chebyshev_levels(n: int, n_cmax: int = 15, coarse: str = "lu"):
-    """Levels that carry a Chebyshev smoother (2 and >= 4, not the coarsest
-    unless the coarsest level uses Chebyshev)."""
-    sizes = [n]
-    while sizes[-1] > n_cmax:
-        sizes.append(sizes[-1] // 2)
-    L = len(sizes)
-    out = []
-    for l in range(2, L + 1):
-        if l == L:
-            if coarse == "cheb":
-                out.append(l)
-        elif l != 3:
-            out.append(l)
-    return out
+def chebyshev_levels(n: int, params: dict):
+    """Levels that carry a Chebyshev smoother, as the library's hierarchy
+    (mg_level_roles) assigns them for this size and schedule."""
+    p = B.default_params(precision="fp64", **params)
+    roles = B.mg_level_roles(n, p)
+    return [l for l, (_, r) in enumerate(roles, start=1) if r in ("cheb", "cheb_adr", "coarse_cheb")]
+
+
+class _Handle:
+    """Owns a library handle until backward runs or the graph is freed."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def release(self):
+        if self.h is not None:
+            B.mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.release()
 
 
 class _Cycles(torch.autograd.Function):
     @staticmethod
     def forward(ctx, phi, weights, u0, g, n, omega, k, bc, K, params):
-        levels = chebyshev_levels(n, params.get("n_cmax", 15), params.get("coarse", "lu"))
+        params = dict(params)
+        params.setdefault("autotune", 0)   # the FP64 cycle's tiles need no tuning per call
+        levels = chebyshev_levels(n, params)
         w = weights.detach().cpu().numpy()
         alpha = {l: float(w[1 + i]) for i, l in enumerate(levels)}
         p = B.default_params(precision="fp64", omega_jacobi=float(w[0]), alpha=alpha, **params)
-        h = B.mg_setup([(n, omega, k.detach().contiguous(), phi.detach().contiguous(), bc)], p)
+        # phi and the weights enter the setup (ADR coefficients, Chebyshev
+        # intervals), so every forward builds its own handle
+        h = _Handle(B.mg_setup([(n, omega, k.detach().contiguous(), phi.detach().contiguous(), bc)], p))
         u = u0.detach().clone().contiguous()
-        B.mg_cycle(h, u, g.detach().contiguous(), K)
+        B.mg_cycle(h.h, u, g.detach().contiguous(), K)
         torch.cuda.synchronize(u.device)
         ctx.h = h
         ctx.K = K
@@ -57,10 +67,9 @@ class _Cycles(torch.autograd.Function):
         gw = np.zeros(B.MG_MAX_LEVELS)
         gu0 = torch.zeros_like(u0)
         try:
-            B.mg_cycle_backward(ctx.h, u0, g, ctx.K, grad_uK.contiguous(), gphi, gw, gu0)
+            B.mg_cycle_backward(ctx.h.h, u0, g, ctx.K, grad_uK.contiguous(), gphi, gw, gu0)
         finally:
-            B.mg_destroy(ctx.h)
-            ctx.h = None
+            ctx.h.release()
         gweights = torch.tensor([gw[0]] + [gw[l - 1] for l in ctx.levels], dtype=torch.float64,
                                 device=phi.device)
         return gphi, gweights, gu0, None, None, None, None, None, None, None

@@ -21,6 +21,8 @@ MG_BC = {"dirichlet": 0, "abc1": 1, "sponge": 2}
 MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_OUTER = {"stationary": 0, "ir": 1, "fgmres": 2}
 MG_COARSE_LU, MG_COARSE_CHEB = 0, 1
+MG_ADR_BC = {"zero": 0, "abc": 1}
+MG_ROLE = {0: "jacobi", 1: "cheb", 2: "none", 3: "cheb_adr", 4: "coarse_lu", 5: "coarse_cheb"}
 MG_OP = {"A": 0, "AH": 1, "L": 2, "LT": 3, "LH": 4}
 MG_MAX_LEVELS = 16
 MG_TILE_CANDIDATES = 5
@@ -35,7 +37,7 @@ class MgParams(ctypes.Structure):
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("shift", ctypes.c_double),
         ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("tile_candidate", ctypes.c_int),
         ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int), ("tail_cluster", ctypes.c_int), ("ray", ctypes.c_int),
-        ("fgmres_passes", ctypes.c_int),
+        ("fgmres_passes", ctypes.c_int), ("adr_bc", ctypes.c_int), ("workspace_limit", ctypes.c_longlong),
     ]
 
 
@@ -96,6 +98,9 @@ def load():
         "mg_cycle_backward": (ip, [vp, vp, vp, ip, vp, vp, vp, vp, vp]),
         "mg_tile_shapes": (ip, [vp, ip, ip, ctypes.POINTER(ip)]),
         "mg_selftest_wait_timeout": (ip, [vp]),
+        "mg_peclet_flags": (ip, [vp, ip]),
+        "mg_workspace_bytes": (ctypes.c_longlong, [vp]),
+        "mg_level_roles": (ip, [ip, ctypes.POINTER(MgParams), ctypes.POINTER(ip), ctypes.POINTER(ip), ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -113,7 +118,8 @@ def exported_symbols():
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
             "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
-            "mg_tile_shapes", "mg_selftest_wait_timeout"]
+            "mg_tile_shapes", "mg_selftest_wait_timeout", "mg_peclet_flags",
+            "mg_workspace_bytes", "mg_level_roles"]
 
 
 class MgError(RuntimeError):
@@ -163,6 +169,8 @@ def default_params(**kw) -> MgParams:
             p.precision = {"fp64": MG_PREC_FP64, "mixed": MG_PREC_MIXED}[v]
         elif k == "outer" and isinstance(v, str):
             p.outer = MG_OUTER[v]
+        elif k == "adr_bc" and isinstance(v, str):
+            p.adr_bc = MG_ADR_BC[v]
         elif k == "coarse" and isinstance(v, str):
             p.coarse = {"lu": MG_COARSE_LU, "cheb": MG_COARSE_CHEB}[v]
         else:
@@ -221,9 +229,35 @@ def mg_level_n(h, inst, level):
 
 
 def mg_level_scalars(h, inst, level):
-    out = (ctypes.c_double * 4)()
-    load().mg_level_scalars(h, inst, level, out, 4)
-    return {"lam_max": out[0], "alpha": out[1], "omega_j": out[2], "h": out[3]}
+    out = (ctypes.c_double * 5)()
+    r = load().mg_level_scalars(h, inst, level, out, 5)
+    if r < 0:
+        _check(r, "mg_level_scalars")
+    return {"lam_max": out[0], "alpha": out[1], "omega_j": out[2], "h": out[3], "peclet": out[4]}
+
+
+def mg_level_roles(n, params: MgParams):
+    """[(n_l, role name)] for l = 1..L of the hierarchy mg_setup builds (no GPU needed)."""
+    sizes, roles = (ctypes.c_int * MG_MAX_LEVELS)(), (ctypes.c_int * MG_MAX_LEVELS)()
+    L = load().mg_level_roles(int(n), ctypes.byref(params), sizes, roles, MG_MAX_LEVELS)
+    if L < 0:
+        _check(L, "mg_level_roles")
+    return [(sizes[l], MG_ROLE[roles[l]]) for l in range(min(L, MG_MAX_LEVELS))]
+
+
+def mg_workspace_bytes(h):
+    r = load().mg_workspace_bytes(h)
+    if r < 0:
+        _check(int(r), "mg_workspace_bytes")
+    return r
+
+
+def mg_peclet_flags(h, inst=0):
+    """Bit l-1 set: ADR level l violates the Peclet condition (Section 3.2.2)."""
+    r = load().mg_peclet_flags(h, inst)
+    if r < 0:
+        _check(r, "mg_peclet_flags")
+    return r
 
 
 def mg_tile_shapes(h, inst, level):

@@ -965,6 +965,11 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
     if (H.prec != MG_PREC_FP64) { set_error("mg_cycle_backward: the adjoint needs an FP64 handle"); return MG_EUNSUPPORTED; }
     if (H.p.coarse != MG_COARSE_LU) { set_error("mg_cycle_backward: coarsest level must be the dense LU"); return MG_EUNSUPPORTED; }
     if (H.p.ray) { set_error("mg_cycle_backward: not available for Wave-Ray handles (no phase input)"); return MG_EUNSUPPORTED; }
+    for (const InstHost& I : H.inst)
+        if (I.adr_abc) {
+            set_error("mg_cycle_backward: not available with the absorbing ADR boundary closure (MG_ADR_BC_ABC)");
+            return MG_EUNSUPPORTED;
+        }
     cudaStream_t st = (cudaStream_t)stream;
     const int ni = (int)H.inst.size();
     auto cp2d = [&](void* dst, size_t dpitch, const void* src, size_t spitch, int n) {

@@ -31,12 +31,14 @@ struct LevelHost {
     double2* inv_helm = nullptr;    // coarsest only
     double2* inv_adr = nullptr;
     double lam_max = 0, alpha = 0;  // Chebyshev interval (levels with Chebyshev)
+    double peclet = 0;              // ADR levels: omega h max(|phi_x|, |phi_y|) (condition: <= 1)
     int cheb = 0;                   // uses Chebyshev smoothing
     int desc = -1;                  // index in the cycle descriptor table
 };
 
 struct InstHost {
     int n = 0, L = 0, bc = 0;
+    int adr_abc = 0;                // ADR boundary closure (1: absorbing condition carried through, see adr_coef_at)
     double omega = 0;
     double omega_j = 0;
     std::vector<LevelHost> lv;      // lv[0] = level 1
@@ -97,6 +99,8 @@ struct Handle {
     std::map<std::string, int*> tail_first;   // per coarse-tail launch: first-level descriptors (device)
     int wave_tail_nmax = 0;                    // wave-cycle levels l >= 4 with n_l <= this run as the shared-memory tail
     std::vector<void*> allocs;      // everything cudaMalloc'ed
+    size_t alloc_bytes = 0;         // their total size
+    long long alloc_limit = 0;      // mg_params.workspace_limit (0: none)
     long long total_elems = 0;      // sum of n^2 over instances
     // graphs
     cudaGraphExec_t g_cycle0 = nullptr;     // cycle from u = 0 (level-1 SG -> SD)
@@ -164,9 +168,13 @@ void setup_inject(const double* k_fine, const double* phi_fine, int n1, double o
 double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
                         double* dscratch, cudaStream_t st);
 double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                       double omega, int bc, double shift, double* dscratch, cudaStream_t st);
+                       double omega, int bc, double shift, int adr_abc, double* dscratch, cudaStream_t st);
+int setup_check_fields(const double* k, const double* phi, int n, double* dscratch, long long* bad_k,
+                       long long* bad_phi, cudaStream_t st);
+double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                    double omega, int bc, double* dscratch, cudaStream_t st);
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, double shift, int which, double2* inv, cudaStream_t st);
+                         double omega, int bc, double shift, int which, int adr_abc, double2* inv, cudaStream_t st);
 
 #define WADR_CHECK(x)                                                                   \
     do {                                                                                \

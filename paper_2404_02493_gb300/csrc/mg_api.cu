@@ -50,8 +50,10 @@ void prof_end(Handle& H, cudaStream_t st, int kind, double bytes, long long pts)
 void* Handle::alloc(size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (alloc_limit > 0 && alloc_bytes + bytes > (size_t)alloc_limit) return nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
     allocs.push_back(p);
+    alloc_bytes += bytes;
     return p;
 }
 
@@ -371,6 +373,25 @@ static int build_tmaps_desc(const LevelDesc& d, int nslot, int prec, CUtensorMap
     return MG_OK;
 }
 
+// Level sizes of an instance (Algorithm 1's hierarchy): coarse node I on fine
+// node 2I+1, n_{l+1} = floor(n_l / 2), coarsened while n_l > n_cmax.
+static std::vector<int> level_sizes(int n, int n_cmax) {
+    std::vector<int> sizes{n};
+    while (sizes.back() > n_cmax && sizes.back() / 2 >= 1) sizes.push_back(sizes.back() / 2);
+    return sizes;
+}
+
+// Role of level l of L (Algorithm 1): Jacobi on level 1, Chebyshev with the
+// ADR corrections on level 2, nothing on level 3, Chebyshev below, the
+// coarsest-level solve on level L (which takes precedence).
+static int level_role(int l, int L, const mg_params& p) {
+    if (l == L) return p.coarse == MG_COARSE_CHEB ? MG_ROLE_COARSE_CHEB : MG_ROLE_COARSE_LU;
+    if (l == 1) return MG_ROLE_JACOBI;
+    if (l == 3) return MG_ROLE_NONE;
+    if (l == 2 && p.adr && p.M > 0 && L >= 3) return MG_ROLE_CHEB_ADR;
+    return MG_ROLE_CHEB;
+}
+
 static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t st) {
     Handle& H = mh->H;
     const mg_params& p = H.p;
@@ -383,10 +404,10 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         I.n = in[b].n;
         I.omega = in[b].omega;
         I.bc = in[b].bc;
+        I.adr_abc = (p.adr_bc == MG_ADR_BC_ABC && I.bc == MG_BC_ABC1) ? 1 : 0;
         I.off = off;
         off += (long long)I.n * I.n;
-        std::vector<int> sizes{I.n};
-        while (sizes.back() > p.n_cmax && sizes.back() / 2 >= 1) sizes.push_back(sizes.back() / 2);
+        const std::vector<int> sizes = level_sizes(I.n, p.n_cmax);
         I.L = (int)sizes.size();
         if (I.L < 2) { set_error("mg_setup: n must exceed n_cmax"); return MG_EINVAL; }
         if (I.L > MG_MAX_LEVELS) { set_error("mg_setup: too many levels"); return MG_EINVAL; }
@@ -465,6 +486,19 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         }
     }
     H.total_elems = off;
+    // --- input validation: k finite and positive, phi finite
+    double* vscr = (double*)H.alloc(64);
+    if (!vscr) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
+    for (int b = 0; b < ninst; ++b) {
+        long long bad_k = 0, bad_phi = 0;
+        int rc = setup_check_fields(in[b].k, in[b].phi, in[b].n, vscr, &bad_k, &bad_phi, st);
+        if (rc) return rc;
+        if (bad_k || bad_phi) {
+            set_error("mg_setup: instance " + std::to_string(b) + ": " + std::to_string(bad_k) +
+                      " nodes with k not finite and positive, " + std::to_string(bad_phi) + " nodes with phi not finite");
+            return MG_EINVAL;
+        }
+    }
     // --- FP64 fields by injection
     for (int b = 0; b < ninst; ++b) {
         InstHost& I = H.inst[b];
@@ -534,8 +568,9 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.fshift = (float)d.shift;
             d.has_shift = d.shift != 0.0;
             d.gs = lv.adr ? setup_adr_scale(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
-                                            dscr, st)
+                                            I.adr_abc, dscr, st)
                           : 1.0;
+            if (lv.adr) lv.peclet = setup_peclet(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, dscr, st);
             d.fgs = (float)d.gs;
             d.bc = I.bc;
             d.inst = b;
@@ -555,7 +590,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 I.omega_j = p.omega_jacobi > 0 ? p.omega_jacobi : jacobi_default(lv.h, kmax);
                 s[S::OMEGA_J] = I.omega_j;
             }
-            const bool cheb = (l >= 2) && ((l == I.L) ? (p.coarse == MG_COARSE_CHEB) : (l != 3));
+            const int role = level_role(l, I.L, p);
+            const bool cheb = role == MG_ROLE_CHEB || role == MG_ROLE_CHEB_ADR || role == MG_ROLE_COARSE_CHEB;
             lv.cheb = cheb;
             if (cheb) {
                 std::vector<double> kk((size_t)lv.n * lv.pitch);
@@ -572,11 +608,11 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             }
             if (l == I.L) {
                 int r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
-                                             0, lv.inv_helm, st);
+                                             0, 0, lv.inv_helm, st);
                 if (r) return r;
                 if (lv.inv_adr) {
                     r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc,
-                                             p.shift, 1, lv.inv_adr, st);
+                                             p.shift, 1, I.adr_abc, lv.inv_adr, st);
                     if (r) return r;
                 }
             }
@@ -601,11 +637,13 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 d.scal = H.scal + (size_t)S::SIZE * di;
                 d.part = H.part + (size_t)MAXB * MAXDOT * di;
                 d.counter = H.counter + (size_t)NCOUNTERS * di;
-                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, dscr, st);
+                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, I.adr_abc,
+                                       dscr, st);
                 d.fgs = (float)d.gs;
                 d.coarse = (l < I.L) ? di + 1 : -1;
                 if (l == I.L) {
                     int r = setup_coarse_inverse(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, 1,
+                                                 I.adr_abc,
                                                  v.inv_adr, st);
                     if (r) return r;
                 }
@@ -724,6 +762,7 @@ static void free_all(Handle& H) {
     if (H.hpin) cudaFreeHost(H.hpin);
     if (H.herr) cudaFreeHost(H.herr);
     H.allocs.clear();
+    H.alloc_bytes = 0;
 }
 
 // user dense (n x n, at element offset) <-> pitched slot
@@ -840,6 +879,8 @@ void mg_default_params(mg_params* p) {
     p->tail_cluster = 0;
     p->ray = 0;
     p->fgmres_passes = 2;
+    p->workspace_limit = 0;
+    p->adr_bc = MG_ADR_BC_ZERO;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -850,7 +891,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
         p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1 || p->ray < 0 ||
-        p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3) {
+        p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3 || p->workspace_limit < 0 ||
+        p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }
@@ -863,6 +905,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     }
     mg_handle* mh = new mg_handle();
     mh->H.p = *p;
+    mh->H.alloc_limit = p->workspace_limit;
     // automatic coarse tail: the shared-memory tail of the levels with n <= 31
     // pays off for a single instance (one block per instance runs those
     // levels); with many instances the per-level launches spread the work
@@ -936,10 +979,44 @@ int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int n
     const InstHost& I = h->H.inst[inst];
     if (level < 1 || level > I.L) return MG_EINVAL;
     const LevelHost& lv = I.lv[level - 1];
-    double v[4] = {lv.lam_max, lv.alpha, I.omega_j, lv.h};
-    int k = std::min(nout, 4);
+    double v[5] = {lv.lam_max, lv.alpha, I.omega_j, lv.h, lv.peclet};
+    int k = std::min(nout, 5);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
+}
+
+int mg_level_roles(int n, const mg_params* p, int* sizes, int* roles, int maxl) {
+    if (!p || n < 3 || p->n_cmax < 1 || maxl < 0 || (maxl > 0 && (!sizes || !roles))) {
+        set_error("mg_level_roles: bad argument");
+        return MG_EINVAL;
+    }
+    const std::vector<int> sz = level_sizes(n, p->n_cmax);
+    const int L = (int)sz.size();
+    for (int l = 1; l <= std::min(L, maxl); ++l) {
+        sizes[l - 1] = sz[(size_t)l - 1];
+        roles[l - 1] = level_role(l, L, *p);
+    }
+    return L;
+}
+
+long long mg_workspace_bytes(const mg_handle* h) {
+    if (!h) {
+        set_error("mg_workspace_bytes: null handle");
+        return MG_EINVAL;
+    }
+    return (long long)h->H.alloc_bytes;
+}
+
+int mg_peclet_flags(const mg_handle* h, int inst) {
+    if (!h || inst < 0 || inst >= (int)h->H.inst.size()) {
+        set_error("mg_peclet_flags: bad argument");
+        return MG_EINVAL;
+    }
+    const InstHost& I = h->H.inst[inst];
+    int flags = 0;
+    for (int l = 2; l <= I.L; ++l)
+        if (I.lv[l - 1].adr && I.lv[l - 1].peclet > 1.0) flags |= 1 << (l - 1);
+    return flags;
 }
 
 int mg_tile_shapes(const mg_handle* h, int inst, int level, int* out) {
@@ -1089,10 +1166,12 @@ int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_strea
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     cudaEventRecord(ev0, st);
-    int status = MG_OK;
+    // a non-finite initial residual (non-finite g or u) fails every
+    // comparison: report it instead of leaving the loop with MG_OK
+    int status = std::isfinite(rel) ? MG_OK : MG_EDIVERGED;
     const int ni = (int)H.inst.size();
     std::vector<double> est(ni);
-    while (rel >= H.p.tol && it < H.p.maxit) {
+    while (status == MG_OK && rel >= H.p.tol && it < H.p.maxit) {
         if (H.p.outer == MG_OUTER_FGMRES) {
             // one restart: inner iterations until the estimate meets tol
             for (int j = 0; j < H.p.restart && it < H.p.maxit; ++j) {
@@ -1129,7 +1208,7 @@ int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_strea
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    if (status == MG_OK && rel >= H.p.tol) status = MG_ENOTCONV;
+    if (status == MG_OK && !(rel < H.p.tol)) status = MG_ENOTCONV;
     rc = mg_solve_end(h, u, nullptr, stream);
     if (rc) return rc;
     if (info) {

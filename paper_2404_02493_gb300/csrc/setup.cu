@@ -1,6 +1,7 @@
 // Setup kernels (FP64): coefficient injection, ADR coefficients, level-2
 // modulation, the Gershgorin bound of A^*A and the coarsest-level dense LU.
 // These run once per mg_setup; none is on the per-cycle path.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -50,6 +51,65 @@ void setup_plane_phase(double* phi64, int n, int pitch, double h1, int scale, do
     k_plane_phase<<<g, b, 0, st>>>(phi64, n, pitch, h1, scale, cx, cy);
 }
 
+// Input validation of one instance's fine fields (dense n x n): counts the
+// nodes whose k is not a finite positive number (out[0]) and whose phi is
+// not finite (out[1]).
+__global__ void k_check_fields(const double* __restrict__ k, const double* __restrict__ phi, long long npt,
+                               unsigned long long* out) {
+    unsigned long long bad_k = 0, bad_phi = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npt; p += (long long)gridDim.x * blockDim.x) {
+        const double kv = k[p], pv = phi[p];
+        bad_k += !(isfinite(kv) && kv > 0.0);
+        bad_phi += !isfinite(pv);
+    }
+    if (bad_k) atomicAdd(out, bad_k);
+    if (bad_phi) atomicAdd(out + 1, bad_phi);
+}
+
+int setup_check_fields(const double* k, const double* phi, int n, double* dscratch, long long* bad_k,
+                       long long* bad_phi, cudaStream_t st) {
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
+    WADR_CHECK(cudaMemsetAsync(o, 0, 2 * sizeof(unsigned long long), st));
+    const long long npt = (long long)n * n;
+    const int blocks = (int)std::min<long long>((npt + 255) / 256, 1216);
+    k_check_fields<<<blocks, 256, 0, st>>>(k, phi, npt, o);
+    WADR_CHECK(cudaGetLastError());
+    unsigned long long v[2] = {0, 0};
+    WADR_CHECK(cudaMemcpyAsync(v, o, sizeof(v), cudaMemcpyDeviceToHost, st));
+    WADR_CHECK(cudaStreamSynchronize(st));
+    *bad_k = (long long)v[0];
+    *bad_phi = (long long)v[1];
+    return MG_OK;
+}
+
+// Peclet number of an ADR level (Section 3.2.2: the central-difference ADR
+// discretisation needs 2 omega h max(|phi_x|, |phi_y|) <= 2): the maximum over
+// nodes of omega h max(|phi_x|, |phi_y|), with the same phase derivatives as
+// the ADR coefficients.  The condition holds where the value is <= 1.
+__global__ void k_peclet(const double* phi64, const double* k64, const double* sig64, int n, int pitch, double h,
+                         double omega, int bc, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, 0.0, i, j, 0);
+    const double v = omega * h * fmax(fabs(c.px), fabs(c.py));
+    atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+                    double omega, int bc, double* dscratch, cudaStream_t st) {
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
+    cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
+    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
+    k_peclet<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, o);
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    double r;
+    memcpy(&r, &v, sizeof(r));
+    return r;
+}
+
 // max over nodes of the absolute row sum |A_pp| + (in-grid neighbours)/h^2
 __device__ __forceinline__ double helm_row_sum(const double* k64, const double* sig64, int n, int pitch,
                                                double h, int bc, double shift, int i, int j) {
@@ -93,11 +153,11 @@ double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch
 
 // max over nodes of the absolute row sum of the ADR operator |d| + sum |c_dir|
 __global__ void k_adr_rowmax(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
-                             double h, double omega, int bc, double shift, unsigned long long* out) {
+                             double h, double omega, int bc, double shift, int adr_abc, unsigned long long* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= n || j >= n) return;
-    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j);
+    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_abc);
     const double v = sqrt(dabs2(c.d)) + sqrt(dabs2(c.cw)) + sqrt(dabs2(c.ce)) + sqrt(dabs2(c.cs)) +
                      sqrt(dabs2(c.cn));
     atomicMax(out, (unsigned long long)__double_as_longlong(v));
@@ -107,11 +167,11 @@ __global__ void k_adr_rowmax(const double* phi64, const double* k64, const doubl
 // s * (max row sum of |L|) in (1/2, 1], so that ||s L||_inf <= 1 and the
 // basis vectors (s L)^j r0 stay O(|r0|) without rounding from s itself.
 double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                       double omega, int bc, double shift, double* dscratch, cudaStream_t st) {
+                       double omega, int bc, double shift, int adr_abc, double* dscratch, cudaStream_t st) {
     unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
     cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
     dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, shift, o);
+    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, shift, adr_abc, o);
     unsigned long long v = 0;
     cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -126,7 +186,7 @@ double setup_adr_scale(const double* k64, const double* phi64, const double* sig
 // ---------------------------------------------------------------- dense LU
 // Dense matrix of the coarsest operator (N = n^2, row p = j*n + i).
 __global__ void k_dense(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                        double omega, int bc, double shift, int which, double2* A) {
+                        double omega, int bc, double shift, int which, int adr_abc, double2* A) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = n * n;
     if (p >= N) return;
@@ -148,7 +208,7 @@ __global__ void k_dense(const double* k64, const double* phi64, const double* si
         if (j > 0) row[p - n] = make_double2(-ih2, 0);
         if (j < n - 1) row[p + n] = make_double2(-ih2, 0);
     } else {
-        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j);
+        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_abc);
         row[p] = c.d;
         if (i > 0) row[p - 1] = c.cw;
         if (i < n - 1) row[p + 1] = c.ce;
@@ -228,7 +288,7 @@ __global__ void k_lu_inv(const double2* LU, const int* perm, int N, double2* inv
 }
 
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, double shift, int which, double2* inv, cudaStream_t st) {
+                         double omega, int bc, double shift, int which, int adr_abc, double2* inv, cudaStream_t st) {
     const int N = n * n;
     double2* A = nullptr;
     int* perm = nullptr;
@@ -237,7 +297,7 @@ int setup_coarse_inverse(const double* k64, const double* phi64, const double* s
     if (cudaMalloc(&perm, sizeof(int) * (N + 1)) != cudaSuccess) { cudaFree(A); return MG_ENOMEM; }
     info = perm + N;
     cudaMemsetAsync(info, 0, sizeof(int), st);
-    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, pitch, h, omega, bc, shift, which, A);
+    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, pitch, h, omega, bc, shift, which, adr_abc, A);
     k_lu<<<1, 1024, 0, st>>>(A, N, perm, info);
     k_lu_inv<<<(N + 63) / 64, 64, 0, st>>>(A, perm, N, inv);
     int hinfo = 0;

@@ -29,8 +29,16 @@ struct AdrCoef {
 //   cw = -1/h^2 + i w (px+|px|)/h,  ce = -1/h^2 - i w (px-|px|)/h  (same in y),
 // with central differences of phi after linear extrapolation of one ghost
 // layer (second order inside, first order on the boundary, Section 3.2.1).
+// Boundary closure of the ADR unknown (the paper states none):
+//   adr_abc = 0: zero ghost a_g = 0 on every side;
+//   adr_abc = 1: the first-order absorbing condition of the Helmholtz
+//     problem carried through the same substitution v = a exp(i w phi):
+//     u_g = (1 + i k h) u_b gives a_g = (1 + i k h) exp(-i w (phi_b - phi_in)) a_b,
+//     phi_in the inner neighbour (the ghost phase is the linear extrapolation
+//     used for the derivatives); each missing neighbour adds its stencil
+//     coefficient times that factor to the diagonal.
 __device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
-                                      double h, double omega, int bc, double shift, int i, int j) {
+                                      double h, double omega, int bc, double shift, int i, int j, int adr_abc) {
     auto P = [&](int ii, int jj) { return phi64[(long long)jj * pitch + ii]; };
     const double pc = P(i, j);
     const double pw = i > 0 ? P(i - 1, j) : 2.0 * pc - P(i + 1, j);
@@ -56,6 +64,20 @@ __device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, co
     c.cn = make_double2(-ih2, -wh * (py - ay));
     c.px = px;
     c.py = py;
+    if (adr_abc) {
+        // ghost factor (1 + i k h) exp(-i w (phi_b - phi_in)) for each missing neighbour
+        auto ghost = [&](double2 cg, double pin) {
+            double sn, cs;
+            sincos(-omega * (pc - pin), &sn, &cs);
+            const double2 rho = make_double2(cs - k * h * sn, sn + k * h * cs);
+            c.d.x += cg.x * rho.x - cg.y * rho.y;
+            c.d.y += cg.x * rho.y + cg.y * rho.x;
+        };
+        if (i == 0) ghost(c.cw, pe);
+        if (i == n - 1) ghost(c.ce, pw);
+        if (j == 0) ghost(c.cs, pn);
+        if (j == n - 1) ghost(c.cn, ps);
+    }
     return c;
 }
 
@@ -71,11 +93,11 @@ __global__ void k_fields(const double* k64, const double* sig64, int n, int pitc
 
 template <typename T>
 __global__ void k_adr_fields(const double* phi64, const double* k64, const double* sig64, int n, int pitch, double h,
-                             double omega, int bc, double shift, quad<T>* out) {
+                             double omega, int bc, double shift, int adr_abc, quad<T>* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= n || j >= n) return;
-    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j);
+    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_abc);
     quad<T> q;
     q.x = (T)c.px;
     q.y = (T)c.py;

@@ -61,3 +61,35 @@ def test_kernel_kind_table_matches_the_header(lib):
     assert "unknown" not in names and len(set(names)) == len(names), names
     assert lib.mg_kernel_name(binding.MG_KERNEL_KINDS).decode() == "unknown"
     assert {"gmres_gram", "chebyshev_step", "adr_tail", "wave_tail", "fgmres_dots"} <= set(names)
+
+
+@pytest.mark.parametrize("n,n_cmax,coarse,M", [(4095, 15, "lu", 8), (4095, 31, "lu", 8), (128, 16, "lu", 8),
+                                                (100, 12, "cheb", 8), (63, 7, "lu", 0), (31, 15, "lu", 8),
+                                                (7, 3, "lu", 8)])
+def test_level_roles_match_the_oracle_hierarchy(lib, n, n_cmax, coarse, M):
+    """mg_level_roles (no GPU, no handle) gives the oracle's level sizes and
+    Algorithm 1's role per level."""
+    from oracle.cycle import build_sizes
+    p = binding.default_params(n_cmax=n_cmax, coarse=coarse, M=M)
+    roles = binding.mg_level_roles(n, p)
+    sizes = build_sizes(n, n_cmax)
+    assert [s for s, _ in roles] == sizes
+    L = len(sizes)
+    for l, (_, r) in enumerate(roles, start=1):
+        if l == L:
+            want = "coarse_cheb" if coarse == "cheb" else "coarse_lu"
+        elif l == 1:
+            want = "jacobi"
+        elif l == 3:
+            want = "none"
+        elif l == 2:
+            want = "cheb_adr" if (M > 0 and L >= 3) else "cheb"
+        else:
+            want = "cheb"
+        assert r == want, (l, r, want)
+
+
+def test_level_roles_rejects_bad_sizes(lib):
+    p = binding.default_params()
+    with pytest.raises(binding.MgError):
+        binding.mg_level_roles(2, p)
