@@ -83,6 +83,8 @@ NaSymbols na_sym[64];
 
 // Device addresses of the static scratch for the current device (host code
 // must not pass the symbols themselves: on the host they are stand-ins).
+// Looked up once per device ordinal and kept for the life of the process's
+// context on that device (a cudaDeviceReset would invalidate them).
 static int na_setup(NaSymbols** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
