@@ -113,6 +113,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle
+def host_cpu():
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    import platform
+    return {"host_cpu_count": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def oracle_cycle_rate(steps: int, warmup: int):
     """The oracle (complex128 NumPy, single thread) on the sample workload:
     seconds per outer step (residual, one cycle, update)."""
@@ -147,13 +168,19 @@ def run_reference(args):
     dt = oracle_cycle_rate(args.steps, args.warmup)
     scale = (N_SAMPLE / N_FULL) ** 2        # work per cycle is proportional to the points
     value = scale / dt
-    sample = (f"oracle outer steps on the same recipe at n={N_SAMPLE}, omega={OMEGA_SAMPLE:g} "
-              f"({dt:.2f} s per step), scaled to n={N_FULL} by the point ratio {scale:.4f}")
+    sample = (f"{args.steps} oracle outer steps (after {args.warmup} untimed) on the same recipe at n={N_SAMPLE}, "
+              f"omega={OMEGA_SAMPLE:g}: {dt:.3f} s per step measured; the n={N_FULL} rate is extrapolated by the "
+              f"point ratio {scale:.4f}")
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, **host_cpu(),
+           "threads_used": 1}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / scale,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "value_kind": f"extrapolated to n={N_FULL} from the measured n={N_SAMPLE} steps (point ratio)",
+            "ms_per_step_measured_at": {"n": N_SAMPLE, "omega": OMEGA_SAMPLE},
+            "ms_per_step_extrapolated_n4095": dt * 1e3 / scale,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": workload_config(N_FULL, OMEGA_FULL),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -520,9 +547,10 @@ def run_ours(args):
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         dt = oracle_cycle_rate(2, 0)
         scale = (N_SAMPLE / N_FULL) ** 2
-        cpu = {"value": scale / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": scale / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "threads_used": 1,
                "sample": f"2 oracle outer steps on the same recipe at n={N_SAMPLE}, omega={OMEGA_SAMPLE:g} "
-                         f"({dt:.2f} s each), scaled to n={N_FULL} by the point ratio {scale:.4f}"}
+                         f"({dt:.2f} s each), scaled to n={N_FULL} by the point ratio {scale:.4f}",
+               **host_cpu()}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
