@@ -70,6 +70,8 @@ enum { MG_OUTER_STATIONARY = 0, MG_OUTER_IR = 1, MG_OUTER_FGMRES = 2 };
 enum { MG_COARSE_LU = 0, MG_COARSE_CHEB = 1 };
 /* Boundary closure of the ADR unknown a (the paper states none; see mg_params.adr_bc). */
 enum { MG_ADR_BC_ZERO = 0, MG_ADR_BC_ABC = 1 };
+/* Reaction term of the ADR operator (see mg_params.adr_reaction). */
+enum { MG_ADR_REACTION_CONTINUOUS = 0, MG_ADR_REACTION_DISCRETE = 1 };
 
 #define MG_MAX_LEVELS 16
 #define MG_TILE_CANDIDATES 5   /* halo-tile shape candidates per ADR GMRES kernel */
@@ -130,6 +132,12 @@ typedef struct mg_params {
                                problem carried through v = a exp(i omega phi): ghost a_g = (1 + i k h)
                                exp(-i omega (phi_b - phi_in)) a_b, phi_in the inner neighbour (other boundary
                                kinds keep the zero ghost, which is what u = 0 on the boundary gives) */
+    int adr_reaction;       /* MG_ADR_REACTION_CONTINUOUS (default): eq. ADR's omega^2 (|grad phi|^2 - s^2);
+                               MG_ADR_REACTION_DISCRETE: omega^2 |grad phi|^2 replaced by the 5-point symbol of
+                               the same plane wave, (4/h^2)(sin^2(omega h phi_x/2) + sin^2(omega h phi_y/2)), on
+                               every ADR level.  Not in the paper: with the eikonal phase the continuous term
+                               disagrees with the dispersion of the 5-point operator at omega h ~ 1, and repeated
+                               ADR corrections then amplify the residual on large grids */
     long long workspace_limit; /* 0 (default): none; > 0: mg_setup fails with MG_ENOMEM, freeing what it
                                had allocated, when the handle's device workspace would exceed this many bytes
                                (for callers that share the GPU; mg_workspace_bytes reports the size) */

@@ -37,6 +37,7 @@ class CycleParams:
     adr_bc: str = "zero"           # ADR boundary closure: "zero" ghost | "abc" (absorbing, carried through)
     adr_scheme: str = "upwind"     # ADR convection: "upwind" (eq. upwind) | "central" (Fig. discremethod)
     adr_solver: str = "vcycle"     # ADR system: one V-cycle (Section 3.2.2) | "direct" (Fig. discremethod)
+    adr_reaction: str = "continuous"  # eq. ADR's w^2(|grad phi|^2 - s^2) | "discrete" (5-point symbol; option)
 
 
 def build_sizes(n: int, n_cmax: int):
@@ -73,9 +74,10 @@ def helmholtz_sparse(lev: Level) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(n * n, n * n), dtype=np.complex128)
 
 
-def adr_sparse(lev: Level, closure: str = "zero", scheme: str = "upwind") -> sp.csr_matrix:
+def adr_sparse(lev: Level, closure: str = "zero", scheme: str = "upwind",
+               reaction: str = "continuous") -> sp.csr_matrix:
     """Assembly of the ADR matrix from its coefficients."""
-    c = adr_coefficients(lev, closure, scheme)
+    c = adr_coefficients(lev, closure, scheme, reaction)
     n = lev.n
     rows, cols, vals = [], [], []
     for j in range(n):
@@ -143,10 +145,11 @@ class Hierarchy:
                         pl = inject(pl)
                     levs.append(dataclasses.replace(self.levels[l - 1], phi=pl))
                 pa = self.p
-                coefs = {l: adr_coefficients(levs[l - 1], pa.adr_bc, pa.adr_scheme) for l in range(2, self.L + 1)}
+                opt = (pa.adr_bc, pa.adr_scheme, pa.adr_reaction)
+                coefs = {l: adr_coefficients(levs[l - 1], *opt) for l in range(2, self.L + 1)}
                 mod = np.exp(1j * conv * omega * levs[1].phi)   # e^{+i conv w phi_2}
-                lu = scipy.linalg.lu_factor(adr_sparse(levs[-1], pa.adr_bc, pa.adr_scheme).toarray())
-                direct = (spla.splu(adr_sparse(levs[1], pa.adr_bc, pa.adr_scheme).tocsc())
+                lu = scipy.linalg.lu_factor(adr_sparse(levs[-1], *opt).toarray())
+                direct = (spla.splu(adr_sparse(levs[1], *opt).tocsc())
                           if pa.adr_solver == "direct" else None)
                 self.adr_sets.append((coefs, mod, lu, direct))
             self.adr, self.mod, self.lu_adr = self.adr_sets[0][:3]

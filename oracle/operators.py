@@ -131,7 +131,8 @@ def phase_derivatives(phi: np.ndarray, h: float):
     return phix, phiy, lap
 
 
-def adr_coefficients(lev: Level, closure: str = "zero", scheme: str = "upwind") -> ADRCoefficients:
+def adr_coefficients(lev: Level, closure: str = "zero", scheme: str = "upwind",
+                     reaction: str = "continuous") -> ADRCoefficients:
     """Discrete ADR operator obtained by substituting v = a exp(i conv w phi)
     into the Helmholtz equation (eq. Rytov, eq. ADR):
 
@@ -143,6 +144,9 @@ def adr_coefficients(lev: Level, closure: str = "zero", scheme: str = "upwind") 
     eq. upwind, whose 5-point form (Section 3.3) is
       (1/2h)[ 2(|px|+|py|) a_c + (-px-|px|) a_W + (px-|px|) a_E
               + (-py-|py|) a_S + (py-|py|) a_N ].
+    reaction="discrete" replaces w^2 |grad phi|^2 by the 5-point symbol of
+    the plane wave exp(i w phi) with the local gradient,
+    (4/h^2)(sin^2(w h px/2) + sin^2(w h py/2)) (not in the paper; an option).
     scheme="central" replaces the upwind convection by the central
     difference (1/2h)[px (a_E - a_W) + py (a_N - a_S)], the discretisation
     Section 3.2.2 compares against (Fig. discremethod).
@@ -165,8 +169,14 @@ def adr_coefficients(lev: Level, closure: str = "zero", scheme: str = "upwind") 
         raise ValueError(scheme)
     s2 = (lev.k / w) ** 2
     ic = 1j * lev.conv
+    if reaction == "continuous":
+        grad2 = w * w * (phix ** 2 + phiy ** 2)
+    elif reaction == "discrete":
+        grad2 = 4.0 / (h * h) * (np.sin(0.5 * w * h * phix) ** 2 + np.sin(0.5 * w * h * phiy) ** 2)
+    else:
+        raise ValueError(reaction)
     d = (4.0 / (h * h) - ic * 2 * w * (ax + ay) / h - ic * w * lap
-         + w * w * (phix ** 2 + phiy ** 2 - s2)).astype(np.complex128)
+         + grad2 - w * w * s2).astype(np.complex128)
     if lev.bc == "sponge":
         d = d - ic * w * lev.gamma * s2
     if lev.shift:

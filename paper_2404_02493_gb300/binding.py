@@ -22,6 +22,7 @@ MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_OUTER = {"stationary": 0, "ir": 1, "fgmres": 2}
 MG_COARSE_LU, MG_COARSE_CHEB = 0, 1
 MG_ADR_BC = {"zero": 0, "abc": 1}
+MG_ADR_REACTION = {"continuous": 0, "discrete": 1}
 MG_ROLE = {0: "jacobi", 1: "cheb", 2: "none", 3: "cheb_adr", 4: "coarse_lu", 5: "coarse_cheb"}
 MG_OP = {"A": 0, "AH": 1, "L": 2, "LT": 3, "LH": 4}
 MG_MAX_LEVELS = 16
@@ -37,7 +38,8 @@ class MgParams(ctypes.Structure):
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("shift", ctypes.c_double),
         ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("tile_candidate", ctypes.c_int),
         ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int), ("tail_cluster", ctypes.c_int), ("ray", ctypes.c_int),
-        ("fgmres_passes", ctypes.c_int), ("adr_bc", ctypes.c_int), ("workspace_limit", ctypes.c_longlong),
+        ("fgmres_passes", ctypes.c_int), ("adr_bc", ctypes.c_int), ("adr_reaction", ctypes.c_int),
+        ("workspace_limit", ctypes.c_longlong),
     ]
 
 
@@ -171,6 +173,8 @@ def default_params(**kw) -> MgParams:
             p.outer = MG_OUTER[v]
         elif k == "adr_bc" and isinstance(v, str):
             p.adr_bc = MG_ADR_BC[v]
+        elif k == "adr_reaction" and isinstance(v, str):
+            p.adr_reaction = MG_ADR_REACTION[v]
         elif k == "coarse" and isinstance(v, str):
             p.coarse = {"lu": MG_COARSE_LU, "cheb": MG_COARSE_CHEB}[v]
         else:

@@ -151,6 +151,8 @@ template <typename T> __device__ __forceinline__ cplx<T>* partp(const LevelDesc&
 
 constexpr int MAXDOT = 8;        // complex partial sums per block
 constexpr int NCOUNTERS = 8;
+// Options of the ADR coefficients (InstHost::adr_flags; see adr_coef_at).
+constexpr int ADR_ABC = 1, ADR_DISC = 2;
 constexpr int NT = 256;          // threads per block of every grid kernel
 constexpr int BX = 32, BY = 8;   // block shape
 

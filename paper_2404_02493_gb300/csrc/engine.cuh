@@ -153,7 +153,7 @@ struct Engine : EngineBase {
                 k_fields<T><<<gg, bb, 0, st>>>(lv.k64, lv.sig64, lv.n, lv.pitch, (T*)lv.kf, (T*)lv.sig);
                 if (lv.adr)
                     k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega,
-                                                      I.bc, H.p.shift, I.adr_abc, (quad<T>*)lv.adr);
+                                                      I.bc, H.p.shift, I.adr_flags, (quad<T>*)lv.adr);
                 if (lv.mod)
                     k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.pitch, I.omega, (cplx<T>*)lv.mod);
             }
@@ -163,7 +163,7 @@ struct Engine : EngineBase {
                     LevelHost& lv = vl[l - 1];
                     dim3 bb(32, 8), gg((lv.n + 31) / 32, (lv.n + 7) / 8);
                     k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega,
-                                                      I.bc, H.p.shift, I.adr_abc, (quad<T>*)lv.adr);
+                                                      I.bc, H.p.shift, I.adr_flags, (quad<T>*)lv.adr);
                     if (lv.mod)
                         k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.pitch, I.omega, (cplx<T>*)lv.mod);
                 }

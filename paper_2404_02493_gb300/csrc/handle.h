@@ -38,7 +38,7 @@ struct LevelHost {
 
 struct InstHost {
     int n = 0, L = 0, bc = 0;
-    int adr_abc = 0;                // ADR boundary closure (1: absorbing condition carried through, see adr_coef_at)
+    int adr_flags = 0;              // ADR_ABC | ADR_DISC options of the ADR coefficients (see adr_coef_at)
     double omega = 0;
     double omega_j = 0;
     std::vector<LevelHost> lv;      // lv[0] = level 1
@@ -168,13 +168,13 @@ void setup_inject(const double* k_fine, const double* phi_fine, int n1, double o
 double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
                         double* dscratch, cudaStream_t st);
 double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                       double omega, int bc, double shift, int adr_abc, double* dscratch, cudaStream_t st);
+                       double omega, int bc, double shift, int adr_flags, double* dscratch, cudaStream_t st);
 int setup_check_fields(const double* k, const double* phi, int n, double* dscratch, long long* bad_k,
                        long long* bad_phi, cudaStream_t st);
 double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
                     double omega, int bc, double* dscratch, cudaStream_t st);
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, double shift, int which, int adr_abc, double2* inv, cudaStream_t st);
+                         double omega, int bc, double shift, int which, int adr_flags, double2* inv, cudaStream_t st);
 
 #define WADR_CHECK(x)                                                                   \
     do {                                                                                \

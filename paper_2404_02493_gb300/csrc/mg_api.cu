@@ -404,7 +404,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         I.n = in[b].n;
         I.omega = in[b].omega;
         I.bc = in[b].bc;
-        I.adr_abc = (p.adr_bc == MG_ADR_BC_ABC && I.bc == MG_BC_ABC1) ? 1 : 0;
+        I.adr_flags = ((p.adr_bc == MG_ADR_BC_ABC && I.bc == MG_BC_ABC1) ? ADR_ABC : 0) |
+                      (p.adr_reaction == MG_ADR_REACTION_DISCRETE ? ADR_DISC : 0);
         I.off = off;
         off += (long long)I.n * I.n;
         const std::vector<int> sizes = level_sizes(I.n, p.n_cmax);
@@ -568,7 +569,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.fshift = (float)d.shift;
             d.has_shift = d.shift != 0.0;
             d.gs = lv.adr ? setup_adr_scale(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
-                                            I.adr_abc, dscr, st)
+                                            I.adr_flags, dscr, st)
                           : 1.0;
             if (lv.adr) lv.peclet = setup_peclet(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, dscr, st);
             d.fgs = (float)d.gs;
@@ -612,7 +613,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 if (r) return r;
                 if (lv.inv_adr) {
                     r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc,
-                                             p.shift, 1, I.adr_abc, lv.inv_adr, st);
+                                             p.shift, 1, I.adr_flags, lv.inv_adr, st);
                     if (r) return r;
                 }
             }
@@ -637,13 +638,13 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 d.scal = H.scal + (size_t)S::SIZE * di;
                 d.part = H.part + (size_t)MAXB * MAXDOT * di;
                 d.counter = H.counter + (size_t)NCOUNTERS * di;
-                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, I.adr_abc,
+                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, I.adr_flags,
                                        dscr, st);
                 d.fgs = (float)d.gs;
                 d.coarse = (l < I.L) ? di + 1 : -1;
                 if (l == I.L) {
                     int r = setup_coarse_inverse(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, 1,
-                                                 I.adr_abc,
+                                                 I.adr_flags,
                                                  v.inv_adr, st);
                     if (r) return r;
                 }
@@ -881,6 +882,7 @@ void mg_default_params(mg_params* p) {
     p->fgmres_passes = 2;
     p->workspace_limit = 0;
     p->adr_bc = MG_ADR_BC_ZERO;
+    p->adr_reaction = MG_ADR_REACTION_CONTINUOUS;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -892,7 +894,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
         p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1 || p->ray < 0 ||
         p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3 || p->workspace_limit < 0 ||
-        p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC) {
+        p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC ||
+        p->adr_reaction < MG_ADR_REACTION_CONTINUOUS || p->adr_reaction > MG_ADR_REACTION_DISCRETE) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }

@@ -153,11 +153,11 @@ double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch
 
 // max over nodes of the absolute row sum of the ADR operator |d| + sum |c_dir|
 __global__ void k_adr_rowmax(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
-                             double h, double omega, int bc, double shift, int adr_abc, unsigned long long* out) {
+                             double h, double omega, int bc, double shift, int adr_flags, unsigned long long* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= n || j >= n) return;
-    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_abc);
+    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_flags);
     const double v = sqrt(dabs2(c.d)) + sqrt(dabs2(c.cw)) + sqrt(dabs2(c.ce)) + sqrt(dabs2(c.cs)) +
                      sqrt(dabs2(c.cn));
     atomicMax(out, (unsigned long long)__double_as_longlong(v));
@@ -167,11 +167,11 @@ __global__ void k_adr_rowmax(const double* phi64, const double* k64, const doubl
 // s * (max row sum of |L|) in (1/2, 1], so that ||s L||_inf <= 1 and the
 // basis vectors (s L)^j r0 stay O(|r0|) without rounding from s itself.
 double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                       double omega, int bc, double shift, int adr_abc, double* dscratch, cudaStream_t st) {
+                       double omega, int bc, double shift, int adr_flags, double* dscratch, cudaStream_t st) {
     unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
     cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
     dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, shift, adr_abc, o);
+    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, shift, adr_flags, o);
     unsigned long long v = 0;
     cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -186,7 +186,7 @@ double setup_adr_scale(const double* k64, const double* phi64, const double* sig
 // ---------------------------------------------------------------- dense LU
 // Dense matrix of the coarsest operator (N = n^2, row p = j*n + i).
 __global__ void k_dense(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                        double omega, int bc, double shift, int which, int adr_abc, double2* A) {
+                        double omega, int bc, double shift, int which, int adr_flags, double2* A) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = n * n;
     if (p >= N) return;
@@ -208,7 +208,7 @@ __global__ void k_dense(const double* k64, const double* phi64, const double* si
         if (j > 0) row[p - n] = make_double2(-ih2, 0);
         if (j < n - 1) row[p + n] = make_double2(-ih2, 0);
     } else {
-        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_abc);
+        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_flags);
         row[p] = c.d;
         if (i > 0) row[p - 1] = c.cw;
         if (i < n - 1) row[p + 1] = c.ce;
@@ -288,7 +288,7 @@ __global__ void k_lu_inv(const double2* LU, const int* perm, int N, double2* inv
 }
 
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, double shift, int which, int adr_abc, double2* inv, cudaStream_t st) {
+                         double omega, int bc, double shift, int which, int adr_flags, double2* inv, cudaStream_t st) {
     const int N = n * n;
     double2* A = nullptr;
     int* perm = nullptr;
@@ -297,7 +297,7 @@ int setup_coarse_inverse(const double* k64, const double* phi64, const double* s
     if (cudaMalloc(&perm, sizeof(int) * (N + 1)) != cudaSuccess) { cudaFree(A); return MG_ENOMEM; }
     info = perm + N;
     cudaMemsetAsync(info, 0, sizeof(int), st);
-    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, pitch, h, omega, bc, shift, which, adr_abc, A);
+    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, pitch, h, omega, bc, shift, which, adr_flags, A);
     k_lu<<<1, 1024, 0, st>>>(A, N, perm, info);
     k_lu_inv<<<(N + 63) / 64, 64, 0, st>>>(A, perm, N, inv);
     int hinfo = 0;

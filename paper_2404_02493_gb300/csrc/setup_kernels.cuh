@@ -29,16 +29,22 @@ struct AdrCoef {
 //   cw = -1/h^2 + i w (px+|px|)/h,  ce = -1/h^2 - i w (px-|px|)/h  (same in y),
 // with central differences of phi after linear extrapolation of one ghost
 // layer (second order inside, first order on the boundary, Section 3.2.1).
-// Boundary closure of the ADR unknown (the paper states none):
-//   adr_abc = 0: zero ghost a_g = 0 on every side;
-//   adr_abc = 1: the first-order absorbing condition of the Helmholtz
+// adr_flags (bit mask):
+// ADR_ABC -- boundary closure of the ADR unknown (the paper states none):
+//   clear: zero ghost a_g = 0 on every side;
+//   set: the first-order absorbing condition of the Helmholtz
 //     problem carried through the same substitution v = a exp(i w phi):
 //     u_g = (1 + i k h) u_b gives a_g = (1 + i k h) exp(-i w (phi_b - phi_in)) a_b,
 //     phi_in the inner neighbour (the ghost phase is the linear extrapolation
 //     used for the derivatives); each missing neighbour adds its stencil
 //     coefficient times that factor to the diagonal.
+// ADR_DISC -- reaction term: clear: eq. ADR's w^2 (px^2 + py^2 - s^2); set:
+//   w^2 (px^2 + py^2) replaced by the 5-point symbol of the same plane wave,
+//   (4/h^2) (sin^2(w h px / 2) + sin^2(w h py / 2)), so that a locally plane
+//   wave exp(i w phi) carries the reaction the discrete Helmholtz operator
+//   gives it (a deviation from the printed equation; off by default).
 __device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
-                                      double h, double omega, int bc, double shift, int i, int j, int adr_abc) {
+                                      double h, double omega, int bc, double shift, int i, int j, int adr_flags) {
     auto P = [&](int ii, int jj) { return phi64[(long long)jj * pitch + ii]; };
     const double pc = P(i, j);
     const double pw = i > 0 ? P(i - 1, j) : 2.0 * pc - P(i + 1, j);
@@ -52,7 +58,13 @@ __device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, co
     const double s2 = (k / omega) * (k / omega);
     const double ax = fabs(px), ay = fabs(py);
     AdrCoef c;
-    double dre = 4.0 / (h * h) + omega * omega * (px * px + py * py - s2);
+    double dre;
+    if (adr_flags & ADR_DISC) {
+        const double sx = sin(0.5 * omega * h * px), sy = sin(0.5 * omega * h * py);
+        dre = 4.0 / (h * h) + 4.0 / (h * h) * (sx * sx + sy * sy) - omega * omega * s2;
+    } else {
+        dre = 4.0 / (h * h) + omega * omega * (px * px + py * py - s2);
+    }
     double dim = -2.0 * omega * (ax + ay) / h - omega * lap;
     if (bc == BC_SPONGE) dim -= sig64[p];
     if (shift != 0.0) dim -= shift * k * k;
@@ -64,7 +76,7 @@ __device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, co
     c.cn = make_double2(-ih2, -wh * (py - ay));
     c.px = px;
     c.py = py;
-    if (adr_abc) {
+    if (adr_flags & ADR_ABC) {
         // ghost factor (1 + i k h) exp(-i w (phi_b - phi_in)) for each missing neighbour
         auto ghost = [&](double2 cg, double pin) {
             double sn, cs;
@@ -93,11 +105,11 @@ __global__ void k_fields(const double* k64, const double* sig64, int n, int pitc
 
 template <typename T>
 __global__ void k_adr_fields(const double* phi64, const double* k64, const double* sig64, int n, int pitch, double h,
-                             double omega, int bc, double shift, int adr_abc, quad<T>* out) {
+                             double omega, int bc, double shift, int adr_flags, quad<T>* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= n || j >= n) return;
-    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_abc);
+    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_flags);
     quad<T> q;
     q.x = (T)c.px;
     q.y = (T)c.py;

@@ -1,8 +1,12 @@
-"""The absorbing boundary closure of the ADR unknown (mg_params.adr_bc =
-MG_ADR_BC_ABC; the paper states no ADR boundary condition; this closure
+"""Options of the ADR operator against the oracle built with the same
+options: the absorbing boundary closure of the ADR unknown (mg_params.adr_bc
+= MG_ADR_BC_ABC; the paper states no ADR boundary condition; this closure
 carries the first-order absorbing condition of the Helmholtz problem through
-the substitution v = a exp(i omega phi) of eq. Rytov / eq. ADR) against the
-oracle built with the same closure.
+the substitution v = a exp(i omega phi) of eq. Rytov / eq. ADR) and the
+discrete reaction term (mg_params.adr_reaction =
+MG_ADR_REACTION_DISCRETE: omega^2 |grad phi|^2 replaced by the 5-point
+symbol of the plane wave, an option that is not in the paper), alone and
+together.
 
 Tolerances as in the other parity tests: operators 1e-13, the coarsest ADR
 solve and one FP64 cycle 1e-12, one complex-FP32 cycle 1e-5 per cycle;
@@ -36,18 +40,23 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=list(CASES))
+OPTIONS = [("abc", "continuous"), ("zero", "discrete"), ("abc", "discrete")]
+
+
+@pytest.fixture(scope="module", params=[(c, o) for c in CASES for o in OPTIONS],
+                ids=lambda p: f"{p[0]}-{p[1][0]}-{p[1][1]}")
 def case(request):
-    I, ncm = CASES[request.param]()
-    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=ncm, adr_bc="abc"))
-    h = lib_handle([I], "fp64", n_cmax=ncm, adr_bc="abc")
-    yield I, ncm, H, h
+    name, (closure, reaction) = request.param
+    I, ncm = CASES[name]()
+    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=ncm, adr_bc=closure, adr_reaction=reaction))
+    h = lib_handle([I], "fp64", n_cmax=ncm, adr_bc=closure, adr_reaction=reaction)
+    yield I, ncm, H, h, closure, reaction
     B.mg_destroy(h)
 
 
-def test_adr_operator_with_closure(case):
-    I, ncm, H, h = case
-    H0 = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=ncm))
+def test_adr_operator_with_options(case):
+    I, ncm, H, h, closure, reaction = case
+    H0 = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=ncm, adr_reaction=reaction))
     for l in range(2, H.L + 1):
         n = H.lev(l).n
         x = rnd((n, n), 40 + l)
@@ -55,14 +64,14 @@ def test_adr_operator_with_closure(case):
         B.mg_apply(h, 0, l, "L", x, y)
         ref = adr_apply(H.adr[l], x)
         assert rel(y, ref) < 1e-13, (l, rel(y, ref))
-        # only the boundary rows differ from the zero-ghost operator
+        # the closure changes only the boundary rows
         ref0 = adr_apply(H0.adr[l], x)
         d = np.abs(ref - ref0)
-        assert d[1:-1, 1:-1].max() == 0.0 and d.max() > 0.0
+        assert d[1:-1, 1:-1].max() == 0.0 and (d.max() > 0.0) == (closure == "abc")
 
 
-def test_coarsest_adr_solve_with_closure(case):
-    I, ncm, H, h = case
+def test_coarsest_adr_solve_with_options(case):
+    I, ncm, H, h, closure, reaction = case
     n = H.lev(H.L).n
     b = rnd((n, n), 7)
     x = np.zeros_like(b)
@@ -70,8 +79,8 @@ def test_coarsest_adr_solve_with_closure(case):
     assert rel(adr_apply(H.adr[H.L], x), b) < 1e-12
 
 
-def test_cycle_fp64_with_closure(case):
-    I, ncm, H, h = case
+def test_cycle_fp64_with_options(case):
+    I, ncm, H, h, closure, reaction = case
     u = rnd(I.g.shape, 5) * 1e-3
     uu = u.copy()
     B.mg_cycle(h, uu, I.g.copy(), 1)
@@ -79,10 +88,11 @@ def test_cycle_fp64_with_closure(case):
     assert rel(uu, ref) < 1e-12, rel(uu, ref)
 
 
-def test_cycle_mixed_and_fgmres_with_closure():
+@pytest.mark.parametrize("closure,reaction", OPTIONS)
+def test_cycle_mixed_and_fgmres_with_options(closure, reaction):
     I = synth.config_lognormal(n=127, omega=60.0, seed=3)
-    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=15, adr_bc="abc"))
-    h = lib_handle([I], "mixed", n_cmax=15, adr_bc="abc", tol=1e-6, maxit=300)
+    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=15, adr_bc=closure, adr_reaction=reaction))
+    h = lib_handle([I], "mixed", n_cmax=15, adr_bc=closure, adr_reaction=reaction, tol=1e-6, maxit=300)
     try:
         u = np.zeros(I.g.shape, np.complex64)
         B.mg_cycle(h, u, I.g.astype(np.complex64), 1)
@@ -96,8 +106,8 @@ def test_cycle_mixed_and_fgmres_with_closure():
         B.mg_destroy(h)
 
 
-def test_adjoint_refuses_the_closure(case):
-    I, ncm, H, h = case
+def test_adjoint_refuses_the_options(case):
+    I, ncm, H, h, closure, reaction = case
     gphi = np.zeros_like(I.phi)
     with pytest.raises(B.MgError) as e:
         B.mg_cycle_backward(h, np.zeros_like(I.g), I.g.copy(), 1, np.ones_like(I.g), gphi)

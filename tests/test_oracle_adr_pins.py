@@ -112,3 +112,32 @@ def test_abc_closure_is_the_helmholtz_ghost_through_the_substitution():
         ag = ug[sl] / np.exp(1j * w * phig)       # a_g = u_g / exp(i w phi_g)
         np.testing.assert_allclose(diff[sl], coef[sl] * ag, rtol=1e-12, atol=1e-9 * np.abs(diff).max())
     assert np.abs(diff[1:-1, 1:-1]).max() == 0.0
+
+
+def test_discrete_reaction_is_the_modulated_helmholtz_operator_on_plane_waves():
+    """The discrete reaction option (not the paper's form): for a plane-wave
+    phase phi = cos(t) x + sin(t) y and constant k, the constant envelope
+    a = 1 gives exactly exp(-i w phi) A exp(i w phi) at every interior node
+    (the upwind convection of a constant vanishes, and 4 sin^2(x/2) =
+    2 - 2 cos x), while eq. ADR's continuous term misses it by the 5-point
+    dispersion error, which at w h ~ 1 is of the order of the operator's
+    smallest eigenvalues."""
+    n, w = 63, 60.0
+    h = 1.0 / (n + 1)
+    x = (np.arange(n) + 1) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    for t in (0.0, 0.3, np.pi / 4, 2.0):
+        phi = np.cos(t) * X + np.sin(t) * Y
+        lev = Level(n=n, h=h, k=np.full((n, n), w), phi=phi, gamma=np.zeros((n, n)), omega=w, bc="dirichlet")
+        one = np.ones((n, n), complex)
+        mod = np.exp(1j * w * phi)
+        ref = np.conj(mod) * helmholtz_apply(lev, mod)
+        inner = (slice(1, -1), slice(1, -1))
+        disc = adr_apply(adr_coefficients(lev, reaction="discrete"), one)
+        cont = adr_apply(adr_coefficients(lev), one)
+        scale = np.abs(ref[inner]).max() + 1.0 / (h * h)
+        np.testing.assert_allclose(disc[inner], ref[inner], rtol=0, atol=1e-11 * scale)
+        # the continuous term misses by (w h)^4 / (12 h^2) (cos^4 t + sin^4 t) to leading order
+        miss = np.abs(cont[inner] - ref[inner]).max()
+        want = (w * h) ** 4 / (12 * h * h) * (np.cos(t) ** 4 + np.sin(t) ** 4)
+        assert abs(miss - want) < 0.15 * want, (t, miss, want)
