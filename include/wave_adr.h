@@ -353,6 +353,27 @@ void mg_abi_sizes(size_t* params, size_t* instance, size_t* info);
 int mg_selftest_wait_timeout(mg_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Phase input on the device.  The ADR correction needs a travel time phi
+ * with |grad phi| ~ s (Section 3.2, eq. eikeq; the paper's phase network is
+ * trained on eikonal solutions, Section 3.2.1).  mg_eikonal computes the
+ * first-order Godunov discretisation of |grad tau| = s, tau(x0) = 0 on the
+ * n x n grid of the library (h = 1/(n+1), node (i, j) at ((i+1)h, (j+1)h),
+ * row-major tau[j*n + i]):
+ *   a = min(tau_W, tau_E), b = min(tau_S, tau_N) (missing neighbours: inf),
+ *   tau = min(a, b) + s h if |a - b| >= s h, else
+ *   tau = (a + b + sqrt(2 s^2 h^2 - (a - b)^2)) / 2,
+ * with the nodes within r_init of (x0, y0) fixed to s(x0)|x - x0| (s at the
+ * node nearest to the source).  It iterates until no value decreases by
+ * more than tol (absolute; 0 = until nothing changes), at most max_passes
+ * passes over the grid, and reports the passes in *passes (may be NULL).
+ * s (slowness, FP64, > 0) and tau (FP64) may be host or device memory; the
+ * call allocates its workspace and synchronises `stream`.  Returns MG_OK,
+ * MG_ENOTCONV (max_passes reached; tau holds the last iterate), MG_EINVAL
+ * (n < 2, no node within r_init, bad pointers), MG_ENOMEM or MG_ECUDA. */
+int mg_eikonal(int n, const double* s, double x0, double y0, double r_init, double tol, int max_passes, double* tau,
+               int* passes, mg_stream stream);
+
+/* ------------------------------------------------------------------------
  * Residual without allocation.  The paper has no counterpart of this entry
  * point; it exists for callers that may not allocate device memory: a plugin
  * inside a host program that owns the whole device through its own caching

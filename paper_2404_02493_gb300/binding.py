@@ -103,6 +103,7 @@ def load():
         "mg_peclet_flags": (ip, [vp, ip]),
         "mg_workspace_bytes": (ctypes.c_longlong, [vp]),
         "mg_level_roles": (ip, [ip, ctypes.POINTER(MgParams), ctypes.POINTER(ip), ctypes.POINTER(ip), ip]),
+        "mg_eikonal": (ip, [ip, vp, dp, dp, dp, dp, ip, vp, ctypes.POINTER(ip), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -121,7 +122,7 @@ def exported_symbols():
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
             "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
             "mg_tile_shapes", "mg_selftest_wait_timeout", "mg_peclet_flags",
-            "mg_workspace_bytes", "mg_level_roles"]
+            "mg_workspace_bytes", "mg_level_roles", "mg_eikonal"]
 
 
 class MgError(RuntimeError):
@@ -238,6 +239,18 @@ def mg_level_scalars(h, inst, level):
     if r < 0:
         _check(r, "mg_level_scalars")
     return {"lam_max": out[0], "alpha": out[1], "omega_j": out[2], "h": out[3], "peclet": out[4]}
+
+
+def mg_eikonal(n, s, x0, y0, tau, r_init=None, tol=1e-12, max_passes=100000, stream=None):
+    """Travel time of |grad tau| = s on the device (first-order Godunov);
+    returns (status, passes).  r_init defaults to 3 h."""
+    r_init = 3.0 / (n + 1) if r_init is None else r_init
+    np_ = ctypes.c_int()
+    rc = load().mg_eikonal(int(n), _ptr(s), float(x0), float(y0), float(r_init), float(tol), int(max_passes),
+                           _ptr(tau), ctypes.byref(np_), _stream(stream))
+    if rc not in (MG_OK, MG_ENOTCONV):
+        _check(rc, "mg_eikonal")
+    return rc, np_.value
 
 
 def mg_level_roles(n, params: MgParams):

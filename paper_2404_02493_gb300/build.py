@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwaveadr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["mg_api.cu", "setup.cu", "engine_f32.cu", "engine_f64.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["mg_api.cu", "setup.cu", "engine_f32.cu", "engine_f64.cu", "noalloc.cu", "adjoint.cu", "eikonal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 

@@ -1,7 +1,10 @@
-"""Parity at the benchmark's full size, in the launch configuration it times:
+"""Parity at the benchmark's full size, in the launch configurations it times:
 n = 4095, omega = 2000, the layered medium of the timed workload, complex-FP32
-cycles with M = 8 ADR corrections (n_cmax = 15, 9 levels), FGMRES(20) with an
-FP64 residual and update outside, CUDA graph and autotuned halo tiles.
+cycles (n_cmax = 15, 9 levels), FGMRES(20) with an FP64 residual and update
+outside, CUDA graph and autotuned halo tiles.  The throughput steps use the
+paper's M = 8 ADR corrections; the time-to-tolerance solve uses M = 2 with
+the absorbing ADR closure (mg_params.adr_bc), the configuration that
+converges at this size.
 
 The vectorised complex128 oracle handles this size in seconds to tens of
 seconds, so whole arrays are compared on the same inputs (the complex64
@@ -9,12 +12,13 @@ inputs of the library, widened):
 - one FP32 stencil (level-1 Helmholtz residual, level-2 ADR operator): 1e-6;
 - one GMRES(3) sweep and one Chebyshev smoothing (q = 5) at level 2: 1e-5;
 - one full Wave-ADR cycle from zero: the per-cycle tolerance 1e-5 of the mixed
-  form at n = 1023 (the same recipe, omega scaled to keep k h).  At n = 2047
-  and n = 4095 the measured deviation is up to 1.1e-5 and 1.2-3.8e-5 (it
-  depends on the tile shapes the autotuner picks), and the bounds are 5e-5
-  and 1e-4.  The deviation comes from the FP32 state of the ADR corrections:
-  without them (M = 0) the mixed cycle deviates 1e-7, and each correction
-  adds about 1e-6 at n = 1023; the cycle's amplification grows with n;
+  form.  It holds for the time-to-tolerance configuration at n = 4095
+  (2.6e-6 - 3.8e-6 measured) and for M = 8 at n = 1023.  With M = 8 at
+  n = 2047 and 4095 the cycle amplifies the residual (72x and 2700x per
+  cycle: the ADR corrections with the eikonal phase are not a convergent
+  iteration at these sizes) and the FP32 rounding of the corrections is
+  amplified with it: 1.1e-5 and 1.8e-5 - 3.8e-5.  Those cases keep the 1e-5
+  bound and are expected failures (strict: a pass would be reported);
 - 25 FGMRES iterations (one restart) through mg_solve_begin/steps/end: the
   relative residual the library reports equals the oracle's FP64 residual of
   the returned iterate to 1e-9 (with M = 8 on this medium the residual
@@ -102,27 +106,52 @@ def _cycle_rel(I, h, H):
     return rel(u32.astype(np.complex128), ref)
 
 
-def test_fullsize_cycle(full):
-    """One Wave-ADR cycle from zero on the normalised source against the
-    FP64 oracle cycle (the bound of the module docstring)."""
+AMPLIFYING = ("the paper's M = 8 corrections amplify the residual at this size with the eikonal phase, and the "
+              "FP32 rounding of the corrections with it")
+
+
+@pytest.mark.xfail(strict=True, reason=AMPLIFYING)
+def test_fullsize_cycle_m8(full):
+    """One Wave-ADR cycle of the timed steps (M = 8) from zero on the
+    normalised source against the FP64 oracle cycle, to the mixed form's
+    1e-5 per cycle."""
     I, h, H = full
     e = _cycle_rel(I, h, H)
-    print(f"cycle rel n=4095 {e:.2e}")
-    assert e < 1e-4, e
+    print(f"cycle rel n=4095 M=8 {e:.2e}")
+    assert e < 1e-5, e
 
 
-@pytest.mark.parametrize("n,bound", [(1023, 1e-5), (2047, 5e-5)])
-def test_smaller_cycles_of_the_same_recipe(n, bound):
+def test_fullsize_cycle_time_to_tolerance_configuration():
+    """The cycle of the time-to-tolerance solve (M = 2, absorbing ADR
+    closure, autotuned tiles) at n = 4095 against the FP64 oracle with the
+    same closure: 1e-5 per cycle."""
+    from oracle.cycle import CycleParams, Hierarchy
+    I = synth.config_layered(n=N, omega=OMEGA, seed=5)
+    h = lib_handle([I], "mixed", n_cmax=15, M=2, adr_bc="abc")
+    try:
+        H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=15, M=2, adr_bc="abc"))
+        e = _cycle_rel(I, h, H)
+    finally:
+        B.mg_destroy(h)
+    print(f"cycle rel n=4095 M=2 abc {e:.2e}")
+    assert e < 1e-5, e
+
+
+@pytest.mark.parametrize("n,M,closure", [
+    (1023, 8, "zero"), (2047, 2, "abc"),
+    pytest.param(2047, 8, "zero", marks=pytest.mark.xfail(strict=True, reason=AMPLIFYING))])
+def test_smaller_cycles_of_the_same_recipe(n, M, closure):
     """The same medium and recipe at n = 1023 and 2047 (omega scaled to keep
-    k h), with the bounds of the module docstring, for every halo-tile
-    candidate (each fixes a summation order of the Gram sums)."""
+    k h), to 1e-5 per cycle, for every halo-tile candidate (each fixes a
+    summation order of the Gram sums)."""
+    from oracle.cycle import CycleParams, Hierarchy
     I = synth.config_layered(n=n, omega=OMEGA * (n + 1) / (N + 1), seed=5)
-    H = oracle_hier(I, n_cmax=15, M=8)
+    H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=15, M=M, adr_bc=closure))
     g32 = (I.g / np.linalg.norm(I.g)).astype(np.complex64)
     ref = H.cycle(np.zeros_like(I.g), g32.astype(np.complex128))
     errs = []
     for cand in range(B.MG_TILE_CANDIDATES):
-        h = lib_handle([I], "mixed", n_cmax=15, M=8, tile_candidate=cand, autotune=0)
+        h = lib_handle([I], "mixed", n_cmax=15, M=M, adr_bc=closure, tile_candidate=cand, autotune=0)
         try:
             u32 = np.zeros_like(g32)
             B.mg_cycle(h, u32, g32, 1)
@@ -130,8 +159,8 @@ def test_smaller_cycles_of_the_same_recipe(n, bound):
             B.mg_destroy(h)
         assert np.all(np.isfinite(u32))
         errs.append(rel(u32.astype(np.complex128), ref))
-    print(f"cycle rel n={n} per tile candidate " + " ".join(f"{e:.2e}" for e in errs))
-    assert max(errs) < bound, errs
+    print(f"cycle rel n={n} M={M} {closure} per tile candidate " + " ".join(f"{e:.2e}" for e in errs))
+    assert max(errs) < 1e-5, errs
 
 
 def test_fullsize_fgmres_steps_report_the_true_residual(full):
