@@ -500,7 +500,7 @@ def test_wave_ray_sets_have_unit_plane_wave_gradients():
     M = 8
     H = Hierarchy(I.n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=7, M=M, ray=True))
     assert len(H.adr_sets) == M
-    for m, (coefs, mod, lu) in enumerate(H.adr_sets):
+    for m, (coefs, mod, lu, _) in enumerate(H.adr_sets):
         th = 2 * np.pi * m / M
         for l, c in coefs.items():
             assert np.allclose(c.phix, np.cos(th), atol=1e-11, rtol=0)
