@@ -329,7 +329,8 @@ def adjoint_leg(B, torch, dev, st, batch):
             "batch": batch, "K": 8, "backward_seconds": t_bwd, "forward_seconds": t_fwd,
             "value": batch * 8 / t_bwd, "unit": "instance-cycle adjoints/s",
             "backward_over_forward": t_bwd / t_fwd if t_fwd > 0 else None,
-            "note": "wall clock of one mg_cycle_backward call (host-driven reverse sweep, instance by instance)"}
+            "note": "wall clock of one mg_cycle_backward call: every instance's reverse sweep on its own stream, "
+                    "the first reverse step eager, the others replaying it as a CUDA graph"}
 
 
 def precision_leg(B, torch, dev, st, n=1023, omega=500.0):

@@ -28,6 +28,7 @@
 #include <complex>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -123,9 +124,16 @@ __global__ void ka_prolong(int nf, int pf, int nc, int pc, const double2* e, dou
     y[p] = acc ? dadd(y[p], v) : v;
 }
 
+// up to 8 (x, y) vector pairs of a dot-product launch, passed by value
+struct DotPtrs {
+    const double2* x[8];
+    const double2* y[8];
+};
+
 // block partials of up to 8 dot products sum conj(x_k) y_k
-__global__ void ka_dots(int n, int pitch, int npair, const double2* const* xs, const double2* const* ys,
-                        double2* part) {
+__global__ void ka_dots(int n, int pitch, int npair, DotPtrs P, double2* part) {
+    const double2* const* xs = P.x;
+    const double2* const* ys = P.y;
     __shared__ double2 sh[8 * 8];
     double2 acc[8];
 #pragma unroll
@@ -142,6 +150,115 @@ __global__ void ka_dots(int n, int pitch, int npair, const double2* const* xs, c
     if (threadIdx.x == 0)
         for (int k = 0; k < 8; ++k) part[blockIdx.x * 8 + k] = acc[k];
 }
+
+// the nb block partials of a ka_dots launch summed in block order: out[k]
+__global__ void ka_dots_fin(const double2* part, int nb, int np, double2* out) {
+    __shared__ double2 sh[8 * 8];
+    double2 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_double2(0, 0);
+    for (int b = threadIdx.x; b < nb; b += ANT)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < np) acc[k] = dadd(acc[k], part[b * 8 + k]);
+    block_sum<double2, 8>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < np; ++k) out[k] = acc[k];
+}
+
+// complex 3 x 3 solve, Gaussian elimination with partial pivoting (largest
+// modulus), as the least-squares step of GMRES(3) needs it
+__device__ inline void solve3_dev(const double2 (&G)[3][3], const double2* z, double2* c) {
+    double2 M[3][4];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) M[i][j] = G[i][j];
+        M[i][3] = z[i];
+    }
+    for (int k = 0; k < 3; ++k) {
+        int pv = k;
+        for (int i = k + 1; i < 3; ++i)
+            if (dabs2(M[i][k]) > dabs2(M[pv][k])) pv = i;
+        for (int j = 0; j < 4; ++j) {
+            const double2 t = M[k][j];
+            M[k][j] = M[pv][j];
+            M[pv][j] = t;
+        }
+        for (int i = k + 1; i < 3; ++i) {
+            const double2 f = ddiv(M[i][k], M[k][k]);
+            for (int j = k; j < 4; ++j) M[i][j] = dsub(M[i][j], dmul(f, M[k][j]));
+        }
+    }
+    for (int i = 2; i >= 0; --i) {
+        double2 sm = M[i][3];
+        for (int j = i + 1; j < 3; ++j) sm = dsub(sm, dmul(M[i][j], c[j]));
+        c[i] = ddiv(sm, M[i][i]);
+    }
+}
+__device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// GMRES(3) least squares from the dots d1 = (<w0,w0>, <w0,w1>, <w0,w2>,
+// <w1,w1>, <w1,w2>, <w2,w2>, <w0,r0>, <w1,r0>) and d2 = <w2,r0>: the tape's
+// scalars t = (c[3], G[9] row-major, z[3], zero flag); c = 0 when r0 = 0.
+__global__ void ka_gm_solve(const double2* d1, const double2* d2, double2* t) {
+    double2 G[3][3];
+    G[0][0] = d1[0]; G[0][1] = d1[1]; G[0][2] = d1[2];
+    G[1][1] = d1[3]; G[1][2] = d1[4]; G[2][2] = d1[5];
+    G[1][0] = dconj(G[0][1]); G[2][0] = dconj(G[0][2]); G[2][1] = dconj(G[1][2]);
+    const double2 z[3] = {d1[6], d1[7], d2[0]};
+    const bool zero = !(sqrt(dabs2(G[0][0])) > 0);
+    double2 c[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    if (!zero) solve3_dev(G, z, c);
+    for (int k = 0; k < 3; ++k) t[k] = c[k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) t[3 + 3 * i + j] = G[i][j];
+    for (int k = 0; k < 3; ++k) t[12 + k] = z[k];
+    t[15] = make_double2(zero ? 1.0 : 0.0, 0.0);
+}
+
+// Adjoint coefficients of GMRES(3) from the tape t and cb_q = <k_q, xbar>:
+// zb = G^{-H} cb, Gb = -zb c^H and
+//   o[q]            conj(c_q)                   (kbar_q = conj(c_q) xbar)
+//   o[3 + i]        zb_i                        (r0bar = sum_i w_i zb_i)
+//   o[6 + 4q + i]   Gb[i][q] + conj(Gb[q][i])   (wbar_q = sum_i w_i (.) + r0 conj(zb_q))
+//   o[9 + 4q]       conj(zb_q)
+// all zero when the forward sweep had r0 = 0.
+__global__ void ka_gm_back(const double2* t, const double2* cb, double2* o) {
+    for (int k = 0; k < 18; ++k) o[k] = make_double2(0, 0);
+    if (t[15].x != 0.0) return;
+    double2 GH[3][3], c[3], zb[3], Gb[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) GH[i][j] = dconj(t[3 + 3 * j + i]);
+    for (int k = 0; k < 3; ++k) c[k] = t[k];
+    const double2 cbv[3] = {cb[0], cb[1], cb[2]};
+    solve3_dev(GH, cbv, zb);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Gb[i][j] = dsc(dmul(zb[i], dconj(c[j])), -1.0);
+    for (int q = 0; q < 3; ++q) {
+        o[q] = dconj(c[q]);
+        o[3 + q] = zb[q];
+        for (int i = 0; i < 3; ++i) o[6 + 4 * q + i] = dadd(Gb[i][q], dconj(Gb[q][i]));
+        o[9 + 4 * q] = dconj(zb[q]);
+    }
+}
+
+// out (+)= sum_t c_t x_t with c_t read from device memory (cp_t) when
+// cp_t is set, else the immediate value
+__global__ void ka_lincomb_p(int n, int pitch, double2* out, int acc, const double2* x0, const double2* c0p,
+                             double2 c0, const double2* x1, const double2* c1p, double2 c1, const double2* x2,
+                             const double2* c2p, double2 c2, const double2* x3, const double2* c3p, double2 c3) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, i, j)) return;
+    const long long p = (long long)j * pitch + i;
+    double2 v = acc ? out[p] : make_double2(0, 0);
+    if (x0) v = dadd(v, dmul(c0p ? *c0p : c0, x0[p]));
+    if (x1) v = dadd(v, dmul(c1p ? *c1p : c1, x1[p]));
+    if (x2) v = dadd(v, dmul(c2p ? *c2p : c2, x2[p]));
+    if (x3) v = dadd(v, dmul(c3p ? *c3p : c3, x3[p]));
+    out[p] = v;
+}
+
+// dst += scale Re(src)  (weight gradients accumulated on the device)
+__global__ void ka_accum_re(double* dst, const double2* src, double scale) { dst[0] += scale * src[0].x; }
 
 // ADR coefficient gradients of y = s L a with cotangent ybar:
 // qbar = (phix_bar, phiy_bar, d_bar.re, d_bar.im) per node.
@@ -231,7 +348,6 @@ struct AdjLevel {
     double* qbar = nullptr;       // ADR coefficient gradients (4 per node)
     double2* mbar = nullptr;      // modulation gradient (level 2)
     double kscale = 1.0;          // fixed Krylov basis scale of this level
-    double cbar1[16], cbar2[16];  // Chebyshev coefficient gradients
 };
 
 struct Adjoint {
@@ -241,9 +357,10 @@ struct Adjoint {
     std::vector<AdjLevel> lv;
     std::vector<double2*> all;
     double2* part = nullptr;
-    const double2** dptrs = nullptr;
-    double2* hpart = nullptr;
-    double wj_bar = 0;
+    double2* arena = nullptr;      // device scalars of one reverse step (bump allocated)
+    int arena_top = 0;
+    static constexpr int ARENA = 1 << 16;
+    double* wsum = nullptr;        // device: [0] d/d omega_J, [l] d/d alpha_l
     int err = 0;
 
     Adjoint(Handle& h, InstHost& inst, cudaStream_t s) : H(h), I(inst), st(s) {}
@@ -254,8 +371,8 @@ struct Adjoint {
             cudaFree(L.mbar);
         }
         cudaFree(part);
-        cudaFree((void*)dptrs);
-        cudaFreeHost(hpart);
+        cudaFree(arena);
+        cudaFree(wsum);
     }
 
     int blocks(int n) const { return (int)(((long long)n * n + ANT - 1) / ANT); }
@@ -278,11 +395,11 @@ struct Adjoint {
                 if (cudaMalloc(&L.mbar, sizeof(double2) * L.n * L.n) != cudaSuccess) return MG_ENOMEM;
                 cudaMemsetAsync(L.mbar, 0, sizeof(double2) * L.n * L.n, st);
             }
-            for (int m = 0; m < 16; ++m) L.cbar1[m] = L.cbar2[m] = 0;
         }
         if (cudaMalloc(&part, sizeof(double2) * 8 * 1024) != cudaSuccess) return MG_ENOMEM;
-        if (cudaMalloc((void**)&dptrs, sizeof(double2*) * 16) != cudaSuccess) return MG_ENOMEM;
-        if (cudaMallocHost(&hpart, sizeof(double2) * 8 * 1024) != cudaSuccess) return MG_ENOMEM;
+        if (cudaMalloc(&arena, sizeof(double2) * ARENA) != cudaSuccess) return MG_ENOMEM;
+        if (cudaMalloc(&wsum, sizeof(double) * (MG_MAX_LEVELS + 1)) != cudaSuccess) return MG_ENOMEM;
+        cudaMemsetAsync(wsum, 0, sizeof(double) * (MG_MAX_LEVELS + 1), st);
         return MG_OK;
     }
 
@@ -308,6 +425,7 @@ struct Adjoint {
     }
     // after one cycle's reverse sweep every vector is free again
     void reset() {
+        arena_top = 0;
         for (auto& L : lv) L.pool = L.owned;
         for (void* t : tapes) delete_tape(t);
         tapes.clear();
@@ -345,24 +463,39 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         ka_adr_grad<<<blocks(L.n), ANT, 0, st>>>(L.d, ybar, a, s, L.qbar);
     }
-    // conj(x_k)^T y_k for up to 8 pairs (synchronises)
-    std::vector<cd> dots(int l, std::vector<std::pair<const double2*, const double2*>> pr) {
+    // k device scalars of this reverse step
+    double2* scalars(int k) {
+        if (arena_top + k > ARENA) {
+            err = MG_ENOMEM;
+            arena_top = 0;
+        }
+        double2* p = arena + arena_top;
+        arena_top += (k + 1) & ~1;
+        return p;
+    }
+    // conj(x_k)^T y_k for up to 8 pairs into device scalars (no synchronisation)
+    double2* dots(int l, std::vector<std::pair<const double2*, const double2*>> pr) {
         AdjLevel& L = lv[l];
         const int np = (int)pr.size();
-        const double2* h[16];
+        DotPtrs P;
         for (int k = 0; k < 8; ++k) {
-            h[k] = k < np ? pr[k].first : pr[0].first;
-            h[8 + k] = k < np ? pr[k].second : pr[0].second;
+            P.x[k] = k < np ? pr[k].first : pr[0].first;
+            P.y[k] = k < np ? pr[k].second : pr[0].second;
         }
-        cudaMemcpyAsync((void*)dptrs, h, sizeof(h), cudaMemcpyHostToDevice, st);
         const int nb = std::min(blocks(L.n), 1024);
-        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, dptrs, dptrs + 8, part);
-        cudaMemcpyAsync(hpart, part, sizeof(double2) * 8 * nb, cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
-        std::vector<cd> out(np, 0.0);
-        for (int b = 0; b < nb; ++b)
-            for (int k = 0; k < np; ++k) out[k] += cd(hpart[b * 8 + k].x, hpart[b * 8 + k].y);
+        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, P, part);
+        double2* out = scalars(np);
+        ka_dots_fin<<<1, ANT, 0, st>>>(part, nb, np, out);
         return out;
+    }
+    // out (+)= sum_t cp_t x_t, coefficients in device memory
+    void lin_dev(int l, double2* out, bool acc, const double2* x0, const double2* c0p, const double2* x1 = nullptr,
+                 const double2* c1p = nullptr, const double2* x2 = nullptr, const double2* c2p = nullptr,
+                 const double2* x3 = nullptr, const double2* c3p = nullptr, double2 c3 = make_double2(0, 0)) {
+        AdjLevel& L = lv[l];
+        const double2 z = make_double2(0, 0);
+        ka_lincomb_p<<<blocks(L.n), ANT, 0, st>>>(L.n, L.pitch, out, acc, x0, c0p, z, x1, c1p, z, x2, c2p, z, x3,
+                                                  c3p, c3);
     }
 
     // ----- Chebyshev coefficients and their alpha-derivatives (dual numbers)
@@ -397,10 +530,7 @@ struct Adjoint {
     struct GmTape {
         double2 *r0 = nullptr, *x0 = nullptr, *b = nullptr;   // x0 null: from zero (r0 = b)
         double2 *k[3] = {nullptr, nullptr, nullptr}, *w[3] = {nullptr, nullptr, nullptr};
-        cd c[3] = {0, 0, 0};
-        cd G[3][3];
-        cd z[3];
-        bool zero = false;
+        double2* sc = nullptr;   // device: c[3], G[9], z[3], zero flag (ka_gm_solve)
     };
     struct AdrTape {
         int l;
@@ -445,61 +575,25 @@ struct Adjoint {
         apply(l, 2, T.k[1], T.w[1], 1.0);
         lin(l, T.k[2], false, T.w[1], s);
         apply(l, 2, T.k[2], T.w[2], 1.0);
-        auto d1 = dots(l, {{T.w[0], T.w[0]}, {T.w[0], T.w[1]}, {T.w[0], T.w[2]}, {T.w[1], T.w[1]},
-                           {T.w[1], T.w[2]}, {T.w[2], T.w[2]}, {T.w[0], T.r0}, {T.w[1], T.r0}});
-        auto d2 = dots(l, {{T.w[2], T.r0}});
-        T.G[0][0] = d1[0]; T.G[0][1] = d1[1]; T.G[0][2] = d1[2];
-        T.G[1][1] = d1[3]; T.G[1][2] = d1[4]; T.G[2][2] = d1[5];
-        T.G[1][0] = std::conj(T.G[0][1]); T.G[2][0] = std::conj(T.G[0][2]); T.G[2][1] = std::conj(T.G[1][2]);
-        T.z[0] = d1[6]; T.z[1] = d1[7]; T.z[2] = d2[0];
-        T.zero = !(std::abs(T.G[0][0]) > 0);
-        if (!T.zero) solve3(T.G, T.z, T.c);
+        double2* d1 = dots(l, {{T.w[0], T.w[0]}, {T.w[0], T.w[1]}, {T.w[0], T.w[2]}, {T.w[1], T.w[1]},
+                               {T.w[1], T.w[2]}, {T.w[2], T.w[2]}, {T.w[0], T.r0}, {T.w[1], T.r0}});
+        double2* d2 = dots(l, {{T.w[2], T.r0}});
+        T.sc = scalars(16);
+        ka_gm_solve<<<1, 1, 0, st>>>(d1, d2, T.sc);
         // x = x0 + K c
-        lin(l, x, false, T.k[0], T.c[0], T.k[1], T.c[1], T.k[2], T.c[2], x0, 1.0);
-    }
-
-    static void solve3(const cd G[3][3], const cd* z, cd* c) {
-        cd M[3][4];
-        for (int i = 0; i < 3; ++i) {
-            for (int j = 0; j < 3; ++j) M[i][j] = G[i][j];
-            M[i][3] = z[i];
-        }
-        for (int k = 0; k < 3; ++k) {
-            int pv = k;
-            for (int i = k + 1; i < 3; ++i)
-                if (std::abs(M[i][k]) > std::abs(M[pv][k])) pv = i;
-            for (int j = 0; j < 4; ++j) std::swap(M[k][j], M[pv][j]);
-            for (int i = k + 1; i < 3; ++i) {
-                const cd f = M[i][k] / M[k][k];
-                for (int j = k; j < 4; ++j) M[i][j] -= f * M[k][j];
-            }
-        }
-        for (int i = 2; i >= 0; --i) {
-            cd s = M[i][3];
-            for (int j = i + 1; j < 3; ++j) s -= M[i][j] * c[j];
-            c[i] = s / M[i][i];
-        }
+        lin_dev(l, x, false, T.k[0], T.sc + 0, T.k[1], T.sc + 1, T.k[2], T.sc + 2, x0, nullptr, make_double2(1, 0));
     }
 
     // reverse of gm_forward: xbar given; adds to bbar, x0bar (if x0), ADR gradients
+    // (with r0 = 0 in the forward sweep every coefficient is zero and the
+    // sweep below reduces to x0bar += xbar)
     void gm_backward(int l, GmTape& T, double2* xbar, double2* bbar, double2* x0bar) {
-        if (T.zero) {
-            if (x0bar) lin(l, x0bar, true, xbar, 1.0);
-            return;
-        }
         AdjLevel& L = lv[l];
         const double s = L.kscale;
-        // x = x0 + K c
-        auto cb = dots(l, {{T.k[0], xbar}, {T.k[1], xbar}, {T.k[2], xbar}});
-        // c = G^{-1} z: zbar = G^{-H} cbar, Gbar = -zbar c^H
-        cd GH[3][3];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) GH[i][j] = std::conj(T.G[j][i]);
-        cd zb[3];
-        solve3(GH, cb.data(), zb);
-        cd Gb[3][3];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) Gb[i][j] = -zb[i] * std::conj(T.c[j]);
+        // x = x0 + K c; c = G^{-1} z: zbar = G^{-H} cbar, Gbar = -zbar c^H
+        double2* cb = dots(l, {{T.k[0], xbar}, {T.k[1], xbar}, {T.k[2], xbar}});
+        double2* co = scalars(18);
+        ka_gm_back<<<1, 1, 0, st>>>(T.sc, cb, co);
         double2* r0b = get(l);
         double2* kb[3];
         double2* wb[3];
@@ -508,16 +602,13 @@ struct Adjoint {
             wb[q] = get(l);
         }
         // kbar_j = conj(c_j) xbar
-        for (int q = 0; q < 3; ++q) lin(l, kb[q], false, xbar, std::conj(T.c[q]));
+        for (int q = 0; q < 3; ++q) lin_dev(l, kb[q], false, xbar, co + q);
         // z_i = w_i^H r0: r0bar += sum_i w_i zbar_i ; wbar_i += r0 conj(zbar_i)
-        lin(l, r0b, false, T.w[0], zb[0], T.w[1], zb[1], T.w[2], zb[2]);
+        lin_dev(l, r0b, false, T.w[0], co + 3, T.w[1], co + 4, T.w[2], co + 5);
         // G_ij = w_i^H w_j: wbar_j += sum_i w_i Gbar_ij ; wbar_i += sum_j w_j conj(Gbar_ij)
-        for (int q = 0; q < 3; ++q) {
-            cd a0 = Gb[0][q] + std::conj(Gb[q][0]);
-            cd a1 = Gb[1][q] + std::conj(Gb[q][1]);
-            cd a2 = Gb[2][q] + std::conj(Gb[q][2]);
-            lin(l, wb[q], false, T.w[0], a0, T.w[1], a1, T.w[2], a2, T.r0, std::conj(zb[q]));
-        }
+        for (int q = 0; q < 3; ++q)
+            lin_dev(l, wb[q], false, T.w[0], co + 6 + 4 * q, T.w[1], co + 7 + 4 * q, T.w[2], co + 8 + 4 * q, T.r0,
+                    co + 9 + 4 * q);
         // w_q = L k_q
         for (int q = 0; q < 3; ++q) {
             apply(l, 4, wb[q], kb[q], 1.0, true);
@@ -662,14 +753,15 @@ struct Adjoint {
                 lin(l, t, false, T.g, 1.0);
             }
             apply(l, 1, t, s, 1.0);
-            // d_m = c1 d_{m-1} + c2 s_m
-            auto dd = dots(l, {{s, db}});
-            L.cbar2[m] += dd[0].real();
+            // d_m = c1 d_{m-1} + c2 s_m; alpha_bar += Re<s_m, d_m bar> dc2/dalpha
+            //                                       + Re<d_{m-1}, d_m bar> dc1/dalpha
+            double2* dd = dots(l, {{s, db}});
+            ka_accum_re<<<1, 1, 0, st>>>(wsum + l, dd, d2[m]);
             if (m > 0) {
                 // d_{m-1} = x_m - x_{m-1}
                 lin(l, dprev, false, T.x[m], 1.0, T.x[m - 1], -1.0);
-                auto d2v = dots(l, {{dprev, db}});
-                L.cbar1[m] += d2v[0].real();
+                double2* d2v = dots(l, {{dprev, db}});
+                ka_accum_re<<<1, 1, 0, st>>>(wsum + l, d2v, d1[m]);
             }
             lin(l, sb, false, db, c2[m]);
             // s = A^H t, t = g - A x_m: t_bar = A s_bar
@@ -679,18 +771,12 @@ struct Adjoint {
             // d_{m-1} bar = c1 d_m bar
             if (m > 0) lin(l, db, false, db, c1[m]);
         }
-        // alpha gradient from the coefficient gradients
-        double ab = 0;
-        for (int m = 0; m < q; ++m) ab += L.cbar1[m] * d1[m] + L.cbar2[m] * d2[m];
-        alpha_bar[l] += ab;
-        for (int m = 0; m < 16; ++m) L.cbar1[m] = L.cbar2[m] = 0;
         put(l, db);
         put(l, dprev);
         put(l, s);
         put(l, t);
         put(l, sb);
     }
-    double alpha_bar[MG_MAX_LEVELS + 1] = {0};
 
     // ----- wave cycle
     bool is_cheb(int l) const { return I.lv[l - 1].cheb; }
@@ -798,8 +884,7 @@ struct Adjoint {
         double2* t = get(l);
         if (l == 1) {
             // u_out = u2 + wj v2, v2 = D^{-1}(g - A u2)
-            auto dv = dots(l, {{T->v2, uob}});
-            wj_bar += dv[0].real();
+            ka_accum_re<<<1, 1, 0, st>>>(wsum, dots(l, {{T->v2, uob}}), 1.0);
             lin(l, u2b, false, uob, 1.0);
             diag(l, uob, t, true, wj, false);        // t = wj D^{-H} ubar
             lin(l, gbar, true, t, 1.0);
@@ -851,8 +936,7 @@ struct Adjoint {
             apply(l, 1, rb, ub, -1.0, true);
             if (l == 1) {
                 // u1 = u_in + wj v1, v1 = D^{-1}(g - A u_in)
-                auto dv = dots(l, {{T->v1, ub}});
-                wj_bar += dv[0].real();
+                ka_accum_re<<<1, 1, 0, st>>>(wsum, dots(l, {{T->v1, ub}}), 1.0);
                 if (uib) lin(l, uib, true, ub, 1.0);
                 diag(l, ub, t, true, wj, false);
                 lin(l, gbar, true, t, 1.0);
@@ -1010,61 +1094,134 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
                                        cudaMemcpyDeviceToDevice, st));
         }
     }
-    // ---- reverse sweep per instance
+    // ---- reverse sweep: every instance on a stream of its own.  The sweep
+    // has no host synchronisation, so one step of an instance is a fixed
+    // launch sequence on fixed buffers: the first step runs eagerly (it fills
+    // the vector pools), the next is captured into a CUDA graph, and the other
+    // K - 2 steps replay it.  The instances' streams run concurrently.
+    std::vector<cudaStream_t> ss(ni, nullptr);
+    std::vector<std::unique_ptr<Adjoint>> adj(ni);
+    std::vector<cudaGraphExec_t> gexec(ni, nullptr);
+    struct Bufs { double2 *ub, *ubin, *uin, *gd, *gbar, *uout; };
+    std::vector<Bufs> bf(ni);
+    auto cleanup_all = [&]() {
+        for (int b = 0; b < ni; ++b) {
+            if (ss[b]) cudaStreamSynchronize(ss[b]);
+            if (gexec[b]) cudaGraphExecDestroy(gexec[b]);
+            adj[b].reset();
+            if (ss[b]) cudaStreamDestroy(ss[b]);
+        }
+        cleanup();
+    };
     for (int b = 0; b < ni; ++b) {
         InstHost& I = H.inst[b];
         LevelHost& l1 = I.lv[0];
-        Adjoint A(H, I, st);
-        int rc = A.init();
-        if (rc) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return rc; }
-        double2* ub = dalloc(sizeof(double2) * l1.slot_stride);
-        double2* ubin = dalloc(sizeof(double2) * l1.slot_stride);
-        double2* gd = dalloc(sizeof(double2) * l1.slot_stride);
-        double2* gbar = dalloc(sizeof(double2) * l1.slot_stride);
-        double2* uout = dalloc(sizeof(double2) * l1.slot_stride);
-        if (!ub || !ubin || !gd || !gbar || !uout) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return MG_ENOMEM; }
-        WADR_CHECK(cp2d(ub, l1.pitch, (const char*)gbar_uK + I.off * 16, l1.n, l1.n));
-        WADR_CHECK(cp2d(gd, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n));
-        for (int k = K - 1; k >= 0; --k) {
-            Adjoint::WaveTape* T = A.wave_forward(1, ck[b][k], gd, uout);
-            WADR_CHECK(cudaMemsetAsync(ubin, 0, sizeof(double2) * l1.slot_stride, st));
-            A.wave_backward(T, ub, ubin, gbar);
-            std::swap(ub, ubin);
-            if (A.err) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return A.err; }
-            WADR_CHECK(cudaGetLastError());
-            A.reset();
+        Bufs& B = bf[b];
+        B.ub = dalloc(sizeof(double2) * l1.slot_stride);
+        B.ubin = dalloc(sizeof(double2) * l1.slot_stride);
+        B.uin = dalloc(sizeof(double2) * l1.slot_stride);
+        B.gd = dalloc(sizeof(double2) * l1.slot_stride);
+        B.gbar = dalloc(sizeof(double2) * l1.slot_stride);
+        B.uout = dalloc(sizeof(double2) * l1.slot_stride);
+        if (!B.ub || !B.ubin || !B.uin || !B.gd || !B.gbar || !B.uout) {
+            cleanup_all();
+            set_error("mg_cycle_backward: out of device memory");
+            return MG_ENOMEM;
         }
+        WADR_CHECK(cp2d(B.ub, l1.pitch, (const char*)gbar_uK + I.off * 16, l1.n, l1.n));
+        WADR_CHECK(cp2d(B.gd, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n));
+    }
+    cudaEvent_t ev_ready = nullptr;
+    WADR_CHECK(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+    WADR_CHECK(cudaEventRecord(ev_ready, st));
+    int rc = MG_OK;
+    for (int b = 0; b < ni && !rc; ++b) {
+        if (cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking) != cudaSuccess) { rc = MG_ECUDA; break; }
+        cudaStreamWaitEvent(ss[b], ev_ready, 0);
+        adj[b].reset(new Adjoint(H, H.inst[b], ss[b]));
+        if (adj[b]->init()) rc = MG_ENOMEM;
+    }
+    // one reverse step of instance b from the checkpoint in B.uin
+    auto step = [&](int b) {
+        Adjoint& A = *adj[b];
+        Bufs& B = bf[b];
+        const size_t bytes = sizeof(double2) * H.inst[b].lv[0].slot_stride;
+        Adjoint::WaveTape* T = A.wave_forward(1, B.uin, B.gd, B.uout);
+        cudaMemsetAsync(B.ubin, 0, bytes, ss[b]);
+        A.wave_backward(T, B.ub, B.ubin, B.gbar);
+        cudaMemcpyAsync(B.ub, B.ubin, bytes, cudaMemcpyDeviceToDevice, ss[b]);
+        A.reset();
+    };
+    // first step of every instance (eager), then the captured step
+    for (int b = 0; b < ni && !rc; ++b) {
+        const size_t bytes = sizeof(double2) * H.inst[b].lv[0].slot_stride;
+        cudaMemcpyAsync(bf[b].uin, ck[b][K - 1], bytes, cudaMemcpyDeviceToDevice, ss[b]);
+        step(b);
+        if (adj[b]->err) rc = adj[b]->err;
+    }
+    for (int b = 0; b < ni && !rc && K > 1; ++b) {
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(ss[b], cudaStreamCaptureModeRelaxed) != cudaSuccess) { rc = MG_ECUDA; break; }
+        step(b);
+        if (cudaStreamEndCapture(ss[b], &gr) != cudaSuccess || !gr) { rc = MG_ECUDA; break; }
+        const cudaError_t ie = cudaGraphInstantiate(&gexec[b], gr, 0);
+        cudaGraphDestroy(gr);
+        if (ie != cudaSuccess || adj[b]->err) rc = adj[b]->err ? adj[b]->err : MG_ECUDA;
+    }
+    for (int k = K - 2; k >= 0 && !rc; --k)
+        for (int b = 0; b < ni; ++b) {
+            const size_t bytes = sizeof(double2) * H.inst[b].lv[0].slot_stride;
+            cudaMemcpyAsync(bf[b].uin, ck[b][k], bytes, cudaMemcpyDeviceToDevice, ss[b]);
+            if (cudaGraphLaunch(gexec[b], ss[b]) != cudaSuccess) { rc = MG_ECUDA; break; }
+        }
+    if (rc) {
+        const cudaError_t e = cudaGetLastError();
+        cudaEventDestroy(ev_ready);
+        cleanup_all();
+        set_error(rc == MG_ENOMEM ? std::string("mg_cycle_backward: out of device memory")
+                                  : std::string("mg_cycle_backward: ") + cudaGetErrorString(e));
+        return rc;
+    }
+    // gradients of every instance, in instance order on its own stream
+    for (int b = 0; b < ni; ++b) {
+        InstHost& I = H.inst[b];
+        LevelHost& l1 = I.lv[0];
+        Adjoint& A = *adj[b];
+        cudaStream_t sb = ss[b];
+        double2* ub = bf[b].ub;
         if (grad_u0) {
             // grad_u0 += ub
             std::vector<double2> hu((size_t)l1.n * l1.n), hg((size_t)l1.n * l1.n);
             WADR_CHECK(cudaMemcpy2DAsync(hu.data(), (size_t)l1.n * 16, ub, (size_t)l1.pitch * 16, (size_t)l1.n * 16,
-                                         l1.n, cudaMemcpyDeviceToHost, st));
-            WADR_CHECK(cudaMemcpyAsync(hg.data(), (const char*)grad_u0 + I.off * 16, hg.size() * 16, cudaMemcpyDefault, st));
-            WADR_CHECK(cudaStreamSynchronize(st));
+                                         l1.n, cudaMemcpyDeviceToHost, sb));
+            WADR_CHECK(cudaMemcpyAsync(hg.data(), (const char*)grad_u0 + I.off * 16, hg.size() * 16, cudaMemcpyDefault, sb));
+            WADR_CHECK(cudaStreamSynchronize(sb));
             for (size_t q = 0; q < hu.size(); ++q) { hg[q].x += hu[q].x; hg[q].y += hu[q].y; }
-            WADR_CHECK(cudaMemcpyAsync((char*)grad_u0 + I.off * 16, hg.data(), hg.size() * 16, cudaMemcpyDefault, st));
+            WADR_CHECK(cudaMemcpyAsync((char*)grad_u0 + I.off * 16, hg.data(), hg.size() * 16, cudaMemcpyDefault, sb));
         }
         if (grad_weights) {
             // grad_weights may be host or device memory: read, accumulate, write back
-            double gw[MG_MAX_LEVELS];
+            double gw[MG_MAX_LEVELS], ws[MG_MAX_LEVELS + 1];
             double* gdst = grad_weights + (size_t)b * MG_MAX_LEVELS;
-            WADR_CHECK(cudaMemcpyAsync(gw, gdst, sizeof(gw), cudaMemcpyDefault, st));
-            WADR_CHECK(cudaStreamSynchronize(st));
-            gw[0] += A.wj_bar;
-            for (int l = 2; l <= I.L; ++l) gw[l - 1] += A.alpha_bar[l];
-            WADR_CHECK(cudaMemcpyAsync(gdst, gw, sizeof(gw), cudaMemcpyDefault, st));
-            WADR_CHECK(cudaStreamSynchronize(st));
+            WADR_CHECK(cudaMemcpyAsync(gw, gdst, sizeof(gw), cudaMemcpyDefault, sb));
+            WADR_CHECK(cudaMemcpyAsync(ws, A.wsum, sizeof(ws), cudaMemcpyDeviceToHost, sb));
+            WADR_CHECK(cudaStreamSynchronize(sb));
+            gw[0] += ws[0];
+            for (int l = 2; l <= I.L; ++l) gw[l - 1] += ws[l];
+            WADR_CHECK(cudaMemcpyAsync(gdst, gw, sizeof(gw), cudaMemcpyDefault, sb));
+            WADR_CHECK(cudaStreamSynchronize(sb));
         }
         if (grad_phi) {
             std::vector<double> gp((size_t)I.n * I.n);
-            WADR_CHECK(cudaMemcpyAsync(gp.data(), grad_phi + I.off, gp.size() * 8, cudaMemcpyDefault, st));
-            WADR_CHECK(cudaStreamSynchronize(st));
-            chain_to_phi(I, A.lv, st, gp.data());
-            WADR_CHECK(cudaMemcpyAsync(grad_phi + I.off, gp.data(), gp.size() * 8, cudaMemcpyDefault, st));
+            WADR_CHECK(cudaMemcpyAsync(gp.data(), grad_phi + I.off, gp.size() * 8, cudaMemcpyDefault, sb));
+            WADR_CHECK(cudaStreamSynchronize(sb));
+            chain_to_phi(I, A.lv, sb, gp.data());
+            WADR_CHECK(cudaMemcpyAsync(grad_phi + I.off, gp.data(), gp.size() * 8, cudaMemcpyDefault, sb));
         }
-        WADR_CHECK(cudaStreamSynchronize(st));
+        WADR_CHECK(cudaStreamSynchronize(sb));
     }
-    cleanup();
+    cudaEventDestroy(ev_ready);
+    cleanup_all();
     WADR_CHECK(cudaGetLastError());
     return MG_OK;
 }
