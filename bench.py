@@ -4,19 +4,22 @@
 Workload: n = 4095 x 4095 interior points, omega = 2000 (k up to 2000,
 k h <= 0.49), six smoothed horizontal layers c in [1.5, 4.5] times
 (1 + 0.1 GRF), centred Gaussian source, eikonal phase; complex-FP32 Wave-ADR
-cycles (n_cmax = 15: 9 levels; M = 8 ADR corrections) as the flexible
-preconditioner of FGMRES(20) whose residual and solution update are FP64
-(the mixed form).
+cycles (n_cmax = 15: 9 levels) as the flexible preconditioner of FGMRES(20)
+whose residual and solution update are FP64 (the mixed form), with M = 2 ADR
+corrections and the absorbing ADR boundary closure: the configuration that
+reaches the 1e-6 tolerance at this size.  (The paper's M = 8 amplifies the
+residual here with the eikonal phase; its step rate is reported as the leg
+paper_M8.)
 
 A step is one FGMRES iteration: one Wave-ADR cycle (all of Algorithm 1:
-Jacobi, Chebyshev, transfers, 8 ADR corrections with their GMRES(3)
+Jacobi, Chebyshev, transfers, the ADR corrections with their GMRES(3)
 V-cycles, coarsest LU) on the current Krylov vector, the product with A and
 the Gram-Schmidt step; every 20 steps the FP64 update and residual.
 `value` = cycles per second over all ranks (each rank solves its own
 replica; the single solve does not shard).  Also reported: time to 1e-6
-relative residual, an end-to-end rate through the C ABI with host buffers,
-the roofline of the dominant kernel launch (CUDA-event profile), and the
-oracle on the host cores.
+relative residual on the same handle, an end-to-end rate through the C ABI
+with host buffers, the roofline of the dominant kernel launch (CUDA-event
+profile), and the oracle on the host cores.
 
 --impl reference times the oracle (plain complex128 NumPy) on a bounded
 sample of the same workload instead.
@@ -43,11 +46,12 @@ N_FULL, OMEGA_FULL = 4095, 2000.0
 N_SAMPLE, OMEGA_SAMPLE = 1023, 500.0      # same medium recipe and k h, 1/16 of the points
 
 
-def workload_config(n, omega, M=8, outer="fgmres"):
+def workload_config(n, omega, M=2, outer="fgmres", adr_bc="abc"):
     return {"workload": f"layered GRF medium n={n} omega={omega:g} (k h <= 0.49), complex-FP32 Wave-ADR "
-                        f"cycles (M={M}, n_cmax=15, 9 levels) as the preconditioner of FGMRES(20) with FP64 "
-                        f"residual and update; one step = one FGMRES iteration = one cycle",
-            "n": n, "omega": omega, "M": M,
+                        f"cycles (M={M} ADR corrections, ADR boundary closure '{adr_bc}', n_cmax=15, 9 levels) as "
+                        f"the preconditioner of FGMRES(20) with FP64 residual and update, the configuration of "
+                        f"the time-to-1e-6 solve; one step = one FGMRES iteration = one cycle",
+            "n": n, "omega": omega, "M": M, "adr_bc": adr_bc,
             "outer": "FGMRES(20) in FP64 refinement" if outer == "fgmres" else "IR (FP64 residual and update)",
             "cycle_dtype": "complex64",
             "l2": "inputs larger than L2: level-1 vectors are 134 MB each and a step streams ~20 GB"}
@@ -141,7 +145,7 @@ def oracle_cycle_rate(steps: int, warmup: int):
     import oracle
     from oracle.cycle import CycleParams, Hierarchy
     inst = synth.config_layered(n=N_SAMPLE, omega=OMEGA_SAMPLE, seed=5)
-    H = Hierarchy(inst.n, inst.k, inst.phi, inst.omega, inst.bc, CycleParams(n_cmax=15))
+    H = Hierarchy(inst.n, inst.k, inst.phi, inst.omega, inst.bc, CycleParams(n_cmax=15, M=2, adr_bc="abc"))
     u = np.zeros_like(inst.g)
     lev = H.lev(1)
 
@@ -333,17 +337,19 @@ def adjoint_leg(B, torch, dev, st, batch):
                     "the first reverse step eager, the others replaying it as a CUDA graph"}
 
 
-def precision_leg(B, torch, dev, st, n=1023, omega=500.0):
+def precision_leg(B, torch, dev, st, n=1023, omega=500.0, medium="layered"):
     """Time to 1e-6 relative residual of the same problem (the layered recipe
-    at n=1023, omega=500, M=8, FGMRES(20), zero start) with complex-FP32
-    cycles in FP64 refinement and with plain FP64 cycles; every solve reports
-    its final FP64 residual."""
+    at n=1023, omega=500, or the log-normal medium of seed 2 at n=511,
+    omega=200; M=8, FGMRES(20), zero start) with complex-FP32 cycles in FP64
+    refinement and with plain FP64 cycles; every solve reports its final FP64
+    residual."""
     import synth
-    inst = synth.config_layered(n=n, omega=omega, seed=5)
+    inst = (synth.config_layered(n=n, omega=omega, seed=5) if medium == "layered"
+            else synth.config_lognormal(n=n, omega=omega, seed=2))
     k = torch.from_numpy(inst.k).to(dev)
     phi = torch.from_numpy(inst.phi).to(dev)
     g = torch.from_numpy(inst.g).to(dev)
-    out = {"workload": f"layered medium n={n} omega={omega:g}, M=8, FGMRES(20) to 1e-6 from u=0", "solves": {}}
+    out = {"workload": f"{medium} medium n={n} omega={omega:g}, M=8, FGMRES(20) to 1e-6 from u=0", "solves": {}}
     for prec in ("mixed", "fp64"):
         p = B.default_params(precision=prec, n_cmax=15, tol=1e-6, maxit=2000, M=8)
         h = B.mg_setup([(n, omega, k, phi, "abc1")], p, stream=st)
@@ -431,6 +437,31 @@ def eikonal_leg(B, torch, dev, st, n=N_FULL):
             "max_abs_diff_vs_host": diff}
 
 
+def paper_m8_leg(B, torch, dev, st, n, omega, k, phi, g, steps, warmup):
+    """The paper's M = 8 ADR corrections (zero ADR ghost) on the same
+    workload: the rate of its FGMRES steps and the residual they reach.  At
+    this size the correction amplifies the residual with the eikonal phase
+    and the solve does not converge."""
+    p = B.default_params(precision="mixed", n_cmax=15, tol=0.0, maxit=1 << 30, M=8)
+    h = B.mg_setup([(n, omega, k, phi, "abc1")], p, stream=st)
+    B.mg_solve_begin(h, torch.zeros_like(g), g, stream=st)
+    B.mg_solve_steps(h, warmup, stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    B.mg_solve_steps(h, steps, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rel = B.mg_solve_end(h, stream=st)
+    recs = B.mg_profile_records(h, 2, stream=st)
+    dom = max(recs, key=lambda r: r[2])
+    B.mg_destroy(h)
+    return {"M": 8, "adr_bc": "zero", "steps": steps, "value": steps / (ms * 1e-3), "unit": "cycles/s",
+            "ms_per_step": ms / steps, "rel_residual_after_steps": rel,
+            "dominant_kernel": f"{dom[0]}@{dom[1]}", "dominant_GBps": dom[3] / (dom[2] * 1e-3) / 1e9}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -453,7 +484,7 @@ def run_ours(args):
     phi = torch.from_numpy(inst.phi).to(dev)
     g = torch.from_numpy(inst.g).to(dev)
     params = B.default_params(precision="mixed", n_cmax=15, tol=1e-6, maxit=args.tts_maxit, M=args.M,
-                              outer=args.outer)
+                              outer=args.outer, adr_bc=args.adr_bc)
     st = torch.cuda.current_stream()
     t0 = time.time()
     h = B.mg_setup([(n, omega, k, phi, "abc1")], params, stream=st)
@@ -540,33 +571,28 @@ def run_ours(args):
            "note": "per step: H2D of u and g (complex128, pinned), FP64 residual, one outer step, "
                    "D2H of u and the residual norm, all through mg_solve_begin/steps/end"}
 
-    # ---- time to tolerance (zero start) on a handle with args.tts_M ADR corrections
+    # ---- time to tolerance (zero start) on the timed handle
     tts = None
     if not args.no_tts:
-        B.mg_destroy(h)
-        h = None
-        p2 = B.default_params(precision="mixed", n_cmax=15, tol=1e-6, maxit=args.tts_maxit, M=args.tts_M,
-                              adr_bc=args.tts_adr_bc)
-        h2 = B.mg_setup([(n, omega, k, phi, "abc1")], p2, stream=st)
         u = torch.zeros_like(g)
         w0 = time.time()
-        status, its, rr, hist, secs = B.mg_solve(h2, u, g, history_len=0, stream=st)
+        status, its, rr, hist, secs = B.mg_solve(h, u, g, history_len=0, stream=st)
         tts = {"status": {0: "converged", -4: "maxit", -5: "diverged"}.get(status, status), "iterations": its,
                "rel_residual": rr, "device_seconds": secs, "wall_seconds": time.time() - w0, "tol": 1e-6,
-               "M": args.tts_M, "adr_bc": args.tts_adr_bc,
+               "M": args.M, "adr_bc": args.adr_bc,
                "outer": "FGMRES(20), complex-FP32 Krylov vectors, FP64 residual and update",
-               "note": "M=8 (the paper's value, used by the timed steps) and M=3 stagnate at this size with the "
-                       "first-arrival eikonal phase standing in for the paper's trained phase, in FP64 as well; "
-                       "M=2 converges (with the zero ADR ghost: 3268 iterations, 9.5 s). adr_bc='abc' is the "
-                       "absorbing boundary carried into the ADR equation (an option; the paper states no ADR "
-                       "boundary condition)"}
-        h = h2
-
-    if h is not None:
-        B.mg_destroy(h)
+               "note": "the timed steps' handle from u = 0.  The paper's M=8 (leg paper_M8) and M=3 stagnate at "
+                       "this size with the first-arrival eikonal phase standing in for the paper's trained phase, "
+                       "in FP64 as well; M=2 converges (with the zero ADR ghost: 3268 iterations, 9.5 s). "
+                       "adr_bc='abc' is the absorbing boundary carried into the ADR equation (an option; the "
+                       "paper states no ADR boundary condition)"}
+    B.mg_destroy(h)
+    h = None
+    paper = None if args.no_paper_m8 else paper_m8_leg(B, torch, dev, st, n, omega, k, phi, g, 50, args.warmup)
 
     batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3, ws, rank)
     precision = None if args.no_precision else precision_leg(B, torch, dev, st)
+    precision2 = None if args.no_precision else precision_leg(B, torch, dev, st, 511, 200.0, "log-normal")
     shifted = None if args.no_shifted else shifted_leg(B, torch, dev, st)
     ray = None if args.no_ray else ray_leg(B, torch, dev, st)
     adjoint = None if args.no_adjoint else adjoint_leg(B, torch, dev, st, args.adjoint_batch)
@@ -586,11 +612,12 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(n, omega, args.M, args.outer), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": workload_config(n, omega, args.M, args.outer, args.adr_bc), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-            "time_to_tolerance": tts, "rel_residual_after_timed_steps": rel_after,
+            "time_to_tolerance": tts, "rel_residual_after_timed_steps": rel_after, "paper_M8": paper,
             "cycle_roofline": cycle_roofline, "kernels": kernels, "top_launches": top_records,
-            "batched": batched, "adjoint": adjoint, "eikonal": eik, "precision_comparison": precision, "shifted": shifted, "wave_ray": ray,
+            "batched": batched, "adjoint": adjoint, "eikonal": eik, "precision_comparison": precision,
+            "precision_comparison_lognormal_n511": precision2, "shifted": shifted, "wave_ray": ray,
             "setup_seconds": t_setup, "input_generation_seconds": t_inputs}
     print(json.dumps(line), flush=True)
     return 0
@@ -608,10 +635,10 @@ def main():
     ap.add_argument("--no-tts", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--M", type=int, default=8, help="ADR corrections per cycle in the timed steps")
-    ap.add_argument("--tts-M", type=int, default=2, help="ADR corrections for the time-to-tolerance solve")
-    ap.add_argument("--tts-adr-bc", default="abc", choices=["zero", "abc"],
-                    help="ADR boundary closure for the time-to-tolerance solve")
+    ap.add_argument("--M", type=int, default=2,
+                    help="ADR corrections per cycle of the timed steps and the time-to-tolerance solve")
+    ap.add_argument("--adr-bc", default="abc", choices=["zero", "abc"], help="ADR boundary closure")
+    ap.add_argument("--no-paper-m8", action="store_true")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "ir"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=20)

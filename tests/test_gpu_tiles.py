@@ -157,3 +157,43 @@ def test_wave_tail_matches_per_level_launches(prec, tol, bc, shift):
     finally:
         B.mg_destroy(ht)
         B.mg_destroy(hp)
+
+
+@pytest.mark.parametrize("cand", range(B.MG_TILE_CANDIDATES))
+def test_config2_fp64_every_tile_candidate(cand):
+    """The log-normal medium at n = 511, omega = 200 (seed 2) in FP64: two
+    cycles from a random start against the oracle, 1e-12 per cycle, for every
+    halo-tile candidate."""
+    I = synth.config_lognormal(n=511, omega=200.0, seed=2)
+    h = lib_handle([I], "fp64", n_cmax=15, tile_candidate=cand, autotune=0)
+    H = oracle_hier(I, n_cmax=15)
+    try:
+        u = rnd(I.g.shape, 11) * 1e-3
+        uu = u.copy()
+        B.mg_cycle(h, uu, I.g.copy(), 1)
+        ref = H.cycle(u, I.g)
+        assert rel(uu, ref) < 1e-12, (cand, rel(uu, ref))
+        B.mg_cycle(h, uu, I.g.copy(), 1)
+        ref = H.cycle(ref, I.g)
+        assert rel(uu, ref) < 1e-12, (cand, rel(uu, ref))
+    finally:
+        B.mg_destroy(h)
+
+
+@pytest.mark.parametrize("cand", [0, 1, 3])
+def test_n1023_fp64_blocks_loop_over_several_tiles(cand):
+    """n = 1023 in FP64 (level 2 has 511 x 511 nodes: more tiles and strips
+    than one wave of resident blocks, so every block of the persistent,
+    double-buffered tile loops handles several): one cycle against the
+    oracle, 1e-12."""
+    I = synth.config_lognormal(n=1023, omega=500.0, seed=300)
+    h = lib_handle([I], "fp64", n_cmax=15, tile_candidate=cand, autotune=0)
+    H = oracle_hier(I, n_cmax=15)
+    try:
+        u = rnd(I.g.shape, 12) * 1e-3
+        uu = u.copy()
+        B.mg_cycle(h, uu, I.g.copy(), 1)
+        ref = H.cycle(u, I.g)
+        assert rel(uu, ref) < 1e-12, (cand, rel(uu, ref))
+    finally:
+        B.mg_destroy(h)
