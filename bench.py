@@ -538,6 +538,10 @@ def run_ours(args):
     cycle_roofline = {"algorithmic_GB_per_step": step_bytes / 1e9,
                       "achieved_GBps": step_bytes / (ms * 1e-3 / args.steps) / 1e9,
                       "frac_of_peak": step_bytes / (ms * 1e-3 / args.steps) / 1e9 / peak}
+    # the whole step beside the dominant kernel: every kernel's algorithmic
+    # bytes over the timed step time (launch gaps and small levels included)
+    roofline["whole_step"] = {"achieved": cycle_roofline["achieved_GBps"], "frac": cycle_roofline["frac_of_peak"],
+                              "algorithmic_GB_per_step": cycle_roofline["algorithmic_GB_per_step"]}
     kernels = {}
     for name, pts, kms, kby, kla in recs:
         e = kernels.setdefault(name, {"ms_per_step": 0.0, "bytes": 0.0, "launches_per_step": 0})

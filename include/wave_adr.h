@@ -112,12 +112,12 @@ typedef struct mg_params {
     int pdl;                /* 1: kernels are launched with programmatic dependent launch (a kernel's
                                descriptor prologue overlaps its predecessor); 0 (default): plain launches
                                (measured 0.1 ms per n=4095 cycle faster on this GPU) */
-    int tail_cluster;       /* 0 (default): shared-memory tail -- one block per instance runs the pre-smoothing
-                               chain down to the coarsest level, the FP64 coarsest solve follows, one block per
-                               instance runs the post-smoothing chain up (3 launches per ADR cycle; a level
-                               joins the tail only if its vectors fit in one block's shared memory);
-                               1..16: one thread-block cluster of that many CTAs per instance runs the whole
-                               tail in one launch, data through L2 (slower on this GPU) */
+    int tail_cluster;       /* must be 0: the coarse tail is the shared-memory tail -- one block per instance
+                               runs the pre-smoothing chain down to the coarsest level, the FP64 coarsest solve
+                               follows, one block per instance runs the post-smoothing chain up (3 launches per
+                               ADR cycle; a level joins the tail only if its vectors fit in one block's shared
+                               memory).  Other values return MG_EINVAL (a cluster-per-instance tail was measured
+                               slower on this GPU and is not built) */
     int ray;                /* 0 (default): the M ADR corrections use the input phase phi (Wave-ADR);
                                1: Wave-Ray (the ray equations of Section 3.2): correction m = 1..M uses the
                                plane-wave phase phi_m = cos(theta_m) x + sin(theta_m) y, theta_m =

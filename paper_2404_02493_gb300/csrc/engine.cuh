@@ -18,7 +18,7 @@
 #include "fgmres.cuh"
 #include "kernels.cuh"
 #include "gmres_sstep.cuh"
-#include "tail.cuh"
+#include "cheb_stream.cuh"
 #include "tail_smem.cuh"
 #include "tail_wave.cuh"
 #include "setup_kernels.cuh"
@@ -105,6 +105,52 @@ struct Engine : EngineBase {
             kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sin, sout, m, flags);
         }, t.pts);
     }
+    // NS Chebyshev steps m .. m + NS - 1 as warp-streaming strips
+    // (k_cheb_stream, complex FP32).  Band height: of the candidates, the one
+    // whose busiest warp marches the fewest rows (units per resident warp
+    // rounded up, times the band plus its 2 NS halo rows).
+    template <int NS, bool HS>
+    void launch_cheb_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, int sin, int sout, int sdin,
+                               int sdout, int m, int flags, cudaStream_t st) {
+        constexpr int SO = cs_out<NS>();
+        const int smem = cs_smem<T, HS>();
+        int nmax = 0;
+        for (int q : ds) nmax = std::max(nmax, H.hdesc[(size_t)q].n);
+        const int nstrips = (nmax + SO - 1) / SO;
+        constexpr int WPB = cs_wpb<HS>();
+        const long long warps = (long long)occ_cap(k_cheb_stream<T, NS, 16, HS>, smem, 32 * WPB) * WPB;
+        int best = 16;
+        long long bcost = -1;
+        for (int rh : {16, 24, 32, 64}) {
+            const long long units = (long long)nstrips * ((nmax + rh - 1) / rh);
+            const long long cost = (units + warps - 1) / warps * (rh + 2 * NS);
+            if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
+        }
+        auto run = [&](auto kern, int rh) {
+            const SegTable& t = H.seg_tiles(ds, SO, rh * WPB, false, occ_cap(kern, smem, 32 * WPB));
+            go(H, st, KK_CHEB, bpp * (double)t.pts, [&] {
+                kl(kern, t.nblocks, dim3(32, WPB), smem, st, kd(H, t), t.d, t.nseg, sin, sout, sdin, sdout, m, flags);
+            }, t.pts);
+        };
+        switch (best) {
+        case 16: run(k_cheb_stream<T, NS, 16, HS>, 16); break;
+        case 24: run(k_cheb_stream<T, NS, 24, HS>, 24); break;
+        case 32: run(k_cheb_stream<T, NS, 32, HS>, 32); break;
+        default: run(k_cheb_stream<T, NS, 64, HS>, 64); break;
+        }
+    }
+    template <int NS>
+    void launch_cheb_stream(Handle& H, const std::vector<int>& ds, double bpp, int sin, int sout, int sdin, int sdout,
+                            int m, int flags, cudaStream_t st) {
+        if constexpr (std::is_same<T, float>::value) {
+            bool hs = false;
+            for (int q : ds) hs = hs || H.hdesc[(size_t)q].sig != nullptr;
+            if (hs)
+                launch_cheb_stream_hs<NS, true>(H, ds, bpp, sin, sout, sdin, sdout, m, flags, st);
+            else
+                launch_cheb_stream_hs<NS, false>(H, ds, bpp, sin, sout, sdin, sdout, m, flags, st);
+        }
+    }
     template <int MODE>
     void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
                          cudaStream_t st) {
@@ -172,20 +218,61 @@ struct Engine : EngineBase {
     }
 
     // ------------------------------------------------------------ pieces
-    // q Chebyshev steps; from_zero: the first step starts from x = 0.  The
-    // output slots alternate so that the final iterate lands in SU.
-    void cheb_steps(Handle& H, const std::vector<int>& ds, int q, int xin, bool from_zero, cudaStream_t st) {
+    // In the complex-FP32 cycle the Chebyshev steps of levels l >= 2 with
+    // n >= CS_MIN_N run as warp-streaming strips, steps (m, m + 1) fused in
+    // one pass (k_cheb_stream<2>), after a single first step
+    // (k_cheb_stream<1>) when q is odd.  Smaller levels (where a strip march
+    // is latency-bound), level 1 and FP64 use the tile kernel k_cheb_step,
+    // one step per launch.
+    static constexpr bool kStream = std::is_same<T, float>::value;
+    static bool cheb_stream_on(Handle& H, const std::vector<int>& ds, int l) {
+        if (!kStream || l < 2) return false;
+        int nmax = 0;
+        for (int q : ds) nmax = std::max(nmax, H.hdesc[(size_t)q].n);
+        return nmax >= CS_MIN_N;
+    }
+    // launches that q steps take on level l
+    static int cheb_launches(Handle& H, const std::vector<int>& ds, int l, int q) {
+        return (q >= 2 && cheb_stream_on(H, ds, l)) ? (q + 1) / 2 : q;
+    }
+
+    // q Chebyshev steps on level l from the iterate in xin (zero when
+    // from_zero).  The x slots alternate between SU and SX2, starting so
+    // that the final iterate lands in SU when from_zero, else on the slot
+    // the alternation from xin reaches; returns it.  The direction d of a
+    // fused pair ping-pongs between SD and STMP (free while level l
+    // smooths); the last step never writes d.
+    int cheb_steps(Handle& H, const std::vector<int>& ds, int l, int q, int xin, bool from_zero, cudaStream_t st) {
+        const int nl = cheb_launches(H, ds, l, q);
         int cur = xin;
-        int out = from_zero ? ((q & 1) ? SU : SX2) : (xin == SU ? SX2 : SU);
-        for (int m = 0; m < q; ++m) {
+        int out = from_zero ? ((nl & 1) ? SU : SX2) : (xin == SU ? SX2 : SU);
+        int m = 0, dsl = SD;
+        auto advance = [&] { cur = out; out = (cur == SU) ? SX2 : SU; };
+        const bool stream = cheb_stream_on(H, ds, l);
+        const bool pairs = nl != q;
+        for (; m < q && (!pairs || (m == 0 && (q & 1))); ++m) {
             const bool xz = (m == 0 && from_zero), last = (m == q - 1);
             const int flags = (xz ? 1 : 0) | (last ? 2 : 0);
             // reads x (unless zero), g, k, d (m > 0); writes x, d (unless last)
             const double bpp = (xz ? 0 : C) + C + R + (m > 0 ? C : 0) + C + (last ? 0 : C);
-            launch_cheb(H, ds, bpp, cur, out, m, flags, st);
-            cur = out;
-            out = (cur == SU) ? SX2 : SU;
+            if (stream)
+                launch_cheb_stream<1>(H, ds, bpp, cur, out, SD, SD, m, flags, st);
+            else
+                launch_cheb(H, ds, bpp, cur, out, m, flags, st);
+            advance();
         }
+        for (; m < q; m += 2) {
+            const bool xz = (m == 0 && from_zero), last = (m + 1 == q - 1);
+            const int flags = (xz ? 1 : 0) | (last ? 2 : 0);
+            const int dnext = dsl == SD ? STMP : SD;
+            // as one step: x_m (unless zero), g, k, d_{m-1} (m > 0) read;
+            // x_{m+2}, d_{m+1} (unless last) written
+            const double bpp = (xz ? 0 : C) + C + R + (m > 0 ? C : 0) + C + (last ? 0 : C);
+            launch_cheb_stream<2>(H, ds, bpp, cur, out, dsl, dnext, m, flags, st);
+            dsl = dnext;
+            advance();
+        }
+        return cur;
     }
 
     // ------------------------------------------------------------ s-step GMRES(3)
@@ -351,41 +438,6 @@ struct Engine : EngineBase {
         }, t.pts);
     }
 
-    // The ADR sub-V-cycle adrv(l..L) of the instances in `tail` in one
-    // launch: one thread-block cluster per instance (tail.cuh).  The cluster
-    // size is 16 CTAs (non-portable) when the GPU can schedule it, else 8.
-    int tail_cluster(Handle& H) {
-        auto kern = k_adr_tail<T>;
-        static bool nonportable = false;   // clusters of more than 8 CTAs need the opt-in
-        if (!nonportable) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaGetLastError();
-            nonportable = true;
-        }
-        if (H.p.tail_cluster > 0) return H.p.tail_cluster;
-        static int cl = 0;
-        if (cl) return cl;
-        for (int c : {16, 8}) {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = c;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(c);
-            cfg.blockDim = dim3(TAIL_THREADS);
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int num = 0;
-            if (cudaOccupancyMaxActiveClusters(&num, kern, &cfg) == cudaSuccess && num > 0) {
-                cl = c;
-                break;
-            }
-            cudaGetLastError();
-        }
-        if (!cl) cl = 8;
-        return cl;
-    }
     // Shared-memory tail (tail_smem.cuh): the largest dynamic shared memory
     // its kernels may use (opt-in limit minus their static shared memory),
     // set on both kernels once.
@@ -507,57 +559,17 @@ struct Engine : EngineBase {
         }, pts);
     }
 
-    void launch_tail(Handle& H, int l, const std::vector<int>& tail, cudaStream_t st) {
-        if (H.p.tail_cluster == 0) {
-            launch_tail_smem(H, l, tail, st);
-            return;
-        }
-        const std::vector<int> ds = adescs(H, l, tail);
-        const std::string key = "tail" + desc_key(ds);
-        auto it = H.tail_first.find(key);
-        int* dfirst = nullptr;
-        if (it == H.tail_first.end()) {
-            dfirst = (int*)H.alloc(sizeof(int) * ds.size());
-            cudaMemcpy(dfirst, ds.data(), sizeof(int) * ds.size(), cudaMemcpyHostToDevice);
-            H.tail_first[key] = dfirst;
-        } else {
-            dfirst = it->second;
-        }
-        const int cl = tail_cluster(H);
-        long long pts = 0;
-        for (int b : tail)
-            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].n;
-        // per ADR level point: two gram passes, the pre- and post-smoothing updates and the prolongation,
-        // as the multi-launch kernels count them
-        const double bpp = 2 * (3 * C + Q) + (4 * C + Q + C / 4) + (4 * C + Q + C / 4) + 5 * C;
-        go(H, st, KK_ADR_TAIL, bpp * (double)pts, [&] {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = cl;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(cl * (unsigned)tail.size());
-            cfg.blockDim = dim3(TAIL_THREADS);
-            cfg.dynamicSmemBytes = 0;
-            cfg.stream = st;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            cudaLaunchKernelEx(&cfg, k_adr_tail<T>, (const LevelDesc*)H.ddesc, (const int*)dfirst);
-        }, pts);
-    }
-
     // Instance b runs levels l.. of the ADR V-cycle with per-level launches
     // (not the coarsest level, not in the coarse tail).
     static bool adr_per_level(Handle& H, int b, int l) {
         return H.inst[b].L > l && !in_tail(H, b, l);
     }
     // Level l (not the coarsest) of instance b starts or lies in the coarse
-    // tail: l >= 3, n_l <= tail_nmax and, for the shared-memory tail
-    // (tail_cluster == 0), its vectors fit in one block's shared memory.
+    // tail: l >= 3, n_l <= tail_nmax and its vectors fit in one block's
+    // shared memory.
     static bool in_tail(Handle& H, int b, int l) {
         const int n = H.inst[b].lv[l - 1].n;
-        return l >= 3 && n <= H.p.tail_nmax && (H.p.tail_cluster > 0 || ts_fits(n));
+        return l >= 3 && n <= H.p.tail_nmax && ts_fits(n);
     }
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
     // level l, result in SAX (or, at level 2 with `modulate`, added as
@@ -570,7 +582,7 @@ struct Engine : EngineBase {
         for (int b : I) (H.inst[b].L == l ? co : rest0).push_back(b);
         if (!co.empty()) coarse_solve(H, co, l, 1, st);
         for (int b : rest0) (adr_per_level(H, b, l) ? rest : tail).push_back(b);
-        if (!tail.empty()) launch_tail(H, l, tail, st);
+        if (!tail.empty()) launch_tail_smem(H, l, tail, st);
         if (rest.empty()) return;
         const std::vector<int> ds = adescs(H, l, rest);
         const TileChoice tc = tiles_of(H, ds);
@@ -611,7 +623,7 @@ struct Engine : EngineBase {
             if (H.p.coarse == MG_COARSE_LU) {
                 coarse_solve(H, co, l, 0, st);
             } else {
-                cheb_steps(H, descs(H, l, co), H.p.coarse_cheb_iters, SU, true, st);
+                cheb_steps(H, descs(H, l, co), l, H.p.coarse_cheb_iters, SU, true, st);
             }
         }
         if (rest.empty()) return;
@@ -626,7 +638,7 @@ struct Engine : EngineBase {
         const std::vector<int> ds = descs(H, l, rest);
         const int q = H.p.cheb_iters;
         const bool smooth = (l != 3);      // no smoothing on level 3 (Section 3.1.3)
-        if (smooth) cheb_steps(H, ds, q, SU, true, st);
+        if (smooth) cheb_steps(H, ds, l, q, SU, true, st);
         launch_restrict<MODE_HELM>(H, ds, KK_RESTRICT_HELM, smooth ? 2 * C + R + C / 4 : C + C / 4, SU, SG,
                                    SG, smooth ? 0 : 1, st);
         wave(H, l + 1, rest, st);
@@ -634,9 +646,9 @@ struct Engine : EngineBase {
             launch_prolong<PMODE_ADD>(H, ds, KK_PROLONG_ADD, C + C / 4, SU, SU, SG, SU, SU, 1, st);
             return;
         }
-        const int out = (q & 1) ? SX2 : SU;
+        const int out = (cheb_launches(H, ds, l, q) & 1) ? SX2 : SU;
         launch_prolong<PMODE_ADD>(H, ds, KK_PROLONG_ADD, 2 * C + C / 4, SU, SU, SG, out, out, 0, st);
-        cheb_steps(H, ds, q, out, false, st);
+        cheb_steps(H, ds, l, q, out, false, st);
         if (l == 2 && H.p.adr && H.p.M > 0) adr_corrections(H, rest, H.p.M, st);
     }
 
@@ -801,17 +813,9 @@ struct Engine : EngineBase {
         case OP_JACOBI:
             kl(k_jacobi<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg, SX2, SG, SU, 0);
             return SU;
-        case OP_CHEB: {
-            // a0 steps from the iterate in SU
-            int cur = SU, out = SX2;
-            for (int m = 0; m < a0; ++m) {
-                int flags = (m == a0 - 1 ? 2 : 0);
-                launch_cheb(H, descs(H, level, I), 0, cur, out, m, flags, st);
-                cur = out;
-                out = (cur == SU) ? SX2 : SU;
-            }
-            return cur;
-        }
+        case OP_CHEB:
+            // a0 steps from the iterate in SU, as the cycle runs them
+            return a0 > 0 ? cheb_steps(H, descs(H, level, I), level, a0, SU, false, st) : SU;
         case OP_GMRES: {
             const std::vector<int> ds = descs(H, level, I);
             const TileChoice tc = tiles_of(H, ds);

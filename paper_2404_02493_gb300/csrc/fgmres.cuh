@@ -281,7 +281,9 @@ __device__ __forceinline__ bool fg_stream(const LevelDesc& d, const SegCtx& c, i
         if (__syncthreads_or(landed ? 0 : 1) != 0) {
             if (tid == 0) {
                 if (d.err) atomicExch(d.err, 1u);
-                for (int q = i + 1; q < min(i + g.ns, nmine); ++q) mbar_wait(&bars[q % g.ns], (unsigned)((q / g.ns) & 1));
+                // stages i .. i + ns - 2 may still have copies in flight into
+                // shared memory: wait once more (bounded) before leaving
+                for (int q = i; q < min(i + g.ns, nmine); ++q) mbar_wait(&bars[q % g.ns], (unsigned)((q / g.ns) & 1));
             }
             __syncthreads();
             return false;

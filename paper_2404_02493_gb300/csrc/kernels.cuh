@@ -269,19 +269,26 @@ __device__ __forceinline__ void load_region(cplx<T>* sm, const cplx<T>* __restri
 // out-of-grid element is zero-filled (source size 0, nothing is read).  A
 // tile's copies are issued together and waited for as one commit group, so
 // the next tile of a block can stream in while the current one is computed.
+// The memory clobbers keep the compiler from moving shared-memory reads
+// across an issue (which may overwrite a ring slot) or above a wait (before
+// the data landed): the warp-private rings of the streaming kernels have no
+// block barrier that would order them.
 template <int B>
 __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, bool ok) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
     if (B == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 4 : 0));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 4 : 0)
+                     : "memory");
     else if (B == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 8 : 0));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 8 : 0)
+                     : "memory");
     else
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 16 : 0));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 16 : 0)
+                     : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename E>
 __device__ __forceinline__ void cp_async_elem(E* sdst, const E* gsrc, bool ok) {

@@ -892,7 +892,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
         p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
-        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster < 0 || p->tail_cluster > 16 || p->tail_nmax < -1 || p->ray < 0 ||
+        p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster != 0 || p->tail_nmax < -1 || p->ray < 0 ||
         p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3 || p->workspace_limit < 0 ||
         p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC ||
         p->adr_reaction < MG_ADR_REACTION_CONTINUOUS || p->adr_reaction > MG_ADR_REACTION_DISCRETE) {
@@ -915,7 +915,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     // over more SMs
     // the wave-cycle tail (tail_wave.cuh) follows an explicit tail_nmax; automatic: levels with n <= 63
     mh->H.wave_tail_nmax = mh->H.p.tail_nmax >= 0 ? mh->H.p.tail_nmax : 63;
-    if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = (ninst == 1 && mh->H.p.tail_cluster == 0) ? 31 : 0;
+    if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = ninst == 1 ? 31 : 0;
     mh->H.prec = p->precision;
     mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();
     // k and phi may be host memory: stage them on the device for the setup kernels

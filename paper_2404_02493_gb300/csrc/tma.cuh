@@ -141,7 +141,12 @@ struct TmaPipe {
         pending[b] = true;
     }
     // true if buffer b's copies landed (block-uniform).  On expiry: error
-    // word set, the other buffer drained (bounded), false for every thread.
+    // word set, false for every thread, after thread 0 has waited once more
+    // (bounded) for the copies still in flight into this block's shared
+    // memory: those of buffer b and, if issued, of the other buffer.  The
+    // copies read device memory and complete within microseconds unless the
+    // memory system has failed; if even the second limit passes, the context
+    // is lost anyway and the block leaves without them.
     __device__ __forceinline__ bool wait(int b, unsigned* err) {
         const bool ok = __syncthreads_and(mbar_wait(&bar[b], phase[b]) ? 1 : 0) != 0;
         phase[b] ^= 1;
@@ -149,6 +154,7 @@ struct TmaPipe {
         if (!ok) {
             if (threadIdx.x == 0 && threadIdx.y == 0) {
                 if (err) atomicExch(err, 1u);
+                mbar_wait(&bar[b], phase[b] ^ 1);
                 if (pending[b ^ 1]) mbar_wait(&bar[b ^ 1], phase[b ^ 1]);
             }
             __syncthreads();

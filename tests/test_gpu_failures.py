@@ -41,6 +41,14 @@ def test_setup_rejects_bad_fields(field, value):
     assert "not finite" in str(e.value)
 
 
+@pytest.mark.parametrize("kw", [dict(tail_cluster=16), dict(cheb_iters=0), dict(cheb_iters=17), dict(restart=0),
+                                dict(adr_bc=2), dict(adr_reaction=-1), dict(fgmres_passes=4), dict(ray=2)])
+def test_setup_rejects_out_of_range_schedule(kw):
+    with pytest.raises(B.MgError) as e:
+        lib_handle([_inst()], "mixed", n_cmax=7, **kw)
+    assert e.value.code == B.MG_EINVAL
+
+
 def test_setup_workspace_limit_gives_enomem_and_leaks_nothing():
     I = _inst()
     h = lib_handle([I], "mixed", n_cmax=7)

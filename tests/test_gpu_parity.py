@@ -123,6 +123,46 @@ def test_chebyshev(pair, q):
         assert rel(uu, ref) < 1e-12, (l, rel(uu, ref))
 
 
+BIG32 = {
+    # level 2 = 1042: 19 strips (the last one ragged) and ragged row bands
+    "abc2085": lambda: inst_medium(2085, 600.0, seed=6),
+    # level 2 = 1024 with the sponge term (the kernel variant with its ring)
+    "sponge2049": lambda: inst_medium(2049, 500.0, seed=7, bc="sponge"),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES) + ["ragged511"] + list(BIG32))
+def pair32(request):
+    if request.param == "ragged511":
+        I, ncm = inst_medium(511, 150.0, seed=6), 15
+    elif request.param in BIG32:
+        I, ncm = BIG32[request.param](), 15
+    else:
+        I, ncm = CASES[request.param]()
+    P = Pair(I, "mixed", n_cmax=ncm)
+    yield P
+    P.close()
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5])
+def test_chebyshev_fp32(pair32, q):
+    """Complex-FP32 Chebyshev steps as the mixed cycle runs them against the
+    FP64 oracle, on every Chebyshev level.  Levels with n < 1024: one tile
+    step per launch (several 32 x 16 tiles with ragged tails); levels with
+    n >= 1024 (abc2085, sponge2049): warp-streaming strips, steps m and m + 1
+    in one pass after a single first step when q is odd, the 4-column halo
+    of a pair crossing strip, band and grid edges; the sponge term
+    (sponge63, sponge2049)."""
+    H = pair32.H
+    for l in H.lam_max:
+        u, g = pair32.vec(l, 6), pair32.vec(l, 7)
+        uu = u.copy()
+        B.mg_chebyshev(pair32.h, 0, l, uu, g, q)
+        a, b = H.lam_max[l] / H.alpha[l], H.lam_max[l]
+        ref = chebyshev(H.lev(l), u.astype(np.complex128), g.astype(np.complex128), a, b, q)
+        assert rel(uu.astype(np.complex128), ref) < 1e-5, (l, rel(uu, ref))
+
+
 def test_gmres3(pair):
     H = pair.H
     for l in H.adr:

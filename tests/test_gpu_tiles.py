@@ -92,18 +92,16 @@ def test_autotuner_picks_listed_candidates():
         B.mg_destroy(hd)
 
 
-@pytest.mark.parametrize("cluster", [0, 16])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
-def test_coarse_tail_matches_per_level_launches(prec, tol, cluster):
-    """The coarse ADR levels as a tail (tail_nmax = 511) against one launch
-    per pass (tail_nmax = 0) and against the oracle, on a batch of uneven
-    instances (the tail takes different numbers of levels per instance).
-    cluster = 0: shared-memory tail (down / coarsest / up launches; a level
-    joins only if its vectors fit in one block, so FP64 starts lower);
-    cluster = 16: one thread-block cluster per instance."""
+def test_coarse_tail_matches_per_level_launches(prec, tol):
+    """The coarse ADR levels as a shared-memory tail (tail_nmax = 511: down /
+    coarsest / up launches; a level joins only if its vectors fit in one
+    block, so FP64 starts lower) against one launch per pass (tail_nmax = 0)
+    and against the oracle, on a batch of uneven instances (the tail takes
+    different numbers of levels per instance)."""
     insts = [_inst(95, 40.0, 31), _inst(200, 60.0, 32), _inst(127, 50.0, 33)]
-    ht = lib_handle(insts, prec, n_cmax=12, tail_nmax=511, tail_cluster=cluster)
-    hp = lib_handle(insts, prec, n_cmax=12, tail_nmax=0, tail_cluster=cluster)
+    ht = lib_handle(insts, prec, n_cmax=12, tail_nmax=511)
+    hp = lib_handle(insts, prec, n_cmax=12, tail_nmax=0)
     try:
         dt = np.complex128 if prec == "fp64" else np.complex64
         g = np.concatenate([(I.g / np.linalg.norm(I.g)).ravel() for I in insts]).astype(dt)
