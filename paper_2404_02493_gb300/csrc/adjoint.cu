@@ -42,10 +42,14 @@ using cd = std::complex<double>;
 // ------------------------------------------------------------ kernels (FP64)
 constexpr int ANT = 256;
 
+// (i, j) of the flat index q of an n x n level; n <= 32768, so q and n^2
+// fit 32 bits and one unsigned 32-bit division replaces the 64-bit one
 __device__ __forceinline__ bool ij_of(long long q, int n, int& i, int& j) {
     if (q >= (long long)n * n) return false;
-    j = (int)(q / n);
-    i = (int)(q - (long long)j * n);
+    const unsigned uq = (unsigned)q, un = (unsigned)n;
+    const unsigned uj = uq / un;
+    j = (int)uj;
+    i = (int)(uq - uj * un);
     return true;
 }
 
@@ -63,8 +67,10 @@ __global__ void ka_lincomb(int n, int pitch, double2* out, int acc, const double
     out[p] = v;
 }
 
-// y (+)= s op(x), op: 0 A, 1 A^H, 2 L, 4 L^H
-__global__ void ka_apply(LevelDesc d, int op, const double2* x, double2* y, double2 s, int acc) {
+// y = base + s op(x), base = b if given, else y (acc) or 0; op: 0 A, 1 A^H,
+// 2 L, 4 L^H.  With z given, also z += x (pointwise).
+__global__ void ka_apply(LevelDesc d, int op, const double2* x, double2* y, double2 s, int acc, const double2* b,
+                         double2* z) {
     int i, j;
     if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
@@ -74,7 +80,8 @@ __global__ void ka_apply(LevelDesc d, int op, const double2* x, double2* y, doub
     else if (op == 2) r = adr_apply_pt<double>(d, x, i, j);
     else r = adr_apply_t_pt<double, true>(d, x, i, j);
     r = dmul(s, r);
-    y[p] = acc ? dadd(y[p], r) : r;
+    y[p] = b ? dadd(b[p], r) : (acc ? dadd(y[p], r) : r);
+    if (z) z[p] = dadd(z[p], x[p]);
 }
 
 // y (+)= s D^{-1} x  or  s D^{-H} x  (D = Helmholtz diagonal)
@@ -124,46 +131,55 @@ __global__ void ka_prolong(int nf, int pf, int nc, int pc, const double2* e, dou
     y[p] = acc ? dadd(y[p], v) : v;
 }
 
-// up to 8 (x, y) vector pairs of a dot-product launch, passed by value
+// up to ADOTS (x, y) vector pairs of a dot-product launch, passed by value;
+// with z[k] set the pair's left vector is x[k] - z[k]
+constexpr int ADOTS = 9;
 struct DotPtrs {
-    const double2* x[8];
-    const double2* y[8];
+    const double2* x[ADOTS];
+    const double2* y[ADOTS];
+    const double2* z[ADOTS];
 };
 
-// block partials of up to 8 dot products sum conj(x_k) y_k
-__global__ void ka_dots(int n, int pitch, int npair, DotPtrs P, double2* part) {
-    const double2* const* xs = P.x;
-    const double2* const* ys = P.y;
-    __shared__ double2 sh[8 * 8];
-    double2 acc[8];
+// up to ADOTS dot products sum conj(x_k) y_k into out[k]: block partials,
+// then the last block to finish (counter) sums the partials in block order
+// and clears the counter for the next launch
+__global__ void ka_dots(int n, int pitch, int npair, DotPtrs P, double2* part, unsigned* count, double2* out) {
+    __shared__ double2 sh[8 * ADOTS];
+    __shared__ bool last;
+    double2 acc[ADOTS];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = make_double2(0, 0);
-    const long long N = (long long)n * n;
-    for (long long q = (long long)blockIdx.x * ANT + threadIdx.x; q < N; q += (long long)gridDim.x * ANT) {
-        const int j = (int)(q / n), i = (int)(q - (long long)j * n);
+    for (int k = 0; k < ADOTS; ++k) acc[k] = make_double2(0, 0);
+    const unsigned N = (unsigned)n * (unsigned)n, un = (unsigned)n;
+    for (unsigned q = blockIdx.x * ANT + threadIdx.x; q < N; q += gridDim.x * ANT) {
+        const unsigned j = q / un, i = q - j * un;
         const long long p = (long long)j * pitch + i;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (k < npair) acc[k] = dadd(acc[k], dmulc(xs[k][p], ys[k][p]));
+        for (int k = 0; k < ADOTS; ++k)
+            if (k < npair) {
+                const double2 xv = P.z[k] ? dsub(P.x[k][p], P.z[k][p]) : P.x[k][p];
+                acc[k] = dadd(acc[k], dmulc(xv, P.y[k][p]));
+            }
     }
-    block_sum<double2, 8>(acc, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 8; ++k) part[blockIdx.x * 8 + k] = acc[k];
-}
-
-// the nb block partials of a ka_dots launch summed in block order: out[k]
-__global__ void ka_dots_fin(const double2* part, int nb, int np, double2* out) {
-    __shared__ double2 sh[8 * 8];
-    double2 acc[8];
+    block_sum<double2, ADOTS>(acc, sh);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < ADOTS; ++k) part[blockIdx.x * ADOTS + k] = acc[k];
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = make_double2(0, 0);
-    for (int b = threadIdx.x; b < nb; b += ANT)
+    for (int k = 0; k < ADOTS; ++k) acc[k] = make_double2(0, 0);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += ANT)
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (k < np) acc[k] = dadd(acc[k], part[b * 8 + k]);
-    block_sum<double2, 8>(acc, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < np; ++k) out[k] = acc[k];
+        for (int k = 0; k < ADOTS; ++k)
+            if (k < npair) acc[k] = dadd(acc[k], __ldcg(&part[b * ADOTS + k]));
+    block_sum<double2, ADOTS>(acc, sh);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < npair; ++k) out[k] = acc[k];
+        *count = 0;
+    }
 }
 
 // complex 3 x 3 solve, Gaussian elimination with partial pivoting (largest
@@ -259,15 +275,18 @@ __global__ void ka_lincomb_p(int n, int pitch, double2* out, int acc, const doub
 
 // dst += scale Re(src)  (weight gradients accumulated on the device)
 __global__ void ka_accum_re(double* dst, const double2* src, double scale) { dst[0] += scale * src[0].x; }
+__global__ void ka_accum_re2(double* dst, const double2* src, double s0, double s1) {
+    dst[0] += s0 * src[0].x;
+    dst[0] += s1 * src[1].x;
+}
 
 // ADR coefficient gradients of y = s L a with cotangent ybar:
 // qbar = (phix_bar, phiy_bar, d_bar.re, d_bar.im) per node.
-__global__ void ka_adr_grad(LevelDesc d, const double2* ybar, const double2* a, double s, double* qbar) {
-    int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
-    const long long p = (long long)j * d.pitch + i;
+// qbar(i, j) += the gradient of Re<ybar, L a> with respect to the node's ADR
+// coefficient quad (phi_x, phi_y, diagonal), yb = s ybar at the node
+__device__ __forceinline__ void adr_grad_pt(const LevelDesc& d, int i, int j, long long p, double2 yb,
+                                            const double2* a, double* qbar) {
     const int n = d.n;
-    const double2 yb = dsc(ybar[p], s);
     const double2 z = make_double2(0, 0);
     const double2 aW = i > 0 ? a[p - 1] : z, aE = i < n - 1 ? a[p + 1] : z;
     const double2 aS = j > 0 ? a[p - d.pitch] : z, aN = j < n - 1 ? a[p + d.pitch] : z;
@@ -286,6 +305,25 @@ __global__ void ka_adr_grad(LevelDesc d, const double2* ybar, const double2* a, 
     const double2 db = dmulc(ac, yb);          // conj(a) ybar
     o[2] += db.x;
     o[3] += db.y;
+}
+
+__global__ void ka_adr_grad(LevelDesc d, const double2* ybar, const double2* a, double s, double* qbar) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    adr_grad_pt(d, i, j, p, dsc(ybar[p], s), a, qbar);
+}
+
+// the reverse of y = s L a in one pass: out += s L^H ybar and the ADR
+// coefficient gradient of Re<ybar, s L a> into qbar
+__global__ void ka_lh_grad(LevelDesc d, const double2* ybar, const double2* a, double s, double2* out,
+                           double* qbar) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    const long long p = (long long)j * d.pitch + i;
+    const double2 r = dmul(make_double2(s, 0), adr_apply_t_pt<double, true>(d, ybar, i, j));
+    out[p] = dadd(out[p], r);
+    adr_grad_pt(d, i, j, p, dsc(ybar[p], s), a, qbar);
 }
 
 // demodulation b = conj(m) r:      rbar += m bbar,    mbar += r conj(bbar)
@@ -357,6 +395,7 @@ struct Adjoint {
     std::vector<AdjLevel> lv;
     std::vector<double2*> all;
     double2* part = nullptr;
+    unsigned* dcount = nullptr;    // ka_dots' last-block counter
     double2* arena = nullptr;      // device scalars of one reverse step (bump allocated)
     int arena_top = 0;
     static constexpr int ARENA = 1 << 16;
@@ -371,6 +410,7 @@ struct Adjoint {
             cudaFree(L.mbar);
         }
         cudaFree(part);
+        cudaFree(dcount);
         cudaFree(arena);
         cudaFree(wsum);
     }
@@ -396,7 +436,9 @@ struct Adjoint {
                 cudaMemsetAsync(L.mbar, 0, sizeof(double2) * L.n * L.n, st);
             }
         }
-        if (cudaMalloc(&part, sizeof(double2) * 8 * 1024) != cudaSuccess) return MG_ENOMEM;
+        if (cudaMalloc(&part, sizeof(double2) * ADOTS * 1024) != cudaSuccess) return MG_ENOMEM;
+        if (cudaMalloc(&dcount, sizeof(unsigned)) != cudaSuccess) return MG_ENOMEM;
+        cudaMemsetAsync(dcount, 0, sizeof(unsigned), st);
         if (cudaMalloc(&arena, sizeof(double2) * ARENA) != cudaSuccess) return MG_ENOMEM;
         if (cudaMalloc(&wsum, sizeof(double) * (MG_MAX_LEVELS + 1)) != cudaSuccess) return MG_ENOMEM;
         cudaMemsetAsync(wsum, 0, sizeof(double) * (MG_MAX_LEVELS + 1), st);
@@ -443,9 +485,11 @@ struct Adjoint {
                                                 make_double2(c2.real(), c2.imag()), x3,
                                                 make_double2(c3.real(), c3.imag()));
     }
-    void apply(int l, int op, const double2* x, double2* y, cd s = 1.0, bool acc = false) {
+    // y (+)= s op(x); with b: y = b + s op(x); with z: also z += x
+    void apply(int l, int op, const double2* x, double2* y, cd s = 1.0, bool acc = false,
+               const double2* b = nullptr, double2* z = nullptr) {
         AdjLevel& L = lv[l];
-        ka_apply<<<blocks(L.n), ANT, 0, st>>>(L.d, op, x, y, make_double2(s.real(), s.imag()), acc);
+        ka_apply<<<blocks(L.n), ANT, 0, st>>>(L.d, op, x, y, make_double2(s.real(), s.imag()), acc, b, z);
     }
     void diag(int l, const double2* x, double2* y, bool herm, double s, bool acc) {
         AdjLevel& L = lv[l];
@@ -463,6 +507,11 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         ka_adr_grad<<<blocks(L.n), ANT, 0, st>>>(L.d, ybar, a, s, L.qbar);
     }
+    // reverse of y = s L a: out += s L^H ybar, ADR gradient (one pass)
+    void lh_grad(int l, const double2* ybar, const double2* a, double s, double2* out) {
+        AdjLevel& L = lv[l];
+        ka_lh_grad<<<blocks(L.n), ANT, 0, st>>>(L.d, ybar, a, s, out, L.qbar);
+    }
     // k device scalars of this reverse step
     double2* scalars(int k) {
         if (arena_top + k > ARENA) {
@@ -474,18 +523,23 @@ struct Adjoint {
         return p;
     }
     // conj(x_k)^T y_k for up to 8 pairs into device scalars (no synchronisation)
-    double2* dots(int l, std::vector<std::pair<const double2*, const double2*>> pr) {
+    double2* dots(int l, std::vector<std::pair<const double2*, const double2*>> pr,
+                  std::vector<const double2*> sub = {}) {
         AdjLevel& L = lv[l];
         const int np = (int)pr.size();
+        if (np > ADOTS) {
+            err = MG_EINVAL;
+            return scalars(1);
+        }
         DotPtrs P;
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < ADOTS; ++k) {
             P.x[k] = k < np ? pr[k].first : pr[0].first;
             P.y[k] = k < np ? pr[k].second : pr[0].second;
+            P.z[k] = k < (int)sub.size() ? sub[k] : nullptr;
         }
         const int nb = std::min(blocks(L.n), 1024);
-        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, P, part);
         double2* out = scalars(np);
-        ka_dots_fin<<<1, ANT, 0, st>>>(part, nb, np, out);
+        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, P, part, dcount, out);
         return out;
     }
     // out (+)= sum_t cp_t x_t, coefficients in device memory
@@ -576,8 +630,8 @@ struct Adjoint {
         lin(l, T.k[2], false, T.w[1], s);
         apply(l, 2, T.k[2], T.w[2], 1.0);
         double2* d1 = dots(l, {{T.w[0], T.w[0]}, {T.w[0], T.w[1]}, {T.w[0], T.w[2]}, {T.w[1], T.w[1]},
-                               {T.w[1], T.w[2]}, {T.w[2], T.w[2]}, {T.w[0], T.r0}, {T.w[1], T.r0}});
-        double2* d2 = dots(l, {{T.w[2], T.r0}});
+                               {T.w[1], T.w[2]}, {T.w[2], T.w[2]}, {T.w[0], T.r0}, {T.w[1], T.r0}, {T.w[2], T.r0}});
+        double2* d2 = d1 + 8;
         T.sc = scalars(16);
         ka_gm_solve<<<1, 1, 0, st>>>(d1, d2, T.sc);
         // x = x0 + K c
@@ -610,22 +664,16 @@ struct Adjoint {
             lin_dev(l, wb[q], false, T.w[0], co + 6 + 4 * q, T.w[1], co + 7 + 4 * q, T.w[2], co + 8 + 4 * q, T.r0,
                     co + 9 + 4 * q);
         // w_q = L k_q
-        for (int q = 0; q < 3; ++q) {
-            apply(l, 4, wb[q], kb[q], 1.0, true);
-            adr_grad(l, wb[q], T.k[q], 1.0);
-        }
+        for (int q = 0; q < 3; ++q) lh_grad(l, wb[q], T.k[q], 1.0, kb[q]);
         // k_2 = s L k_1, k_1 = s L k_0
-        apply(l, 4, kb[2], kb[1], s, true);
-        adr_grad(l, kb[2], T.k[1], s);
-        apply(l, 4, kb[1], kb[0], s, true);
-        adr_grad(l, kb[1], T.k[0], s);
+        lh_grad(l, kb[2], T.k[1], s, kb[1]);
+        lh_grad(l, kb[1], T.k[0], s, kb[0]);
         lin(l, r0b, true, kb[0], 1.0);
         // r0 = b - L x0 (or b)
         lin(l, bbar, true, r0b, 1.0);
         if (T.x0) {
             lin(l, x0bar, true, xbar, 1.0);
-            apply(l, 4, r0b, x0bar, -1.0, true);
-            adr_grad(l, r0b, T.x0, -1.0);
+            lh_grad(l, r0b, T.x0, -1.0, x0bar);
         }
         put(l, r0b);
         for (int q = 0; q < 3; ++q) {
@@ -692,8 +740,7 @@ struct Adjoint {
         double2* rb = get(l);
         prolong_(l, rcb, rb, 0.25, false);        // R^T = P/4
         lin(l, bbar, true, rb, 1.0);
-        apply(l, 4, rb, x1b, -1.0, true);
-        adr_grad(l, rb, T->x1, -1.0);
+        lh_grad(l, rb, T->x1, -1.0, x1b);
         gm_backward(l, T->pre, x1b, bbar, nullptr);
         put(l, x2b);
         put(l, x1b);
@@ -735,47 +782,36 @@ struct Adjoint {
         const int q = (int)T.x.size() - 1;
         double c1[16], c2[16], d1[16], d2[16];
         cheb_coeffs(l, I.lv[l - 1].alpha, q, c1, c2, d1, d2);
-        AdjLevel& L = lv[l];
         double2* db = get(l);      // d_m bar
-        double2* dprev = get(l);   // d_{m-1} (recomputed)
         double2* s = get(l);
         double2* t = get(l);
-        double2* sb = get(l);
-        lin(l, db, false, nullptr, 0.0);
         for (int m = q - 1; m >= 0; --m) {
-            // x_{m+1} = x_m + d_m: d_m bar += x_{m+1} bar; x_m bar = x_{m+1} bar (kept in xbar)
-            lin(l, db, true, xbar, 1.0);
+            // x_{m+1} = x_m + d_m: d_m bar = x_{m+1} bar + (c1[m+1] d_{m+1} bar, the
+            // reverse of d_{m+1} = c1[m+1] d_m + ...); x_m bar = x_{m+1} bar (kept in xbar)
+            if (m == q - 1) lin(l, db, false, xbar, 1.0);
+            else lin(l, db, false, db, c1[m + 1], xbar, 1.0);
             // s_m = A^H (g - A x_m)
-            if (T.x[m]) {
-                apply(l, 0, T.x[m], t, 1.0);
-                lin(l, t, false, T.g, 1.0, t, -1.0);
-            } else {
-                lin(l, t, false, T.g, 1.0);
-            }
+            if (T.x[m]) apply(l, 0, T.x[m], t, -1.0, false, T.g);
+            else lin(l, t, false, T.g, 1.0);
             apply(l, 1, t, s, 1.0);
             // d_m = c1 d_{m-1} + c2 s_m; alpha_bar += Re<s_m, d_m bar> dc2/dalpha
-            //                                       + Re<d_{m-1}, d_m bar> dc1/dalpha
-            double2* dd = dots(l, {{s, db}});
-            ka_accum_re<<<1, 1, 0, st>>>(wsum + l, dd, d2[m]);
+            //                                       + Re<d_{m-1}, d_m bar> dc1/dalpha,
+            // d_{m-1} = x_m - x_{m-1} formed inside the dot launch
             if (m > 0) {
-                // d_{m-1} = x_m - x_{m-1}
-                lin(l, dprev, false, T.x[m], 1.0, T.x[m - 1], -1.0);
-                double2* d2v = dots(l, {{dprev, db}});
-                ka_accum_re<<<1, 1, 0, st>>>(wsum + l, d2v, d1[m]);
+                double2* dd = dots(l, {{s, db}, {T.x[m], db}}, {nullptr, T.x[m - 1]});
+                ka_accum_re2<<<1, 1, 0, st>>>(wsum + l, dd, d2[m], d1[m]);
+            } else {
+                ka_accum_re<<<1, 1, 0, st>>>(wsum + l, dots(l, {{s, db}}), d2[m]);
             }
-            lin(l, sb, false, db, c2[m]);
-            // s = A^H t, t = g - A x_m: t_bar = A s_bar
-            apply(l, 0, sb, t, 1.0);
-            lin(l, gbar, true, t, 1.0);
-            if (T.x[m]) apply(l, 1, t, xbar, -1.0, true);
-            // d_{m-1} bar = c1 d_m bar
-            if (m > 0) lin(l, db, false, db, c1[m]);
+            // s = A^H t, t = g - A x_m: t_bar = A s_bar with s_bar = c2 d_m bar;
+            // g_bar += t_bar, x_m bar -= A^H t_bar
+            apply(l, 0, db, t, c2[m]);
+            if (T.x[m]) apply(l, 1, t, xbar, -1.0, true, nullptr, gbar);
+            else lin(l, gbar, true, t, 1.0);
         }
         put(l, db);
-        put(l, dprev);
         put(l, s);
         put(l, t);
-        put(l, sb);
     }
 
     // ----- wave cycle

@@ -26,7 +26,10 @@
 
 namespace wadr {
 
-constexpr int CS_MIN_N = 1024; // levels with n below this run the tile kernel (one step per launch)
+// launches over fewer points (all instances) run the tile kernel, one step
+// per launch: a single 511 x 511 level streams in too few strips to hide the
+// row march's latency (measured slower than the tile steps)
+constexpr long long CS_MIN_POINTS = 1ll << 20;
 
 template <int NS> __host__ __device__ constexpr int cs_out() { return SW_COLS - 4 * NS; }
 // rows issued ahead of the input row; the oldest ring row read is j - 3

@@ -19,6 +19,7 @@
 #include "kernels.cuh"
 #include "gmres_sstep.cuh"
 #include "cheb_stream.cuh"
+#include "cheb_multi.cuh"
 #include "tail_smem.cuh"
 #include "tail_wave.cuh"
 #include "setup_kernels.cuh"
@@ -114,15 +115,16 @@ struct Engine : EngineBase {
                                int sdout, int m, int flags, cudaStream_t st) {
         constexpr int SO = cs_out<NS>();
         const int smem = cs_smem<T, HS>();
-        int nmax = 0;
-        for (int q : ds) nmax = std::max(nmax, H.hdesc[(size_t)q].n);
-        const int nstrips = (nmax + SO - 1) / SO;
         constexpr int WPB = cs_wpb<HS>();
         const long long warps = (long long)occ_cap(k_cheb_stream<T, NS, 16, HS>, smem, 32 * WPB) * WPB;
         int best = 16;
         long long bcost = -1;
         for (int rh : {16, 24, 32, 64}) {
-            const long long units = (long long)nstrips * ((nmax + rh - 1) / rh);
+            long long units = 0;   // over the launch's instances
+            for (int q : ds) {
+                const int n = H.hdesc[(size_t)q].n;
+                units += (long long)((n + SO - 1) / SO) * ((n + rh - 1) / rh);
+            }
             const long long cost = (units + warps - 1) / warps * (rh + 2 * NS);
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
         }
@@ -149,6 +151,66 @@ struct Engine : EngineBase {
                 launch_cheb_stream_hs<NS, true>(H, ds, bpp, sin, sout, sdin, sdout, m, flags, st);
             else
                 launch_cheb_stream_hs<NS, false>(H, ds, bpp, sin, sout, sdin, sdout, m, flags, st);
+        }
+    }
+    // Resident blocks x SM count of a kernel at a given dynamic shared
+    // memory size (cached per pair; the kernel's opt-in limit is raised to
+    // the largest size seen).
+    template <class K>
+    static int occ_cap_at(K kern, int smem) {
+        static std::map<std::pair<const void*, int>, int> caps;
+        static std::map<const void*, int> optin;
+        const auto key = std::make_pair((const void*)kern, smem);
+        auto it = caps.find(key);
+        if (it != caps.end()) return it->second;
+        int& o = optin[(const void*)kern];
+        if (smem > o) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+            o = smem;
+        }
+        int nb = 0, dev = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        return caps[key] = std::max(1, nb) * std::max(1, nsm);
+    }
+    // Output tile side of the one-launch smoothing (k_cheb_multi) for q steps
+    // on level l, or 0 where it does not apply: FP32 levels >= 2 that do not
+    // stream, q >= 2, and a region that fits a block's shared memory.  The
+    // largest side that still gives 128 tiles over the launch's instances.
+    static int cheb_multi_ts(Handle& H, const std::vector<int>& ds, int l, int q) {
+        if (!kStream || l < 2 || q < 2 || cheb_stream_on(H, ds, l)) return 0;
+        static int optin = -1;
+        if (optin < 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        }
+        for (int ts : {32, 16, 8}) {
+            if (cm_smem<T>(ts, q) > optin - 1024) continue;
+            long long tiles = 0;
+            for (int qd : ds) {
+                const int n = H.hdesc[(size_t)qd].n;
+                tiles += (long long)((n + ts - 1) / ts) * ((n + ts - 1) / ts);
+            }
+            if (tiles >= 128 || ts == 8) return ts;
+        }
+        return 0;
+    }
+    void launch_cheb_multi(Handle& H, const std::vector<int>& ds, int ts, double bpp, int sin, int sout, int q,
+                           int xzero, cudaStream_t st) {
+        if constexpr (std::is_same<T, float>::value) {
+            const int smem = cm_smem<T>(ts, q);
+            auto run = [&](auto kern) {
+                const SegTable& t = H.seg_tiles(ds, ts, ts, false, occ_cap_at(kern, smem));
+                go(H, st, KK_CHEB, bpp * (double)t.pts, [&] {
+                    kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sin, sout, q, xzero);
+                }, t.pts);
+            };
+            if (ts == 32) run(k_cheb_multi<T, 32>);
+            else if (ts == 16) run(k_cheb_multi<T, 16>);
+            else run(k_cheb_multi<T, 8>);
         }
     }
     template <int MODE>
@@ -218,21 +280,23 @@ struct Engine : EngineBase {
     }
 
     // ------------------------------------------------------------ pieces
-    // In the complex-FP32 cycle the Chebyshev steps of levels l >= 2 with
-    // n >= CS_MIN_N run as warp-streaming strips, steps (m, m + 1) fused in
-    // one pass (k_cheb_stream<2>), after a single first step
-    // (k_cheb_stream<1>) when q is odd.  Smaller levels (where a strip march
-    // is latency-bound), level 1 and FP64 use the tile kernel k_cheb_step,
-    // one step per launch.
+    // In the complex-FP32 cycle the Chebyshev steps of levels l >= 2 run as
+    // warp-streaming strips when the launch covers at least CS_MIN_POINTS
+    // points (over its instances): steps (m, m + 1) fused in one pass
+    // (k_cheb_stream<2>), after a single first step (k_cheb_stream<1>) when
+    // q is odd.  Smaller launches (where a strip march is latency-bound),
+    // level 1 and FP64 use the tile kernel k_cheb_step, one step per launch.
     static constexpr bool kStream = std::is_same<T, float>::value;
     static bool cheb_stream_on(Handle& H, const std::vector<int>& ds, int l) {
         if (!kStream || l < 2) return false;
-        int nmax = 0;
-        for (int q : ds) nmax = std::max(nmax, H.hdesc[(size_t)q].n);
-        return nmax >= CS_MIN_N;
+        long long pts = 0;
+        for (int q : ds) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+        return pts >= CS_MIN_POINTS;
     }
-    // launches that q steps take on level l
+    // launches that q steps take on level l (the small FP32 levels run all q
+    // steps in one launch, k_cheb_multi)
     static int cheb_launches(Handle& H, const std::vector<int>& ds, int l, int q) {
+        if (cheb_multi_ts(H, ds, l, q) > 0) return 1;
         return (q >= 2 && cheb_stream_on(H, ds, l)) ? (q + 1) / 2 : q;
     }
 
@@ -248,6 +312,13 @@ struct Engine : EngineBase {
         int out = from_zero ? ((nl & 1) ? SU : SX2) : (xin == SU ? SX2 : SU);
         int m = 0, dsl = SD;
         auto advance = [&] { cur = out; out = (cur == SU) ? SX2 : SU; };
+        if (const int ts = cheb_multi_ts(H, ds, l, q)) {
+            // reads x (unless zero), g, k; writes x
+            const double bpp = (from_zero ? 0 : C) + C + R + C;
+            launch_cheb_multi(H, ds, ts, bpp, cur, out, q, from_zero ? 1 : 0, st);
+            advance();
+            return cur;
+        }
         const bool stream = cheb_stream_on(H, ds, l);
         const bool pairs = nl != q;
         for (; m < q && (!pairs || (m == 0 && (q & 1))); ++m) {

@@ -17,8 +17,9 @@ inputs of the library, widened):
   n = 2047 and 4095 the cycle amplifies the residual (72x and 2700x per
   cycle: the ADR corrections with the eikonal phase are not a convergent
   iteration at these sizes) and the FP32 rounding of the corrections is
-  amplified with it: 1.1e-5 and 1.8e-5 - 3.8e-5.  Those cases keep the 1e-5
-  bound and are expected failures (strict: a pass would be reported);
+  amplified with it: 1.1e-5 and 7.2e-6 - 3.8e-5, depending on the rounding
+  path of the kernels.  Those cases keep the 1e-5 bound and are expected
+  failures that may pass (not strict);
 - 25 FGMRES iterations (one restart) through mg_solve_begin/steps/end: the
   relative residual the library reports equals the oracle's FP64 residual of
   the returned iterate to 1e-9 (with M = 8 on this medium the residual
@@ -107,10 +108,12 @@ def _cycle_rel(I, h, H):
 
 
 AMPLIFYING = ("the paper's M = 8 corrections amplify the residual at this size with the eikonal phase, and the "
-              "FP32 rounding of the corrections with it")
+              "FP32 rounding of the corrections with it: the deviation depends on the rounding path of the kernels "
+              "and straddles 1e-5 (7.2e-6 to 3.8e-5 at n = 4095 over kernel variants), so the bound is kept and the "
+              "test is an expected failure that may pass")
 
 
-@pytest.mark.xfail(strict=True, reason=AMPLIFYING)
+@pytest.mark.xfail(strict=False, reason=AMPLIFYING)
 def test_fullsize_cycle_m8(full):
     """One Wave-ADR cycle of the timed steps (M = 8) from zero on the
     normalised source against the FP64 oracle cycle, to the mixed form's
@@ -139,7 +142,7 @@ def test_fullsize_cycle_time_to_tolerance_configuration():
 
 @pytest.mark.parametrize("n,M,closure", [
     (1023, 8, "zero"), (2047, 2, "abc"),
-    pytest.param(2047, 8, "zero", marks=pytest.mark.xfail(strict=True, reason=AMPLIFYING))])
+    pytest.param(2047, 8, "zero", marks=pytest.mark.xfail(strict=False, reason=AMPLIFYING))])
 def test_smaller_cycles_of_the_same_recipe(n, M, closure):
     """The same medium and recipe at n = 1023 and 2047 (omega scaled to keep
     k h), to 1e-5 per cycle, for every halo-tile candidate (each fixes a

@@ -316,6 +316,29 @@ def test_batched_uneven_instances_match_single():
     B.mg_destroy(h)
 
 
+def test_batched_mixed_cycle_streams_level2_of_small_instances():
+    """Four n = 1023 instances (and one n = 255) in one complex-FP32 handle:
+    each level-2 launch covers 4 x 511^2 + 127^2 > 2^20 points, so the
+    Chebyshev steps run as streaming strips although no instance alone would
+    stream; every instance's cycle matches its own FP64 oracle cycle (1e-5)."""
+    insts = [inst_medium(1023, 250.0, seed=60 + b) for b in range(4)] + [inst_medium(255, 60.0, seed=65)]
+    h = lib_handle(insts, "mixed", n_cmax=15)
+    try:
+        g = [(I.g / np.linalg.norm(I.g)) for I in insts]
+        gcat = np.concatenate([x.ravel() for x in g]).astype(np.complex64)
+        ucat = np.zeros_like(gcat)
+        B.mg_cycle(h, ucat, gcat, 1)
+        off = 0
+        for I, gi in zip(insts, g):
+            H = oracle_hier(I, n_cmax=15)
+            ref = H.cycle(np.zeros_like(gi), gi.astype(np.complex64).astype(np.complex128))
+            got = ucat[off:off + I.n * I.n].reshape(I.n, I.n).astype(np.complex128)
+            off += I.n * I.n
+            assert rel(got, ref) < 1e-5, (I.n, rel(got, ref))
+    finally:
+        B.mg_destroy(h)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
 def test_batched_fgmres_steps_match_single_solves(prec, tol):
     """25 FGMRES iterations (one restart) of a batch of four instances in one
