@@ -20,6 +20,7 @@
 #include "gmres_sstep.cuh"
 #include "cheb_stream.cuh"
 #include "cheb_multi.cuh"
+#include "restrict_stream.cuh"
 #include "tail_smem.cuh"
 #include "tail_wave.cuh"
 #include "setup_kernels.cuh"
@@ -212,6 +213,52 @@ struct Engine : EngineBase {
             else if (ts == 16) run(k_cheb_multi<T, 16>);
             else run(k_cheb_multi<T, 8>);
         }
+    }
+    // Level-1 pre-smoothing from zero + residual + restriction as
+    // warp-streaming strips (k_restrict_jac0_stream, complex FP32) for
+    // launches of at least CS_MIN_POINTS points; band height of coarse rows
+    // chosen as for the Chebyshev strips.  Returns false where it does not
+    // apply (FP64, small launches).
+    template <bool HS>
+    void launch_restrict_jac0_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, cudaStream_t st) {
+        const int smem = rs_smem<T, HS>();
+        const long long warps = (long long)occ_cap(k_restrict_jac0_stream<T, 16, HS>, smem, 32 * RS_WPB) * RS_WPB;
+        int best = 16;
+        long long bcost = -1;
+        for (int rh : {8, 16, 32}) {
+            long long units = 0;
+            for (int q : ds) {
+                const int n = H.hdesc[(size_t)q].n, nc = (n - 1) / 2;
+                units += (long long)((n + RS_SO - 1) / RS_SO) * ((nc + rh - 1) / rh);
+            }
+            const long long cost = (units + warps - 1) / warps * (2 * rh + 3);
+            if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
+        }
+        auto run = [&](auto kern, int rh) {
+            // segment shares by fine points: a unit is RS_SO x 2 rh fine nodes
+            const SegTable& t = H.seg_tiles(ds, RS_SO, 2 * rh * RS_WPB, false, occ_cap(kern, smem, 32 * RS_WPB));
+            go(H, st, KK_RESTRICT_JAC0, bpp * (double)t.pts, [&] {
+                kl(kern, t.nblocks, dim3(32, RS_WPB), smem, st, kd(H, t), t.d, t.nseg, SU, SG, SG);
+            }, t.pts);
+        };
+        if (best == 8) run(k_restrict_jac0_stream<T, 8, HS>, 8);
+        else if (best == 16) run(k_restrict_jac0_stream<T, 16, HS>, 16);
+        else run(k_restrict_jac0_stream<T, 32, HS>, 32);
+    }
+    bool launch_restrict_jac0_stream(Handle& H, const std::vector<int>& ds, double bpp, cudaStream_t st) {
+        if constexpr (std::is_same<T, float>::value) {
+            long long pts = 0;
+            bool hs = false;
+            for (int q : ds) {
+                pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+                hs = hs || H.hdesc[(size_t)q].sig != nullptr;
+            }
+            if (pts < CS_MIN_POINTS) return false;
+            if (hs) launch_restrict_jac0_stream_hs<true>(H, ds, bpp, st);
+            else launch_restrict_jac0_stream_hs<false>(H, ds, bpp, st);
+            return true;
+        }
+        return false;
     }
     template <int MODE>
     void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
@@ -737,7 +784,8 @@ struct Engine : EngineBase {
         const std::vector<int> ds1 = descs(H, 1, I);
         const SegTable& t = H.seg(ds1, false, kPts);
         if (uzero) {
-            launch_restrict<MODE_JAC0>(H, ds1, KK_RESTRICT_JAC0, 2 * C + R + C / 4, SU, SG, SG, 1, st);
+            if (!launch_restrict_jac0_stream(H, ds1, 2 * C + R + C / 4, st))
+                launch_restrict<MODE_JAC0>(H, ds1, KK_RESTRICT_JAC0, 2 * C + R + C / 4, SU, SG, SG, 1, st);
         } else {
             LAUNCH(KK_JACOBI, t, 3 * C + R, k_jacobi<T>, SX2, SG, SU, 0);
             launch_restrict<MODE_HELM>(H, ds1, KK_RESTRICT_HELM, 2 * C + R + C / 4, SU, SG, SG, 0, st);

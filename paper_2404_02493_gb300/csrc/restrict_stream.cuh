@@ -1,0 +1,129 @@
+// Level-1 pre-smoothing from zero fused with the residual and its full
+// weighting restriction (the k_restrict<MODE_JAC0> operation), as
+// warp-streaming strips (stream.cuh), complex FP32:
+//   u1 = w D^{-1} g  (to slot sx),  r = g - A u1,  r_c = R r  (to slot sc of level 2)
+// A strip holds 64 fine columns X0 .. X0 + 63, X0 = 60 k - 2; lanes 1 .. 30
+// own the fine columns [60 k, 60 k + 60) (two each) and the coarse columns
+// [30 k, 30 k + 30): coarse column I of lane L has its fine centre at the
+// lane's second column, the third fine column comes from the next lane.  A
+// unit is a strip and a band of coarse rows [J0, J1); its march over fine
+// input rows j forms u1 at row j (pointwise), r at row j - 1 and, when
+// j - 1 = 2 J + 2, coarse row J from r rows 2 J .. 2 J + 2.  g, k and the
+// sponge term arrive by one cp.async per lane and row into a per-warp ring.
+// u1 is zero outside the grid because g is zero-filled there; r is only used
+// inside it.  The arithmetic per node and its order are those of
+// k_restrict<MODE_JAC0>.
+#pragma once
+#include "cheb_stream.cuh"
+
+namespace wadr {
+
+constexpr int RS_SO = 60;   // fine result columns per strip
+constexpr int RS_AH = 6;    // rows issued ahead (the oldest ring row read is j - 1)
+template <typename T, bool HS> __host__ __device__ constexpr int rs_ring_bytes() {
+    return (int)((sizeof(cplx<T>) + (HS ? 2 : 1) * sizeof(T)) * SW_DEP * SW_COLS);
+}
+constexpr int RS_WPB = 8;
+template <typename T, bool HS> __host__ __device__ constexpr int rs_smem() { return RS_WPB * rs_ring_bytes<T, HS>(); }
+
+template <typename T, int RHC, bool HS>
+__global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __grid_constant__ KDesc A,
+                                                                      const Seg* __restrict__ Sg, int nseg, int sx,
+                                                                      int sb, int sc) {
+    extern __shared__ __align__(16) unsigned char rs_smem_[];
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = lane + 32 * warp;
+    unsigned char* const base = rs_smem_ + warp * rs_ring_bytes<T, HS>();
+    cplx<T>* const Gr = reinterpret_cast<cplx<T>*>(base);
+    T* const Kr = reinterpret_cast<T*>(Gr + SW_DEP * SW_COLS);
+    T* const Sr = Kr + SW_DEP * SW_COLS;
+    __shared__ LevelDesc d;
+    __shared__ LevelDesc dc;
+    SegCtx c = seg_begin(A, Sg, nseg, d);
+    coarse_desc(A, nseg, d, dc, tid);
+    __syncthreads();
+    const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
+    const int nstrips = (n + RS_SO - 1) / RS_SO, nunits = nstrips * ((nc + RHC - 1) / RHC);
+    const cplx<T>* const gv = slot<T>(d, sb);
+    cplx<T>* const xs = slot<T>(d, sx);
+    cplx<T>* const out = slot<T>(dc, sc);
+    const T* const kf = reinterpret_cast<const T*>(d.kf);
+    const T* const sgf = reinterpret_cast<const T*>(d.sig);
+    const T ih2 = LC<T>::ih2(d);
+    const T wj = scalp<T>(d)[S::OMEGA_J];
+    const T h2 = LC<T>::h(d) * LC<T>::h(d);
+    const bool own = lane >= 1 && lane <= 30;
+    for (int u = c.lb * RS_WPB + warp; u < nunits; u += c.nb * RS_WPB) {
+        const int sk = u % nstrips, band = u / nstrips;
+        const int X0 = RS_SO * sk - 2;
+        const int J0 = RHC * band, J1 = min(J0 + RHC, nc);
+        const int fy0 = 2 * J0, fy1 = (J1 == nc) ? n : 2 * J1;   // own fine rows of u1
+        const int j0 = 2 * J0 - 1, j1 = 2 * J1 + 1;
+        const int col = X0 + 2 * lane;
+        const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
+        const int I = X0 / 2 + lane;   // coarse column of the lane
+        auto issue = [&](int r) {
+            ring_issue2<cplx<T>>(Gr, gv, n, pitch, X0, r, lane);
+            ring_issue2<T>(Kr, kf, n, pitch, X0, r, lane);
+            if (HS) ring_issue2<T>(Sr, sgf, n, pitch, X0, r, lane);
+        };
+#pragma unroll
+        for (int r = 0; r < RS_AH; ++r) {
+            if (j0 + r <= j1) issue(j0 + r);
+            cp_async_commit();
+        }
+        P2<T> ua2 = p2zero<T>(), ua1 = p2zero<T>();   // u1 at j-2, j-1
+        P2<T> dg1 = p2zero<T>();                      // diagonal at j-1
+        P2<T> r3 = p2zero<T>(), r2 = p2zero<T>();     // r at j-3, j-2
+        for (int j = j0; j <= j1; ++j) {
+            if (j + RS_AH <= j1) issue(j + RS_AH);
+            cp_async_commit();
+            cp_async_wait<RS_AH>();
+            // u1 = w h^2 g / (h^2 D) at row j (one division per node)
+            P2<T> g0;
+            ring_read<cplx<T>>(Gr, j, lane, g0.v0, g0.v1);
+            T k0, k1, s0 = T(0), s1 = T(0);
+            ring_read<T>(Kr, j, lane, k0, k1);
+            if (HS) ring_read<T>(Sr, j, lane, s0, s1);
+            const P2<T> dg0 = diag_row<T>(d, j, col, k0, k1, s0, s1);
+            P2<T> u0;
+            {
+                const T a0 = wj * h2 / (dg0.v0.x * dg0.v0.x + dg0.v0.y * dg0.v0.y);
+                const T a1 = wj * h2 / (dg0.v1.x * dg0.v1.x + dg0.v1.y * dg0.v1.y);
+                u0.v0 = mk<T>((g0.v0.x * dg0.v0.x + g0.v0.y * dg0.v0.y) * a0,
+                              (g0.v0.y * dg0.v0.x - g0.v0.x * dg0.v0.y) * a0);
+                u0.v1 = mk<T>((g0.v1.x * dg0.v1.x + g0.v1.y * dg0.v1.y) * a1,
+                              (g0.v1.y * dg0.v1.x - g0.v1.x * dg0.v1.y) * a1);
+            }
+            if (own && j >= fy0 && j < fy1) {
+                const long long p = (long long)j * pitch + col;
+                if (cin0) xs[p] = u0.v0;
+                if (cin1) xs[p + 1] = u0.v1;
+            }
+            // r = g - A u1 at row j - 1
+            P2<T> rr;
+            ring_read<cplx<T>>(Gr, j - 1, lane, rr.v0, rr.v1);
+            const P2<T> au = helm_row<T, false>(dg1, ua1, ua2, u0, ih2);
+            rr.v0 = csub<T>(rr.v0, au.v0);
+            rr.v1 = csub<T>(rr.v1, au.v1);
+            // coarse row J = (j - 3) / 2 from r rows 2 J (r3), 2 J + 1 (r2), 2 J + 2 (rr)
+            if (((j - j0) & 1) == 0 && j >= j0 + 4) {
+                const int J = (j - 3) >> 1;
+                const cplx<T> e3 = shfl_dn1<T>(r3.v0), e2 = shfl_dn1<T>(r2.v0), e1 = shfl_dn1<T>(rr.v0);
+                if (own && I < nc && J < J1) {
+                    const cplx<T> s4 = r2.v1;
+                    const cplx<T> s2 = cadd<T>(cadd<T>(r2.v0, e2), cadd<T>(r3.v1, rr.v1));
+                    const cplx<T> s1 = cadd<T>(cadd<T>(r3.v0, e3), cadd<T>(rr.v0, e1));
+                    const cplx<T> v = cadd<T>(cadd<T>(cscale<T>(s4, T(4)), cscale<T>(s2, T(2))), s1);
+                    out[(long long)J * cpitch + I] = cscale<T>(v, T(0.0625));
+                }
+            }
+            r3 = r2; r2 = rr;
+            ua2 = ua1; ua1 = u0;
+            dg1 = dg0;
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+}
+
+}  // namespace wadr

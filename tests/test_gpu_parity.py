@@ -339,6 +339,27 @@ def test_batched_mixed_cycle_streams_level2_of_small_instances():
         B.mg_destroy(h)
 
 
+@pytest.mark.parametrize("n", [1100, 1081])
+def test_mixed_cycle_streaming_level1(n):
+    """One complex-FP32 cycle from zero at n = 1100 (even: the last fine row
+    and column lie beyond the coarse grid's footprint) and n = 1081 (the last
+    60-column strip holds one column): level 1's pre-smoothing, residual and
+    restriction run as streaming strips (n^2 >= 2^20); the cycle matches the
+    FP64 oracle cycle to 1e-5."""
+    I = inst_medium(n, 0.25 * n, seed=70 + n % 7)
+    h = lib_handle([I], "mixed", n_cmax=15, M=2)
+    try:
+        g = I.g / np.linalg.norm(I.g)
+        g32 = g.astype(np.complex64)
+        u = np.zeros_like(g32)
+        B.mg_cycle(h, u, g32, 1)
+        H = oracle_hier(I, n_cmax=15, M=2)
+        ref = H.cycle(np.zeros_like(g), g32.astype(np.complex128))
+        assert rel(u.astype(np.complex128), ref) < 1e-5, rel(u, ref)
+    finally:
+        B.mg_destroy(h)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
 def test_batched_fgmres_steps_match_single_solves(prec, tol):
     """25 FGMRES iterations (one restart) of a batch of four instances in one
