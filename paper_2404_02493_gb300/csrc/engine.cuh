@@ -260,6 +260,51 @@ struct Engine : EngineBase {
         }
         return false;
     }
+    // Level-1 prolongation + Jacobi post-smoothing as warp-streaming strips
+    // (k_prolong_jac_stream, complex FP32) for launches of at least
+    // CS_MIN_POINTS points; false where it does not apply.
+    template <bool HS>
+    void launch_prolong_jac_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, int sx, int sc, int sb,
+                                      int sout, cudaStream_t st) {
+        const int smem = ps_smem<T, HS>();
+        const long long warps = (long long)occ_cap(k_prolong_jac_stream<T, 32, HS>, smem, 32 * RS_WPB) * RS_WPB;
+        int best = 32;
+        long long bcost = -1;
+        for (int rh : {16, 32, 64}) {
+            long long units = 0;
+            for (int q : ds) {
+                const int n = H.hdesc[(size_t)q].n;
+                units += (long long)((n + RS_SO - 1) / RS_SO) * ((n + rh - 1) / rh);
+            }
+            const long long cost = (units + warps - 1) / warps * (rh + 2);
+            if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
+        }
+        auto run = [&](auto kern, int rh) {
+            const SegTable& t = H.seg_tiles(ds, RS_SO, rh * RS_WPB, false, occ_cap(kern, smem, 32 * RS_WPB));
+            go(H, st, KK_PROLONG_JAC, bpp * (double)t.pts, [&] {
+                kl(kern, t.nblocks, dim3(32, RS_WPB), smem, st, kd(H, t), t.d, t.nseg, sx, sc, sb, sout);
+            }, t.pts);
+        };
+        if (best == 16) run(k_prolong_jac_stream<T, 16, HS>, 16);
+        else if (best == 32) run(k_prolong_jac_stream<T, 32, HS>, 32);
+        else run(k_prolong_jac_stream<T, 64, HS>, 64);
+    }
+    bool launch_prolong_jac_stream(Handle& H, const std::vector<int>& ds, double bpp, int sx, int sc, int sb,
+                                   int sout, cudaStream_t st) {
+        if constexpr (std::is_same<T, float>::value) {
+            long long pts = 0;
+            bool hs = false;
+            for (int q : ds) {
+                pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+                hs = hs || H.hdesc[(size_t)q].sig != nullptr;
+            }
+            if (pts < CS_MIN_POINTS) return false;
+            if (hs) launch_prolong_jac_stream_hs<true>(H, ds, bpp, sx, sc, sb, sout, st);
+            else launch_prolong_jac_stream_hs<false>(H, ds, bpp, sx, sc, sb, sout, st);
+            return true;
+        }
+        return false;
+    }
     template <int MODE>
     void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
                          cudaStream_t st) {
@@ -791,7 +836,8 @@ struct Engine : EngineBase {
             launch_restrict<MODE_HELM>(H, ds1, KK_RESTRICT_HELM, 2 * C + R + C / 4, SU, SG, SG, 0, st);
         }
         wave(H, 2, I, st);
-        launch_prolong<PMODE_JAC>(H, ds1, KK_PROLONG_JAC, 3 * C + C / 4 + R, SU, SU, SG, SD, SD, 0, st);
+        if (!launch_prolong_jac_stream(H, ds1, 3 * C + C / 4 + R, SU, SU, SG, SD, st))
+            launch_prolong<PMODE_JAC>(H, ds1, KK_PROLONG_JAC, 3 * C + C / 4 + R, SU, SU, SG, SD, SD, 0, st);
     }
 
     const SegTable& outer_tab(Handle& H) {

@@ -126,4 +126,136 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
     }
 }
 
+// ------------------------------------------------------------ prolongation + Jacobi
+// The level-1 post-smoothing step (the k_prolong<PMODE_JAC> operation) as
+// warp-streaming strips, complex FP32:
+//   u = x + P e  (e: the coarse correction, slot sc of level 2),
+//   out = u + w D^{-1} (g - A u)  (slot sout).
+// Strips and owned columns as above; lane L also holds coarse column
+// X0 / 2 + L: an odd fine column lies on it, an even one halfway between it
+// and the previous lane's.  A fine row r lies on coarse row (r - 1) / 2 (odd
+// r) or halfway between rows r / 2 - 1 and r / 2 (even r); coarse row r / 2 is
+// issued with fine row r into a small per-warp ring.  March: u at input row
+// j, the Jacobi update at row j - 1.  u is zero outside the grid.
+constexpr int PS_AH = 6;   // fine rows issued ahead (the oldest read is j - 1)
+template <typename T, bool HS> __host__ __device__ constexpr int ps_ring_bytes() {
+    return (int)((2 * sizeof(cplx<T>) + (HS ? 2 : 1) * sizeof(T)) * SW_DEP * SW_COLS +
+                 sizeof(cplx<T>) * SW_DEP * 32);
+}
+template <typename T, bool HS> __host__ __device__ constexpr int ps_smem() { return RS_WPB * ps_ring_bytes<T, HS>(); }
+
+template <typename T, int RH, bool HS>
+__global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid_constant__ KDesc A,
+                                                                    const Seg* __restrict__ Sg, int nseg, int sx,
+                                                                    int sc, int sb, int sout) {
+    extern __shared__ __align__(16) unsigned char ps_smem_[];
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = lane + 32 * warp;
+    unsigned char* const base = ps_smem_ + warp * ps_ring_bytes<T, HS>();
+    cplx<T>* const Xr = reinterpret_cast<cplx<T>*>(base);
+    cplx<T>* const Gr = Xr + SW_DEP * SW_COLS;
+    T* const Kr = reinterpret_cast<T*>(Gr + SW_DEP * SW_COLS);
+    T* const Sr = Kr + SW_DEP * SW_COLS;
+    cplx<T>* const Er = reinterpret_cast<cplx<T>*>(Kr + (HS ? 2 : 1) * SW_DEP * SW_COLS);   // [SW_DEP][32]
+    __shared__ LevelDesc d;
+    __shared__ LevelDesc dc;
+    SegCtx c = seg_begin(A, Sg, nseg, d);
+    coarse_desc(A, nseg, d, dc, tid);
+    __syncthreads();
+    const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
+    const int nstrips = (n + RS_SO - 1) / RS_SO, nunits = nstrips * ((n + RH - 1) / RH);
+    const cplx<T>* const xv = slot<T>(d, sx);
+    const cplx<T>* const gv = slot<T>(d, sb);
+    const cplx<T>* const ev = slot<T>(dc, sc);
+    cplx<T>* const os = slot<T>(d, sout);
+    const T* const kf = reinterpret_cast<const T*>(d.kf);
+    const T* const sgf = reinterpret_cast<const T*>(d.sig);
+    const T ih2 = LC<T>::ih2(d);
+    const T wjh2 = scalp<T>(d)[S::OMEGA_J] * LC<T>::h(d) * LC<T>::h(d);
+    const bool own = lane >= 1 && lane <= 30;
+    for (int u = c.lb * RS_WPB + warp; u < nunits; u += c.nb * RS_WPB) {
+        const int sk = u % nstrips, band = u / nstrips;
+        const int X0 = RS_SO * sk - 2;
+        const int y0 = RH * band, y1 = min(y0 + RH, n);
+        const int j0 = y0 - 1, j1 = y1;
+        const int col = X0 + 2 * lane;
+        const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
+        const int ci = X0 / 2 + lane;   // the lane's coarse column
+        const bool cci = (unsigned)ci < (unsigned)nc;
+        auto issue = [&](int r) {
+            ring_issue2<cplx<T>>(Xr, xv, n, pitch, X0, r, lane);
+            ring_issue2<cplx<T>>(Gr, gv, n, pitch, X0, r, lane);
+            ring_issue2<T>(Kr, kf, n, pitch, X0, r, lane);
+            if (HS) ring_issue2<T>(Sr, sgf, n, pitch, X0, r, lane);
+            if (!(r & 1) || r == j0) {
+                // coarse row r / 2 (for the first row, the row below it as well)
+                const int cr = (r & 1) ? (r - 1) >> 1 : r >> 1;
+                const bool ok = cci && (unsigned)cr < (unsigned)nc;
+                cp_async_elem<cplx<T>>(Er + (cr & (SW_DEP - 1)) * 32 + lane,
+                                       ok ? ev + (long long)cr * cpitch + ci : ev, ok);
+                if (r == j0 && !(r & 1)) {
+                    const int cb = (r >> 1) - 1;
+                    const bool okb = cci && (unsigned)cb < (unsigned)nc;
+                    cp_async_elem<cplx<T>>(Er + (cb & (SW_DEP - 1)) * 32 + lane,
+                                           okb ? ev + (long long)cb * cpitch + ci : ev, okb);
+                }
+            }
+        };
+#pragma unroll
+        for (int r = 0; r < PS_AH; ++r) {
+            if (j0 + r <= j1) issue(j0 + r);
+            cp_async_commit();
+        }
+        P2<T> ua2 = p2zero<T>(), ua1 = p2zero<T>();   // u at j-2, j-1
+        for (int j = j0; j <= j1; ++j) {
+            if (j + PS_AH <= j1) issue(j + PS_AH);
+            cp_async_commit();
+            cp_async_wait<PS_AH>();
+            // u = x + P e at row j: coarse rows ja and ja + 1 (weights wb0, wb1)
+            const int ja = (j - 1) >> 1;
+            const T wb0 = (j & 1) ? T(1) : T(0.5), wb1 = T(1) - wb0;
+            const cplx<T> elo = Er[(ja & (SW_DEP - 1)) * 32 + lane];
+            const cplx<T> ehi = (j & 1) ? zero2<T>() : Er[((ja + 1) & (SW_DEP - 1)) * 32 + lane];
+            const cplx<T> plo = shfl_up1<T>(elo), phi = shfl_up1<T>(ehi);   // coarse column ci - 1
+            P2<T> u0;
+            // even fine column col: coarse ci - 1, ci with (1/2, 1/2); odd col + 1: coarse ci with (1, 0)
+            u0.v0 = cscale<T>(cadd<T>(cscale<T>(plo, T(0.5)), cscale<T>(elo, T(0.5))), wb0);
+            u0.v0 = cadd<T>(u0.v0, cscale<T>(cadd<T>(cscale<T>(phi, T(0.5)), cscale<T>(ehi, T(0.5))), wb1));
+            u0.v1 = cadd<T>(cscale<T>(elo, wb0), cscale<T>(ehi, wb1));
+            P2<T> x0;
+            ring_read<cplx<T>>(Xr, j, lane, x0.v0, x0.v1);
+            u0.v0 = cadd<T>(x0.v0, u0.v0);
+            u0.v1 = cadd<T>(x0.v1, u0.v1);
+            const bool roj = (unsigned)j < (unsigned)n;
+            u0 = p2sel<T>(u0, roj && cin0, roj && cin1);
+            // Jacobi at row j - 1
+            const int r1 = j - 1;
+            T k0, k1, s0 = T(0), s1 = T(0);
+            ring_read<T>(Kr, r1, lane, k0, k1);
+            if (HS) ring_read<T>(Sr, r1, lane, s0, s1);
+            const P2<T> dg = diag_row<T>(d, r1, col, k0, k1, s0, s1);
+            P2<T> rr;
+            ring_read<cplx<T>>(Gr, r1, lane, rr.v0, rr.v1);
+            const P2<T> au = helm_row<T, false>(dg, ua1, ua2, u0, ih2);
+            rr.v0 = csub<T>(rr.v0, au.v0);
+            rr.v1 = csub<T>(rr.v1, au.v1);
+            if (own && r1 >= y0 && r1 < y1) {
+                const long long p = (long long)r1 * pitch + col;
+                if (cin0) {
+                    const T a = wjh2 / (dg.v0.x * dg.v0.x + dg.v0.y * dg.v0.y);
+                    os[p] = cadd<T>(ua1.v0, mk<T>((rr.v0.x * dg.v0.x + rr.v0.y * dg.v0.y) * a,
+                                                  (rr.v0.y * dg.v0.x - rr.v0.x * dg.v0.y) * a));
+                }
+                if (cin1) {
+                    const T a = wjh2 / (dg.v1.x * dg.v1.x + dg.v1.y * dg.v1.y);
+                    os[p + 1] = cadd<T>(ua1.v1, mk<T>((rr.v1.x * dg.v1.x + rr.v1.y * dg.v1.y) * a,
+                                                      (rr.v1.y * dg.v1.x - rr.v1.x * dg.v1.y) * a));
+                }
+            }
+            ua2 = ua1; ua1 = u0;
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+}
+
 }  // namespace wadr
