@@ -263,34 +263,37 @@ struct Engine : EngineBase {
     // Level-1 prolongation + Jacobi post-smoothing as warp-streaming strips
     // (k_prolong_jac_stream, complex FP32) for launches of at least
     // CS_MIN_POINTS points; false where it does not apply.
-    template <bool HS>
+    template <bool HS, bool FG>
     void launch_prolong_jac_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, int sx, int sc, int sb,
                                       int sout, cudaStream_t st) {
+        constexpr int SO = FG ? SW_OUT : RS_SO;
         const int smem = ps_smem<T, HS>();
-        const long long warps = (long long)occ_cap(k_prolong_jac_stream<T, 32, HS>, smem, 32 * RS_WPB) * RS_WPB;
+        const long long warps = (long long)occ_cap(k_prolong_jac_stream<T, 32, HS, FG>, smem, 32 * RS_WPB) * RS_WPB;
         int best = 32;
         long long bcost = -1;
         for (int rh : {16, 32, 64}) {
             long long units = 0;
             for (int q : ds) {
                 const int n = H.hdesc[(size_t)q].n;
-                units += (long long)((n + RS_SO - 1) / RS_SO) * ((n + rh - 1) / rh);
+                units += (long long)((n + SO - 1) / SO) * ((n + rh - 1) / rh);
             }
-            const long long cost = (units + warps - 1) / warps * (rh + 2);
+            const long long cost = (units + warps - 1) / warps * (rh + (FG ? 4 : 2));
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
         }
         auto run = [&](auto kern, int rh) {
-            const SegTable& t = H.seg_tiles(ds, RS_SO, rh * RS_WPB, false, occ_cap(kern, smem, 32 * RS_WPB));
+            const SegTable& t = H.seg_tiles(ds, SO, rh * RS_WPB, false, occ_cap(kern, smem, 32 * RS_WPB));
             go(H, st, KK_PROLONG_JAC, bpp * (double)t.pts, [&] {
                 kl(kern, t.nblocks, dim3(32, RS_WPB), smem, st, kd(H, t), t.d, t.nseg, sx, sc, sb, sout);
             }, t.pts);
         };
-        if (best == 16) run(k_prolong_jac_stream<T, 16, HS>, 16);
-        else if (best == 32) run(k_prolong_jac_stream<T, 32, HS>, 32);
-        else run(k_prolong_jac_stream<T, 64, HS>, 64);
+        if (best == 16) run(k_prolong_jac_stream<T, 16, HS, FG>, 16);
+        else if (best == 32) run(k_prolong_jac_stream<T, 32, HS, FG>, 32);
+        else run(k_prolong_jac_stream<T, 64, HS, FG>, 64);
     }
+    // fg: inside an FGMRES iteration, write z to Z_j and A z to V_{j+1}
+    // (the separate k_fg_matvec launch is then left out)
     bool launch_prolong_jac_stream(Handle& H, const std::vector<int>& ds, double bpp, int sx, int sc, int sb,
-                                   int sout, cudaStream_t st) {
+                                   int sout, bool fg, cudaStream_t st) {
         if constexpr (std::is_same<T, float>::value) {
             long long pts = 0;
             bool hs = false;
@@ -299,12 +302,20 @@ struct Engine : EngineBase {
                 hs = hs || H.hdesc[(size_t)q].sig != nullptr;
             }
             if (pts < CS_MIN_POINTS) return false;
-            if (hs) launch_prolong_jac_stream_hs<true>(H, ds, bpp, sx, sc, sb, sout, st);
-            else launch_prolong_jac_stream_hs<false>(H, ds, bpp, sx, sc, sb, sout, st);
+            if (fg) {
+                if (hs) launch_prolong_jac_stream_hs<true, true>(H, ds, bpp + C, sx, sc, sb, sout, st);
+                else launch_prolong_jac_stream_hs<false, true>(H, ds, bpp + C, sx, sc, sb, sout, st);
+            } else {
+                if (hs) launch_prolong_jac_stream_hs<true, false>(H, ds, bpp, sx, sc, sb, sout, st);
+                else launch_prolong_jac_stream_hs<false, false>(H, ds, bpp, sx, sc, sb, sout, st);
+            }
             return true;
         }
         return false;
     }
+    // set by fg_iter around its cycle: the cycle's last pass may form the
+    // FGMRES matvec (fg_fused reports whether it did)
+    bool fg_want = false, fg_fused = false;
     template <int MODE>
     void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
                          cudaStream_t st) {
@@ -836,7 +847,9 @@ struct Engine : EngineBase {
             launch_restrict<MODE_HELM>(H, ds1, KK_RESTRICT_HELM, 2 * C + R + C / 4, SU, SG, SG, 0, st);
         }
         wave(H, 2, I, st);
-        if (!launch_prolong_jac_stream(H, ds1, 3 * C + C / 4 + R, SU, SU, SG, SD, st))
+        const bool streamed = launch_prolong_jac_stream(H, ds1, 3 * C + C / 4 + R, SU, SU, SG, SD, fg_want, st);
+        fg_fused = streamed && fg_want;
+        if (!streamed)
             launch_prolong<PMODE_JAC>(H, ds1, KK_PROLONG_JAC, 3 * C + C / 4 + R, SU, SU, SG, SD, SD, 0, st);
     }
 
@@ -896,11 +909,16 @@ struct Engine : EngineBase {
         go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
             kl(k_fg_prep<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
         }, t.pts);
+        fg_want = true;
         cycle(H, true, st);
+        fg_want = false;
         const int cyc = H.launches_cycle;
-        go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
-            kl(k_fg_matvec<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
-        }, t.pts);
+        const bool fused = fg_fused;
+        fg_fused = false;
+        if (!fused)
+            go(H, st, KK_FG_MATVEC, (3 * C + R) * t.pts, [&] {
+                kl(k_fg_matvec<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
+            }, t.pts);
         {
             std::vector<int> od;
             for (auto& I : H.inst) od.push_back(I.outer_desc);
@@ -940,7 +958,7 @@ struct Engine : EngineBase {
             }
         }
         H.launches_cycle = cyc;
-        H.launches_step = cyc + (H.p.fgmres_passes == 2 ? 4 : 5);
+        H.launches_step = cyc + (H.p.fgmres_passes == 2 ? 4 : 5) - (fused ? 1 : 0);
         H.fg_j = j + 1;
     }
 

@@ -688,6 +688,14 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         }
         I.outer_desc = b;
         H.houter.push_back(d);
+        if (p.outer == MG_OUTER_FGMRES) {
+            // the level-1 cycle descriptor reaches this instance's Krylov vectors
+            // too: the cycle's last pass can write Z_j and A Z_j directly
+            LevelDesc& c1 = H.hdesc[l1.desc];
+            c1.kv = I.kv;
+            c1.fs = d.fs;
+            c1.krestart = p.restart;
+        }
     }
     // tensor maps of the tile kernels and the device error word
     {

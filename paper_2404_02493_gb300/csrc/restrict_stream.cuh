@@ -15,6 +15,7 @@
 // k_restrict<MODE_JAC0>.
 #pragma once
 #include "cheb_stream.cuh"
+#include "fgmres.cuh"
 
 namespace wadr {
 
@@ -137,6 +138,11 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
 // r) or halfway between rows r / 2 - 1 and r / 2 (even r); coarse row r / 2 is
 // issued with fine row r into a small per-warp ring.  March: u at input row
 // j, the Jacobi update at row j - 1.  u is zero outside the grid.
+// FG: inside an FGMRES iteration the result is the preconditioned vector
+// z = Z_j itself; it goes to Z_j and W = V_{j+1} = A z is formed one row
+// later in the same pass (the k_fg_matvec operation), with j read from the
+// FGMRES scalars on the device.  The extra stencil level costs a column on
+// each side: strips of 56 owned columns (lanes 2 .. 29), X0 = 56 k - 4.
 constexpr int PS_AH = 6;   // fine rows issued ahead (the oldest read is j - 1)
 template <typename T, bool HS> __host__ __device__ constexpr int ps_ring_bytes() {
     return (int)((2 * sizeof(cplx<T>) + (HS ? 2 : 1) * sizeof(T)) * SW_DEP * SW_COLS +
@@ -144,10 +150,11 @@ template <typename T, bool HS> __host__ __device__ constexpr int ps_ring_bytes()
 }
 template <typename T, bool HS> __host__ __device__ constexpr int ps_smem() { return RS_WPB * ps_ring_bytes<T, HS>(); }
 
-template <typename T, int RH, bool HS>
+template <typename T, int RH, bool HS, bool FG>
 __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid_constant__ KDesc A,
                                                                     const Seg* __restrict__ Sg, int nseg, int sx,
                                                                     int sc, int sb, int sout) {
+    constexpr int SO = FG ? SW_OUT : RS_SO, HW = FG ? 4 : 2, OWN0 = FG ? 2 : 1;
     extern __shared__ __align__(16) unsigned char ps_smem_[];
     const int lane = threadIdx.x, warp = threadIdx.y, tid = lane + 32 * warp;
     unsigned char* const base = ps_smem_ + warp * ps_ring_bytes<T, HS>();
@@ -162,21 +169,23 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
     coarse_desc(A, nseg, d, dc, tid);
     __syncthreads();
     const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
-    const int nstrips = (n + RS_SO - 1) / RS_SO, nunits = nstrips * ((n + RH - 1) / RH);
+    const int nstrips = (n + SO - 1) / SO, nunits = nstrips * ((n + RH - 1) / RH);
     const cplx<T>* const xv = slot<T>(d, sx);
     const cplx<T>* const gv = slot<T>(d, sb);
     const cplx<T>* const ev = slot<T>(dc, sc);
-    cplx<T>* const os = slot<T>(d, sout);
+    const int jk = FG ? (int)d.fs[FS::J] : 0;
+    cplx<T>* const os = FG ? zvec<T>(d, jk) : slot<T>(d, sout);
+    cplx<T>* const wv = FG ? kvec<T>(d, jk + 1) : nullptr;
     const T* const kf = reinterpret_cast<const T*>(d.kf);
     const T* const sgf = reinterpret_cast<const T*>(d.sig);
     const T ih2 = LC<T>::ih2(d);
     const T wjh2 = scalp<T>(d)[S::OMEGA_J] * LC<T>::h(d) * LC<T>::h(d);
-    const bool own = lane >= 1 && lane <= 30;
+    const bool own = lane >= OWN0 && lane <= 31 - OWN0;
     for (int u = c.lb * RS_WPB + warp; u < nunits; u += c.nb * RS_WPB) {
         const int sk = u % nstrips, band = u / nstrips;
-        const int X0 = RS_SO * sk - 2;
+        const int X0 = SO * sk - HW;
         const int y0 = RH * band, y1 = min(y0 + RH, n);
-        const int j0 = y0 - 1, j1 = y1;
+        const int j0 = y0 - (FG ? 2 : 1), j1 = y1 + (FG ? 1 : 0);
         const int col = X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const int ci = X0 / 2 + lane;   // the lane's coarse column
@@ -206,6 +215,8 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
             cp_async_commit();
         }
         P2<T> ua2 = p2zero<T>(), ua1 = p2zero<T>();   // u at j-2, j-1
+        P2<T> ob3 = p2zero<T>(), ob2 = p2zero<T>();   // FG: z at j-3, j-2
+        P2<T> dgp = p2zero<T>();                      // FG: diagonal at j-2
         for (int j = j0; j <= j1; ++j) {
             if (j + PS_AH <= j1) issue(j + PS_AH);
             cp_async_commit();
@@ -238,17 +249,37 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
             const P2<T> au = helm_row<T, false>(dg, ua1, ua2, u0, ih2);
             rr.v0 = csub<T>(rr.v0, au.v0);
             rr.v1 = csub<T>(rr.v1, au.v1);
-            if (own && r1 >= y0 && r1 < y1) {
-                const long long p = (long long)r1 * pitch + col;
-                if (cin0) {
+            const bool wr1 = own && r1 >= y0 && r1 < y1;
+            if (FG || wr1) {
+                P2<T> o1;
+                {
                     const T a = wjh2 / (dg.v0.x * dg.v0.x + dg.v0.y * dg.v0.y);
-                    os[p] = cadd<T>(ua1.v0, mk<T>((rr.v0.x * dg.v0.x + rr.v0.y * dg.v0.y) * a,
+                    o1.v0 = cadd<T>(ua1.v0, mk<T>((rr.v0.x * dg.v0.x + rr.v0.y * dg.v0.y) * a,
                                                   (rr.v0.y * dg.v0.x - rr.v0.x * dg.v0.y) * a));
                 }
-                if (cin1) {
+                {
                     const T a = wjh2 / (dg.v1.x * dg.v1.x + dg.v1.y * dg.v1.y);
-                    os[p + 1] = cadd<T>(ua1.v1, mk<T>((rr.v1.x * dg.v1.x + rr.v1.y * dg.v1.y) * a,
-                                                      (rr.v1.y * dg.v1.x - rr.v1.x * dg.v1.y) * a));
+                    o1.v1 = cadd<T>(ua1.v1, mk<T>((rr.v1.x * dg.v1.x + rr.v1.y * dg.v1.y) * a,
+                                                  (rr.v1.y * dg.v1.x - rr.v1.x * dg.v1.y) * a));
+                }
+                if (wr1) {
+                    const long long p = (long long)r1 * pitch + col;
+                    if (cin0) os[p] = o1.v0;
+                    if (cin1) os[p + 1] = o1.v1;
+                }
+                if constexpr (FG) {
+                    // W = A z at row j - 2 (z zero outside the grid)
+                    const bool ro1 = (unsigned)r1 < (unsigned)n;
+                    o1 = p2sel<T>(o1, ro1 && cin0, ro1 && cin1);
+                    const int r2 = j - 2;
+                    const P2<T> w = helm_row<T, false>(dgp, ob2, ob3, o1, ih2);
+                    if (own && r2 >= y0 && r2 < y1) {
+                        const long long p = (long long)r2 * pitch + col;
+                        if (cin0) wv[p] = w.v0;
+                        if (cin1) wv[p + 1] = w.v1;
+                    }
+                    ob3 = ob2; ob2 = o1;
+                    dgp = dg;
                 }
             }
             ua2 = ua1; ua1 = u0;

@@ -397,6 +397,38 @@ def test_batched_fgmres_steps_match_single_solves(prec, tol):
         assert rel(helmholtz_apply(H.lev(1), got.reshape(I.n, I.n)), I.g) < 0.5
 
 
+def test_fused_fgmres_matvec_matches_separate():
+    """25 complex-FP32 FGMRES iterations of a batch (n = 1023 and 255: the
+    level-1 launches cover more than 2^20 points, so the cycle's last pass
+    streams and forms Z_j and W = A Z_j itself) against each instance alone
+    (1023^2 < 2^20: tile prolongation, then the separate FGMRES matvec)."""
+    insts = [inst_medium(1023, 250.0, seed=81), inst_medium(255, 60.0, seed=82)]
+    K = 25
+
+    def run(group):
+        h = lib_handle(group, "mixed", n_cmax=15, M=2, tol=0.0, maxit=1 << 30)
+        u = np.zeros(sum(I.n * I.n for I in group), dtype=np.complex128)
+        g = np.concatenate([I.g.ravel() for I in group])
+        try:
+            B.mg_solve_begin(h, u, g)
+            B.mg_solve_steps(h, K)
+            B.mg_solve_end(h, u)
+        finally:
+            B.mg_destroy(h)
+        return u
+
+    ub = run(insts)
+    off = 0
+    for I in insts:
+        us = run([I])
+        got = ub[off:off + I.n * I.n]
+        off += I.n * I.n
+        assert np.all(np.isfinite(got))
+        assert rel(got, us) < 1e-4, (I.n, rel(got, us))
+        H = oracle_hier(I, n_cmax=15)
+        assert rel(helmholtz_apply(H.lev(1), got.reshape(I.n, I.n)), I.g) < 0.5
+
+
 def test_degenerate_inputs():
     """Zero right-hand side and zero iterate stay zero; GMRES with b = L x
     returns x (r0 = 0)."""
