@@ -232,7 +232,7 @@ def recorded_traffic(kernel, shape=None):
     return None if v is None else float(v)
 
 
-def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0):
+def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0, n_cmax=15):
     """The batched workload: 64 instances of uneven size (255, 511, 1023 in
     turn, k0 = 0.4 n pi / 5, log-normal media, random sources) in one handle;
     complex-FP32 cycles preconditioning FGMRES(20) with an FP64 residual and
@@ -252,7 +252,7 @@ def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0):
     insts = [all_insts[i] for i in mine]
     t_in = time.time() - t0
     spec = [(I.n, I.omega, torch.from_numpy(I.k).to(dev), torch.from_numpy(I.phi).to(dev), "abc1") for I in insts]
-    p = B.default_params(precision="mixed", n_cmax=15, outer="fgmres", tol=0.0, maxit=1 << 30)
+    p = B.default_params(precision="mixed", n_cmax=n_cmax, outer="fgmres", tol=0.0, maxit=1 << 30)
     t0 = time.time()
     h = B.mg_setup(spec, p, stream=st)
     torch.cuda.synchronize()
@@ -274,6 +274,19 @@ def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0):
     step_bytes = sum(r[3] for r in recs) / 2
     peak, _ = measured_peak()
     tiles = {f"n={insts[b].n}": B.mg_tile_shapes(h, b, 2) for b in range(min(3, len(insts)))}
+    # per-kernel view of the batched step (non-graph emission of 2 steps)
+    tot_ms = sum(r[2] for r in recs)
+    bkern = {}
+    for name, pts, kms, kby, kla in recs:
+        e = bkern.setdefault(name, {"ms_per_step": 0.0, "bytes": 0.0, "launches_per_step": 0})
+        e["ms_per_step"] += kms / 2
+        e["bytes"] += kby
+        e["launches_per_step"] += kla // 2
+    for e in bkern.values():
+        e["share"] = e["ms_per_step"] * 2 / tot_ms if tot_ms > 0 else None
+        e["GBps"] = e["bytes"] / 2 / (e["ms_per_step"] * 1e-3) / 1e9 if e["ms_per_step"] > 0 else None
+        del e["bytes"]
+    bkern = dict(sorted(bkern.items(), key=lambda kv: -kv[1]["ms_per_step"])[:10])
     B.mg_destroy(h)
     if ws > 1:
         t = torch.tensor([ms, step_bytes], device=dev, dtype=torch.float64)
@@ -288,12 +301,12 @@ def batched_leg(B, torch, dev, st, steps, warmup, ws=1, rank=0):
                         "media c in [1, 3] (seeds 100..163), random sources in [0.2, 0.8]^2; complex-FP32 Wave-ADR "
                         "cycles (M=8) preconditioning FGMRES(20) with FP64 residual and update, per instance; one "
                         "CUDA-graph launch per step runs one FGMRES iteration (one cycle) of every instance",
-            "instances": 64, "fine_points": pts, "steps": steps, "warmup": warmup,
+            "instances": 64, "fine_points": pts, "n_cmax": n_cmax, "steps": steps, "warmup": warmup,
             "value": 64 * steps / (ms * 1e-3), "unit": "instance-cycles/s", "ms_per_step": ms / steps,
             "algorithmic_GB_per_step": step_bytes / 1e9,
             "achieved_GBps": step_bytes / (ms * 1e-3 / steps) / 1e9,
             "frac_of_peak": step_bytes / (ms * 1e-3 / steps) / 1e9 / peak,
-            "gpu_launches_per_step": launches, "level2_tiles": tiles, "rel_residual_after": rel,
+            "gpu_launches_per_step": launches, "level2_tiles": tiles, "kernels": bkern, "rel_residual_after": rel,
             "setup_seconds": t_setup, "input_generation_seconds": t_in, "ranks": ws,
             "instances_per_rank": [len(my_shard([I.n * I.n for I in all_insts], r, ws)) for r in range(ws)],
             "scaling": "strong: the 64 instances are split over the ranks" if ws > 1 else None}
@@ -594,7 +607,8 @@ def run_ours(args):
     h = None
     paper = None if args.no_paper_m8 else paper_m8_leg(B, torch, dev, st, n, omega, k, phi, g, 50, args.warmup)
 
-    batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3, ws, rank)
+    batched = None if args.no_batched else batched_leg(B, torch, dev, st, args.batched_steps, 3, ws, rank,
+                                                       args.batched_n_cmax)
     precision = None if args.no_precision else precision_leg(B, torch, dev, st)
     precision2 = None if args.no_precision else precision_leg(B, torch, dev, st, 511, 200.0, "log-normal")
     shifted = None if args.no_shifted else shifted_leg(B, torch, dev, st)
@@ -645,6 +659,8 @@ def main():
     ap.add_argument("--no-paper-m8", action="store_true")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "ir"])
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-n-cmax", type=int, default=15,
+                    help="coarsest-level bound of the batched handle (coarsen while n > n_cmax)")
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
