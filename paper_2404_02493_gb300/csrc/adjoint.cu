@@ -140,46 +140,86 @@ struct DotPtrs {
     const double2* z[ADOTS];
 };
 
-// up to ADOTS dot products sum conj(x_k) y_k into out[k]: block partials,
-// then the last block to finish (counter) sums the partials in block order
-// and clears the counter for the next launch
-__global__ void ka_dots(int n, int pitch, int npair, DotPtrs P, double2* part, unsigned* count, double2* out) {
-    __shared__ double2 sh[8 * ADOTS];
+// up to ADOTS dot products sum conj(x_k) y_k into out[k].  FP64 issues at a
+// small fraction of the FP32 rate on this GPU, so the reductions are laid out
+// to spend few FP64 instructions: each thread accumulates many elements (the
+// host launches a few blocks per SM), a warp then transposes its 2 ADOTS
+// partial sums through shared memory and lane l adds up column l (31 adds
+// instead of a 5-level shuffle tree per value), the warps' sums are added in
+// warp order, and the last block to finish (counter) adds the blocks'
+// partials in 8 interleaved groups, then the groups in order.  The order is
+// fixed, so the result is reproducible.
+constexpr int ADV = 2 * ADOTS;   // doubles per thread
+__global__ void __launch_bounds__(ANT) ka_dots(int n, int pitch, int npair, DotPtrs P, double* part, unsigned* count,
+                                               double2* out) {
+    __shared__ double tr[ANT / 32][32][ADV + 1];
+    __shared__ double ws[ANT / 32][ADV];
     __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double2 acc[ADOTS];
 #pragma unroll
     for (int k = 0; k < ADOTS; ++k) acc[k] = make_double2(0, 0);
     const unsigned N = (unsigned)n * (unsigned)n, un = (unsigned)n;
-    for (unsigned q = blockIdx.x * ANT + threadIdx.x; q < N; q += gridDim.x * ANT) {
+    for (unsigned q = blockIdx.x * ANT + tid; q < N; q += gridDim.x * ANT) {
         const unsigned j = q / un, i = q - j * un;
         const long long p = (long long)j * pitch + i;
 #pragma unroll
         for (int k = 0; k < ADOTS; ++k)
             if (k < npair) {
+                // a norm pair (x = y) accumulates |x|^2 only, any other pair
+                // Re and Im of conj(x) y, as FMA chains
                 const double2 xv = P.z[k] ? dsub(P.x[k][p], P.z[k][p]) : P.x[k][p];
-                acc[k] = dadd(acc[k], dmulc(xv, P.y[k][p]));
+                if (P.x[k] == P.y[k] && !P.z[k]) {
+                    acc[k].x = fma(xv.x, xv.x, acc[k].x);
+                    acc[k].x = fma(xv.y, xv.y, acc[k].x);
+                } else {
+                    const double2 yv = P.y[k][p];
+                    acc[k].x = fma(xv.x, yv.x, acc[k].x);
+                    acc[k].x = fma(xv.y, yv.y, acc[k].x);
+                    acc[k].y = fma(xv.x, yv.y, acc[k].y);
+                    acc[k].y = fma(-xv.y, yv.x, acc[k].y);
+                }
             }
     }
-    block_sum<double2, ADOTS>(acc, sh);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < ADOTS; ++k) part[blockIdx.x * ADOTS + k] = acc[k];
-        __threadfence();
-        last = atomicAdd(count, 1u) == gridDim.x - 1;
+#pragma unroll
+    for (int k = 0; k < ADOTS; ++k) {
+        tr[wid][lane][2 * k] = acc[k].x;
+        tr[wid][lane][2 * k + 1] = acc[k].y;
     }
+    __syncwarp();
+    if (lane < 2 * npair) {
+        double sm = tr[wid][0][lane];
+        for (int r = 1; r < 32; ++r) sm += tr[wid][r][lane];
+        ws[wid][lane] = sm;
+    }
+    __syncthreads();
+    if (tid < 2 * npair) {
+        double sm = ws[0][tid];
+#pragma unroll
+        for (int w = 1; w < ANT / 32; ++w) sm += ws[w][tid];
+        part[(long long)blockIdx.x * ADV + tid] = sm;
+        __threadfence();   // every writer publishes its partial before the count
+    }
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-#pragma unroll
-    for (int k = 0; k < ADOTS; ++k) acc[k] = make_double2(0, 0);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += ANT)
-#pragma unroll
-        for (int k = 0; k < ADOTS; ++k)
-            if (k < npair) acc[k] = dadd(acc[k], __ldcg(&part[b * ADOTS + k]));
-    block_sum<double2, ADOTS>(acc, sh);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < npair; ++k) out[k] = acc[k];
-        *count = 0;
+    // value v = tid % ADV of group g = tid / ADV sums blocks g, g + 8, ...
+    const int v = tid % ADV, g = tid / ADV;
+    if (g < 8 && v < 2 * npair) {
+        double sm = 0.0;
+        for (int b = g; b < (int)gridDim.x; b += 8) sm += __ldcg(&part[(long long)b * ADV + v]);
+        tr[0][g][v] = sm;
     }
+    __syncthreads();
+    if (tid < 2 * npair) {
+        double sm = tr[0][0][tid];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) sm += tr[0][q][tid];
+        reinterpret_cast<double*>(out)[tid] = sm;
+    }
+    if (tid == 0) *count = 0;
 }
 
 // complex 3 x 3 solve, Gaussian elimination with partial pivoting (largest
@@ -190,22 +230,39 @@ __device__ inline void solve3_dev(const double2 (&G)[3][3], const double2* z, do
         for (int j = 0; j < 3; ++j) M[i][j] = G[i][j];
         M[i][3] = z[i];
     }
+    // every index is a constant after unrolling (the pivot row is swapped in
+    // by selects), so M stays in registers
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
         int pv = k;
-        for (int i = k + 1; i < 3; ++i)
-            if (dabs2(M[i][k]) > dabs2(M[pv][k])) pv = i;
-        for (int j = 0; j < 4; ++j) {
-            const double2 t = M[k][j];
-            M[k][j] = M[pv][j];
-            M[pv][j] = t;
+        double best = dabs2(M[k][k]);
+#pragma unroll
+        for (int i = k + 1; i < 3; ++i) {
+            const double a = dabs2(M[i][k]);
+            if (a > best) {
+                best = a;
+                pv = i;
+            }
         }
+#pragma unroll
+        for (int i = k + 1; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double2 t = M[k][j], u = M[i][j];
+                M[k][j] = (i == pv) ? u : t;
+                M[i][j] = (i == pv) ? t : u;
+            }
+#pragma unroll
         for (int i = k + 1; i < 3; ++i) {
             const double2 f = ddiv(M[i][k], M[k][k]);
+#pragma unroll
             for (int j = k; j < 4; ++j) M[i][j] = dsub(M[i][j], dmul(f, M[k][j]));
         }
     }
+#pragma unroll
     for (int i = 2; i >= 0; --i) {
         double2 sm = M[i][3];
+#pragma unroll
         for (int j = i + 1; j < 3; ++j) sm = dsub(sm, dmul(M[i][j], c[j]));
         c[i] = ddiv(sm, M[i][i]);
     }
@@ -356,20 +413,44 @@ __global__ void ka_apply_mod(LevelDesc d, int mode, const double2* x, const doub
 }
 
 // y (+)= M x or M^H x with a dense FP64 n^2 x n^2 matrix (coarsest level)
-__global__ void ka_gemv(int n, int pitch, const double2* M, const double2* x, double2* y, int herm, int acc) {
-    const int row = blockIdx.x * ANT + threadIdx.x;
+// y (+)= M x or M^H x with the dense coarsest-level inverse M (N = n^2 rows):
+// one warp per row (the rows spread over many SMs; FP64 is slow per SM), the
+// lanes take every 32nd column with FMA chains, then a shuffle tree
+constexpr int GEMV_ROWS = ANT / 32;   // rows per block
+__global__ void __launch_bounds__(ANT) ka_gemv(int n, int pitch, const double2* M, const double2* x, double2* y,
+                                               int herm, int acc) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * GEMV_ROWS + (threadIdx.x >> 5);
     const int N = n * n;
-    if (row >= N) return;
+    if (row >= N) return;   // whole warps leave together
     double2 s = make_double2(0, 0);
-    for (int c = 0; c < N; ++c) {
-        const int i = c % n, j = c / n;
+    for (int c = lane; c < N; c += 32) {
+        const int j = c / n, i = c - j * n;
         const double2 xv = x[(long long)j * pitch + i];
-        if (herm) s = dadd(s, dmulc(M[(long long)c * N + row], xv));
-        else s = dadd(s, dmul(M[(long long)row * N + c], xv));
+        if (herm) {
+            const double2 m = M[(long long)c * N + row];   // conj(m) x
+            s.x = fma(m.x, xv.x, s.x);
+            s.x = fma(m.y, xv.y, s.x);
+            s.y = fma(m.x, xv.y, s.y);
+            s.y = fma(-m.y, xv.x, s.y);
+        } else {
+            const double2 m = M[(long long)row * N + c];   // m x
+            s.x = fma(m.x, xv.x, s.x);
+            s.x = fma(-m.y, xv.y, s.x);
+            s.y = fma(m.x, xv.y, s.y);
+            s.y = fma(m.y, xv.x, s.y);
+        }
     }
-    const int i = row % n, j = row / n;
-    const long long p = (long long)j * pitch + i;
-    y[p] = acc ? dadd(y[p], s) : s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+    }
+    if (lane == 0) {
+        const int j = row / n, i = row - j * n;
+        const long long p = (long long)j * pitch + i;
+        y[p] = acc ? dadd(y[p], s) : s;
+    }
 }
 
 // ------------------------------------------------------------ host side
@@ -416,6 +497,16 @@ struct Adjoint {
     }
 
     int blocks(int n) const { return (int)(((long long)n * n + ANT - 1) / ANT); }
+    static int num_sms() {
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (nsm < 1) nsm = 1;
+        }
+        return nsm;
+    }
 
     int init() {
         lv.resize(I.L + 1);
@@ -537,9 +628,9 @@ struct Adjoint {
             P.y[k] = k < np ? pr[k].second : pr[0].second;
             P.z[k] = k < (int)sub.size() ? sub[k] : nullptr;
         }
-        const int nb = std::min(blocks(L.n), 1024);
+        const int nb = std::min(blocks(L.n), 2 * num_sms());
         double2* out = scalars(np);
-        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, P, part, dcount, out);
+        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, P, reinterpret_cast<double*>(part), dcount, out);
         return out;
     }
     // out (+)= sum_t cp_t x_t, coefficients in device memory
@@ -691,7 +782,7 @@ struct Adjoint {
         T->b = b;
         if (l == I.L) {
             AdjLevel& L = lv[l];
-            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, b, x_out, 0, 0);
+            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, b, x_out, 0, 0);
             T->coarse_x = x_out;
             return T;
         }
@@ -719,7 +810,7 @@ struct Adjoint {
             AdjLevel& L = lv[l];
             // x = X b: bbar += X^H xbar ; L_bar = -bbar_new x^H
             double2* bb = get(l);
-            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
+            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
             lin(l, bbar, true, bb, 1.0);
             adr_grad(l, bb, T->coarse_x, -1.0);
             put(l, bb);
@@ -828,7 +919,7 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         if (l == I.L) {
             // from zero: u = A^{-1} g
-            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, g, u_out, 0, 0);
+            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, g, u_out, 0, 0);
             return T;
         }
         const double wj = I.omega_j;
@@ -910,7 +1001,7 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         if (l == I.L) {
             double2* gb = get(l);
-            ka_gemv<<<(L.n * L.n + ANT - 1) / ANT, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, uob, gb, 1, 0);
+            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, uob, gb, 1, 0);
             lin(l, gbar, true, gb, 1.0);
             put(l, gb);
             return;
