@@ -330,6 +330,29 @@ __global__ void ka_lincomb_p(int n, int pitch, double2* out, int acc, const doub
     out[p] = v;
 }
 
+// The vector part of the GMRES(3) adjoint in one pass, coefficients o from
+// ka_gm_back: kb_q = o[q] xbar; r0b = sum_i o[3 + i] w_i;
+// wb_q = sum_i o[6 + 4q + i] w_i + o[9 + 4q] r0 (each sum in that order, as
+// the linear combinations it replaces)
+__global__ void ka_gm_back_vec(int n, int pitch, const double2* xbar, const double2* w0, const double2* w1,
+                               const double2* w2, const double2* r0, const double2* o, double2* kb0, double2* kb1,
+                               double2* kb2, double2* r0b, double2* wb0, double2* wb1, double2* wb2) {
+    int i, j;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, i, j)) return;
+    const long long p = (long long)j * pitch + i;
+    const double2 xb = xbar[p], a0 = w0[p], a1 = w1[p], a2 = w2[p], rv = r0[p];
+    const double2 z = make_double2(0, 0);
+    kb0[p] = dadd(z, dmul(o[0], xb));
+    kb1[p] = dadd(z, dmul(o[1], xb));
+    kb2[p] = dadd(z, dmul(o[2], xb));
+    r0b[p] = dadd(dadd(dadd(z, dmul(o[3], a0)), dmul(o[4], a1)), dmul(o[5], a2));
+    double2* const wb[3] = {wb0, wb1, wb2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        wb[q][p] = dadd(dadd(dadd(dadd(z, dmul(o[6 + 4 * q], a0)), dmul(o[7 + 4 * q], a1)), dmul(o[8 + 4 * q], a2)),
+                        dmul(o[9 + 4 * q], rv));
+}
+
 // dst += scale Re(src)  (weight gradients accumulated on the device)
 __global__ void ka_accum_re(double* dst, const double2* src, double scale) { dst[0] += scale * src[0].x; }
 __global__ void ka_accum_re2(double* dst, const double2* src, double s0, double s1) {
@@ -348,17 +371,18 @@ __device__ __forceinline__ void adr_grad_pt(const LevelDesc& d, int i, int j, lo
     const double2 aW = i > 0 ? a[p - 1] : z, aE = i < n - 1 ? a[p + 1] : z;
     const double2 aS = j > 0 ? a[p - d.pitch] : z, aN = j < n - 1 ? a[p + d.pitch] : z;
     const quad<double> q = reinterpret_cast<const quad<double>*>(d.adr)[p];
-    const double sx = (q.x > 0) - (q.x < 0), sy = (q.y > 0) - (q.y < 0);
     const double wh = d.wh;
-    // d(La)/d phix = i wh [(1+sx) aW - (1-sx) aE]
-    double2 tx = dsub(dsc(aW, 1 + sx), dsc(aE, 1 - sx));
-    tx = make_double2(-wh * tx.y, wh * tx.x);
-    double2 ty = dsub(dsc(aS, 1 + sy), dsc(aN, 1 - sy));
-    ty = make_double2(-wh * ty.y, wh * ty.x);
+    // d(La)/d phix = i wh [(1+sx) aW - (1-sx) aE], sx = sign(phix): the factors
+    // are 0, 1 or 2, so the bracket is 2 aW, -2 aE or aW - aE, formed as the sum
+    // of two selected operands (exact, one complex addition)
+    const double2 nE = make_double2(-aE.x, -aE.y), nN = make_double2(-aN.x, -aN.y);
+    const double2 tx = dadd(q.x > 0 ? aW : (q.x < 0 ? nE : aW), q.x > 0 ? aW : nE);
+    const double2 ty = dadd(q.y > 0 ? aS : (q.y < 0 ? nN : aS), q.y > 0 ? aS : nN);
     const double2 ac = a[p];
     double* o = qbar + 4 * ((long long)j * n + i);
-    o[0] += yb.x * tx.x + yb.y * tx.y;        // Re(conj(yb) tx)
-    o[1] += yb.x * ty.x + yb.y * ty.y;
+    // Re(conj(yb) i wh t) = wh (yb.y t.x - yb.x t.y)
+    o[0] = fma(wh, fma(yb.y, tx.x, -yb.x * tx.y), o[0]);
+    o[1] = fma(wh, fma(yb.y, ty.x, -yb.x * ty.y), o[1]);
     const double2 db = dmulc(ac, yb);          // conj(a) ybar
     o[2] += db.x;
     o[3] += db.y;
@@ -746,14 +770,12 @@ struct Adjoint {
             kb[q] = get(l);
             wb[q] = get(l);
         }
-        // kbar_j = conj(c_j) xbar
-        for (int q = 0; q < 3; ++q) lin_dev(l, kb[q], false, xbar, co + q);
-        // z_i = w_i^H r0: r0bar += sum_i w_i zbar_i ; wbar_i += r0 conj(zbar_i)
-        lin_dev(l, r0b, false, T.w[0], co + 3, T.w[1], co + 4, T.w[2], co + 5);
-        // G_ij = w_i^H w_j: wbar_j += sum_i w_i Gbar_ij ; wbar_i += sum_j w_j conj(Gbar_ij)
-        for (int q = 0; q < 3; ++q)
-            lin_dev(l, wb[q], false, T.w[0], co + 6 + 4 * q, T.w[1], co + 7 + 4 * q, T.w[2], co + 8 + 4 * q, T.r0,
-                    co + 9 + 4 * q);
+        // in one pass over xbar, w_0..w_2, r0:
+        //   kbar_j = conj(c_j) xbar;
+        //   z_i = w_i^H r0: r0bar = sum_i w_i zbar_i, wbar_i += r0 conj(zbar_i);
+        //   G_ij = w_i^H w_j: wbar_j += sum_i w_i Gbar_ij, wbar_i += sum_j w_j conj(Gbar_ij)
+        ka_gm_back_vec<<<blocks(L.n), ANT, 0, st>>>(L.n, L.pitch, xbar, T.w[0], T.w[1], T.w[2], T.r0, co, kb[0],
+                                                     kb[1], kb[2], r0b, wb[0], wb[1], wb[2]);
         // w_q = L k_q
         for (int q = 0; q < 3; ++q) lh_grad(l, wb[q], T.k[q], 1.0, kb[q]);
         // k_2 = s L k_1, k_1 = s L k_0
