@@ -22,6 +22,8 @@
 // value is read by the lane that later overwrites it, so sdout may equal
 // sdin.  Flags: 1 = x_m is zero, 2 = do not write the last step's d.
 #pragma once
+#include <type_traits>
+
 #include "stream.cuh"
 
 namespace wadr {
@@ -72,6 +74,22 @@ __device__ __forceinline__ void ring_issue2(E* ring, const E* __restrict__ g, in
 template <typename T>
 __device__ __forceinline__ P2<T> diag_row(const LevelDesc& d, int j, int col, T k0, T k1, T sg0, T sg1) {
     return P2<T>{helm_diag_h2<T>(d, col, j, k0, sg0), helm_diag_h2<T>(d, col + 1, j, k1, sg1)};
+}
+
+// the same for a row and columns strictly inside the grid (the absorbing
+// boundary terms are zero there; equal to helm_diag_h2 bit for bit)
+template <typename T>
+__device__ __forceinline__ cplx<T> helm_diag_in(const LevelDesc& d, T k, T sig) {
+    const T h = LC<T>::h(d), kh = k * h;
+    const T re = T(4) - kh * kh;
+    T im = T(0);
+    if (d.bc == BC_SPONGE) im -= h * h * sig;
+    if (d.has_shift) im -= LC<T>::shift(d) * kh * kh;
+    return mk<T>(re, im);
+}
+template <typename T>
+__device__ __forceinline__ P2<T> diag_in_row(const LevelDesc& d, T k0, T k1, T sg0, T sg1) {
+    return P2<T>{helm_diag_in<T>(d, k0, sg0), helm_diag_in<T>(d, k1, sg1)};
 }
 
 // (A v) at one row of the lane's pair (A^* v with CONJ), from the centre
@@ -137,6 +155,7 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
         const int j0 = y0 - 2 * NS, j1 = y1 - 1 + 2 * NS;
         const int col = X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
+        const bool colint = X0 >= 1 && X0 + SW_COLS - 1 <= n - 2;   // all 64 columns in [1, n - 2]
         auto issue = [&](int r) {
             if (!xzero) ring_issue2<cplx<T>>(Xr, xin, n, pitch, X0, r, lane);
             ring_issue2<cplx<T>>(Gr, gv, n, pitch, X0, r, lane);
@@ -160,83 +179,90 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
             if (j + AH <= j1) issue(j + AH);
             cp_async_commit();
             cp_async_wait<AH>();
-            P2<T> x0 = p2zero<T>();
-            if (!xzero) ring_read<cplx<T>>(Xr, j, lane, x0.v0, x0.v1);
-            // the diagonal of row j - 1, used by every level on that row
-            const int r1 = j - 1;
-            T k0, k1, s0 = T(0), s1 = T(0);
-            ring_read<T>(Kr, r1, lane, k0, k1);
-            if (HS) ring_read<T>(Sr, r1, lane, s0, s1);
-            const P2<T> dg1 = diag_row<T>(d, r1, col, k0, k1, s0, s1);
-            // level 1: t_m = g - A x_m at row j - 1
-            const bool ro1 = (unsigned)r1 < (unsigned)n;
-            P2<T> t1;
-            ring_read<cplx<T>>(Gr, r1, lane, t1.v0, t1.v1);
-            if (!xzero) {
-                const P2<T> ax = helm_row<T, false>(dg1, xa1, xa2, x0, ih2);
-                t1.v0 = csub<T>(t1.v0, ax.v0);
-                t1.v1 = csub<T>(t1.v1, ax.v1);
-            }
-            t1 = p2sel<T>(t1, ro1 && cin0, ro1 && cin1);
-            // level 2: d_m, x_{m+1} at row j - 2
-            const int r2 = j - 2;
-            const bool ro2 = (unsigned)r2 < (unsigned)n;
-            const P2<T> sv = helm_row<T, true>(dg2, ta2, ta3, t1, ih2);
-            P2<T> dm{cscale<T>(sv.v0, c2a), cscale<T>(sv.v1, c2a)};
-            if (rd) {
-                P2<T> dp;
-                ring_read<cplx<T>>(Dr, r2, lane, dp.v0, dp.v1);
-                dm.v0 = cadd<T>(dm.v0, cscale<T>(dp.v0, c1a));
-                dm.v1 = cadd<T>(dm.v1, cscale<T>(dp.v1, c1a));
-            }
-            const P2<T> xm1{cadd<T>(xa2.v0, dm.v0), cadd<T>(xa2.v1, dm.v1)};
-            if constexpr (NS == 1) {
-                if (own && r2 >= y0 && r2 < y1) {
-                    const long long p = (long long)r2 * pitch + col;
-                    if (cin0) {
-                        xout[p] = xm1.v0;
-                        if (wd) dout[p] = dm.v0;
-                    }
-                    if (cin1) {
-                        xout[p + 1] = xm1.v1;
-                        if (wd) dout[p + 1] = dm.v1;
-                    }
+            // rows and columns strictly inside the grid (warp-uniform): no zero
+            // selects, no boundary terms in the diagonal
+            auto row = [&](auto edge) {
+                constexpr bool E = decltype(edge)::value;
+                P2<T> x0 = p2zero<T>();
+                if (!xzero) ring_read<cplx<T>>(Xr, j, lane, x0.v0, x0.v1);
+                // the diagonal of row j - 1, used by every level on that row
+                const int r1 = j - 1;
+                T k0, k1, s0 = T(0), s1 = T(0);
+                ring_read<T>(Kr, r1, lane, k0, k1);
+                if (HS) ring_read<T>(Sr, r1, lane, s0, s1);
+                const P2<T> dg1 = E ? diag_row<T>(d, r1, col, k0, k1, s0, s1) : diag_in_row<T>(d, k0, k1, s0, s1);
+                // level 1: t_m = g - A x_m at row j - 1
+                const bool ro1 = (unsigned)r1 < (unsigned)n;
+                P2<T> t1;
+                ring_read<cplx<T>>(Gr, r1, lane, t1.v0, t1.v1);
+                if (!xzero) {
+                    const P2<T> ax = helm_row<T, false>(dg1, xa1, xa2, x0, ih2);
+                    t1.v0 = csub<T>(t1.v0, ax.v0);
+                    t1.v1 = csub<T>(t1.v1, ax.v1);
                 }
-            } else {
-                const P2<T> xn = p2sel<T>(xm1, ro2 && cin0, ro2 && cin1);
-                const P2<T> dn = p2sel<T>(dm, ro2 && cin0, ro2 && cin1);
-                // level 3: t_{m+1} = g - A x_{m+1} at row j - 3
-                const int r3 = j - 3;
-                const bool ro3 = (unsigned)r3 < (unsigned)n;
-                P2<T> t2;
-                ring_read<cplx<T>>(Gr, r3, lane, t2.v0, t2.v1);
-                const P2<T> ax = helm_row<T, false>(dg3, xb3, xb4, xn, ih2);
-                t2.v0 = csub<T>(t2.v0, ax.v0);
-                t2.v1 = csub<T>(t2.v1, ax.v1);
-                t2 = p2sel<T>(t2, ro3 && cin0, ro3 && cin1);
-                // level 4: d_{m+1}, x_{m+2} at row j - 4
-                const int r4 = j - 4;
-                const P2<T> s2 = helm_row<T, true>(dg4, tb4, tb5, t2, ih2);
-                if (own && r4 >= y0 && r4 < y1) {
-                    const long long p = (long long)r4 * pitch + col;
-                    const cplx<T> e0 = cadd<T>(cscale<T>(s2.v0, c2b), cscale<T>(db4.v0, c1b));
-                    const cplx<T> e1 = cadd<T>(cscale<T>(s2.v1, c2b), cscale<T>(db4.v1, c1b));
-                    if (cin0) {
-                        xout[p] = cadd<T>(xb4.v0, e0);
-                        if (wd) dout[p] = e0;
-                    }
-                    if (cin1) {
-                        xout[p + 1] = cadd<T>(xb4.v1, e1);
-                        if (wd) dout[p + 1] = e1;
-                    }
+                if constexpr (E) t1 = p2sel<T>(t1, ro1 && cin0, ro1 && cin1);
+                // level 2: d_m, x_{m+1} at row j - 2
+                const int r2 = j - 2;
+                const bool ro2 = (unsigned)r2 < (unsigned)n;
+                const P2<T> sv = helm_row<T, true>(dg2, ta2, ta3, t1, ih2);
+                P2<T> dm{cscale<T>(sv.v0, c2a), cscale<T>(sv.v1, c2a)};
+                if (rd) {
+                    P2<T> dp;
+                    ring_read<cplx<T>>(Dr, r2, lane, dp.v0, dp.v1);
+                    dm.v0 = cadd<T>(dm.v0, cscale<T>(dp.v0, c1a));
+                    dm.v1 = cadd<T>(dm.v1, cscale<T>(dp.v1, c1a));
                 }
-                tb5 = tb4; tb4 = t2;
-                xb4 = xb3; xb3 = xn;
-                db4 = db3; db3 = dn;
-            }
-            ta3 = ta2; ta2 = t1;
-            xa2 = xa1; xa1 = x0;
-            dg4 = dg3; dg3 = dg2; dg2 = dg1;
+                const P2<T> xm1{cadd<T>(xa2.v0, dm.v0), cadd<T>(xa2.v1, dm.v1)};
+                if constexpr (NS == 1) {
+                    if (own && r2 >= y0 && r2 < y1) {
+                        const long long p = (long long)r2 * pitch + col;
+                        if (cin0) {
+                            xout[p] = xm1.v0;
+                            if (wd) dout[p] = dm.v0;
+                        }
+                        if (cin1) {
+                            xout[p + 1] = xm1.v1;
+                            if (wd) dout[p + 1] = dm.v1;
+                        }
+                    }
+                } else {
+                    const P2<T> xn = E ? p2sel<T>(xm1, ro2 && cin0, ro2 && cin1) : xm1;
+                    const P2<T> dn = E ? p2sel<T>(dm, ro2 && cin0, ro2 && cin1) : dm;
+                    // level 3: t_{m+1} = g - A x_{m+1} at row j - 3
+                    const int r3 = j - 3;
+                    const bool ro3 = (unsigned)r3 < (unsigned)n;
+                    P2<T> t2;
+                    ring_read<cplx<T>>(Gr, r3, lane, t2.v0, t2.v1);
+                    const P2<T> ax = helm_row<T, false>(dg3, xb3, xb4, xn, ih2);
+                    t2.v0 = csub<T>(t2.v0, ax.v0);
+                    t2.v1 = csub<T>(t2.v1, ax.v1);
+                    if constexpr (E) t2 = p2sel<T>(t2, ro3 && cin0, ro3 && cin1);
+                    // level 4: d_{m+1}, x_{m+2} at row j - 4
+                    const int r4 = j - 4;
+                    const P2<T> s2 = helm_row<T, true>(dg4, tb4, tb5, t2, ih2);
+                    if (own && r4 >= y0 && r4 < y1) {
+                        const long long p = (long long)r4 * pitch + col;
+                        const cplx<T> e0 = cadd<T>(cscale<T>(s2.v0, c2b), cscale<T>(db4.v0, c1b));
+                        const cplx<T> e1 = cadd<T>(cscale<T>(s2.v1, c2b), cscale<T>(db4.v1, c1b));
+                        if (cin0) {
+                            xout[p] = cadd<T>(xb4.v0, e0);
+                            if (wd) dout[p] = e0;
+                        }
+                        if (cin1) {
+                            xout[p + 1] = cadd<T>(xb4.v1, e1);
+                            if (wd) dout[p + 1] = e1;
+                        }
+                    }
+                    tb5 = tb4; tb4 = t2;
+                    xb4 = xb3; xb3 = xn;
+                    db4 = db3; db3 = dn;
+                }
+                ta3 = ta2; ta2 = t1;
+                xa2 = xa1; xa1 = x0;
+                dg4 = dg3; dg3 = dg2; dg2 = dg1;
+            };
+            if (colint && j >= 3 && j <= n - 1) row(std::false_type{});
+            else row(std::true_type{});
         }
         cp_async_wait<0>();
         __syncwarp();
