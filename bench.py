@@ -54,7 +54,7 @@ def workload_config(n, omega, M=2, outer="fgmres", adr_bc="abc"):
             "n": n, "omega": omega, "M": M, "adr_bc": adr_bc,
             "outer": "FGMRES(20) in FP64 refinement" if outer == "fgmres" else "IR (FP64 residual and update)",
             "cycle_dtype": "complex64",
-            "l2": "inputs larger than L2: level-1 vectors are 134 MB each and a step streams ~20 GB"}
+            "l2": "inputs larger than L2: level-1 vectors are 134 MB each and a step streams ~6.3 GB (M = 2)"}
 
 
 def dist_env():
