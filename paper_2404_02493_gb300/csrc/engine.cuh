@@ -801,7 +801,8 @@ struct Engine : EngineBase {
             }
         }
         if (rest.empty()) return;
-        if (l >= 4 && H.wave_tail_nmax > 0 && H.p.cheb_iters >= 2) {
+        // (the tail ends with the dense LU, so it serves only the LU coarsest solve)
+        if (l >= 4 && H.wave_tail_nmax > 0 && H.p.cheb_iters >= 2 && H.p.coarse == MG_COARSE_LU) {
             bool all = true;
             for (int b : rest) all = all && in_wave_tail(H, b, l);
             if (all) {

@@ -429,6 +429,51 @@ def test_fused_fgmres_matvec_matches_separate():
         assert rel(helmholtz_apply(H.lev(1), got.reshape(I.n, I.n)), I.g) < 0.5
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+@pytest.mark.parametrize("n,ncm", [(127, 15), (200, 12)])
+def test_cycle_with_chebyshev_on_the_coarsest_level(prec, tol, n, ncm):
+    """Algorithm 1's coarsest-level smoother (Chebyshev, 10 steps from zero)
+    in place of the dense LU: one cycle from zero against the oracle's cycle
+    with the same choice (FP64 to 1e-12; complex FP32, where the 10 steps run
+    in one k_cheb_multi launch with a 20-node ring, to 1e-5)."""
+    I = inst_medium(n, 0.4 * n, seed=90 + n % 11)
+    h = lib_handle([I], prec, n_cmax=ncm, coarse="cheb")
+    try:
+        g = I.g / np.linalg.norm(I.g)
+        dt = np.complex128 if prec == "fp64" else np.complex64
+        gg = g.astype(dt)
+        u = np.zeros_like(gg)
+        B.mg_cycle(h, u, gg, 1)
+        H = oracle_hier(I, n_cmax=ncm, coarse="cheb")
+        ref = H.cycle(np.zeros_like(g), gg.astype(np.complex128))
+        assert np.all(np.isfinite(u))
+        assert rel(u.astype(np.complex128), ref) < tol, rel(u, ref)
+    finally:
+        B.mg_destroy(h)
+
+
+@pytest.mark.parametrize("q,extra", [(2, {}), (3, {"use_graph": 0}), (4, {"pdl": 1})])
+def test_mixed_cycle_chebyshev_step_counts(q, extra):
+    """One complex-FP32 cycle at n = 2049 with q = 2, 3, 4 Chebyshev steps
+    per smoothing (level 2 streams: pairs only, or a single step and a pair;
+    the smaller levels run q steps in one launch; the wave cycle chooses the
+    first output slot from the launch count) against the oracle cycle with
+    the same q, to 1e-5.  Also the eager emission (use_graph = 0) and
+    programmatic dependent launch (pdl = 1)."""
+    I = inst_medium(2049, 500.0, seed=95 + q)
+    h = lib_handle([I], "mixed", n_cmax=15, M=2, cheb_iters=q, **extra)
+    try:
+        g = I.g / np.linalg.norm(I.g)
+        g32 = g.astype(np.complex64)
+        u = np.zeros_like(g32)
+        B.mg_cycle(h, u, g32, 1)
+        H = oracle_hier(I, n_cmax=15, M=2, cheb_iters=q)
+        ref = H.cycle(np.zeros_like(g), g32.astype(np.complex128))
+        assert rel(u.astype(np.complex128), ref) < 1e-5, rel(u, ref)
+    finally:
+        B.mg_destroy(h)
+
+
 def test_degenerate_inputs():
     """Zero right-hand side and zero iterate stay zero; GMRES with b = L x
     returns x (r0 = 0)."""
