@@ -220,7 +220,7 @@ struct Engine : EngineBase {
     // chosen as for the Chebyshev strips.  Returns false where it does not
     // apply (FP64, small launches).
     template <bool HS>
-    void launch_restrict_jac0_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, cudaStream_t st) {
+    void launch_restrict_jac0_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, int fgv, cudaStream_t st) {
         const int smem = rs_smem<T, HS>();
         const long long warps = (long long)occ_cap(k_restrict_jac0_stream<T, 16, HS>, smem, 32 * RS_WPB) * RS_WPB;
         int best = 16;
@@ -238,7 +238,7 @@ struct Engine : EngineBase {
             // segment shares by fine points: a unit is RS_SO x 2 rh fine nodes
             const SegTable& t = H.seg_tiles(ds, RS_SO, 2 * rh * RS_WPB, false, occ_cap(kern, smem, 32 * RS_WPB));
             go(H, st, KK_RESTRICT_JAC0, bpp * (double)t.pts, [&] {
-                kl(kern, t.nblocks, dim3(32, RS_WPB), smem, st, kd(H, t), t.d, t.nseg, SU, SG, SG);
+                kl(kern, t.nblocks, dim3(32, RS_WPB), smem, st, kd(H, t), t.d, t.nseg, SU, SG, SG, fgv);
             }, t.pts);
         };
         if (best == 8) run(k_restrict_jac0_stream<T, 8, HS>, 8);
@@ -254,8 +254,9 @@ struct Engine : EngineBase {
                 hs = hs || H.hdesc[(size_t)q].sig != nullptr;
             }
             if (pts < CS_MIN_POINTS) return false;
-            if (hs) launch_restrict_jac0_stream_hs<true>(H, ds, bpp, st);
-            else launch_restrict_jac0_stream_hs<false>(H, ds, bpp, st);
+            const int fgv = fg_gvec ? 1 : 0;
+            if (hs) launch_restrict_jac0_stream_hs<true>(H, ds, bpp, fgv, st);
+            else launch_restrict_jac0_stream_hs<false>(H, ds, bpp, fgv, st);
             return true;
         }
         return false;
@@ -314,8 +315,16 @@ struct Engine : EngineBase {
         return false;
     }
     // set by fg_iter around its cycle: the cycle's last pass may form the
-    // FGMRES matvec (fg_fused reports whether it did)
-    bool fg_want = false, fg_fused = false;
+    // FGMRES matvec (fg_fused reports whether it did); fg_gvec: the level-1
+    // passes read g from the basis vector V_j (k_fg_prep left out)
+    bool fg_want = false, fg_fused = false, fg_gvec = false;
+    // the level-1 passes of the cycle stream (FP32, launch of >= CS_MIN_POINTS)
+    static bool level1_streams(Handle& H, const std::vector<int>& ds1) {
+        if (!kStream) return false;
+        long long pts = 0;
+        for (int q : ds1) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+        return pts >= CS_MIN_POINTS;
+    }
     template <int MODE>
     void launch_restrict(Handle& H, const std::vector<int>& ds, int kind, double bpp, int sx, int sb, int sc, int uzero,
                          cudaStream_t st) {
@@ -907,12 +916,21 @@ struct Engine : EngineBase {
         const SegTable& t = outer_tab(H);
         const int j = H.fg_j;
         dim3 bd(BX, BY);
-        go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
-            kl(k_fg_prep<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
-        }, t.pts);
-        fg_want = true;
+        // With the two-pass Gram-Schmidt and streaming level-1 passes, V_j is
+        // not normalised in place nor copied to the cycle's g (k_fg_prep): the
+        // cycle's level-1 passes and the Gram-Schmidt passes read it where it
+        // lies and scale it on the fly, and pass B writes it corrected.
+        const bool two = H.p.fgmres_passes == 2;
+        const bool gvec = two && level1_streams(H, descs(H, 1, all(H)));
+        if (!gvec)
+            go(H, st, KK_FG_PREP, (j > 0 ? 3 : 2) * C * t.pts, [&] {
+                kl(k_fg_prep<T>, t.nblocks, bd, 0, st, kd(H, t), t.d, t.nseg);
+            }, t.pts);
+        fg_want = two;
+        fg_gvec = gvec;
         cycle(H, true, st);
         fg_want = false;
+        fg_gvec = false;
         const int cyc = H.launches_cycle;
         const bool fused = fg_fused;
         fg_fused = false;
@@ -933,11 +951,12 @@ struct Engine : EngineBase {
                 const int cap = occ_cap(a, smem);
                 occ_cap(b, smem);
                 const SegTable& tg = H.seg_outer_chunks(od, g.pw, cap);
+                const int vs = gvec ? 1 : 0;
                 go(H, st, KK_FG_DOTS, (j + 2) * C * tg.pts, [&] {
-                    kl(a, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg, g);
+                    kl(a, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg, g, vs);
                 }, tg.pts);
                 go(H, st, KK_FG_ORTH, (j + 4) * C * tg.pts, [&] {
-                    kl(b, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg, g);
+                    kl(b, tg.nblocks, bd, smem, st, kd(H, tg), tg.d, tg.nseg, g, vs);
                 }, tg.pts);
             } else {
                 auto k0 = k_fg_gs<T, 0>;
@@ -959,7 +978,7 @@ struct Engine : EngineBase {
             }
         }
         H.launches_cycle = cyc;
-        H.launches_step = cyc + (H.p.fgmres_passes == 2 ? 4 : 5) - (fused ? 1 : 0);
+        H.launches_step = cyc + (H.p.fgmres_passes == 2 ? 4 : 5) - (fused ? 1 : 0) - (gvec ? 1 : 0);
         H.fg_j = j + 1;
     }
 

@@ -398,11 +398,13 @@ __global__ void __launch_bounds__(NT, 1) k_fg_gs(const __grid_constant__ KDesc A
 // the orthonormal basis), so the method is CGS2 with the re-orthogonalisation
 // of each new vector moved to the next step.  At the end of a restart the
 // pending column enters the update with its provisional rotation.
+// vinv: the pending vector's scale (1 when k_fg_prep normalised it in place;
+// 1 / ||W1_{j-1}|| when it was left as W1_{j-1}, see fg_iter)
 template <typename TC, int J>
 __device__ __forceinline__ void fg_lag_dots(const cplx<TC>* __restrict__ sv, int PJ, int cnt, cplx<TC> (&s1)[MAXR],
-                                            cplx<TC> (&s2)[MAXR], cplx<TC>& s3, TC& nv, int tid) {
+                                            cplx<TC> (&s2)[MAXR], cplx<TC>& s3, TC& nv, TC vinv, int tid) {
     for (int e = tid; e < cnt; e += NT) {
-        const cplx<TC> vt = sv[J * PJ + e], w = sv[(J + 1) * PJ + e];
+        const cplx<TC> vt = cscale<TC>(sv[J * PJ + e], vinv), w = sv[(J + 1) * PJ + e];
 #pragma unroll
         for (int q = 0; q < J; ++q) {
             const cplx<TC> vq = sv[q * PJ + e];
@@ -416,9 +418,10 @@ __device__ __forceinline__ void fg_lag_dots(const cplx<TC>* __restrict__ sv, int
 template <typename TC, int J>
 __device__ __forceinline__ void fg_lag_update(const cplx<TC>* __restrict__ sv, int PJ, int cnt,
                                               cplx<TC>* __restrict__ vout, cplx<TC>* __restrict__ wout,
-                                              const cplx<TC>* s1c, const cplx<TC>* hc, TC ibeta, TC& nrm, int tid) {
+                                              const cplx<TC>* s1c, const cplx<TC>* hc, TC ibeta, TC& nrm, TC vinv,
+                                              int tid) {
     for (int e = tid; e < cnt; e += NT) {
-        cplx<TC> v = sv[J * PJ + e], w = sv[(J + 1) * PJ + e];
+        cplx<TC> v = cscale<TC>(sv[J * PJ + e], vinv), w = sv[(J + 1) * PJ + e];
 #pragma unroll
         for (int q = 0; q < J; ++q) {
             const cplx<TC> vq = sv[q * PJ + e];
@@ -445,7 +448,7 @@ __device__ __forceinline__ void fg_rotate(const double* f, int j, double2* col) 
 
 template <typename TC, int PASS>
 __global__ void __launch_bounds__(NT, 1) k_fg_lag(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
-                                                  int nseg, FgGeom g) {
+                                                  int nseg, FgGeom g, int vscale) {
     extern __shared__ unsigned char fg_raw[];
     TmaCarve cv(fg_raw);
     cplx<TC>* const stg0 = cv.take<cplx<TC>>(g.ns * (MAXR + 1) * g.pw);
@@ -475,12 +478,15 @@ __global__ void __launch_bounds__(NT, 1) k_fg_lag(const __grid_constant__ KDesc 
     for (int q = 0; q < MAXR; ++q) s1[q] = s2[q] = zero2<TC>();
     TC nv = TC(0), nrm = TC(0);
     const TC ibeta = PASS == 1 ? ibeta_sh : TC(1);
+    // vscale: the pending vector V_jj is still W1_{jj-1} (k_fg_prep left out)
+    const double hnv = (vscale && jj > 0) ? d.fs[FS::HN + jj] : 1.0;
+    const TC vinv = (TC)(hnv > 0 ? 1.0 / hnv : 0.0);
     const bool ok = fg_stream<TC>(d, c, jj, w, stg0, g, bars,
                                   [&](const cplx<TC>* sv, int PJ, int cnt, long long e0) {
         fg_dispatch<MAXR>(jj, [&](auto Jc) {
             constexpr int JJ = decltype(Jc)::value;
-            if (PASS == 0) fg_lag_dots<TC, JJ>(sv, PJ, cnt, s1, s2, s3, nv, tid);
-            else fg_lag_update<TC, JJ>(sv, PJ, cnt, vj + e0, w + e0, s1c, hc, ibeta, nrm, tid);
+            if (PASS == 0) fg_lag_dots<TC, JJ>(sv, PJ, cnt, s1, s2, s3, nv, vinv, tid);
+            else fg_lag_update<TC, JJ>(sv, PJ, cnt, vj + e0, w + e0, s1c, hc, ibeta, nrm, vinv, tid);
         });
     });
     if (!ok) return;

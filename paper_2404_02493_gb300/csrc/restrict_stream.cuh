@@ -30,7 +30,7 @@ template <typename T, bool HS> __host__ __device__ constexpr int rs_smem() { ret
 template <typename T, int RHC, bool HS>
 __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __grid_constant__ KDesc A,
                                                                       const Seg* __restrict__ Sg, int nseg, int sx,
-                                                                      int sb, int sc) {
+                                                                      int sb, int sc, int fgv) {
     extern __shared__ __align__(16) unsigned char rs_smem_[];
     const int lane = threadIdx.x, warp = threadIdx.y, tid = lane + 32 * warp;
     unsigned char* const base = rs_smem_ + warp * rs_ring_bytes<T, HS>();
@@ -44,7 +44,13 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
     __syncthreads();
     const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
     const int nstrips = (n + RS_SO - 1) / RS_SO, nunits = nstrips * ((nc + RHC - 1) / RHC);
-    const cplx<T>* const gv = slot<T>(d, sb);
+    // fgv: inside an FGMRES iteration g is the basis vector V_j, read where it
+    // lies (still unnormalised) and scaled by 1 / ||V_j|| on the fly, as
+    // k_fg_prep would have copied it
+    const int jk = fgv ? (int)d.fs[FS::J] : 0;
+    const double hnv = (fgv && jk > 0) ? d.fs[FS::HN + jk] : 1.0;
+    const T gsc = (T)(hnv > 0 ? 1.0 / hnv : 0.0);
+    const cplx<T>* const gv = fgv ? kvec<T>(d, jk) : slot<T>(d, sb);
     cplx<T>* const xs = slot<T>(d, sx);
     cplx<T>* const out = slot<T>(dc, sc);
     const T* const kf = reinterpret_cast<const T*>(d.kf);
@@ -82,6 +88,7 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
             // u1 = w h^2 g / (h^2 D) at row j (one division per node)
             P2<T> g0;
             ring_read<cplx<T>>(Gr, j, lane, g0.v0, g0.v1);
+            if (fgv) g0 = P2<T>{cscale<T>(g0.v0, gsc), cscale<T>(g0.v1, gsc)};
             T k0, k1, s0 = T(0), s1 = T(0);
             ring_read<T>(Kr, j, lane, k0, k1);
             if (HS) ring_read<T>(Sr, j, lane, s0, s1);
@@ -103,6 +110,7 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
             // r = g - A u1 at row j - 1
             P2<T> rr;
             ring_read<cplx<T>>(Gr, j - 1, lane, rr.v0, rr.v1);
+            if (fgv) rr = P2<T>{cscale<T>(rr.v0, gsc), cscale<T>(rr.v1, gsc)};
             const P2<T> au = helm_row<T, false>(dg1, ua1, ua2, u0, ih2);
             rr.v0 = csub<T>(rr.v0, au.v0);
             rr.v1 = csub<T>(rr.v1, au.v1);
@@ -171,9 +179,12 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
     const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
     const int nstrips = (n + SO - 1) / SO, nunits = nstrips * ((n + RH - 1) / RH);
     const cplx<T>* const xv = slot<T>(d, sx);
-    const cplx<T>* const gv = slot<T>(d, sb);
     const cplx<T>* const ev = slot<T>(dc, sc);
     const int jk = FG ? (int)d.fs[FS::J] : 0;
+    // FG: g is the basis vector V_j, scaled on the fly (see k_restrict_jac0_stream)
+    const double hnv = (FG && jk > 0) ? d.fs[FS::HN + jk] : 1.0;
+    const T gsc = (T)(hnv > 0 ? 1.0 / hnv : 0.0);
+    const cplx<T>* const gv = FG ? kvec<T>(d, jk) : slot<T>(d, sb);
     cplx<T>* const os = FG ? zvec<T>(d, jk) : slot<T>(d, sout);
     cplx<T>* const wv = FG ? kvec<T>(d, jk + 1) : nullptr;
     const T* const kf = reinterpret_cast<const T*>(d.kf);
@@ -246,6 +257,7 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
             const P2<T> dg = diag_row<T>(d, r1, col, k0, k1, s0, s1);
             P2<T> rr;
             ring_read<cplx<T>>(Gr, r1, lane, rr.v0, rr.v1);
+            if (FG) rr = P2<T>{cscale<T>(rr.v0, gsc), cscale<T>(rr.v1, gsc)};
             const P2<T> au = helm_row<T, false>(dg, ua1, ua2, u0, ih2);
             rr.v0 = csub<T>(rr.v0, au.v0);
             rr.v1 = csub<T>(rr.v1, au.v1);

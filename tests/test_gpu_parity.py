@@ -339,14 +339,15 @@ def test_batched_mixed_cycle_streams_level2_of_small_instances():
         B.mg_destroy(h)
 
 
-@pytest.mark.parametrize("n", [1100, 1081])
-def test_mixed_cycle_streaming_level1(n):
+@pytest.mark.parametrize("n,bc", [(1100, "abc1"), (1081, "abc1"), (1100, "sponge")])
+def test_mixed_cycle_streaming_level1(n, bc):
     """One complex-FP32 cycle from zero at n = 1100 (even: the last fine row
     and column lie beyond the coarse grid's footprint) and n = 1081 (the last
     60-column strip holds one column): level 1's pre-smoothing, residual and
     restriction run as streaming strips (n^2 >= 2^20); the cycle matches the
-    FP64 oracle cycle to 1e-5."""
-    I = inst_medium(n, 0.25 * n, seed=70 + n % 7)
+    FP64 oracle cycle to 1e-5; with the sponge boundary the passes carry its
+    term in their rings."""
+    I = inst_medium(n, 0.25 * n, seed=70 + n % 7, bc=bc)
     h = lib_handle([I], "mixed", n_cmax=15, M=2)
     try:
         g = I.g / np.linalg.norm(I.g)
@@ -397,12 +398,13 @@ def test_batched_fgmres_steps_match_single_solves(prec, tol):
         assert rel(helmholtz_apply(H.lev(1), got.reshape(I.n, I.n)), I.g) < 0.5
 
 
-def test_fused_fgmres_matvec_matches_separate():
+@pytest.mark.parametrize("bc", ["abc1", "sponge"])
+def test_fused_fgmres_matvec_matches_separate(bc):
     """25 complex-FP32 FGMRES iterations of a batch (n = 1023 and 255: the
     level-1 launches cover more than 2^20 points, so the cycle's last pass
     streams and forms Z_j and W = A Z_j itself) against each instance alone
     (1023^2 < 2^20: tile prolongation, then the separate FGMRES matvec)."""
-    insts = [inst_medium(1023, 250.0, seed=81), inst_medium(255, 60.0, seed=82)]
+    insts = [inst_medium(1023, 250.0, seed=81, bc=bc), inst_medium(255, 60.0, seed=82, bc=bc)]
     K = 25
 
     def run(group):
