@@ -193,7 +193,11 @@ int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream
  * (flexible GMRES(restart) preconditioned by one cycle from zero).  u is the
  * complex128 initial guess (zeros: the paper's zero start) and receives the
  * solution; g is complex128.  Synchronises `stream` once per outer
- * iteration.  Returns MG_OK, MG_ENOTCONV or MG_EDIVERGED (also in info). */
+ * iteration.  FGMRES reads each inner iteration's residual estimate while the
+ * next inner iteration already runs: info->iterations is the first iteration
+ * whose estimate met tol, and the returned u and rel_residual include the one
+ * inner iteration launched after it (within the same restart and maxit).
+ * Returns MG_OK, MG_ENOTCONV or MG_EDIVERGED (also in info). */
 int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_stream stream);
 
 /* Building blocks of mg_solve for callers that drive the outer iteration

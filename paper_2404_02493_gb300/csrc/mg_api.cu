@@ -1182,18 +1182,44 @@ int mg_solve(mg_handle* h, void* u, const void* g, mg_solve_info* info, mg_strea
     int status = std::isfinite(rel) ? MG_OK : MG_EDIVERGED;
     const int ni = (int)H.inst.size();
     std::vector<double> est(ni);
+    // the host reads each inner iteration's residual estimate while the next
+    // iteration already runs (an event per pinned slot instead of a stream
+    // synchronisation), so the GPU does not idle for the round trip; when an
+    // estimate meets tol, the one iteration launched after it has run too
+    // (its column enters the update, the residual only falls further) and the
+    // count reported is the first iteration that met tol
+    struct EvPair {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~EvPair() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evp;
+    WADR_CHECK(cudaEventCreateWithFlags(&evp.e[0], cudaEventDisableTiming));
+    WADR_CHECK(cudaEventCreateWithFlags(&evp.e[1], cudaEventDisableTiming));
+    cudaEvent_t* const evc = evp.e;
     while (status == MG_OK && rel >= H.p.tol && it < H.p.maxit) {
         if (H.p.outer == MG_OUTER_FGMRES) {
             // one restart: inner iterations until the estimate meets tol
+            bool inflight = false;   // iteration j already launched
             for (int j = 0; j < H.p.restart && it < H.p.maxit; ++j) {
-                rc = fg_iter_launch(h, st);
-                if (rc) return rc;
+                if (!inflight) {
+                    rc = fg_iter_launch(h, st);
+                    if (rc) return rc;
+                }
                 ++it;
-                WADR_CHECK(cudaMemcpyAsync(H.hpin, H.est, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
-                WADR_CHECK(cudaStreamSynchronize(st));
+                double* slot = H.hpin + (size_t)(j & 1) * ni;
+                WADR_CHECK(cudaMemcpyAsync(slot, H.est, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+                WADR_CHECK(cudaEventRecord(evc[j & 1], st));
+                inflight = j + 1 < H.p.restart && it < H.p.maxit;
+                if (inflight) {
+                    rc = fg_iter_launch(h, st);
+                    if (rc) return rc;
+                }
+                WADR_CHECK(cudaEventSynchronize(evc[j & 1]));
                 double e = 0;
                 for (int b = 0; b < ni; ++b) {
-                    const double v = H.hpin[b] * (gn[b] > 0 ? rn[b] / gn[b] : rn[b]);
+                    const double v = slot[b] * (gn[b] > 0 ? rn[b] / gn[b] : rn[b]);
                     e = std::isfinite(v) ? std::max(e, v) : v;
                 }
                 if (info && info->history && nh < info->history_len) info->history[nh++] = e;
