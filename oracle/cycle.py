@@ -9,7 +9,7 @@ import scipy.linalg
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .operators import (Level, adr_apply, adr_coefficients, coarse_size,
+from .operators import (Level, adr_apply, adr_coefficients, coarse_size, grid_spacing,
                         helmholtz_apply, helmholtz_diag, inject, prolong, restrict,
                         sponge_gamma, missing_neighbours)
 from .smoothers import (alpha_spectral, chebyshev, chebyshev_interval, gmres,
@@ -23,7 +23,7 @@ class CycleParams:
     smoothing on level 3), Section 3.2.2 (one ADR V-cycle with one GMRES(3)
     sweep before and after), Section 4.2 (M = 8 ADR corrections) and a dense
     LU on the coarsest level."""
-    n_cmax: int = 15               # coarsen while n > n_cmax
+    n_cmax: int = 15               # coarsen while max(n, ny) > n_cmax
     jacobi_iters: int = 1
     cheb_iters: int = 5
     coarse: str = "lu"             # "lu" | "cheb"
@@ -47,20 +47,32 @@ def build_sizes(n: int, n_cmax: int):
     return sizes
 
 
+def build_shapes(n: int, ny: int, n_cmax: int):
+    """(n_l, ny_l) of levels 1..L of an n x ny grid: both sides halve
+    together (coarse node I on fine node 2I+1, Section 3.1.2) while the
+    longer side exceeds n_cmax and both coarse sides keep a node.  On the
+    square this is build_sizes."""
+    shapes = [(n, ny)]
+    while (max(shapes[-1]) > n_cmax and coarse_size(shapes[-1][0]) >= 1
+           and coarse_size(shapes[-1][1]) >= 1):
+        shapes.append((coarse_size(shapes[-1][0]), coarse_size(shapes[-1][1])))
+    return shapes
+
+
 def helmholtz_sparse(lev: Level) -> sp.csr_matrix:
     """Independent assembly of the Helmholtz matrix, node by node, from the
     5-point stencil and the boundary rules of Section 2 (used to pin the
     vectorised stencil apply and for the dense coarsest-level LU)."""
-    n, h = lev.n, lev.h
+    n, ny, h = lev.n, lev.rows, lev.h
     rows, cols, vals = [], [], []
     ih2 = 1.0 / (h * h)
-    for j in range(n):
+    for j in range(ny):
         for i in range(n):
             p = j * n + i
             kk = lev.k[j, i]
             diag = 4.0 - h * h * kk * kk + 0j
             for (jj, ii) in ((j, i - 1), (j, i + 1), (j - 1, i), (j + 1, i)):
-                if 0 <= jj < n and 0 <= ii < n:
+                if 0 <= jj < ny and 0 <= ii < n:
                     rows.append(p); cols.append(jj * n + ii); vals.append(-ih2)
                 elif lev.bc == "abc1":
                     # ghost value (1 + i conv k h) u_b moved onto the diagonal
@@ -71,45 +83,49 @@ def helmholtz_sparse(lev: Level) -> sp.csr_matrix:
             if lev.shift:
                 diag -= 1j * lev.conv * lev.shift * h * h * kk * kk
             rows.append(p); cols.append(p); vals.append(diag * ih2)
-    return sp.csr_matrix((vals, (rows, cols)), shape=(n * n, n * n), dtype=np.complex128)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n * ny, n * ny), dtype=np.complex128)
 
 
 def adr_sparse(lev: Level, closure: str = "zero", scheme: str = "upwind",
                reaction: str = "continuous") -> sp.csr_matrix:
     """Assembly of the ADR matrix from its coefficients."""
     c = adr_coefficients(lev, closure, scheme, reaction)
-    n = lev.n
+    n, ny = lev.n, lev.rows
     rows, cols, vals = [], [], []
-    for j in range(n):
+    for j in range(ny):
         for i in range(n):
             p = j * n + i
             rows.append(p); cols.append(p); vals.append(c.d[j, i])
             for (jj, ii, cf) in ((j, i - 1, c.cW), (j, i + 1, c.cE),
                                  (j - 1, i, c.cS), (j + 1, i, c.cN)):
-                if 0 <= jj < n and 0 <= ii < n:
+                if 0 <= jj < ny and 0 <= ii < n:
                     rows.append(p); cols.append(jj * n + ii); vals.append(cf[j, i])
-    return sp.csr_matrix((vals, (rows, cols)), shape=(n * n, n * n), dtype=np.complex128)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n * ny, n * ny), dtype=np.complex128)
 
 
 class Hierarchy:
     """Levels 1..L of one problem, the per-level weights and the coarsest
     LU factors (Algorithm 1: re-discretised operator A_H on every level;
-    coefficients by injection)."""
+    coefficients by injection).  n nodes per row, ny rows (default n; the
+    non-square domains of Section 4.3.3)."""
 
     def __init__(self, n: int, k: np.ndarray, phi: np.ndarray, omega: float,
                  bc: str = "abc1", params: CycleParams | None = None,
-                 conv: int = 1, shift: float = 0.0):
+                 conv: int = 1, shift: float = 0.0, ny: int | None = None):
         self.p = params or CycleParams()
-        sizes = build_sizes(n, self.p.n_cmax)
-        self.L = len(sizes)
-        gamma = sponge_gamma(n, omega) if bc == "sponge" else np.zeros((n, n))
+        ny = ny or n
+        shapes = build_shapes(n, ny, self.p.n_cmax)
+        self.L = len(shapes)
+        gamma = sponge_gamma(n, omega, ny) if bc == "sponge" else np.zeros((ny, n))
         self.levels: list[Level] = []
         kk, ph, ga = np.asarray(k, float), np.asarray(phi, float), gamma
-        for l, nl in enumerate(sizes):
+        assert kk.shape == (ny, n) and ph.shape == (ny, n)
+        for l, (nl, nyl) in enumerate(shapes):
             if l > 0:
                 kk, ph, ga = inject(kk), inject(ph), inject(ga)
-            self.levels.append(Level(n=nl, h=1.0 / (nl + 1), k=kk, phi=ph, gamma=ga,
-                                     omega=float(omega), bc=bc, conv=conv, shift=shift))
+            self.levels.append(Level(n=nl, h=grid_spacing(nl, nyl), k=kk, phi=ph, gamma=ga,
+                                     omega=float(omega), bc=bc, conv=conv, shift=shift,
+                                     ny=0 if nyl == nl else nyl))
         f = self.levels[0]
         self.omega_j = (self.p.omega_jacobi if self.p.omega_jacobi is not None
                         else jacobi_weight_default(f.h, float(np.max(f.k))))
@@ -120,7 +136,7 @@ class Hierarchy:
                 lev = self.levels[l - 1]
                 self.lam_max[l] = lambda_max_gershgorin(lev)
                 self.alpha[l] = self.p.alphas.get(
-                    l, alpha_spectral(lev.n, lev.h, float(np.max(lev.k))))
+                    l, alpha_spectral(lev.n, lev.h, float(np.max(lev.k)), lev.rows))
         self.adr = {}
         self.mod = None
         cl = self.levels[-1]
@@ -131,7 +147,8 @@ class Hierarchy:
         self.adr_sets = []
         if self.p.adr and self.L >= 3:
             if self.p.ray:
-                X, Y = np.meshgrid((np.arange(n) + 1) / (n + 1), (np.arange(n) + 1) / (n + 1), indexing="xy")
+                m1 = max(n, ny) + 1
+                X, Y = np.meshgrid((np.arange(n) + 1) / m1, (np.arange(ny) + 1) / m1, indexing="xy")
                 phases = []
                 for m in range(self.p.M):
                     th = m * 2.0 * np.pi / self.p.M
@@ -196,7 +213,7 @@ class Hierarchy:
         x = gmres(op, b, None, self.p.gmres_m)
         r = b - op(x)
         ec = self.adr_vcycle(l + 1, restrict(r), m)
-        x = x + prolong(ec, self.lev(l).n)
+        x = x + prolong(ec, self.lev(l).n, self.lev(l).rows)
         x = gmres(op, b, x, self.p.gmres_m)
         return x
 
@@ -229,7 +246,7 @@ class Hierarchy:
         r = g - helmholtz_apply(lev, u)
         rc = restrict(r)
         ec = self.cycle(np.zeros_like(rc), rc, l + 1)
-        u = u + prolong(ec, lev.n)
+        u = u + prolong(ec, lev.n, lev.rows)
         # post-smoothing
         if l == 1:
             u = jacobi(lev, u, g, self.omega_j, self.p.jacobi_iters)

@@ -1,7 +1,11 @@
 """Oracle operators: Helmholtz, ADR, restriction, prolongation (complex128).
 
-Arrays are indexed [j, i] (row j = y), node (i, j) at ((i+1)h, (j+1)h),
-h = 1/(n+1) (Section 2).  Neighbours: W = (j, i-1), E = (j, i+1),
+Arrays are indexed [j, i] (row j = y), node (i, j) at ((i+1)h, (j+1)h)
+(Section 2).  A grid has n nodes per row (x) and ny rows (y; ny = n for the
+paper's square domains).  The spacing is the same in both directions,
+h = 1/(max(n, ny)+1): the longer side of the domain has unit length, the
+domain is [0, (n+1)h] x [0, (ny+1)h] (the non-square media of Section 4.3.3;
+the paper does not fix the scaling).  Neighbours: W = (j, i-1), E = (j, i+1),
 S = (j-1, i), N = (j+1, i).
 """
 from __future__ import annotations
@@ -23,11 +27,21 @@ class Level:
     bc: str                # "abc1" | "sponge" | "dirichlet"
     conv: int = 1          # +1: exp(+i w phi) convention, -1: paper's printed signs
     shift: float = 0.0     # shifted Helmholtz: extra -i*conv*shift*k^2 (Section 4.3.2)
+    ny: int = 0            # rows; 0: square (ny = n)
+
+    @property
+    def rows(self) -> int:
+        return self.ny or self.n
 
 
-def missing_neighbours(n: int) -> np.ndarray:
+def grid_spacing(n: int, ny: int | None = None) -> float:
+    """h = 1/(max(n, ny)+1): unit length on the longer side."""
+    return 1.0 / (max(n, ny or n) + 1)
+
+
+def missing_neighbours(n: int, ny: int | None = None) -> np.ndarray:
     """Number of the four 5-point neighbours that fall outside the grid."""
-    m = np.zeros((n, n))
+    m = np.zeros((ny or n, n))
     m[:, 0] += 1
     m[:, -1] += 1
     m[0, :] += 1
@@ -35,15 +49,19 @@ def missing_neighbours(n: int) -> np.ndarray:
     return m
 
 
-def sponge_gamma(n: int, omega: float) -> np.ndarray:
+def sponge_gamma(n: int, omega: float, ny: int | None = None) -> np.ndarray:
     """Sponge damping mask (Section 2, eq. sponge): zero inside, rising to
     omega at the boundary over one wavelength W = 2*pi/omega.  The printed
     text fixes neither the shape nor the exact width; we take
-    gamma(d) = omega * ((W - d)/W)^2 for d < W, d = distance to the boundary."""
-    h = 1.0 / (n + 1)
+    gamma(d) = omega * ((W - d)/W)^2 for d < W, d = distance to the boundary
+    of the domain [0, (n+1)h] x [0, (ny+1)h]."""
+    ny = ny or n
+    h = grid_spacing(n, ny)
     x = (np.arange(n) + 1.0) * h
-    X, Y = np.meshgrid(x, x, indexing="xy")
-    d = np.minimum(np.minimum(X, 1 - X), np.minimum(Y, 1 - Y))
+    y = (np.arange(ny) + 1.0) * h
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    lx, ly = (n + 1) * h, (ny + 1) * h
+    d = np.minimum(np.minimum(X, lx - X), np.minimum(Y, ly - Y))
     W = 2 * np.pi / omega
     return np.where(d < W, omega * ((W - d) / W) ** 2, 0.0)
 
@@ -56,7 +74,7 @@ def helmholtz_diag(lev: Level) -> np.ndarray:
     h, k = lev.h, lev.k
     base = (4.0 - h * h * k * k).astype(np.complex128)
     if lev.bc == "abc1":
-        m = missing_neighbours(lev.n)
+        m = missing_neighbours(lev.n, lev.rows)
         base = base - m * (1.0 + 1j * lev.conv * k * h)
     elif lev.bc == "sponge":
         s2 = (k / lev.omega) ** 2
@@ -116,8 +134,8 @@ def phase_derivatives(phi: np.ndarray, h: float):
     differences after linear extrapolation of one ghost layer,
     phi_{-1} = 2 phi_0 - phi_1, which turns the boundary gradient into the
     one-sided first-order difference."""
-    n = phi.shape[0]
-    p = np.zeros((n + 2, n + 2))
+    ny, nx = phi.shape
+    p = np.zeros((ny + 2, nx + 2))
     p[1:-1, 1:-1] = phi
     p[1:-1, 0] = 2 * phi[:, 0] - phi[:, 1]
     p[1:-1, -1] = 2 * phi[:, -1] - phi[:, -2]
@@ -251,34 +269,36 @@ def coarse_size(n: int) -> int:
 def restrict(r: np.ndarray) -> np.ndarray:
     """Full weighting (Section 3.1.2; 2D kernel (1/16)[1 2 1; 2 4 2; 1 2 1]
     with stride two, Section 3.3).  Fine values outside the grid are zero."""
-    n = r.shape[0]
-    nc = coarse_size(n)
-    p = np.zeros((n + 2, n + 2), dtype=r.dtype)
+    ny, nx = r.shape
+    ncy, ncx = coarse_size(ny), coarse_size(nx)
+    p = np.zeros((ny + 2, nx + 2), dtype=r.dtype)
     p[1:-1, 1:-1] = r
-    out = np.zeros((nc, nc), dtype=r.dtype)
+    out = np.zeros((ncy, ncx), dtype=r.dtype)
     for b in range(3):
         for a in range(3):
             # fine index 2J+1+(b-1) -> padded index 2J+1+b
-            sl = p[b + 1: b + 1 + 2 * nc: 2, a + 1: a + 1 + 2 * nc: 2]
+            sl = p[b + 1: b + 1 + 2 * ncy: 2, a + 1: a + 1 + 2 * ncx: 2]
             out += _W[a] * _W[b] / 16.0 * sl
     return out
 
 
-def prolong(e: np.ndarray, n_fine: int) -> np.ndarray:
+def prolong(e: np.ndarray, n_fine: int, ny_fine: int | None = None) -> np.ndarray:
     """Bilinear interpolation I_H^h = 4 (I_h^H)^T in 2D (2 (I_h^H)^T per
     dimension, Section 3.1.2): kernel (1/4)[1 2 1; 2 4 2; 1 2 1] as a
-    stride-two transposed convolution (Section 3.3)."""
-    nc = e.shape[0]
-    assert nc == coarse_size(n_fine)
-    p = np.zeros((n_fine + 2, n_fine + 2), dtype=e.dtype)
+    stride-two transposed convolution (Section 3.3).  n_fine nodes per row,
+    ny_fine rows (default n_fine)."""
+    ny_fine = ny_fine or n_fine
+    ncy, ncx = e.shape
+    assert ncx == coarse_size(n_fine) and ncy == coarse_size(ny_fine)
+    p = np.zeros((ny_fine + 2, n_fine + 2), dtype=e.dtype)
     for b in range(3):
         for a in range(3):
-            p[b + 1: b + 1 + 2 * nc: 2, a + 1: a + 1 + 2 * nc: 2] += \
+            p[b + 1: b + 1 + 2 * ncy: 2, a + 1: a + 1 + 2 * ncx: 2] += \
                 _W[a] * _W[b] / 4.0 * e
     return p[1:-1, 1:-1].copy()
 
 
 def inject(f: np.ndarray) -> np.ndarray:
     """Coefficient injection onto the coarse grid: sample fine node 2I+1."""
-    nc = coarse_size(f.shape[0])
-    return f[1:2 * nc:2, 1:2 * nc:2].copy()
+    ncy, ncx = coarse_size(f.shape[0]), coarse_size(f.shape[1])
+    return f[1:2 * ncy:2, 1:2 * ncx:2].copy()

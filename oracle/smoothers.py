@@ -32,21 +32,25 @@ def lambda_max_gershgorin(lev: Level) -> float:
     For the complex-symmetric A, ||A||_2 <= sqrt(||A||_1 ||A||_inf) =
     ||A||_inf."""
     D = helmholtz_diag(lev)
-    nnb = 4.0 - missing_neighbours(lev.n)
+    nnb = 4.0 - missing_neighbours(lev.n, lev.rows)
     row = np.abs(D) + nnb / (lev.h * lev.h)
     return float(np.max(row) ** 2)
 
 
-def alpha_spectral(n: int, h: float, kref: float) -> float:
+def alpha_spectral(n: int, h: float, kref: float, ny: int | None = None) -> float:
     """alpha = lambda_max / median(eig(A^*A)) (Section 3.1.1 and 3.2.1: the
     lower end lambda_max/alpha of the Chebyshev interval approximates the
     median of the spectrum of A^*A), evaluated on the constant-kref
-    Dirichlet 5-point operator, whose eigenvalues are the tensor sums
-    (4 sin^2(p pi h/2) + 4 sin^2(q pi h/2))/h^2 - kref^2 (eq. eigs in 2D).
-    The median of an even count is the mean of the two middle values."""
-    j = np.arange(1, n + 1)
-    s = 4.0 * np.sin(j * np.pi * h / 2) ** 2 / (h * h)
-    lam = (s[:, None] + s[None, :] - kref * kref).ravel()
+    Dirichlet 5-point operator on n x ny nodes of spacing h, whose
+    eigenvalues are the tensor sums
+    (4 sin^2(p pi/(2(n+1))) + 4 sin^2(q pi/(2(ny+1))))/h^2 - kref^2
+    (eq. eigs in 2D; on the square h = 1/(n+1) and the sines are
+    sin(p pi h/2)).  The median of an even count is the mean of the two
+    middle values."""
+    ny = ny or n
+    sx = 4.0 * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2 / (h * h)
+    sy = 4.0 * np.sin(np.arange(1, ny + 1) * np.pi / (2 * (ny + 1))) ** 2 / (h * h)
+    lam = (sy[:, None] + sx[None, :] - kref * kref).ravel()
     ev = lam * lam
     return float(ev.max() / np.median(ev))
 

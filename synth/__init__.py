@@ -7,7 +7,9 @@ here.
 
 Grid convention (Section 2): n x n interior nodes of the unit square,
 h = 1/(n+1), node (i, j) at x = ((i+1)h, (j+1)h), arrays indexed [j, i]
-(row j is the y coordinate).
+(row j is the y coordinate).  Non-square grids (Section 4.3.3) have n nodes
+per row and ny rows at the same spacing h = 1/(max(n, ny)+1): the longer
+side has unit length.
 
 Media stand in for the paper's CIFAR-10 / OpenFWI / STL-10 slowness models
 (Section 4.1), which are not available: smooth Gaussian random fields and
@@ -29,23 +31,27 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def grid_coords(n: int):
-    """Node coordinates (X, Y) of the n x n interior grid, h = 1/(n+1)."""
-    h = 1.0 / (n + 1)
+def grid_coords(n: int, ny: int | None = None):
+    """Node coordinates (X, Y) of the n x ny interior grid (ny = n: the unit
+    square, h = 1/(n+1)); h = 1/(max(n, ny)+1)."""
+    ny = ny or n
+    h = 1.0 / (max(n, ny) + 1)
     x = (np.arange(n) + 1.0) * h
-    X, Y = np.meshgrid(x, x, indexing="xy")
+    y = (np.arange(ny) + 1.0) * h
+    X, Y = np.meshgrid(x, y, indexing="xy")
     return X, Y, h
 
 
-def grf(n: int, corr_len: float, seed: int) -> np.ndarray:
-    """Standardised Gaussian random field: white noise (seeded) smoothed by a
-    periodic Gaussian filter of standard deviation `corr_len` (unit-square
-    lengths), then shifted/scaled to mean 0, standard deviation 1."""
+def grf(n: int, corr_len: float, seed: int, ny: int | None = None) -> np.ndarray:
+    """Standardised Gaussian random field on n x ny nodes: white noise
+    (seeded) smoothed by a periodic Gaussian filter of standard deviation
+    `corr_len` (lengths of the unit longer side), then shifted/scaled to
+    mean 0, standard deviation 1."""
+    ny = ny or n
     rng = np.random.default_rng(seed)
-    w = rng.standard_normal((n, n))
-    h = 1.0 / (n + 1)
-    f = np.fft.fftfreq(n, d=h)
-    FX, FY = np.meshgrid(f, f, indexing="xy")
+    w = rng.standard_normal((ny, n))
+    h = 1.0 / (max(n, ny) + 1)
+    FX, FY = np.meshgrid(np.fft.fftfreq(n, d=h), np.fft.fftfreq(ny, d=h), indexing="xy")
     filt = np.exp(-2.0 * np.pi ** 2 * corr_len ** 2 * (FX ** 2 + FY ** 2))
     z = np.real(np.fft.ifft2(np.fft.fft2(w) * filt))
     z = (z - z.mean()) / z.std()
@@ -62,12 +68,14 @@ def lognormal_speed(n: int, seed: int, corr_len: float = 0.1, cmin: float = 1.0,
 
 def layered_speed(n: int, seed: int, nlayers: int = 6, cmin: float = 1.5,
                   cmax: float = 4.5, smooth_h: float = 4.0, pert: float = 0.1,
-                  corr_len: float = 0.1) -> np.ndarray:
+                  corr_len: float = 0.1, ny: int | None = None) -> np.ndarray:
     """Horizontal layers whose speed rises linearly with depth (y) from cmin to
     cmax, interfaces smoothed by a Gaussian of `smooth_h` grid spacings,
-    multiplied by (1 + pert * GRF), clipped to [cmin, cmax]."""
-    X, Y, h = grid_coords(n)
-    y = Y[:, 0]
+    multiplied by (1 + pert * GRF), clipped to [cmin, cmax].  The layers
+    divide the depth of the domain, (ny+1)h, evenly."""
+    ny = ny or n
+    X, Y, h = grid_coords(n, ny)
+    y = Y[:, 0] if ny == n else Y[:, 0] / ((ny + 1) * h)
     idx = np.clip(np.floor(nlayers * y).astype(int), 0, nlayers - 1)
     prof = cmin + (cmax - cmin) * idx / (nlayers - 1)
     # 1-D Gaussian smoothing along depth, edge values replicated
@@ -79,22 +87,23 @@ def layered_speed(n: int, seed: int, nlayers: int = 6, cmin: float = 1.5,
     padded = np.concatenate([np.full(rad, prof[0]), prof, np.full(rad, prof[-1])])
     prof_s = np.convolve(padded, ker, mode="valid")
     c = np.repeat(prof_s[:, None], n, axis=1)
-    c = c * (1.0 + pert * grf(n, corr_len, seed))
+    c = c * (1.0 + pert * grf(n, corr_len, seed, ny))
     return np.clip(c, cmin, cmax)
 
 
-def gaussian_source(n: int, x0: float, y0: float, sigma_h: float = 2.0) -> np.ndarray:
+def gaussian_source(n: int, x0: float, y0: float, sigma_h: float = 2.0,
+                    ny: int | None = None) -> np.ndarray:
     """g = exp(-|x-x0|^2 / (2 sigma^2)) / (2 pi sigma^2), sigma = sigma_h * h."""
-    X, Y, h = grid_coords(n)
+    X, Y, h = grid_coords(n, ny)
     sig = sigma_h * h
     r2 = (X - x0) ** 2 + (Y - y0) ** 2
     return np.exp(-r2 / (2 * sig * sig)) / (2 * np.pi * sig * sig)
 
 
-def distance_phase(n: int, x0: float, y0: float) -> np.ndarray:
+def distance_phase(n: int, x0: float, y0: float, ny: int | None = None) -> np.ndarray:
     """phi = |x - x0|, the eikonal solution for s = 1 (Section 3.2, eq.
     eikonal_cons)."""
-    X, Y, h = grid_coords(n)
+    X, Y, h = grid_coords(n, ny)
     return np.sqrt((X - x0) ** 2 + (Y - y0) ** 2)
 
 
@@ -116,6 +125,8 @@ def _eikonal_lib():
         ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_double,
         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
         ctypes.c_void_p]
+    lib.eikonal_fast_sweep_rect.restype = ctypes.c_int
+    lib.eikonal_fast_sweep_rect.argtypes = [ctypes.c_int] + lib.eikonal_fast_sweep.argtypes
     _eik_lib = lib
     return lib
 
@@ -133,14 +144,14 @@ def build_eikonal() -> str:
 
 def eikonal(s: np.ndarray, x0: float, y0: float, r_init_h: float = 3.0,
             max_iter: int = 200, tol: float = 1e-12) -> np.ndarray:
-    """Travel time tau with |grad tau| = s, tau(x0) = 0, by fast sweeping."""
-    n = s.shape[0]
-    assert s.shape == (n, n)
-    h = 1.0 / (n + 1)
+    """Travel time tau with |grad tau| = s, tau(x0) = 0, by fast sweeping
+    (s of shape (ny, n); h = 1/(max(n, ny)+1))."""
+    ny, n = s.shape
+    h = 1.0 / (max(n, ny) + 1)
     s64 = np.ascontiguousarray(s, dtype=np.float64)
     tau = np.empty_like(s64)
-    it = _eikonal_lib().eikonal_fast_sweep(
-        n, h, s64.ctypes.data, float(x0), float(y0), r_init_h * h, max_iter,
+    it = _eikonal_lib().eikonal_fast_sweep_rect(
+        n, ny, h, s64.ctypes.data, float(x0), float(y0), r_init_h * h, max_iter,
         tol, tau.ctypes.data)
     if it < 0:
         raise ValueError("eikonal: no grid node within the initial radius")
@@ -198,6 +209,26 @@ def config_layered(n: int = 4095, omega: float = 2000.0, seed: int = 5) -> Insta
     phi = eikonal(s, *x0)
     return Instance(n=n, omega=float(omega), k=kk, phi=phi, g=g, bc="abc1",
                     x0=x0, name=f"layered-seed{seed}-n{n}-w{omega:g}")
+
+
+def config_layered_rect(n: int = 1023, ny: int = 511, omega: float = 500.0, seed: int = 7,
+                        x0=None, bc: str = "abc1") -> Instance:
+    """Non-square medium (the role of Section 4.3.3's Marmousi, Salt and
+    Overthrust models, which are not available): n x ny nodes (n per row),
+    h = 1/(max(n, ny)+1), six smoothed horizontal layers c in [1.5, 4.5]
+    times (1 + 0.1 GRF), s = 1.5/c, k = omega*s, a Gaussian source near the
+    top of the domain (default: centred in x, at a quarter of the depth),
+    eikonal phase."""
+    h = 1.0 / (max(n, ny) + 1)
+    if x0 is None:
+        x0 = (0.5 * (n + 1) * h, 0.25 * (ny + 1) * h)
+    c = layered_speed(n, seed, ny=ny)
+    s = 1.5 / c
+    kk = omega * s
+    g = gaussian_source(n, *x0, ny=ny).astype(np.complex128)
+    phi = eikonal(s, *x0)
+    return Instance(n=n, omega=float(omega), k=kk, phi=phi, g=g, bc=bc, x0=tuple(x0),
+                    name=f"layered-rect-seed{seed}-{n}x{ny}-w{omega:g}", meta={"ny": ny})
 
 
 def config_batch(count: int = 64, sizes=(255, 511, 1023), seed0: int = 100):
