@@ -15,7 +15,9 @@
  *
  * Conventions
  *   - Grid: n x n interior nodes of the unit square, h = 1/(n+1), node (i, j)
- *     at ((i+1)h, (j+1)h).  User arrays are dense row-major, index j*n + i
+ *     at ((i+1)h, (j+1)h); or n x ny nodes of a rectangle (mg_instance.ny,
+ *     Section 4.3.3's non-square domains) at the same spacing in x and y,
+ *     h = 1/(max(n, ny)+1).  User arrays are dense row-major, index j*n + i
  *     (row j = y).  Batched calls concatenate the instances' arrays in the
  *     order they were given to mg_setup.
  *   - Complex vectors are interleaved (re, im): complex128 (double[2]) for
@@ -84,7 +86,8 @@ enum { MG_ADR_REACTION_CONTINUOUS = 0, MG_ADR_REACTION_DISCRETE = 1 };
  * tolerance 1e-6). */
 typedef struct mg_params {
     int precision;          /* MG_PREC_FP64 | MG_PREC_MIXED (complex-FP32 cycle, FP64 outer) */
-    int n_cmax;             /* coarsen while n > n_cmax (default 15); coarsest n^2 <= 1024 */
+    int n_cmax;             /* coarsen while max(n, ny) > n_cmax (default 15); coarsest n ny <= 1024 and
+                               both sides >= 2 */
     int jacobi_iters;       /* 1 */
     int cheb_iters;         /* 5 (<= 16) */
     int coarse;             /* MG_COARSE_LU (dense FP64 LU) | MG_COARSE_CHEB (Algorithm 1, q=10) */
@@ -143,13 +146,19 @@ typedef struct mg_params {
                                (for callers that share the GPU; mg_workspace_bytes reports the size) */
 } mg_params;
 
-/* One Helmholtz problem -Lap u - k^2 u = g (Section 2). */
+/* One Helmholtz problem -Lap u - k^2 u = g (Section 2) on n x ny interior
+ * nodes: arrays are row-major with n nodes per row (x) and ny rows (y),
+ * element (i, j) at j*n + i, node at ((i+1)h, (j+1)h), h = 1/(max(n, ny)+1)
+ * (the longer side has unit length; square: h = 1/(n+1)).  Non-square
+ * domains are Section 4.3.3's; both sides halve together down the
+ * hierarchy. */
 typedef struct mg_instance {
-    int n;                  /* interior nodes per side, n > n_cmax */
+    int n;                  /* interior nodes per row (x); max(n, ny) > n_cmax */
     double omega;           /* reference angular frequency (= max k), > 0 */
-    const double* k;        /* n*n wavenumber field k(x) > 0 (FP64) */
-    const double* phi;      /* n*n phase field phi (FP64); eikonal travel time */
+    const double* k;        /* n*ny wavenumber field k(x) > 0 (FP64) */
+    const double* phi;      /* n*ny phase field phi (FP64); eikonal travel time */
     int bc;                 /* MG_BC_* */
+    int ny;                 /* rows (y); 0: ny = n (square) */
 } mg_instance;
 
 typedef struct mg_solve_info {
@@ -176,9 +185,11 @@ const char* mg_last_error(void);
  * [lambda_max/alpha, lambda_max] (Section 3.1.1) is set from the Gershgorin
  * bound and the spectral alpha rule, and the coarsest Helmholtz and ADR
  * operators are factored by a device-side dense FP64 LU with partial
- * pivoting.  Synchronises `stream`.  Errors: MG_EINVAL (n <= n_cmax, n_L^2 >
- * 1024, omega <= 0, null pointers, non-finite k or phi), MG_ENOMEM,
- * MG_ECUDA. */
+ * pivoting.  Synchronises `stream`.  Errors: MG_EINVAL (max(n, ny) <= n_cmax,
+ * coarsest level of more than 1024 nodes or with a side below 2, omega <= 0,
+ * null pointers, non-finite k or phi), MG_ENOMEM, MG_ECUDA.  Handles with a
+ * non-square instance run every level with its own launches (the coarse and
+ * wave tails are for square levels). */
 int mg_setup(mg_handle** h, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream);
 
 /* u <- cycle^ncycles(u, g) (Algorithm 1 from level 1), in the handle's cycle
@@ -236,7 +247,8 @@ long long mg_workspace_bytes(const mg_handle* h);
  * checkpoint and swept backwards with the transposed operators (A^H, L^H,
  * R^T = P/4, P^T = 4R), the reversed Chebyshev recurrence and GMRES(3)
  * differentiated through its least-squares definition.  FP64 handles with
- * the LU coarsest level only (MG_EUNSUPPORTED otherwise).  Pointers may be
+ * the LU coarsest level and square instances only (MG_EUNSUPPORTED
+ * otherwise).  Pointers may be
  * host or device memory; synchronises `stream`. */
 int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const void* gbar_uK, double* grad_phi,
                       double* grad_weights, void* grad_u0, mg_stream stream);
@@ -263,7 +275,8 @@ int mg_profile_records(mg_handle* h, int nsteps, int* kind, long long* pts, doub
 
 /* ------------------------------------------------------------------------
  * Level operations: single-instance entry points into the same kernels the
- * cycle uses, for verification.  All vectors are dense n_l x n_l in the
+ * cycle uses, for verification.  All vectors are dense n_l x ny_l (ny_l rows of
+ * n_l) in the
  * cycle precision of the handle; `inst` selects the instance, `level` is
  * 1-based.  Synchronous with respect to `stream` only through copies.
  * ---------------------------------------------------------------------- */
@@ -283,8 +296,10 @@ int mg_level_roles(int n, const mg_params* p, int* sizes, int* roles, int maxl);
 
 /* Number of levels L of an instance (Algorithm 1's max-level). */
 int mg_num_levels(const mg_handle* h, int inst);
-/* n_l of level `level`. */
+/* n_l (nodes per row) of level `level`. */
 int mg_level_n(const mg_handle* h, int inst, int level);
+/* ny_l (rows) of level `level` (= n_l on square instances). */
+int mg_level_ny(const mg_handle* h, int inst, int level);
 /* Setup scalars of a level: out[0] = lambda_max (Gershgorin bound of A^*A),
  * out[1] = alpha, out[2] = Jacobi weight, out[3] = h, out[4] = Peclet
  * number omega h max(|phi_x|, |phi_y|) of the ADR operator (0 on levels

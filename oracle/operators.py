@@ -60,7 +60,9 @@ def sponge_gamma(n: int, omega: float, ny: int | None = None) -> np.ndarray:
     x = (np.arange(n) + 1.0) * h
     y = (np.arange(ny) + 1.0) * h
     X, Y = np.meshgrid(x, y, indexing="xy")
-    lx, ly = (n + 1) * h, (ny + 1) * h
+    m = max(n, ny)
+    lx = 1.0 if n == m else (n + 1) * h     # the longer side has unit length
+    ly = 1.0 if ny == m else (ny + 1) * h
     d = np.minimum(np.minimum(X, lx - X), np.minimum(Y, ly - Y))
     W = 2 * np.pi / omega
     return np.where(d < W, omega * ((W - d) / W) ** 2, 0.0)

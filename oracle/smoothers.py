@@ -48,8 +48,11 @@ def alpha_spectral(n: int, h: float, kref: float, ny: int | None = None) -> floa
     sin(p pi h/2)).  The median of an even count is the mean of the two
     middle values."""
     ny = ny or n
-    sx = 4.0 * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2 / (h * h)
-    sy = 4.0 * np.sin(np.arange(1, ny + 1) * np.pi / (2 * (ny + 1))) ** 2 / (h * h)
+    if ny == n:
+        sx = sy = 4.0 * np.sin(np.arange(1, n + 1) * np.pi * h / 2) ** 2 / (h * h)
+    else:
+        sx = 4.0 * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2 / (h * h)
+        sy = 4.0 * np.sin(np.arange(1, ny + 1) * np.pi / (2 * (ny + 1))) ** 2 / (h * h)
     lam = (sy[:, None] + sx[None, :] - kref * kref).ravel()
     ev = lam * lam
     return float(ev.max() / np.median(ev))

@@ -45,7 +45,7 @@ class MgParams(ctypes.Structure):
 
 class MgInstance(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("omega", ctypes.c_double), ("k", ctypes.c_void_p),
-                ("phi", ctypes.c_void_p), ("bc", ctypes.c_int)]
+                ("phi", ctypes.c_void_p), ("bc", ctypes.c_int), ("ny", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):
@@ -75,6 +75,7 @@ def load():
         "mg_destroy": (None, [vp]),
         "mg_num_levels": (ip, [vp, ip]),
         "mg_level_n": (ip, [vp, ip, ip]),
+        "mg_level_ny": (ip, [vp, ip, ip]),
         "mg_level_scalars": (ip, [vp, ip, ip, ctypes.POINTER(dp), ip]),
         "mg_apply": (ip, [vp, ip, ip, ip, vp, vp, vp]),
         "mg_residual": (ip, [vp, ip, ip, vp, vp, vp, vp]),
@@ -116,7 +117,7 @@ def load():
 def exported_symbols():
     """Names declared by the C ABI (the binding's signature table)."""
     return ["mg_default_params", "mg_last_error", "mg_setup", "mg_cycle", "mg_solve", "mg_destroy",
-            "mg_num_levels", "mg_level_n", "mg_level_scalars", "mg_apply", "mg_residual",
+            "mg_num_levels", "mg_level_n", "mg_level_ny", "mg_level_scalars", "mg_apply", "mg_residual",
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
@@ -185,14 +186,17 @@ def default_params(**kw) -> MgParams:
 
 # ------------------------------------------------------------------ C names
 def mg_setup(instances, params: MgParams, stream=None):
-    """instances: sequence of (n, omega, k, phi, bc) with k, phi float64 arrays
-    (device tensors or host arrays).  Returns the opaque handle pointer."""
+    """instances: sequence of (n, omega, k, phi, bc) or (n, omega, k, phi, bc,
+    ny) with k, phi float64 arrays of ny rows of n (device tensors or host
+    arrays; ny omitted or 0: square).  Returns the opaque handle pointer."""
     lib = load()
     arr = (MgInstance * len(instances))()
     keep = []
-    for i, (n, omega, k, phi, bc) in enumerate(instances):
+    for i, inst in enumerate(instances):
+        n, omega, k, phi, bc = inst[:5]
         keep += [k, phi]
         arr[i].n = int(n)
+        arr[i].ny = int(inst[5]) if len(inst) > 5 else 0
         arr[i].omega = float(omega)
         arr[i].k = _ptr(k).value
         arr[i].phi = _ptr(phi).value
@@ -231,6 +235,11 @@ def mg_num_levels(h, inst=0):
 def mg_level_n(h, inst, level):
     r = load().mg_level_n(h, inst, level)
     return _check(r, "mg_level_n") if r < 0 else r
+
+
+def mg_level_ny(h, inst, level):
+    r = load().mg_level_ny(h, inst, level)
+    return _check(r, "mg_level_ny") if r < 0 else r
 
 
 def mg_level_scalars(h, inst, level):

@@ -1199,6 +1199,11 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
     if (H.p.coarse != MG_COARSE_LU) { set_error("mg_cycle_backward: coarsest level must be the dense LU"); return MG_EUNSUPPORTED; }
     if (H.p.ray) { set_error("mg_cycle_backward: not available for Wave-Ray handles (no phase input)"); return MG_EUNSUPPORTED; }
     for (const InstHost& I : H.inst)
+        if (I.ny != I.n) {
+            set_error("mg_cycle_backward: square grids only (the adjoint kernels assume n x n levels)");
+            return MG_EUNSUPPORTED;
+        }
+    for (const InstHost& I : H.inst)
         if (I.adr_flags) {
             set_error("mg_cycle_backward: not available with the absorbing ADR boundary closure (MG_ADR_BC_ABC) "
                       "or the discrete reaction term (MG_ADR_REACTION_DISCRETE)");

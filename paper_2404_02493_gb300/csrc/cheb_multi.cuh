@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(NT) k_cheb_multi(const __grid_constant__ KDesc
     cplx<T>* const G = Tt + WW;
     cplx<T>* const DG = G + WW;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * blockDim.x;
-    const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + TS - 1) / TS, ntiles = ntx * ((n + TS - 1) / TS);
+    const int n = d.n, ny = d.ny, pitch = d.pitch;
+    const int ntx = (n + TS - 1) / TS, ntiles = ntx * ((ny + TS - 1) / TS);
     const cplx<T>* const xin = slot<T>(d, sxin);
     const cplx<T>* const gv = slot<T>(d, SG);
     cplx<T>* const xout = slot<T>(d, sxout);
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(NT) k_cheb_multi(const __grid_constant__ KDesc
             const int r = e / W, cc = e - r * W;
             const int gi = x0 + cc, gj = y0 + r;
             cplx<T> xv = zero2<T>(), gval = zero2<T>(), dg = zero2<T>();
-            if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+            if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny) {
                 const long long p = (long long)gj * pitch + gi;
                 if (!xzero) xv = xin[p];
                 gval = gv[p];
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_cheb_multi(const __grid_constant__ KDesc
                     const int e = r * W + cc;
                     const int gi = x0 + cc, gj = y0 + r;
                     cplx<T> tv = zero2<T>();
-                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny) {
                         tv = G[e];
                         if (!xz) {
                             const cplx<T> sn = cadd<T>(cadd<T>(X[e - 1], X[e + 1]), cadd<T>(X[e - W], X[e + W]));
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(NT) k_cheb_multi(const __grid_constant__ KDesc
                 for (int cc = lo2 + tx; cc < W - lo2; cc += BX) {
                     const int e = r * W + cc;
                     const int gi = x0 + cc, gj = y0 + r;
-                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny) {
                         const cplx<T> sn =
                             cadd<T>(cadd<T>(Tt[e - 1], Tt[e + 1]), cadd<T>(Tt[e - W], Tt[e + W]));
                         cplx<T> dg = DG[e];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT) k_cheb_multi(const __grid_constant__ KDesc
         for (int r = H + ty; r < H + TS; r += BY)
             for (int cc = H + tx; cc < H + TS; cc += BX) {
                 const int gi = x0 + cc, gj = y0 + r;
-                if (gi < n && gj < n) xout[(long long)gj * pitch + gi] = X[r * W + cc];
+                if (gi < n && gj < ny) xout[(long long)gj * pitch + gi] = X[r * W + cc];
             }
         __syncthreads();
     }

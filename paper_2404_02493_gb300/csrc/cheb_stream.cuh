@@ -54,11 +54,11 @@ template <typename T, bool HS> __host__ __device__ constexpr int cs_smem() {
 // inside the grid on the left; a pair straddling column n keeps its first
 // element and zero-fills the second).
 template <typename E>
-__device__ __forceinline__ void ring_issue2(E* ring, const E* __restrict__ g, int n, int pitch, int X0, int r,
-                                            int lane) {
+__device__ __forceinline__ void ring_issue2(E* ring, const E* __restrict__ g, int n, int ny, int pitch, int X0,
+                                            int r, int lane) {
     E* slotp = ring + (r & (SW_DEP - 1)) * SW_COLS + 2 * lane;
     const int c0 = X0 + 2 * lane;
-    const int cnt = ((unsigned)r < (unsigned)n && (unsigned)c0 < (unsigned)n) ? min(2, n - c0) : 0;
+    const int cnt = ((unsigned)r < (unsigned)ny && (unsigned)c0 < (unsigned)n) ? min(2, n - c0) : 0;
     const E* src = cnt ? g + (long long)r * pitch + c0 : g;
     const unsigned sa = (unsigned)__cvta_generic_to_shared(slotp);
     const int sz = cnt * (int)sizeof(E);
@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
     T* const Sr = Kr + SW_DEP * SW_COLS;
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int n = d.n, pitch = d.pitch;
-    const int nstrips = (n + SO - 1) / SO, nunits = nstrips * ((n + RH - 1) / RH);
+    const int n = d.n, ny = d.ny, pitch = d.pitch;
+    const int nstrips = (n + SO - 1) / SO, nunits = nstrips * ((ny + RH - 1) / RH);
     const cplx<T>* const xin = slot<T>(d, sxin);
     const cplx<T>* const gv = slot<T>(d, SG);
     const cplx<T>* const din = slot<T>(d, sdin);
@@ -151,17 +151,17 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
     constexpr int WPB = cs_wpb<HS>();
     for (int u = c.lb * WPB + warp; u < nunits; u += c.nb * WPB) {
         const int sk = u % nstrips, band = u / nstrips;
-        const int X0 = SO * sk - HW, y0 = RH * band, y1 = min(y0 + RH, n);
+        const int X0 = SO * sk - HW, y0 = RH * band, y1 = min(y0 + RH, ny);
         const int j0 = y0 - 2 * NS, j1 = y1 - 1 + 2 * NS;
         const int col = X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const bool colint = X0 >= 1 && X0 + SW_COLS - 1 <= n - 2;   // all 64 columns in [1, n - 2]
         auto issue = [&](int r) {
-            if (!xzero) ring_issue2<cplx<T>>(Xr, xin, n, pitch, X0, r, lane);
-            ring_issue2<cplx<T>>(Gr, gv, n, pitch, X0, r, lane);
-            ring_issue2<T>(Kr, kf, n, pitch, X0, r, lane);
-            if (HS) ring_issue2<T>(Sr, sgf, n, pitch, X0, r, lane);
-            if (rd) ring_issue2<cplx<T>>(Dr, din, n, pitch, X0, r, lane);
+            if (!xzero) ring_issue2<cplx<T>>(Xr, xin, n, ny, pitch, X0, r, lane);
+            ring_issue2<cplx<T>>(Gr, gv, n, ny, pitch, X0, r, lane);
+            ring_issue2<T>(Kr, kf, n, ny, pitch, X0, r, lane);
+            if (HS) ring_issue2<T>(Sr, sgf, n, ny, pitch, X0, r, lane);
+            if (rd) ring_issue2<cplx<T>>(Dr, din, n, ny, pitch, X0, r, lane);
         };
 #pragma unroll
         for (int r = 0; r < AH; ++r) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
                 if (HS) ring_read<T>(Sr, r1, lane, s0, s1);
                 const P2<T> dg1 = E ? diag_row<T>(d, r1, col, k0, k1, s0, s1) : diag_in_row<T>(d, k0, k1, s0, s1);
                 // level 1: t_m = g - A x_m at row j - 1
-                const bool ro1 = (unsigned)r1 < (unsigned)n;
+                const bool ro1 = (unsigned)r1 < (unsigned)ny;
                 P2<T> t1;
                 ring_read<cplx<T>>(Gr, r1, lane, t1.v0, t1.v1);
                 if (!xzero) {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
                 if constexpr (E) t1 = p2sel<T>(t1, ro1 && cin0, ro1 && cin1);
                 // level 2: d_m, x_{m+1} at row j - 2
                 const int r2 = j - 2;
-                const bool ro2 = (unsigned)r2 < (unsigned)n;
+                const bool ro2 = (unsigned)r2 < (unsigned)ny;
                 const P2<T> sv = helm_row<T, true>(dg2, ta2, ta3, t1, ih2);
                 P2<T> dm{cscale<T>(sv.v0, c2a), cscale<T>(sv.v1, c2a)};
                 if (rd) {
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
                     const P2<T> dn = E ? p2sel<T>(dm, ro2 && cin0, ro2 && cin1) : dm;
                     // level 3: t_{m+1} = g - A x_{m+1} at row j - 3
                     const int r3 = j - 3;
-                    const bool ro3 = (unsigned)r3 < (unsigned)n;
+                    const bool ro3 = (unsigned)r3 < (unsigned)ny;
                     P2<T> t2;
                     ring_read<cplx<T>>(Gr, r3, lane, t2.v0, t2.v1);
                     const P2<T> ax = helm_row<T, false>(dg3, xb3, xb4, xn, ih2);
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
                 xa2 = xa1; xa1 = x0;
                 dg4 = dg3; dg3 = dg2; dg2 = dg1;
             };
-            if (colint && j >= 3 && j <= n - 1) row(std::false_type{});
+            if (colint && j >= 3 && j <= ny - 1) row(std::false_type{});
             else row(std::true_type{});
         }
         cp_async_wait<0>();

@@ -77,7 +77,7 @@ enum Bc : int { BC_DIRICHLET = 0, BC_ABC1 = 1, BC_SPONGE = 2 };
 struct LevelDesc {
     void* vec;              // slot base (cplx<T>)
     long long slot_stride;  // elements between slots
-    const void* kf;         // wavenumber k (T), n x pitch
+    const void* kf;         // wavenumber k (T), ny rows of pitch elements
     const void* sig;        // sponge term w*gamma*s^2 (T) or null
     const void* adr;        // ADR coefficients quad<T> (phix, phiy, d.re, d.im) or null
     const void* mod;        // exp(+i w phi) (cplx<T>), level 2 only, or null
@@ -86,7 +86,8 @@ struct LevelDesc {
     void* scal;             // scalar area (see namespace S), working precision T
     void* part;             // reduction partials [max_blocks][MAXDOT] of cplx<T>
     unsigned* counter;      // last-block counters [NCOUNTERS]
-    int n, pitch;
+    int n, pitch;           // nodes per row (x), row pitch (elements)
+    int ny;                 // rows (y); ny = n on square grids
     double h, inv_h2;
     double omega;           // scalar angular frequency (ADR)
     double shift;           // shifted Helmholtz coefficient (0: none)
@@ -186,7 +187,7 @@ __device__ __forceinline__ cplx<T> helm_diag_h2(const LevelDesc& d, int i, int j
     T re = T(4) - kh * kh;
     T im = T(0);
     if (d.bc == BC_ABC1) {
-        int m = (i == 0) + (i == d.n - 1) + (j == 0) + (j == d.n - 1);
+        int m = (i == 0) + (i == d.n - 1) + (j == 0) + (j == d.ny - 1);
         re -= (T)m;
         im -= (T)m * kh;
     } else if (d.bc == BC_SPONGE) {

@@ -123,8 +123,8 @@ struct Engine : EngineBase {
         for (int rh : {16, 24, 32, 64}) {
             long long units = 0;   // over the launch's instances
             for (int q : ds) {
-                const int n = H.hdesc[(size_t)q].n;
-                units += (long long)((n + SO - 1) / SO) * ((n + rh - 1) / rh);
+                const int n = H.hdesc[(size_t)q].n, ny = H.hdesc[(size_t)q].ny;
+                units += (long long)((n + SO - 1) / SO) * ((ny + rh - 1) / rh);
             }
             const long long cost = (units + warps - 1) / warps * (rh + 2 * NS);
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
@@ -192,8 +192,8 @@ struct Engine : EngineBase {
             if (cm_smem<T>(ts, q) > optin - 1024) continue;
             long long tiles = 0;
             for (int qd : ds) {
-                const int n = H.hdesc[(size_t)qd].n;
-                tiles += (long long)((n + ts - 1) / ts) * ((n + ts - 1) / ts);
+                const int n = H.hdesc[(size_t)qd].n, ny = H.hdesc[(size_t)qd].ny;
+                tiles += (long long)((n + ts - 1) / ts) * ((ny + ts - 1) / ts);
             }
             if (tiles >= 128 || ts == 8) return ts;
         }
@@ -228,8 +228,8 @@ struct Engine : EngineBase {
         for (int rh : {8, 16, 32}) {
             long long units = 0;
             for (int q : ds) {
-                const int n = H.hdesc[(size_t)q].n, nc = (n - 1) / 2;
-                units += (long long)((n + RS_SO - 1) / RS_SO) * ((nc + rh - 1) / rh);
+                const int n = H.hdesc[(size_t)q].n, ncy = (H.hdesc[(size_t)q].ny - 1) / 2;
+                units += (long long)((n + RS_SO - 1) / RS_SO) * ((ncy + rh - 1) / rh);
             }
             const long long cost = (units + warps - 1) / warps * (2 * rh + 3);
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
@@ -250,7 +250,7 @@ struct Engine : EngineBase {
             long long pts = 0;
             bool hs = false;
             for (int q : ds) {
-                pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+                pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].ny;
                 hs = hs || H.hdesc[(size_t)q].sig != nullptr;
             }
             if (pts < CS_MIN_POINTS) return false;
@@ -275,8 +275,8 @@ struct Engine : EngineBase {
         for (int rh : {16, 32, 64}) {
             long long units = 0;
             for (int q : ds) {
-                const int n = H.hdesc[(size_t)q].n;
-                units += (long long)((n + SO - 1) / SO) * ((n + rh - 1) / rh);
+                const int n = H.hdesc[(size_t)q].n, ny = H.hdesc[(size_t)q].ny;
+                units += (long long)((n + SO - 1) / SO) * ((ny + rh - 1) / rh);
             }
             const long long cost = (units + warps - 1) / warps * (rh + (FG ? 4 : 2));
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
@@ -299,7 +299,7 @@ struct Engine : EngineBase {
             long long pts = 0;
             bool hs = false;
             for (int q : ds) {
-                pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+                pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].ny;
                 hs = hs || H.hdesc[(size_t)q].sig != nullptr;
             }
             if (pts < CS_MIN_POINTS) return false;
@@ -322,7 +322,7 @@ struct Engine : EngineBase {
     static bool level1_streams(Handle& H, const std::vector<int>& ds1) {
         if (!kStream) return false;
         long long pts = 0;
-        for (int q : ds1) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+        for (int q : ds1) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].ny;
         return pts >= CS_MIN_POINTS;
     }
     template <int MODE>
@@ -369,23 +369,24 @@ struct Engine : EngineBase {
             InstHost& I = H.inst[b];
             for (int l = 1; l <= I.L; ++l) {
                 LevelHost& lv = I.lv[l - 1];
-                dim3 bb(32, 8), gg((lv.n + 31) / 32, (lv.n + 7) / 8);
-                k_fields<T><<<gg, bb, 0, st>>>(lv.k64, lv.sig64, lv.n, lv.pitch, (T*)lv.kf, (T*)lv.sig);
+                dim3 bb(32, 8), gg((lv.n + 31) / 32, (lv.ny + 7) / 8);
+                k_fields<T><<<gg, bb, 0, st>>>(lv.k64, lv.sig64, lv.n, lv.ny, lv.pitch, (T*)lv.kf, (T*)lv.sig);
                 if (lv.adr)
-                    k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega,
-                                                      I.bc, H.p.shift, I.adr_flags, (quad<T>*)lv.adr);
+                    k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h,
+                                                      I.omega, I.bc, H.p.shift, I.adr_flags, (quad<T>*)lv.adr);
                 if (lv.mod)
-                    k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.pitch, I.omega, (cplx<T>*)lv.mod);
+                    k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.ny, lv.pitch, I.omega, (cplx<T>*)lv.mod);
             }
             // Wave-Ray corrections 2..M: their own ADR quads and modulation
             for (auto& vl : I.rv)
                 for (int l = 2; l <= I.L; ++l) {
                     LevelHost& lv = vl[l - 1];
-                    dim3 bb(32, 8), gg((lv.n + 31) / 32, (lv.n + 7) / 8);
-                    k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega,
-                                                      I.bc, H.p.shift, I.adr_flags, (quad<T>*)lv.adr);
+                    dim3 bb(32, 8), gg((lv.n + 31) / 32, (lv.ny + 7) / 8);
+                    k_adr_fields<T><<<gg, bb, 0, st>>>(lv.phi64, lv.k64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h,
+                                                      I.omega, I.bc, H.p.shift, I.adr_flags, (quad<T>*)lv.adr);
                     if (lv.mod)
-                        k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.pitch, I.omega, (cplx<T>*)lv.mod);
+                        k_mod_field<T><<<gg, bb, 0, st>>>(lv.phi64, lv.n, lv.ny, lv.pitch, I.omega,
+                                                         (cplx<T>*)lv.mod);
                 }
         }
         return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ECUDA;
@@ -402,7 +403,7 @@ struct Engine : EngineBase {
     static bool cheb_stream_on(Handle& H, const std::vector<int>& ds, int l) {
         if (!kStream || l < 2) return false;
         long long pts = 0;
-        for (int q : ds) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].n;
+        for (int q : ds) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].ny;
         return pts >= CS_MIN_POINTS;
     }
     // launches that q steps take on level l (the small FP32 levels run all q

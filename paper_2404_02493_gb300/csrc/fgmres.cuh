@@ -96,14 +96,14 @@ __global__ void __launch_bounds__(NT) k_fg_start(const __grid_constant__ KDesc A
                                                  int nseg) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const double2* r = slot<double>(d, SD);
     cplx<TC>* v0 = kvec<TC>(d, 0);
     const double sc = scalp<double>(d)[S::SCALE];
     const TC inv = (TC)(sc > 0 ? 1.0 / sc : 0.0);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         const double2 rv = __ldg(r + p);
         v0[p] = mk<TC>((TC)rv.x * inv, (TC)rv.y * inv);
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(NT) k_fg_prep(const __grid_constant__ KDesc A,
                                                 int nseg) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const int jj = (int)d.fs[FS::J];
     cplx<TC>* v = kvec<TC>(d, jj);
     cplx<TC>* g = xslot<TC>(d, SG);
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_fg_prep(const __grid_constant__ KDesc A,
     const TC inv = (TC)(hn > 0 ? 1.0 / hn : 0.0);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         cplx<TC> x = v[p];
         if (jj > 0) {
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const __grid_constant__ KDesc 
                                                   int nseg) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const int jj = (int)d.fs[FS::J];
     const cplx<TC>* z = xslot<TC>(d, SD);
     cplx<TC>* zj = zvec<TC>(d, jj);
@@ -161,10 +161,10 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const __grid_constant__ KDesc 
     const TC* sg = reinterpret_cast<const TC*>(d.xsig);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         const cplx<TC> zc = __ldg(z + p);
-        const cplx<TC> s = nbr_sum<TC>(z, d.n, d.pitch, i, j, p);
+        const cplx<TC> s = nbr_sum<TC>(z, d.n, d.ny, d.pitch, i, j, p);
         const cplx<TC> dg = helm_diag_h2<TC>(d, i, j, __ldg(kf + p), sg ? __ldg(sg + p) : TC(0));
         zj[p] = zc;
         w[p] = cscale<TC>(csub<TC>(cmul<TC>(dg, zc), s), ih2);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT) k_fg_matvec(const __grid_constant__ KDesc 
 }
 
 // Gram-Schmidt passes of FGMRES over the level-1 vectors.  The padded
-// vectors are contiguous (pitch * n values, zero in the row padding), so a
+// vectors are contiguous (pitch * ny values, zero in the row padding), so a
 // pass treats them as flat arrays cut into chunks: for each chunk the block
 // streams W and V_0..V_j in by 1D bulk copies into one stage of a ring of
 // shared-memory stages (the copies of the next chunks are in flight while
@@ -245,7 +245,7 @@ template <typename TC, class Body>
 __device__ __forceinline__ bool fg_stream(const LevelDesc& d, const SegCtx& c, int jj, const cplx<TC>* w,
                                           cplx<TC>* stg0, FgGeom g, uint64_t* bars, Body&& body) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const long long N = (long long)d.n * d.pitch;
+    const long long N = (long long)d.ny * d.pitch;
     const int PJ = (MAXR + 1) * g.pw / (jj + 2) / 32 * 32;
     const long long nchunks = (N + PJ - 1) / PJ;
     const int nmine = c.lb < nchunks ? (int)((nchunks - 1 - c.lb) / c.nb + 1) : 0;
@@ -640,11 +640,11 @@ __global__ void __launch_bounds__(NT) k_fg_update(const __grid_constant__ KDesc 
     cplx<TC> yq[MAXR];
 #pragma unroll
     for (int q = 0; q < MAXR; ++q) yq[q] = q < m ? from_d<TC>(ysh[q]) : zero2<TC>();
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     double2* u = slot<double>(d, SU);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         // e = Z y accumulated in the cycle precision over <= 22 terms,
         // then added to the FP64 solution

@@ -128,7 +128,7 @@ __device__ __forceinline__ cplx<T> sl_q(const quad<T>& q, const cplx<T>* __restr
 // WO + 2 from (ox - 1, oy - 1) and coefficients Q of stride WQ from
 // (ox - QO, oy - QO); zero outside the grid.
 template <typename T, int WO, int HO, int WQ, int QO>
-__device__ __forceinline__ void sl_stage(int n, const cplx<T>* __restrict__ Sin, cplx<T>* __restrict__ Sout,
+__device__ __forceinline__ void sl_stage(int n, int ny, const cplx<T>* __restrict__ Sin, cplx<T>* __restrict__ Sout,
                                          const quad<T>* __restrict__ Q, int ox, int oy, T ih2, T wh, T s) {
     constexpr int WI = WO + 2, NE = WO * HO;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void sl_stage(int n, const cplx<T>* __restrict__ Sin,
             const int r = e / WO, cc = e - r * WO;
             const int gi = ox + cc, gj = oy + r;
             cplx<T> v = zero2<T>();
-            if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n)
+            if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny)
                 v = sl_q<T>(Q[(r + QO) * WQ + cc + QO], Sin, (r + 1) * WI + cc + 1, WI, ih2, wh, s);
             Sout[e] = v;
         }
@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(NT) k_gs_gram_tile(const __grid_constant__ KDe
     __shared__ int flag;
     SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + TX - 1) / TX, ntiles = ntx * ((n + TY - 1) / TY);
+    const int n = d.n, ny = d.ny, pitch = d.pitch;
+    const int ntx = (n + TX - 1) / TX, ntiles = ntx * ((ny + TY - 1) / TY);
     const cplx<T>* r0 = slot<T>(d, sr0);
     cplx<T>* k1o = slot<T>(d, SK1);
     cplx<T>* k2o = slot<T>(d, SK2);
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(NT) k_gs_gram_tile(const __grid_constant__ KDe
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
     auto issue = [&](int t, int b) {
         const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-        async_region<cplx<T>, W0, H0>(S0b + b * W0 * H0, r0, n, pitch, x0 - 3, y0 - 3);
-        async_region<quad<T>, W1, H1>(Qb + b * W1 * H1, coef, n, pitch, x0 - 2, y0 - 2);
+        async_region<cplx<T>, W0, H0>(S0b + b * W0 * H0, r0, n, ny, pitch, x0 - 3, y0 - 3);
+        async_region<quad<T>, W1, H1>(Qb + b * W1 * H1, coef, n, ny, pitch, x0 - 2, y0 - 2);
     };
     GramAcc<T> ac;
     ac.zero();
@@ -261,15 +261,15 @@ __global__ void __launch_bounds__(NT) k_gs_gram_tile(const __grid_constant__ KDe
         const cplx<T>* S0 = S0b + buf * W0 * H0;
         const quad<T>* Q = Qb + buf * W1 * H1;
         const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-        sl_stage<T, W1, H1, W1, 0>(n, S0, S1, Q, x0 - 2, y0 - 2, ih2, wh, s);
+        sl_stage<T, W1, H1, W1, 0>(n, ny, S0, S1, Q, x0 - 2, y0 - 2, ih2, wh, s);
         __syncthreads();
-        sl_stage<T, W2, H2, W1, 1>(n, S1, S2, Q, x0 - 1, y0 - 1, ih2, wh, s);
+        sl_stage<T, W2, H2, W1, 1>(n, ny, S1, S2, Q, x0 - 1, y0 - 1, ih2, wh, s);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < TX * TY / NT; ++k) {
             const int e = tid + k * NT;
             const int r = e / TX, cc = e - r * TX;
-            if (x0 + cc < n && y0 + r < n) {
+            if (x0 + cc < n && y0 + r < ny) {
                 const int b2 = (r + 1) * W2 + cc + 1;
                 const cplx<T> k0 = S0[(r + 3) * W0 + cc + 3], k1 = S1[(r + 2) * W1 + cc + 2], k2 = S2[b2];
                 const cplx<T> k3 = sl_q<T>(Q[(r + 2) * W1 + cc + 2], S2, b2, W2, ih2, wh, s);
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_con
     __shared__ cplx<T> sh[8 * 8];
     __shared__ int flag;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int n = d.n, pitch = d.pitch;
-    const int nstrips = (n + SW_OUT - 1) / SW_OUT, nunits = nstrips * ((n + RH - 1) / RH);
+    const int n = d.n, ny = d.ny, pitch = d.pitch;
+    const int nstrips = (n + SW_OUT - 1) / SW_OUT, nunits = nstrips * ((ny + RH - 1) / RH);
     const cplx<T>* r0 = slot<T>(d, sr0);
     cplx<T>* k1o = slot<T>(d, SK1);
     cplx<T>* k2o = slot<T>(d, SK2);
@@ -314,14 +314,14 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_con
     GramAcc<T> ac;
     ac.zero();
     for (int u = c.lb * GS_WPB + warp; u < nunits; u += c.nb * GS_WPB) {
-        const StripGeo gg = strip_geo(u, nstrips, RH, n);
+        const StripGeo gg = strip_geo(u, nstrips, RH, ny);
         const int j0 = gg.y0 - 3, j1 = gg.y1 + 2;
         const int col = gg.X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const bool own = lane >= 2 && lane < 30;
         auto issue = [&](int r) {
-            ring_issue<cplx<T>>(Kr, r0, n, pitch, gg.X0, r, lane);
-            ring_issue<quad<T>>(Qr, coef, n, pitch, gg.X0, r, lane);
+            ring_issue<cplx<T>>(Kr, r0, n, ny, pitch, gg.X0, r, lane);
+            ring_issue<quad<T>>(Qr, coef, n, ny, pitch, gg.X0, r, lane);
         };
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -338,10 +338,10 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_con
             ring_read<cplx<T>>(Kr, j, lane, a3.v0, a3.v1);
             quad<T> q0, q1;
             ring_read<quad<T>>(Qr, j - 1, lane, q0, q1);
-            const bool r1 = (unsigned)(j - 1) < (unsigned)n;
+            const bool r1 = (unsigned)(j - 1) < (unsigned)ny;
             const P2<T> k1 = sl_row<T>(q0, q1, a2, a1, a3, ih2, wh, s, r1 && cin0, r1 && cin1);
             ring_read<quad<T>>(Qr, j - 2, lane, q0, q1);
-            const bool r2 = (unsigned)(j - 2) < (unsigned)n;
+            const bool r2 = (unsigned)(j - 2) < (unsigned)ny;
             const P2<T> k2 = sl_row<T>(q0, q1, b1, b0, k1, ih2, wh, s, r2 && cin0, r2 && cin1);
             ring_read<quad<T>>(Qr, j - 3, lane, q0, q1);
             const bool r3 = j - 3 >= gg.y0 && j - 3 < gg.y1;
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const __grid_constant__ KDesc A, 
     coarse_desc(A, nseg, d, dc, tid);
     TmaPipe pipe;
     pipe.init(bars);
-    const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
-    const int ntx = (nc + CX - 1) / CX, ntiles = ntx * ((nc + CY - 1) / CY);
+    const int n = d.n, ny = d.ny, pitch = d.pitch, nc = dc.n, ncy = dc.ny, cpitch = dc.pitch;
+    const int ntx = (nc + CX - 1) / CX, ntiles = ntx * ((ncy + CY - 1) / CY);
     cplx<T>* xs = slot<T>(d, sx);
     cplx<T>* out = slot<T>(dc, sc);
     const T ih2 = LC<T>::ih2(d), wh = LC<T>::wh(d), s = LC<T>::gs(d);
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const __grid_constant__ KDesc A, 
         const int fx0 = 2 * I0, fy0 = 2 * J0;
         // fine nodes this tile writes (the last tile in a direction takes the rest)
         const int ox1 = (I0 + CX >= nc) ? n : 2 * (I0 + CX);
-        const int oy1 = (J0 + CY >= nc) ? n : 2 * (J0 + CY);
+        const int oy1 = (J0 + CY >= ncy) ? ny : 2 * (J0 + CY);
 #pragma unroll
         for (int k = 0; k < (NF + NT - 1) / NT; ++k) {
             const int e = tid + k * NT;
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const __grid_constant__ KDesc A, 
                 const int r = e / FW, cc = e - r * FW;
                 const int gi = fx0 + cc, gj = fy0 + r;
                 cplx<T> v = zero2<T>();
-                if (gi < n && gj < n) {
+                if (gi < n && gj < ny) {
                     const int b2 = (r + 1) * KW + cc + 2, a = r * AW + cc;
                     const cplx<T> k0 = K0s[a], k1 = K1s[a], k2 = K2s[b2];
                     const cplx<T> k3 = sl_q<T>(Q[e], K2s, b2, KW, ih2, wh, s);
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(NT) k_gs_pre(const __grid_constant__ KDesc A, 
             if (e < CX * CY) {
                 const int ty = e / CX, tx = e - ty * CX;
                 const int I = I0 + tx, J = J0 + ty;
-                if (I < nc && J < nc) {
+                if (I < nc && J < ncy) {
                     const int b = (2 * ty + 1) * FW + 2 * tx + 1;
                     const cplx<T> s4 = R[b];
                     const cplx<T> s2 = cadd<T>(cadd<T>(R[b - 1], R[b + 1]), cadd<T>(R[b - FW], R[b + FW]));
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(NT) k_gs_post(const __grid_constant__ KDesc A,
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = n * npr;
+    const int n = d.n, pitch = d.pitch, npr = (n + 1) / 2, npairs = d.ny * npr;
     const cplx<T>* k0 = slot<T>(d, sr0);
     const cplx<T>* k1 = slot<T>(d, SK1);
     const cplx<T>* k2 = slot<T>(d, SK2);

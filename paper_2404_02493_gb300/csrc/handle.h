@@ -16,7 +16,8 @@ constexpr int MAXB = 2048;          // partial-sum capacity (blocks per segment)
 constexpr int MAX_LEVELS = 16;
 
 struct LevelHost {
-    int n = 0, pitch = 0;
+    int n = 0, pitch = 0;           // nodes per row, row pitch (elements)
+    int ny = 0;                     // rows
     double h = 0;
     size_t slot_stride = 0;         // elements
     int nslot = 0;
@@ -37,7 +38,7 @@ struct LevelHost {
 };
 
 struct InstHost {
-    int n = 0, L = 0, bc = 0;
+    int n = 0, ny = 0, L = 0, bc = 0;   // fine grid: n nodes per row, ny rows
     int adr_flags = 0;              // ADR_ABC | ADR_DISC options of the ADR coefficients (see adr_coef_at)
     double omega = 0;
     double omega_j = 0;
@@ -58,8 +59,8 @@ struct SegTable {
     Seg* d = nullptr;
     int nseg = 0, nblocks = 0;     // nseg < 0: a single segment, descriptor -nseg - 1
     bool outer = false;            // descriptors of the outer (FP64) table
-    long long pts = 0;     // sum of n^2 over the segments
-    long long mat = 0;     // sum of (n^2)^2 (dense coarsest matrices)
+    long long pts = 0;     // sum of n ny over the segments
+    long long mat = 0;     // sum of (n ny)^2 (dense coarsest matrices)
 };
 
 // kernel kinds for the event profiler (names in kernel_kind_name)
@@ -101,7 +102,7 @@ struct Handle {
     std::vector<void*> allocs;      // everything cudaMalloc'ed
     size_t alloc_bytes = 0;         // their total size
     long long alloc_limit = 0;      // mg_params.workspace_limit (0: none)
-    long long total_elems = 0;      // sum of n^2 over instances
+    long long total_elems = 0;      // sum of n ny over instances
     // graphs
     cudaGraphExec_t g_cycle0 = nullptr;     // cycle from u = 0 (level-1 SG -> SD)
     cudaGraphExec_t g_irstep = nullptr;     // scale + cycle + update + residual
@@ -162,19 +163,23 @@ EngineBase* make_engine_f32();
 EngineBase* make_engine_f64();
 
 // setup helpers shared by the engines (setup.cu)
-void setup_plane_phase(double* phi64, int n, int pitch, double h1, int scale, double cx, double cy, cudaStream_t st);
-void setup_inject(const double* k_fine, const double* phi_fine, int n1, double omega, int bc, int level,
-                  double* k64, double* phi64, double* sig64, int n, int pitch, cudaStream_t st);
-double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
-                        double* dscratch, cudaStream_t st);
-double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                       double omega, int bc, double shift, int adr_flags, double* dscratch, cudaStream_t st);
-int setup_check_fields(const double* k, const double* phi, int n, double* dscratch, long long* bad_k,
+// (n nodes per row, ny rows, row pitch `pitch`)
+void setup_plane_phase(double* phi64, int n, int ny, int pitch, double h1, int scale, double cx, double cy,
+                       cudaStream_t st);
+void setup_inject(const double* k_fine, const double* phi_fine, int n1, int ny1, double omega, int bc, int level,
+                  double* k64, double* phi64, double* sig64, int n, int ny, int pitch, cudaStream_t st);
+double setup_lambda_max(const double* k64, const double* sig64, int n, int ny, int pitch, double h, int bc,
+                        double shift, double* dscratch, cudaStream_t st);
+double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
+                       double h, double omega, int bc, double shift, int adr_flags, double* dscratch,
+                       cudaStream_t st);
+int setup_check_fields(const double* k, const double* phi, int n, int ny, double* dscratch, long long* bad_k,
                        long long* bad_phi, cudaStream_t st);
-double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch, double h,
                     double omega, int bc, double* dscratch, cudaStream_t st);
-int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, double shift, int which, int adr_flags, double2* inv, cudaStream_t st);
+int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
+                         double h, double omega, int bc, double shift, int which, int adr_flags, double2* inv,
+                         cudaStream_t st);
 
 #define WADR_CHECK(x)                                                                   \
     do {                                                                                \

@@ -74,13 +74,13 @@ __device__ __forceinline__ SegCtx seg_begin(const KDesc& A, const Seg* __restric
 
 // ----------------------------------------------------------- point stencils
 template <typename T>
-__device__ __forceinline__ cplx<T> nbr_sum(const cplx<T>* __restrict__ u, int n, int pitch, int i, int j,
+__device__ __forceinline__ cplx<T> nbr_sum(const cplx<T>* __restrict__ u, int n, int ny, int pitch, int i, int j,
                                            long long p) {
     cplx<T> s = zero2<T>();
     if (i > 0) s = cadd<T>(s, __ldg(u + p - 1));
     if (i < n - 1) s = cadd<T>(s, __ldg(u + p + 1));
     if (j > 0) s = cadd<T>(s, __ldg(u + p - pitch));
-    if (j < n - 1) s = cadd<T>(s, __ldg(u + p + pitch));
+    if (j < ny - 1) s = cadd<T>(s, __ldg(u + p + pitch));
     return s;
 }
 
@@ -91,7 +91,7 @@ __device__ __forceinline__ cplx<T> helm_apply_pt(const LevelDesc& d, const cplx<
     const long long p = (long long)j * d.pitch + i;
     cplx<T> dg = helm_diag_at<T>(d, i, j);
     if (HERM) dg.y = -dg.y;
-    const cplx<T> s = nbr_sum<T>(u, d.n, d.pitch, i, j, p);
+    const cplx<T> s = nbr_sum<T>(u, d.n, d.ny, d.pitch, i, j, p);
     const cplx<T> c = __ldg(u + p);
     const T ih2 = LC<T>::ih2(d);
     return cscale<T>(csub<T>(cmul<T>(dg, c), s), ih2);
@@ -147,7 +147,7 @@ __device__ __forceinline__ cplx<T> adr_apply_pt(const LevelDesc& d, const cplx<T
     cplx<T> w = i > 0 ? __ldg(u + p - 1) : z;
     cplx<T> e = i < n - 1 ? __ldg(u + p + 1) : z;
     cplx<T> s = j > 0 ? __ldg(u + p - d.pitch) : z;
-    cplx<T> nn = j < n - 1 ? __ldg(u + p + d.pitch) : z;
+    cplx<T> nn = j < d.ny - 1 ? __ldg(u + p + d.pitch) : z;
     return adr_pt<T>(load_adr<T>(d, p), LC<T>::ih2(d), LC<T>::wh(d), __ldg(u + p), w, e, s, nn);
 }
 
@@ -171,7 +171,7 @@ __device__ __forceinline__ cplx<T> adr_apply_t_pt(const LevelDesc& d, const cplx
     };
     if (i < n - 1) { quad<T> q = load_adr<T>(d, p + 1); add(p + 1, T(2) * fmax(q.x, T(0))); }        // E nbr's W coef
     if (i > 0) { quad<T> q = load_adr<T>(d, p - 1); add(p - 1, T(-2) * fmin(q.x, T(0))); }           // W nbr's E coef
-    if (j < n - 1) { quad<T> q = load_adr<T>(d, p + d.pitch); add(p + d.pitch, T(2) * fmax(q.y, T(0))); }  // N nbr's S
+    if (j < d.ny - 1) { quad<T> q = load_adr<T>(d, p + d.pitch); add(p + d.pitch, T(2) * fmax(q.y, T(0))); }  // N nbr's S
     if (j > 0) { quad<T> q = load_adr<T>(d, p - d.pitch); add(p - d.pitch, T(-2) * fmin(q.y, T(0))); }     // S nbr's N
     if (CONJ) r.y = -r.y;
     return r;
@@ -184,12 +184,12 @@ __global__ void __launch_bounds__(NT) k_apply(const __grid_constant__ KDesc A, c
                                               int nseg, int op, int sx, int sy) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const cplx<T>* x = slot<T>(d, sx);
     cplx<T>* y = slot<T>(d, sy);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         cplx<T> r;
         if (op == 0) r = helm_apply_pt<T, false>(d, x, i, j);
         else if (op == 1) r = helm_apply_pt<T, true>(d, x, i, j);
@@ -206,13 +206,13 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ KDesc A
                                                  int nseg, int su, int sg, int sr, int uzero) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const cplx<T>* u = slot<T>(d, su);
     const cplx<T>* g = slot<T>(d, sg);
     cplx<T>* r = slot<T>(d, sr);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         cplx<T> v = __ldg(g + p);
         if (!uzero) v = csub<T>(v, helm_apply_pt<T, false>(d, u, i, j));
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const __grid_constant__ KDesc A, 
                                                int nseg, int su, int sg, int sout, int uzero) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const cplx<T>* u = slot<T>(d, su);
     const cplx<T>* g = slot<T>(d, sg);
     cplx<T>* o = slot<T>(d, sout);
@@ -234,13 +234,13 @@ __global__ void __launch_bounds__(NT) k_jacobi(const __grid_constant__ KDesc A, 
     const T ih2 = LC<T>::ih2(d), h2 = LC<T>::h(d) * LC<T>::h(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         cplx<T> dg = helm_diag_at<T>(d, i, j);
         cplx<T> rr = __ldg(g + p);
         cplx<T> uc = uzero ? zero2<T>() : __ldg(u + p);
         if (!uzero) {
-            cplx<T> s = nbr_sum<T>(u, d.n, d.pitch, i, j, p);
+            cplx<T> s = nbr_sum<T>(u, d.n, d.ny, d.pitch, i, j, p);
             rr = csub<T>(rr, cscale<T>(csub<T>(cmul<T>(dg, uc), s), ih2));
         }
         // D = dg / h^2  ->  D^{-1} rr = h^2 rr / dg
@@ -254,13 +254,13 @@ __global__ void __launch_bounds__(NT) k_jacobi(const __grid_constant__ KDesc A, 
 // Load rows [y0, y0+H) x cols [x0, x0+W) of a grid vector into sm (row
 // stride W); zero outside the grid.
 template <typename T>
-__device__ __forceinline__ void load_region(cplx<T>* sm, const cplx<T>* __restrict__ p, int n, int pitch, int x0,
-                                            int y0, int W, int H) {
+__device__ __forceinline__ void load_region(cplx<T>* sm, const cplx<T>* __restrict__ p, int n, int ny, int pitch,
+                                            int x0, int y0, int W, int H) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     for (int e = tid; e < W * H; e += NT) {
         const int r = e / W, cc = e - r * W;
         const int gi = x0 + cc, gj = y0 + r;
-        sm[e] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? __ldg(p + (long long)gj * pitch + gi) : zero2<T>();
+        sm[e] = (gi >= 0 && gi < n && gj >= 0 && gj < ny) ? __ldg(p + (long long)gj * pitch + gi) : zero2<T>();
     }
 }
 
@@ -305,10 +305,11 @@ __device__ __forceinline__ void cp_async_elem(E* sdst, const E* gsrc, bool ok) {
     }
 }
 
-// Issue the copies of rows [y0, y0+H) x cols [x0, x0+W) of an n x n grid
-// array (row pitch `pitch`) into sm (row stride W).
+// Issue the copies of rows [y0, y0+H) x cols [x0, x0+W) of a grid array of ny
+// rows of n (row pitch `pitch`) into sm (row stride W).
 template <typename E, int W, int H>
-__device__ __forceinline__ void async_region(E* sm, const E* __restrict__ g, int n, int pitch, int x0, int y0) {
+__device__ __forceinline__ void async_region(E* sm, const E* __restrict__ g, int n, int ny, int pitch, int x0,
+                                             int y0) {
     constexpr int NE = W * H;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
 #pragma unroll
@@ -317,7 +318,7 @@ __device__ __forceinline__ void async_region(E* sm, const E* __restrict__ g, int
         if (NE % NT == 0 || e < NE) {
             const int r = e / W, cc = e - r * W;
             const int gi = x0 + cc, gj = y0 + r;
-            const bool ok = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n;
+            const bool ok = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny;
             cp_async_elem<E>(sm + e, ok ? g + (long long)gj * pitch + gi : g, ok);
         }
     }
@@ -403,8 +404,8 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const __grid_constant__ KDesc 
     TmaPipe pipe;
     pipe.init(bars);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + CTX - 1) / CTX, ntiles = ntx * ((n + CTY - 1) / CTY);
+    const int n = d.n, ny = d.ny, pitch = d.pitch;
+    const int ntx = (n + CTX - 1) / CTX, ntiles = ntx * ((ny + CTY - 1) / CTY);
     cplx<T>* xo_ = slot<T>(d, sxout);
     cplx<T>* dd = slot<T>(d, SD);
     const bool hs = d.sig != nullptr;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const __grid_constant__ KDesc 
                 const int r = e / CRW, cc = e - r * CRW;
                 const int gi = x0 - 1 + cc, gj = y0 - 1 + r;
                 cplx<T> tv = zero2<T>();
-                if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+                if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny) {
                     tv = bufp(G0, buf, BUFB)[r * CGW + cc + 1];
                     if (!xzero) {
                         const int q = (r + 1) * CXW + cc + 1;
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const __grid_constant__ KDesc 
             const int e = tid + k * NT;
             const int r = e / CTX, cc = e - r * CTX;
             const int gi = x0 + cc, gj = y0 + r;
-            if (gi < n && gj < n) {
+            if (gi < n && gj < ny) {
                 const int q = (r + 1) * CRW + cc + 1;
                 const cplx<T> sn = cadd<T>(cadd<T>(Tt[q - 1], Tt[q + 1]), cadd<T>(Tt[q - CRW], Tt[q + CRW]));
                 const int qk = (r + 1) * CKW + cc + 4;
@@ -525,8 +526,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const _
     coarse_desc(A, nseg, d, dc, tid);
     TmaPipe pipe;
     pipe.init(bars);
-    const int n = d.n, pitch = d.pitch, nc = dc.n;
-    const int ntx = (nc + RCX - 1) / RCX, ntiles = ntx * ((nc + RCY - 1) / RCY);
+    const int n = d.n, ny = d.ny, pitch = d.pitch, nc = dc.n, ncy = dc.ny;
+    const int ntx = (nc + RCX - 1) / RCX, ntiles = ntx * ((ncy + RCY - 1) / RCY);
     const T ih2 = LC<T>::ih2(d);
     cplx<T>* xs = slot<T>(d, sx);
     cplx<T>* out = slot<T>(dc, sc);
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const _
         const int fx0 = 2 * I0, fy0 = 2 * J0;
         // own fine rows/cols for writes of the fine iterate
         const int ox1 = (I0 + RCX >= nc) ? n : 2 * (I0 + RCX);
-        const int oy1 = (J0 + RCY >= nc) ? n : 2 * (J0 + RCY);
+        const int oy1 = (J0 + RCY >= ncy) ? ny : 2 * (J0 + RCY);
         // ring node (r, cc) (origin fx0-1, fy0-1): complex box (r, cc+1), real box (r, cc+3)
         const cplx<T>* X = bufp(X0, buf, BUFB);
         int xw = RXW, xo = 1;
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const _
                     const int r = e / RHW, cc = e - r * RHW;
                     const int gi = fx0 - 1 + cc, gj = fy0 - 1 + r;
                     cplx<T> v = zero2<T>();
-                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n) {
+                    if ((unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny) {
                         const cplx<T> gv = Bv[r * RXW + cc + 1];
                         const int qk = r * RKW + cc + 3;
                         const cplx<T> dg = helm_diag_h2<T>(d, gi, gj, K[qk], hs ? Sg2[qk] : T(0));
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const _
                 const int r = e / RFW, cc = e - r * RFW;
                 const int gi = fx0 + cc, gj = fy0 + r;
                 cplx<T> v = zero2<T>();
-                if (gi < n && gj < n) {
+                if (gi < n && gj < ny) {
                     v = Bv[(r + 1) * RXW + cc + 2];
                     if (needk) {
                         const int q = (r + 1) * xw + cc + 1 + xo;
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_restrict(const _
             const int e = tid + k * NT;
             const int ty = e / RCX, tx = e - ty * RCX;
             const int I = I0 + tx, J = J0 + ty;
-            if (I < nc && J < nc) {
+            if (I < nc && J < ncy) {
                 const int q = (2 * ty + 1) * RFW + 2 * tx + 1;
                 const cplx<T> s4 = R[q];
                 const cplx<T> s2 = cadd<T>(cadd<T>(R[q - 1], R[q + 1]), cadd<T>(R[q - RFW], R[q + RFW]));
@@ -704,8 +705,8 @@ __global__ void __launch_bounds__(NT) k_prolong(const __grid_constant__ KDesc A,
     coarse_desc(A, nseg, d, dc, tid);
     TmaPipe pipe;
     pipe.init(bars);
-    const int n = d.n, pitch = d.pitch;
-    const int ntx = (n + PTX - 1) / PTX, ntiles = ntx * ((n + PTY - 1) / PTY);
+    const int n = d.n, ny = d.ny, pitch = d.pitch;
+    const int ntx = (n + PTX - 1) / PTX, ntiles = ntx * ((ny + PTY - 1) / PTY);
     cplx<T>* os = slot<T>(d, sout);
     cplx<T>* xo = slot<T>(d, sxo);
     const bool hs = d.sig != nullptr;
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(NT) k_prolong(const __grid_constant__ KDesc A,
                 const int r = e / XW, cc = e - r * XW;
                 const int gi = x0 - HAL + cc, gj = y0 - HAL + r;
                 cplx<T> v = zero2<T>();
-                const bool in = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)n;
+                const bool in = (unsigned)gi < (unsigned)n && (unsigned)gj < (unsigned)ny;
                 if (in) {
                     // bilinear weights without branches: coarse node (gi-1) >> 1 and the next one
                     // get (1, 0) for odd gi (coincident node) and (1/2, 1/2) for even gi
@@ -805,7 +806,7 @@ __global__ void __launch_bounds__(NT) k_prolong(const __grid_constant__ KDesc A,
                 const int e = tid + k * NT;
                 const int r = e / PTX, cc = e - r * PTX;
                 const int gi = x0 + cc, gj = y0 + r;
-                if (gi < n && gj < n) {
+                if (gi < n && gj < ny) {
                     const long long p = (long long)gj * pitch + gi;
                     const int q = (r + 1) * XW + cc + 1;
                     if (MODE == PMODE_JAC) {
@@ -836,14 +837,14 @@ __global__ void __launch_bounds__(NT) k_resdemod(const __grid_constant__ KDesc A
                                                  int nseg, int /*unused*/) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const cplx<T>* u = slot<T>(d, SU);
     const cplx<T>* g = slot<T>(d, SG);
     cplx<T>* b = slot<T>(d, SAB);
     const cplx<T>* mod = reinterpret_cast<const cplx<T>*>(d.mod);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         cplx<T> r = csub<T>(__ldg(g + p), helm_apply_pt<T, false>(d, u, i, j));
         b[p] = cmulc<T>(__ldg(mod + p), r);
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(NT) k_coarse(const __grid_constant__ KDesc A, 
     __shared__ double2 bsh[MAXCOARSE];
     SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int n = d.n, N = n * n;
+    const int n = d.n, N = n * d.ny;
     const cplx<T>* b = slot<T>(d, which ? SAB : SG);
     cplx<T>* x = slot<T>(d, which ? SAX : SU);
     const double2* Ainv = which ? d.inv_adr : d.inv_helm;
@@ -922,7 +923,7 @@ __global__ void __launch_bounds__(NT) k_outer_residual(const __grid_constant__ K
     __shared__ double2 sh[8 * 2];
     __shared__ int flag;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const double2* u = slot<double>(d, SU);
     const double2* g = slot<double>(d, SG);
     double2* r = slot<double>(d, SD);
@@ -930,7 +931,7 @@ __global__ void __launch_bounds__(NT) k_outer_residual(const __grid_constant__ K
     double* sc = scalp<double>(d);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         double2 gv = __ldg(g + p);
         double2 v = dsub(gv, helm_apply_pt<double, false>(d, u, i, j));
@@ -957,14 +958,14 @@ __global__ void __launch_bounds__(NT) k_outer_scale(const __grid_constant__ KDes
                                                     int nseg, int src_slot) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     const double2* r = slot<double>(d, src_slot);
     cplx<TC>* out = reinterpret_cast<cplx<TC>*>(d.xvec) + (long long)SG * d.xstride;
     const double sc = scalp<double>(d)[S::SCALE];
     const TC inv = (TC)(sc > 0 ? 1.0 / sc : 0.0);
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         const double2 rv = __ldg(r + p);
         out[p] = mk<TC>((TC)rv.x * inv, (TC)rv.y * inv);
@@ -977,13 +978,13 @@ __global__ void __launch_bounds__(NT) k_outer_update(const __grid_constant__ KDe
                                                      int nseg) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     double2* u = slot<double>(d, SU);
     const cplx<TC>* e = reinterpret_cast<const cplx<TC>*>(d.xvec) + (long long)SD * d.xstride;
     const double sc = scalp<double>(d)[S::SCALE];
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         double2 ev = to_d(__ldg(e + p));
         u[p] = dadd(u[p], dsc(ev, sc));
@@ -998,10 +999,10 @@ __global__ void __launch_bounds__(NT) k_sub(const __grid_constant__ KDesc A, con
                                             int sa, int sb, int sc) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         slot<T>(d, sc)[p] = csub<T>(slot<T>(d, sa)[p], slot<T>(d, sb)[p]);
     }
@@ -1011,10 +1012,10 @@ __global__ void __launch_bounds__(NT) k_copy(const __grid_constant__ KDesc A, co
                                              int sa, int sb) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         const long long p = (long long)j * d.pitch + i;
         slot<T>(d, sb)[p] = slot<T>(d, sa)[p];
     }
@@ -1024,10 +1025,10 @@ __global__ void __launch_bounds__(NT) k_zero(const __grid_constant__ KDesc A, co
                                              int sa) {
     __shared__ LevelDesc d;
     SegCtx c = seg_begin(A, Sg, nseg, d);
-    const int ntx = (d.n + BX - 1) / BX, nty = (d.n + BY - 1) / BY;
+    const int ntx = (d.n + BX - 1) / BX, nty = (d.ny + BY - 1) / BY;
     for (int t = c.lb; t < ntx * nty; t += c.nb) {
         const int i = (t % ntx) * BX + threadIdx.x, j = (t / ntx) * BY + threadIdx.y;
-        if (i >= d.n || j >= d.n) continue;
+        if (i >= d.n || j >= d.ny) continue;
         slot<T>(d, sa)[(long long)j * d.pitch + i] = zero2<T>();
     }
 }

@@ -115,7 +115,7 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
     std::vector<long long> units;
     for (int i : ids) {
         const LevelDesc& d = outer ? houter[i] : hdesc[i];
-        units.push_back(((long long)d.n * d.n + pts - 1) / pts);
+        units.push_back(((long long)d.n * d.ny + pts - 1) / pts);
     }
     const std::vector<int> nb = share_blocks(units, 1216);
     int blk = 0;
@@ -133,7 +133,7 @@ const SegTable& Handle::seg(const std::vector<int>& ids, bool outer, int pts) {
     t.outer = outer;
     for (int i : ids) {
         const LevelDesc& d = outer ? houter[i] : hdesc[i];
-        t.pts += (long long)d.n * d.n;
+        t.pts += (long long)d.n * d.ny;
     }
     finish_table(*this, h, t);
     return segs[key] = t;
@@ -155,9 +155,9 @@ const SegTable& Handle::seg_tiles(const std::vector<int>& ids, int tx, int ty, b
     std::vector<long long> units;
     for (int i : ids) {
         const LevelDesc& d = hdesc[i];
-        const int n = coarse ? hdesc[d.coarse].n : d.n;
-        units.push_back((long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty));
-        t.pts += (long long)d.n * d.n;
+        const int n = coarse ? hdesc[d.coarse].n : d.n, ny = coarse ? hdesc[d.coarse].ny : d.ny;
+        units.push_back((long long)((n + tx - 1) / tx) * ((ny + ty - 1) / ty));
+        t.pts += (long long)d.n * d.ny;
     }
     const std::vector<int> nb = share_blocks(units, cap);
     int blk = 0;
@@ -184,8 +184,8 @@ const SegTable& Handle::seg_outer_chunks(const std::vector<int>& ids, int chunk,
     std::vector<long long> units;
     for (int i : ids) {
         const LevelDesc& d = houter[i];
-        units.push_back(((long long)d.n * d.pitch + chunk - 1) / chunk);
-        t.pts += (long long)d.n * d.n;
+        units.push_back(((long long)d.ny * d.pitch + chunk - 1) / chunk);
+        t.pts += (long long)d.n * d.ny;
     }
     // Several segments: when one wave of blocks (cap) leaves the largest
     // per-block share more than 10% above the mean, the grid is a few waves
@@ -234,7 +234,7 @@ const SegTable& Handle::seg_rows(const std::vector<int>& ids, int rows_per_block
         Seg s;
         s.desc = i;
         s.blk0 = blk;
-        blk += blocks_for((long long)d.n * d.n, rows_per_block);
+        blk += blocks_for((long long)d.n * d.ny, rows_per_block);
         s.blk1 = blk;
         s.pad = 0;
         h.push_back(s);
@@ -242,7 +242,7 @@ const SegTable& Handle::seg_rows(const std::vector<int>& ids, int rows_per_block
     SegTable t;
     t.nblocks = blk;
     for (int i : ids) {
-        const long long N = (long long)hdesc[i].n * hdesc[i].n;
+        const long long N = (long long)hdesc[i].n * hdesc[i].ny;
         t.pts += N;
         t.mat += N * N;
     }
@@ -257,19 +257,25 @@ static double jacobi_default(double h, double kmax) {
 }
 
 // alpha = max(lambda^2) / median(lambda^2) of the constant-k Dirichlet
-// 5-point symbol, lambda_pq = (4 sin^2(p pi h/2) + 4 sin^2(q pi h/2))/h^2 - k^2
-// (Section 3.1.1: lambda_max/alpha approximates the median of eig(A^*A)).
-static double alpha_spectral(int n, double h, double kref) {
-    std::vector<double> s(n);
-    for (int j = 1; j <= n; ++j) {
-        const double v = std::sin(j * M_PI * h / 2.0);
-        s[j - 1] = 4.0 * v * v / (h * h);
-    }
-    std::vector<double> ev((size_t)n * n);
+// 5-point symbol on n x ny nodes of spacing h,
+// lambda_pq = (4 sin^2(p pi/(2(n+1))) + 4 sin^2(q pi/(2(ny+1))))/h^2 - k^2
+// (Section 3.1.1: lambda_max/alpha approximates the median of eig(A^*A)); on
+// the square h = 1/(n+1) and the sines are evaluated as sin(p pi h/2).
+static double alpha_spectral(int n, int ny, double h, double kref) {
+    auto sym = [&](int m) {
+        std::vector<double> s(m);
+        for (int j = 1; j <= m; ++j) {
+            const double v = (n == ny) ? std::sin(j * M_PI * h / 2.0) : std::sin(j * M_PI / (2.0 * (m + 1)));
+            s[j - 1] = 4.0 * v * v / (h * h);
+        }
+        return s;
+    };
+    const std::vector<double> sx = sym(n), sy = sym(ny);
+    std::vector<double> ev((size_t)n * ny);
     double mx = 0;
-    for (int p = 0; p < n; ++p)
+    for (int p = 0; p < ny; ++p)
         for (int q = 0; q < n; ++q) {
-            const double l = s[p] + s[q] - kref * kref;
+            const double l = sy[p] + sx[q] - kref * kref;
             ev[(size_t)p * n + q] = l * l;
             mx = std::max(mx, l * l);
         }
@@ -323,24 +329,24 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // The tensor maps of one (instance, level) in MapId order (see tma.cuh):
-// complex slot maps 3D (2n reals, n rows, slots), quads 3D (4, n, n), reals
-// 2D (n, n); box (W, H) nodes as the tile kernels use them.
+// complex slot maps 3D (2n reals, ny rows, slots), quads 3D (4, n, ny), reals
+// 2D (n, ny); box (W, H) nodes as the tile kernels use them.
 static int build_tmaps_desc(const LevelDesc& d, int nslot, int prec, CUtensorMap* m) {
     auto enc = encode_fn();
     if (!enc) { set_error("mg_setup: cuTensorMapEncodeTiled unavailable"); return MG_ECUDA; }
     const CUtensorMapDataType dt = prec == MG_PREC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t es = prec == MG_PREC_FP64 ? 8 : 4;
-    const cuuint64_t n = (cuuint64_t)d.n, pitch = (cuuint64_t)d.pitch;
+    const cuuint64_t n = (cuuint64_t)d.n, ny = (cuuint64_t)d.ny, pitch = (cuuint64_t)d.pitch;
     const cuuint32_t one[3] = {1, 1, 1};
     auto cplx_map = [&](int id, int W, int H) -> bool {
-        const cuuint64_t dims[3] = {2 * n, n, (cuuint64_t)nslot};
+        const cuuint64_t dims[3] = {2 * n, ny, (cuuint64_t)nslot};
         const cuuint64_t str[2] = {2 * pitch * es, 2 * (cuuint64_t)d.slot_stride * es};
         const cuuint32_t box[3] = {(cuuint32_t)(2 * W), (cuuint32_t)H, 1};
         return enc(&m[id], dt, 3, d.vec, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     auto quad_map = [&](int id, int W, int H) -> bool {
-        const cuuint64_t dims[3] = {4, n, n};
+        const cuuint64_t dims[3] = {4, n, ny};
         const cuuint64_t str[2] = {4 * es, 4 * pitch * es};
         const cuuint32_t box[3] = {4, (cuuint32_t)W, (cuuint32_t)H};
         return enc(&m[id], dt, 3, const_cast<void*>(d.adr), dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -348,7 +354,7 @@ static int build_tmaps_desc(const LevelDesc& d, int nslot, int prec, CUtensorMap
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     auto real_map = [&](int id, const void* base, int W, int H) -> bool {
-        const cuuint64_t dims[2] = {n, n};
+        const cuuint64_t dims[2] = {n, ny};
         const cuuint64_t str[1] = {pitch * es};
         const cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)H};
         return enc(&m[id], dt, 2, const_cast<void*>(base), dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -381,6 +387,16 @@ static std::vector<int> level_sizes(int n, int n_cmax) {
     return sizes;
 }
 
+// The same for an n x ny grid: both sides halve together while the longer
+// one exceeds n_cmax and both coarse sides keep a node.
+static std::vector<std::pair<int, int>> level_shapes(int n, int ny, int n_cmax) {
+    std::vector<std::pair<int, int>> sh{{n, ny}};
+    while (std::max(sh.back().first, sh.back().second) > n_cmax && sh.back().first / 2 >= 1 &&
+           sh.back().second / 2 >= 1)
+        sh.push_back({sh.back().first / 2, sh.back().second / 2});
+    return sh;
+}
+
 // Role of level l of L (Algorithm 1): Jacobi on level 1, Chebyshev with the
 // ADR corrections on level 2, nothing on level 3, Chebyshev below, the
 // coarsest-level solve on level L (which takes precedence).
@@ -402,30 +418,35 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
     for (int b = 0; b < ninst; ++b) {
         InstHost& I = H.inst[b];
         I.n = in[b].n;
+        I.ny = in[b].ny > 0 ? in[b].ny : in[b].n;
         I.omega = in[b].omega;
         I.bc = in[b].bc;
         I.adr_flags = ((p.adr_bc == MG_ADR_BC_ABC && I.bc == MG_BC_ABC1) ? ADR_ABC : 0) |
                       (p.adr_reaction == MG_ADR_REACTION_DISCRETE ? ADR_DISC : 0);
         I.off = off;
-        off += (long long)I.n * I.n;
-        const std::vector<int> sizes = level_sizes(I.n, p.n_cmax);
-        I.L = (int)sizes.size();
-        if (I.L < 2) { set_error("mg_setup: n must exceed n_cmax"); return MG_EINVAL; }
+        off += (long long)I.n * I.ny;
+        const std::vector<std::pair<int, int>> shapes = level_shapes(I.n, I.ny, p.n_cmax);
+        I.L = (int)shapes.size();
+        if (I.L < 2) { set_error("mg_setup: max(n, ny) must exceed n_cmax"); return MG_EINVAL; }
         if (I.L > MG_MAX_LEVELS) { set_error("mg_setup: too many levels"); return MG_EINVAL; }
-        if ((long long)sizes.back() * sizes.back() > MAXCOARSE) {
-            set_error("mg_setup: coarsest level larger than 32 x 32; lower n_cmax");
+        if ((long long)shapes.back().first * shapes.back().second > MAXCOARSE) {
+            set_error("mg_setup: coarsest level has more than 1024 nodes; lower n_cmax");
             return MG_EINVAL;
         }
-        if (sizes.back() < 2) { set_error("mg_setup: coarsest level smaller than 2 x 2"); return MG_EINVAL; }
+        if (std::min(shapes.back().first, shapes.back().second) < 2) {
+            set_error("mg_setup: coarsest level has a side of fewer than 2 nodes (aspect ratio too large for n_cmax)");
+            return MG_EINVAL;
+        }
         H.Lmax = std::max(H.Lmax, I.L);
         I.lv.resize(I.L);
         const bool adr = p.adr && I.L >= 3 && p.M > 0;
         for (int l = 1; l <= I.L; ++l) {
             LevelHost& lv = I.lv[l - 1];
-            lv.n = sizes[l - 1];
+            lv.n = shapes[l - 1].first;
+            lv.ny = shapes[l - 1].second;
             lv.pitch = round_pitch(lv.n);
-            lv.h = 1.0 / (lv.n + 1);
-            lv.slot_stride = (size_t)lv.pitch * lv.n;
+            lv.h = 1.0 / (std::max(lv.n, lv.ny) + 1);
+            lv.slot_stride = (size_t)lv.pitch * lv.ny;
             lv.nslot = (l == 1) ? NSLOT_L1 : NSLOT;
             const size_t npt = lv.slot_stride;
             lv.vec = H.alloc(npt * lv.nslot * esz(prec));
@@ -439,7 +460,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             if (adr && l >= 2) lv.adr = H.alloc(npt * 2 * esz(prec));
             if (adr && l == 2) lv.mod = H.alloc(npt * esz(prec));
             if (l == I.L) {
-                const size_t N = (size_t)lv.n * lv.n;
+                const size_t N = (size_t)lv.n * lv.ny;
                 lv.inv_helm = (double2*)H.alloc(N * N * sizeof(double2));
                 if (adr) lv.inv_adr = (double2*)H.alloc(N * N * sizeof(double2));
             }
@@ -454,6 +475,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                     const LevelHost& base = I.lv[l - 1];
                     LevelHost& v = vl[l - 1];
                     v.n = base.n;
+                    v.ny = base.ny;
                     v.pitch = base.pitch;
                     v.h = base.h;
                     v.slot_stride = base.slot_stride;
@@ -467,7 +489,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                     v.phi64 = (double*)H.alloc(npt * 8);
                     v.adr = H.alloc(npt * 2 * esz(prec));
                     if (l == 2) v.mod = H.alloc(npt * esz(prec));
-                    if (l == I.L) v.inv_adr = (double2*)H.alloc((size_t)v.n * v.n * v.n * v.n * sizeof(double2));
+                    if (l == I.L)
+                        v.inv_adr = (double2*)H.alloc((size_t)v.n * v.ny * v.n * v.ny * sizeof(double2));
                     if (!v.phi64 || !v.adr || (l == 2 && !v.mod) || (l == I.L && !v.inv_adr)) {
                         set_error("mg_setup: out of device memory (Wave-Ray levels)");
                         return MG_ENOMEM;
@@ -492,7 +515,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
     if (!vscr) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
     for (int b = 0; b < ninst; ++b) {
         long long bad_k = 0, bad_phi = 0;
-        int rc = setup_check_fields(in[b].k, in[b].phi, in[b].n, vscr, &bad_k, &bad_phi, st);
+        int rc = setup_check_fields(in[b].k, in[b].phi, H.inst[b].n, H.inst[b].ny, vscr, &bad_k, &bad_phi, st);
         if (rc) return rc;
         if (bad_k || bad_phi) {
             set_error("mg_setup: instance " + std::to_string(b) + ": " + std::to_string(bad_k) +
@@ -505,7 +528,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         InstHost& I = H.inst[b];
         for (int l = 1; l <= I.L; ++l) {
             LevelHost& lv = I.lv[l - 1];
-            setup_inject(in[b].k, in[b].phi, I.n, I.omega, I.bc, l, lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, st);
+            setup_inject(in[b].k, in[b].phi, I.n, I.ny, I.omega, I.bc, l, lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny,
+                         lv.pitch, st);
         }
         if (p.ray && I.lv.size() >= 2 && I.lv[1].adr) {
             // Wave-Ray: correction m (0-based here) uses phi_m = cos(theta) x + sin(theta) y,
@@ -515,7 +539,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 const double cx = std::cos(th), cy = std::sin(th);
                 for (int l = 2; l <= I.L; ++l) {
                     LevelHost& lv = (m == 0) ? I.lv[l - 1] : I.rv[(size_t)m - 1][l - 1];
-                    setup_plane_phase(lv.phi64, lv.n, lv.pitch, I.lv[0].h, 1 << (l - 1), cx, cy, st);
+                    setup_plane_phase(lv.phi64, lv.n, lv.ny, lv.pitch, I.lv[0].h, 1 << (l - 1), cx, cy, st);
                 }
             }
         }
@@ -557,6 +581,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.part = H.part + (size_t)MAXB * MAXDOT * di;
             d.counter = H.counter + (size_t)NCOUNTERS * di;
             d.n = lv.n;
+            d.ny = lv.ny;
             d.pitch = lv.pitch;
             d.h = lv.h;
             d.inv_h2 = 1.0 / (lv.h * lv.h);
@@ -568,10 +593,11 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             d.fwh = (float)d.wh;
             d.fshift = (float)d.shift;
             d.has_shift = d.shift != 0.0;
-            d.gs = lv.adr ? setup_adr_scale(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
-                                            I.adr_flags, dscr, st)
+            d.gs = lv.adr ? setup_adr_scale(lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.omega, I.bc,
+                                            p.shift, I.adr_flags, dscr, st)
                           : 1.0;
-            if (lv.adr) lv.peclet = setup_peclet(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, dscr, st);
+            if (lv.adr)
+                lv.peclet = setup_peclet(lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.omega, I.bc, dscr, st);
             d.fgs = (float)d.gs;
             d.bc = I.bc;
             d.inst = b;
@@ -583,10 +609,10 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             if (l == 1) {
                 double kmax = 0;
                 // level-1 max k: from the FP64 field
-                std::vector<double> kk((size_t)lv.n * lv.pitch);
+                std::vector<double> kk((size_t)lv.ny * lv.pitch);
                 cudaMemcpyAsync(kk.data(), lv.k64, kk.size() * 8, cudaMemcpyDeviceToHost, st);
                 cudaStreamSynchronize(st);
-                for (int j = 0; j < lv.n; ++j)
+                for (int j = 0; j < lv.ny; ++j)
                     for (int i = 0; i < lv.n; ++i) kmax = std::max(kmax, kk[(size_t)j * lv.pitch + i]);
                 I.omega_j = p.omega_jacobi > 0 ? p.omega_jacobi : jacobi_default(lv.h, kmax);
                 s[S::OMEGA_J] = I.omega_j;
@@ -595,24 +621,24 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             const bool cheb = role == MG_ROLE_CHEB || role == MG_ROLE_CHEB_ADR || role == MG_ROLE_COARSE_CHEB;
             lv.cheb = cheb;
             if (cheb) {
-                std::vector<double> kk((size_t)lv.n * lv.pitch);
+                std::vector<double> kk((size_t)lv.ny * lv.pitch);
                 cudaMemcpyAsync(kk.data(), lv.k64, kk.size() * 8, cudaMemcpyDeviceToHost, st);
                 cudaStreamSynchronize(st);
                 double kmax = 0;
-                for (int j = 0; j < lv.n; ++j)
+                for (int j = 0; j < lv.ny; ++j)
                     for (int i = 0; i < lv.n; ++i) kmax = std::max(kmax, kk[(size_t)j * lv.pitch + i]);
-                lv.lam_max = setup_lambda_max(lv.k64, lv.sig64, lv.n, lv.pitch, lv.h, I.bc, p.shift, dscr, st);
-                lv.alpha = (p.alpha[l - 1] > 0) ? p.alpha[l - 1] : alpha_spectral(lv.n, lv.h, kmax);
+                lv.lam_max = setup_lambda_max(lv.k64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.bc, p.shift, dscr, st);
+                lv.alpha = (p.alpha[l - 1] > 0) ? p.alpha[l - 1] : alpha_spectral(lv.n, lv.ny, lv.h, kmax);
                 const int q = (l == I.L) ? p.coarse_cheb_iters : p.cheb_iters;
                 s[S::CHEB_N] = q;
                 cheb_coeffs(lv.lam_max, lv.alpha, q, s + S::CHEB_C1, s + S::CHEB_C2);
             }
             if (l == I.L) {
-                int r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc, p.shift,
-                                             0, 0, lv.inv_helm, st);
+                int r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.omega, I.bc,
+                                             p.shift, 0, 0, lv.inv_helm, st);
                 if (r) return r;
                 if (lv.inv_adr) {
-                    r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.pitch, lv.h, I.omega, I.bc,
+                    r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.omega, I.bc,
                                              p.shift, 1, I.adr_flags, lv.inv_adr, st);
                     if (r) return r;
                 }
@@ -638,14 +664,13 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 d.scal = H.scal + (size_t)S::SIZE * di;
                 d.part = H.part + (size_t)MAXB * MAXDOT * di;
                 d.counter = H.counter + (size_t)NCOUNTERS * di;
-                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, I.adr_flags,
-                                       dscr, st);
+                d.gs = setup_adr_scale(v.k64, v.phi64, v.sig64, v.n, v.ny, v.pitch, v.h, I.omega, I.bc, p.shift,
+                                       I.adr_flags, dscr, st);
                 d.fgs = (float)d.gs;
                 d.coarse = (l < I.L) ? di + 1 : -1;
                 if (l == I.L) {
-                    int r = setup_coarse_inverse(v.k64, v.phi64, v.sig64, v.n, v.pitch, v.h, I.omega, I.bc, p.shift, 1,
-                                                 I.adr_flags,
-                                                 v.inv_adr, st);
+                    int r = setup_coarse_inverse(v.k64, v.phi64, v.sig64, v.n, v.ny, v.pitch, v.h, I.omega, I.bc,
+                                                 p.shift, 1, I.adr_flags, v.inv_adr, st);
                     if (r) return r;
                 }
                 H.hdesc.push_back(d);
@@ -774,13 +799,15 @@ static void free_all(Handle& H) {
     H.alloc_bytes = 0;
 }
 
-// user dense (n x n, at element offset) <-> pitched slot
-static cudaError_t copy_in(const void* user, long long off, size_t es, void* slotp, int n, int pitch, cudaStream_t st) {
-    return cudaMemcpy2DAsync(slotp, (size_t)pitch * es, (const char*)user + off * es, (size_t)n * es, (size_t)n * es, n,
-                             cudaMemcpyDefault, st);
+// user dense (ny rows of n, at element offset) <-> pitched slot
+static cudaError_t copy_in(const void* user, long long off, size_t es, void* slotp, int n, int ny, int pitch,
+                           cudaStream_t st) {
+    return cudaMemcpy2DAsync(slotp, (size_t)pitch * es, (const char*)user + off * es, (size_t)n * es, (size_t)n * es,
+                             ny, cudaMemcpyDefault, st);
 }
-static cudaError_t copy_out(void* user, long long off, size_t es, const void* slotp, int n, int pitch, cudaStream_t st) {
-    return cudaMemcpy2DAsync((char*)user + off * es, (size_t)n * es, slotp, (size_t)pitch * es, (size_t)n * es, n,
+static cudaError_t copy_out(void* user, long long off, size_t es, const void* slotp, int n, int ny, int pitch,
+                            cudaStream_t st) {
+    return cudaMemcpy2DAsync((char*)user + off * es, (size_t)n * es, slotp, (size_t)pitch * es, (size_t)n * es, ny,
                              cudaMemcpyDefault, st);
 }
 static void* slot_ptr(const Handle& H, const LevelHost& lv, int s) {
@@ -908,8 +935,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         return MG_EINVAL;
     }
     for (int b = 0; b < ninst; ++b) {
-        if (!inst[b].k || !inst[b].phi || inst[b].n < 3 || !(inst[b].omega > 0) ||
-            inst[b].bc < MG_BC_DIRICHLET || inst[b].bc > MG_BC_SPONGE) {
+        if (!inst[b].k || !inst[b].phi || inst[b].n < 3 || (inst[b].ny != 0 && inst[b].ny < 3) ||
+            !(inst[b].omega > 0) || inst[b].bc < MG_BC_DIRICHLET || inst[b].bc > MG_BC_SPONGE) {
             set_error("mg_setup: bad instance " + std::to_string(b));
             return MG_EINVAL;
         }
@@ -924,6 +951,13 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     // the wave-cycle tail (tail_wave.cuh) follows an explicit tail_nmax; automatic: levels with n <= 63
     mh->H.wave_tail_nmax = mh->H.p.tail_nmax >= 0 ? mh->H.p.tail_nmax : 63;
     if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = ninst == 1 ? 31 : 0;
+    // the two tails are built for square levels: a handle with a non-square
+    // instance runs every level with its own launches
+    for (int b = 0; b < ninst; ++b)
+        if (inst[b].ny != 0 && inst[b].ny != inst[b].n) {
+            mh->H.wave_tail_nmax = 0;
+            mh->H.p.tail_nmax = 0;
+        }
     mh->H.prec = p->precision;
     mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();
     // k and phi may be host memory: stage them on the device for the setup kernels
@@ -931,7 +965,7 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     std::vector<void*> tmp;
     cudaStream_t st0 = (cudaStream_t)stream;
     for (int b = 0; b < ninst; ++b) {
-        const size_t bytes = sizeof(double) * (size_t)inst[b].n * inst[b].n;
+        const size_t bytes = sizeof(double) * (size_t)inst[b].n * (inst[b].ny > 0 ? inst[b].ny : inst[b].n);
         for (int f = 0; f < 2; ++f) {
             const double* src = f ? inst[b].phi : inst[b].k;
             cudaPointerAttributes a;
@@ -983,6 +1017,13 @@ int mg_level_n(const mg_handle* h, int inst, int level) {
     const InstHost& I = h->H.inst[inst];
     if (level < 1 || level > I.L) return MG_EINVAL;
     return I.lv[level - 1].n;
+}
+
+int mg_level_ny(const mg_handle* h, int inst, int level) {
+    if (!h || inst < 0 || inst >= (int)h->H.inst.size()) return MG_EINVAL;
+    const InstHost& I = h->H.inst[inst];
+    if (level < 1 || level > I.L) return MG_EINVAL;
+    return I.lv[level - 1].ny;
 }
 
 int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int nout) {
@@ -1074,8 +1115,8 @@ int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream
     const size_t es = esz(H.prec);
     for (auto& I : H.inst) {
         LevelHost& l1 = I.lv[0];
-        WADR_CHECK(copy_in(g, I.off, es, slot_ptr(H, l1, SG), l1.n, l1.pitch, st));
-        WADR_CHECK(copy_in(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.pitch, st));
+        WADR_CHECK(copy_in(g, I.off, es, slot_ptr(H, l1, SG), l1.n, l1.ny, l1.pitch, st));
+        WADR_CHECK(copy_in(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.ny, l1.pitch, st));
     }
     for (int c = 0; c < ncycles; ++c) {
         h->eng->cycle(H, false, st);
@@ -1087,7 +1128,7 @@ int mg_cycle(mg_handle* h, void* u, const void* g, int ncycles, mg_stream stream
     }
     for (auto& I : H.inst) {
         LevelHost& l1 = I.lv[0];
-        WADR_CHECK(copy_out(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.pitch, st));
+        WADR_CHECK(copy_out(u, I.off, es, slot_ptr(H, l1, SX2), l1.n, l1.ny, l1.pitch, st));
     }
     WADR_CHECK(cudaGetLastError());
     if (is_host_ptr(u)) return check_device_error(H, st);   // synchronises: host result complete on return
@@ -1103,8 +1144,8 @@ int mg_solve_begin(mg_handle* h, const void* u, const void* g, mg_stream stream)
     for (auto& I : H.inst) {
         LevelHost& l1 = I.lv[0];
         char* ov = (char*)I.outer_vec;
-        WADR_CHECK(copy_in(g, I.off, 16, ov + (size_t)SG * I.outer_stride * 16, l1.n, l1.pitch, st));
-        WADR_CHECK(copy_in(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
+        WADR_CHECK(copy_in(g, I.off, 16, ov + (size_t)SG * I.outer_stride * 16, l1.n, l1.ny, l1.pitch, st));
+        WADR_CHECK(copy_in(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.ny, l1.pitch, st));
     }
     h->eng->outer_residual(H, true, st);
     if (H.p.outer == MG_OUTER_FGMRES) h->eng->fg_start(H, st);
@@ -1149,7 +1190,7 @@ int mg_solve_end(mg_handle* h, void* u, double* rel_residual, mg_stream stream) 
         for (auto& I : H.inst) {
             LevelHost& l1 = I.lv[0];
             const char* ov = (const char*)I.outer_vec;
-            WADR_CHECK(copy_out(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.pitch, st));
+            WADR_CHECK(copy_out(u, I.off, 16, ov + (size_t)SU * I.outer_stride * 16, l1.n, l1.ny, l1.pitch, st));
         }
     }
     std::vector<double> rn, gn;
@@ -1366,14 +1407,14 @@ static int run_op(mg_handle* h, int inst, int level, int what, int a0, int a1,
         int lvl = level + (pr.first >= 100 ? in_level_shift : 0);
         int s = pr.first % 100;
         LevelHost& lv = I.lv[lvl - 1];
-        WADR_CHECK(copy_in(pr.second, 0, es, slot_ptr(H, lv, s), lv.n, lv.pitch, st));
+        WADR_CHECK(copy_in(pr.second, 0, es, slot_ptr(H, lv, s), lv.n, lv.ny, lv.pitch, st));
     }
     int s = h->eng->level_op(H, inst, level, what, a0, a1, st);
     WADR_CHECK(cudaGetLastError());
     if (s < 0) { set_error("level op failed"); return MG_EINVAL; }
     if (out_slot_override >= 0) s = out_slot_override;
     LevelHost& lo = I.lv[level + out_level_shift - 1];
-    WADR_CHECK(copy_out(outp, 0, es, slot_ptr(H, lo, s), lo.n, lo.pitch, st));
+    WADR_CHECK(copy_out(outp, 0, es, slot_ptr(H, lo, s), lo.n, lo.ny, lo.pitch, st));
     WADR_CHECK(cudaStreamSynchronize(st));
     return MG_OK;
 }

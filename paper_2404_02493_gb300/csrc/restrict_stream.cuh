@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
     SegCtx c = seg_begin(A, Sg, nseg, d);
     coarse_desc(A, nseg, d, dc, tid);
     __syncthreads();
-    const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
-    const int nstrips = (n + RS_SO - 1) / RS_SO, nunits = nstrips * ((nc + RHC - 1) / RHC);
+    const int n = d.n, ny = d.ny, pitch = d.pitch, nc = dc.n, ncy = dc.ny, cpitch = dc.pitch;
+    const int nstrips = (n + RS_SO - 1) / RS_SO, nunits = nstrips * ((ncy + RHC - 1) / RHC);
     // fgv: inside an FGMRES iteration g is the basis vector V_j, read where it
     // lies (still unnormalised) and scaled by 1 / ||V_j|| on the fly, as
     // k_fg_prep would have copied it
@@ -62,16 +62,16 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_restrict_jac0_stream(const __gr
     for (int u = c.lb * RS_WPB + warp; u < nunits; u += c.nb * RS_WPB) {
         const int sk = u % nstrips, band = u / nstrips;
         const int X0 = RS_SO * sk - 2;
-        const int J0 = RHC * band, J1 = min(J0 + RHC, nc);
-        const int fy0 = 2 * J0, fy1 = (J1 == nc) ? n : 2 * J1;   // own fine rows of u1
+        const int J0 = RHC * band, J1 = min(J0 + RHC, ncy);
+        const int fy0 = 2 * J0, fy1 = (J1 == ncy) ? ny : 2 * J1;   // own fine rows of u1
         const int j0 = 2 * J0 - 1, j1 = 2 * J1 + 1;
         const int col = X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const int I = X0 / 2 + lane;   // coarse column of the lane
         auto issue = [&](int r) {
-            ring_issue2<cplx<T>>(Gr, gv, n, pitch, X0, r, lane);
-            ring_issue2<T>(Kr, kf, n, pitch, X0, r, lane);
-            if (HS) ring_issue2<T>(Sr, sgf, n, pitch, X0, r, lane);
+            ring_issue2<cplx<T>>(Gr, gv, n, ny, pitch, X0, r, lane);
+            ring_issue2<T>(Kr, kf, n, ny, pitch, X0, r, lane);
+            if (HS) ring_issue2<T>(Sr, sgf, n, ny, pitch, X0, r, lane);
         };
 #pragma unroll
         for (int r = 0; r < RS_AH; ++r) {
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
     SegCtx c = seg_begin(A, Sg, nseg, d);
     coarse_desc(A, nseg, d, dc, tid);
     __syncthreads();
-    const int n = d.n, pitch = d.pitch, nc = dc.n, cpitch = dc.pitch;
-    const int nstrips = (n + SO - 1) / SO, nunits = nstrips * ((n + RH - 1) / RH);
+    const int n = d.n, ny = d.ny, pitch = d.pitch, nc = dc.n, ncy = dc.ny, cpitch = dc.pitch;
+    const int nstrips = (n + SO - 1) / SO, nunits = nstrips * ((ny + RH - 1) / RH);
     const cplx<T>* const xv = slot<T>(d, sx);
     const cplx<T>* const ev = slot<T>(dc, sc);
     const int jk = FG ? (int)d.fs[FS::J] : 0;
@@ -195,26 +195,26 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
     for (int u = c.lb * RS_WPB + warp; u < nunits; u += c.nb * RS_WPB) {
         const int sk = u % nstrips, band = u / nstrips;
         const int X0 = SO * sk - HW;
-        const int y0 = RH * band, y1 = min(y0 + RH, n);
+        const int y0 = RH * band, y1 = min(y0 + RH, ny);
         const int j0 = y0 - (FG ? 2 : 1), j1 = y1 + (FG ? 1 : 0);
         const int col = X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const int ci = X0 / 2 + lane;   // the lane's coarse column
         const bool cci = (unsigned)ci < (unsigned)nc;
         auto issue = [&](int r) {
-            ring_issue2<cplx<T>>(Xr, xv, n, pitch, X0, r, lane);
-            ring_issue2<cplx<T>>(Gr, gv, n, pitch, X0, r, lane);
-            ring_issue2<T>(Kr, kf, n, pitch, X0, r, lane);
-            if (HS) ring_issue2<T>(Sr, sgf, n, pitch, X0, r, lane);
+            ring_issue2<cplx<T>>(Xr, xv, n, ny, pitch, X0, r, lane);
+            ring_issue2<cplx<T>>(Gr, gv, n, ny, pitch, X0, r, lane);
+            ring_issue2<T>(Kr, kf, n, ny, pitch, X0, r, lane);
+            if (HS) ring_issue2<T>(Sr, sgf, n, ny, pitch, X0, r, lane);
             if (!(r & 1) || r == j0) {
                 // coarse row r / 2 (for the first row, the row below it as well)
                 const int cr = (r & 1) ? (r - 1) >> 1 : r >> 1;
-                const bool ok = cci && (unsigned)cr < (unsigned)nc;
+                const bool ok = cci && (unsigned)cr < (unsigned)ncy;
                 cp_async_elem<cplx<T>>(Er + (cr & (SW_DEP - 1)) * 32 + lane,
                                        ok ? ev + (long long)cr * cpitch + ci : ev, ok);
                 if (r == j0 && !(r & 1)) {
                     const int cb = (r >> 1) - 1;
-                    const bool okb = cci && (unsigned)cb < (unsigned)nc;
+                    const bool okb = cci && (unsigned)cb < (unsigned)ncy;
                     cp_async_elem<cplx<T>>(Er + (cb & (SW_DEP - 1)) * 32 + lane,
                                            okb ? ev + (long long)cb * cpitch + ci : ev, okb);
                 }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
             ring_read<cplx<T>>(Xr, j, lane, x0.v0, x0.v1);
             u0.v0 = cadd<T>(x0.v0, u0.v0);
             u0.v1 = cadd<T>(x0.v1, u0.v1);
-            const bool roj = (unsigned)j < (unsigned)n;
+            const bool roj = (unsigned)j < (unsigned)ny;
             u0 = p2sel<T>(u0, roj && cin0, roj && cin1);
             // Jacobi at row j - 1
             const int r1 = j - 1;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(32 * RS_WPB) k_prolong_jac_stream(const __grid
                 }
                 if constexpr (FG) {
                     // W = A z at row j - 2 (z zero outside the grid)
-                    const bool ro1 = (unsigned)r1 < (unsigned)n;
+                    const bool ro1 = (unsigned)r1 < (unsigned)ny;
                     o1 = p2sel<T>(o1, ro1 && cin0, ro1 && cin1);
                     const int r2 = j - 2;
                     const P2<T> w = helm_row<T, false>(dgp, ob2, ob3, o1, ih2);

@@ -15,11 +15,12 @@ namespace wadr {
 // Coefficients of level `level` by injection from the fine grid: coarse node
 // I of level l sits on fine node 2^(l-1) (I+1) - 1 (Algorithm 1's
 // re-discretised operator A_H; coefficients sampled at coinciding nodes).
-__global__ void k_inject(const double* __restrict__ kf, const double* __restrict__ pf, int n1, double omega,
-                         int bc, int level, double* k64, double* phi64, double* sig64, int n, int pitch) {
+__global__ void k_inject(const double* __restrict__ kf, const double* __restrict__ pf, int n1, int ny1,
+                         double omega, int bc, int level, double* k64, double* phi64, double* sig64, int n, int ny,
+                         int pitch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
+    if (i >= n || j >= ny) return;
     const long long f = 1LL << (level - 1);
     const long long fi = f * (i + 1) - 1, fj = f * (j + 1) - 1;
     const long long q = fj * n1 + fi, p = (long long)j * pitch + i;
@@ -28,30 +29,35 @@ __global__ void k_inject(const double* __restrict__ kf, const double* __restrict
     phi64[p] = pf[q];
     if (sig64) {
         // sponge mask: gamma(d) = omega ((W-d)/W)^2 for d < W = 2 pi/omega,
-        // d = distance of the fine node to the boundary; sig = omega gamma s^2
-        const double h1 = 1.0 / (n1 + 1);
+        // d = distance of the fine node to the boundary of [0, lx] x [0, ly]
+        // (the longer side has unit length, h1 = 1/(max(n1, ny1)+1));
+        // sig = omega gamma s^2
+        const int m1 = max(n1, ny1);
+        const double h1 = 1.0 / (m1 + 1);
+        const double lx = n1 == m1 ? 1.0 : (n1 + 1) * h1, ly = ny1 == m1 ? 1.0 : (ny1 + 1) * h1;
         const double x = (fi + 1) * h1, y = (fj + 1) * h1;
-        const double dist = fmin(fmin(x, 1.0 - x), fmin(y, 1.0 - y));
+        const double dist = fmin(fmin(x, lx - x), fmin(y, ly - y));
         const double W = 2.0 * M_PI / omega;
         const double gam = dist < W ? omega * ((W - dist) / W) * ((W - dist) / W) : 0.0;
         sig64[p] = omega * gam * (k / omega) * (k / omega);
     }
 }
 
-void setup_inject(const double* k_fine, const double* phi_fine, int n1, double omega, int bc, int level,
-                  double* k64, double* phi64, double* sig64, int n, int pitch, cudaStream_t st) {
-    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_inject<<<g, b, 0, st>>>(k_fine, phi_fine, n1, omega, bc, level, k64, phi64, sig64, n, pitch);
+void setup_inject(const double* k_fine, const double* phi_fine, int n1, int ny1, double omega, int bc, int level,
+                  double* k64, double* phi64, double* sig64, int n, int ny, int pitch, cudaStream_t st) {
+    dim3 b(32, 8), g((n + 31) / 32, (ny + 7) / 8);
+    k_inject<<<g, b, 0, st>>>(k_fine, phi_fine, n1, ny1, omega, bc, level, k64, phi64, sig64, n, ny, pitch);
 }
 
 // Wave-Ray plane-wave phase cx x + cy y on level l (scale = 2^(l-1), h1 the
 // level-1 spacing), as injection of the level-1 phase places it
-void setup_plane_phase(double* phi64, int n, int pitch, double h1, int scale, double cx, double cy, cudaStream_t st) {
-    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_plane_phase<<<g, b, 0, st>>>(phi64, n, pitch, h1, scale, cx, cy);
+void setup_plane_phase(double* phi64, int n, int ny, int pitch, double h1, int scale, double cx, double cy,
+                       cudaStream_t st) {
+    dim3 b(32, 8), g((n + 31) / 32, (ny + 7) / 8);
+    k_plane_phase<<<g, b, 0, st>>>(phi64, n, ny, pitch, h1, scale, cx, cy);
 }
 
-// Input validation of one instance's fine fields (dense n x n): counts the
+// Input validation of one instance's fine fields (dense n x ny): counts the
 // nodes whose k is not a finite positive number (out[0]) and whose phi is
 // not finite (out[1]).
 __global__ void k_check_fields(const double* __restrict__ k, const double* __restrict__ phi, long long npt,
@@ -66,11 +72,11 @@ __global__ void k_check_fields(const double* __restrict__ k, const double* __res
     if (bad_phi) atomicAdd(out + 1, bad_phi);
 }
 
-int setup_check_fields(const double* k, const double* phi, int n, double* dscratch, long long* bad_k,
+int setup_check_fields(const double* k, const double* phi, int n, int ny, double* dscratch, long long* bad_k,
                        long long* bad_phi, cudaStream_t st) {
     unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
     WADR_CHECK(cudaMemsetAsync(o, 0, 2 * sizeof(unsigned long long), st));
-    const long long npt = (long long)n * n;
+    const long long npt = (long long)n * ny;
     const int blocks = (int)std::min<long long>((npt + 255) / 256, 1216);
     k_check_fields<<<blocks, 256, 0, st>>>(k, phi, npt, o);
     WADR_CHECK(cudaGetLastError());
@@ -86,22 +92,22 @@ int setup_check_fields(const double* k, const double* phi, int n, double* dscrat
 // discretisation needs 2 omega h max(|phi_x|, |phi_y|) <= 2): the maximum over
 // nodes of omega h max(|phi_x|, |phi_y|), with the same phase derivatives as
 // the ADR coefficients.  The condition holds where the value is <= 1.
-__global__ void k_peclet(const double* phi64, const double* k64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, unsigned long long* out) {
+__global__ void k_peclet(const double* phi64, const double* k64, const double* sig64, int n, int ny, int pitch,
+                         double h, double omega, int bc, unsigned long long* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
-    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, 0.0, i, j, 0);
+    if (i >= n || j >= ny) return;
+    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, ny, pitch, h, omega, bc, 0.0, i, j, 0);
     const double v = omega * h * fmax(fabs(c.px), fabs(c.py));
     atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
 
-double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
+double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch, double h,
                     double omega, int bc, double* dscratch, cudaStream_t st) {
     unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
     cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
-    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_peclet<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, o);
+    dim3 b(32, 8), g((n + 31) / 32, (ny + 7) / 8);
+    k_peclet<<<g, b, 0, st>>>(phi64, k64, sig64, n, ny, pitch, h, omega, bc, o);
     unsigned long long v = 0;
     cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -111,12 +117,12 @@ double setup_peclet(const double* k64, const double* phi64, const double* sig64,
 }
 
 // max over nodes of the absolute row sum |A_pp| + (in-grid neighbours)/h^2
-__device__ __forceinline__ double helm_row_sum(const double* k64, const double* sig64, int n, int pitch,
+__device__ __forceinline__ double helm_row_sum(const double* k64, const double* sig64, int n, int ny, int pitch,
                                                double h, int bc, double shift, int i, int j) {
     const long long p = (long long)j * pitch + i;
     const double k = k64[p], kh = k * h;
     double re = 4.0 - kh * kh, im = 0.0;
-    const int m = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1);
+    const int m = (i == 0) + (i == n - 1) + (j == 0) + (j == ny - 1);
     if (bc == BC_ABC1) {
         re -= m;
         im -= m * kh;
@@ -127,22 +133,22 @@ __device__ __forceinline__ double helm_row_sum(const double* k64, const double* 
     return (sqrt(re * re + im * im) + (4 - m)) / (h * h);
 }
 
-__global__ void k_gersh(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
-                        unsigned long long* out) {
+__global__ void k_gersh(const double* k64, const double* sig64, int n, int ny, int pitch, double h, int bc,
+                        double shift, unsigned long long* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
-    const double v = helm_row_sum(k64, sig64, n, pitch, h, bc, shift, i, j);
+    if (i >= n || j >= ny) return;
+    const double v = helm_row_sum(k64, sig64, n, ny, pitch, h, bc, shift, i, j);
     // positive doubles order like their bit patterns
     atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
 
-double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch, double h, int bc, double shift,
-                        double* dscratch, cudaStream_t st) {
+double setup_lambda_max(const double* k64, const double* sig64, int n, int ny, int pitch, double h, int bc,
+                        double shift, double* dscratch, cudaStream_t st) {
     unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
     cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
-    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_gersh<<<g, b, 0, st>>>(k64, sig64, n, pitch, h, bc, shift, o);
+    dim3 b(32, 8), g((n + 31) / 32, (ny + 7) / 8);
+    k_gersh<<<g, b, 0, st>>>(k64, sig64, n, ny, pitch, h, bc, shift, o);
     unsigned long long v = 0;
     cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -152,12 +158,12 @@ double setup_lambda_max(const double* k64, const double* sig64, int n, int pitch
 }
 
 // max over nodes of the absolute row sum of the ADR operator |d| + sum |c_dir|
-__global__ void k_adr_rowmax(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
+__global__ void k_adr_rowmax(const double* phi64, const double* k64, const double* sig64, int n, int ny, int pitch,
                              double h, double omega, int bc, double shift, int adr_flags, unsigned long long* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
-    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_flags);
+    if (i >= n || j >= ny) return;
+    const AdrCoef c = adr_coef_at(phi64, k64, sig64, n, ny, pitch, h, omega, bc, shift, i, j, adr_flags);
     const double v = sqrt(dabs2(c.d)) + sqrt(dabs2(c.cw)) + sqrt(dabs2(c.ce)) + sqrt(dabs2(c.cs)) +
                      sqrt(dabs2(c.cn));
     atomicMax(out, (unsigned long long)__double_as_longlong(v));
@@ -166,12 +172,13 @@ __global__ void k_adr_rowmax(const double* phi64, const double* k64, const doubl
 // Scale of the s-step GMRES basis of an ADR level: the power of two s with
 // s * (max row sum of |L|) in (1/2, 1], so that ||s L||_inf <= 1 and the
 // basis vectors (s L)^j r0 stay O(|r0|) without rounding from s itself.
-double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                       double omega, int bc, double shift, int adr_flags, double* dscratch, cudaStream_t st) {
+double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
+                       double h, double omega, int bc, double shift, int adr_flags, double* dscratch,
+                       cudaStream_t st) {
     unsigned long long* o = reinterpret_cast<unsigned long long*>(dscratch);
     cudaMemsetAsync(o, 0, sizeof(unsigned long long), st);
-    dim3 b(32, 8), g((n + 31) / 32, (n + 7) / 8);
-    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, pitch, h, omega, bc, shift, adr_flags, o);
+    dim3 b(32, 8), g((n + 31) / 32, (ny + 7) / 8);
+    k_adr_rowmax<<<g, b, 0, st>>>(phi64, k64, sig64, n, ny, pitch, h, omega, bc, shift, adr_flags, o);
     unsigned long long v = 0;
     cudaMemcpyAsync(&v, o, sizeof(v), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -184,11 +191,11 @@ double setup_adr_scale(const double* k64, const double* phi64, const double* sig
 }
 
 // ---------------------------------------------------------------- dense LU
-// Dense matrix of the coarsest operator (N = n^2, row p = j*n + i).
-__global__ void k_dense(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                        double omega, int bc, double shift, int which, int adr_flags, double2* A) {
+// Dense matrix of the coarsest operator (N = n ny, row p = j*n + i).
+__global__ void k_dense(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
+                        double h, double omega, int bc, double shift, int which, int adr_flags, double2* A) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = n * n;
+    const int N = n * ny;
     if (p >= N) return;
     const int i = p % n, j = p / n;
     double2* row = A + (long long)p * N;
@@ -198,7 +205,7 @@ __global__ void k_dense(const double* k64, const double* phi64, const double* si
         const long long pp = (long long)j * pitch + i;
         const double k = k64[pp], kh = k * h;
         double re = 4.0 - kh * kh, im = 0.0;
-        const int m = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1);
+        const int m = (i == 0) + (i == n - 1) + (j == 0) + (j == ny - 1);
         if (bc == BC_ABC1) { re -= m; im -= m * kh; }
         else if (bc == BC_SPONGE) { im -= h * h * sig64[pp]; }
         if (shift != 0.0) im -= shift * kh * kh;
@@ -206,14 +213,14 @@ __global__ void k_dense(const double* k64, const double* phi64, const double* si
         if (i > 0) row[p - 1] = make_double2(-ih2, 0);
         if (i < n - 1) row[p + 1] = make_double2(-ih2, 0);
         if (j > 0) row[p - n] = make_double2(-ih2, 0);
-        if (j < n - 1) row[p + n] = make_double2(-ih2, 0);
+        if (j < ny - 1) row[p + n] = make_double2(-ih2, 0);
     } else {
-        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_flags);
+        AdrCoef c = adr_coef_at(phi64, k64, sig64, n, ny, pitch, h, omega, bc, shift, i, j, adr_flags);
         row[p] = c.d;
         if (i > 0) row[p - 1] = c.cw;
         if (i < n - 1) row[p + 1] = c.ce;
         if (j > 0) row[p - n] = c.cs;
-        if (j < n - 1) row[p + n] = c.cn;
+        if (j < ny - 1) row[p + n] = c.cn;
     }
 }
 
@@ -287,9 +294,10 @@ __global__ void k_lu_inv(const double2* LU, const int* perm, int N, double2* inv
     }
 }
 
-int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int pitch, double h,
-                         double omega, int bc, double shift, int which, int adr_flags, double2* inv, cudaStream_t st) {
-    const int N = n * n;
+int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
+                         double h, double omega, int bc, double shift, int which, int adr_flags, double2* inv,
+                         cudaStream_t st) {
+    const int N = n * ny;
     double2* A = nullptr;
     int* perm = nullptr;
     int* info = nullptr;
@@ -297,7 +305,8 @@ int setup_coarse_inverse(const double* k64, const double* phi64, const double* s
     if (cudaMalloc(&perm, sizeof(int) * (N + 1)) != cudaSuccess) { cudaFree(A); return MG_ENOMEM; }
     info = perm + N;
     cudaMemsetAsync(info, 0, sizeof(int), st);
-    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, pitch, h, omega, bc, shift, which, adr_flags, A);
+    k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, ny, pitch, h, omega, bc, shift, which, adr_flags,
+                                              A);
     k_lu<<<1, 1024, 0, st>>>(A, N, perm, info);
     k_lu_inv<<<(N + 63) / 64, 64, 0, st>>>(A, perm, N, inv);
     int hinfo = 0;

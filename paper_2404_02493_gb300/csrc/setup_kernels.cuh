@@ -9,9 +9,10 @@ namespace wadr {
 // i of level l is level-1 node 2^(l-1) (i+1) - 1, at x = 2^(l-1) (i+1) h1,
 // exactly the value injection of the level-1 phase gives.  Products and the
 // sum are rounded separately (no contraction).
-__global__ inline void k_plane_phase(double* phi64, int n, int pitch, double h1, int scale, double cx, double cy) {
+__global__ inline void k_plane_phase(double* phi64, int n, int ny, int pitch, double h1, int scale, double cx,
+                                     double cy) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
+    if (i >= n || j >= ny) return;
     const double x = __dmul_rn((double)(scale * (i + 1)), h1), y = __dmul_rn((double)(scale * (j + 1)), h1);
     phi64[(long long)j * pitch + i] = __dadd_rn(__dmul_rn(cx, x), __dmul_rn(cy, y));
 }
@@ -43,14 +44,15 @@ struct AdrCoef {
 //   (4/h^2) (sin^2(w h px / 2) + sin^2(w h py / 2)), so that a locally plane
 //   wave exp(i w phi) carries the reaction the discrete Helmholtz operator
 //   gives it (a deviation from the printed equation; off by default).
-__device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, const double* sig64, int n, int pitch,
-                                      double h, double omega, int bc, double shift, int i, int j, int adr_flags) {
+__device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, const double* sig64, int n, int ny,
+                                      int pitch, double h, double omega, int bc, double shift, int i, int j,
+                                      int adr_flags) {
     auto P = [&](int ii, int jj) { return phi64[(long long)jj * pitch + ii]; };
     const double pc = P(i, j);
     const double pw = i > 0 ? P(i - 1, j) : 2.0 * pc - P(i + 1, j);
     const double pe = i < n - 1 ? P(i + 1, j) : 2.0 * pc - P(i - 1, j);
     const double ps = j > 0 ? P(i, j - 1) : 2.0 * pc - P(i, j + 1);
-    const double pn = j < n - 1 ? P(i, j + 1) : 2.0 * pc - P(i, j - 1);
+    const double pn = j < ny - 1 ? P(i, j + 1) : 2.0 * pc - P(i, j - 1);
     const double px = (pe - pw) / (2.0 * h), py = (pn - ps) / (2.0 * h);
     const double lap = (pe + pw + pn + ps - 4.0 * pc) / (h * h);
     const long long p = (long long)j * pitch + i;
@@ -88,28 +90,28 @@ __device__ inline AdrCoef adr_coef_at(const double* phi64, const double* k64, co
         if (i == 0) ghost(c.cw, pe);
         if (i == n - 1) ghost(c.ce, pw);
         if (j == 0) ghost(c.cs, pn);
-        if (j == n - 1) ghost(c.cn, ps);
+        if (j == ny - 1) ghost(c.cn, ps);
     }
     return c;
 }
 
 template <typename T>
-__global__ void k_fields(const double* k64, const double* sig64, int n, int pitch, T* kf, T* sigf) {
+__global__ void k_fields(const double* k64, const double* sig64, int n, int ny, int pitch, T* kf, T* sigf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
+    if (i >= n || j >= ny) return;
     const long long p = (long long)j * pitch + i;
     kf[p] = (T)k64[p];
     if (sigf) sigf[p] = (T)sig64[p];
 }
 
 template <typename T>
-__global__ void k_adr_fields(const double* phi64, const double* k64, const double* sig64, int n, int pitch, double h,
-                             double omega, int bc, double shift, int adr_flags, quad<T>* out) {
+__global__ void k_adr_fields(const double* phi64, const double* k64, const double* sig64, int n, int ny, int pitch,
+                             double h, double omega, int bc, double shift, int adr_flags, quad<T>* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
-    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, pitch, h, omega, bc, shift, i, j, adr_flags);
+    if (i >= n || j >= ny) return;
+    AdrCoef c = adr_coef_at(phi64, k64, sig64, n, ny, pitch, h, omega, bc, shift, i, j, adr_flags);
     quad<T> q;
     q.x = (T)c.px;
     q.y = (T)c.py;
@@ -121,10 +123,10 @@ __global__ void k_adr_fields(const double* phi64, const double* k64, const doubl
 // exp(+i w phi) at level 2, argument and sincos in FP64 (Section 3.2, eq.
 // Rytov).
 template <typename T>
-__global__ void k_mod_field(const double* phi64, int n, int pitch, double omega, cplx<T>* mod) {
+__global__ void k_mod_field(const double* phi64, int n, int ny, int pitch, double omega, cplx<T>* mod) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n || j >= n) return;
+    if (i >= n || j >= ny) return;
     const long long p = (long long)j * pitch + i;
     double s, c;
     sincos(omega * phi64[p], &s, &c);

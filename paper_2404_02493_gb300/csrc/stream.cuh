@@ -29,12 +29,12 @@ struct StripGeo {
     int X0, y0, y1;                  // first loaded column, result rows [y0, y1)
 };
 
-__device__ __forceinline__ StripGeo strip_geo(int u, int nstrips, int RH, int n) {
+__device__ __forceinline__ StripGeo strip_geo(int u, int nstrips, int RH, int ny) {
     StripGeo g;
     const int k = u % nstrips, b = u / nstrips;
     g.X0 = SW_OUT * k - 4;
     g.y0 = RH * b;
-    g.y1 = min(g.y0 + RH, n);
+    g.y1 = min(g.y0 + RH, ny);
     return g;
 }
 
@@ -54,14 +54,14 @@ struct P2 {
 };
 template <typename T> __device__ __forceinline__ P2<T> p2zero() { return P2<T>{zero2<T>(), zero2<T>()}; }
 
-// Copy row r of an n x n array (pitch) into ring slot r & (DEP-1) of this
-// lane's two columns; zero outside the grid.
+// Copy row r of an array of ny rows of n (pitch) into ring slot r & (DEP-1)
+// of this lane's two columns; zero outside the grid.
 template <typename E>
-__device__ __forceinline__ void ring_issue(E* ring, const E* __restrict__ g, int n, int pitch, int X0, int r,
+__device__ __forceinline__ void ring_issue(E* ring, const E* __restrict__ g, int n, int ny, int pitch, int X0, int r,
                                            int lane) {
     E* slotp = ring + (r & (SW_DEP - 1)) * SW_COLS + 2 * lane;
     const int c0 = X0 + 2 * lane;
-    const bool rok = (unsigned)r < (unsigned)n;
+    const bool rok = (unsigned)r < (unsigned)ny;
     const long long base = (long long)r * pitch;
     const bool ok0 = rok && (unsigned)c0 < (unsigned)n, ok1 = rok && (unsigned)(c0 + 1) < (unsigned)n;
     cp_async_elem<E>(slotp, ok0 ? g + base + c0 : g, ok0);
