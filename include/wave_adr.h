@@ -144,6 +144,20 @@ typedef struct mg_params {
     long long workspace_limit; /* 0 (default): none; > 0: mg_setup fails with MG_ENOMEM, freeing what it
                                had allocated, when the handle's device workspace would exceed this many bytes
                                (for callers that share the GPU; mg_workspace_bytes reports the size) */
+    int roles[MG_MAX_LEVELS]; /* roles[l-1]: role of level l (MG_ROLE_*, declared below).  -1 (default): the
+                               role by index of Algorithm 1 (Jacobi on level 1, Chebyshev with the ADR
+                               corrections on level 2, nothing on level 3, Chebyshev below).  Levels 2..L-1
+                               take MG_ROLE_JACOBI, MG_ROLE_CHEB, MG_ROLE_NONE or MG_ROLE_CHEB_ADR; level 1 is
+                               always Jacobi (-1 or MG_ROLE_JACOBI); an instance's coarsest level takes the
+                               coarsest solve whatever its entry says.  The effective list (entries and the
+                               defaults of the others) has one MG_ROLE_CHEB_ADR level at most: the level of the
+                               M ADR corrections (their V-cycle runs from it down to L; its residual is
+                               demodulated and the correction modulated there).  The index rule assumes
+                               k h ~ 0.5 on level 1 (Section 3.1); a list lets a coarser or finer grid keep the
+                               smoothers on the levels whose k h they suit.  A handle with a list set runs
+                               every level with its own launches (the tails follow the index roles);
+                               Wave-Ray (ray = 1) and mg_cycle_backward need the index roles (MG_EINVAL,
+                               MG_EUNSUPPORTED) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2) on n x ny interior

@@ -38,6 +38,9 @@ class CycleParams:
     adr_scheme: str = "upwind"     # ADR convection: "upwind" (eq. upwind) | "central" (Fig. discremethod)
     adr_solver: str = "vcycle"     # ADR system: one V-cycle (Section 3.2.2) | "direct" (Fig. discremethod)
     adr_reaction: str = "continuous"  # eq. ADR's w^2(|grad phi|^2 - s^2) | "discrete" (5-point symbol; option)
+    # level -> "jacobi" | "cheb" | "none" | "cheb_adr" for levels 2..L-1 (level 1 is always Jacobi, level L
+    # the coarsest solve); missing levels take Algorithm 1's roles by index (2: cheb_adr, 3: none, >= 4: cheb)
+    roles: dict = field(default_factory=dict)
 
 
 def build_sizes(n: int, n_cmax: int):
@@ -129,6 +132,17 @@ class Hierarchy:
         f = self.levels[0]
         self.omega_j = (self.p.omega_jacobi if self.p.omega_jacobi is not None
                         else jacobi_weight_default(f.h, float(np.max(f.k))))
+        # damping of every Jacobi level: the same rule on the level's own h and max k
+        self.omega_jl = {1: self.omega_j}
+        for l in range(2, self.L):
+            if self.role(l) == "jacobi":
+                lev = self.levels[l - 1]
+                self.omega_jl[l] = (self.p.omega_jacobi if self.p.omega_jacobi is not None
+                                    else jacobi_weight_default(lev.h, float(np.max(lev.k))))
+        # the level of the ADR corrections (None: no ADR correction)
+        la = [l for l in range(2, self.L) if self.role(l) == "cheb_adr"]
+        assert len(la) <= 1, "one ADR-correction level at most"
+        self.la = la[0] if la else None
         self.lam_max = {}
         self.alpha = {}
         for l in range(2, self.L + 1):
@@ -145,7 +159,8 @@ class Hierarchy:
         # ADR sets of the corrections: one (the input phase) for Wave-ADR; for
         # Wave-Ray one per plane-wave direction theta_m = 2 pi m / M
         self.adr_sets = []
-        if self.p.adr and self.L >= 3:
+        if self.p.adr and self.la is not None:
+            la = self.la
             if self.p.ray:
                 m1 = max(n, ny) + 1
                 X, Y = np.meshgrid((np.arange(n) + 1) / m1, (np.arange(ny) + 1) / m1, indexing="xy")
@@ -163,21 +178,35 @@ class Hierarchy:
                     levs.append(dataclasses.replace(self.levels[l - 1], phi=pl))
                 pa = self.p
                 opt = (pa.adr_bc, pa.adr_scheme, pa.adr_reaction)
-                coefs = {l: adr_coefficients(levs[l - 1], *opt) for l in range(2, self.L + 1)}
-                mod = np.exp(1j * conv * omega * levs[1].phi)   # e^{+i conv w phi_2}
+                coefs = {l: adr_coefficients(levs[l - 1], *opt) for l in range(la, self.L + 1)}
+                mod = np.exp(1j * conv * omega * levs[la - 1].phi)   # e^{+i conv w phi} on the ADR level
                 lu = scipy.linalg.lu_factor(adr_sparse(levs[-1], *opt).toarray())
-                direct = (spla.splu(adr_sparse(levs[1], *opt).tocsc())
+                direct = (spla.splu(adr_sparse(levs[la - 1], *opt).tocsc())
                           if pa.adr_solver == "direct" else None)
                 self.adr_sets.append((coefs, mod, lu, direct))
             self.adr, self.mod, self.lu_adr = self.adr_sets[0][:3]
 
     # ------------------------------------------------------------ roles
-    def _uses_cheb(self, l: int) -> bool:
+    def role(self, l: int) -> str:
+        """Role of level l: Algorithm 1's by index (Jacobi on level 1,
+        Chebyshev with the ADR corrections on level 2, nothing on level 3,
+        Chebyshev below), or the schedule's role list for levels 2..L-1
+        (Section 3.1: the roles follow k h, which the paper's index rule
+        assumes to be about 0.5 on level 1); "coarse" on level L."""
+        if l == self.L:
+            return "coarse"
         if l == 1:
-            return False
+            return "jacobi"
+        if l in self.p.roles:
+            r = self.p.roles[l]
+            assert r in ("jacobi", "cheb", "none", "cheb_adr"), r
+            return r
+        return {2: "cheb_adr", 3: "none"}.get(l, "cheb")
+
+    def _uses_cheb(self, l: int) -> bool:
         if l == self.L:
             return self.p.coarse == "cheb"
-        return l != 3
+        return self.role(l) in ("cheb", "cheb_adr")
 
     def weights(self):
         """The smoother weights [omega_J, alpha_l for Chebyshev levels]."""
@@ -204,7 +233,7 @@ class Hierarchy:
         coarse-grid correction, exact solve on the coarsest level.  m: the
         ADR set (Wave-Ray direction)."""
         coefs, _, lu, direct = self.adr_sets[m]
-        if direct is not None and l == 2:
+        if direct is not None and l == self.la:
             return direct.solve(b.ravel()).reshape(b.shape)
         if l == self.L:
             return scipy.linalg.lu_solve(lu, b.ravel()).reshape(b.shape)
@@ -223,12 +252,12 @@ class Hierarchy:
         a = ADR cycle(r_hat); u <- u + a e^{+i conv w phi}.  Wave-Ray
         (Section 3.2): correction m uses the ray equation of plane wave m,
         i.e. phi_m = cos(theta_m) x + sin(theta_m) y."""
-        lev = self.lev(2)
+        lev = self.lev(self.la)
         for m in range(self.p.M):
             k = m if self.p.ray else 0
             mod = self.adr_sets[k][1]
             r = g2 - helmholtz_apply(lev, u2)
-            a = self.adr_vcycle(2, np.conj(mod) * r, k)
+            a = self.adr_vcycle(self.la, np.conj(mod) * r, k)
             u2 = u2 + mod * a
         return u2
 
@@ -237,10 +266,11 @@ class Hierarchy:
         lev = self.lev(l)
         if l == self.L:
             return self.coarse_helmholtz(u, g)
+        role = self.role(l)
         # pre-smoothing
-        if l == 1:
-            u = jacobi(lev, u, g, self.omega_j, self.p.jacobi_iters)
-        elif l != 3:
+        if role == "jacobi":
+            u = jacobi(lev, u, g, self.omega_jl[l], self.p.jacobi_iters)
+        elif role != "none":
             u = self.cheb(l, u, g, self.p.cheb_iters)
         # coarse-grid correction with zero initial guess
         r = g - helmholtz_apply(lev, u)
@@ -248,14 +278,12 @@ class Hierarchy:
         ec = self.cycle(np.zeros_like(rc), rc, l + 1)
         u = u + prolong(ec, lev.n, lev.rows)
         # post-smoothing
-        if l == 1:
-            u = jacobi(lev, u, g, self.omega_j, self.p.jacobi_iters)
-        elif l == 2:
+        if role == "jacobi":
+            u = jacobi(lev, u, g, self.omega_jl[l], self.p.jacobi_iters)
+        elif role != "none":
             u = self.cheb(l, u, g, self.p.cheb_iters)
-            if self.adr:
+            if role == "cheb_adr" and self.adr:
                 u = self.adr_correction(u, g)
-        elif l != 3:
-            u = self.cheb(l, u, g, self.p.cheb_iters)
         return u
 
     def residual(self, u, g):

@@ -39,7 +39,7 @@ class MgParams(ctypes.Structure):
         ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("tile_candidate", ctypes.c_int),
         ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int), ("tail_cluster", ctypes.c_int), ("ray", ctypes.c_int),
         ("fgmres_passes", ctypes.c_int), ("adr_bc", ctypes.c_int), ("adr_reaction", ctypes.c_int),
-        ("workspace_limit", ctypes.c_longlong),
+        ("workspace_limit", ctypes.c_longlong), ("roles", ctypes.c_int * MG_MAX_LEVELS),
     ]
 
 
@@ -179,6 +179,11 @@ def default_params(**kw) -> MgParams:
             p.adr_reaction = MG_ADR_REACTION[v]
         elif k == "coarse" and isinstance(v, str):
             p.coarse = {"lu": MG_COARSE_LU, "cheb": MG_COARSE_CHEB}[v]
+        elif k == "roles":
+            # {level: role name or MG_ROLE_* value}
+            names = {v_: k_ for k_, v_ in MG_ROLE.items()}
+            for l, r in v.items():
+                p.roles[l - 1] = names[r] if isinstance(r, str) else int(r)
         else:
             setattr(p, k, v)
     return p

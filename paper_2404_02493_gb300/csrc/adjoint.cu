@@ -1198,6 +1198,11 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
     if (H.prec != MG_PREC_FP64) { set_error("mg_cycle_backward: the adjoint needs an FP64 handle"); return MG_EUNSUPPORTED; }
     if (H.p.coarse != MG_COARSE_LU) { set_error("mg_cycle_backward: coarsest level must be the dense LU"); return MG_EUNSUPPORTED; }
     if (H.p.ray) { set_error("mg_cycle_backward: not available for Wave-Ray handles (no phase input)"); return MG_EUNSUPPORTED; }
+    for (int i = 0; i < MG_MAX_LEVELS; ++i)
+        if (H.p.roles[i] >= 0) {
+            set_error("mg_cycle_backward: needs the roles by index (no role list)");
+            return MG_EUNSUPPORTED;
+        }
     for (const InstHost& I : H.inst)
         if (I.ny != I.n) {
             set_error("mg_cycle_backward: square grids only (the adjoint kernels assume n x n levels)");

@@ -746,7 +746,7 @@ struct Engine : EngineBase {
     // Instance b runs levels l.. of the ADR V-cycle with per-level launches
     // (not the coarsest level, not in the coarse tail).
     static bool adr_per_level(Handle& H, int b, int l) {
-        return H.inst[b].L > l && !in_tail(H, b, l);
+        return H.inst[b].la > 0 && l >= H.inst[b].la && H.inst[b].L > l && !in_tail(H, b, l);
     }
     // Level l (not the coarsest) of instance b starts or lies in the coarse
     // tail: l >= 3, n_l <= tail_nmax and its vectors fit in one block's
@@ -787,14 +787,15 @@ struct Engine : EngineBase {
         if (!defer) gs_post(H, ds, SV1, SD, modulate ? 2 : 0, st);
     }
 
-    // Algorithm 1's ADR correction steps at level 2 (M times).
+    // Algorithm 1's ADR correction steps on the ADR level la (M times; level
+    // 2 with the roles by index).
     // Wave-Ray (H.p.ray): correction m uses the ADR levels of plane wave m.
-    void adr_corrections(Handle& H, const std::vector<int>& I, int M, cudaStream_t st) {
+    void adr_corrections(Handle& H, const std::vector<int>& I, int la, int M, cudaStream_t st) {
         for (int m = 0; m < M; ++m) {
             H.cur_var = H.p.ray ? m : 0;
-            const SegTable& t = H.seg(adescs(H, 2, I), false, kPts);
+            const SegTable& t = H.seg(adescs(H, la, I), false, kPts);
             LAUNCH(KK_RESDEMOD, t, 4 * C + R, k_resdemod<T>, 0);
-            adrv(H, 2, I, true, st);
+            adrv(H, la, I, true, st);
         }
         H.cur_var = 0;
     }
@@ -821,8 +822,18 @@ struct Engine : EngineBase {
             }
         }
         const std::vector<int> ds = descs(H, l, rest);
+        const int role = H.roles[l - 1];
+        if (role == MG_ROLE_JACOBI) {
+            // damped Jacobi from u = 0 (iterate to SX2) with the residual and
+            // its restriction, the coarse correction, then prolongation with
+            // the Jacobi post-sweep into SU
+            launch_restrict<MODE_JAC0>(H, ds, KK_RESTRICT_JAC0, 2 * C + R + C / 4, SX2, SG, SG, 1, st);
+            wave(H, l + 1, rest, st);
+            launch_prolong<PMODE_JAC>(H, ds, KK_PROLONG_JAC, 3 * C + C / 4 + R, SX2, SU, SG, SU, SU, 0, st);
+            return;
+        }
         const int q = H.p.cheb_iters;
-        const bool smooth = (l != 3);      // no smoothing on level 3 (Section 3.1.3)
+        const bool smooth = role != MG_ROLE_NONE;   // level 3 by index (Section 3.1.3)
         if (smooth) cheb_steps(H, ds, l, q, SU, true, st);
         launch_restrict<MODE_HELM>(H, ds, KK_RESTRICT_HELM, smooth ? 2 * C + R + C / 4 : C + C / 4, SU, SG,
                                    SG, smooth ? 0 : 1, st);
@@ -834,7 +845,7 @@ struct Engine : EngineBase {
         const int out = (cheb_launches(H, ds, l, q) & 1) ? SX2 : SU;
         launch_prolong<PMODE_ADD>(H, ds, KK_PROLONG_ADD, 2 * C + C / 4, SU, SU, SG, out, out, 0, st);
         cheb_steps(H, ds, l, q, out, false, st);
-        if (l == 2 && H.p.adr && H.p.M > 0) adr_corrections(H, rest, H.p.M, st);
+        if (role == MG_ROLE_CHEB_ADR) adr_corrections(H, rest, l, H.p.M, st);
     }
 
     std::vector<int> all(Handle& H) {

@@ -33,12 +33,14 @@ struct LevelHost {
     double2* inv_adr = nullptr;
     double lam_max = 0, alpha = 0;  // Chebyshev interval (levels with Chebyshev)
     double peclet = 0;              // ADR levels: omega h max(|phi_x|, |phi_y|) (condition: <= 1)
+    double omega_j = 0;             // Jacobi levels: the damping weight
     int cheb = 0;                   // uses Chebyshev smoothing
     int desc = -1;                  // index in the cycle descriptor table
 };
 
 struct InstHost {
     int n = 0, ny = 0, L = 0, bc = 0;   // fine grid: n nodes per row, ny rows
+    int la = 0;                     // level of the ADR corrections (0: none)
     int adr_flags = 0;              // ADR_ABC | ADR_DISC options of the ADR coefficients (see adr_coef_at)
     double omega = 0;
     double omega_j = 0;
@@ -99,6 +101,7 @@ struct Handle {
     std::map<std::string, TileChoice> tiles;  // per ADR launch (desc_key), from the autotuner
     std::map<std::string, int*> tail_first;   // per coarse-tail launch: first-level descriptors (device)
     int wave_tail_nmax = 0;                    // wave-cycle levels l >= 4 with n_l <= this run as the shared-memory tail
+    int roles[MAX_LEVELS] = {};                // effective role of level l (l >= 2, below an instance's coarsest)
     std::vector<void*> allocs;      // everything cudaMalloc'ed
     size_t alloc_bytes = 0;         // their total size
     long long alloc_limit = 0;      // mg_params.workspace_limit (0: none)

@@ -397,15 +397,36 @@ static std::vector<std::pair<int, int>> level_shapes(int n, int ny, int n_cmax) 
     return sh;
 }
 
-// Role of level l of L (Algorithm 1): Jacobi on level 1, Chebyshev with the
-// ADR corrections on level 2, nothing on level 3, Chebyshev below, the
-// coarsest-level solve on level L (which takes precedence).
+// Role of level l of L: the schedule's role list where set, else Algorithm
+// 1's by index (Jacobi on level 1, Chebyshev with the ADR corrections on
+// level 2, nothing on level 3, Chebyshev below); the coarsest-level solve on
+// level L takes precedence.  Without ADR corrections (adr = 0 or M = 0) an
+// ADR level smooths with Chebyshev only.
 static int level_role(int l, int L, const mg_params& p) {
     if (l == L) return p.coarse == MG_COARSE_CHEB ? MG_ROLE_COARSE_CHEB : MG_ROLE_COARSE_LU;
     if (l == 1) return MG_ROLE_JACOBI;
-    if (l == 3) return MG_ROLE_NONE;
-    if (l == 2 && p.adr && p.M > 0 && L >= 3) return MG_ROLE_CHEB_ADR;
-    return MG_ROLE_CHEB;
+    int r = p.roles[l - 1] >= 0 ? p.roles[l - 1] : (l == 2 ? MG_ROLE_CHEB_ADR : l == 3 ? MG_ROLE_NONE : MG_ROLE_CHEB);
+    if (r == MG_ROLE_CHEB_ADR && !(p.adr && p.M > 0)) r = MG_ROLE_CHEB;
+    return r;
+}
+static bool roles_set(const mg_params& p) {
+    for (int i = 0; i < MG_MAX_LEVELS; ++i)
+        if (p.roles[i] >= 0) return true;
+    return false;
+}
+// The role list is valid: level 1 Jacobi, levels >= 2 one of the four
+// smoothing roles, one ADR-correction level at most in the effective list.
+static bool roles_valid(const mg_params& p) {
+    if (p.roles[0] != -1 && p.roles[0] != MG_ROLE_JACOBI) return false;
+    int nadr = 0;
+    for (int l = 2; l <= MG_MAX_LEVELS; ++l) {
+        const int r = p.roles[l - 1];
+        if (r < -1 || (r >= 0 && r != MG_ROLE_JACOBI && r != MG_ROLE_CHEB && r != MG_ROLE_NONE &&
+                       r != MG_ROLE_CHEB_ADR))
+            return false;
+        nadr += (r == MG_ROLE_CHEB_ADR || (r < 0 && l == 2));
+    }
+    return nadr <= 1;
 }
 
 static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t st) {
@@ -439,7 +460,11 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         }
         H.Lmax = std::max(H.Lmax, I.L);
         I.lv.resize(I.L);
-        const bool adr = p.adr && I.L >= 3 && p.M > 0;
+        // the level of the ADR corrections (0: none)
+        I.la = 0;
+        for (int l = 2; l < I.L; ++l)
+            if (level_role(l, I.L, p) == MG_ROLE_CHEB_ADR) I.la = l;
+        const bool adr = I.la > 0;
         for (int l = 1; l <= I.L; ++l) {
             LevelHost& lv = I.lv[l - 1];
             lv.n = shapes[l - 1].first;
@@ -457,8 +482,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 lv.sig = H.alloc(npt * rsz(prec));
                 lv.sig64 = (double*)H.alloc(npt * 8);
             }
-            if (adr && l >= 2) lv.adr = H.alloc(npt * 2 * esz(prec));
-            if (adr && l == 2) lv.mod = H.alloc(npt * esz(prec));
+            if (adr && l >= I.la) lv.adr = H.alloc(npt * 2 * esz(prec));
+            if (adr && l == I.la) lv.mod = H.alloc(npt * esz(prec));
             if (l == I.L) {
                 const size_t N = (size_t)lv.n * lv.ny;
                 lv.inv_helm = (double2*)H.alloc(N * N * sizeof(double2));
@@ -606,18 +631,19 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             H.hdesc.push_back(d);
             // scalars
             double* s = hs.data() + (size_t)S::SIZE * di;
-            if (l == 1) {
+            const int role = level_role(l, I.L, p);
+            if (role == MG_ROLE_JACOBI) {
                 double kmax = 0;
-                // level-1 max k: from the FP64 field
+                // the level's max k: from the FP64 field
                 std::vector<double> kk((size_t)lv.ny * lv.pitch);
                 cudaMemcpyAsync(kk.data(), lv.k64, kk.size() * 8, cudaMemcpyDeviceToHost, st);
                 cudaStreamSynchronize(st);
                 for (int j = 0; j < lv.ny; ++j)
                     for (int i = 0; i < lv.n; ++i) kmax = std::max(kmax, kk[(size_t)j * lv.pitch + i]);
-                I.omega_j = p.omega_jacobi > 0 ? p.omega_jacobi : jacobi_default(lv.h, kmax);
-                s[S::OMEGA_J] = I.omega_j;
+                lv.omega_j = p.omega_jacobi > 0 ? p.omega_jacobi : jacobi_default(lv.h, kmax);
+                if (l == 1) I.omega_j = lv.omega_j;
+                s[S::OMEGA_J] = lv.omega_j;
             }
-            const int role = level_role(l, I.L, p);
             const bool cheb = role == MG_ROLE_CHEB || role == MG_ROLE_CHEB_ADR || role == MG_ROLE_COARSE_CHEB;
             lv.cheb = cheb;
             if (cheb) {
@@ -918,6 +944,7 @@ void mg_default_params(mg_params* p) {
     p->workspace_limit = 0;
     p->adr_bc = MG_ADR_BC_ZERO;
     p->adr_reaction = MG_ADR_REACTION_CONTINUOUS;
+    for (int i = 0; i < MG_MAX_LEVELS; ++i) p->roles[i] = -1;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -932,6 +959,15 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC ||
         p->adr_reaction < MG_ADR_REACTION_CONTINUOUS || p->adr_reaction > MG_ADR_REACTION_DISCRETE) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
+        return MG_EINVAL;
+    }
+    if (!roles_valid(*p)) {
+        set_error("mg_setup: role list: level 1 Jacobi, levels >= 2 MG_ROLE_JACOBI / CHEB / NONE / CHEB_ADR, "
+                  "one ADR-correction level at most");
+        return MG_EINVAL;
+    }
+    if (roles_set(*p) && p->ray) {
+        set_error("mg_setup: Wave-Ray corrections need the roles by index (no role list)");
         return MG_EINVAL;
     }
     for (int b = 0; b < ninst; ++b) {
@@ -958,6 +994,12 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
             mh->H.wave_tail_nmax = 0;
             mh->H.p.tail_nmax = 0;
         }
+    // so are the roles: with a role list every level has its own launches
+    if (roles_set(*p)) {
+        mh->H.wave_tail_nmax = 0;
+        mh->H.p.tail_nmax = 0;
+    }
+    for (int l = 2; l <= MG_MAX_LEVELS; ++l) mh->H.roles[l - 1] = level_role(l, MG_MAX_LEVELS + 1, *p);
     mh->H.prec = p->precision;
     mh->eng = (p->precision == MG_PREC_FP64) ? make_engine_f64() : make_engine_f32();
     // k and phi may be host memory: stage them on the device for the setup kernels
@@ -1031,14 +1073,14 @@ int mg_level_scalars(const mg_handle* h, int inst, int level, double* out, int n
     const InstHost& I = h->H.inst[inst];
     if (level < 1 || level > I.L) return MG_EINVAL;
     const LevelHost& lv = I.lv[level - 1];
-    double v[5] = {lv.lam_max, lv.alpha, I.omega_j, lv.h, lv.peclet};
+    double v[5] = {lv.lam_max, lv.alpha, lv.omega_j > 0 ? lv.omega_j : I.omega_j, lv.h, lv.peclet};
     int k = std::min(nout, 5);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
 }
 
 int mg_level_roles(int n, const mg_params* p, int* sizes, int* roles, int maxl) {
-    if (!p || n < 3 || p->n_cmax < 1 || maxl < 0 || (maxl > 0 && (!sizes || !roles))) {
+    if (!p || n < 3 || p->n_cmax < 1 || maxl < 0 || (maxl > 0 && (!sizes || !roles)) || !roles_valid(*p)) {
         set_error("mg_level_roles: bad argument");
         return MG_EINVAL;
     }
@@ -1475,15 +1517,17 @@ int mg_gmres3(mg_handle* h, int inst, int level, const void* b, void* x, int x_n
 int mg_adr_vcycle(mg_handle* h, int inst, const void* b, void* a, mg_stream stream) {
     int rc = check_level(h, inst, 2);
     if (rc) return rc;
-    if (!h->H.inst[inst].lv[1].adr) { set_error("mg_adr_vcycle: ADR disabled"); return MG_EINVAL; }
-    return run_op(h, inst, 2, OP_ADRV, 0, 0, {{SAB, b}}, 0, a, 0, -1, (cudaStream_t)stream);
+    const int la = h->H.inst[inst].la;
+    if (la == 0) { set_error("mg_adr_vcycle: ADR disabled"); return MG_EINVAL; }
+    return run_op(h, inst, la, OP_ADRV, 0, 0, {{SAB, b}}, 0, a, 0, -1, (cudaStream_t)stream);
 }
 
 int mg_adr_correction(mg_handle* h, int inst, void* u, const void* g, mg_stream stream) {
     int rc = check_level(h, inst, 2);
     if (rc) return rc;
-    if (!h->H.inst[inst].lv[1].adr) { set_error("mg_adr_correction: ADR disabled"); return MG_EINVAL; }
-    return run_op(h, inst, 2, OP_ADRCORR, 0, 0, {{SU, u}, {SG, g}}, 0, u, 0, -1, (cudaStream_t)stream);
+    const int la = h->H.inst[inst].la;
+    if (la == 0) { set_error("mg_adr_correction: ADR disabled"); return MG_EINVAL; }
+    return run_op(h, inst, la, OP_ADRCORR, 0, 0, {{SU, u}, {SG, g}}, 0, u, 0, -1, (cudaStream_t)stream);
 }
 
 int mg_coarse_solve(mg_handle* h, int inst, int which, const void* b, void* x, mg_stream stream) {

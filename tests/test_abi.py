@@ -93,3 +93,27 @@ def test_level_roles_rejects_bad_sizes(lib):
     p = binding.default_params()
     with pytest.raises(binding.MgError):
         binding.mg_level_roles(2, p)
+
+
+@pytest.mark.parametrize("n,roles", [(1023, {2: "jacobi", 3: "cheb_adr", 4: "none"}),
+                                     (255, {2: "cheb", 3: "none", 4: "cheb_adr"}),
+                                     (255, {2: "none", 4: "jacobi"})])
+def test_level_roles_follow_the_role_list(lib, n, roles):
+    """A role list (levels 2..L-1) replaces the index roles; the oracle's
+    hierarchy gives the same roles; the coarsest level keeps its solve."""
+    from oracle.cycle import CycleParams, Hierarchy
+    import synth
+    p = binding.default_params(n_cmax=15, roles=roles)
+    got = binding.mg_level_roles(n, p)
+    I = synth.config_constant(n=n, k=8.0)
+    H = Hierarchy(n, I.k, I.phi, I.omega, "abc1", CycleParams(n_cmax=15, roles=roles))
+    assert [r for _, r in got] == [H.role(l) if l < H.L else "coarse_lu" for l in range(1, H.L + 1)]
+
+
+@pytest.mark.parametrize("roles", [{1: "cheb"}, {3: "cheb_adr"}, {2: "coarse_lu"}, {2: "cheb_adr", 4: "cheb_adr"}])
+def test_level_roles_rejects_bad_lists(lib, roles):
+    """Level 1 is Jacobi; one ADR-correction level at most in the effective
+    list (level 2 by index unless set otherwise); only smoothing roles."""
+    p = binding.default_params(roles=roles)
+    with pytest.raises(binding.MgError):
+        binding.mg_level_roles(255, p)

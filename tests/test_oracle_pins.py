@@ -549,3 +549,33 @@ def test_peclet_number_closed_form():
                  phi=np.hypot(*[g - 0.5 for g in np.meshgrid((np.arange(127) + 1) / 128, (np.arange(127) + 1) / 128)]),
                  gamma=np.zeros((127, 127)), omega=omega, bc="abc1")
     assert peclet_number(lev2) <= 1.0
+
+
+def test_role_list_cycle_is_complex_symmetric_with_symmetric_smoothers():
+    """Without ADR corrections, with the same smoother before and after on
+    every level (damped Jacobi, S = I - w D^-1 A; Chebyshev, p(A^* A) with
+    A^-1 p(A A^*) = p(A^* A) A^-1; or none), R = P^T/4 and an exact
+    coarsest solve of the complex-symmetric re-discretised operator, the
+    cycle from zero is a complex-symmetric map B = B^T (recursively from the
+    two-grid identity A^-1 E^T = E A^-1).  This pins the role list's placement
+    of a Jacobi level below level 1 (its own weight, both sweeps) and the
+    transfer scaling; the ADR correction (L is not symmetric) breaks the
+    symmetry, which the test also checks."""
+    from oracle.cycle import CycleParams, Hierarchy
+    I = synth.config_lognormal(n=63, omega=20.0, seed=3)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(I.g.shape) + 1j * rng.standard_normal(I.g.shape)
+    y = rng.standard_normal(I.g.shape) + 1j * rng.standard_normal(I.g.shape)
+
+    def asym(roles, adr=False):
+        H = Hierarchy(63, I.k, I.phi, I.omega, "abc1", CycleParams(n_cmax=7, adr=adr, M=2, roles=roles))
+        z = np.zeros_like(x)
+        a = np.sum(y * H.cycle(z, x))
+        b = np.sum(x * H.cycle(z, y))
+        return abs(a - b) / abs(a)
+
+    assert asym({2: "jacobi", 3: "jacobi"}) < 1e-12
+    assert asym({2: "none", 3: "jacobi"}) < 1e-12
+    assert asym({2: "jacobi", 3: "cheb"}) < 1e-12
+    assert asym({}) < 1e-12
+    assert asym({}, adr=True) > 1e-6
