@@ -405,6 +405,11 @@ int mg_selftest_wait_timeout(mg_stream stream);
  * (n < 2, no node within r_init, bad pointers), MG_ENOMEM or MG_ECUDA. */
 int mg_eikonal(int n, const double* s, double x0, double y0, double r_init, double tol, int max_passes, double* tau,
                int* passes, mg_stream stream);
+/* The same on an n x ny grid (n nodes per row, ny rows; h = 1/(max(n, ny)+1),
+ * the spacing of mg_instance's non-square grids); mg_eikonal is the case
+ * ny = n.  MG_EINVAL also for ny < 2. */
+int mg_eikonal_rect(int n, int ny, const double* s, double x0, double y0, double r_init, double tol, int max_passes,
+                    double* tau, int* passes, mg_stream stream);
 
 /* ------------------------------------------------------------------------
  * Residual without allocation.  The paper has no counterpart of this entry

@@ -1,7 +1,8 @@
 """Oracle eikonal: the travel time tau with |grad tau| = s, tau(x0) = 0
 (Section 3.2, eq. eikeq), discretised by the first-order Godunov upwind
 scheme on the n x n interior grid (h = 1/(n+1), node (i, j) at
-((i+1)h, (j+1)h), arrays [j, i]).
+((i+1)h, (j+1)h), arrays [j, i]), or on n x ny nodes (ny rows) at the
+spacing h = 1/(max(n, ny)+1) of the non-square grids.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -29,15 +30,14 @@ INF = 1e300
 
 
 def _source_init(s: np.ndarray, x0: float, y0: float, r_init: float):
-    n = s.shape[0]
-    h = 1.0 / (n + 1)
-    x = (np.arange(n) + 1) * h
-    X, Y = np.meshgrid(x, x, indexing="xy")
+    ny, n = s.shape
+    h = 1.0 / (max(n, ny) + 1)
+    X, Y = np.meshgrid((np.arange(n) + 1) * h, (np.arange(ny) + 1) * h, indexing="xy")
     r = np.sqrt((X - x0) ** 2 + (Y - y0) ** 2)
     i0 = min(max(int(np.floor(x0 / h - 1.0 + 0.5)), 0), n - 1)
-    j0 = min(max(int(np.floor(y0 / h - 1.0 + 0.5)), 0), n - 1)
+    j0 = min(max(int(np.floor(y0 / h - 1.0 + 0.5)), 0), ny - 1)
     fixed = r <= r_init
-    tau = np.full((n, n), INF)
+    tau = np.full((ny, n), INF)
     tau[fixed] = s[j0, i0] * r[fixed]
     return tau, fixed, h
 
@@ -62,8 +62,7 @@ def eikonal(s: np.ndarray, x0: float, y0: float, r_init_h: float = 3.0, tol: flo
             max_iter: int = 100000) -> np.ndarray:
     """Fixed point of the Godunov discretisation (see the module docstring);
     nodes within r_init = r_init_h * h of the source are fixed."""
-    n = s.shape[0]
-    tau, fixed, h = _source_init(s, x0, y0, r_init_h / (n + 1))
+    tau, fixed, h = _source_init(s, x0, y0, r_init_h / (max(s.shape) + 1))
     if not fixed.any():
         raise ValueError("eikonal: no grid node within the initial radius")
     for _ in range(max_iter):

@@ -105,6 +105,7 @@ def load():
         "mg_workspace_bytes": (ctypes.c_longlong, [vp]),
         "mg_level_roles": (ip, [ip, ctypes.POINTER(MgParams), ctypes.POINTER(ip), ctypes.POINTER(ip), ip]),
         "mg_eikonal": (ip, [ip, vp, dp, dp, dp, dp, ip, vp, ctypes.POINTER(ip), vp]),
+        "mg_eikonal_rect": (ip, [ip, ip, vp, dp, dp, dp, dp, ip, vp, ctypes.POINTER(ip), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -123,7 +124,7 @@ def exported_symbols():
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
             "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
             "mg_tile_shapes", "mg_selftest_wait_timeout", "mg_peclet_flags",
-            "mg_workspace_bytes", "mg_level_roles", "mg_eikonal"]
+            "mg_workspace_bytes", "mg_level_roles", "mg_eikonal", "mg_eikonal_rect"]
 
 
 class MgError(RuntimeError):
@@ -264,6 +265,17 @@ def mg_eikonal(n, s, x0, y0, tau, r_init=None, tol=1e-12, max_passes=100000, str
                            _ptr(tau), ctypes.byref(np_), _stream(stream))
     if rc not in (MG_OK, MG_ENOTCONV):
         _check(rc, "mg_eikonal")
+    return rc, np_.value
+
+
+def mg_eikonal_rect(n, ny, s, x0, y0, tau, r_init=None, tol=1e-12, max_passes=100000, stream=None):
+    """The same on n x ny nodes (h = 1/(max(n, ny)+1)); r_init defaults to 3 h."""
+    r_init = 3.0 / (max(n, ny) + 1) if r_init is None else r_init
+    np_ = ctypes.c_int()
+    rc = load().mg_eikonal_rect(int(n), int(ny), _ptr(s), float(x0), float(y0), float(r_init), float(tol),
+                                int(max_passes), _ptr(tau), ctypes.byref(np_), _stream(stream))
+    if rc not in (MG_OK, MG_ENOTCONV):
+        _check(rc, "mg_eikonal_rect")
     return rc, np_.value
 
 

@@ -40,9 +40,9 @@ constexpr double EINF = 1e300;
 // Source initialisation: tau = s(x0) |x - x0| within r_init, inf elsewhere;
 // fixed[p] = 1 on those nodes.  Products and sums rounded separately (no
 // contraction), as the host generator and the oracle evaluate them.
-__global__ void k_eik_init(int n, double h, const double* __restrict__ s, double x0, double y0, double r_init,
-                           int i0, int j0, double* __restrict__ tau, unsigned char* __restrict__ fixed) {
-    const long long N = (long long)n * n;
+__global__ void k_eik_init(int n, int ny, double h, const double* __restrict__ s, double x0, double y0,
+                           double r_init, int i0, int j0, double* __restrict__ tau, unsigned char* __restrict__ fixed) {
+    const long long N = (long long)n * ny;
     const double s0 = s[(long long)j0 * n + i0];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p % n), j = (int)(p / n);
@@ -66,27 +66,27 @@ __device__ __forceinline__ double godunov_upd(double a, double b, double f) {
 // One pass over the active tiles (see the file comment).  act_in[t] != 0:
 // tile t changed in the previous pass; act_out[t] is set when it changes in
 // this one and *nchanged counts such tiles.
-__global__ void __launch_bounds__(32 * EW) k_eik_pass(int n, double h, const double* __restrict__ s,
+__global__ void __launch_bounds__(32 * EW) k_eik_pass(int n, int ny, double h, const double* __restrict__ s,
                                                       const unsigned char* __restrict__ fixed, double* tau,
                                                       const unsigned char* __restrict__ act_in,
                                                       unsigned char* __restrict__ act_out, unsigned* nchanged,
                                                       double tol, int reps) {
     __shared__ double Ts[EW][ET + 2][ET + 2];
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int ntx = (n + ET - 1) / ET;
+    const int ntx = (n + ET - 1) / ET, nty = (ny + ET - 1) / ET;
     const int t = blockIdx.x * EW + w;
-    if (t >= ntx * ntx) return;
+    if (t >= ntx * nty) return;
     const int tx = t % ntx, ty = t / ntx;
     bool active = act_in[t] != 0;
     if (!active) {
         active = (tx > 0 && act_in[t - 1]) || (tx < ntx - 1 && act_in[t + 1]) || (ty > 0 && act_in[t - ntx]) ||
-                 (ty < ntx - 1 && act_in[t + ntx]);
+                 (ty < nty - 1 && act_in[t + ntx]);
     }
     if (!active) return;                      // warp-uniform
     double (*T)[ET + 2] = Ts[w];
     const int gx0 = tx * ET, gy0 = ty * ET;
     auto G = [&](int gi, int gj) -> double {
-        return (gi >= 0 && gi < n && gj >= 0 && gj < n) ? __ldcg(&tau[(long long)gj * n + gi]) : EINF;
+        return (gi >= 0 && gi < n && gj >= 0 && gj < ny) ? __ldcg(&tau[(long long)gj * n + gi]) : EINF;
     };
     // interior and halo rows (lane = column), halo columns (lane = row)
     for (int r = -1; r <= ET; ++r) T[r + 1][lane + 1] = G(gx0 + lane, gy0 + r);
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(32 * EW) k_eik_pass(int n, double h, const dou
                 if (jj >= 0 && jj < ET) {
                     const int i = fwx ? ii : ET - 1 - ii, j = fwy ? jj : ET - 1 - jj;
                     const int gi = gx0 + i, gj = gy0 + j;
-                    if (gi < n && gj < n) {
+                    if (gi < n && gj < ny) {
                         const long long p = (long long)gj * n + gi;
                         if (!fixed[p]) {
                             const double a = fmin(T[j + 1][i], T[j + 1][i + 2]);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(32 * EW) k_eik_pass(int n, double h, const dou
     // write the interior back (also values that decreased by less than tol)
     for (int r = 0; r < ET; ++r) {
         const int gi = gx0 + lane, gj = gy0 + r;
-        if (gi < n && gj < n) {
+        if (gi < n && gj < ny) {
             const long long p = (long long)gj * n + gi;
             const double v = T[r + 1][lane + 1];
             if (v < __ldcg(&tau[p])) __stcg(&tau[p], v);
@@ -151,22 +151,22 @@ __global__ void __launch_bounds__(32 * EW) k_eik_pass(int n, double h, const dou
 
 using namespace wadr;
 
-extern "C" int mg_eikonal(int n, const double* s, double x0, double y0, double r_init, double tol, int max_passes,
-                          double* tau, int* passes, void* stream) {
-    if (n < 2 || n > 65535 || !s || !tau || !(r_init >= 0) || !(tol >= 0) || max_passes < 1 || !std::isfinite(x0) ||
-        !std::isfinite(y0)) {
+extern "C" int mg_eikonal_rect(int n, int ny, const double* s, double x0, double y0, double r_init, double tol,
+                               int max_passes, double* tau, int* passes, void* stream) {
+    if (n < 2 || n > 65535 || ny < 2 || ny > 65535 || !s || !tau || !(r_init >= 0) || !(tol >= 0) ||
+        max_passes < 1 || !std::isfinite(x0) || !std::isfinite(y0)) {
         set_error("mg_eikonal: bad argument");
         return MG_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const double h = 1.0 / (n + 1);
+    const double h = 1.0 / (std::max(n, ny) + 1);
     // s(x0) is taken at the node nearest to the source (per-axis rounding,
     // clamped: the nearest node of a regular grid); the fixed disc must
     // contain a node, as the host generator requires, and the nearest node is
     // the one to test
     int i0 = (int)std::floor(x0 / h - 1.0 + 0.5), j0 = (int)std::floor(y0 / h - 1.0 + 0.5);
     i0 = std::min(std::max(i0, 0), n - 1);
-    j0 = std::min(std::max(j0, 0), n - 1);
+    j0 = std::min(std::max(j0, 0), ny - 1);
     {
         const double dx = (i0 + 1) * h - x0, dy = (j0 + 1) * h - y0;
         if (!(std::sqrt(dx * dx + dy * dy) <= r_init)) {
@@ -174,8 +174,8 @@ extern "C" int mg_eikonal(int n, const double* s, double x0, double y0, double r
             return MG_EINVAL;
         }
     }
-    const size_t N = (size_t)n * n;
-    const int ntx = (n + ET - 1) / ET, ntiles = ntx * ntx;
+    const size_t N = (size_t)n * ny;
+    const int ntx = (n + ET - 1) / ET, ntiles = ntx * ((ny + ET - 1) / ET);
     auto is_dev = [](const void* q) {
         cudaPointerAttributes a;
         const bool d = cudaPointerGetAttributes(&a, q) == cudaSuccess &&
@@ -208,7 +208,7 @@ extern "C" int mg_eikonal(int n, const double* s, double x0, double y0, double r
         set_error("mg_eikonal: out of device memory");
         return MG_ENOMEM;
     }
-    k_eik_init<<<1216, 256, 0, st>>>(n, h, ds, x0, y0, r_init, i0, j0, dt, fixed);
+    k_eik_init<<<1216, 256, 0, st>>>(n, ny, h, ds, x0, y0, r_init, i0, j0, dt, fixed);
     cudaMemsetAsync(act, 1, (size_t)ntiles, st);            // every tile runs in the first pass
     const dim3 blk(32, EW);
     const unsigned nblk = (unsigned)((ntiles + EW - 1) / EW);
@@ -218,7 +218,7 @@ extern "C" int mg_eikonal(int n, const double* s, double x0, double y0, double r
         unsigned char* a_out = act + (size_t)((pass + 1) & 1) * ntiles;
         cudaMemsetAsync(a_out, 0, (size_t)ntiles, st);
         cudaMemsetAsync(cnt, 0, sizeof(unsigned), st);
-        k_eik_pass<<<nblk, blk, 0, st>>>(n, h, ds, fixed, dt, a_in, a_out, cnt, tol, 2);
+        k_eik_pass<<<nblk, blk, 0, st>>>(n, ny, h, ds, fixed, dt, a_in, a_out, cnt, tol, 2);
         cudaMemcpyAsync(hcnt, cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
@@ -244,4 +244,9 @@ extern "C" int mg_eikonal(int n, const double* s, double x0, double y0, double r
     if (passes) *passes = pass;
     if (rc != MG_OK) set_error("mg_eikonal: max_passes reached before no value changed by more than tol");
     return rc;
+}
+
+extern "C" int mg_eikonal(int n, const double* s, double x0, double y0, double r_init, double tol, int max_passes,
+                          double* tau, int* passes, void* stream) {
+    return mg_eikonal_rect(n, n, s, x0, y0, r_init, tol, max_passes, tau, passes, stream);
 }

@@ -642,8 +642,8 @@ struct Engine : EngineBase {
         return lim;
     }
     // The shared-memory tail holds the vectors of its first level n x n.
-    static bool ts_fits(int n) {
-        return n <= TS_MAXN && ts_up_smem<T>(n) <= ts_smem_limit() && ts_down_smem<T>(n) <= ts_smem_limit();
+    static bool ts_fits(int n, int ny) {
+        return n <= TS_MAXN && ts_up_smem<T>(n, ny) <= ts_smem_limit() && ts_down_smem<T>(n, ny) <= ts_smem_limit();
     }
 
     // Down / coarsest / up launches of the shared-memory tail for the
@@ -662,10 +662,10 @@ struct Engine : EngineBase {
         }
         long long sd = 0, su = 0, pts = 0;
         for (int b : tail) {
-            const int n = H.inst[b].lv[l - 1].n;
-            sd = std::max(sd, ts_down_smem<T>(n));
-            su = std::max(su, ts_up_smem<T>(n));
-            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].n;
+            const int n = H.inst[b].lv[l - 1].n, ny = H.inst[b].lv[l - 1].ny;
+            sd = std::max(sd, ts_down_smem<T>(n, ny));
+            su = std::max(su, ts_up_smem<T>(n, ny));
+            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].ny;
         }
         ts_smem_limit();
         const unsigned nb = (unsigned)tail.size();
@@ -703,8 +703,9 @@ struct Engine : EngineBase {
     // Level l (smoothed, l >= 4, not the coarsest) of instance b starts the
     // wave tail: n_l within the bound and its vectors fit one block.
     static bool in_wave_tail(Handle& H, int b, int l) {
-        const int n = H.inst[b].lv[l - 1].n;
-        return l >= 4 && H.inst[b].L > l && n <= H.wave_tail_nmax && n <= WT_MAXN && wt_smem<T>(n) <= wt_smem_limit();
+        const int n = H.inst[b].lv[l - 1].n, ny = H.inst[b].lv[l - 1].ny;
+        return l >= 4 && H.inst[b].L > l && std::max(n, ny) <= H.wave_tail_nmax && n <= WT_MAXN &&
+               wt_smem<T>(n, ny) <= wt_smem_limit();
     }
     // Down / coarsest / up launches of the wave tail for the instances in
     // `tail` (their level l is the first tail level).
@@ -722,8 +723,8 @@ struct Engine : EngineBase {
         }
         long long sm = 0, pts = 0;
         for (int b : tail) {
-            sm = std::max(sm, wt_smem<T>(H.inst[b].lv[l - 1].n));
-            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].n;
+            sm = std::max(sm, wt_smem<T>(H.inst[b].lv[l - 1].n, H.inst[b].lv[l - 1].ny));
+            for (int q = l; q < H.inst[b].L; ++q) pts += (long long)H.inst[b].lv[q - 1].n * H.inst[b].lv[q - 1].ny;
         }
         wt_smem_limit();
         const unsigned nb = (unsigned)tail.size();
@@ -749,11 +750,11 @@ struct Engine : EngineBase {
         return H.inst[b].la > 0 && l >= H.inst[b].la && H.inst[b].L > l && !in_tail(H, b, l);
     }
     // Level l (not the coarsest) of instance b starts or lies in the coarse
-    // tail: l >= 3, n_l <= tail_nmax and its vectors fit in one block's
-    // shared memory.
+    // tail: l >= 3 (below the ADR-correction level), max(n_l, ny_l) <=
+    // tail_nmax and its vectors fit in one block's shared memory.
     static bool in_tail(Handle& H, int b, int l) {
-        const int n = H.inst[b].lv[l - 1].n;
-        return l >= 3 && n <= H.p.tail_nmax && ts_fits(n);
+        const int n = H.inst[b].lv[l - 1].n, ny = H.inst[b].lv[l - 1].ny;
+        return l >= 3 && l > H.inst[b].la && std::max(n, ny) <= H.p.tail_nmax && ts_fits(n, ny);
     }
     // ADR V-cycle on levels l..L (Section 3.2.2), right-hand side in SAB of
     // level l, result in SAX (or, at level 2 with `modulate`, added as

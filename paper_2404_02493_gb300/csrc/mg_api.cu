@@ -987,14 +987,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     // the wave-cycle tail (tail_wave.cuh) follows an explicit tail_nmax; automatic: levels with n <= 63
     mh->H.wave_tail_nmax = mh->H.p.tail_nmax >= 0 ? mh->H.p.tail_nmax : 63;
     if (mh->H.p.tail_nmax < 0) mh->H.p.tail_nmax = ninst == 1 ? 31 : 0;
-    // the two tails are built for square levels: a handle with a non-square
-    // instance runs every level with its own launches
-    for (int b = 0; b < ninst; ++b)
-        if (inst[b].ny != 0 && inst[b].ny != inst[b].n) {
-            mh->H.wave_tail_nmax = 0;
-            mh->H.p.tail_nmax = 0;
-        }
-    // so are the roles: with a role list every level has its own launches
+    // the two tails follow the index roles: with a role list every level has
+    // its own launches
     if (roles_set(*p)) {
         mh->H.wave_tail_nmax = 0;
         mh->H.p.tail_nmax = 0;

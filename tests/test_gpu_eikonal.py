@@ -80,3 +80,17 @@ def test_device_eikonal_argument_errors_and_pass_limit():
         B.mg_eikonal(1, s, *x0, tau)
     with pytest.raises(B.MgError):          # no node within r_init of an off-node source
         B.mg_eikonal(63, s, 0.5 + 0.5 / 64, 0.5 + 0.5 / 64, tau, r_init=0.1 / 64)
+
+
+@pytest.mark.parametrize("n,ny", [(95, 47), (40, 129), (300, 70)])
+def test_device_eikonal_non_square_equals_oracle_fixed_point(n, ny):
+    """mg_eikonal_rect on n x ny nodes (tiles with ragged edges in both
+    directions) against the oracle's fixed point, a few ulps."""
+    s = 1.5 / synth.layered_speed(n, 5, ny=ny)
+    h = 1.0 / (max(n, ny) + 1)
+    x0 = (0.37 * (n + 1) * h, 0.61 * (ny + 1) * h)
+    ref = oracle_eikonal(s, *x0, tol=0.0)
+    tau = np.zeros_like(s)
+    st, passes = B.mg_eikonal_rect(n, ny, s, x0[0], x0[1], tau, tol=0.0)
+    assert st == B.MG_OK and passes >= 1
+    assert np.abs(tau - ref).max() <= 8 * np.finfo(float).eps * ref.max(), np.abs(tau - ref).max()

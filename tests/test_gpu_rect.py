@@ -292,3 +292,28 @@ def test_rect_setup_rejections():
                                     B._ptr(gb), B._ptr(gw), None, None)
     B.mg_destroy(h)
     assert rc == B.MG_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec,tail", [("fp64", 31), ("mixed", 63)])
+def test_rect_cycle_with_the_tails(prec, tail):
+    """The shared-memory ADR tail and wave tail on non-square levels (255 x 95
+    down to 7 x 2): the cycle equals the oracle's with fewer launches than
+    with every level launched on its own."""
+    n, ny = 255, 95
+    I = rect_inst(n, ny, "abc1", seed=15)
+    H = Hierarchy(n, I.k, I.phi, I.omega, "abc1", CycleParams(n_cmax=7, M=2), ny=ny)
+    spec = [(n, I.omega, I.k, I.phi, "abc1", ny)]
+    h = B.mg_setup(spec, B.default_params(precision=prec, n_cmax=7, M=2, tail_nmax=tail))
+    h0 = B.mg_setup(spec, B.default_params(precision=prec, n_cmax=7, M=2, tail_nmax=0))
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    u = (rnd(I.g.shape, 60) * 1e-3).astype(dt)
+    uu = u.copy()
+    B.mg_cycle(h, uu, I.g.astype(dt), 1)
+    u0 = u.copy()
+    B.mg_cycle(h0, u0, I.g.astype(dt), 1)
+    n_tail, n_plain = B.mg_cycle_launches(h), B.mg_cycle_launches(h0)
+    B.mg_destroy(h)
+    B.mg_destroy(h0)
+    assert n_tail < n_plain, (n_tail, n_plain)
+    ref = H.cycle(u.astype(np.complex128), I.g)
+    assert rel(uu.astype(np.complex128), ref) < (1e-12 if prec == "fp64" else 1e-5), rel(uu, ref)

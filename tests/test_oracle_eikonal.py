@@ -61,3 +61,21 @@ def test_oracle_eikonal_converges_to_the_linear_gradient_solution():
         errs.append(np.abs(tau - exact)[far].max())
     assert errs[-1] < 0.01 * np.abs(exact).max()
     assert errs[1] / errs[0] < 0.75 and errs[2] / errs[1] < 0.75, errs
+
+
+@pytest.mark.parametrize("n,ny", [(95, 47), (40, 129)])
+def test_oracle_eikonal_non_square_equals_fast_sweeping_fixed_point(n, ny):
+    """On n x ny nodes (h = 1/(max(n, ny)+1)) the Jacobi fixed point equals
+    the fast-sweeping generator's node by node, and on a constant medium the
+    row and column through a source on a node carry s |x - x0| exactly."""
+    s = 1.5 / synth.layered_speed(n, 5, ny=ny)
+    h = 1.0 / (max(n, ny) + 1)
+    x0 = (0.37 * (n + 1) * h, 0.61 * (ny + 1) * h)
+    a = eikonal(s, *x0, tol=0.0)
+    b = synth.eikonal(s, *x0, tol=1e-300, max_iter=10000)
+    assert a.shape == (ny, n)
+    assert np.abs(a - b).max() <= 4e-16 * a.max() * 8
+    sv, i0, j0 = 0.7, n // 3, ny // 2
+    tau = eikonal(np.full((ny, n), sv), (i0 + 1) * h, (j0 + 1) * h, tol=0.0)
+    np.testing.assert_allclose(tau[j0, :], sv * np.abs(np.arange(n) - i0) * h, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(tau[:, i0], sv * np.abs(np.arange(ny) - j0) * h, rtol=0, atol=1e-14)
