@@ -70,6 +70,31 @@ __device__ __forceinline__ void ring_issue2(E* ring, const E* __restrict__ g, in
         static_assert(2 * sizeof(E) == 8 || 2 * sizeof(E) == 16, "pair size");
 }
 
+// The lane's two elements of a ring row as one shared-memory load (the pair
+// of a complex row is 16 bytes at a 16-byte offset: every ring starts at a
+// multiple of 16 bytes of the block's dynamic shared memory).
+template <typename T>
+__device__ __forceinline__ P2<T> ring_pair(const cplx<T>* ring, int r, int lane) {
+    const cplx<T>* sp = ring + (r & (SW_DEP - 1)) * SW_COLS + 2 * lane;
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 v = *reinterpret_cast<const float4*>(sp);
+        return P2<T>{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    } else {
+        return P2<T>{sp[0], sp[1]};
+    }
+}
+
+// cp.async of `bytes` (the pair's size) from src into shared address sa,
+// src-size sz (0: zero fill, nothing is read)
+template <int BYTES>
+__device__ __forceinline__ void cp_pair(unsigned sa, const void* src, int sz) {
+    static_assert(BYTES == 8 || BYTES == 16, "pair size");
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(sz) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(sz) : "memory");
+}
+
 // Helmholtz diagonal (times h^2) of the lane's pair at row j
 template <typename T>
 __device__ __forceinline__ P2<T> diag_row(const LevelDesc& d, int j, int col, T k0, T k1, T sg0, T sg1) {
@@ -156,114 +181,148 @@ __global__ void __launch_bounds__(32 * cs_wpb<HS>()) k_cheb_stream(const __grid_
         const int col = X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const bool colint = X0 >= 1 && X0 + SW_COLS - 1 <= n - 2;   // all 64 columns in [1, n - 2]
+        // the lane's pair: its in-grid element count and its ring addresses
+        // (row slot 0); every field has the row pitch, so the copies of a row
+        // share the element offset r * pitch + col
+        const int cntc = cin0 ? min(2, n - col) : 0;
+        // the rings sit at fixed byte offsets from the warp's x ring: g and d
+        // one and two complex rings on, k three complex rings on, the sponge
+        // term one real ring after k
+        constexpr int CE = (int)sizeof(cplx<T>), RE = (int)sizeof(T);
+        constexpr unsigned RING_C = SW_DEP * SW_COLS * CE, RING_R = SW_DEP * SW_COLS * RE;
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(Xr);
+        const unsigned sxa = sbase + 2u * (unsigned)lane * CE;                // the lane's pair, x ring, slot 0
+        const unsigned ska = sbase + 3 * RING_C + 2u * (unsigned)lane * RE;   // the lane's pair, k ring, slot 0
         auto issue = [&](int r) {
-            if (!xzero) ring_issue2<cplx<T>>(Xr, xin, n, ny, pitch, X0, r, lane);
-            ring_issue2<cplx<T>>(Gr, gv, n, ny, pitch, X0, r, lane);
-            ring_issue2<T>(Kr, kf, n, ny, pitch, X0, r, lane);
-            if (HS) ring_issue2<T>(Sr, sgf, n, ny, pitch, X0, r, lane);
-            if (rd) ring_issue2<cplx<T>>(Dr, din, n, ny, pitch, X0, r, lane);
+            const int cnt = (unsigned)r < (unsigned)ny ? cntc : 0;
+            const long long off = cnt ? (long long)r * pitch + col : 0;
+            const unsigned so = (unsigned)((r & (SW_DEP - 1)) * SW_COLS);
+            const unsigned sc = sxa + so * CE;
+            const unsigned sr = ska + so * RE;
+            if (!xzero) cp_pair<2 * CE>(sc, xin + off, cnt * CE);
+            cp_pair<2 * CE>(sc + RING_C, gv + off, cnt * CE);
+            cp_pair<2 * RE>(sr, kf + off, cnt * RE);
+            if (HS) cp_pair<2 * RE>(sr + RING_R, sgf + off, cnt * RE);
+            if (rd) cp_pair<2 * CE>(sc + 2 * RING_C, din + off, cnt * CE);
         };
 #pragma unroll
         for (int r = 0; r < AH; ++r) {
             if (j0 + r <= j1) issue(j0 + r);
             cp_async_commit();
         }
-        // register windows (row offsets relative to the input row j)
-        P2<T> xa2 = p2zero<T>(), xa1 = p2zero<T>();   // x_m at j-2, j-1
-        P2<T> ta3 = p2zero<T>(), ta2 = p2zero<T>();   // t_m at j-3, j-2
-        P2<T> xb4 = p2zero<T>(), xb3 = p2zero<T>();   // x_{m+1} at j-4, j-3
-        P2<T> db4 = p2zero<T>(), db3 = p2zero<T>();   // d_m at j-4, j-3
-        P2<T> tb5 = p2zero<T>(), tb4 = p2zero<T>();   // t_{m+1} at j-5, j-4
+        // register windows of two rows (older, newer) relative to the input
+        // row j: x_m at j-2, j-1; t_m at j-3, j-2; x_{m+1} and d_m at j-4,
+        // j-3; t_{m+1} at j-5, j-4.  Rows alternate which register of a
+        // window holds the older row (the new row overwrites the older one),
+        // so a window advances without copies; the diagonal (rows j-4, j-3,
+        // j-2) shifts.
+        P2<T> xaP = p2zero<T>(), xaQ = p2zero<T>();
+        P2<T> taP = p2zero<T>(), taQ = p2zero<T>();
+        P2<T> xbP = p2zero<T>(), xbQ = p2zero<T>();
+        P2<T> dbP = p2zero<T>(), dbQ = p2zero<T>();
+        P2<T> tbP = p2zero<T>(), tbQ = p2zero<T>();
         P2<T> dg4 = p2zero<T>(), dg3 = p2zero<T>(), dg2 = p2zero<T>();   // diagonal at j-4, j-3, j-2
-        for (int j = j0; j <= j1; ++j) {
+        // one input row j; the O arguments hold the older row of each window
+        // on entry and the new row on return
+        auto row = [&](auto edge, int j, P2<T>& xa2, const P2<T>& xa1, P2<T>& ta3, const P2<T>& ta2, P2<T>& xb4,
+                       const P2<T>& xb3, P2<T>& db4, const P2<T>& db3, P2<T>& tb5, const P2<T>& tb4) {
+            constexpr bool E = decltype(edge)::value;
+            P2<T> x0 = p2zero<T>();
+            if (!xzero) x0 = ring_pair<T>(Xr, j, lane);
+            // the diagonal of row j - 1, used by every level on that row
+            const int r1 = j - 1;
+            T k0, k1, s0 = T(0), s1 = T(0);
+            ring_read<T>(Kr, r1, lane, k0, k1);
+            if (HS) ring_read<T>(Sr, r1, lane, s0, s1);
+            const P2<T> dg1 = E ? diag_row<T>(d, r1, col, k0, k1, s0, s1) : diag_in_row<T>(d, k0, k1, s0, s1);
+            // level 1: t_m = g - A x_m at row j - 1
+            const bool ro1 = (unsigned)r1 < (unsigned)ny;
+            P2<T> t1 = ring_pair<T>(Gr, r1, lane);
+            if (!xzero) {
+                const P2<T> ax = helm_row<T, false>(dg1, xa1, xa2, x0, ih2);
+                t1.v0 = csub<T>(t1.v0, ax.v0);
+                t1.v1 = csub<T>(t1.v1, ax.v1);
+            }
+            if constexpr (E) t1 = p2sel<T>(t1, ro1 && cin0, ro1 && cin1);
+            // level 2: d_m, x_{m+1} at row j - 2
+            const int r2 = j - 2;
+            const bool ro2 = (unsigned)r2 < (unsigned)ny;
+            const P2<T> sv = helm_row<T, true>(dg2, ta2, ta3, t1, ih2);
+            P2<T> dm{cscale<T>(sv.v0, c2a), cscale<T>(sv.v1, c2a)};
+            if (rd) {
+                const P2<T> dp = ring_pair<T>(Dr, r2, lane);
+                dm.v0 = cadd<T>(dm.v0, cscale<T>(dp.v0, c1a));
+                dm.v1 = cadd<T>(dm.v1, cscale<T>(dp.v1, c1a));
+            }
+            const P2<T> xm1{cadd<T>(xa2.v0, dm.v0), cadd<T>(xa2.v1, dm.v1)};
+            if constexpr (NS == 1) {
+                if (own && r2 >= y0 && r2 < y1) {
+                    const long long p = (long long)r2 * pitch + col;
+                    if (cin0) {
+                        xout[p] = xm1.v0;
+                        if (wd) dout[p] = dm.v0;
+                    }
+                    if (cin1) {
+                        xout[p + 1] = xm1.v1;
+                        if (wd) dout[p + 1] = dm.v1;
+                    }
+                }
+            } else {
+                const P2<T> xn = E ? p2sel<T>(xm1, ro2 && cin0, ro2 && cin1) : xm1;
+                const P2<T> dn = E ? p2sel<T>(dm, ro2 && cin0, ro2 && cin1) : dm;
+                // level 3: t_{m+1} = g - A x_{m+1} at row j - 3
+                const int r3 = j - 3;
+                const bool ro3 = (unsigned)r3 < (unsigned)ny;
+                P2<T> t2 = ring_pair<T>(Gr, r3, lane);
+                const P2<T> ax = helm_row<T, false>(dg3, xb3, xb4, xn, ih2);
+                t2.v0 = csub<T>(t2.v0, ax.v0);
+                t2.v1 = csub<T>(t2.v1, ax.v1);
+                if constexpr (E) t2 = p2sel<T>(t2, ro3 && cin0, ro3 && cin1);
+                // level 4: d_{m+1}, x_{m+2} at row j - 4
+                const int r4 = j - 4;
+                const P2<T> s2 = helm_row<T, true>(dg4, tb4, tb5, t2, ih2);
+                if (own && r4 >= y0 && r4 < y1) {
+                    const long long p = (long long)r4 * pitch + col;
+                    const cplx<T> e0 = cadd<T>(cscale<T>(s2.v0, c2b), cscale<T>(db4.v0, c1b));
+                    const cplx<T> e1 = cadd<T>(cscale<T>(s2.v1, c2b), cscale<T>(db4.v1, c1b));
+                    if (cin0) {
+                        xout[p] = cadd<T>(xb4.v0, e0);
+                        if (wd) dout[p] = e0;
+                    }
+                    if (cin1) {
+                        xout[p + 1] = cadd<T>(xb4.v1, e1);
+                        if (wd) dout[p + 1] = e1;
+                    }
+                }
+                tb5 = t2;
+                xb4 = xn;
+                db4 = dn;
+            }
+            ta3 = t1;
+            xa2 = x0;
+            dg4 = dg3; dg3 = dg2; dg2 = dg1;
+        };
+        // rows and columns strictly inside the grid (warp-uniform): no zero
+        // selects, no boundary terms in the diagonal
+        auto step = [&](int j, auto odd) {
             if (j + AH <= j1) issue(j + AH);
             cp_async_commit();
             cp_async_wait<AH>();
-            // rows and columns strictly inside the grid (warp-uniform): no zero
-            // selects, no boundary terms in the diagonal
-            auto row = [&](auto edge) {
-                constexpr bool E = decltype(edge)::value;
-                P2<T> x0 = p2zero<T>();
-                if (!xzero) ring_read<cplx<T>>(Xr, j, lane, x0.v0, x0.v1);
-                // the diagonal of row j - 1, used by every level on that row
-                const int r1 = j - 1;
-                T k0, k1, s0 = T(0), s1 = T(0);
-                ring_read<T>(Kr, r1, lane, k0, k1);
-                if (HS) ring_read<T>(Sr, r1, lane, s0, s1);
-                const P2<T> dg1 = E ? diag_row<T>(d, r1, col, k0, k1, s0, s1) : diag_in_row<T>(d, k0, k1, s0, s1);
-                // level 1: t_m = g - A x_m at row j - 1
-                const bool ro1 = (unsigned)r1 < (unsigned)ny;
-                P2<T> t1;
-                ring_read<cplx<T>>(Gr, r1, lane, t1.v0, t1.v1);
-                if (!xzero) {
-                    const P2<T> ax = helm_row<T, false>(dg1, xa1, xa2, x0, ih2);
-                    t1.v0 = csub<T>(t1.v0, ax.v0);
-                    t1.v1 = csub<T>(t1.v1, ax.v1);
-                }
-                if constexpr (E) t1 = p2sel<T>(t1, ro1 && cin0, ro1 && cin1);
-                // level 2: d_m, x_{m+1} at row j - 2
-                const int r2 = j - 2;
-                const bool ro2 = (unsigned)r2 < (unsigned)ny;
-                const P2<T> sv = helm_row<T, true>(dg2, ta2, ta3, t1, ih2);
-                P2<T> dm{cscale<T>(sv.v0, c2a), cscale<T>(sv.v1, c2a)};
-                if (rd) {
-                    P2<T> dp;
-                    ring_read<cplx<T>>(Dr, r2, lane, dp.v0, dp.v1);
-                    dm.v0 = cadd<T>(dm.v0, cscale<T>(dp.v0, c1a));
-                    dm.v1 = cadd<T>(dm.v1, cscale<T>(dp.v1, c1a));
-                }
-                const P2<T> xm1{cadd<T>(xa2.v0, dm.v0), cadd<T>(xa2.v1, dm.v1)};
-                if constexpr (NS == 1) {
-                    if (own && r2 >= y0 && r2 < y1) {
-                        const long long p = (long long)r2 * pitch + col;
-                        if (cin0) {
-                            xout[p] = xm1.v0;
-                            if (wd) dout[p] = dm.v0;
-                        }
-                        if (cin1) {
-                            xout[p + 1] = xm1.v1;
-                            if (wd) dout[p + 1] = dm.v1;
-                        }
-                    }
-                } else {
-                    const P2<T> xn = E ? p2sel<T>(xm1, ro2 && cin0, ro2 && cin1) : xm1;
-                    const P2<T> dn = E ? p2sel<T>(dm, ro2 && cin0, ro2 && cin1) : dm;
-                    // level 3: t_{m+1} = g - A x_{m+1} at row j - 3
-                    const int r3 = j - 3;
-                    const bool ro3 = (unsigned)r3 < (unsigned)ny;
-                    P2<T> t2;
-                    ring_read<cplx<T>>(Gr, r3, lane, t2.v0, t2.v1);
-                    const P2<T> ax = helm_row<T, false>(dg3, xb3, xb4, xn, ih2);
-                    t2.v0 = csub<T>(t2.v0, ax.v0);
-                    t2.v1 = csub<T>(t2.v1, ax.v1);
-                    if constexpr (E) t2 = p2sel<T>(t2, ro3 && cin0, ro3 && cin1);
-                    // level 4: d_{m+1}, x_{m+2} at row j - 4
-                    const int r4 = j - 4;
-                    const P2<T> s2 = helm_row<T, true>(dg4, tb4, tb5, t2, ih2);
-                    if (own && r4 >= y0 && r4 < y1) {
-                        const long long p = (long long)r4 * pitch + col;
-                        const cplx<T> e0 = cadd<T>(cscale<T>(s2.v0, c2b), cscale<T>(db4.v0, c1b));
-                        const cplx<T> e1 = cadd<T>(cscale<T>(s2.v1, c2b), cscale<T>(db4.v1, c1b));
-                        if (cin0) {
-                            xout[p] = cadd<T>(xb4.v0, e0);
-                            if (wd) dout[p] = e0;
-                        }
-                        if (cin1) {
-                            xout[p + 1] = cadd<T>(xb4.v1, e1);
-                            if (wd) dout[p + 1] = e1;
-                        }
-                    }
-                    tb5 = tb4; tb4 = t2;
-                    xb4 = xb3; xb3 = xn;
-                    db4 = db3; db3 = dn;
-                }
-                ta3 = ta2; ta2 = t1;
-                xa2 = xa1; xa1 = x0;
-                dg4 = dg3; dg3 = dg2; dg2 = dg1;
-            };
-            if (colint && j >= 3 && j <= ny - 1) row(std::false_type{});
-            else row(std::true_type{});
+            const bool in = colint && j >= 3 && j <= ny - 1;
+            if constexpr (decltype(odd)::value) {
+                if (in) row(std::false_type{}, j, xaQ, xaP, taQ, taP, xbQ, xbP, dbQ, dbP, tbQ, tbP);
+                else row(std::true_type{}, j, xaQ, xaP, taQ, taP, xbQ, xbP, dbQ, dbP, tbQ, tbP);
+            } else {
+                if (in) row(std::false_type{}, j, xaP, xaQ, taP, taQ, xbP, xbQ, dbP, dbQ, tbP, tbQ);
+                else row(std::true_type{}, j, xaP, xaQ, taP, taQ, xbP, xbQ, dbP, dbQ, tbP, tbQ);
+            }
+        };
+        int j = j0;
+        for (; j + 1 <= j1; j += 2) {
+            step(j, std::false_type{});
+            step(j + 1, std::true_type{});
         }
+        if (j <= j1) step(j, std::false_type{});
         cp_async_wait<0>();
         __syncwarp();
     }
