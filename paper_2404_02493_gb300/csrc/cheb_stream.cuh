@@ -70,31 +70,6 @@ __device__ __forceinline__ void ring_issue2(E* ring, const E* __restrict__ g, in
         static_assert(2 * sizeof(E) == 8 || 2 * sizeof(E) == 16, "pair size");
 }
 
-// The lane's two elements of a ring row as one shared-memory load (the pair
-// of a complex row is 16 bytes at a 16-byte offset: every ring starts at a
-// multiple of 16 bytes of the block's dynamic shared memory).
-template <typename T>
-__device__ __forceinline__ P2<T> ring_pair(const cplx<T>* ring, int r, int lane) {
-    const cplx<T>* sp = ring + (r & (SW_DEP - 1)) * SW_COLS + 2 * lane;
-    if constexpr (std::is_same<T, float>::value) {
-        const float4 v = *reinterpret_cast<const float4*>(sp);
-        return P2<T>{make_float2(v.x, v.y), make_float2(v.z, v.w)};
-    } else {
-        return P2<T>{sp[0], sp[1]};
-    }
-}
-
-// cp.async of `bytes` (the pair's size) from src into shared address sa,
-// src-size sz (0: zero fill, nothing is read)
-template <int BYTES>
-__device__ __forceinline__ void cp_pair(unsigned sa, const void* src, int sz) {
-    static_assert(BYTES == 8 || BYTES == 16, "pair size");
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(sz) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(sz) : "memory");
-}
-
 // Helmholtz diagonal (times h^2) of the lane's pair at row j
 template <typename T>
 __device__ __forceinline__ P2<T> diag_row(const LevelDesc& d, int j, int col, T k0, T k1, T sg0, T sg1) {

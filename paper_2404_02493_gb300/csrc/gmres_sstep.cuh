@@ -293,7 +293,7 @@ template <typename T> constexpr int gs_ring_bytes(int nq, int nc) {
     return (int)((nq * sizeof(quad<T>) + nc * sizeof(cplx<T>)) * GS_WPB * SW_DEP * SW_COLS);
 }
 template <typename T, int RH>
-__global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_constant__ KDesc A,
+__global__ void __launch_bounds__(32 * GS_WPB, sizeof(T) == 4 ? 4 : 1) k_gs_gram_stream(const __grid_constant__ KDesc A,
                                                                 const Seg* __restrict__ Sg, int nseg, int sr0) {
     extern __shared__ __align__(16) unsigned char gs_smem[];
     const int lane = threadIdx.x, warp = threadIdx.y;
@@ -319,23 +319,37 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_con
         const int col = gg.X0 + 2 * lane;
         const bool cin0 = (unsigned)col < (unsigned)n, cin1 = (unsigned)(col + 1) < (unsigned)n;
         const bool own = lane >= 2 && lane < 30;
+        // the lane's pair: its in-grid element count and ring addresses (row
+        // slot 0); K and the quads share the row offset r * pitch + col
+        const int cntc = cin0 ? min(2, n - col) : 0;
+        const unsigned sk = (unsigned)__cvta_generic_to_shared(Kr + 2 * lane);
+        const unsigned sq = (unsigned)__cvta_generic_to_shared(Qr + 2 * lane);
         auto issue = [&](int r) {
-            ring_issue<cplx<T>>(Kr, r0, n, ny, pitch, gg.X0, r, lane);
-            ring_issue<quad<T>>(Qr, coef, n, ny, pitch, gg.X0, r, lane);
+            const int cnt = (unsigned)r < (unsigned)ny ? cntc : 0;
+            const long long off = cnt ? (long long)r * pitch + col : 0;
+            const unsigned so = (unsigned)((r & (SW_DEP - 1)) * SW_COLS);
+            ring_issue_pair<cplx<T>>(sk + so * (unsigned)sizeof(cplx<T>), r0, off, cnt);
+            ring_issue_pair<quad<T>>(sq + so * (unsigned)sizeof(quad<T>), coef, off, cnt);
         };
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (j0 + r <= j1) issue(j0 + r);
             cp_async_commit();
         }
-        P2<T> a0 = p2zero<T>(), a1 = p2zero<T>(), a2 = p2zero<T>();
-        P2<T> b0 = p2zero<T>(), b1 = p2zero<T>(), c0w = p2zero<T>(), c1w = p2zero<T>();
-        for (int j = j0; j <= j1; ++j) {
+        // register windows of two rows (older, newer): K0 at j-2, j-1; K1 at
+        // j-3, j-2; K2 at j-4, j-3.  Rows alternate which register holds the
+        // older row (the new row overwrites it), so the windows advance
+        // without copies.  K0 at j-3 (the Gram terms' row) is read again from
+        // the ring.
+        P2<T> aP = p2zero<T>(), aQ = p2zero<T>();
+        P2<T> bP = p2zero<T>(), bQ = p2zero<T>();
+        P2<T> cP = p2zero<T>(), cQ = p2zero<T>();
+        auto row = [&](int j, P2<T>& a1, const P2<T>& a2, P2<T>& b0, const P2<T>& b1, P2<T>& c0w,
+                       const P2<T>& c1w) {
             if (j + 4 <= j1) issue(j + 4);
             cp_async_commit();
             cp_async_wait<4>();
-            P2<T> a3;
-            ring_read<cplx<T>>(Kr, j, lane, a3.v0, a3.v1);
+            const P2<T> a3 = ring_pair<T>(Kr, j, lane);
             quad<T> q0, q1;
             ring_read<quad<T>>(Qr, j - 1, lane, q0, q1);
             const bool r1 = (unsigned)(j - 1) < (unsigned)ny;
@@ -358,14 +372,22 @@ __global__ void __launch_bounds__(32 * GS_WPB) k_gs_gram_stream(const __grid_con
                     if (cin1) k2o[p + 1] = k2.v1;
                 }
                 if (r3) {
+                    // K0 at j - 3 (issued: j - 3 >= y0 > j0)
+                    const P2<T> a0 = ring_pair<T>(Kr, j - 3, lane);
                     if (cin0) gram_acc<T>(ac, a0.v0, b0.v0, c1w.v0, k3.v0);
                     if (cin1) gram_acc<T>(ac, a0.v1, b0.v1, c1w.v1, k3.v1);
                 }
             }
-            a0 = a1; a1 = a2; a2 = a3;
-            b0 = b1; b1 = k1;
-            c0w = c1w; c1w = k2;
+            a1 = a3;
+            b0 = k1;
+            c0w = k2;
+        };
+        int j = j0;
+        for (; j + 1 <= j1; j += 2) {
+            row(j, aP, aQ, bP, bQ, cP, cQ);
+            row(j + 1, aQ, aP, bQ, bP, cQ, cP);
         }
+        if (j <= j1) row(j, aP, aQ, bP, bQ, cP, cQ);
         cp_async_wait<0>();
         __syncwarp();
     }

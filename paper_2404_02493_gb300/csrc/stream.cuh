@@ -16,6 +16,8 @@
 // by eight columns (read from L2).  Columns and rows outside the grid hold
 // zero (cp.async zero fill for inputs; results forced to zero).
 #pragma once
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace wadr {
@@ -67,6 +69,53 @@ __device__ __forceinline__ void ring_issue(E* ring, const E* __restrict__ g, int
     cp_async_elem<E>(slotp, ok0 ? g + base + c0 : g, ok0);
     cp_async_elem<E>(slotp + 1, ok1 ? g + base + c0 + 1 : g, ok1);
 }
+// The lane's two elements of a ring row as one shared-memory load (the pair
+// of a complex row is 16 bytes at a 16-byte offset: every ring starts at a
+// multiple of 16 bytes of the block's dynamic shared memory).
+template <typename T>
+__device__ __forceinline__ P2<T> ring_pair(const cplx<T>* ring, int r, int lane) {
+    const cplx<T>* sp = ring + (r & (SW_DEP - 1)) * SW_COLS + 2 * lane;
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 v = *reinterpret_cast<const float4*>(sp);
+        return P2<T>{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    } else {
+        return P2<T>{sp[0], sp[1]};
+    }
+}
+
+// cp.async of `bytes` (the pair's size) from src into shared address sa,
+// src-size sz (0: zero fill, nothing is read)
+template <int BYTES>
+__device__ __forceinline__ void cp_pair(unsigned sa, const void* src, int sz) {
+    static_assert(BYTES == 8 || BYTES == 16, "pair size");
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(sz) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(sz) : "memory");
+}
+
+// The lane's pair of a row (cnt = 0, 1 or 2 of its elements in the grid, the
+// rest zero-filled) into the ring at shared address sa (the pair's slot):
+// one 16-byte copy for 8-byte elements, 16-byte pieces of each element
+// otherwise.  src = base + off is the pair's first element (off even: the
+// pair starts at a 16-byte boundary of a row whose pitch is a multiple of 32).
+template <typename E>
+__device__ __forceinline__ void ring_issue_pair(unsigned sa, const E* __restrict__ base, long long off, int cnt) {
+    static_assert(sizeof(E) == 8 || sizeof(E) % 16 == 0, "element size");
+    if constexpr (sizeof(E) == 8) {
+        cp_pair<16>(sa, base + off, cnt * 8);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const bool ok = cnt > e;
+            const char* src = reinterpret_cast<const char*>(ok ? base + off + e : base);
+#pragma unroll
+            for (int pc = 0; pc < (int)sizeof(E) / 16; ++pc)
+                cp_pair<16>(sa + (unsigned)(e * (int)sizeof(E) + 16 * pc), src + 16 * pc, ok ? 16 : 0);
+        }
+    }
+}
+
 template <typename E>
 __device__ __forceinline__ void ring_read(const E* ring, int r, int lane, E& a, E& b) {
     const E* slotp = ring + (r & (SW_DEP - 1)) * SW_COLS + 2 * lane;
