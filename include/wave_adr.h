@@ -158,6 +158,10 @@ typedef struct mg_params {
                                every level with its own launches (the tails follow the index roles);
                                Wave-Ray (ray = 1) and mg_cycle_backward need the index roles (MG_EINVAL,
                                MG_EUNSUPPORTED) */
+    double sponge_width;    /* MG_BC_SPONGE: width of the damping layer in shortest wavelengths 2 pi / omega
+                               (default 1; > 0) */
+    double sponge_power;    /* MG_BC_SPONGE: exponent of the profile gamma(d) = omega ((W - d) / W)^power,
+                               d < W the distance to the boundary, W the layer width (default 2; > 0) */
 } mg_params;
 
 /* One Helmholtz problem -Lap u - k^2 u = g (Section 2) on n x ny interior

@@ -41,6 +41,8 @@ class CycleParams:
     # level -> "jacobi" | "cheb" | "none" | "cheb_adr" for levels 2..L-1 (level 1 is always Jacobi, level L
     # the coarsest solve); missing levels take Algorithm 1's roles by index (2: cheb_adr, 3: none, >= 4: cheb)
     roles: dict = field(default_factory=dict)
+    sponge_width: float = 1.0      # sponge layer width in shortest wavelengths 2 pi / omega
+    sponge_power: float = 2.0      # exponent of the sponge profile
 
 
 def build_sizes(n: int, n_cmax: int):
@@ -119,7 +121,8 @@ class Hierarchy:
         ny = ny or n
         shapes = build_shapes(n, ny, self.p.n_cmax)
         self.L = len(shapes)
-        gamma = sponge_gamma(n, omega, ny) if bc == "sponge" else np.zeros((ny, n))
+        gamma = (sponge_gamma(n, omega, ny, self.p.sponge_width, self.p.sponge_power) if bc == "sponge"
+                 else np.zeros((ny, n)))
         self.levels: list[Level] = []
         kk, ph, ga = np.asarray(k, float), np.asarray(phi, float), gamma
         assert kk.shape == (ny, n) and ph.shape == (ny, n)

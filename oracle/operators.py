@@ -49,12 +49,14 @@ def missing_neighbours(n: int, ny: int | None = None) -> np.ndarray:
     return m
 
 
-def sponge_gamma(n: int, omega: float, ny: int | None = None) -> np.ndarray:
+def sponge_gamma(n: int, omega: float, ny: int | None = None, width: float = 1.0,
+                 power: float = 2.0) -> np.ndarray:
     """Sponge damping mask (Section 2, eq. sponge): zero inside, rising to
-    omega at the boundary over one wavelength W = 2*pi/omega.  The printed
-    text fixes neither the shape nor the exact width; we take
-    gamma(d) = omega * ((W - d)/W)^2 for d < W, d = distance to the boundary
-    of the domain [0, (n+1)h] x [0, (ny+1)h]."""
+    omega at the boundary over `width` wavelengths, W = width * 2*pi/omega.
+    The printed text fixes neither the shape nor the exact width; we take
+    gamma(d) = omega * ((W - d)/W)^power for d < W (default: one wavelength,
+    power 2), d = distance to the boundary of the domain
+    [0, (n+1)h] x [0, (ny+1)h]."""
     ny = ny or n
     h = grid_spacing(n, ny)
     x = (np.arange(n) + 1.0) * h
@@ -64,8 +66,9 @@ def sponge_gamma(n: int, omega: float, ny: int | None = None) -> np.ndarray:
     lx = 1.0 if n == m else (n + 1) * h     # the longer side has unit length
     ly = 1.0 if ny == m else (ny + 1) * h
     d = np.minimum(np.minimum(X, lx - X), np.minimum(Y, ly - Y))
-    W = 2 * np.pi / omega
-    return np.where(d < W, omega * ((W - d) / W) ** 2, 0.0)
+    W = width * (2 * np.pi / omega) if width != 1.0 else 2 * np.pi / omega
+    t = (W - d) / W
+    return np.where(d < W, omega * (t ** 2 if power == 2.0 else np.abs(t) ** power), 0.0)
 
 
 def helmholtz_diag(lev: Level) -> np.ndarray:

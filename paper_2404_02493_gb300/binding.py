@@ -40,6 +40,7 @@ class MgParams(ctypes.Structure):
         ("tail_nmax", ctypes.c_int), ("pdl", ctypes.c_int), ("tail_cluster", ctypes.c_int), ("ray", ctypes.c_int),
         ("fgmres_passes", ctypes.c_int), ("adr_bc", ctypes.c_int), ("adr_reaction", ctypes.c_int),
         ("workspace_limit", ctypes.c_longlong), ("roles", ctypes.c_int * MG_MAX_LEVELS),
+        ("sponge_width", ctypes.c_double), ("sponge_power", ctypes.c_double),
     ]
 
 

@@ -169,8 +169,9 @@ EngineBase* make_engine_f64();
 // (n nodes per row, ny rows, row pitch `pitch`)
 void setup_plane_phase(double* phi64, int n, int ny, int pitch, double h1, int scale, double cx, double cy,
                        cudaStream_t st);
-void setup_inject(const double* k_fine, const double* phi_fine, int n1, int ny1, double omega, int bc, int level,
-                  double* k64, double* phi64, double* sig64, int n, int ny, int pitch, cudaStream_t st);
+void setup_inject(const double* k_fine, const double* phi_fine, int n1, int ny1, double omega, int bc,
+                  double sponge_width, double sponge_power, int level, double* k64, double* phi64, double* sig64, int n,
+                  int ny, int pitch, cudaStream_t st);
 double setup_lambda_max(const double* k64, const double* sig64, int n, int ny, int pitch, double h, int bc,
                         double shift, double* dscratch, cudaStream_t st);
 double setup_adr_scale(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,

@@ -553,8 +553,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
         InstHost& I = H.inst[b];
         for (int l = 1; l <= I.L; ++l) {
             LevelHost& lv = I.lv[l - 1];
-            setup_inject(in[b].k, in[b].phi, I.n, I.ny, I.omega, I.bc, l, lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny,
-                         lv.pitch, st);
+            setup_inject(in[b].k, in[b].phi, I.n, I.ny, I.omega, I.bc, p.sponge_width, p.sponge_power, l, lv.k64,
+                         lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, st);
         }
         if (p.ray && I.lv.size() >= 2 && I.lv[1].adr) {
             // Wave-Ray: correction m (0-based here) uses phi_m = cos(theta) x + sin(theta) y,
@@ -945,6 +945,8 @@ void mg_default_params(mg_params* p) {
     p->adr_bc = MG_ADR_BC_ZERO;
     p->adr_reaction = MG_ADR_REACTION_CONTINUOUS;
     for (int i = 0; i < MG_MAX_LEVELS; ++i) p->roles[i] = -1;
+    p->sponge_width = 1.0;
+    p->sponge_power = 2.0;
 }
 
 int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_params* p, mg_stream stream) {
@@ -957,7 +959,8 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
         p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster != 0 || p->tail_nmax < -1 || p->ray < 0 ||
         p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3 || p->workspace_limit < 0 ||
         p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC ||
-        p->adr_reaction < MG_ADR_REACTION_CONTINUOUS || p->adr_reaction > MG_ADR_REACTION_DISCRETE) {
+        p->adr_reaction < MG_ADR_REACTION_CONTINUOUS || p->adr_reaction > MG_ADR_REACTION_DISCRETE ||
+        !(p->sponge_width > 0 && p->sponge_width < 1e6) || !(p->sponge_power > 0 && p->sponge_power < 1e3)) {
         set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
         return MG_EINVAL;
     }

@@ -16,8 +16,8 @@ namespace wadr {
 // I of level l sits on fine node 2^(l-1) (I+1) - 1 (Algorithm 1's
 // re-discretised operator A_H; coefficients sampled at coinciding nodes).
 __global__ void k_inject(const double* __restrict__ kf, const double* __restrict__ pf, int n1, int ny1,
-                         double omega, int bc, int level, double* k64, double* phi64, double* sig64, int n, int ny,
-                         int pitch) {
+                         double omega, int bc, double swidth, double spower, int level, double* k64, double* phi64,
+                         double* sig64, int n, int ny, int pitch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= n || j >= ny) return;
@@ -28,7 +28,8 @@ __global__ void k_inject(const double* __restrict__ kf, const double* __restrict
     k64[p] = k;
     phi64[p] = pf[q];
     if (sig64) {
-        // sponge mask: gamma(d) = omega ((W-d)/W)^2 for d < W = 2 pi/omega,
+        // sponge mask: gamma(d) = omega ((W-d)/W)^p for d < W = width 2 pi/omega
+        // (default one wavelength, p = 2),
         // d = distance of the fine node to the boundary of [0, lx] x [0, ly]
         // (the longer side has unit length, h1 = 1/(max(n1, ny1)+1));
         // sig = omega gamma s^2
@@ -37,16 +38,19 @@ __global__ void k_inject(const double* __restrict__ kf, const double* __restrict
         const double lx = n1 == m1 ? 1.0 : (n1 + 1) * h1, ly = ny1 == m1 ? 1.0 : (ny1 + 1) * h1;
         const double x = (fi + 1) * h1, y = (fj + 1) * h1;
         const double dist = fmin(fmin(x, lx - x), fmin(y, ly - y));
-        const double W = 2.0 * M_PI / omega;
-        const double gam = dist < W ? omega * ((W - dist) / W) * ((W - dist) / W) : 0.0;
+        const double W = swidth == 1.0 ? 2.0 * M_PI / omega : swidth * (2.0 * M_PI / omega);
+        const double t = (W - dist) / W;
+        const double gam = dist < W ? (spower == 2.0 ? omega * t * t : omega * pow(t, spower)) : 0.0;
         sig64[p] = omega * gam * (k / omega) * (k / omega);
     }
 }
 
-void setup_inject(const double* k_fine, const double* phi_fine, int n1, int ny1, double omega, int bc, int level,
-                  double* k64, double* phi64, double* sig64, int n, int ny, int pitch, cudaStream_t st) {
+void setup_inject(const double* k_fine, const double* phi_fine, int n1, int ny1, double omega, int bc,
+                  double sponge_width, double sponge_power, int level, double* k64, double* phi64, double* sig64, int n,
+                  int ny, int pitch, cudaStream_t st) {
     dim3 b(32, 8), g((n + 31) / 32, (ny + 7) / 8);
-    k_inject<<<g, b, 0, st>>>(k_fine, phi_fine, n1, ny1, omega, bc, level, k64, phi64, sig64, n, ny, pitch);
+    k_inject<<<g, b, 0, st>>>(k_fine, phi_fine, n1, ny1, omega, bc, sponge_width, sponge_power, level, k64, phi64,
+                              sig64, n, ny, pitch);
 }
 
 // Wave-Ray plane-wave phase cx x + cy y on level l (scale = 2^(l-1), h1 the

@@ -317,3 +317,18 @@ def test_rect_cycle_with_the_tails(prec, tail):
     assert n_tail < n_plain, (n_tail, n_plain)
     ref = H.cycle(u.astype(np.complex128), I.g)
     assert rel(uu.astype(np.complex128), ref) < (1e-12 if prec == "fp64" else 1e-5), rel(uu, ref)
+
+
+@pytest.mark.parametrize("n,ny,width,power", [(127, 127, 1.5, 3.0), (127, 63, 0.5, 1.0)])
+def test_sponge_profile_parameters_cycle(n, ny, width, power):
+    """A sponge layer of another width and exponent (mg_params.sponge_width,
+    sponge_power): the FP64 cycle equals the oracle's with the same profile."""
+    I = rect_inst(n, ny, "sponge", seed=16)
+    ex = {"sponge_width": width, "sponge_power": power}
+    H = Hierarchy(n, I.k, I.phi, I.omega, "sponge", CycleParams(n_cmax=7, M=2, **ex), ny=ny)
+    h = B.mg_setup([(n, I.omega, I.k, I.phi, "sponge", ny)], B.default_params(precision="fp64", n_cmax=7, M=2, **ex))
+    u = rnd(I.g.shape, 70) * 1e-3
+    uu = u.copy()
+    B.mg_cycle(h, uu, I.g.copy(), 1)
+    B.mg_destroy(h)
+    assert rel(uu, H.cycle(u, I.g)) < 1e-12

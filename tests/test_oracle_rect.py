@@ -150,3 +150,20 @@ def test_rect_fgmres_converges_to_the_assembled_solution():
     A = _kron_helmholtz(n, ny, h, k)
     r = g.ravel() - A @ u.ravel()
     assert np.linalg.norm(r) < 1.01e-8 * np.linalg.norm(g)
+
+
+def test_sponge_profile_parameters():
+    """The sponge profile's width (in wavelengths) and exponent: a layer of w
+    wavelengths at frequency omega is w times the one-wavelength layer at
+    omega / w (W = w 2 pi / omega = 2 pi / (omega / w)); power 1 gives the
+    linear ramp; the defaults are the one-wavelength quadratic profile."""
+    n, ny, w = 95, 63, 80.0
+    base = sponge_gamma(n, w, ny)
+    assert np.array_equal(sponge_gamma(n, w, ny, 1.0, 2.0), base)
+    for width in (0.5, 1.5, 2.0):
+        assert np.allclose(sponge_gamma(n, w, ny, width, 2.0), width * sponge_gamma(n, w / width, ny),
+                           rtol=1e-13, atol=1e-13 * w)
+    lin = sponge_gamma(n, w, ny, 1.0, 1.0)
+    nz = base > 0
+    assert np.allclose(lin[nz] ** 2, w * base[nz], rtol=1e-12)
+    assert np.array_equal(lin > 0, nz)
