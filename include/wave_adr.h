@@ -88,7 +88,10 @@ typedef struct mg_params {
     int precision;          /* MG_PREC_FP64 | MG_PREC_MIXED (complex-FP32 cycle, FP64 outer) */
     int n_cmax;             /* coarsen while max(n, ny) > n_cmax (default 15); coarsest n ny <= 1024 and
                                both sides >= 2 */
-    int jacobi_iters;       /* 1 */
+    int jacobi_iters;       /* damped Jacobi sweeps before and after on a Jacobi level (1, Algorithm 1; 1..16).
+                               One sweep fuses into the residual/restriction and prolongation passes (and, on
+                               level 1 inside FGMRES, into the basis-vector reads and the matvec); with more
+                               the sweeps are passes of their own */
     int cheb_iters;         /* 5 (<= 16) */
     int coarse;             /* MG_COARSE_LU (dense FP64 LU) | MG_COARSE_CHEB (Algorithm 1, q=10) */
     int coarse_cheb_iters;  /* 10 */

@@ -320,7 +320,7 @@ struct Engine : EngineBase {
     bool fg_want = false, fg_fused = false, fg_gvec = false;
     // the level-1 passes of the cycle stream (FP32, launch of >= CS_MIN_POINTS)
     static bool level1_streams(Handle& H, const std::vector<int>& ds1) {
-        if (!kStream) return false;
+        if (!kStream || H.p.jacobi_iters != 1) return false;
         long long pts = 0;
         for (int q : ds1) pts += (long long)H.hdesc[(size_t)q].n * H.hdesc[(size_t)q].ny;
         return pts >= CS_MIN_POINTS;
@@ -824,6 +824,10 @@ struct Engine : EngineBase {
         }
         const std::vector<int> ds = descs(H, l, rest);
         const int role = H.roles[l - 1];
+        if (role == MG_ROLE_JACOBI && H.p.jacobi_iters > 1) {
+            jacobi_level_nu(H, ds, H.p.jacobi_iters, -1, SX2, SU, SD, [&] { wave(H, l + 1, rest, st); }, st);
+            return;
+        }
         if (role == MG_ROLE_JACOBI) {
             // damped Jacobi from u = 0 (iterate to SX2) with the residual and
             // its restriction, the coarse correction, then prolongation with
@@ -855,6 +859,38 @@ struct Engine : EngineBase {
         return I;
     }
 
+    // nu > 1 damped Jacobi sweeps (eq. sjac, mg_params.jacobi_iters) on the
+    // levels ds: from zero (xin < 0) or from slot xin; sweep i writes the
+    // slot out_i with out_nu = last and out_i alternating between last and
+    // other (xin is neither out_1 nor, for a sweep, its own output).
+    int jacobi_first_out(int nu, int last, int other) { return (nu & 1) ? last : other; }
+    void jacobi_sweeps(Handle& H, const std::vector<int>& ds, int nu, int xin, int last, int other, cudaStream_t st) {
+        const SegTable& t = H.seg(ds, false, kPts);
+        int in = xin, out = jacobi_first_out(nu, last, other);
+        for (int i = 1; i <= nu; ++i) {
+            const bool z = in < 0;
+            LAUNCH(KK_JACOBI, t, (z ? 2 * C : 3 * C) + R, k_jacobi<T>, z ? out : in, SG, out, z ? 1 : 0);
+            in = out;
+            out = (out == last) ? other : last;
+        }
+    }
+    // Several sweeps around the coarse correction of a Jacobi level: pre from
+    // zero (or from xin) into `xs`, residual restricted to the next level,
+    // the coarse cycle (emitted by `coarse`), x' = xs + P e, post sweeps into
+    // `res`.  scratch: a free slot of the level.
+    template <class Coarse>
+    void jacobi_level_nu(Handle& H, const std::vector<int>& ds, int nu, int xin, int xs, int res, int scratch,
+                         Coarse&& coarse, cudaStream_t st) {
+        jacobi_sweeps(H, ds, nu, xin, xs, xin == res || xin < 0 ? scratch : res, st);
+        launch_restrict<MODE_HELM>(H, ds, KK_RESTRICT_HELM, 2 * C + R + C / 4, xs, SG, SG, 0, st);
+        coarse();
+        const int other = (res == scratch) ? xs : scratch;
+        const int o1 = jacobi_first_out(nu, res, other);
+        const int pslot = (o1 != xs) ? xs : (o1 == res ? other : res);
+        launch_prolong<PMODE_ADD>(H, ds, KK_PROLONG_ADD, 2 * C + C / 4, xs, SU, SG, pslot, pslot, 0, st);
+        jacobi_sweeps(H, ds, nu, pslot, res, other, st);
+    }
+
     // One cycle from level 1: input u in SX2 (unless uzero), g in SG; result
     // in SD of level 1.
     void cycle(Handle& H, bool uzero, cudaStream_t st) override {
@@ -862,6 +898,12 @@ struct Engine : EngineBase {
         std::vector<int> I = all(H);
         const std::vector<int> ds1 = descs(H, 1, I);
         const SegTable& t = H.seg(ds1, false, kPts);
+        const int nu = H.p.jacobi_iters;
+        if (nu > 1) {
+            jacobi_level_nu(H, ds1, nu, uzero ? -1 : SX2, SU, SD, SD, [&] { wave(H, 2, I, st); }, st);
+            fg_fused = false;
+            return;
+        }
         if (uzero) {
             if (!launch_restrict_jac0_stream(H, ds1, 2 * C + R + C / 4, st))
                 launch_restrict<MODE_JAC0>(H, ds1, KK_RESTRICT_JAC0, 2 * C + R + C / 4, SU, SG, SG, 1, st);

@@ -954,14 +954,14 @@ int mg_setup(mg_handle** out, const mg_instance* inst, int ninst, const mg_param
     *out = nullptr;
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) { set_error("mg_setup: precision"); return MG_EINVAL; }
     if (p->cheb_iters < 1 || p->cheb_iters > 16 || p->coarse_cheb_iters < 1 || p->coarse_cheb_iters > 16 ||
-        p->jacobi_iters != 1 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
+        p->jacobi_iters < 1 || p->jacobi_iters > 16 || p->M < 0 || p->n_cmax < 1 || p->restart < 1 || p->restart > MAXR ||
         p->outer < MG_OUTER_STATIONARY || p->outer > MG_OUTER_FGMRES || p->tile_candidate < -1 ||
         p->tile_candidate >= MG_TILE_CANDIDATES || p->tail_cluster != 0 || p->tail_nmax < -1 || p->ray < 0 ||
         p->ray > 1 || p->fgmres_passes < 2 || p->fgmres_passes > 3 || p->workspace_limit < 0 ||
         p->adr_bc < MG_ADR_BC_ZERO || p->adr_bc > MG_ADR_BC_ABC ||
         p->adr_reaction < MG_ADR_REACTION_CONTINUOUS || p->adr_reaction > MG_ADR_REACTION_DISCRETE ||
         !(p->sponge_width > 0 && p->sponge_width < 1e6) || !(p->sponge_power > 0 && p->sponge_power < 1e3)) {
-        set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters == 1, restart 1..22)");
+        set_error("mg_setup: schedule parameter out of range (cheb_iters 1..16, jacobi_iters 1..16, restart 1..22)");
         return MG_EINVAL;
     }
     if (!roles_valid(*p)) {

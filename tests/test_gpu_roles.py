@@ -146,3 +146,45 @@ def test_roles_refusals():
                                     B._ptr(gp), B._ptr(gw), None, None)
     B.mg_destroy(h)
     assert rc == B.MG_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("nu", [2, 3])
+@pytest.mark.parametrize("roles", [{}, SHIFTED])
+def test_several_jacobi_sweeps_fp64(nu, roles):
+    """mg_params.jacobi_iters > 1 (eq. sjac applied nu times before and after
+    on every Jacobi level, from zero and from a given iterate): FP64 cycle
+    equals the oracle's, 1e-12."""
+    I = inst(127)
+    p = B.default_params(precision="fp64", n_cmax=7, M=2, roles=roles, jacobi_iters=nu)
+    h = B.mg_setup([(127, I.omega, I.k, I.phi, "abc1")], p)
+    H = Hierarchy(127, I.k, I.phi, I.omega, "abc1", CycleParams(n_cmax=7, M=2, roles=roles, jacobi_iters=nu))
+    u = rnd(I.g.shape, 80) * 1e-3
+    uu = u.copy()
+    B.mg_cycle(h, uu, I.g.copy(), 1)
+    B.mg_destroy(h)
+    assert rel(uu, H.cycle(u, I.g)) < 1e-12
+
+
+def test_several_jacobi_sweeps_mixed_fgmres():
+    """Two sweeps in the complex-FP32 cycle at n = 2047 (the level-1 passes do
+    not stream then; FGMRES copies the basis vector and forms the matvec on
+    its own): one cycle within 1e-5 of the oracle, and FGMRES(20) reaches
+    1e-6 with the oracle's iteration count +-1 on n = 255."""
+    I = inst(2047, seed=5)
+    ex = {"adr_bc": "abc", "adr_reaction": "discrete"}
+    h, H = pair(I, {}, prec="mixed", n_cmax=15, jacobi_iters=2, **ex)
+    g = I.g.astype(np.complex64)
+    u = np.zeros_like(g)
+    B.mg_cycle(h, u, g, 1)
+    B.mg_destroy(h)
+    ref = H.cycle(np.zeros_like(I.g), I.g)
+    assert rel(u.astype(np.complex128), ref) < 1e-5
+    J = inst(255, seed=6)
+    Hs = Hierarchy(255, J.k, J.phi, J.omega, "abc1", CycleParams(n_cmax=15, M=2, jacobi_iters=2, **ex))
+    _, it_o, _ = oracle.solve_fgmres(Hs, J.g, tol=1e-6, maxit=400)
+    p = B.default_params(precision="mixed", n_cmax=15, M=2, jacobi_iters=2, tol=1e-6, maxit=400, **ex)
+    h = B.mg_setup([(255, J.omega, J.k, J.phi, "abc1")], p)
+    uu = np.zeros_like(J.g)
+    st, it, rr, _, _ = B.mg_solve(h, uu, J.g.copy())
+    B.mg_destroy(h)
+    assert st == B.MG_OK and rr < 1e-6 and abs(it - it_o) <= 1, (st, it, it_o, rr)
