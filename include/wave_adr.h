@@ -314,6 +314,10 @@ enum { MG_ROLE_JACOBI = 0, MG_ROLE_CHEB = 1, MG_ROLE_NONE = 2, MG_ROLE_CHEB_ADR 
  * l to roles[l-1] for l = 1..min(L, maxl) and returns L (or MG_EINVAL).  The
  * coarsest level's role takes precedence (for L <= 3). */
 int mg_level_roles(int n, const mg_params* p, int* sizes, int* roles, int maxl);
+/* The same for an n x ny instance (n nodes per row, ny rows): n_l and ny_l
+ * of level l to nxs[l-1] and nys[l-1], its role to roles[l-1]; returns L (or
+ * MG_EINVAL, also for ny < 3). */
+int mg_level_shapes(int n, int ny, const mg_params* p, int* nxs, int* nys, int* roles, int maxl);
 
 /* Number of levels L of an instance (Algorithm 1's max-level). */
 int mg_num_levels(const mg_handle* h, int inst);

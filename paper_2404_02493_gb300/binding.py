@@ -105,6 +105,8 @@ def load():
         "mg_peclet_flags": (ip, [vp, ip]),
         "mg_workspace_bytes": (ctypes.c_longlong, [vp]),
         "mg_level_roles": (ip, [ip, ctypes.POINTER(MgParams), ctypes.POINTER(ip), ctypes.POINTER(ip), ip]),
+        "mg_level_shapes": (ip, [ip, ip, ctypes.POINTER(MgParams), ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                 ctypes.POINTER(ip), ip]),
         "mg_eikonal": (ip, [ip, vp, dp, dp, dp, dp, ip, vp, ctypes.POINTER(ip), vp]),
         "mg_eikonal_rect": (ip, [ip, ip, vp, dp, dp, dp, dp, ip, vp, ctypes.POINTER(ip), vp]),
     }
@@ -125,7 +127,7 @@ def exported_symbols():
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
             "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
             "mg_tile_shapes", "mg_selftest_wait_timeout", "mg_peclet_flags",
-            "mg_workspace_bytes", "mg_level_roles", "mg_eikonal", "mg_eikonal_rect"]
+            "mg_workspace_bytes", "mg_level_roles", "mg_level_shapes", "mg_eikonal", "mg_eikonal_rect"]
 
 
 class MgError(RuntimeError):
@@ -287,6 +289,15 @@ def mg_level_roles(n, params: MgParams):
     if L < 0:
         _check(L, "mg_level_roles")
     return [(sizes[l], MG_ROLE[roles[l]]) for l in range(min(L, MG_MAX_LEVELS))]
+
+
+def mg_level_shapes(n, ny, params: MgParams):
+    """[(n_l, ny_l, role name)] for l = 1..L of an n x ny instance (no GPU needed)."""
+    nx, nys, roles = ((ctypes.c_int * MG_MAX_LEVELS)() for _ in range(3))
+    L = load().mg_level_shapes(int(n), int(ny), ctypes.byref(params), nx, nys, roles, MG_MAX_LEVELS)
+    if L < 0:
+        _check(L, "mg_level_shapes")
+    return [(nx[l], nys[l], MG_ROLE[roles[l]]) for l in range(min(L, MG_MAX_LEVELS))]
 
 
 def mg_workspace_bytes(h):

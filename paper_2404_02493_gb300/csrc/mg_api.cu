@@ -1090,6 +1090,27 @@ int mg_level_roles(int n, const mg_params* p, int* sizes, int* roles, int maxl) 
     return L;
 }
 
+int mg_level_shapes(int n, int ny, const mg_params* p, int* nxs, int* nys, int* roles, int maxl) {
+    if (!p || n < 3 || ny < 3 || p->n_cmax < 1 || maxl < 0 || (maxl > 0 && (!nxs || !nys || !roles)) ||
+        !roles_valid(*p)) {
+        set_error("mg_level_shapes: bad argument");
+        return MG_EINVAL;
+    }
+    const std::vector<std::pair<int, int>> sh = level_shapes(n, ny, p->n_cmax);
+    const int L = (int)sh.size();
+    if (L < 2 || L > MG_MAX_LEVELS || std::min(sh.back().first, sh.back().second) < 2 ||
+        (long long)sh.back().first * sh.back().second > MAXCOARSE) {
+        set_error("mg_level_shapes: no valid hierarchy for this size and n_cmax (as mg_setup)");
+        return MG_EINVAL;
+    }
+    for (int l = 1; l <= std::min(L, maxl); ++l) {
+        nxs[l - 1] = sh[(size_t)l - 1].first;
+        nys[l - 1] = sh[(size_t)l - 1].second;
+        roles[l - 1] = level_role(l, L, *p);
+    }
+    return L;
+}
+
 long long mg_workspace_bytes(const mg_handle* h) {
     if (!h) {
         set_error("mg_workspace_bytes: null handle");

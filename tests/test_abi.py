@@ -117,3 +117,19 @@ def test_level_roles_rejects_bad_lists(lib, roles):
     p = binding.default_params(roles=roles)
     with pytest.raises(binding.MgError):
         binding.mg_level_roles(255, p)
+
+
+@pytest.mark.parametrize("n,ny,n_cmax", [(4095, 2047, 15), (127, 63, 7), (100, 37, 12), (63, 127, 7), (255, 7, 15)])
+def test_level_shapes_match_the_oracle_hierarchy(lib, n, ny, n_cmax):
+    """mg_level_shapes (no GPU): the oracle's n x ny hierarchy and roles; a
+    coarsest side below two nodes is refused as mg_setup refuses it."""
+    from oracle.cycle import build_shapes
+    p = binding.default_params(n_cmax=n_cmax)
+    shapes = build_shapes(n, ny, n_cmax)
+    if min(shapes[-1]) < 2:
+        with pytest.raises(binding.MgError):
+            binding.mg_level_shapes(n, ny, p)
+        return
+    got = binding.mg_level_shapes(n, ny, p)
+    assert [(a, b) for a, b, _ in got] == shapes
+    assert got[0][2] == "jacobi" and got[-1][2] == "coarse_lu"
