@@ -107,26 +107,41 @@ struct Engine : EngineBase {
             kl(kern, t.nblocks, dim3(BX, BY), smem, st, kd(H, t), t.d, t.nseg, sin, sout, m, flags);
         }, t.pts);
     }
+    // Rows the busiest warp of a warp-streaming launch marches with bands of
+    // rh rows (ry fine rows per band row: 2 for the restriction's coarse
+    // bands): the segment table gives every instance whole blocks of wpb
+    // warps (share_blocks over block units of so columns x rh wpb ry rows, as
+    // seg_tiles builds it), and a segment's warps take its strips x bands in
+    // turn; the busiest warp's units times the band plus its halo rows.
+    static long long stream_rows(Handle& H, const std::vector<int>& ds, int so, int rh, int ry, int wpb, int cap,
+                                 int halo) {
+        std::vector<long long> bu, wu;
+        for (int q : ds) {
+            const LevelDesc& d = H.hdesc[(size_t)q];
+            const long long strips = (d.n + so - 1) / so;
+            bu.push_back(strips * ((d.ny + rh * wpb * ry - 1) / (rh * wpb * ry)));
+            wu.push_back(strips * ((d.ny + rh * ry - 1) / (rh * ry)));
+        }
+        const std::vector<int> nb = share_blocks(bu, cap);
+        long long load = 0;
+        for (size_t q = 0; q < ds.size(); ++q)
+            load = std::max(load, (wu[q] + (long long)nb[q] * wpb - 1) / ((long long)nb[q] * wpb));
+        return load * (rh * ry + halo);
+    }
     // NS Chebyshev steps m .. m + NS - 1 as warp-streaming strips
     // (k_cheb_stream, complex FP32).  Band height: of the candidates, the one
-    // whose busiest warp marches the fewest rows (units per resident warp
-    // rounded up, times the band plus its 2 NS halo rows).
+    // whose busiest warp marches the fewest rows (stream_rows).
     template <int NS, bool HS>
     void launch_cheb_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, int sin, int sout, int sdin,
                                int sdout, int m, int flags, cudaStream_t st) {
         constexpr int SO = cs_out<NS>();
         const int smem = cs_smem<T, HS>();
         constexpr int WPB = cs_wpb<HS>();
-        const long long warps = (long long)occ_cap(k_cheb_stream<T, NS, 16, HS>, smem, 32 * WPB) * WPB;
+        const int cap = occ_cap(k_cheb_stream<T, NS, 16, HS>, smem, 32 * WPB);
         int best = 16;
         long long bcost = -1;
         for (int rh : {16, 24, 32, 64}) {
-            long long units = 0;   // over the launch's instances
-            for (int q : ds) {
-                const int n = H.hdesc[(size_t)q].n, ny = H.hdesc[(size_t)q].ny;
-                units += (long long)((n + SO - 1) / SO) * ((ny + rh - 1) / rh);
-            }
-            const long long cost = (units + warps - 1) / warps * (rh + 2 * NS);
+            const long long cost = stream_rows(H, ds, SO, rh, 1, WPB, cap, 2 * NS);
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
         }
         auto run = [&](auto kern, int rh) {
@@ -222,16 +237,11 @@ struct Engine : EngineBase {
     template <bool HS>
     void launch_restrict_jac0_stream_hs(Handle& H, const std::vector<int>& ds, double bpp, int fgv, cudaStream_t st) {
         const int smem = rs_smem<T, HS>();
-        const long long warps = (long long)occ_cap(k_restrict_jac0_stream<T, 16, HS>, smem, 32 * RS_WPB) * RS_WPB;
+        const int cap = occ_cap(k_restrict_jac0_stream<T, 16, HS>, smem, 32 * RS_WPB);
         int best = 16;
         long long bcost = -1;
         for (int rh : {8, 16, 32}) {
-            long long units = 0;
-            for (int q : ds) {
-                const int n = H.hdesc[(size_t)q].n, ncy = (H.hdesc[(size_t)q].ny - 1) / 2;
-                units += (long long)((n + RS_SO - 1) / RS_SO) * ((ncy + rh - 1) / rh);
-            }
-            const long long cost = (units + warps - 1) / warps * (2 * rh + 3);
+            const long long cost = stream_rows(H, ds, RS_SO, rh, 2, RS_WPB, cap, 3);
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
         }
         auto run = [&](auto kern, int rh) {
@@ -269,16 +279,11 @@ struct Engine : EngineBase {
                                       int sout, cudaStream_t st) {
         constexpr int SO = FG ? SW_OUT : RS_SO;
         const int smem = ps_smem<T, HS>();
-        const long long warps = (long long)occ_cap(k_prolong_jac_stream<T, 32, HS, FG>, smem, 32 * RS_WPB) * RS_WPB;
+        const int cap = occ_cap(k_prolong_jac_stream<T, 32, HS, FG>, smem, 32 * RS_WPB);
         int best = 32;
         long long bcost = -1;
         for (int rh : {16, 32, 64}) {
-            long long units = 0;
-            for (int q : ds) {
-                const int n = H.hdesc[(size_t)q].n, ny = H.hdesc[(size_t)q].ny;
-                units += (long long)((n + SO - 1) / SO) * ((ny + rh - 1) / rh);
-            }
-            const long long cost = (units + warps - 1) / warps * (rh + (FG ? 4 : 2));
+            const long long cost = stream_rows(H, ds, SO, rh, 1, RS_WPB, cap, FG ? 4 : 2);
             if (bcost < 0 || cost < bcost) { bcost = cost; best = rh; }
         }
         auto run = [&](auto kern, int rh) {

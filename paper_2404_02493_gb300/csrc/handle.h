@@ -79,6 +79,9 @@ struct TileChoice {
 };
 
 std::string desc_key(const std::vector<int>& descs);
+// Blocks per segment of a launch: every segment at least one, the rest of
+// the cap given greedily to the segment with the most work units per block.
+std::vector<int> share_blocks(const std::vector<long long>& units, int cap);
 
 struct Handle {
     mg_params p{};

@@ -65,7 +65,7 @@ void* Handle::alloc(size_t bytes) {
 // gets at most min(units, MAXB) blocks; a single segment gets
 // min(units, cap, MAXB).  Blocks that loop over several units keep their
 // copy pipelines busy and pay the descriptor set-up once.
-static std::vector<int> share_blocks(const std::vector<long long>& units, int cap) {
+std::vector<int> share_blocks(const std::vector<long long>& units, int cap) {
     const size_t ns = units.size();
     std::vector<int> nb(ns, 1);
     long long tot = 0;
