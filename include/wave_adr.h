@@ -268,8 +268,9 @@ long long mg_workspace_bytes(const mg_handle* h);
  * checkpoint and swept backwards with the transposed operators (A^H, L^H,
  * R^T = P/4, P^T = 4R), the reversed Chebyshev recurrence and GMRES(3)
  * differentiated through its least-squares definition.  FP64 handles with
- * the LU coarsest level and square instances only (MG_EUNSUPPORTED
- * otherwise).  Pointers may be
+ * the LU coarsest level and the default level roles only (MG_EUNSUPPORTED
+ * otherwise); instances may be non-square (grad_phi then holds ny rows of
+ * n).  Pointers may be
  * host or device memory; synchronises `stream`. */
 int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, int K, const void* gbar_uK, double* grad_phi,
                       double* grad_weights, void* grad_u0, mg_stream stream);

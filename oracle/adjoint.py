@@ -43,38 +43,38 @@ def nbr_sum(u):
 
 def restrict(r):
     """Full weighting (Section 3.1.2), zero outside the grid."""
-    n = r.shape[0]
-    nc = coarse_size(n)
-    p = torch.zeros((n + 2, n + 2), dtype=r.dtype)
+    ny, n = r.shape
+    ncy, ncx = coarse_size(ny), coarse_size(n)
+    p = torch.zeros((ny + 2, n + 2), dtype=r.dtype)
     p[1:-1, 1:-1] = r
     w = (1.0, 2.0, 1.0)
-    out = torch.zeros((nc, nc), dtype=r.dtype)
+    out = torch.zeros((ncy, ncx), dtype=r.dtype)
     for b in range(3):
         for a in range(3):
-            out = out + (w[a] * w[b] / 16.0) * p[b + 1: b + 1 + 2 * nc: 2, a + 1: a + 1 + 2 * nc: 2]
+            out = out + (w[a] * w[b] / 16.0) * p[b + 1: b + 1 + 2 * ncy: 2, a + 1: a + 1 + 2 * ncx: 2]
     return out
 
 
-def prolong(e, n):
-    """Bilinear interpolation, 4 R^T (Section 3.1.2)."""
-    nc = e.shape[0]
-    p = torch.zeros((n + 2, n + 2), dtype=e.dtype)
+def prolong(e, n, ny):
+    """Bilinear interpolation, 4 R^T (Section 3.1.2), onto n nodes per row
+    and ny rows."""
+    ncy, ncx = e.shape
+    p = torch.zeros((ny + 2, n + 2), dtype=e.dtype)
     w = (1.0, 2.0, 1.0)
     for b in range(3):
         for a in range(3):
-            p[b + 1: b + 1 + 2 * nc: 2, a + 1: a + 1 + 2 * nc: 2] = \
-                p[b + 1: b + 1 + 2 * nc: 2, a + 1: a + 1 + 2 * nc: 2] + (w[a] * w[b] / 4.0) * e
+            p[b + 1: b + 1 + 2 * ncy: 2, a + 1: a + 1 + 2 * ncx: 2] = \
+                p[b + 1: b + 1 + 2 * ncy: 2, a + 1: a + 1 + 2 * ncx: 2] + (w[a] * w[b] / 4.0) * e
     return p[1:-1, 1:-1]
 
 
 def inject(f):
-    nc = coarse_size(f.shape[0])
-    return f[1:2 * nc:2, 1:2 * nc:2]
+    ncy, ncx = coarse_size(f.shape[0]), coarse_size(f.shape[1])
+    return f[1:2 * ncy:2, 1:2 * ncx:2]
 
 
 def phase_derivatives(phi, h):
     """Central differences after linear ghost extrapolation (Section 3.2.1)."""
-    n = phi.shape[0]
     W = torch.cat([(2 * phi[:, 0] - phi[:, 1])[:, None], phi[:, :-1]], 1)
     E = torch.cat([phi[:, 1:], (2 * phi[:, -1] - phi[:, -2])[:, None]], 1)
     S = torch.cat([(2 * phi[0, :] - phi[1, :])[None, :], phi[:-1, :]], 0)
@@ -87,7 +87,7 @@ class TLevel:
 
     def __init__(self, lev: Level, phi_t):
         self.lev = lev
-        self.n, self.h = lev.n, lev.h
+        self.n, self.ny, self.h = lev.n, lev.rows, lev.h
         self.D = _t(helmholtz_diag(lev))                 # no phi dependence
         self.phi = phi_t
         self.adr = None
@@ -127,16 +127,16 @@ class TLevel:
 
     def L_dense(self):
         """Dense ADR matrix (row p = j*n + i), differentiable in phi."""
-        n = self.n
+        n, ny = self.n, self.ny
         c = self.adr
-        N = n * n
+        N = n * ny
         M = torch.zeros((N, N), dtype=C128)
         idx = torch.arange(N)
         j, i = idx // n, idx % n
         M[idx, idx] = c["d"].reshape(-1)
         for (dj, di, key) in ((0, -1, "cW"), (0, 1, "cE"), (-1, 0, "cS"), (1, 0, "cN")):
             jj, ii = j + dj, i + di
-            ok = (jj >= 0) & (jj < n) & (ii >= 0) & (ii < n)
+            ok = (jj >= 0) & (jj < ny) & (ii >= 0) & (ii < n)
             M[idx[ok], (jj * n + ii)[ok]] = c[key].reshape(-1)[ok]
         return M
 
@@ -240,7 +240,7 @@ class TorchCycle:
         x = gmres(lv.L, b, None, self.p.gmres_m)
         r = b - lv.L(x)
         ec = self.adr_vcycle(l + 1, restrict(r))
-        x = x + prolong(ec, lv.n)
+        x = x + prolong(ec, lv.n, lv.ny)
         return gmres(lv.L, b, x, self.p.gmres_m)
 
     def cycle(self, u, g, l=1):
@@ -253,7 +253,7 @@ class TorchCycle:
         elif l != 3:
             u = self.cheb(l, u, g, self.p.cheb_iters)
         rc = restrict(g - lv.A(u))
-        u = u + prolong(self.cycle(torch.zeros_like(rc), rc, l + 1), lv.n)
+        u = u + prolong(self.cycle(torch.zeros_like(rc), rc, l + 1), lv.n, lv.ny)
         if l == 1:
             u = self.jacobi(u, g)
         elif l == 2:

@@ -42,10 +42,10 @@ using cd = std::complex<double>;
 // ------------------------------------------------------------ kernels (FP64)
 constexpr int ANT = 256;
 
-// (i, j) of the flat index q of an n x n level; n <= 32768, so q and n^2
-// fit 32 bits and one unsigned 32-bit division replaces the 64-bit one
-__device__ __forceinline__ bool ij_of(long long q, int n, int& i, int& j) {
-    if (q >= (long long)n * n) return false;
+// (i, j) of the flat index q of a level of ny rows of n; n ny < 2^32, so q
+// fits 32 bits and one unsigned 32-bit division replaces the 64-bit one
+__device__ __forceinline__ bool ij_of(long long q, int n, int ny, int& i, int& j) {
+    if (q >= (long long)n * ny) return false;
     const unsigned uq = (unsigned)q, un = (unsigned)n;
     const unsigned uj = uq / un;
     j = (int)uj;
@@ -54,10 +54,10 @@ __device__ __forceinline__ bool ij_of(long long q, int n, int& i, int& j) {
 }
 
 // out (+)= sum_t c_t x_t   (up to 4 terms; null pointers skipped)
-__global__ void ka_lincomb(int n, int pitch, double2* out, int acc, const double2* x0, double2 c0, const double2* x1,
-                           double2 c1, const double2* x2, double2 c2, const double2* x3, double2 c3) {
+__global__ void ka_lincomb(int n, int ny, int pitch, double2* out, int acc, const double2* x0, double2 c0,
+                           const double2* x1, double2 c1, const double2* x2, double2 c2, const double2* x3, double2 c3) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, ny, i, j)) return;
     const long long p = (long long)j * pitch + i;
     double2 v = acc ? out[p] : make_double2(0, 0);
     if (x0) v = dadd(v, dmul(c0, x0[p]));
@@ -72,7 +72,7 @@ __global__ void ka_lincomb(int n, int pitch, double2* out, int acc, const double
 __global__ void ka_apply(LevelDesc d, int op, const double2* x, double2* y, double2 s, int acc, const double2* b,
                          double2* z) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, d.ny, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
     double2 r;
     if (op == 0) r = helm_apply_pt<double, false>(d, x, i, j);
@@ -87,7 +87,7 @@ __global__ void ka_apply(LevelDesc d, int op, const double2* x, double2* y, doub
 // y (+)= s D^{-1} x  or  s D^{-H} x  (D = Helmholtz diagonal)
 __global__ void ka_diag(LevelDesc d, const double2* x, double2* y, int herm, double s, int acc) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, d.ny, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
     double2 dg = helm_diag_at<double>(d, i, j);
     dg = dsc(dg, d.inv_h2);
@@ -97,15 +97,16 @@ __global__ void ka_diag(LevelDesc d, const double2* x, double2* y, int herm, dou
 }
 
 // y_coarse (+)= s R x_fine   (full weighting)
-__global__ void ka_restrict(int nf, int pf, int nc, int pc, const double2* x, double2* y, double s, int acc) {
+__global__ void ka_restrict(int nf, int nyf, int pf, int nc, int nyc, int pc, const double2* x, double2* y, double s,
+                            int acc) {
     int I, J;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, nc, I, J)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, nc, nyc, I, J)) return;
     double2 v = make_double2(0, 0);
     const double w[3] = {1, 2, 1};
     for (int b = 0; b < 3; ++b)
         for (int a = 0; a < 3; ++a) {
             const int i = 2 * I + a, j = 2 * J + b;   // fine index 2I+1+(a-1)
-            if (i < nf && j < nf) v = dadd(v, dsc(x[(long long)j * pf + i], w[a] * w[b] / 16.0));
+            if (i < nf && j < nyf) v = dadd(v, dsc(x[(long long)j * pf + i], w[a] * w[b] / 16.0));
         }
     v = dsc(v, s);
     const long long q = (long long)J * pc + I;
@@ -113,9 +114,10 @@ __global__ void ka_restrict(int nf, int pf, int nc, int pc, const double2* x, do
 }
 
 // y_fine (+)= s P e_coarse  (bilinear)
-__global__ void ka_prolong(int nf, int pf, int nc, int pc, const double2* e, double2* y, double s, int acc) {
+__global__ void ka_prolong(int nf, int nyf, int pf, int nc, int nyc, int pc, const double2* e, double2* y, double s,
+                           int acc) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, nf, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, nf, nyf, i, j)) return;
     int ia[2], ja[2];
     double wa[2], wb[2];
     int na, nb;
@@ -124,7 +126,7 @@ __global__ void ka_prolong(int nf, int pf, int nc, int pc, const double2* e, dou
     double2 v = make_double2(0, 0);
     for (int q = 0; q < nb; ++q)
         for (int r = 0; r < na; ++r)
-            if (ia[r] >= 0 && ia[r] < nc && ja[q] >= 0 && ja[q] < nc)
+            if (ia[r] >= 0 && ia[r] < nc && ja[q] >= 0 && ja[q] < nyc)
                 v = dadd(v, dsc(e[(long long)ja[q] * pc + ia[r]], wa[r] * wb[q]));
     v = dsc(v, s);
     const long long p = (long long)j * pf + i;
@@ -150,8 +152,8 @@ struct DotPtrs {
 // partials in 8 interleaved groups, then the groups in order.  The order is
 // fixed, so the result is reproducible.
 constexpr int ADV = 2 * ADOTS;   // doubles per thread
-__global__ void __launch_bounds__(ANT) ka_dots(int n, int pitch, int npair, DotPtrs P, double* part, unsigned* count,
-                                               double2* out) {
+__global__ void __launch_bounds__(ANT) ka_dots(int n, int ny, int pitch, int npair, DotPtrs P, double* part,
+                                               unsigned* count, double2* out) {
     __shared__ double tr[ANT / 32][32][ADV + 1];
     __shared__ double ws[ANT / 32][ADV];
     __shared__ bool last;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(ANT) ka_dots(int n, int pitch, int npair, DotP
     double2 acc[ADOTS];
 #pragma unroll
     for (int k = 0; k < ADOTS; ++k) acc[k] = make_double2(0, 0);
-    const unsigned N = (unsigned)n * (unsigned)n, un = (unsigned)n;
+    const unsigned N = (unsigned)n * (unsigned)ny, un = (unsigned)n;
     for (unsigned q = blockIdx.x * ANT + tid; q < N; q += gridDim.x * ANT) {
         const unsigned j = q / un, i = q - j * un;
         const long long p = (long long)j * pitch + i;
@@ -316,11 +318,11 @@ __global__ void ka_gm_back(const double2* t, const double2* cb, double2* o) {
 
 // out (+)= sum_t c_t x_t with c_t read from device memory (cp_t) when
 // cp_t is set, else the immediate value
-__global__ void ka_lincomb_p(int n, int pitch, double2* out, int acc, const double2* x0, const double2* c0p,
+__global__ void ka_lincomb_p(int n, int ny, int pitch, double2* out, int acc, const double2* x0, const double2* c0p,
                              double2 c0, const double2* x1, const double2* c1p, double2 c1, const double2* x2,
                              const double2* c2p, double2 c2, const double2* x3, const double2* c3p, double2 c3) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, ny, i, j)) return;
     const long long p = (long long)j * pitch + i;
     double2 v = acc ? out[p] : make_double2(0, 0);
     if (x0) v = dadd(v, dmul(c0p ? *c0p : c0, x0[p]));
@@ -334,11 +336,11 @@ __global__ void ka_lincomb_p(int n, int pitch, double2* out, int acc, const doub
 // ka_gm_back: kb_q = o[q] xbar; r0b = sum_i o[3 + i] w_i;
 // wb_q = sum_i o[6 + 4q + i] w_i + o[9 + 4q] r0 (each sum in that order, as
 // the linear combinations it replaces)
-__global__ void ka_gm_back_vec(int n, int pitch, const double2* xbar, const double2* w0, const double2* w1,
+__global__ void ka_gm_back_vec(int n, int ny, int pitch, const double2* xbar, const double2* w0, const double2* w1,
                                const double2* w2, const double2* r0, const double2* o, double2* kb0, double2* kb1,
                                double2* kb2, double2* r0b, double2* wb0, double2* wb1, double2* wb2) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, n, ny, i, j)) return;
     const long long p = (long long)j * pitch + i;
     const double2 xb = xbar[p], a0 = w0[p], a1 = w1[p], a2 = w2[p], rv = r0[p];
     const double2 z = make_double2(0, 0);
@@ -369,7 +371,7 @@ __device__ __forceinline__ void adr_grad_pt(const LevelDesc& d, int i, int j, lo
     const int n = d.n;
     const double2 z = make_double2(0, 0);
     const double2 aW = i > 0 ? a[p - 1] : z, aE = i < n - 1 ? a[p + 1] : z;
-    const double2 aS = j > 0 ? a[p - d.pitch] : z, aN = j < n - 1 ? a[p + d.pitch] : z;
+    const double2 aS = j > 0 ? a[p - d.pitch] : z, aN = j < d.ny - 1 ? a[p + d.pitch] : z;
     const quad<double> q = reinterpret_cast<const quad<double>*>(d.adr)[p];
     const double wh = d.wh;
     // d(La)/d phix = i wh [(1+sx) aW - (1-sx) aE], sx = sign(phix): the factors
@@ -390,7 +392,7 @@ __device__ __forceinline__ void adr_grad_pt(const LevelDesc& d, int i, int j, lo
 
 __global__ void ka_adr_grad(LevelDesc d, const double2* ybar, const double2* a, double s, double* qbar) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, d.ny, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
     adr_grad_pt(d, i, j, p, dsc(ybar[p], s), a, qbar);
 }
@@ -400,7 +402,7 @@ __global__ void ka_adr_grad(LevelDesc d, const double2* ybar, const double2* a, 
 __global__ void ka_lh_grad(LevelDesc d, const double2* ybar, const double2* a, double s, double2* out,
                            double* qbar) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, d.ny, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
     const double2 r = dmul(make_double2(s, 0), adr_apply_t_pt<double, true>(d, ybar, i, j));
     out[p] = dadd(out[p], r);
@@ -411,7 +413,7 @@ __global__ void ka_lh_grad(LevelDesc d, const double2* ybar, const double2* a, d
 // modulated update u += m a:       abar  = conj(m) ubar, mbar += conj(a) ubar
 __global__ void ka_mod(LevelDesc d, int mode, const double2* x, const double2* xbar, double2* ybar, double2* mbar) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, d.ny, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
     const double2 m = reinterpret_cast<const double2*>(d.mod)[p];
     const long long q = (long long)j * d.n + i;
@@ -429,23 +431,22 @@ __global__ void ka_mod(LevelDesc d, int mode, const double2* x, const double2* x
 // forward modulation: mode 0: out = conj(m) x ; mode 1: out = u + m x
 __global__ void ka_apply_mod(LevelDesc d, int mode, const double2* x, const double2* u, double2* out) {
     int i, j;
-    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, i, j)) return;
+    if (!ij_of((long long)blockIdx.x * ANT + threadIdx.x, d.n, d.ny, i, j)) return;
     const long long p = (long long)j * d.pitch + i;
     const double2 m = reinterpret_cast<const double2*>(d.mod)[p];
     if (mode == 0) out[p] = dmulc(m, x[p]);
     else out[p] = dadd(u[p], dmul(m, x[p]));
 }
 
-// y (+)= M x or M^H x with a dense FP64 n^2 x n^2 matrix (coarsest level)
-// y (+)= M x or M^H x with the dense coarsest-level inverse M (N = n^2 rows):
+// y (+)= M x or M^H x with the dense coarsest-level inverse M (N = n ny rows):
 // one warp per row (the rows spread over many SMs; FP64 is slow per SM), the
 // lanes take every 32nd column with FMA chains, then a shuffle tree
 constexpr int GEMV_ROWS = ANT / 32;   // rows per block
-__global__ void __launch_bounds__(ANT) ka_gemv(int n, int pitch, const double2* M, const double2* x, double2* y,
-                                               int herm, int acc) {
+__global__ void __launch_bounds__(ANT) ka_gemv(int n, int ny, int pitch, const double2* M, const double2* x,
+                                               double2* y, int herm, int acc) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * GEMV_ROWS + (threadIdx.x >> 5);
-    const int N = n * n;
+    const int N = n * ny;
     if (row >= N) return;   // whole warps leave together
     double2 s = make_double2(0, 0);
     for (int c = lane; c < N; c += 32) {
@@ -484,7 +485,7 @@ struct Vec {
 
 struct AdjLevel {
     LevelDesc d;          // host copy (device pointers)
-    int n = 0, pitch = 0;
+    int n = 0, ny = 0, pitch = 0;   // nodes per row, rows, row pitch
     size_t sz = 0;        // elements per vector
     std::vector<double2*> pool;   // free vectors
     std::vector<double2*> owned;  // every vector of this level
@@ -520,7 +521,7 @@ struct Adjoint {
         cudaFree(wsum);
     }
 
-    int blocks(int n) const { return (int)(((long long)n * n + ANT - 1) / ANT); }
+    int blocks(const AdjLevel& L) const { return (int)(((long long)L.n * L.ny + ANT - 1) / ANT); }
     static int num_sms() {
         static int nsm = 0;
         if (!nsm) {
@@ -538,17 +539,18 @@ struct Adjoint {
             AdjLevel& L = lv[l];
             L.d = H.hdesc[I.lv[l - 1].desc];
             L.n = L.d.n;
+            L.ny = L.d.ny;
             L.pitch = L.d.pitch;
-            L.sz = (size_t)L.pitch * L.n;
+            L.sz = (size_t)L.pitch * L.ny;
             if (L.d.adr) {
-                if (cudaMalloc(&L.qbar, sizeof(double) * 4 * L.n * L.n) != cudaSuccess) return MG_ENOMEM;
-                cudaMemsetAsync(L.qbar, 0, sizeof(double) * 4 * L.n * L.n, st);
+                if (cudaMalloc(&L.qbar, sizeof(double) * 4 * L.n * L.ny) != cudaSuccess) return MG_ENOMEM;
+                cudaMemsetAsync(L.qbar, 0, sizeof(double) * 4 * L.n * L.ny, st);
                 // fixed Krylov scale: 1 / (Gershgorin bound of L)
                 L.kscale = 1.0 / (8.0 * L.d.inv_h2 + 4.0 * I.omega * I.omega + 8.0 * L.d.wh);
             }
             if (L.d.mod) {
-                if (cudaMalloc(&L.mbar, sizeof(double2) * L.n * L.n) != cudaSuccess) return MG_ENOMEM;
-                cudaMemsetAsync(L.mbar, 0, sizeof(double2) * L.n * L.n, st);
+                if (cudaMalloc(&L.mbar, sizeof(double2) * L.n * L.ny) != cudaSuccess) return MG_ENOMEM;
+                cudaMemsetAsync(L.mbar, 0, sizeof(double2) * L.n * L.ny, st);
             }
         }
         if (cudaMalloc(&part, sizeof(double2) * ADOTS * 1024) != cudaSuccess) return MG_ENOMEM;
@@ -595,7 +597,7 @@ struct Adjoint {
     void lin(int l, double2* out, bool acc, const double2* x0, cd c0, const double2* x1 = nullptr, cd c1 = 0,
              const double2* x2 = nullptr, cd c2 = 0, const double2* x3 = nullptr, cd c3 = 0) {
         AdjLevel& L = lv[l];
-        ka_lincomb<<<blocks(L.n), ANT, 0, st>>>(L.n, L.pitch, out, acc, x0, make_double2(c0.real(), c0.imag()), x1,
+        ka_lincomb<<<blocks(L), ANT, 0, st>>>(L.n, L.ny, L.pitch, out, acc, x0, make_double2(c0.real(), c0.imag()), x1,
                                                 make_double2(c1.real(), c1.imag()), x2,
                                                 make_double2(c2.real(), c2.imag()), x3,
                                                 make_double2(c3.real(), c3.imag()));
@@ -604,28 +606,28 @@ struct Adjoint {
     void apply(int l, int op, const double2* x, double2* y, cd s = 1.0, bool acc = false,
                const double2* b = nullptr, double2* z = nullptr) {
         AdjLevel& L = lv[l];
-        ka_apply<<<blocks(L.n), ANT, 0, st>>>(L.d, op, x, y, make_double2(s.real(), s.imag()), acc, b, z);
+        ka_apply<<<blocks(L), ANT, 0, st>>>(L.d, op, x, y, make_double2(s.real(), s.imag()), acc, b, z);
     }
     void diag(int l, const double2* x, double2* y, bool herm, double s, bool acc) {
         AdjLevel& L = lv[l];
-        ka_diag<<<blocks(L.n), ANT, 0, st>>>(L.d, x, y, herm, s, acc);
+        ka_diag<<<blocks(L), ANT, 0, st>>>(L.d, x, y, herm, s, acc);
     }
     void restrict_(int l, const double2* xf, double2* yc, double s, bool acc) {
         AdjLevel &F = lv[l], &Cc = lv[l + 1];
-        ka_restrict<<<blocks(Cc.n), ANT, 0, st>>>(F.n, F.pitch, Cc.n, Cc.pitch, xf, yc, s, acc);
+        ka_restrict<<<blocks(Cc), ANT, 0, st>>>(F.n, F.ny, F.pitch, Cc.n, Cc.ny, Cc.pitch, xf, yc, s, acc);
     }
     void prolong_(int l, const double2* ec, double2* yf, double s, bool acc) {
         AdjLevel &F = lv[l], &Cc = lv[l + 1];
-        ka_prolong<<<blocks(F.n), ANT, 0, st>>>(F.n, F.pitch, Cc.n, Cc.pitch, ec, yf, s, acc);
+        ka_prolong<<<blocks(F), ANT, 0, st>>>(F.n, F.ny, F.pitch, Cc.n, Cc.ny, Cc.pitch, ec, yf, s, acc);
     }
     void adr_grad(int l, const double2* ybar, const double2* a, double s) {
         AdjLevel& L = lv[l];
-        ka_adr_grad<<<blocks(L.n), ANT, 0, st>>>(L.d, ybar, a, s, L.qbar);
+        ka_adr_grad<<<blocks(L), ANT, 0, st>>>(L.d, ybar, a, s, L.qbar);
     }
     // reverse of y = s L a: out += s L^H ybar, ADR gradient (one pass)
     void lh_grad(int l, const double2* ybar, const double2* a, double s, double2* out) {
         AdjLevel& L = lv[l];
-        ka_lh_grad<<<blocks(L.n), ANT, 0, st>>>(L.d, ybar, a, s, out, L.qbar);
+        ka_lh_grad<<<blocks(L), ANT, 0, st>>>(L.d, ybar, a, s, out, L.qbar);
     }
     // k device scalars of this reverse step
     double2* scalars(int k) {
@@ -652,9 +654,9 @@ struct Adjoint {
             P.y[k] = k < np ? pr[k].second : pr[0].second;
             P.z[k] = k < (int)sub.size() ? sub[k] : nullptr;
         }
-        const int nb = std::min(blocks(L.n), 2 * num_sms());
+        const int nb = std::min(blocks(L), 2 * num_sms());
         double2* out = scalars(np);
-        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.pitch, np, P, reinterpret_cast<double*>(part), dcount, out);
+        ka_dots<<<nb, ANT, 0, st>>>(L.n, L.ny, L.pitch, np, P, reinterpret_cast<double*>(part), dcount, out);
         return out;
     }
     // out (+)= sum_t cp_t x_t, coefficients in device memory
@@ -663,7 +665,7 @@ struct Adjoint {
                  const double2* x3 = nullptr, const double2* c3p = nullptr, double2 c3 = make_double2(0, 0)) {
         AdjLevel& L = lv[l];
         const double2 z = make_double2(0, 0);
-        ka_lincomb_p<<<blocks(L.n), ANT, 0, st>>>(L.n, L.pitch, out, acc, x0, c0p, z, x1, c1p, z, x2, c2p, z, x3,
+        ka_lincomb_p<<<blocks(L), ANT, 0, st>>>(L.n, L.ny, L.pitch, out, acc, x0, c0p, z, x1, c1p, z, x2, c2p, z, x3,
                                                   c3p, c3);
     }
 
@@ -774,7 +776,7 @@ struct Adjoint {
         //   kbar_j = conj(c_j) xbar;
         //   z_i = w_i^H r0: r0bar = sum_i w_i zbar_i, wbar_i += r0 conj(zbar_i);
         //   G_ij = w_i^H w_j: wbar_j += sum_i w_i Gbar_ij, wbar_i += sum_j w_j conj(Gbar_ij)
-        ka_gm_back_vec<<<blocks(L.n), ANT, 0, st>>>(L.n, L.pitch, xbar, T.w[0], T.w[1], T.w[2], T.r0, co, kb[0],
+        ka_gm_back_vec<<<blocks(L), ANT, 0, st>>>(L.n, L.ny, L.pitch, xbar, T.w[0], T.w[1], T.w[2], T.r0, co, kb[0],
                                                      kb[1], kb[2], r0b, wb[0], wb[1], wb[2]);
         // w_q = L k_q
         for (int q = 0; q < 3; ++q) lh_grad(l, wb[q], T.k[q], 1.0, kb[q]);
@@ -804,7 +806,7 @@ struct Adjoint {
         T->b = b;
         if (l == I.L) {
             AdjLevel& L = lv[l];
-            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, b, x_out, 0, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_adr, b, x_out, 0, 0);
             T->coarse_x = x_out;
             return T;
         }
@@ -832,7 +834,7 @@ struct Adjoint {
             AdjLevel& L = lv[l];
             // x = X b: bbar += X^H xbar ; L_bar = -bbar_new x^H
             double2* bb = get(l);
-            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
             lin(l, bbar, true, bb, 1.0);
             adr_grad(l, bb, T->coarse_x, -1.0);
             put(l, bb);
@@ -941,7 +943,7 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         if (l == I.L) {
             // from zero: u = A^{-1} g
-            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, g, u_out, 0, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_helm, g, u_out, 0, 0);
             return T;
         }
         const double wj = I.omega_j;
@@ -1023,7 +1025,7 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         if (l == I.L) {
             double2* gb = get(l);
-            ka_gemv<<<(L.n * L.n + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.pitch, I.lv[l - 1].inv_helm, uob, gb, 1, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_helm, uob, gb, 1, 0);
             lin(l, gbar, true, gb, 1.0);
             put(l, gb);
             return;
@@ -1120,23 +1122,23 @@ static void chain_to_phi(const InstHost& I, const std::vector<AdjLevel>& lv, cud
     for (int l = 2; l <= I.L; ++l) {
         const AdjLevel& L = lv[l];
         if (!L.qbar) continue;
-        const int n = L.n, pitch = L.pitch;
+        const int n = L.n, ny = L.ny, pitch = L.pitch;
         const double h = I.lv[l - 1].h;
-        std::vector<double> qb((size_t)4 * n * n), quads((size_t)4 * pitch * n);
+        std::vector<double> qb((size_t)4 * n * ny), quads((size_t)4 * pitch * ny);
         cudaMemcpyAsync(qb.data(), L.qbar, sizeof(double) * qb.size(), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(quads.data(), L.d.adr, sizeof(double) * quads.size(), cudaMemcpyDeviceToHost, st);
         std::vector<double> mb;
         std::vector<double> mod;
         if (L.mbar) {
-            mb.resize((size_t)2 * n * n);
-            mod.resize((size_t)2 * pitch * n);
+            mb.resize((size_t)2 * n * ny);
+            mod.resize((size_t)2 * pitch * ny);
             cudaMemcpyAsync(mb.data(), L.mbar, sizeof(double) * mb.size(), cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(mod.data(), L.d.mod, sizeof(double) * mod.size(), cudaMemcpyDeviceToHost, st);
         }
         cudaStreamSynchronize(st);
-        std::vector<double> gphi((size_t)n * n, 0.0);
+        std::vector<double> gphi((size_t)n * ny, 0.0);
         auto G = [&](int i, int j) -> double& { return gphi[(size_t)j * n + i]; };
-        for (int j = 0; j < n; ++j)
+        for (int j = 0; j < ny; ++j)
             for (int i = 0; i < n; ++i) {
                 const size_t q = (size_t)j * n + i, pq = (size_t)j * pitch + i;
                 const double px = quads[4 * pq], py = quads[4 * pq + 1];
@@ -1149,7 +1151,7 @@ static void chain_to_phi(const InstHost& I, const std::vector<AdjLevel>& lv, cud
                 const double ax = gx / (2 * h), ay = gy / (2 * h), al = gl / (h * h);
                 auto addE = [&](double v) { if (i < n - 1) G(i + 1, j) += v; else { G(n - 1, j) += 2 * v; G(n - 2, j) -= v; } };
                 auto addW = [&](double v) { if (i > 0) G(i - 1, j) += v; else { G(0, j) += 2 * v; G(1, j) -= v; } };
-                auto addN = [&](double v) { if (j < n - 1) G(i, j + 1) += v; else { G(i, n - 1) += 2 * v; G(i, n - 2) -= v; } };
+                auto addN = [&](double v) { if (j < ny - 1) G(i, j + 1) += v; else { G(i, ny - 1) += 2 * v; G(i, ny - 2) -= v; } };
                 auto addS = [&](double v) { if (j > 0) G(i, j - 1) += v; else { G(i, 0) += 2 * v; G(i, 1) -= v; } };
                 addE(ax + al);
                 addW(-ax + al);
@@ -1163,7 +1165,7 @@ static void chain_to_phi(const InstHost& I, const std::vector<AdjLevel>& lv, cud
                 }
             }
         const long long f = 1LL << (l - 1);
-        for (int j = 0; j < n; ++j)
+        for (int j = 0; j < ny; ++j)
             for (int i = 0; i < n; ++i)
                 grad_phi_host[(f * (j + 1) - 1) * n1 + (f * (i + 1) - 1)] += G(i, j);
     }
@@ -1172,19 +1174,19 @@ static void chain_to_phi(const InstHost& I, const std::vector<AdjLevel>& lv, cud
 void Adjoint::ka_mod_demod(int l, const double2* r, double2* b) {
     // b = conj(m) r
     AdjLevel& L = lv[l];
-    ka_apply_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 0, r, nullptr, b);
+    ka_apply_mod<<<blocks(L), ANT, 0, st>>>(L.d, 0, r, nullptr, b);
 }
 void Adjoint::ka_mod_update(int l, const double2* u, const double2* a, double2* out) {
     AdjLevel& L = lv[l];
-    ka_apply_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 1, a, u, out);
+    ka_apply_mod<<<blocks(L), ANT, 0, st>>>(L.d, 1, a, u, out);
 }
 void Adjoint::ka_mod_update_back(int l, const double2* a, const double2* nxb, double2* ab) {
     AdjLevel& L = lv[l];
-    ka_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 1, a, nxb, ab, L.mbar);
+    ka_mod<<<blocks(L), ANT, 0, st>>>(L.d, 1, a, nxb, ab, L.mbar);
 }
 void Adjoint::ka_mod_demod_back(int l, const double2* r, const double2* bb, double2* rb) {
     AdjLevel& L = lv[l];
-    ka_mod<<<blocks(L.n), ANT, 0, st>>>(L.d, 0, r, bb, rb, L.mbar);
+    ka_mod<<<blocks(L), ANT, 0, st>>>(L.d, 0, r, bb, rb, L.mbar);
 }
 
 }  // namespace wadr
@@ -1204,11 +1206,6 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
             return MG_EUNSUPPORTED;
         }
     for (const InstHost& I : H.inst)
-        if (I.ny != I.n) {
-            set_error("mg_cycle_backward: square grids only (the adjoint kernels assume n x n levels)");
-            return MG_EUNSUPPORTED;
-        }
-    for (const InstHost& I : H.inst)
         if (I.adr_flags) {
             set_error("mg_cycle_backward: not available with the absorbing ADR boundary closure (MG_ADR_BC_ABC) "
                       "or the discrete reaction term (MG_ADR_REACTION_DISCRETE)");
@@ -1216,8 +1213,9 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
         }
     cudaStream_t st = (cudaStream_t)stream;
     const int ni = (int)H.inst.size();
-    auto cp2d = [&](void* dst, size_t dpitch, const void* src, size_t spitch, int n) {
-        return cudaMemcpy2DAsync(dst, dpitch * 16, src, spitch * 16, (size_t)n * 16, n, cudaMemcpyDefault, st);
+    // dense user rows (ny rows of n) <-> pitched level-1 rows
+    auto cp2d = [&](void* dst, size_t dpitch, const void* src, size_t spitch, int n, int ny) {
+        return cudaMemcpy2DAsync(dst, dpitch * 16, src, spitch * 16, (size_t)n * 16, ny, cudaMemcpyDefault, st);
     };
     // ---- checkpoints u_0 .. u_{K-1} (pitched level-1 layout) by the regular forward
     std::vector<std::vector<double2*>> ck(ni);
@@ -1238,8 +1236,9 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
             ck[b][k] = dalloc(sizeof(double2) * l1.slot_stride);
             if (!ck[b][k]) { cleanup(); set_error("mg_cycle_backward: out of device memory"); return MG_ENOMEM; }
         }
-        WADR_CHECK(cp2d(ck[b][0], l1.pitch, (const char*)u0 + I.off * 16, l1.n, l1.n));
-        WADR_CHECK(cp2d((char*)l1.vec + (size_t)SG * l1.slot_stride * 16, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n));
+        WADR_CHECK(cp2d(ck[b][0], l1.pitch, (const char*)u0 + I.off * 16, l1.n, l1.n, l1.ny));
+        WADR_CHECK(cp2d((char*)l1.vec + (size_t)SG * l1.slot_stride * 16, l1.pitch, (const char*)g + I.off * 16, l1.n,
+                        l1.n, l1.ny));
         WADR_CHECK(cudaMemcpyAsync((char*)l1.vec + (size_t)SX2 * l1.slot_stride * 16, ck[b][0], l1.slot_stride * 16,
                                    cudaMemcpyDeviceToDevice, st));
     }
@@ -1287,8 +1286,8 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
             set_error("mg_cycle_backward: out of device memory");
             return MG_ENOMEM;
         }
-        WADR_CHECK(cp2d(B.ub, l1.pitch, (const char*)gbar_uK + I.off * 16, l1.n, l1.n));
-        WADR_CHECK(cp2d(B.gd, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n));
+        WADR_CHECK(cp2d(B.ub, l1.pitch, (const char*)gbar_uK + I.off * 16, l1.n, l1.n, l1.ny));
+        WADR_CHECK(cp2d(B.gd, l1.pitch, (const char*)g + I.off * 16, l1.n, l1.n, l1.ny));
     }
     cudaEvent_t ev_ready = nullptr;
     WADR_CHECK(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
@@ -1350,9 +1349,9 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
         double2* ub = bf[b].ub;
         if (grad_u0) {
             // grad_u0 += ub
-            std::vector<double2> hu((size_t)l1.n * l1.n), hg((size_t)l1.n * l1.n);
+            std::vector<double2> hu((size_t)l1.n * l1.ny), hg((size_t)l1.n * l1.ny);
             WADR_CHECK(cudaMemcpy2DAsync(hu.data(), (size_t)l1.n * 16, ub, (size_t)l1.pitch * 16, (size_t)l1.n * 16,
-                                         l1.n, cudaMemcpyDeviceToHost, sb));
+                                         l1.ny, cudaMemcpyDeviceToHost, sb));
             WADR_CHECK(cudaMemcpyAsync(hg.data(), (const char*)grad_u0 + I.off * 16, hg.size() * 16, cudaMemcpyDefault, sb));
             WADR_CHECK(cudaStreamSynchronize(sb));
             for (size_t q = 0; q < hu.size(); ++q) { hg[q].x += hu[q].x; hg[q].y += hu[q].y; }
@@ -1371,7 +1370,7 @@ extern "C" int mg_cycle_backward(mg_handle* h, const void* u0, const void* g, in
             WADR_CHECK(cudaStreamSynchronize(sb));
         }
         if (grad_phi) {
-            std::vector<double> gp((size_t)I.n * I.n);
+            std::vector<double> gp((size_t)I.n * I.ny);
             WADR_CHECK(cudaMemcpyAsync(gp.data(), grad_phi + I.off, gp.size() * 8, cudaMemcpyDefault, sb));
             WADR_CHECK(cudaStreamSynchronize(sb));
             chain_to_phi(I, A.lv, sb, gp.data());

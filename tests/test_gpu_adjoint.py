@@ -65,6 +65,35 @@ def test_adjoint_matches_reference_gradient(n, omega, ncm, M):
         assert abs(gw[l - 1] - g) < 1e-6 * abs(g), (l, gw[l - 1], g)
 
 
+@pytest.mark.parametrize("n,ny", [(63, 31), (31, 63), (95, 47)])
+def test_adjoint_non_square_matches_reference_gradient(n, ny):
+    """n x ny levels (coarsening both sides together): phi, weight and u0
+    gradients against autograd through the oracle cycle on the same grid."""
+    h = 1.0 / (max(n, ny) + 1)
+    x0 = ((int(0.43 * (n + 1)) + 0.5) * h, (int(0.31 * (ny + 1)) + 0.5) * h)
+    I = synth.config_layered_rect(n=n, ny=ny, omega=0.6 * (max(n, ny) + 1), seed=12, x0=x0)
+    H = Hierarchy(n, I.k, I.phi, I.omega, I.bc, CycleParams(n_cmax=7, M=2), ny=ny)
+    K = 2
+    loss_r, gphi_r, gw_r, ga_r, uK_r = loss_and_grads(H, I.g, I.phi, K)
+    hd = B.mg_setup([(n, I.omega, I.k, I.phi, I.bc, ny)], B.default_params(precision="fp64", n_cmax=7, M=2))
+    u = np.zeros_like(I.g)
+    B.mg_cycle(hd, u, I.g.copy(), K)
+    lev = H.lev(1)
+    r = I.g - helmholtz_apply(lev, u)
+    gphi = np.zeros_like(I.phi)
+    gw = np.zeros(B.MG_MAX_LEVELS)
+    gu0 = np.zeros_like(I.g)
+    B.mg_cycle_backward(hd, np.zeros_like(I.g), I.g.copy(), K, -2.0 * helmholtz_apply_h(lev, r), gphi, gw, gu0)
+    B.mg_destroy(hd)
+    assert rel(u, uK_r) < 1e-7
+    assert abs(float(np.sum(np.abs(r) ** 2)) - loss_r) < 1e-7 * loss_r
+    assert rel(gphi, gphi_r) < 1e-5, rel(gphi, gphi_r)
+    assert abs(gw[0] - gw_r) < 1e-6 * abs(gw_r)
+    for l, g in ga_r.items():
+        assert abs(gw[l - 1] - g) < 1e-6 * abs(g), (l, gw[l - 1], g)
+    assert np.all(np.isfinite(gu0)) and np.abs(gu0).max() > 0
+
+
 def test_adjoint_matches_finite_differences_of_gpu_forward():
     n, omega, ncm, M = 63, 30.0, 7, 2
     I, H = setup_case(n, omega, ncm, M, seed=5)
