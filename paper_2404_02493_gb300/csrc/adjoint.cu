@@ -806,7 +806,7 @@ struct Adjoint {
         T->b = b;
         if (l == I.L) {
             AdjLevel& L = lv[l];
-            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_adr, b, x_out, 0, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, (const double2*)I.lv[l - 1].inv_adr, b, x_out, 0, 0);
             T->coarse_x = x_out;
             return T;
         }
@@ -834,7 +834,7 @@ struct Adjoint {
             AdjLevel& L = lv[l];
             // x = X b: bbar += X^H xbar ; L_bar = -bbar_new x^H
             double2* bb = get(l);
-            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, (const double2*)I.lv[l - 1].inv_adr, xbar, bb, 1, 0);
             lin(l, bbar, true, bb, 1.0);
             adr_grad(l, bb, T->coarse_x, -1.0);
             put(l, bb);
@@ -943,7 +943,7 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         if (l == I.L) {
             // from zero: u = A^{-1} g
-            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_helm, g, u_out, 0, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, (const double2*)I.lv[l - 1].inv_helm, g, u_out, 0, 0);
             return T;
         }
         const double wj = I.omega_j;
@@ -1025,7 +1025,7 @@ struct Adjoint {
         AdjLevel& L = lv[l];
         if (l == I.L) {
             double2* gb = get(l);
-            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, I.lv[l - 1].inv_helm, uob, gb, 1, 0);
+            ka_gemv<<<(L.n * L.ny + GEMV_ROWS - 1) / GEMV_ROWS, ANT, 0, st>>>(L.n, L.ny, L.pitch, (const double2*)I.lv[l - 1].inv_helm, uob, gb, 1, 0);
             lin(l, gbar, true, gb, 1.0);
             put(l, gb);
             return;

@@ -81,8 +81,8 @@ struct LevelDesc {
     const void* sig;        // sponge term w*gamma*s^2 (T) or null
     const void* adr;        // ADR coefficients quad<T> (phix, phiy, d.re, d.im) or null
     const void* mod;        // exp(+i w phi) (cplx<T>), level 2 only, or null
-    const double2* inv_helm;  // coarsest level: dense inverse of A (FP64), N x N
-    const double2* inv_adr;   // coarsest level: dense inverse of L_ADR (FP64)
+    const void* inv_helm;   // coarsest level: dense inverse of A (cplx<T>), N x N
+    const void* inv_adr;    // coarsest level: dense inverse of L_ADR (cplx<T>)
     void* scal;             // scalar area (see namespace S), working precision T
     void* part;             // reduction partials [max_blocks][MAXDOT] of cplx<T>
     unsigned* counter;      // last-block counters [NCOUNTERS]

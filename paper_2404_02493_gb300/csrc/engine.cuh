@@ -621,8 +621,8 @@ struct Engine : EngineBase {
 
     void coarse_solve(Handle& H, const std::vector<int>& I, int level, int which, cudaStream_t st) {
         const SegTable& t = H.seg_rows(which ? adescs(H, level, I) : descs(H, level, I), NT / 32);
-        // the dense FP64 inverse is read once, plus the two vectors
-        go(H, st, KK_COARSE, 16.0 * (double)t.mat + 2 * C * (double)t.pts, [&] {
+        // the dense inverse (cycle precision) is read once, plus the two vectors
+        go(H, st, KK_COARSE, C * (double)t.mat + 2 * C * (double)t.pts, [&] {
             kl(k_coarse<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, which);
         }, t.pts);
     }

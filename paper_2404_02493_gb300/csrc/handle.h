@@ -29,8 +29,8 @@ struct LevelHost {
     double* k64 = nullptr;          // k in FP64 (setup, outer loop at level 1)
     double* phi64 = nullptr;        // phi in FP64 (setup, adjoint)
     double* sig64 = nullptr;        // sponge term in FP64 or null
-    double2* inv_helm = nullptr;    // coarsest only
-    double2* inv_adr = nullptr;
+    void* inv_helm = nullptr;       // coarsest only: dense inverses in the cycle precision
+    void* inv_adr = nullptr;
     double lam_max = 0, alpha = 0;  // Chebyshev interval (levels with Chebyshev)
     double peclet = 0;              // ADR levels: omega h max(|phi_x|, |phi_y|) (condition: <= 1)
     double omega_j = 0;             // Jacobi levels: the damping weight
@@ -185,7 +185,7 @@ int setup_check_fields(const double* k, const double* phi, int n, int ny, double
 double setup_peclet(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch, double h,
                     double omega, int bc, double* dscratch, cudaStream_t st);
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
-                         double h, double omega, int bc, double shift, int which, int adr_flags, double2* inv,
+                         double h, double omega, int bc, double shift, int which, int adr_flags, void* inv, int single,
                          cudaStream_t st);
 
 #define WADR_CHECK(x)                                                                   \

@@ -853,40 +853,45 @@ __global__ void __launch_bounds__(NT) k_resdemod(const __grid_constant__ KDesc A
 
 
 // ----------------------------------------------------------- coarsest level
-// x = A^{-1} b with the dense FP64 inverse formed at setup from the LU
-// factors.  One warp per matrix row; the right-hand side is staged in shared
-// memory (n_L^2 <= 1024).  which: 0 Helmholtz (SG -> SU), 1 ADR (SAB -> SAX).
+// x = A^{-1} b with the dense inverse formed at setup from the LU factors in
+// FP64 and stored in the cycle precision T (N = n ny <= 1024 rows).  The
+// complex-FP32 cycle applies it in FP32: FP64 arithmetic issues at a small
+// fraction of the FP32 rate on this GPU, and the rounding of the inverse
+// moves the cycle by about 1e-7 relative, below its own FP32 rounding.  One
+// warp per matrix row; the right-hand side is staged in shared memory.
+// which: 0 Helmholtz (SG -> SU), 1 ADR (SAB -> SAX).
 constexpr int MAXCOARSE = 1024;
 template <typename T>
 __global__ void __launch_bounds__(NT) k_coarse(const __grid_constant__ KDesc A, const Seg* __restrict__ Sg,
                                                int nseg, int which) {
     __shared__ LevelDesc d;
-    __shared__ double2 bsh[MAXCOARSE];
+    __shared__ cplx<T> bsh[MAXCOARSE];
     SegCtx c = seg_begin(A, Sg, nseg, d);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int n = d.n, N = n * d.ny;
     const cplx<T>* b = slot<T>(d, which ? SAB : SG);
     cplx<T>* x = slot<T>(d, which ? SAX : SU);
-    const double2* Ainv = which ? d.inv_adr : d.inv_helm;
+    const cplx<T>* Ainv = reinterpret_cast<const cplx<T>*>(which ? d.inv_adr : d.inv_helm);
     for (int q = tid; q < N; q += NT) {
         const int i = q % n, j = q / n;
-        bsh[q] = to_d(__ldg(b + (long long)j * d.pitch + i));
+        bsh[q] = __ldg(b + (long long)j * d.pitch + i);
     }
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5;
     for (int row = c.lb * (NT / 32) + wid; row < N; row += c.nb * (NT / 32)) {
-        const double2* a = Ainv + (long long)row * N;
+        const cplx<T>* a = Ainv + (long long)row * N;
         // four fused multiply-adds per complex term into four independent
-        // accumulators (columns q mod 128 in four groups of 32): a dependent
-        // FP64 FMA is slow on this GPU, so one chain per lane would set the
-        // time
-        double2 ac[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+        // accumulators (columns q mod 128 in four groups of 32), so that no
+        // single dependent FMA chain sets the time
+        cplx<T> ac[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ac[u].x = ac[u].y = T(0);
         for (int q0 = lane; q0 < N; q0 += 128) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int q = q0 + 32 * u;
                 if (q < N) {
-                    const double2 av = __ldg(a + q), bv = bsh[q];
+                    const cplx<T> av = __ldg(a + q), bv = bsh[q];
                     ac[u].x = fma(av.x, bv.x, ac[u].x);
                     ac[u].x = fma(-av.y, bv.y, ac[u].x);
                     ac[u].y = fma(av.x, bv.y, ac[u].y);
@@ -894,7 +899,9 @@ __global__ void __launch_bounds__(NT) k_coarse(const __grid_constant__ KDesc A, 
                 }
             }
         }
-        double2 acc = dadd(dadd(ac[0], ac[1]), dadd(ac[2], ac[3]));
+        cplx<T> acc;
+        acc.x = (ac[0].x + ac[1].x) + (ac[2].x + ac[3].x);
+        acc.y = (ac[0].y + ac[1].y) + (ac[2].y + ac[3].y);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
@@ -902,7 +909,7 @@ __global__ void __launch_bounds__(NT) k_coarse(const __grid_constant__ KDesc A, 
         }
         if (lane == 0) {
             const int i = row % n, j = row / n;
-            x[(long long)j * d.pitch + i] = from_d<T>(acc);
+            x[(long long)j * d.pitch + i] = acc;
         }
     }
 }

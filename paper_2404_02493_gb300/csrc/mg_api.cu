@@ -486,8 +486,8 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             if (adr && l == I.la) lv.mod = H.alloc(npt * esz(prec));
             if (l == I.L) {
                 const size_t N = (size_t)lv.n * lv.ny;
-                lv.inv_helm = (double2*)H.alloc(N * N * sizeof(double2));
-                if (adr) lv.inv_adr = (double2*)H.alloc(N * N * sizeof(double2));
+                lv.inv_helm = H.alloc(N * N * esz(prec));
+                if (adr) lv.inv_adr = H.alloc(N * N * esz(prec));
             }
             if (!lv.vec || !lv.kf || !lv.k64 || !lv.phi64) { set_error("mg_setup: out of device memory"); return MG_ENOMEM; }
             cudaMemsetAsync(lv.vec, 0, npt * lv.nslot * esz(prec), st);
@@ -515,7 +515,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                     v.adr = H.alloc(npt * 2 * esz(prec));
                     if (l == 2) v.mod = H.alloc(npt * esz(prec));
                     if (l == I.L)
-                        v.inv_adr = (double2*)H.alloc((size_t)v.n * v.ny * v.n * v.ny * sizeof(double2));
+                        v.inv_adr = H.alloc((size_t)v.n * v.ny * v.n * v.ny * esz(prec));
                     if (!v.phi64 || !v.adr || (l == 2 && !v.mod) || (l == I.L && !v.inv_adr)) {
                         set_error("mg_setup: out of device memory (Wave-Ray levels)");
                         return MG_ENOMEM;
@@ -661,11 +661,11 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
             }
             if (l == I.L) {
                 int r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.omega, I.bc,
-                                             p.shift, 0, 0, lv.inv_helm, st);
+                                             p.shift, 0, 0, lv.inv_helm, prec == MG_PREC_MIXED, st);
                 if (r) return r;
                 if (lv.inv_adr) {
                     r = setup_coarse_inverse(lv.k64, lv.phi64, lv.sig64, lv.n, lv.ny, lv.pitch, lv.h, I.omega, I.bc,
-                                             p.shift, 1, I.adr_flags, lv.inv_adr, st);
+                                             p.shift, 1, I.adr_flags, lv.inv_adr, prec == MG_PREC_MIXED, st);
                     if (r) return r;
                 }
             }
@@ -696,7 +696,7 @@ static int build(mg_handle* mh, const mg_instance* in, int ninst, cudaStream_t s
                 d.coarse = (l < I.L) ? di + 1 : -1;
                 if (l == I.L) {
                     int r = setup_coarse_inverse(v.k64, v.phi64, v.sig64, v.n, v.ny, v.pitch, v.h, I.omega, I.bc,
-                                                 p.shift, 1, I.adr_flags, v.inv_adr, st);
+                                                 p.shift, 1, I.adr_flags, v.inv_adr, prec == MG_PREC_MIXED, st);
                     if (r) return r;
                 }
                 H.hdesc.push_back(d);

@@ -298,26 +298,44 @@ __global__ void k_lu_inv(const double2* LU, const int* perm, int N, double2* inv
     }
 }
 
+// FP64 inverse -> complex FP32 (round to nearest)
+__global__ void k_inv_to_c64(const double2* src, float2* dst, long long m) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) dst[q] = make_float2((float)src[q].x, (float)src[q].y);
+}
+
+// The dense inverse is always formed in FP64 (LU with partial pivoting, then
+// one triangular solve pair per column); single != 0 stores it rounded to
+// complex FP32 for the complex-FP32 cycle, else as complex FP64.
 int setup_coarse_inverse(const double* k64, const double* phi64, const double* sig64, int n, int ny, int pitch,
-                         double h, double omega, int bc, double shift, int which, int adr_flags, double2* inv,
+                         double h, double omega, int bc, double shift, int which, int adr_flags, void* inv, int single,
                          cudaStream_t st) {
     const int N = n * ny;
+    const long long NN = (long long)N * N;
     double2* A = nullptr;
+    double2* inv64 = single ? nullptr : (double2*)inv;
     int* perm = nullptr;
     int* info = nullptr;
-    if (cudaMalloc(&A, sizeof(double2) * (size_t)N * N) != cudaSuccess) return MG_ENOMEM;
+    if (cudaMalloc(&A, sizeof(double2) * (size_t)NN) != cudaSuccess) return MG_ENOMEM;
     if (cudaMalloc(&perm, sizeof(int) * (N + 1)) != cudaSuccess) { cudaFree(A); return MG_ENOMEM; }
+    if (single && cudaMalloc(&inv64, sizeof(double2) * (size_t)NN) != cudaSuccess) {
+        cudaFree(A);
+        cudaFree(perm);
+        return MG_ENOMEM;
+    }
     info = perm + N;
     cudaMemsetAsync(info, 0, sizeof(int), st);
     k_dense<<<(N + 127) / 128, 128, 0, st>>>(k64, phi64, sig64, n, ny, pitch, h, omega, bc, shift, which, adr_flags,
                                               A);
     k_lu<<<1, 1024, 0, st>>>(A, N, perm, info);
-    k_lu_inv<<<(N + 63) / 64, 64, 0, st>>>(A, perm, N, inv);
+    k_lu_inv<<<(N + 63) / 64, 64, 0, st>>>(A, perm, N, inv64);
+    if (single) k_inv_to_c64<<<(unsigned)((NN + 255) / 256), 256, 0, st>>>(inv64, (float2*)inv, NN);
     int hinfo = 0;
     cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     cudaFree(A);
     cudaFree(perm);
+    if (single) cudaFree(inv64);
     if (e != cudaSuccess) {
         set_error(std::string("coarse LU: ") + cudaGetErrorString(e));
         return MG_ECUDA;

@@ -10,7 +10,7 @@
 //                shared memory; x of each level goes to its SAX slot and the
 //                restricted right-hand sides to the SAB slots of the levels
 //                below (the coarsest one included)
-//   k_coarse     the FP64 coarsest solve of the multi-launch path
+//   k_coarse     the coarsest solve of the multi-launch path
 //   k_adr_up     one block per instance; for levels L-1 .. l0: x' = x + P e,
 //                r0 = b - L x', GMRES(3) from x', x = x' + z; the result of
 //                level l0 goes to its SAX slot

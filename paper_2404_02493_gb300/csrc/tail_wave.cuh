@@ -10,7 +10,7 @@
 //                Chebyshev steps from x = 0 on the level's g, x to its SU
 //                slot, the residual g - A x restricted by full weighting to
 //                the SG slot of level l+1 (the coarsest one included)
-//   k_coarse     the FP64 coarsest solve of the multi-launch path
+//   k_coarse     the coarsest solve of the multi-launch path
 //   k_wave_up    one block per instance; for l = L-1 .. l0: x' = x + P e
 //                (e the result of level l+1), q Chebyshev steps from x', the
 //                result to the level's SU slot

@@ -78,7 +78,11 @@ def test_solve_reports_not_converged_at_maxit():
 @pytest.mark.parametrize("prec,outer", [("mixed", "fgmres"), ("fp64", "ir")])
 def test_solve_reports_divergence_on_nonfinite_rhs(prec, outer):
     I = _inst()
-    h = lib_handle([I], prec, n_cmax=7, maxit=5, outer=outer)
+    # one fixed halo-tile candidate: the autotuner's timed choice sets the
+    # summation order of the Gram sums, so two handles agree to the last bit
+    # only with the same choice
+    kw = dict(n_cmax=7, maxit=5, outer=outer, tile_candidate=3)
+    h = lib_handle([I], prec, **kw)
     try:
         g = I.g.copy()
         g[3, 3] = np.nan
@@ -90,7 +94,7 @@ def test_solve_reports_divergence_on_nonfinite_rhs(prec, outer):
         st2, it2, rr2, _, _ = B.mg_solve(h, u2, I.g.copy())
     finally:
         B.mg_destroy(h)
-    h = lib_handle([I], prec, n_cmax=7, maxit=5, outer=outer)
+    h = lib_handle([I], prec, **kw)
     try:
         u3 = np.zeros_like(I.g)
         st3, it3, rr3, _, _ = B.mg_solve(h, u3, I.g.copy())
