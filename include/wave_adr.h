@@ -455,6 +455,18 @@ int mg_eikonal_rect(int n, int ny, const double* s, double x0, double y0, double
 int mg_residual_norm_noalloc(int n, double omega, const double* k, int bc, const void* u, const void* g, void* r,
                              double* norm2, mg_stream stream);
 
+/* mg_residual_norm_noalloc_rect: the same on a grid of ny rows of n nodes
+ * (the non-square domains of Section 4.3.3; h = 1/(max(n, ny)+1), the
+ * longer side of unit length, k, u, g and r dense with ny rows of n), with
+ * the sponge profile's width (in wavelengths) and exponent as in mg_params
+ * (sponge_width in (0, 1e6), sponge_power in (0, 1e3); 1 and 2 give the
+ * profile of mg_residual_norm_noalloc).  n and ny must be in 1..32768;
+ * MG_EINVAL otherwise or for a bad pointer, bc or sponge parameter.  Same
+ * scratch, asynchrony and ordering rules as mg_residual_norm_noalloc, which
+ * is this call with ny = n, sponge_width = 1 and sponge_power = 2. */
+int mg_residual_norm_noalloc_rect(int n, int ny, double omega, const double* k, int bc, const void* u, const void* g,
+                                  void* r, double* norm2, double sponge_width, double sponge_power, mg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

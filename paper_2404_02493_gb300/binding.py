@@ -97,6 +97,7 @@ def load():
         "mg_kernel_name": (ctypes.c_char_p, [ip]),
         "mg_step_launches": (ip, [vp]),
         "mg_residual_norm_noalloc": (ip, [ip, dp, vp, ip, vp, vp, vp, vp, vp]),
+        "mg_residual_norm_noalloc_rect": (ip, [ip, ip, dp, vp, ip, vp, vp, vp, vp, dp, dp, vp]),
         "mg_profile_records": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(ip), ip, vp]),
         "mg_cycle_backward": (ip, [vp, vp, vp, ip, vp, vp, vp, vp, vp]),
@@ -125,7 +126,8 @@ def exported_symbols():
             "mg_restrict_residual", "mg_prolong_add", "mg_jacobi", "mg_chebyshev", "mg_gmres3",
             "mg_adr_vcycle", "mg_adr_correction", "mg_coarse_solve", "mg_cycle_launches", "mg_abi_sizes",
             "mg_solve_begin", "mg_solve_steps", "mg_solve_end", "mg_profile_steps", "mg_kernel_name",
-            "mg_step_launches", "mg_residual_norm_noalloc", "mg_profile_records", "mg_cycle_backward",
+            "mg_step_launches", "mg_residual_norm_noalloc", "mg_residual_norm_noalloc_rect", "mg_profile_records",
+            "mg_cycle_backward",
             "mg_tile_shapes", "mg_selftest_wait_timeout", "mg_peclet_flags",
             "mg_workspace_bytes", "mg_level_roles", "mg_level_shapes", "mg_eikonal", "mg_eikonal_rect"]
 
@@ -410,6 +412,16 @@ def mg_residual_norm_noalloc(n, omega, k, bc, u, g, r, norm2, stream=None):
     bc = MG_BC[bc] if isinstance(bc, str) else int(bc)
     _check(load().mg_residual_norm_noalloc(int(n), float(omega), _ptr(k), bc, _ptr(u), _ptr(g), _ptr(r),
                                            _ptr(norm2), _stream(stream)), "mg_residual_norm_noalloc")
+
+
+def mg_residual_norm_noalloc_rect(n, ny, omega, k, bc, u, g, r, norm2, sponge_width=1.0, sponge_power=2.0,
+                                  stream=None):
+    """The same on ny rows of n nodes with the sponge profile's width and
+    exponent; allocates nothing."""
+    bc = MG_BC[bc] if isinstance(bc, str) else int(bc)
+    _check(load().mg_residual_norm_noalloc_rect(int(n), int(ny), float(omega), _ptr(k), bc, _ptr(u), _ptr(g), _ptr(r),
+                                                _ptr(norm2), float(sponge_width), float(sponge_power),
+                                                _stream(stream)), "mg_residual_norm_noalloc_rect")
 
 
 def mg_profile_records(h, nsteps, stream=None, maxrec=256):

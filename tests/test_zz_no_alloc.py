@@ -103,3 +103,39 @@ def test_noalloc_rejects_sizes_beyond_the_maximum(torch_cuda):
         with pytest.raises(B.MgError) as e:
             B.mg_residual_norm_noalloc(n, 1.0, k, "abc1", x, x, x, nrm)
         assert e.value.code == B.MG_EINVAL
+
+
+@pytest.mark.parametrize("n,ny,bc,width,power", [(63, 31, "abc1", 1.0, 2.0), (31, 63, "sponge", 1.0, 2.0),
+                                                 (95, 47, "sponge", 1.5, 1.0), (255, 129, "dirichlet", 1.0, 2.0),
+                                                 (3, 1, "abc1", 1.0, 2.0)])
+def test_noalloc_rect_matches_oracle(torch_cuda, n, ny, bc, width, power):
+    """ny rows of n nodes (h = 1/(max(n, ny)+1)) with the sponge profile's
+    width and exponent: residual and norm against the oracle's on the same
+    grid, 1e-13; with ny = n, width 1 and power 2 the square entry point."""
+    torch = torch_cuda
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(n + ny)
+    h = 1.0 / (max(n, ny) + 1)
+    omega = 0.4 / h
+    k = omega * (0.6 + 0.4 * rng.random((ny, n)))
+    lev = Level(n=n, ny=ny, h=h, k=k, phi=np.zeros((ny, n)),
+                gamma=sponge_gamma(n, omega, ny, width, power) if bc == "sponge" else np.zeros((ny, n)),
+                omega=omega, bc=bc)
+    for call in range(2):
+        u = rng.standard_normal((ny, n)) + 1j * rng.standard_normal((ny, n))
+        g = rng.standard_normal((ny, n)) + 1j * rng.standard_normal((ny, n))
+        kk = torch.from_numpy(np.ascontiguousarray(k)).to(dev)
+        ut, gt = torch.from_numpy(u).to(dev), torch.from_numpy(g).to(dev)
+        r = torch.empty_like(ut)
+        norm2 = torch.empty(1, dtype=torch.float64, device=dev)
+        B.mg_residual_norm_noalloc_rect(n, ny, omega, kk, bc, ut, gt, r, norm2, width, power)
+        torch.cuda.synchronize()
+        r_or = helmholtz_residual(lev, u, g)
+        assert np.linalg.norm(r.cpu().numpy() - r_or) <= 1e-13 * np.linalg.norm(r_or)
+        assert abs(norm2.item() - np.vdot(r_or, r_or).real) <= 1e-13 * norm2.item()
+    x = torch.zeros(4, dtype=torch.complex128, device=dev)
+    kx = torch.ones(4, dtype=torch.float64, device=dev)
+    for args in ((2, 0, 1.0, 2.0), (2, 32769, 1.0, 2.0), (2, 2, 0.0, 2.0), (2, 2, 1.0, -1.0)):
+        with pytest.raises(B.MgError) as e:
+            B.mg_residual_norm_noalloc_rect(args[0], args[1], 1.0, kx, "sponge", x, x, x, kx, args[2], args[3])
+        assert e.value.code == B.MG_EINVAL
