@@ -619,8 +619,17 @@ struct Engine : EngineBase {
         return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ECUDA;
     }
 
-    void coarse_solve(Handle& H, const std::vector<int>& I, int level, int which, cudaStream_t st) {
-        const SegTable& t = H.seg_rows(which ? adescs(H, level, I) : descs(H, level, I), NT / 32);
+    // Dense coarsest solve of the instances I, each on its own coarsest level
+    // (level L of instance b is H.inst[b].L): instances of different depth
+    // share one launch, as k_coarse reads every segment's own descriptor.
+    void coarse_solve(Handle& H, const std::vector<int>& I, int which, cudaStream_t st) {
+        std::vector<int> ds;
+        ds.reserve(I.size());
+        for (int b : I) {
+            const std::vector<int> one{b};
+            ds.push_back(which ? adescs(H, H.inst[b].L, one)[0] : descs(H, H.inst[b].L, one)[0]);
+        }
+        const SegTable& t = H.seg_rows(ds, NT / 32);
         // the dense inverse (cycle precision) is read once, plus the two vectors
         go(H, st, KK_COARSE, C * (double)t.mat + 2 * C * (double)t.pts, [&] {
             kl(k_coarse<T>, t.nblocks, dim3(BX, BY), 0, st, kd(H, t), t.d, t.nseg, which);
@@ -679,9 +688,7 @@ struct Engine : EngineBase {
         go(H, st, KK_ADR_TAIL, ((3 * C + Q) + (4 * C + Q + C / 4)) * (double)pts, [&] {
             k_adr_down<T><<<nb, TS_THREADS, (size_t)sd, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst);
         }, pts);
-        std::map<int, std::vector<int>> byL;
-        for (int b : tail) byL[H.inst[b].L].push_back(b);
-        for (auto& g : byL) coarse_solve(H, g.second, g.first, 1, st);
+        coarse_solve(H, tail, 1, st);   // every depth in one launch
         go(H, st, KK_ADR_TAIL, ((4 * C + Q + C) + (3 * C + Q) + 5 * C) * (double)pts, [&] {
             k_adr_up<T><<<nb, TS_THREADS, (size_t)su, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst);
         }, pts);
@@ -741,9 +748,7 @@ struct Engine : EngineBase {
         go(H, st, KK_WAVE_TAIL, (cheb_zero + 2 * C + R + C / 4) * (double)pts, [&] {
             k_wave_down<T><<<nb, WT_THREADS, (size_t)sm, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst, q);
         }, pts);
-        std::map<int, std::vector<int>> byL;
-        for (int b : tail) byL[H.inst[b].L].push_back(b);
-        for (auto& g : byL) coarse_solve(H, g.second, g.first, 0, st);
+        coarse_solve(H, tail, 0, st);   // every depth in one launch
         go(H, st, KK_WAVE_TAIL, (2 * C + C / 4 + cheb_x) * (double)pts, [&] {
             k_wave_up<T><<<nb, WT_THREADS, (size_t)sm, st>>>((const LevelDesc*)H.ddesc, (const int*)dfirst, q);
         }, pts);
@@ -766,19 +771,29 @@ struct Engine : EngineBase {
     // exp(+i w phi) a to the wave iterate SU).  With `defer` (a recursive
     // call) the post-smoothing update of the per-level instances is left to
     // the caller's prolongation (PMODE_ADRF), which forms the result on the
-    // fly; SAX of this level is then not written.
-    void adrv(Handle& H, int l, const std::vector<int>& I, bool modulate, cudaStream_t st, bool defer = false) {
-        std::vector<int> co, rest0, tail, rest;
+    // fly; SAX of this level is then not written.  The coarsest solves of
+    // instances that end above the deepest level reached are owed (`owed`)
+    // and run in one launch with those of the deepest instances: each
+    // instance's coarse SAX is read only by its own prolongation, after the
+    // recursion returns.
+    void adrv(Handle& H, int l, const std::vector<int>& I, bool modulate, cudaStream_t st, bool defer = false,
+              std::vector<int>* owed = nullptr) {
+        std::vector<int> co, rest0, tail, rest, mine;
         for (int b : I) (H.inst[b].L == l ? co : rest0).push_back(b);
-        if (!co.empty()) coarse_solve(H, co, l, 1, st);
         for (int b : rest0) (adr_per_level(H, b, l) ? rest : tail).push_back(b);
+        std::vector<int>& due = owed ? *owed : mine;
+        due.insert(due.end(), co.begin(), co.end());
+        if (rest.empty() && !due.empty()) {
+            coarse_solve(H, due, 1, st);
+            due.clear();
+        }
         if (!tail.empty()) launch_tail_smem(H, l, tail, st);
         if (rest.empty()) return;
         const std::vector<int> ds = adescs(H, l, rest);
         const TileChoice tc = tiles_of(H, ds);
         gs_gram(H, ds, tc.gram, SAB, st);   // pre-smoothing from x = 0: r0 = b
         gs_pre(H, ds, tc.pre, st);          // x to SAX, restricted residual to SAB of l+1
-        adrv(H, l + 1, rest, false, st, true);
+        adrv(H, l + 1, rest, false, st, true, &due);
         // x' = x + P e, r0 = b - L x'; e is the coarse SAX (coarsest level or
         // coarse tail) or the coarse post-smoothing result formed here
         std::vector<int> plain, fused;
@@ -812,7 +827,7 @@ struct Engine : EngineBase {
         for (int b : I) (H.inst[b].L == l ? co : rest).push_back(b);
         if (!co.empty()) {
             if (H.p.coarse == MG_COARSE_LU) {
-                coarse_solve(H, co, l, 0, st);
+                coarse_solve(H, co, 0, st);
             } else {
                 cheb_steps(H, descs(H, l, co), l, H.p.coarse_cheb_iters, SU, true, st);
             }
@@ -1103,7 +1118,7 @@ struct Engine : EngineBase {
             adrv(H, level, I, true, st);
             return SU;
         case OP_COARSE:
-            coarse_solve(H, I, level, a0, st);
+            coarse_solve(H, I, a0, st);
             return a0 ? SAX : SU;
         }
         return -1;
