@@ -69,8 +69,8 @@ def test_plane_wave_zero_residual():
 
 # ------------------------------------------------------------------ P2
 def test_shifted_plane_wave_zero_residual():
-    """Shifted Helmholtz (Section 4.3.2, k^2 -> k^2 (1 + i beta) in the
-    spec convention): a plane wave whose second wavenumber is the
+    """Shifted Helmholtz (Section 4.3.2, k^2 -> k^2 (1 + i beta), the sign
+    convention of mg_params.shift): a plane wave whose second wavenumber is the
     complex root of 4 sin^2(k1 h/2) + 4 sin^2(k2 h/2) = k^2 h^2 (1 + i beta)
     is annihilated by the shifted stencil (Dirichlet ghosts moved to g).  The
     opposite sign of the shift, or no shift, leaves an O(1) residual."""
